@@ -1,0 +1,294 @@
+"""FP64 CPU oracle (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg may import this package; the product path never does.  It wraps the plain
+C implementation in ``oracle.c`` (built with gcc, OpenMP over independent
+pixels or edges) and converts every input to float64 exactly, so that the
+oracle consumes the same stored values as the GPU path (dequantised).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from typing import Dict, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lib = None
+
+DEFAULT_PARAMS: Dict = dict(
+    sigma_ray=0.01, sigma_dist=0.1, huber_delta=1.345, q_min=1.5,
+    lm_lambda=1e-8, lm_iters=10, win_radius=3, n_levels=2, win_dilation=(2, 1, 1, 1),
+    max_rel_dist3d=0.1, conv_tol=1e-10,
+)
+
+
+class _Params(C.Structure):
+    _fields_ = [
+        ("sigma_ray", C.c_double), ("sigma_dist", C.c_double), ("huber_delta", C.c_double),
+        ("q_min", C.c_double), ("lm_lambda", C.c_double), ("lm_iters", C.c_int),
+        ("win_radius", C.c_int), ("n_levels", C.c_int), ("win_dilation", C.c_int * 4),
+        ("max_rel_dist3d", C.c_double), ("conv_tol", C.c_double),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with gcc (C11, OpenMP, no FP contraction)."""
+    src = os.path.join(_HERE, "oracle.c")
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= max(
+            os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
+        return _SO
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _SO + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-fno-fast-math", "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_SO)
+        dp = C.POINTER(C.c_double)
+        ip = C.POINTER(C.c_int32)
+        lp = C.POINTER(C.c_int64)
+        pp = C.POINTER(_Params)
+        for name, args, res in [
+            ("orc_sim3_exp", [dp, dp], None), ("orc_sim3_log", [dp, dp], None),
+            ("orc_sim3_mul", [dp, dp, dp], None), ("orc_sim3_inv", [dp, dp], None),
+            ("orc_sim3_act", [dp, dp, dp], None), ("orc_sim3_matrix", [dp, dp], None),
+            ("orc_sim3_adjoint", [dp, dp], None), ("orc_sim3_retract", [dp, dp], None),
+            ("orc_ray_image", [dp, C.c_int64, dp], None),
+            ("orc_match", [pp, C.c_int, C.c_int, C.c_int, dp, dp, dp, dp, dp, dp, ip, lp, C.c_int64, ip, dp, dp],
+             None),
+            ("orc_residual_jacobian", [dp, dp, dp, dp, dp, dp], C.c_int),
+            ("orc_linearize_edge", [pp, dp, dp, C.c_int64, dp, dp, ip, dp, dp, dp, dp, lp], None),
+            ("orc_gn_solve", [C.c_int, C.c_int, ip, dp, dp, C.c_int, dp, dp], C.c_int),
+            ("orc_gauss_newton", [pp, C.c_int, C.c_int, ip, lp, lp, dp, ip, dp, C.c_int, C.c_int, dp, dp,
+                                  C.POINTER(C.c_int)], C.c_int),
+            ("orc_cost_grad", [pp, C.c_int, C.c_int, ip, lp, lp, dp, dp, ip, dp, dp, dp, dp], None),
+            ("orc_num_threads", [], C.c_int),
+        ]:
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def params(**over) -> _Params:
+    p = dict(DEFAULT_PARAMS)
+    p.update(over)
+    s = _Params()
+    for k, v in p.items():
+        if k == "win_dilation":
+            dil = list(v) + [1] * (4 - len(v))
+            s.win_dilation = (C.c_int * 4)(*dil[:4])
+        else:
+            setattr(s, k, v)
+    return s
+
+
+def _d(a) -> np.ndarray:
+    """Exact float64 copy of a torch tensor or array (dequantises fp16/fp32)."""
+    try:
+        import torch
+        if torch.is_tensor(a):
+            a = a.detach().to("cpu").to(torch.float64).numpy()
+    except ImportError:  # pragma: no cover
+        pass
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _i32(a) -> np.ndarray:
+    try:
+        import torch
+        if torch.is_tensor(a):
+            a = a.detach().to("cpu").numpy()
+    except ImportError:  # pragma: no cover
+        pass
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+def _i64(a) -> np.ndarray:
+    try:
+        import torch
+        if torch.is_tensor(a):
+            a = a.detach().to("cpu").numpy()
+    except ImportError:  # pragma: no cover
+        pass
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int64))
+
+
+def _p(a, t=C.c_double):
+    return a.ctypes.data_as(C.POINTER(t))
+
+
+# ---------------------------------------------------------------- Sim(3)
+
+def sim3_exp(tau) -> np.ndarray:
+    tau = _d(tau).reshape(7)
+    T = np.zeros(8)
+    lib().orc_sim3_exp(_p(tau), _p(T))
+    return T
+
+
+def sim3_log(T) -> np.ndarray:
+    T = _d(T).reshape(8)
+    tau = np.zeros(7)
+    lib().orc_sim3_log(_p(T), _p(tau))
+    return tau
+
+
+def sim3_mul(A, B) -> np.ndarray:
+    A, B = _d(A).reshape(8), _d(B).reshape(8)
+    out = np.zeros(8)
+    lib().orc_sim3_mul(_p(A), _p(B), _p(out))
+    return out
+
+
+def sim3_inv(A) -> np.ndarray:
+    A = _d(A).reshape(8)
+    out = np.zeros(8)
+    lib().orc_sim3_inv(_p(A), _p(out))
+    return out
+
+
+def sim3_act(T, x) -> np.ndarray:
+    T, x = _d(T).reshape(8), _d(x).reshape(3)
+    y = np.zeros(3)
+    lib().orc_sim3_act(_p(T), _p(x), _p(y))
+    return y
+
+
+def sim3_matrix(T) -> np.ndarray:
+    T = _d(T).reshape(8)
+    M = np.zeros(16)
+    lib().orc_sim3_matrix(_p(T), _p(M))
+    return M.reshape(4, 4)
+
+
+def sim3_adjoint(T) -> np.ndarray:
+    T = _d(T).reshape(8)
+    Ad = np.zeros(49)
+    lib().orc_sim3_adjoint(_p(T), _p(Ad))
+    return Ad.reshape(7, 7)
+
+
+def sim3_retract(tau, T) -> np.ndarray:
+    tau, T = _d(tau).reshape(7), _d(T).reshape(8).copy()
+    lib().orc_sim3_retract(_p(tau), _p(T))
+    return T
+
+
+def ray_image(X) -> np.ndarray:
+    X = _d(X).reshape(-1, 3)
+    R = np.zeros_like(X)
+    lib().orc_ray_image(_p(X), X.shape[0], _p(R))
+    return R
+
+
+# ---------------------------------------------------------------- matching
+
+def match(H: int, W: int, X_ref, X_qry, D_ref, D_qry, Q_ref, Q_qry, init_idx=None, pix=None,
+          diag: bool = False, **par):
+    """Projective matching plus refinement for one edge.  Returns (idx int32,
+    q float64[, diag [n, 9]]) for the query pixels `pix` (all if None)."""
+    Xr, Xq = _d(X_ref).reshape(-1, 3), _d(X_qry).reshape(-1, 3)
+    Dr, Dq = _d(D_ref), _d(D_qry)
+    d = Dr.shape[-1]
+    Dr, Dq = Dr.reshape(-1, d), Dq.reshape(-1, d)
+    Qr, Qq = _d(Q_ref).reshape(-1), _d(Q_qry).reshape(-1)
+    n = H * W if pix is None else len(pix)
+    idx = np.zeros(n, dtype=np.int32)
+    q = np.zeros(n)
+    dg = np.zeros((n, 9)) if diag else None
+    ini = _i32(init_idx) if init_idx is not None else None
+    px = _i64(pix) if pix is not None else None
+    lib().orc_match(C.byref(params(**par)), H, W, d, _p(Xr), _p(Xq), _p(Dr), _p(Dq), _p(Qr), _p(Qq),
+                    _p(ini, C.c_int32) if ini is not None else None,
+                    _p(px, C.c_int64) if px is not None else None, n,
+                    _p(idx, C.c_int32), _p(q), _p(dg) if dg is not None else None)
+    return (idx, q, dg) if diag else (idx, q)
+
+
+def match_workload(w, e: int, pix=None, diag=False, init_idx=None, **par):
+    sl = w.edge_slice(e)
+    H, W = int(w.kf_hw[w.edges[e, 1], 0]), int(w.kf_hw[w.edges[e, 1], 1])
+    return match(H, W, w.X_ref[sl], w.X_qry[sl], w.D_ref[sl], w.D_qry[sl], w.Q_ref[sl], w.Q_qry[sl],
+                 init_idx=init_idx, pix=pix, diag=diag, **par)
+
+
+# ---------------------------------------------------------------- Gauss-Newton
+
+def residual_jacobian(Ti, Tj, Xj_n, Xi_m):
+    Ti, Tj, a, b = _d(Ti).reshape(8), _d(Tj).reshape(8), _d(Xj_n).reshape(3), _d(Xi_m).reshape(3)
+    r = np.zeros(4)
+    J = np.zeros(56)
+    ok = lib().orc_residual_jacobian(_p(Ti), _p(Tj), _p(a), _p(b), _p(r), _p(J))
+    return bool(ok), r, J.reshape(4, 14)
+
+
+def linearize_edge(Ti, Tj, X_i, X_j, idx, q, **par):
+    Ti, Tj = _d(Ti).reshape(8), _d(Tj).reshape(8)
+    Xi, Xj = _d(X_i).reshape(-1, 3), _d(X_j).reshape(-1, 3)
+    idx = _i32(idx).reshape(-1)
+    q = _d(q).reshape(-1)
+    H = np.zeros(196)
+    g = np.zeros(14)
+    c = np.zeros(1)
+    nv = np.zeros(1, dtype=np.int64)
+    lib().orc_linearize_edge(C.byref(params(**par)), _p(Ti), _p(Tj), idx.shape[0], _p(Xi), _p(Xj),
+                             _p(idx, C.c_int32), _p(q), _p(H), _p(g), _p(c), _p(nv, C.c_int64))
+    return H.reshape(14, 14), g, float(c[0]), int(nv[0])
+
+
+def gn_solve(N, edges, H14, g14, T, gauge=0):
+    edges = _i32(edges).reshape(-1, 2)
+    H14 = _d(H14).reshape(-1, 196)
+    g14 = _d(g14).reshape(-1, 14)
+    T = _d(T).reshape(N, 8).copy()
+    tau = np.zeros((N, 7))
+    st = lib().orc_gn_solve(N, edges.shape[0], _p(edges, C.c_int32), _p(H14), _p(g14), gauge, _p(T), _p(tau))
+    return st, T, tau
+
+
+def gauss_newton(N, edges, kf_off, e_off, X_canon, idx, q, T, iters, gauge=0, **par):
+    edges = _i32(edges).reshape(-1, 2)
+    kf_off, e_off = _i64(kf_off), _i64(e_off)
+    X = _d(X_canon).reshape(-1, 3)
+    idx = _i32(idx).reshape(-1)
+    q = _d(q).reshape(-1)
+    T = _d(T).reshape(N, 8).copy()
+    hist = np.zeros(max(iters, 1))
+    done = C.c_int(0)
+    st = lib().orc_gauss_newton(C.byref(params(**par)), N, edges.shape[0], _p(edges, C.c_int32),
+                                _p(kf_off, C.c_int64), _p(e_off, C.c_int64), _p(X), _p(idx, C.c_int32), _p(q),
+                                iters, gauge, _p(T), _p(hist), C.byref(done))
+    return st, T, hist[:done.value], done.value
+
+
+def cost_grad(N, edges, kf_off, e_off, T, X_canon, idx, q, **par):
+    edges = _i32(edges).reshape(-1, 2)
+    kf_off, e_off = _i64(kf_off), _i64(e_off)
+    X = _d(X_canon).reshape(-1, 3)
+    idx = _i32(idx).reshape(-1)
+    q = _d(q).reshape(-1)
+    T = _d(T).reshape(N, 8)
+    dX = np.zeros_like(X)
+    dq = np.zeros_like(q)
+    c = np.zeros(1)
+    lib().orc_cost_grad(C.byref(params(**par)), N, edges.shape[0], _p(edges, C.c_int32), _p(kf_off, C.c_int64),
+                        _p(e_off, C.c_int64), _p(T), _p(X), _p(idx, C.c_int32), _p(q), _p(dX), _p(dq), _p(c))
+    return float(c[0]), dX, dq
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())

@@ -1,0 +1,240 @@
+/*
+ * mslam.h -- C ABI of the GB300 (sm_103a) library for the data-parallel hot
+ * path of MASt3R-SLAM (Murai, Dexheimer, Davison, arXiv 2412.12392):
+ * iterative projective matching of two-view pointmaps (Sec. 3.2) feeding a
+ * ray-error Sim(3) Gauss-Newton over a keyframe graph (Sec. 3.3, Sec. 3.5).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Memory: every array argument is a DEVICE pointer owned by the caller
+ *   unless its comment says "host".  The library allocates no device memory;
+ *   scratch space comes from the caller's `workspace` (size from
+ *   mslam_workspace_bytes).  Host memory is used only inside mslam_plan_*.
+ * - Streams: `stream` is a cudaStream_t cast to void* (NULL = legacy default
+ *   stream).  Compute calls only enqueue work; they never synchronise, so a
+ *   sequence of them can be captured into a CUDA graph.
+ * - Errors: argument errors are detected on the host and returned at once
+ *   (nothing is enqueued); a failed launch returns MSLAM_ERR_CUDA.  Errors
+ *   that only the GPU can see (a non-positive Cholesky pivot, a non-finite
+ *   step) are written to the caller's per-graph `dev_status` array, read
+ *   after synchronising.  mslam_last_error() describes the last host-side
+ *   error of the calling thread.
+ * - Pools: per-keyframe tensors (canonical pointmaps) are concatenated in
+ *   keyframe order, H_k W_k pixels each ("keyframe pool"); per-edge tensors
+ *   (the pair prediction's pointmaps, descriptors and confidences, and the
+ *   matches) are concatenated in edge order, H_j W_j pixels per edge ("edge
+ *   pool").  Pixels are row-major (n = v W + u).
+ * - Pointmaps are [pixels, 3] (x, y, z) of the storage dtype; descriptors
+ *   [pixels, d]; confidences [pixels].  MSLAM_F32 stores float, MSLAM_F16
+ *   stores IEEE half; all arithmetic is float (FP32) except the pose algebra,
+ *   the per-edge block assembly and the Cholesky solve, which are FP64.
+ * - Poses T_wc are [N, 8] FP64: translation (3), unit quaternion x y z w (4),
+ *   scale (1), mapping a camera point X to s R X + t (Sec. 3.1, Eq. 1).
+ *   Tangent vectors tau are [N, 7]: (rho, phi, sigma) with
+ *   Exp(tau) = expm([[ [phi]x + sigma I, rho ], [0, 0]]) and the left-plus
+ *   update T <- Exp(tau) o T (Eq. 1).
+ */
+#ifndef MSLAM_H
+#define MSLAM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MSLAM_OK = 0,
+  MSLAM_ERR_ARG = 1,       /* invalid argument (host check) */
+  MSLAM_ERR_CUDA = 2,      /* CUDA launch or runtime error */
+  MSLAM_ERR_NOT_PD = 3,    /* reduced system not positive definite (dev_status) */
+  MSLAM_ERR_TIMEOUT = 4,   /* a bounded device wait gave up (dev_status) */
+  MSLAM_ERR_NONFINITE = 5, /* non-finite step (dev_status) */
+  MSLAM_ERR_RANGE = 6      /* size beyond a stated limit */
+} mslam_status;
+
+typedef enum { MSLAM_F32 = 0, MSLAM_F16 = 1 } mslam_dtype;
+
+/* Launch forms: the plain form issues one launch per edge from a host loop;
+ * the default (batched) form covers every edge of every graph in one
+ * persistent launch per stage. */
+#define MSLAM_FLAG_PER_EDGE 1u
+
+/* Workspace kinds for mslam_workspace_bytes */
+#define MSLAM_OP_LINEARIZE 1
+#define MSLAM_OP_SOLVE 2
+#define MSLAM_OP_BACKWARD 3
+
+/* Constants of the method.  The paper names these quantities without values
+ * where marked "reading"; defaults are set by mslam_default_params. */
+typedef struct {
+  float sigma_ray;       /* sigma_r of the weight w(q, sigma^2) = sigma^2 / q (Sec. 3.3); reading 0.01 */
+  float sigma_dist;      /* sigma of the "small weight" distance term (Sec. 3.3, 3.5); reading 0.1 */
+  float huber_delta;     /* Huber threshold of the robust norm on whitened residuals; reading 1.345 */
+  float q_min;           /* matches with q <= q_min get w = infinity, i.e. are dropped (Sec. 3.3); reading 1.5 */
+  float lm_lambda;       /* Levenberg-Marquardt damping of the matching step (Sec. 3.2); reading 1e-8 */
+  int32_t lm_iters;      /* matching iterations; Sec. 3.2: 10 suffice for almost all valid pixels */
+  int32_t win_radius;    /* refinement window radius r: (2r+1)^2 candidates per level; reading 3 */
+  int32_t n_levels;      /* coarse-to-fine refinement levels (0..4); reading 2 */
+  int32_t win_dilation[4]; /* candidate spacing per level, coarse first; reading {2, 1} */
+  float max_rel_dist3d;  /* match invalid if |X_ref[m] - x| > this * |x| (Sec. 3.2 "large distances in 3D"); reading 0.1 */
+  double conv_tol;       /* a graph stops updating once max|tau| < conv_tol (Sec. 3.5 "terminates upon convergence") */
+} mslam_params;
+
+/* Fill `p` with the default readings listed above. */
+void mslam_default_params(mslam_params* p);
+
+/* Human-readable description of the calling thread's last host-side error. */
+const char* mslam_last_error(void);
+
+/* Library version string. */
+const char* mslam_version(void);
+
+/* ------------------------------------------------------------------------ */
+/* Graph plan: the static structure of one or more keyframe graphs.         */
+/* ------------------------------------------------------------------------ */
+/* A plan holds the keyframe sizes, the directed edge list (Sec. 3.4: edges
+ * are added in both directions), the pools' offsets, the work tiles of the
+ * batched kernels and the symbolic block-sparse Cholesky factorisation of
+ * each graph's 7N system with its first keyframe fixed (Sec. 3.5), ordered
+ * by minimum degree.  It is built on the host once per edge structure.
+ *
+ *   N            number of keyframes (poses), >= 1
+ *   kf_hw        host [N, 2] int32: H, W of each keyframe (2 <= H, W <= 8192)
+ *   E            number of directed edges, >= 0
+ *   edges        host [E, 2] int32: (i, j) = (reference keyframe, query
+ *                keyframe); i != j, same graph, same image size
+ *   graph_of_kf  host [N] int32 graph id in [0, G) or NULL (one graph).  The
+ *                lowest-indexed keyframe of each graph is its fixed pose.
+ *   out          receives the plan; destroy with mslam_plan_destroy.
+ * Errors: MSLAM_ERR_ARG on any inconsistency (nothing is created). */
+typedef struct mslam_plan mslam_plan;
+mslam_status mslam_plan_create(int32_t N, const int32_t* kf_hw, int32_t E, const int32_t* edges,
+                               const int32_t* graph_of_kf, mslam_plan** out);
+void mslam_plan_destroy(mslam_plan* plan);
+
+/* Bytes of device memory the plan's tables need, and their upload into a
+ * caller-owned device buffer `dev` (>= 256-byte aligned) on `stream`.  The
+ * buffer must outlive every call that uses the plan.  The host staging copy
+ * is complete when the call returns. */
+size_t mslam_plan_device_bytes(const mslam_plan* plan);
+mslam_status mslam_plan_upload(mslam_plan* plan, void* dev, size_t bytes, void* stream);
+
+/* Pool sizes: sum of H_k W_k over keyframes; sum of H_j W_j over edges. */
+int64_t mslam_plan_kf_pixels(const mslam_plan* plan);
+int64_t mslam_plan_edge_pixels(const mslam_plan* plan);
+int32_t mslam_plan_num_graphs(const mslam_plan* plan);
+/* Host copies of the structure: kf_off [N + 1] and e_off [E + 1] pixel
+ * offsets of the pools; order [N] = elimination position of each keyframe
+ * within its graph (-1 for the fixed keyframe); counts [4] = non-zero 7x7
+ * blocks of L, update triples, work tiles of the linearisation, match blocks. */
+void mslam_plan_offsets(const mslam_plan* plan, int64_t* kf_off, int64_t* e_off);
+void mslam_plan_stats(const mslam_plan* plan, int32_t* order, int64_t* counts);
+
+/* Scratch bytes a call of kind `op` (MSLAM_OP_*) needs for this plan. */
+size_t mslam_workspace_bytes(const mslam_plan* plan, int32_t op);
+
+/* ------------------------------------------------------------------------ */
+/* (a1-a3) Projective matching with feature refinement, Sec. 3.2, Eq. 2.     */
+/* ------------------------------------------------------------------------ */
+/* For every query pixel n of every edge e = (i, j) in [edge_begin, edge_end)
+ * (-1, -1 = all edges):
+ *   a1  the reference camera model psi(X_ref) = X_ref / |X_ref| (Sec. 3.1),
+ *       evaluated at the four bilinear taps each iteration (a zero or
+ *       non-finite reference point has the zero ray);
+ *   a2  x = X_qry[n]; p starts at init_idx[n] (if init_idx != NULL and
+ *       init_idx[n] >= 0) else at n itself (the identity map, Sec. 3.2), and
+ *       takes lm_iters steps (J^T J + lm_lambda I) dp = -J^T r of the ray
+ *       error r = R(p) - psi(x), R bilinear in the stored rays of the cell
+ *       (clamp(floor u, 0, W-2), clamp(floor v, 0, H-2)), p clamped to the
+ *       image after each step;
+ *   a3  p is rounded half-up to a pixel, refined over n_levels windows of
+ *       (2 win_radius + 1)^2 candidates spaced win_dilation[l] apart to the
+ *       maximum descriptor dot product <D_qry[n], D_ref[c]> (first maximum in
+ *       row-major order), and invalidated if x is zero/non-finite or
+ *       |X_ref[m] - x| > max_rel_dist3d |x|; q = sqrt(Q_ref[m] Q_qry[n]).
+ * Arguments (edge pools, dtype dt): X_ref, X_qry [P, 3]; D_ref, D_qry [P, d]
+ * with d in {16, 24, 32}, 16-byte aligned; Q_ref, Q_qry [P]; init_idx [P]
+ * int32 or NULL; outputs idx_out [P] int32 (m within the reference image,
+ * -1 = invalid) and q_out [P] (dt; 0 where invalid).
+ * flags: MSLAM_FLAG_PER_EDGE = one launch per edge, else one launch.
+ * Errors: MSLAM_ERR_ARG for a null or misaligned pointer, unsupported d or
+ * bad parameters; MSLAM_ERR_CUDA if a launch fails. */
+mslam_status mslam_match(const mslam_params* p, const mslam_plan* plan, mslam_dtype dt, int32_t d,
+                         const void* X_ref, const void* X_qry, const void* D_ref, const void* D_qry,
+                         const void* Q_ref, const void* Q_qry, const int32_t* init_idx, int32_t* idx_out,
+                         void* q_out, int32_t edge_begin, int32_t edge_end, uint32_t flags, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* (a4-a5) Linearisation of the ray-error cost, Eq. backend_ray, Supp. S1.   */
+/* ------------------------------------------------------------------------ */
+/* For every edge e = (i, j) and every query pixel n with idx[n] = m >= 0 and
+ * q[n] > q_min: x = T_ij X_canon_j[n] with T_ij = T_i^-1 T_j, y =
+ * X_canon_i[m]; residuals r = psi(x) - psi(y) (3) and r_d = |x| - |y| (Supp.
+ * S1.2); weights lambda = q / sigma^2 per term with one Huber IRLS weight on
+ * the whitened ray residual norm and one on the distance residual; relative
+ * Jacobians [(I - u u^T)/|x|, -[x]x/|x|, 0] and [u^T, 0, |x|] (u = x/|x|)
+ * reduced per edge in FP32 (per-thread then tree sums, FP64 across tiles),
+ * then mapped to the 14 x 14 block with Ad_{T_i^-1} (Supp. S1.4): H_ii = H_jj =
+ * Ad^T H_rel Ad, H_ij = H_ji = -Ad^T H_rel Ad, g_i = -Ad^T g_rel,
+ * g_j = Ad^T g_rel.
+ * Arguments: T_wc [N, 8] FP64; X_canon keyframe pool [Pk, 3] (dt); idx, q
+ * edge pools [P] (int32, dt).  Outputs: H_blocks [E, 14, 14] FP32 row-major
+ * (rows/cols 0..6 = pose i, 7..13 = pose j), g_blocks [E, 14] FP32, cost [E]
+ * FP64 (sum of Huber costs), n_valid [E] int32 or NULL (matches used).
+ * workspace >= mslam_workspace_bytes(plan, MSLAM_OP_LINEARIZE), 256-byte
+ * aligned.  flags: MSLAM_FLAG_PER_EDGE = plain form (a host loop of
+ * per-edge launches), else one persistent launch over all tiles.
+ * Errors: MSLAM_ERR_ARG, MSLAM_ERR_CUDA. */
+mslam_status mslam_gn_linearize(const mslam_params* p, const mslam_plan* plan, mslam_dtype dt, const double* T_wc,
+                                const void* X_canon, const int32_t* idx, const void* q, float* H_blocks,
+                                float* g_blocks, double* cost, int32_t* n_valid, void* workspace,
+                                size_t ws_bytes, uint32_t flags, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* (a6-a8) Gauss-Newton solve with the first pose fixed, Sec. 3.5.           */
+/* ------------------------------------------------------------------------ */
+/* Per graph: assemble the 14 x 14 edge blocks into the block-sparse 7N
+ * system in FP64 (each block summed in edge order), drop the graph's first
+ * keyframe (gauge), factor with a block Cholesky in the plan's
+ * minimum-degree order, solve (J^T W J) tau = -J^T W r (Eq. gauss_newton)
+ * and retract every other pose, T_k <- Exp(tau_k) o T_k, in FP64.
+ * Arguments: H_blocks, g_blocks from mslam_gn_linearize; T_wc [N, 8] FP64
+ * updated in place (the fixed poses are never written); tau [N, 7] FP64
+ * output or NULL; dev_status [G] int32, zeroed by the caller before the
+ * first iteration: a graph whose entry is non-zero is skipped.  The solve
+ * writes 1 once max|tau| < conv_tol (converged), MSLAM_ERR_NOT_PD if a pivot
+ * is not above 1e-12 times its assembled diagonal entry (the pose update is
+ * then skipped), MSLAM_ERR_NONFINITE if the step is not finite.
+ * workspace >= mslam_workspace_bytes(plan, MSLAM_OP_SOLVE).
+ * Errors (returned): MSLAM_ERR_ARG, MSLAM_ERR_CUDA. */
+mslam_status mslam_gn_solve(const mslam_params* p, const mslam_plan* plan, const float* H_blocks,
+                            const float* g_blocks, double* T_wc, double* tau, int32_t* dev_status, void* workspace,
+                            size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* (a9) Adjoint of the weighted cost (project form; not in the paper).      */
+/* ------------------------------------------------------------------------ */
+/* Gradient of L = dL_dcost * E_g(T, X_canon, q) + dL_dtau . tau(T, X_canon, q)
+ * with respect to the canonical pointmaps and the match confidences, where
+ * E_g is Eq. backend_ray at the poses T_wc (matches and the q_min mask held
+ * fixed, Huber weights differentiated) and tau = -H^-1 g is one
+ * Gauss-Newton step from T_wc (Eq. gauss_newton).  The per-pixel residuals
+ * and Jacobians are recomputed, not stored.
+ * Arguments: as mslam_gn_linearize, plus H_blocks and g_blocks of the
+ * linearisation at T_wc (needed when dL_dtau != NULL), dL_dtau [N, 7] FP64
+ * device or NULL, dL_dcost host scalar; outputs dL_dX [Pk, 3] FP32 and dL_dq
+ * [P] FP32, overwritten.  workspace >= mslam_workspace_bytes(plan,
+ * MSLAM_OP_BACKWARD).  Errors: MSLAM_ERR_ARG, MSLAM_ERR_CUDA; a singular
+ * system sets dev_status[g] = MSLAM_ERR_NOT_PD. */
+mslam_status mslam_gn_backward(const mslam_params* p, const mslam_plan* plan, mslam_dtype dt, const double* T_wc,
+                               const void* X_canon, const int32_t* idx, const void* q, const float* H_blocks,
+                               const float* g_blocks, const double* dL_dtau, double dL_dcost, float* dL_dX,
+                               float* dL_dq, int32_t* dev_status, void* workspace, size_t ws_bytes,
+                               void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MSLAM_H */

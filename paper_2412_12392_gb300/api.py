@@ -1,0 +1,267 @@
+"""Thin Python binding of include/mslam.h: argument marshalling only.
+
+Every function here checks tensor devices, dtypes and shapes, then calls the
+C entry point of the same name on the current CUDA stream; all computation
+happens in the CUDA kernels of libmslam.so.  Device memory (outputs and
+workspaces) is allocated with torch and handed to the library, which
+allocates nothing itself.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import Params, check, lib
+
+DTYPES = {torch.float32: _lib.MSLAM_F32, torch.float16: _lib.MSLAM_F16}
+
+
+def default_params(**over) -> Params:
+    """mslam_default_params with optional field overrides."""
+    p = Params()
+    lib().mslam_default_params(C.byref(p))
+    for k, v in over.items():
+        if k == "win_dilation":
+            dil = list(v) + [1] * (4 - len(v))
+            p.win_dilation = (C.c_int32 * 4)(*dil[:4])
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def params_dict(p: Params) -> dict:
+    """The parameter block as a plain dict (for the oracle)."""
+    return dict(sigma_ray=p.sigma_ray, sigma_dist=p.sigma_dist, huber_delta=p.huber_delta, q_min=p.q_min,
+                lm_lambda=p.lm_lambda, lm_iters=p.lm_iters, win_radius=p.win_radius, n_levels=p.n_levels,
+                win_dilation=tuple(p.win_dilation), max_rel_dist3d=p.max_rel_dist3d, conv_tol=p.conv_tol)
+
+
+def _stream(device=None) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else t.data_ptr()
+
+
+def _need(t: torch.Tensor, name: str, dtype=None, numel=None, device=None):
+    if not torch.is_tensor(t):
+        raise TypeError(f"{name} must be a torch tensor")
+    if t.device.type != "cuda":
+        raise ValueError(f"{name} must be a CUDA tensor (got {t.device})")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype} (got {t.dtype})")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+
+
+class Plan:
+    """mslam_plan: the static structure of one or more keyframe graphs,
+    uploaded to a torch-owned device buffer."""
+
+    def __init__(self, kf_hw, edges, graph_of_kf=None, device="cuda"):
+        kf = np.ascontiguousarray(np.asarray(kf_hw, dtype=np.int32).reshape(-1, 2))
+        ed = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+        gk = None if graph_of_kf is None else np.ascontiguousarray(np.asarray(graph_of_kf, dtype=np.int32))
+        self.N, self.E = kf.shape[0], ed.shape[0]
+        h = C.c_void_p()
+        check(lib().mslam_plan_create(self.N, kf.ctypes.data, self.E, ed.ctypes.data if self.E else None,
+                                      gk.ctypes.data if gk is not None else None, C.byref(h)), "mslam_plan_create")
+        self._h = h
+        self.kf_hw, self.edges = kf, ed
+        self.kf_pixels = int(lib().mslam_plan_kf_pixels(h))
+        self.edge_pixels = int(lib().mslam_plan_edge_pixels(h))
+        self.G = int(lib().mslam_plan_num_graphs(h))
+        self.kf_off = np.zeros(self.N + 1, dtype=np.int64)
+        self.e_off = np.zeros(self.E + 1, dtype=np.int64)
+        lib().mslam_plan_offsets(h, self.kf_off.ctypes.data, self.e_off.ctypes.data)
+        self.order = np.zeros(self.N, dtype=np.int32)
+        self.counts = np.zeros(4, dtype=np.int64)
+        lib().mslam_plan_stats(h, self.order.ctypes.data, self.counts.ctypes.data)
+        self.device = torch.device(device)
+        self.dev = None
+        if self.device.type == "cuda":
+            self.upload()
+
+    def upload(self):
+        nbytes = int(lib().mslam_plan_device_bytes(self._h))
+        self.dev = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        check(lib().mslam_plan_upload(self._h, self.dev.data_ptr(), nbytes, _stream(self.device)),
+              "mslam_plan_upload")
+
+    def workspace_bytes(self, op: int) -> int:
+        return int(lib().mslam_workspace_bytes(self._h, op))
+
+    def workspace(self, op: int) -> torch.Tensor:
+        return torch.empty(max(self.workspace_bytes(op), 256), dtype=torch.uint8, device=self.device)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        try:
+            if getattr(self, "_h", None) and _lib._lib is not None:
+                lib().mslam_plan_destroy(self._h)
+                self._h = None
+        except Exception:  # pragma: no cover - interpreter shutdown
+            pass
+
+
+def match(plan: Plan, params: Params, X_ref, X_qry, D_ref, D_qry, Q_ref, Q_qry, init_idx=None, idx_out=None,
+          q_out=None, edge_range: Tuple[int, int] = (-1, -1), per_edge: bool = False):
+    """mslam_match (Sec. 3.2): returns (idx int32 [P], q [P])."""
+    dt = X_ref.dtype
+    if dt not in DTYPES:
+        raise ValueError(f"unsupported storage dtype {dt}")
+    P = plan.edge_pixels
+    d = D_ref.shape[-1]
+    for t, nm, ne in ((X_ref, "X_ref", 3 * P), (X_qry, "X_qry", 3 * P), (D_ref, "D_ref", d * P),
+                      (D_qry, "D_qry", d * P), (Q_ref, "Q_ref", P), (Q_qry, "Q_qry", P)):
+        _need(t, nm, dt, ne)
+    if init_idx is not None:
+        _need(init_idx, "init_idx", torch.int32, P)
+    if idx_out is None:
+        idx_out = torch.empty(P, dtype=torch.int32, device=X_ref.device)
+    if q_out is None:
+        q_out = torch.empty(P, dtype=dt, device=X_ref.device)
+    _need(idx_out, "idx_out", torch.int32, P)
+    _need(q_out, "q_out", dt, P)
+    check(lib().mslam_match(C.byref(params), plan.handle, DTYPES[dt], d, X_ref.data_ptr(), X_qry.data_ptr(),
+                            D_ref.data_ptr(), D_qry.data_ptr(), Q_ref.data_ptr(), Q_qry.data_ptr(),
+                            _ptr(init_idx), idx_out.data_ptr(), q_out.data_ptr(), int(edge_range[0]),
+                            int(edge_range[1]), _lib.MSLAM_FLAG_PER_EDGE if per_edge else 0,
+                            _stream(X_ref.device)), "mslam_match")
+    return idx_out, q_out
+
+
+def gn_linearize(plan: Plan, params: Params, T_wc, X_canon, idx, q, H=None, g=None, cost=None, n_valid=None,
+                 workspace=None, per_edge: bool = False):
+    """mslam_gn_linearize (Eq. backend_ray): returns (H [E,14,14], g [E,14],
+    cost [E], n_valid [E])."""
+    dt = X_canon.dtype
+    if dt not in DTYPES:
+        raise ValueError(f"unsupported storage dtype {dt}")
+    dev = X_canon.device
+    _need(T_wc, "T_wc", torch.float64, 8 * plan.N)
+    _need(X_canon, "X_canon", dt, 3 * plan.kf_pixels)
+    _need(idx, "idx", torch.int32, plan.edge_pixels)
+    _need(q, "q", dt, plan.edge_pixels)
+    E = plan.E
+    H = torch.empty(E, 14, 14, dtype=torch.float32, device=dev) if H is None else H
+    g = torch.empty(E, 14, dtype=torch.float32, device=dev) if g is None else g
+    cost = torch.empty(E, dtype=torch.float64, device=dev) if cost is None else cost
+    n_valid = torch.empty(E, dtype=torch.int32, device=dev) if n_valid is None else n_valid
+    _need(H, "H", torch.float32, 196 * E)
+    _need(g, "g", torch.float32, 14 * E)
+    _need(cost, "cost", torch.float64, E)
+    _need(n_valid, "n_valid", torch.int32, E)
+    ws = plan.workspace(_lib.MSLAM_OP_LINEARIZE) if workspace is None else workspace
+    check(lib().mslam_gn_linearize(C.byref(params), plan.handle, DTYPES[dt], T_wc.data_ptr(), X_canon.data_ptr(),
+                                   idx.data_ptr(), q.data_ptr(), H.data_ptr(), g.data_ptr(), cost.data_ptr(),
+                                   n_valid.data_ptr(), ws.data_ptr(), ws.numel(),
+                                   _lib.MSLAM_FLAG_PER_EDGE if per_edge else 0, _stream(dev)), "mslam_gn_linearize")
+    return H, g, cost, n_valid
+
+
+def gn_solve(plan: Plan, params: Params, H, g, T_wc, tau=None, dev_status=None, workspace=None):
+    """mslam_gn_solve (Sec. 3.5): updates T_wc in place; returns (tau, dev_status)."""
+    dev = T_wc.device
+    _need(H, "H", torch.float32, 196 * plan.E)
+    _need(g, "g", torch.float32, 14 * plan.E)
+    _need(T_wc, "T_wc", torch.float64, 8 * plan.N)
+    if dev_status is None:
+        dev_status = torch.zeros(plan.G, dtype=torch.int32, device=dev)
+    _need(dev_status, "dev_status", torch.int32, plan.G)
+    if tau is not None:
+        _need(tau, "tau", torch.float64, 7 * plan.N)
+    ws = plan.workspace(_lib.MSLAM_OP_SOLVE) if workspace is None else workspace
+    check(lib().mslam_gn_solve(C.byref(params), plan.handle, H.data_ptr(), g.data_ptr(), T_wc.data_ptr(),
+                               _ptr(tau), dev_status.data_ptr(), ws.data_ptr(), ws.numel(), _stream(dev)),
+          "mslam_gn_solve")
+    return tau, dev_status
+
+
+def gn_backward(plan: Plan, params: Params, T_wc, X_canon, idx, q, H=None, g=None, dL_dtau=None,
+                dL_dcost: float = 1.0, dL_dX=None, dL_dq=None, dev_status=None, workspace=None):
+    """mslam_gn_backward: gradient of dL_dcost * E_g + dL_dtau . tau with
+    respect to X_canon and q.  Returns (dL_dX float32 [Pk,3], dL_dq float32 [P], dev_status)."""
+    dt = X_canon.dtype
+    dev = X_canon.device
+    _need(T_wc, "T_wc", torch.float64, 8 * plan.N)
+    _need(X_canon, "X_canon", dt, 3 * plan.kf_pixels)
+    _need(idx, "idx", torch.int32, plan.edge_pixels)
+    _need(q, "q", dt, plan.edge_pixels)
+    if dL_dtau is not None:
+        _need(dL_dtau, "dL_dtau", torch.float64, 7 * plan.N)
+        _need(H, "H", torch.float32, 196 * plan.E)
+        _need(g, "g", torch.float32, 14 * plan.E)
+    dL_dX = torch.empty(plan.kf_pixels, 3, dtype=torch.float32, device=dev) if dL_dX is None else dL_dX
+    dL_dq = torch.empty(plan.edge_pixels, dtype=torch.float32, device=dev) if dL_dq is None else dL_dq
+    if dev_status is None:
+        dev_status = torch.zeros(plan.G, dtype=torch.int32, device=dev)
+    ws = plan.workspace(_lib.MSLAM_OP_BACKWARD) if workspace is None else workspace
+    check(lib().mslam_gn_backward(C.byref(params), plan.handle, DTYPES[dt], T_wc.data_ptr(), X_canon.data_ptr(),
+                                  idx.data_ptr(), q.data_ptr(), _ptr(H), _ptr(g), _ptr(dL_dtau), float(dL_dcost),
+                                  dL_dX.data_ptr(), dL_dq.data_ptr(), dev_status.data_ptr(), ws.data_ptr(),
+                                  ws.numel(), _stream(dev)), "mslam_gn_backward")
+    return dL_dX, dL_dq, dev_status
+
+
+class GaussNewton:
+    """Device-resident Gauss-Newton loop over a plan (Sec. 3.5): buffers are
+    allocated once, so the loop can be captured into a CUDA graph."""
+
+    def __init__(self, plan: Plan, params: Params, X_canon, idx, q, per_edge: bool = False):
+        self.plan, self.params, self.per_edge = plan, params, per_edge
+        self.X, self.idx, self.q = X_canon, idx, q
+        dev = X_canon.device
+        E, N = plan.E, plan.N
+        self.H = torch.empty(E, 14, 14, dtype=torch.float32, device=dev)
+        self.g = torch.empty(E, 14, dtype=torch.float32, device=dev)
+        self.cost = torch.empty(E, dtype=torch.float64, device=dev)
+        self.n_valid = torch.empty(E, dtype=torch.int32, device=dev)
+        self.tau = torch.zeros(N, 7, dtype=torch.float64, device=dev)
+        self.status = torch.zeros(plan.G, dtype=torch.int32, device=dev)
+        self.ws_lin = plan.workspace(_lib.MSLAM_OP_LINEARIZE)
+        self.ws_solve = plan.workspace(_lib.MSLAM_OP_SOLVE)
+        self.T = torch.empty(N, 8, dtype=torch.float64, device=dev)
+        self.graph = None
+
+    def step(self):
+        gn_linearize(self.plan, self.params, self.T, self.X, self.idx, self.q, self.H, self.g, self.cost,
+                     self.n_valid, self.ws_lin, self.per_edge)
+        gn_solve(self.plan, self.params, self.H, self.g, self.T, self.tau, self.status, self.ws_solve)
+
+    def run(self, T_init, iters: int):
+        self.T.copy_(T_init)
+        self.status.zero_()
+        for _ in range(iters):
+            self.step()
+        return self.T
+
+    def capture(self, iters: int):
+        """Capture `iters` steps (on the current buffers) into a CUDA graph."""
+        s = torch.cuda.Stream(self.X.device)
+        s.wait_stream(torch.cuda.current_stream(self.X.device))
+        with torch.cuda.stream(s):
+            self.step()  # warm-up outside capture (lazy module loading)
+        torch.cuda.current_stream(self.X.device).wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            for _ in range(iters):
+                self.step()
+        self.graph = g
+        return g
+
+    def replay(self, T_init):
+        self.T.copy_(T_init)
+        self.status.zero_()
+        self.graph.replay()
+        return self.T

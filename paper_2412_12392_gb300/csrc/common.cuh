@@ -1,0 +1,262 @@
+// Shared definitions of the CUDA library: plan tables as laid out in device
+// memory, parameter block, FP16/FP32 loads, FP64 Sim(3) device algebra and
+// the host-side error plumbing.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mslam.h"
+
+namespace mslam {
+
+constexpr int kLinTile = 4096;       // pixels per linearisation work tile
+constexpr int kLinThreads = 256;     // threads per linearisation block
+constexpr int kNumAcc = 30;          // accumulators of the relative 7x7 system
+constexpr int kAccStride = 32;       // floats per tile partial in the workspace
+constexpr int kMatchBX = 32;         // match block: 32 x 8 query pixels
+constexpr int kMatchBY = 8;
+constexpr int kSolveThreads = 512;
+
+// One directed edge as seen by the kernels.
+struct DevEdge {
+  int32_t i, j;         // reference keyframe, query keyframe
+  int32_t H, W;         // image size (both keyframes)
+  int64_t off_e;        // offset of the edge in the edge pools (pixels)
+  int64_t off_i, off_j; // offsets of the keyframes in the keyframe pool
+  int32_t graph;        // graph id
+  int32_t tile_begin;   // linearisation tiles of this edge: [tile_begin, tile_end)
+  int32_t tile_end;
+  int32_t mblock_begin; // first match block of this edge (flat grid)
+};
+
+struct DevTile {
+  int32_t edge;
+  int32_t begin;  // pixel range within the edge
+  int32_t end;
+  int32_t pad;
+};
+
+// Per-graph symbolic factorisation (all indices local to the graph, arrays
+// concatenated across graphs at the given offsets).
+struct DevGraph {
+  int32_t m;          // non-fixed poses = block rows of the reduced system
+  int32_t n_blocks;   // 7x7 blocks of L: m diagonal blocks first, then off-diagonal
+  int32_t gauge;      // fixed keyframe (global index)
+  int32_t pad0;
+  int32_t off_pose;   // -> pose_of_pos [m]: global keyframe at elimination position p
+  int32_t off_col;    // -> col_ptr [m + 1] (into col_rows / col_blk, relative)
+  int32_t off_colent; // -> col_rows, col_blk entries
+  int32_t off_trip;   // -> trip_ptr [m + 1]
+  int32_t off_tripent;// -> trips (3 ints each: target, src_row_block, src_col_block)
+  int32_t off_asm;    // -> asm_ptr [n_blocks + 1]
+  int32_t off_asment; // -> asm entries: edge * 4 + quadrant
+  int32_t off_gasm;   // -> gasm_ptr [m + 1]
+  int32_t off_gasment;// -> gasm entries: edge * 2 + side
+  int32_t pad1;
+  int64_t ws_off;     // offset (doubles) of this graph's numeric workspace
+};
+
+// Device view of a plan (pointers into the uploaded table blob).
+struct PlanView {
+  int32_t N, E, G, n_tiles, n_mblocks;
+  const DevEdge* edges;
+  const DevTile* tiles;
+  const DevGraph* graphs;
+  const int32_t* ints;  // all int32 symbolic arrays of the graphs
+};
+
+// Parameters converted for the kernels.
+struct KParams {
+  float sigma_ray, sigma_dist, huber_delta, q_min, lm_lambda, max_rel_dist3d;
+  int lm_iters, win_radius, n_levels;
+  int win_dilation[4];
+  double conv_tol;
+};
+
+inline KParams to_kparams(const mslam_params& p) {
+  KParams k;
+  k.sigma_ray = p.sigma_ray;
+  k.sigma_dist = p.sigma_dist;
+  k.huber_delta = p.huber_delta;
+  k.q_min = p.q_min;
+  k.lm_lambda = p.lm_lambda;
+  k.max_rel_dist3d = p.max_rel_dist3d;
+  k.lm_iters = p.lm_iters;
+  k.win_radius = p.win_radius;
+  k.n_levels = p.n_levels;
+  for (int l = 0; l < 4; ++l) k.win_dilation[l] = p.win_dilation[l];
+  k.conv_tol = p.conv_tol;
+  return k;
+}
+
+// ---------------------------------------------------------------- loads
+template <typename T> __device__ __forceinline__ float ldf(const T* p);
+template <> __device__ __forceinline__ float ldf<float>(const float* p) { return __ldg(p); }
+template <> __device__ __forceinline__ float ldf<__half>(const __half* p) {
+  return __half2float(__ldg(reinterpret_cast<const __half*>(p)));
+}
+template <typename T> __device__ __forceinline__ void stf(T* p, float v);
+template <> __device__ __forceinline__ void stf<float>(float* p, float v) { *p = v; }
+template <> __device__ __forceinline__ void stf<__half>(__half* p, float v) { *p = __float2half_rn(v); }
+
+template <typename T>
+__device__ __forceinline__ float3 ld3(const T* base, int64_t pix) {
+  const T* p = base + 3 * pix;
+  return make_float3(ldf(p), ldf(p + 1), ldf(p + 2));
+}
+
+__device__ __forceinline__ bool finite3(float3 a) {
+  return isfinite(a.x) && isfinite(a.y) && isfinite(a.z);
+}
+
+// ---------------------------------------------------------------- FP64 Sim(3)
+// Pose: t (3), q = (x, y, z, w) (4), s (1); X -> s R(q) X + t.
+struct Sim3d {
+  double t[3];
+  double q[4];
+  double s;
+};
+
+__device__ __forceinline__ Sim3d load_pose(const double* T) {
+  Sim3d a;
+  for (int k = 0; k < 3; ++k) a.t[k] = T[k];
+  for (int k = 0; k < 4; ++k) a.q[k] = T[3 + k];
+  a.s = T[7];
+  return a;
+}
+
+__device__ __forceinline__ void store_pose(const Sim3d& a, double* T) {
+  for (int k = 0; k < 3; ++k) T[k] = a.t[k];
+  for (int k = 0; k < 4; ++k) T[3 + k] = a.q[k];
+  T[7] = a.s;
+}
+
+__device__ __forceinline__ void rot_of(const double q[4], double R[9]) {
+  const double x = q[0], y = q[1], z = q[2], w = q[3];
+  const double xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z, wx = w * x, wy = w * y,
+               wz = w * z;
+  R[0] = 1.0 - 2.0 * (yy + zz); R[1] = 2.0 * (xy - wz);       R[2] = 2.0 * (xz + wy);
+  R[3] = 2.0 * (xy + wz);       R[4] = 1.0 - 2.0 * (xx + zz); R[5] = 2.0 * (yz - wx);
+  R[6] = 2.0 * (xz - wy);       R[7] = 2.0 * (yz + wx);       R[8] = 1.0 - 2.0 * (xx + yy);
+}
+
+__device__ __forceinline__ void qmul(const double a[4], const double b[4], double c[4]) {
+  c[3] = a[3] * b[3] - (a[0] * b[0] + a[1] * b[1] + a[2] * b[2]);
+  c[0] = a[3] * b[0] + b[3] * a[0] + (a[1] * b[2] - a[2] * b[1]);
+  c[1] = a[3] * b[1] + b[3] * a[1] + (a[2] * b[0] - a[0] * b[2]);
+  c[2] = a[3] * b[2] + b[3] * a[2] + (a[0] * b[1] - a[1] * b[0]);
+}
+
+__device__ __forceinline__ void qnormalise(double q[4]) {
+  const double inv = 1.0 / sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  for (int k = 0; k < 4; ++k) q[k] *= inv;
+}
+
+// a o b
+__device__ __forceinline__ Sim3d compose(const Sim3d& a, const Sim3d& b) {
+  Sim3d c;
+  double R[9];
+  rot_of(a.q, R);
+  for (int r = 0; r < 3; ++r) c.t[r] = a.s * (R[3 * r] * b.t[0] + R[3 * r + 1] * b.t[1] + R[3 * r + 2] * b.t[2]) + a.t[r];
+  qmul(a.q, b.q, c.q);
+  qnormalise(c.q);
+  c.s = a.s * b.s;
+  return c;
+}
+
+__device__ __forceinline__ Sim3d inverse(const Sim3d& a) {
+  Sim3d b;
+  double R[9];
+  rot_of(a.q, R);
+  b.s = 1.0 / a.s;
+  for (int r = 0; r < 3; ++r) b.t[r] = -b.s * (R[r] * a.t[0] + R[3 + r] * a.t[1] + R[6 + r] * a.t[2]);
+  b.q[0] = -a.q[0]; b.q[1] = -a.q[1]; b.q[2] = -a.q[2]; b.q[3] = a.q[3];
+  return b;
+}
+
+// Ad_T (7x7, row-major) for T Exp(tau) T^-1 = Exp(Ad_T tau), tau = (rho, phi, sigma):
+// [[sR, [t]x R, -t], [0, R, 0], [0, 0, 1]].
+__device__ __forceinline__ void adjoint_of(const Sim3d& a, double Ad[49]) {
+  double R[9];
+  rot_of(a.q, R);
+  for (int k = 0; k < 49; ++k) Ad[k] = 0.0;
+  const double* t = a.t;
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      Ad[7 * r + c] = a.s * R[3 * r + c];
+      Ad[7 * (3 + r) + 3 + c] = R[3 * r + c];
+    }
+  // [t]x R: row r of [t]x dotted with column c of R
+  for (int c = 0; c < 3; ++c) {
+    Ad[7 * 0 + 3 + c] = -t[2] * R[3 + c] + t[1] * R[6 + c];
+    Ad[7 * 1 + 3 + c] = t[2] * R[c] - t[0] * R[6 + c];
+    Ad[7 * 2 + 3 + c] = -t[1] * R[c] + t[0] * R[3 + c];
+  }
+  Ad[7 * 0 + 6] = -t[0];
+  Ad[7 * 1 + 6] = -t[1];
+  Ad[7 * 2 + 6] = -t[2];
+  Ad[48] = 1.0;
+}
+
+// m_n(s) = integral_0^1 x^n e^{s x} dx: a power series for |s| < 1, the
+// upward recurrence m_n = (e^s - n m_{n-1}) / s otherwise.
+__device__ __forceinline__ double moment_exp(int n, double s) {
+  if (fabs(s) < 1.0) {
+    double c = 1.0, acc = 0.0;
+    for (int k = 0; k < 30; ++k) {
+      acc += c / (double)(n + k + 1);
+      c *= s / (double)(k + 1);
+    }
+    return acc;
+  }
+  const double es = exp(s);
+  double mval = expm1(s) / s;
+  for (int k = 1; k <= n; ++k) mval = (es - k * mval) / s;
+  return mval;
+}
+
+// Exp(tau) for tau = (rho, phi, sigma): R = exp([phi]x), s = e^sigma,
+// t = V rho with V = int_0^1 e^{x sigma} R(x phi) dx = a I + b [phi]x + c [phi]x^2.
+__device__ __forceinline__ Sim3d sim3_exp(const double tau[7]) {
+  const double px = tau[3], py = tau[4], pz = tau[5], sg = tau[6];
+  const double th2 = px * px + py * py + pz * pz, th = sqrt(th2);
+  double a = moment_exp(0, sg), b, c;
+  if (th < 1e-4) {
+    b = moment_exp(1, sg) - th2 * moment_exp(3, sg) / 6.0;
+    c = 0.5 * moment_exp(2, sg) - th2 * moment_exp(4, sg) / 24.0;
+  } else {
+    double sn, cs;
+    sincos(th, &sn, &cs);
+    const double es = exp(sg), den = sg * sg + th2;
+    const double ic = ((es * cs - 1.0) * sg + es * th * sn) / den;  // int e^{sx} cos(th x)
+    const double is = (es * sn * sg - (es * cs - 1.0) * th) / den;  // int e^{sx} sin(th x)
+    b = is / th;
+    c = (a - ic) / th2;
+  }
+  Sim3d e;
+  const double h = (th < 1e-6) ? (0.5 - th2 / 48.0) : sin(0.5 * th) / th;
+  e.q[0] = h * px; e.q[1] = h * py; e.q[2] = h * pz; e.q[3] = cos(0.5 * th);
+  qnormalise(e.q);
+  e.s = exp(sg);
+  const double r0 = tau[0], r1 = tau[1], r2 = tau[2];
+  // phi x rho and phi x (phi x rho)
+  const double c0 = py * r2 - pz * r1, c1 = pz * r0 - px * r2, c2 = px * r1 - py * r0;
+  const double d0 = py * c2 - pz * c1, d1 = pz * c0 - px * c2, d2 = px * c1 - py * c0;
+  e.t[0] = a * r0 + b * c0 + c * d0;
+  e.t[1] = a * r1 + b * c1 + c * d1;
+  e.t[2] = a * r2 + b * c2 + c * d2;
+  return e;
+}
+
+// ---------------------------------------------------------------- host errors
+void set_error(const char* fmt, ...);
+mslam_status cuda_check(cudaError_t e, const char* what);
+bool check_plan_uploaded(const mslam_plan* plan);
+PlanView plan_view(const mslam_plan* plan);
+// Host-side per-edge ranges: linearisation tiles [t0, t1), match blocks [b0, b1).
+void plan_edge_tiles(const mslam_plan* plan, int e, int* t0, int* t1);
+void plan_edge_mblocks(const mslam_plan* plan, int e, int* b0, int* b1);
+
+}  // namespace mslam

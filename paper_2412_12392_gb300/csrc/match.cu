@@ -1,0 +1,302 @@
+// (a1-a3) Iterative projective matching with feature refinement, Sec. 3.2.
+//
+// One thread per query pixel, blocks of 32 x 8 query pixels so that a
+// block's bilinear taps and refinement windows fall in a compact region of
+// the reference image (served from L1/L2).  Per pixel:
+//   a1  the reference camera model psi(X_ref) is evaluated at the four
+//       bilinear taps of every iteration (a zero or non-finite reference
+//       point has the zero ray);
+//   a2  lm_iters Levenberg-Marquardt steps on |R(p) - psi(x)|^2 (Eq. 2) with
+//       the analytic 3x2 Jacobian of the bilinear cell and a closed-form 2x2
+//       solve, p clamped to the image;
+//   a3  rounding, coarse-to-fine descriptor window argmax (FP32 dot products
+//       in index order), the 3D distance test and q = sqrt(Q_ref Q_qry).
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace mslam {
+
+struct MatchConst {
+  float lm_lambda, max_rel;
+  int lm_iters, radius, n_levels;
+  int dil[4];
+};
+
+template <typename T>
+__device__ __forceinline__ float3 ray_at(const T* X, int64_t pix) {
+  const float3 a = ld3(X, pix);
+  const float n2 = fmaf(a.x, a.x, fmaf(a.y, a.y, a.z * a.z));
+  if (!(n2 > 0.0f && n2 < INFINITY)) return make_float3(0.0f, 0.0f, 0.0f);
+  const float inv = rsqrtf(n2);
+  return make_float3(a.x * inv, a.y * inv, a.z * inv);
+}
+
+// descriptor row loads: D floats of a row into registers
+template <typename T, int D> struct DescRow;
+
+template <int D> struct DescRow<float, D> {
+  static __device__ __forceinline__ void load(const float* row, float* out) {
+    const float4* r4 = reinterpret_cast<const float4*>(row);
+#pragma unroll
+    for (int k = 0; k < D / 4; ++k) {
+      const float4 v = __ldg(r4 + k);
+      out[4 * k] = v.x;
+      out[4 * k + 1] = v.y;
+      out[4 * k + 2] = v.z;
+      out[4 * k + 3] = v.w;
+    }
+  }
+  static __device__ __forceinline__ float dot(const float* row, const float* q) {
+    const float4* r4 = reinterpret_cast<const float4*>(row);
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < D / 4; ++k) {
+      const float4 v = __ldg(r4 + k);
+      s = fmaf(q[4 * k], v.x, s);
+      s = fmaf(q[4 * k + 1], v.y, s);
+      s = fmaf(q[4 * k + 2], v.z, s);
+      s = fmaf(q[4 * k + 3], v.w, s);
+    }
+    return s;
+  }
+};
+
+template <int D> struct DescRow<__half, D> {
+  static __device__ __forceinline__ void load(const __half* row, float* out) {
+    const uint4* r4 = reinterpret_cast<const uint4*>(row);
+#pragma unroll
+    for (int k = 0; k < D / 8; ++k) {
+      const uint4 v = __ldg(r4 + k);
+      const __half2* h = reinterpret_cast<const __half2*>(&v);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float2 f = __half22float2(h[c]);
+        out[8 * k + 2 * c] = f.x;
+        out[8 * k + 2 * c + 1] = f.y;
+      }
+    }
+  }
+  static __device__ __forceinline__ float dot(const __half* row, const float* q) {
+    const uint4* r4 = reinterpret_cast<const uint4*>(row);
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < D / 8; ++k) {
+      const uint4 v = __ldg(r4 + k);
+      const __half2* h = reinterpret_cast<const __half2*>(&v);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float2 f = __half22float2(h[c]);
+        s = fmaf(q[8 * k + 2 * c], f.x, s);
+        s = fmaf(q[8 * k + 2 * c + 1], f.y, s);
+      }
+    }
+    return s;
+  }
+};
+
+template <typename T, int D>
+__global__ void __launch_bounds__(kMatchBX* kMatchBY) match_kernel(
+    PlanView pv, MatchConst mc, const T* __restrict__ Xr, const T* __restrict__ Xq, const T* __restrict__ Dr,
+    const T* __restrict__ Dq, const T* __restrict__ Qr, const T* __restrict__ Qq, const int32_t* __restrict__ init,
+    int32_t* __restrict__ out_idx, T* __restrict__ out_q, int e_begin, int e_end, int block_base) {
+  const int gb = block_base + blockIdx.x;
+  // edge of this block: the last edge in [e_begin, e_end) whose first block <= gb
+  int lo = e_begin, hi = e_end - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pv.edges[mid].mblock_begin <= gb) lo = mid;
+    else hi = mid - 1;
+  }
+  const DevEdge ed = pv.edges[lo];
+  const int W = ed.W, H = ed.H;
+  const int local = gb - ed.mblock_begin;
+  const int nbx = (W + kMatchBX - 1) / kMatchBX;
+  const int u = (local % nbx) * kMatchBX + (threadIdx.x % kMatchBX);
+  const int v = (local / nbx) * kMatchBY + (threadIdx.x / kMatchBX);
+  if (u >= W || v >= H) return;
+  const int64_t HW = (int64_t)H * W;
+  const int n = v * W + u;
+  const int64_t o = ed.off_e;
+  const T* Xr_e = Xr + 3 * o;
+  const float3 x = ld3(Xq + 3 * o, n);
+  const float nx2 = fmaf(x.x, x.x, fmaf(x.y, x.y, x.z * x.z));
+  if (!(finite3(x) && nx2 > 0.0f)) {
+    out_idx[o + n] = -1;
+    stf(out_q + o + n, 0.0f);
+    return;
+  }
+  const float inx = rsqrtf(nx2);
+  const float3 tg = make_float3(x.x * inx, x.y * inx, x.z * inx);
+  int p0 = n;
+  if (init) {
+    const int32_t ii = init[o + n];
+    if (ii >= 0 && ii < HW) p0 = ii;
+  }
+  float pu = (float)(p0 % W), pv_ = (float)(p0 / W);
+  const float lam = mc.lm_lambda;
+  for (int it = 0; it < mc.lm_iters; ++it) {
+    const int u0 = min(max((int)floorf(pu), 0), W - 2);
+    const int v0 = min(max((int)floorf(pv_), 0), H - 2);
+    const float a = pu - (float)u0, b = pv_ - (float)v0;
+    const int64_t t00 = (int64_t)v0 * W + u0;
+    const float3 R00 = ray_at(Xr_e, t00), R10 = ray_at(Xr_e, t00 + 1);
+    const float3 R01 = ray_at(Xr_e, t00 + W), R11 = ray_at(Xr_e, t00 + W + 1);
+    const float ua = 1.0f - a, ub = 1.0f - b;
+    const float3 Ju = make_float3(ub * (R10.x - R00.x) + b * (R11.x - R01.x), ub * (R10.y - R00.y) + b * (R11.y - R01.y),
+                                  ub * (R10.z - R00.z) + b * (R11.z - R01.z));
+    const float3 Jv = make_float3(ua * (R01.x - R00.x) + a * (R11.x - R10.x), ua * (R01.y - R00.y) + a * (R11.y - R10.y),
+                                  ua * (R01.z - R00.z) + a * (R11.z - R10.z));
+    const float w00 = ua * ub, w10 = a * ub, w01 = ua * b, w11 = a * b;
+    const float rx = w00 * R00.x + w10 * R10.x + w01 * R01.x + w11 * R11.x - tg.x;
+    const float ry = w00 * R00.y + w10 * R10.y + w01 * R01.y + w11 * R11.y - tg.y;
+    const float rz = w00 * R00.z + w10 * R10.z + w01 * R01.z + w11 * R11.z - tg.z;
+    const float a00 = Ju.x * Ju.x + Ju.y * Ju.y + Ju.z * Ju.z + lam;
+    const float a01 = Ju.x * Jv.x + Ju.y * Jv.y + Ju.z * Jv.z;
+    const float a11 = Jv.x * Jv.x + Jv.y * Jv.y + Jv.z * Jv.z + lam;
+    const float b0 = -(Ju.x * rx + Ju.y * ry + Ju.z * rz);
+    const float b1 = -(Jv.x * rx + Jv.y * ry + Jv.z * rz);
+    const float det = a00 * a11 - a01 * a01;
+    if (det > 0.0f) {
+      pu += (a11 * b0 - a01 * b1) / det;
+      pv_ += (a00 * b1 - a01 * b0) / det;
+    }
+    // clamp (fmaxf/fminf also map a NaN to the image)
+    pu = fminf(fmaxf(pu, 0.0f), (float)(W - 1));
+    pv_ = fminf(fmaxf(pv_, 0.0f), (float)(H - 1));
+  }
+  int cu = min((int)floorf(pu + 0.5f), W - 1), cv = min((int)floorf(pv_ + 0.5f), H - 1);
+  // coarse-to-fine refinement: maximum descriptor similarity in a window
+  float dq[D];
+  DescRow<T, D>::load(Dq + (o + n) * D, dq);
+  const T* Dr_e = Dr + o * D;
+  const int r = mc.radius;
+  for (int lev = 0; lev < mc.n_levels; ++lev) {
+    const int dil = mc.dil[lev];
+    float best = -INFINITY;
+    int bu = cu, bv = cv;
+    for (int dy = -r; dy <= r; ++dy) {
+      const int vv = cv + dy * dil;
+      if (vv < 0 || vv >= H) continue;
+      for (int dx = -r; dx <= r; ++dx) {
+        const int uu = cu + dx * dil;
+        if (uu < 0 || uu >= W) continue;
+        const float s = DescRow<T, D>::dot(Dr_e + ((int64_t)vv * W + uu) * D, dq);
+        if (s > best) {
+          best = s;
+          bu = uu;
+          bv = vv;
+        }
+      }
+    }
+    cu = bu;
+    cv = bv;
+  }
+  const int m = cv * W + cu;
+  const float3 y = ld3(Xr_e, m);
+  const float dxv = y.x - x.x, dyv = y.y - x.y, dzv = y.z - x.z;
+  const float dist = sqrtf(dxv * dxv + dyv * dyv + dzv * dzv);
+  const bool ok = finite3(y) && dist <= mc.max_rel * sqrtf(nx2);
+  out_idx[o + n] = ok ? m : -1;
+  stf(out_q + o + n, ok ? sqrtf(ldf(Qr + o + m) * ldf(Qq + o + n)) : 0.0f);
+}
+
+template <typename T, int D>
+static void launch_match(const PlanView& pv, const MatchConst& mc, const void* Xr, const void* Xq, const void* Dr,
+                         const void* Dq, const void* Qr, const void* Qq, const int32_t* init, int32_t* out_idx,
+                         void* out_q, int e0, int e1, int b0, int nblocks, cudaStream_t s) {
+  match_kernel<T, D><<<nblocks, kMatchBX * kMatchBY, 0, s>>>(
+      pv, mc, static_cast<const T*>(Xr), static_cast<const T*>(Xq), static_cast<const T*>(Dr),
+      static_cast<const T*>(Dq), static_cast<const T*>(Qr), static_cast<const T*>(Qq), init, out_idx,
+      static_cast<T*>(out_q), e0, e1, b0);
+}
+
+}  // namespace mslam
+
+using namespace mslam;
+
+extern "C" mslam_status mslam_match(const mslam_params* p, const mslam_plan* plan, mslam_dtype dt, int32_t d,
+                                    const void* X_ref, const void* X_qry, const void* D_ref, const void* D_qry,
+                                    const void* Q_ref, const void* Q_qry, const int32_t* init_idx, int32_t* idx_out,
+                                    void* q_out, int32_t edge_begin, int32_t edge_end, uint32_t flags,
+                                    void* stream) {
+  if (!p || !check_plan_uploaded(plan)) {
+    if (!p) set_error("params is NULL");
+    return MSLAM_ERR_ARG;
+  }
+  if (dt != MSLAM_F32 && dt != MSLAM_F16) {
+    set_error("unsupported dtype %d", (int)dt);
+    return MSLAM_ERR_ARG;
+  }
+  if (d != 16 && d != 24 && d != 32) {
+    set_error("descriptor dimension %d not supported (16, 24 or 32)", d);
+    return MSLAM_ERR_ARG;
+  }
+  if (!X_ref || !X_qry || !D_ref || !D_qry || !Q_ref || !Q_qry || !idx_out || !q_out) {
+    set_error("match: NULL device pointer");
+    return MSLAM_ERR_ARG;
+  }
+  const size_t esz = dt == MSLAM_F32 ? 4 : 2;
+  auto mis = [&](const void* ptr, size_t al) { return (reinterpret_cast<uintptr_t>(ptr) % al) != 0; };
+  if (mis(D_ref, 16) || mis(D_qry, 16) || mis(X_ref, esz) || mis(X_qry, esz) || mis(Q_ref, esz) ||
+      mis(Q_qry, esz) || mis(q_out, esz) || mis(idx_out, 4) || (init_idx && mis(init_idx, 4))) {
+    set_error("match: misaligned pointer (descriptors need 16-byte alignment)");
+    return MSLAM_ERR_ARG;
+  }
+  if (p->lm_iters < 0 || p->lm_iters > 1000 || p->win_radius < 0 || p->win_radius > 32 || p->n_levels < 0 ||
+      p->n_levels > 4 || !(p->lm_lambda >= 0.0f) || !(p->max_rel_dist3d >= 0.0f)) {
+    set_error("match: parameter out of range");
+    return MSLAM_ERR_ARG;
+  }
+  for (int l = 0; l < p->n_levels; ++l)
+    if (p->win_dilation[l] < 1 || p->win_dilation[l] > 64) {
+      set_error("match: win_dilation[%d] = %d out of range", l, p->win_dilation[l]);
+      return MSLAM_ERR_ARG;
+    }
+  const PlanView pv = plan_view(plan);
+  int e0 = edge_begin, e1 = edge_end;
+  if (e0 < 0 && e1 < 0) {
+    e0 = 0;
+    e1 = pv.E;
+  }
+  if (e0 < 0 || e1 > pv.E || e0 > e1) {
+    set_error("match: edge range [%d, %d) outside [0, %d)", e0, e1, pv.E);
+    return MSLAM_ERR_ARG;
+  }
+  if (e0 == e1) return MSLAM_OK;
+  MatchConst mc;
+  mc.lm_lambda = p->lm_lambda;
+  mc.max_rel = p->max_rel_dist3d;
+  mc.lm_iters = p->lm_iters;
+  mc.radius = p->win_radius;
+  mc.n_levels = p->n_levels;
+  for (int l = 0; l < 4; ++l) mc.dil[l] = p->win_dilation[l];
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  auto go = [&](int a, int b) {
+    int b0, b1x, bt0, bt1;
+    plan_edge_mblocks(plan, a, &b0, &bt0);
+    plan_edge_mblocks(plan, b - 1, &bt1, &b1x);
+    (void)bt0;
+    (void)bt1;
+    const int nb = b1x - b0;
+#define MSLAM_MATCH_CASE(TT, DD)                                                                              \
+  launch_match<TT, DD>(pv, mc, X_ref, X_qry, D_ref, D_qry, Q_ref, Q_qry, init_idx, idx_out, q_out, a, b, b0, nb, \
+                       s)
+    if (dt == MSLAM_F32) {
+      if (d == 16) MSLAM_MATCH_CASE(float, 16);
+      else if (d == 24) MSLAM_MATCH_CASE(float, 24);
+      else MSLAM_MATCH_CASE(float, 32);
+    } else {
+      if (d == 16) MSLAM_MATCH_CASE(__half, 16);
+      else if (d == 24) MSLAM_MATCH_CASE(__half, 24);
+      else MSLAM_MATCH_CASE(__half, 32);
+    }
+#undef MSLAM_MATCH_CASE
+  };
+  if (flags & MSLAM_FLAG_PER_EDGE) {
+    for (int e = e0; e < e1; ++e) go(e, e + 1);
+  } else {
+    go(e0, e1);
+  }
+  return cuda_check(cudaGetLastError(), "match launch");
+}

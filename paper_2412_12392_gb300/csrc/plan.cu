@@ -1,0 +1,417 @@
+// Host side of the library: parameters, error strings and the graph plan --
+// pool offsets, work tiles, and the symbolic block Cholesky of every graph's
+// gauge-reduced 7N system (Sec. 3.5: "sparse Cholesky decomposition as the
+// system is not dense"), ordered by greedy minimum degree.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <set>
+#include <vector>
+
+#include "common.cuh"
+
+struct mslam_plan {
+  int32_t N = 0, E = 0, G = 0;
+  std::vector<int32_t> kf_hw, edges, graph_of_kf;
+  std::vector<int64_t> kf_off, e_off;
+  std::vector<mslam::DevEdge> dedges;
+  std::vector<mslam::DevTile> tiles;
+  std::vector<mslam::DevGraph> graphs;
+  std::vector<int32_t> ints;
+  std::vector<int32_t> order;
+  int64_t n_blocks_total = 0, n_trips_total = 0, solve_ws_doubles = 0;
+  int32_t n_mblocks = 0;
+  void* dev = nullptr;
+  size_t dev_bytes = 0;
+  size_t off_edges = 0, off_tiles = 0, off_graphs = 0, off_ints = 0, blob_bytes = 0;
+};
+
+namespace mslam {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+}
+
+mslam_status cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return MSLAM_OK;
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return MSLAM_ERR_CUDA;
+}
+
+bool check_plan_uploaded(const mslam_plan* plan) {
+  if (!plan) {
+    set_error("plan is NULL");
+    return false;
+  }
+  if (!plan->dev) {
+    set_error("plan has not been uploaded (mslam_plan_upload)");
+    return false;
+  }
+  return true;
+}
+
+PlanView plan_view(const mslam_plan* plan) {
+  PlanView v;
+  const char* base = static_cast<const char*>(plan->dev);
+  v.N = plan->N;
+  v.E = plan->E;
+  v.G = plan->G;
+  v.n_tiles = (int32_t)plan->tiles.size();
+  v.n_mblocks = plan->n_mblocks;
+  v.edges = reinterpret_cast<const DevEdge*>(base + plan->off_edges);
+  v.tiles = reinterpret_cast<const DevTile*>(base + plan->off_tiles);
+  v.graphs = reinterpret_cast<const DevGraph*>(base + plan->off_graphs);
+  v.ints = reinterpret_cast<const int32_t*>(base + plan->off_ints);
+  return v;
+}
+
+void plan_edge_tiles(const mslam_plan* plan, int e, int* t0, int* t1) {
+  *t0 = plan->dedges[e].tile_begin;
+  *t1 = plan->dedges[e].tile_end;
+}
+
+void plan_edge_mblocks(const mslam_plan* plan, int e, int* b0, int* b1) {
+  *b0 = plan->dedges[e].mblock_begin;
+  *b1 = (e + 1 < plan->E) ? plan->dedges[e + 1].mblock_begin : plan->n_mblocks;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Symbolic factorisation of one graph.
+static void build_graph(mslam_plan* P, int g, const std::vector<int>& kfs) {
+  DevGraph dg{};
+  const int gauge = kfs.front();  // lowest-indexed keyframe of the graph
+  dg.gauge = gauge;
+  const int m = (int)kfs.size() - 1;
+  dg.m = m;
+  // undirected adjacency between the non-fixed keyframes
+  std::map<int, std::set<int>> adj;
+  for (int k : kfs)
+    if (k != gauge) adj[k];
+  for (int e = 0; e < P->E; ++e) {
+    const int i = P->edges[2 * e], j = P->edges[2 * e + 1];
+    if (P->graph_of_kf[i] != g) continue;
+    if (i != gauge && j != gauge) {
+      adj[i].insert(j);
+      adj[j].insert(i);
+    }
+  }
+  // greedy minimum degree (ties: lowest keyframe index); elimination makes
+  // the remaining neighbours a clique, whose members become column rows
+  std::vector<int> pos_kf;          // elimination position -> keyframe
+  std::vector<std::vector<int>> nb; // neighbours (keyframes) at elimination
+  std::map<int, std::set<int>> live = adj;
+  while (!live.empty()) {
+    int best = -1;
+    size_t bd = SIZE_MAX;
+    for (auto& kv : live)
+      if (kv.second.size() < bd) {
+        bd = kv.second.size();
+        best = kv.first;
+      }
+    std::vector<int> ns(live[best].begin(), live[best].end());
+    for (int a : ns) {
+      live[a].erase(best);
+      for (int b : ns)
+        if (a != b) live[a].insert(b);
+    }
+    live.erase(best);
+    pos_kf.push_back(best);
+    nb.push_back(ns);
+  }
+  std::map<int, int> pos_of;
+  for (int p = 0; p < m; ++p) pos_of[pos_kf[p]] = p;
+  for (int p = 0; p < m; ++p) P->order[pos_kf[p]] = p;
+  P->order[gauge] = -1;
+
+  // L pattern: column p has rows pos_of[neighbours] (all > p), sorted
+  std::vector<std::vector<int>> rows(m);
+  for (int p = 0; p < m; ++p) {
+    for (int k : nb[p]) rows[p].push_back(pos_of[k]);
+    std::sort(rows[p].begin(), rows[p].end());
+  }
+  std::map<std::pair<int, int>, int> blk;  // (row, col) -> block id
+  int nb_total = m;
+  for (int p = 0; p < m; ++p)
+    for (int r : rows[p]) blk[{r, p}] = nb_total++;
+  dg.n_blocks = nb_total;
+
+  std::vector<int32_t>& I = P->ints;
+  dg.off_pose = (int32_t)I.size();
+  for (int p = 0; p < m; ++p) I.push_back(pos_kf[p]);
+  dg.off_col = (int32_t)I.size();
+  {
+    int acc = 0;
+    for (int p = 0; p <= m; ++p) {
+      I.push_back(acc);
+      if (p < m) acc += (int)rows[p].size();
+    }
+  }
+  dg.off_colent = (int32_t)I.size();
+  for (int p = 0; p < m; ++p)
+    for (int r : rows[p]) {
+      I.push_back(r);
+      I.push_back(blk[{r, p}]);
+    }
+  // update triples of column p: A(rb, ra) -= L(rb, p) L(ra, p)^T for ra <= rb
+  dg.off_trip = (int32_t)I.size();
+  std::vector<int32_t> trips;
+  {
+    int acc = 0;
+    std::vector<int> ptr;
+    for (int p = 0; p < m; ++p) {
+      ptr.push_back(acc);
+      const auto& R = rows[p];
+      for (size_t a = 0; a < R.size(); ++a)
+        for (size_t b = a; b < R.size(); ++b) {
+          const int ra = R[a], rb = R[b];
+          const int target = (ra == rb) ? ra : blk.at({rb, ra});
+          trips.push_back(target);
+          trips.push_back(blk.at({rb, p}));
+          trips.push_back(blk.at({ra, p}));
+          ++acc;
+        }
+    }
+    ptr.push_back(acc);
+    for (int v : ptr) I.push_back(v);
+    P->n_trips_total += acc;
+  }
+  dg.off_tripent = (int32_t)I.size();
+  I.insert(I.end(), trips.begin(), trips.end());
+
+  // assembly lists (edge order): quadrant 0 = H_ii, 1 = H_jj, 2 = rows i cols j, 3 = rows j cols i
+  std::vector<std::vector<int>> asml(nb_total), gasm(m);
+  for (int e = 0; e < P->E; ++e) {
+    const int i = P->edges[2 * e], j = P->edges[2 * e + 1];
+    if (P->graph_of_kf[i] != g) continue;
+    if (i != gauge) {
+      asml[pos_of[i]].push_back(4 * e + 0);
+      gasm[pos_of[i]].push_back(2 * e + 0);
+    }
+    if (j != gauge) {
+      asml[pos_of[j]].push_back(4 * e + 1);
+      gasm[pos_of[j]].push_back(2 * e + 1);
+    }
+    if (i != gauge && j != gauge) {
+      const int pi = pos_of[i], pj = pos_of[j];
+      if (pi > pj)
+        asml[blk.at({pi, pj})].push_back(4 * e + 2);
+      else
+        asml[blk.at({pj, pi})].push_back(4 * e + 3);
+    }
+  }
+  dg.off_asm = (int32_t)I.size();
+  {
+    int acc = 0;
+    for (int b = 0; b <= nb_total; ++b) {
+      I.push_back(acc);
+      if (b < nb_total) acc += (int)asml[b].size();
+    }
+  }
+  dg.off_asment = (int32_t)I.size();
+  for (auto& v : asml) I.insert(I.end(), v.begin(), v.end());
+  dg.off_gasm = (int32_t)I.size();
+  {
+    int acc = 0;
+    for (int p = 0; p <= m; ++p) {
+      I.push_back(acc);
+      if (p < m) acc += (int)gasm[p].size();
+    }
+  }
+  dg.off_gasment = (int32_t)I.size();
+  for (auto& v : gasm) I.insert(I.end(), v.begin(), v.end());
+
+  dg.ws_off = P->solve_ws_doubles;
+  // numeric workspace: blocks (49 each), rhs (7 m), assembled diagonal (7 m)
+  P->solve_ws_doubles += (int64_t)nb_total * 49 + 14 * (int64_t)m;
+  P->n_blocks_total += nb_total;
+  P->graphs.push_back(dg);
+}
+
+}  // namespace mslam
+
+using namespace mslam;
+
+extern "C" {
+
+void mslam_default_params(mslam_params* p) {
+  if (!p) return;
+  p->sigma_ray = 0.01f;
+  p->sigma_dist = 0.1f;
+  p->huber_delta = 1.345f;
+  p->q_min = 1.5f;
+  p->lm_lambda = 1e-8f;
+  p->lm_iters = 10;
+  p->win_radius = 3;
+  p->n_levels = 2;
+  p->win_dilation[0] = 2;
+  p->win_dilation[1] = 1;
+  p->win_dilation[2] = 1;
+  p->win_dilation[3] = 1;
+  p->max_rel_dist3d = 0.1f;
+  p->conv_tol = 1e-10;
+}
+
+const char* mslam_last_error(void) { return g_err; }
+
+const char* mslam_version(void) { return "mslam-gb300 0.1 (sm_103a)"; }
+
+mslam_status mslam_plan_create(int32_t N, const int32_t* kf_hw, int32_t E, const int32_t* edges,
+                               const int32_t* graph_of_kf, mslam_plan** out) {
+  if (!out) {
+    set_error("out is NULL");
+    return MSLAM_ERR_ARG;
+  }
+  *out = nullptr;
+  if (N < 1 || !kf_hw || E < 0 || (E > 0 && !edges)) {
+    set_error("bad sizes or NULL host arrays (N=%d, E=%d)", N, E);
+    return MSLAM_ERR_ARG;
+  }
+  mslam_plan* P = new mslam_plan();
+  P->N = N;
+  P->E = E;
+  P->kf_hw.assign(kf_hw, kf_hw + 2 * N);
+  P->edges.assign(edges, edges + 2 * (size_t)E);
+  P->graph_of_kf.assign(N, 0);
+  if (graph_of_kf) P->graph_of_kf.assign(graph_of_kf, graph_of_kf + N);
+  int G = 0;
+  for (int k = 0; k < N; ++k) {
+    const int H = kf_hw[2 * k], W = kf_hw[2 * k + 1];
+    if (H < 2 || W < 2 || H > 8192 || W > 8192 || P->graph_of_kf[k] < 0 || P->graph_of_kf[k] >= N) {
+      set_error("keyframe %d: bad size %dx%d or graph id %d", k, H, W, P->graph_of_kf[k]);
+      delete P;
+      return MSLAM_ERR_ARG;
+    }
+    G = std::max(G, P->graph_of_kf[k] + 1);
+  }
+  std::vector<std::vector<int>> kfs(G);
+  for (int k = 0; k < N; ++k) kfs[P->graph_of_kf[k]].push_back(k);
+  for (int g = 0; g < G; ++g)
+    if (kfs[g].empty()) {
+      set_error("graph id %d has no keyframe", g);
+      delete P;
+      return MSLAM_ERR_ARG;
+    }
+  P->G = G;
+  P->kf_off.assign(N + 1, 0);
+  for (int k = 0; k < N; ++k) P->kf_off[k + 1] = P->kf_off[k] + (int64_t)kf_hw[2 * k] * kf_hw[2 * k + 1];
+  P->e_off.assign(E + 1, 0);
+  for (int e = 0; e < E; ++e) {
+    const int i = edges[2 * e], j = edges[2 * e + 1];
+    if (i < 0 || j < 0 || i >= N || j >= N || i == j || P->graph_of_kf[i] != P->graph_of_kf[j] ||
+        kf_hw[2 * i] != kf_hw[2 * j] || kf_hw[2 * i + 1] != kf_hw[2 * j + 1]) {
+      set_error("edge %d = (%d, %d): out of range, self edge, different graphs or sizes", e, i, j);
+      delete P;
+      return MSLAM_ERR_ARG;
+    }
+    const int H = kf_hw[2 * j], W = kf_hw[2 * j + 1];
+    P->e_off[e + 1] = P->e_off[e] + (int64_t)H * W;
+    DevEdge d{};
+    d.i = i;
+    d.j = j;
+    d.H = H;
+    d.W = W;
+    d.off_e = P->e_off[e];
+    d.off_i = P->kf_off[i];
+    d.off_j = P->kf_off[j];
+    d.graph = P->graph_of_kf[i];
+    d.tile_begin = (int32_t)P->tiles.size();
+    for (int b = 0; b < H * W; b += kLinTile) {
+      DevTile t{};
+      t.edge = e;
+      t.begin = b;
+      t.end = std::min(H * W, b + kLinTile);
+      P->tiles.push_back(t);
+    }
+    d.tile_end = (int32_t)P->tiles.size();
+    d.mblock_begin = P->n_mblocks;
+    P->n_mblocks += ((W + kMatchBX - 1) / kMatchBX) * ((H + kMatchBY - 1) / kMatchBY);
+    P->dedges.push_back(d);
+  }
+  P->order.assign(N, -1);
+  for (int g = 0; g < G; ++g) build_graph(P, g, kfs[g]);
+  size_t off = 0;
+  P->off_edges = off;
+  off = align256(off + sizeof(DevEdge) * P->dedges.size());
+  P->off_tiles = off;
+  off = align256(off + sizeof(DevTile) * P->tiles.size());
+  P->off_graphs = off;
+  off = align256(off + sizeof(DevGraph) * P->graphs.size());
+  P->off_ints = off;
+  off = align256(off + sizeof(int32_t) * P->ints.size());
+  P->blob_bytes = std::max<size_t>(off, 256);
+  *out = P;
+  return MSLAM_OK;
+}
+
+void mslam_plan_destroy(mslam_plan* plan) { delete plan; }
+
+size_t mslam_plan_device_bytes(const mslam_plan* plan) { return plan ? plan->blob_bytes : 0; }
+
+mslam_status mslam_plan_upload(mslam_plan* plan, void* dev, size_t bytes, void* stream) {
+  if (!plan || !dev || bytes < plan->blob_bytes || (reinterpret_cast<uintptr_t>(dev) & 255)) {
+    set_error("plan upload: NULL plan/buffer, buffer smaller than %zu bytes, or not 256-byte aligned",
+              plan ? plan->blob_bytes : (size_t)0);
+    return MSLAM_ERR_ARG;
+  }
+  std::vector<char> blob(plan->blob_bytes, 0);
+  std::memcpy(blob.data() + plan->off_edges, plan->dedges.data(), sizeof(DevEdge) * plan->dedges.size());
+  std::memcpy(blob.data() + plan->off_tiles, plan->tiles.data(), sizeof(DevTile) * plan->tiles.size());
+  std::memcpy(blob.data() + plan->off_graphs, plan->graphs.data(), sizeof(DevGraph) * plan->graphs.size());
+  std::memcpy(blob.data() + plan->off_ints, plan->ints.data(), sizeof(int32_t) * plan->ints.size());
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  mslam_status st = cuda_check(cudaMemcpyAsync(dev, blob.data(), blob.size(), cudaMemcpyHostToDevice, s),
+                               "plan upload");
+  if (st != MSLAM_OK) return st;
+  // the staging vector is freed on return: wait for the copy out of it
+  st = cuda_check(cudaStreamSynchronize(s), "plan upload sync");
+  if (st != MSLAM_OK) return st;
+  plan->dev = dev;
+  plan->dev_bytes = bytes;
+  return MSLAM_OK;
+}
+
+int64_t mslam_plan_kf_pixels(const mslam_plan* plan) { return plan ? plan->kf_off.back() : 0; }
+int64_t mslam_plan_edge_pixels(const mslam_plan* plan) { return plan ? plan->e_off.back() : 0; }
+int32_t mslam_plan_num_graphs(const mslam_plan* plan) { return plan ? plan->G : 0; }
+
+void mslam_plan_offsets(const mslam_plan* plan, int64_t* kf_off, int64_t* e_off) {
+  if (!plan) return;
+  if (kf_off) std::copy(plan->kf_off.begin(), plan->kf_off.end(), kf_off);
+  if (e_off) std::copy(plan->e_off.begin(), plan->e_off.end(), e_off);
+}
+
+void mslam_plan_stats(const mslam_plan* plan, int32_t* order, int64_t* counts) {
+  if (!plan) return;
+  if (order) std::copy(plan->order.begin(), plan->order.end(), order);
+  if (counts) {
+    counts[0] = plan->n_blocks_total;
+    counts[1] = plan->n_trips_total;
+    counts[2] = (int64_t)plan->tiles.size();
+    counts[3] = plan->n_mblocks;
+  }
+}
+
+size_t mslam_workspace_bytes(const mslam_plan* plan, int32_t op) {
+  if (!plan) return 0;
+  switch (op) {
+    case MSLAM_OP_LINEARIZE:
+      return align256(sizeof(float) * kAccStride * std::max<size_t>(plan->tiles.size(), 1));
+    case MSLAM_OP_SOLVE:
+      return align256(sizeof(double) * std::max<int64_t>(plan->solve_ws_doubles, 1));
+    case MSLAM_OP_BACKWARD:
+      return align256(sizeof(double) * std::max<int64_t>(plan->solve_ws_doubles, 1)) +
+             align256(sizeof(double) * 7 * (size_t)plan->N) * 2;
+    default:
+      return 0;
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,316 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs (the oracle consumes the stored values, dequantised).
+
+Covers matching (Sec. 3.2), linearisation (Eq. backend_ray, Supp. S1), the
+gauge-fixed solve and retraction (Sec. 3.5), the full Gauss-Newton loop, both
+storage dtypes, the plain per-edge and the batched launch forms, CUDA-graph
+capture, and the degenerate cases (invalid pixels, disconnected graphs,
+single keyframe, empty edge list)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from parity import (BLOCK_RTOL, MATCH_AGREE, assert_poses_close, block_rel_err, f64, match_agreement,
+                    pose_errors)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2412_12392_gb300 import build
+    build.build()
+    import paper_2412_12392_gb300 as M
+    return M
+
+
+def to_dev(w, dtype=torch.float32):
+    return w.to_storage(dtype).to("cuda")
+
+
+def gpu_match(M, plan, P, wd, **kw):
+    return M.match(plan, P, wd.X_ref, wd.X_qry, wd.D_ref, wd.D_qry, wd.Q_ref, wd.Q_qry, **kw)
+
+
+def oracle_match_all(w, par, diag=True):
+    idx, q, dg = [], [], []
+    for e in range(w.E):
+        out = oracle.match_workload(w, e, diag=diag, **par)
+        idx.append(out[0])
+        q.append(out[1])
+        if diag:
+            dg.append(out[2])
+    return np.concatenate(idx), np.concatenate(q), (np.concatenate(dg) if diag else None)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
+def test_match_parity_tiny(M, tiny_wl, dtype):
+    P = M.default_params()
+    par = M.params_dict(P)
+    ws = tiny_wl.to_storage(dtype)  # the oracle reads the stored (dequantised) values
+    wd = ws.to("cuda")
+    plan = M.Plan(ws.kf_hw.numpy(), ws.edges.numpy())
+    idx_g, q_g = gpu_match(M, plan, P, wd)
+    torch.cuda.synchronize()
+    idx_r, q_r, dg = oracle_match_all(ws, par)
+    agree, ndis, nunion, expl = match_agreement(idx_g, idx_r, dg, par)
+    print(f"match parity {dtype}: agree {agree:.6f} ({ndis} of {nunion}), explained {expl:.3f}")
+    assert agree >= MATCH_AGREE
+    both = (f64(idx_g) == idx_r) & (idx_r >= 0)
+    qg = f64(q_g)[both]
+    qr = q_r[both].astype(np.float32 if dtype == torch.float32 else np.float16).astype(np.float64)
+    rtol = 2e-6 if dtype == torch.float32 else 1e-3
+    assert np.abs(qg - qr).max() <= rtol * np.abs(qr).max()
+
+
+def test_match_forms_and_init_agree(M, tiny_wl):
+    P = M.default_params()
+    wd = to_dev(tiny_wl)
+    plan = M.Plan(tiny_wl.kf_hw.numpy(), tiny_wl.edges.numpy())
+    a_idx, a_q = gpu_match(M, plan, P, wd)
+    b_idx, b_q = gpu_match(M, plan, P, wd, per_edge=True)
+    assert torch.equal(a_idx, b_idx) and torch.equal(a_q, b_q)
+    # edge sub-range touches only that edge's slice
+    c_idx = torch.full_like(a_idx, -7)
+    c_q = torch.zeros_like(a_q)
+    gpu_match(M, plan, P, wd, idx_out=c_idx, q_out=c_q, edge_range=(1, 2))
+    sl = tiny_wl.edge_slice(1)
+    assert torch.equal(c_idx[sl], a_idx[sl])
+    assert bool((c_idx[:sl.start] == -7).all()) and bool((c_idx[sl.stop:] == -7).all())
+    # initialisation from previous matches (tracking) against the oracle
+    par = M.params_dict(P)
+    init = tiny_wl.gt_match.to("cuda")
+    i_idx, _ = gpu_match(M, plan, P, wd, init_idx=init)
+    r_idx = np.concatenate([oracle.match_workload(tiny_wl, e, init_idx=tiny_wl.gt_match[tiny_wl.edge_slice(e)],
+                                                  **par)[0] for e in range(tiny_wl.E)])
+    agree, *_ = match_agreement(i_idx, r_idx)
+    assert agree >= MATCH_AGREE
+
+
+def test_match_invalid_and_edge_pixels(M):
+    """Zero / NaN query points are rejected; queries projecting outside the
+    reference image clamp to the border; out-of-range init indices fall back
+    to the identity."""
+    rng = np.random.default_rng(3)
+    H, W, d = 20, 36, 16
+    X = np.c_[rng.uniform(-1, 1, H * W), rng.uniform(-1, 1, H * W), rng.uniform(2, 4, H * W)].astype(np.float32)
+    Xq = X.copy() * 1.01
+    Xq[::5] = 0
+    Xq[2::17] = np.nan
+    Xq[3::13, 0] += 5.0  # far outside the field of view
+    D = rng.normal(size=(H * W, d)).astype(np.float32)
+    D /= np.linalg.norm(D, axis=1, keepdims=True)
+    Q = rng.uniform(1, 10, H * W).astype(np.float32)
+    init = np.arange(H * W, dtype=np.int32)
+    init[1::9] = 10 ** 8
+    init[4::11] = -3
+    plan = M.Plan([[H, W], [H, W]], [[0, 1]])
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    P = M.default_params()
+    idx_g, q_g = M.match(plan, P, t(X), t(Xq), t(D), t(D), t(Q), t(Q), init_idx=t(init))
+    par = M.params_dict(P)
+    idx_r, q_r, dg = oracle.match(H, W, X, Xq, D, D, Q, Q, init_idx=np.where((init >= 0) & (init < H * W), init, -1),
+                                  diag=True, **par)
+    assert bool((idx_g.cpu().numpy()[::5] == -1).all()) and bool((idx_g.cpu().numpy()[2::17] == -1).all())
+    agree, *_ = match_agreement(idx_g, idx_r)
+    assert agree >= 0.99
+
+
+def oracle_blocks(w, T, idx, q, par):
+    H, g, c, nv = [], [], [], []
+    for e in range(w.E):
+        i, j = int(w.edges[e, 0]), int(w.edges[e, 1])
+        sl = w.edge_slice(e)
+        Hb, gb, cb, nb = oracle.linearize_edge(T[i], T[j], w.X_canon[w.kf_slice(i)], w.X_canon[w.kf_slice(j)],
+                                               idx[sl], q[sl], **par)
+        H.append(Hb)
+        g.append(gb)
+        c.append(cb)
+        nv.append(nb)
+    return np.array(H), np.array(g), np.array(c), np.array(nv)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
+def test_linearize_parity_tiny(M, tiny_wl, dtype):
+    P = M.default_params()
+    par = M.params_dict(P)
+    ws = tiny_wl.to_storage(dtype)
+    # matches from the oracle, q stored in the storage dtype for both sides
+    idx_r, q_r, _ = oracle_match_all(ws, par, diag=False)
+    q_s = torch.from_numpy(q_r).to(dtype)
+    wd = ws.to("cuda")
+    plan = M.Plan(ws.kf_hw.numpy(), ws.edges.numpy())
+    T = ws.T_init.clone()
+    H, g, c, nv = M.gn_linearize(plan, P, T.cuda(), wd.X_canon, torch.from_numpy(idx_r).cuda(), q_s.cuda())
+    torch.cuda.synchronize()
+    Hr, gr, cr, nvr = oracle_blocks(ws, T.numpy(), idx_r, q_s, par)
+    eh, eg = block_rel_err(H, Hr), block_rel_err(g, gr)
+    print(f"linearize {dtype}: max H rel {eh.max():.2e}, g rel {eg.max():.2e}")
+    assert eh.max() <= BLOCK_RTOL and eg.max() <= BLOCK_RTOL
+    assert np.allclose(f64(c), cr, rtol=1e-5)
+    assert np.array_equal(nv.cpu().numpy(), nvr)
+    # the plain per-edge form gives bitwise the same blocks
+    H2, g2, c2, nv2 = M.gn_linearize(plan, P, T.cuda(), wd.X_canon, torch.from_numpy(idx_r).cuda(), q_s.cuda(),
+                                     per_edge=True)
+    assert torch.equal(H, H2) and torch.equal(g, g2) and torch.equal(c, c2)
+
+
+def test_solve_parity_on_oracle_blocks(M, tiny_wl):
+    """The solve alone: both sides consume the oracle's blocks (rounded to
+    FP32 for the GPU input, read back exactly by the oracle)."""
+    P = M.default_params()
+    par = M.params_dict(P)
+    w = tiny_wl
+    idx_r, q_r, _ = oracle_match_all(w, par, diag=False)
+    Hr, gr, _, _ = oracle_blocks(w, w.T_init.numpy(), idx_r, q_r, par)
+    H32 = torch.from_numpy(Hr).float()
+    g32 = torch.from_numpy(gr).float()
+    plan = M.Plan(w.kf_hw.numpy(), w.edges.numpy())
+    T = w.T_init.clone().cuda()
+    tau, st = M.gn_solve(plan, P, H32.cuda(), g32.cuda(), T, tau=torch.zeros(w.N, 7, dtype=torch.float64,
+                                                                              device="cuda"))
+    torch.cuda.synchronize()
+    s, T_r, tau_r = oracle.gn_solve(w.N, w.edges.numpy(), H32.double(), g32.double(), w.T_init.numpy())
+    assert s == 0 and int(st[0]) in (0, 1)
+    assert np.abs(f64(tau) - tau_r).max() <= 1e-9 * max(1.0, np.abs(tau_r).max())
+    assert torch.equal(T[0].cpu(), w.T_init[0])  # gauge untouched, bitwise
+    assert_poses_close(T, T_r, 1e-9)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
+def test_gauss_newton_parity_tiny(M, tiny_wl, dtype):
+    P = M.default_params()
+    par = M.params_dict(P)
+    ws = tiny_wl.to_storage(dtype)
+    idx_r, q_r, _ = oracle_match_all(ws, par, diag=False)
+    q_s = torch.from_numpy(q_r).to(dtype)
+    wd = ws.to("cuda")
+    plan = M.Plan(ws.kf_hw.numpy(), ws.edges.numpy())
+    gn = M.GaussNewton(plan, P, wd.X_canon, torch.from_numpy(idx_r).cuda(), q_s.cuda())
+    T_g = gn.run(ws.T_init.cuda(), ws.n_gn_iters).cpu()
+    st, T_r, hist, done = oracle.gauss_newton(ws.N, ws.edges.numpy(), ws.kf_off.numpy(), ws.e_off.numpy(),
+                                              ws.X_canon, idx_r, q_s, ws.T_init.numpy(), ws.n_gn_iters, **par)
+    assert st == 0
+    e = assert_poses_close(T_g, T_r)
+    print(f"GN parity {dtype}: max (rot, trans, scale) {e.max(axis=0)}")
+    assert torch.equal(T_g[0], ws.T_init[0])
+    # and the optimisation really moved the poses toward the ground truth
+    e0 = pose_errors(ws.T_init, ws.T_gt)[1:, 0].max()
+    e1 = pose_errors(T_g, ws.T_gt)[1:, 0].max()
+    assert e1 < 0.25 * e0
+
+
+def test_full_pipeline_tiny(M, tiny_wl):
+    """GPU matching feeding GPU Gauss-Newton against the oracle doing both."""
+    P = M.default_params()
+    par = M.params_dict(P)
+    w = tiny_wl
+    wd = to_dev(w)
+    plan = M.Plan(w.kf_hw.numpy(), w.edges.numpy())
+    idx_g, q_g = gpu_match(M, plan, P, wd)
+    gn = M.GaussNewton(plan, P, wd.X_canon, idx_g, q_g)
+    T_g = gn.run(w.T_init.cuda(), w.n_gn_iters).cpu()
+    idx_r, q_r, _ = oracle_match_all(w, par, diag=False)
+    st, T_r, _, _ = oracle.gauss_newton(w.N, w.edges.numpy(), w.kf_off.numpy(), w.e_off.numpy(), w.X_canon, idx_r,
+                                        q_r, w.T_init.numpy(), w.n_gn_iters, **par)
+    assert_poses_close(T_g, T_r)
+
+
+def test_cuda_graph_replay_matches_eager(M, tiny_wl):
+    P = M.default_params()
+    w = tiny_wl
+    wd = to_dev(w)
+    plan = M.Plan(w.kf_hw.numpy(), w.edges.numpy())
+    idx_g, q_g = gpu_match(M, plan, P, wd)
+    gn = M.GaussNewton(plan, P, wd.X_canon, idx_g, q_g)
+    T_e = gn.run(w.T_init.cuda(), 5).clone()
+    gn.capture(5)
+    T_c = gn.replay(w.T_init.cuda()).clone()
+    torch.cuda.synchronize()
+    assert torch.equal(T_e, T_c)
+
+
+def test_exact_recovery_gpu(M):
+    from test_oracle_gn import exact_graph
+    rng = np.random.default_rng(1)
+    T_gt, X, edges, kf_off, e_off, idx, q = exact_graph(rng, N=5, H=32, W=48)
+    N = T_gt.shape[0]
+    T0 = T_gt.copy()
+    for k in range(1, N):
+        T0[k] = oracle.sim3_mul(oracle.sim3_exp(np.r_[rng.normal(size=3) * 0.05, rng.normal(size=3) * 0.03, 0.05]),
+                                T_gt[k])
+    plan = M.Plan([[32, 48]] * N, edges)
+    P = M.default_params()
+    gn = M.GaussNewton(plan, P, torch.from_numpy(X).float().cuda(), torch.from_numpy(idx).cuda(),
+                       torch.from_numpy(q).float().cuda())
+    T = gn.run(torch.from_numpy(T0).cuda(), 15).cpu()
+    # float storage of the points limits the recovery to ~1e-7
+    assert_poses_close(T, T_gt, 1e-5)
+
+
+def test_disconnected_graph_not_pd(M):
+    from test_oracle_gn import exact_edge
+    rng = np.random.default_rng(4)
+    Ti, Tj, Xi, Xj, idx, q = exact_edge(rng, H=16, W=16)
+    N = 4
+    X = np.concatenate([Xi, Xj, Xi, Xj]).astype(np.float32)
+    plan = M.Plan([[16, 16]] * N, [[0, 1], [2, 3]])
+    T0 = torch.from_numpy(np.stack([Ti, Tj, Ti, Tj])).cuda()
+    P = M.default_params()
+    idx2 = torch.from_numpy(np.concatenate([idx, idx])).cuda()
+    q2 = torch.from_numpy(np.concatenate([q, q]).astype(np.float32)).cuda()
+    H, g, c, nv = M.gn_linearize(plan, P, T0, torch.from_numpy(X).cuda(), idx2, q2)
+    T = T0.clone()
+    tau, st = M.gn_solve(plan, P, H, g, T)
+    torch.cuda.synchronize()
+    assert int(st[0]) == 3
+    assert torch.equal(T, T0)
+
+
+def test_degenerate_plans(M):
+    P = M.default_params()
+    # one keyframe, no edges: nothing to solve, converged at once
+    plan = M.Plan([[8, 8]], np.zeros((0, 2), np.int32))
+    T = torch.tensor([[0, 0, 0, 0, 0, 0, 1, 1.0]], dtype=torch.float64, device="cuda")
+    H = torch.zeros(0, 14, 14, device="cuda")
+    g = torch.zeros(0, 14, device="cuda")
+    tau, st = M.gn_solve(plan, P, H, g, T)
+    torch.cuda.synchronize()
+    assert int(st[0]) == 1
+    # two graphs in one plan: each keeps its own first keyframe fixed
+    from test_oracle_gn import exact_edge
+    rng = np.random.default_rng(5)
+    Ti, Tj, Xi, Xj, idx, q = exact_edge(rng, H=16, W=16)
+    plan2 = M.Plan([[16, 16]] * 4, [[0, 1], [1, 0], [2, 3], [3, 2]], graph_of_kf=[0, 0, 1, 1])
+    assert plan2.G == 2 and list(plan2.order) == [-1, 0, -1, 0]
+    X = torch.from_numpy(np.concatenate([Xi, Xj, Xi, Xj]).astype(np.float32)).cuda()
+    idx4 = torch.from_numpy(np.concatenate([idx] * 4)).cuda()
+    q4 = torch.from_numpy(np.concatenate([q] * 4).astype(np.float32)).cuda()
+    T0 = np.stack([Ti, Tj, Ti, Tj])
+    T0p = T0.copy()
+    T0p[1] = oracle.sim3_mul(oracle.sim3_exp(np.r_[0.02, 0, 0.01, 0.01, 0, 0, 0.02]), T0[1])
+    T0p[3] = T0p[1]
+    gn = M.GaussNewton(plan2, P, X, idx4, q4)
+    T = gn.run(torch.from_numpy(T0p).cuda(), 10).cpu()
+    assert_poses_close(T, T0, 1e-5)
+    assert torch.equal(T[0], torch.from_numpy(T0p[0])) and torch.equal(T[2], torch.from_numpy(T0p[2]))
+
+
+def test_argument_errors_do_not_launch(M, tiny_wl):
+    from paper_2412_12392_gb300 import _lib
+    P = M.default_params()
+    wd = to_dev(tiny_wl)
+    plan = M.Plan(tiny_wl.kf_hw.numpy(), tiny_wl.edges.numpy())
+    with pytest.raises(_lib.MslamError) as ei:
+        M.match(plan, P, wd.X_ref, wd.X_qry, wd.D_ref[:, :12].contiguous(), wd.D_qry[:, :12].contiguous(),
+                wd.Q_ref, wd.Q_qry)
+    assert ei.value.status == _lib.MSLAM_ERR_ARG
+    bad = M.default_params(sigma_ray=0.0)
+    idx, q = gpu_match(M, plan, P, wd)
+    with pytest.raises(_lib.MslamError):
+        M.gn_linearize(plan, bad, tiny_wl.T_init.cuda(), wd.X_canon, idx, q)
+    with pytest.raises(_lib.MslamError):
+        M.Plan([[16, 16], [16, 16]], [[0, 0]])

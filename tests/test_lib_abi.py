@@ -1,0 +1,124 @@
+"""CPU-only checks of the C ABI: the library builds for sm_103a, loads without
+a GPU, exports every function include/mslam.h declares, and its host-side
+plan logic (pool offsets, tiles, minimum-degree symbolic factorisation,
+argument validation) is right.  No compute call is made."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2412_12392_gb300 import _lib, build
+    build.build()
+    return _lib.lib()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "mslam.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mslam_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    from paper_2412_12392_gb300 import _lib
+    names = declared_functions()
+    assert len(names) >= 16
+    for n in names:
+        assert hasattr(L, n), n
+        assert n in _lib.SIGNATURES, f"{n} has no binding signature"
+
+
+def test_params_struct_layout(L):
+    from paper_2412_12392_gb300 import _lib
+    p = _lib.Params()
+    L.mslam_default_params(C.byref(p))
+    assert C.sizeof(p) == 64
+    assert abs(p.sigma_ray - 0.01) < 1e-8 and p.lm_iters == 10 and list(p.win_dilation)[:2] == [2, 1]
+
+
+def plan(kf_hw, edges, graph=None):
+    import paper_2412_12392_gb300 as M
+    return M.Plan(kf_hw, edges, graph, device="cpu")
+
+
+def test_plan_offsets_and_tiles(L):
+    kf = [[96, 128]] * 3 + [[48, 64]] * 2
+    edges = [[0, 1], [1, 2], [2, 0], [3, 4], [4, 3]]
+    p = plan(kf, edges, [0, 0, 0, 1, 1])
+    assert p.G == 2
+    assert list(p.kf_off) == [0, 12288, 24576, 36864, 39936, 43008]
+    assert list(p.e_off) == [0, 12288, 24576, 36864, 39936, 43008]
+    tiles = sum((h * w + 4095) // 4096 for h, w in [kf[j] for _, j in edges])
+    assert p.counts[2] == tiles
+    mblocks = sum(((w + 31) // 32) * ((h + 7) // 8) for h, w in [kf[j] for _, j in edges])
+    assert p.counts[3] == mblocks
+    assert p.order[0] == -1 and p.order[3] == -1
+
+
+def symbolic_blocks(N, edges, order):
+    """Independent symbolic Cholesky: eliminate in the plan's order on a dense
+    boolean block pattern; count non-zero blocks of L and update pairs."""
+    keep = [k for k in range(N) if order[k] >= 0]
+    m = len(keep)
+    pos = {k: order[k] for k in keep}
+    A = np.zeros((m, m), bool)
+    for i, j in edges:
+        if i in pos and j in pos:
+            A[pos[i], pos[j]] = A[pos[j], pos[i]] = True
+    np.fill_diagonal(A, True)
+    nnz, trips = 0, 0
+    for p in range(m):
+        rows = [r for r in range(p + 1, m) if A[r, p]]
+        nnz += len(rows)
+        trips += len(rows) * (len(rows) + 1) // 2
+        for a in rows:
+            for b in rows:
+                A[a, b] = True
+    return m + nnz, trips
+
+
+def test_symbolic_factorisation_matches_dense_elimination(L):
+    import synth
+    w = synth.global_graph(N=64, n_pairs=128, H=8, W=8)
+    p = plan(w.kf_hw.numpy(), w.edges.numpy())
+    nb, nt = symbolic_blocks(64, w.edges.numpy(), p.order)
+    assert (p.counts[0], p.counts[1]) == (nb, nt)
+    # the ordering is a permutation of the non-fixed keyframes
+    assert sorted(p.order[1:]) == list(range(63))
+    # minimum degree beats the natural order on this loop graph
+    nat = np.r_[-1, np.arange(63)]
+    nb_nat, nt_nat = symbolic_blocks(64, w.edges.numpy(), nat)
+    assert nt < nt_nat
+
+
+@pytest.mark.parametrize("kf,edges,graph", [
+    ([[16, 16], [16, 16]], [[0, 0]], None),          # self edge
+    ([[16, 16], [16, 16]], [[0, 2]], None),          # out of range
+    ([[16, 16], [8, 16]], [[0, 1]], None),           # size mismatch
+    ([[16, 16], [16, 16]], [[0, 1]], [0, 1]),        # edge across graphs
+    ([[1, 16], [16, 16]], [[0, 1]], None),           # image too small
+    ([[16, 16], [16, 16]], [[0, 1]], [0, 2]),        # graph id 1 empty
+])
+def test_plan_rejects_bad_structure(L, kf, edges, graph):
+    from paper_2412_12392_gb300 import _lib
+    with pytest.raises(_lib.MslamError) as ei:
+        plan(kf, edges, graph)
+    assert ei.value.status == _lib.MSLAM_ERR_ARG
+    assert _lib.last_error()
+
+
+def test_calls_reject_unuploaded_plan_and_null_args(L):
+    from paper_2412_12392_gb300 import _lib
+    p = plan([[16, 16], [16, 16]], [[0, 1]])
+    prm = _lib.Params()
+    L.mslam_default_params(C.byref(prm))
+    st = L.mslam_gn_solve(C.byref(prm), p.handle, None, None, None, None, None, None, 0, None)
+    assert st == _lib.MSLAM_ERR_ARG and "uploaded" in _lib.last_error()
+    st = L.mslam_match(None, p.handle, 0, 16, *([None] * 9), -1, -1, 0, None)
+    assert st == _lib.MSLAM_ERR_ARG

@@ -1,0 +1,496 @@
+"""Benchmark of the hot path: projective matching over every edge of a keyframe
+graph followed by Gauss-Newton iterations (linearise + gauge-fixed Cholesky
+solve + retraction), on seeded synthetic 512 x 384 pointmaps.
+
+One step = mslam_match over all edges + n_gn x (mslam_gn_linearize,
+mslam_gn_solve).  value = matched-pixel GN iterations per second over the
+whole step (matching time included), summed over ranks.  Prints one JSON
+line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mslam|reference]
+                  [--workload global|tracking] [--form batched|plain]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "matched-pixel GN iters/s + matches/s @512x384, batched vs plain, % HBM peak"
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mslam", choices=["mslam", "reference"])
+    ap.add_argument("--workload", default="global", choices=["global", "tracking"])
+    ap.add_argument("--form", default="batched", choices=["batched", "plain"])
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 per-edge comparison")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--small", action="store_true", help="a reduced graph (8 keyframes) for profiling")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- setup
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def make_workload(args, rank: int, device, hw=None):
+    """This rank's replica: an independent graph (seed offset by rank), so the
+    per-GPU work is fixed as ranks are added (weak scaling)."""
+    import synth
+    H, W = hw if hw is not None else (384, 512)
+    if args.workload == "tracking":
+        return synth.tracking(device=device, seed=1 + 1000 * rank, H=H, W=W)
+    if args.small:
+        return synth.global_graph(device=device, seed=2 + 1000 * rank, N=8, n_pairs=12, H=H, W=W)
+    return synth.global_graph(device=device, seed=2 + 1000 * rank, H=H, W=W)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.out = open(os.path.join(ROOT, f".clocks_{os.getpid()}.csv"), "w+")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.out,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        res = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return res
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.flush()
+        self.out.seek(0)
+        rows = [r.strip().split(",") for r in self.out.read().strip().splitlines() if r.strip()]
+        name = self.out.name
+        self.out.close()
+        os.remove(name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip() == "Active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if sm:
+            res = {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return res
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+class Arm:
+    """Device-resident inputs and buffers of one launch form."""
+
+    def __init__(self, M, w, dtype, per_edge: bool):
+        self.M, self.w, self.per_edge = M, w, per_edge
+        self.P = M.default_params()
+        self.wd = w.to_storage(dtype)
+        # descriptors in the kernel's chunk-planar layout (a one-off layout change)
+        self.Dr = M.chunk_descriptors(self.wd.D_ref)
+        self.Dq = M.chunk_descriptors(self.wd.D_qry)
+        self.plan = M.Plan(w.kf_hw.numpy(), w.edges.numpy())
+        dev = self.wd.X_canon.device
+        self.idx = torch.empty(self.plan.edge_pixels, dtype=torch.int32, device=dev)
+        self.q = torch.empty(self.plan.edge_pixels, dtype=dtype, device=dev)
+        # the batched form gathers the used matches once per step and streams
+        # them in every iteration; the plain form gathers in every iteration
+        self.gn = M.GaussNewton(self.plan, self.P, self.wd.X_canon, self.idx, self.q, per_edge=per_edge,
+                                packed=not per_edge)
+        self.T0 = w.T_init.to(dev)
+        self.iters = w.n_gn_iters
+
+    def match(self):
+        wd = self.wd
+        self.M.match(self.plan, self.P, wd.X_ref, wd.X_qry, self.Dr, self.Dq, wd.Q_ref, wd.Q_qry,
+                     idx_out=self.idx, q_out=self.q, per_edge=self.per_edge)
+
+    def step(self, ev=None):
+        """One pass of the hot path; ev = optional list collecting
+        (match_start, match_end, [(lin_start, lin_end)]) CUDA events."""
+        self.gn.T.copy_(self.T0)
+        self.gn.status.zero_()
+        if ev is None:
+            self.match()
+            self.gn.pack()
+            for _ in range(self.iters):
+                self.gn.step()
+            return
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        self.match()
+        e[1].record()
+        self.gn.pack()
+        e[2].record()
+        lins = []
+        for _ in range(self.iters):
+            a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            a.record()
+            self.gn.linearize()
+            b.record()
+            self.gn.solve()
+            c.record()
+            lins.append((a, b, c))
+        ev.append((e[0], e[1], e[2], lins))
+
+    def launches_per_step(self) -> int:
+        """Kernels of this library launched per step: match; (batched) pack;
+        per iteration the relative-pose, tile and finalize kernels of the
+        linearisation (per edge in the plain form) and the solve."""
+        E = self.plan.E
+        if self.per_edge:
+            return E + self.iters * (1 + 2 * E + 1)
+        return 1 + 1 + self.iters * 4
+
+
+def time_steps(arm, steps, warmup, world, sampler=None, with_events=True):
+    for _ in range(warmup):
+        arm.step()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev = [] if with_events else None
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    if sampler:
+        sampler.start()
+    t0.record()
+    for _ in range(steps):
+        arm.step(ev)
+    t1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    barrier(world)
+    ms = t0.elapsed_time(t1) / steps
+    stats = None
+    if ev:
+        match_ms = np.mean([a.elapsed_time(b) for a, b, _, _ in ev])
+        pack_ms = np.mean([b.elapsed_time(c) for _, b, c, _ in ev])
+        lin_ms = np.mean([a.elapsed_time(b) for _, _, _, L in ev for a, b, c in L])
+        solve_ms = np.mean([b.elapsed_time(c) for _, _, _, L in ev for a, b, c in L])
+        stats = dict(match_ms=float(match_ms), pack_ms=float(pack_ms), lin_ms=float(lin_ms),
+                     solve_ms=float(solve_ms))
+    return ms, stats, clocks
+
+
+def run_gpu(args, world, rank, local):
+    import paper_2412_12392_gb300 as M
+    from paper_2412_12392_gb300 import build
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = make_workload(args, rank, dev)
+    dtype = torch.float16 if args.form == "batched" else torch.float32
+    arm = Arm(M, w, dtype, per_edge=(args.form == "plain"))
+    arm.step()
+    torch.cuda.synchronize()
+    n_matched = int(((arm.idx >= 0) & (arm.q.float() > arm.P.q_min)).sum())
+    n_query = int(arm.plan.edge_pixels)
+    peaks, peak_src = measured_peaks()
+    sampler = ClockSampler(local) if rank == 0 else None
+    ms, stats, clocks = time_steps(arm, args.steps, args.warmup, world, sampler)
+    ms = max_over_ranks(ms, world)
+    tot_matched = sum_over_ranks(n_matched, world)
+    tot_query = sum_over_ranks(n_query, world)
+    value = tot_matched * arm.iters / (ms * 1e-3)
+    # per-kernel rooflines (algorithmic bytes / flops per launch over the
+    # CUDA-event duration of that launch in the timed region)
+    d = w.d
+    esz = 2 if dtype == torch.float16 else 4
+    lin_bytes = n_matched * (6 * esz + 4 + esz)      # X_i[m], X_j[n], idx, q
+    match_bytes = n_query * (6 * esz + 2 * d * esz + 2 * esz + 4 + esz)
+    match_flop = n_query * (w.n_match_iters * 80 + arm.P.n_levels * (2 * arm.P.win_radius + 1) ** 2 * 2 * d)
+    hbm = float(peaks["hbm_gbs"])
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = nsm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    lin_gbs = lin_bytes / (stats["lin_ms"] * 1e-3) / 1e9
+    match_tfs = match_flop / (stats["match_ms"] * 1e-3) / 1e12
+    rl_lin = {"kernel": "gn_linearize", "bound": "hbm", "achieved": round(lin_gbs, 1), "peak": hbm,
+              "unit": "GB/s", "frac": round(lin_gbs / hbm, 4), "traffic": None,
+              "algorithmic_bytes": int(lin_bytes), "ms": round(stats["lin_ms"], 4),
+              "peak_source": f"{peak_src} hbm_gbs"}
+    rl_match = {"kernel": "match", "bound": "alu", "achieved": round(match_tfs, 2), "peak": round(fp32_peak, 1),
+                "unit": "TFLOP/s", "frac": round(match_tfs / fp32_peak, 4), "traffic": None,
+                "algorithmic_flop": int(match_flop), "algorithmic_bytes": int(match_bytes),
+                "hbm_frac": round(match_bytes / (stats["match_ms"] * 1e-3) / 1e9 / hbm, 4),
+                "ms": round(stats["match_ms"], 4),
+                "peak_source": f"FP32 FMA: {nsm} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz"}
+    lin_share = stats["lin_ms"] * arm.iters
+    dominant = rl_match if stats["match_ms"] >= lin_share else rl_lin
+    out = {
+        "metric": METRIC, "value": value, "unit": "matched-pixel GN iters/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f16-storage/f32-math/f64-solve" if esz == 2 else
+        "f32/f64-solve", "data": "synthetic (seeded box-room pointmaps, no network or dataset)",
+        "config": {"workload": f"{w.name}: {w.N} keyframes, {w.E} directed edges, "
+                               f"{int(w.kf_hw[0, 1])}x{int(w.kf_hw[0, 0])}, d={d}, {w.n_gn_iters} GN iters",
+                   "form": args.form, "global_batch": w.E, "seq_len": None, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (per-step edge pools of several GB)"},
+        "matches_per_s": tot_query / (stats["match_ms"] * 1e-3) if stats else None,
+        "gn_iters_per_s_gn_only": tot_matched * arm.iters / (((stats["lin_ms"] + stats["solve_ms"]) * arm.iters
+                                                              + stats["pack_ms"]) * 1e-3),
+        "stage_ms": {k: round(v, 4) for k, v in stats.items()},
+        "matched_pixels": n_matched, "query_pixels": n_query,
+        "roofline": dominant, "roofline_kernels": [rl_match, rl_lin],
+        "gpu_launches": arm.launches_per_step() * args.steps,
+        "clocks": clocks,
+    }
+    return out, arm, w
+
+
+def e2e_measure(args, M, w, dtype, world, rank, local):
+    """Same metric through the public API with host (pinned) inputs copied in
+    and the poses copied out inside the timed region."""
+    dev = torch.device("cuda", local)
+    wh = w.to_storage(dtype).to("cpu")
+    names = ["X_ref", "X_qry", "D_ref", "D_qry", "Q_ref", "Q_qry", "X_canon"]
+    # host inputs in the kernel's layout (descriptors chunk-planar)
+    host = {k: (M.chunk_descriptors(getattr(wh, k)) if k.startswith("D_") else getattr(wh, k)).pin_memory()
+            for k in names}
+    T_host = w.T_init.cpu().pin_memory()
+    arm = Arm(M, w, dtype, per_edge=False)
+    dbuf = {k: getattr(arm.wd, k) for k in names}
+    dbuf["D_ref"], dbuf["D_qry"] = arm.Dr, arm.Dq
+    T_out = torch.empty_like(T_host).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in host.values()) + T_host.numel() * 8
+    d2h = T_out.numel() * 8
+
+    def step():
+        for k in names:
+            dbuf[k].copy_(host[k], non_blocking=True)
+        arm.T0.copy_(T_host, non_blocking=True)
+        arm.step()
+        T_out.copy_(arm.gn.T, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    steps = max(2, args.steps // 2)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(steps):
+        step()
+    t1.record()
+    torch.cuda.synchronize()
+    ms = max_over_ranks(t0.elapsed_time(t1) / steps, world)
+    n_matched = int(((arm.idx >= 0) & (arm.q.float() > arm.P.q_min)).sum())
+    val = sum_over_ranks(n_matched, world) * arm.iters / (ms * 1e-3)
+    return {"value": val, "unit": "matched-pixel GN iters/s", "ms_per_step": ms, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h)}
+
+
+# ----------------------------------------------------------------------------- oracle arm
+
+def oracle_sample(w, seconds: float, n_gn_iters: int, par: dict, seed: int = 0):
+    """Time the FP64 oracle on a bounded sample of the workload: matching of
+    sampled query pixels, then linearisation + solve on whole edges.  Returns
+    (matched-pixel GN iters/s for the whole step at the workload's mix,
+    matches/s, details)."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    # matching: sampled pixels of the first edges
+    e = 0
+    H, W = int(w.kf_hw[0, 0]), int(w.kf_hw[0, 1])
+    t_match, n_match = 0.0, 0
+    budget = seconds * 0.5
+    idx_all = {}
+    while t_match < budget and e < w.E:
+        pix = np.sort(rng.choice(H * W, size=min(H * W, 32768), replace=False))
+        t = time.perf_counter()
+        idx, q = oracle.match_workload(w, e, pix=pix, **par)
+        t_match += time.perf_counter() - t
+        n_match += len(pix)
+        e += 1
+    # GN: full linearisation of whole edges with ground-truth matches + one solve
+    t_gn, n_px_it = 0.0, 0
+    T = w.T_init.numpy()
+    e = 0
+    H14, g14 = [], []
+    while t_gn < seconds * 0.5 and e < w.E:
+        i, j = int(w.edges[e, 0]), int(w.edges[e, 1])
+        sl = w.edge_slice(e)
+        idx = w.gt_match[sl].numpy()
+        q = w.Q_qry[sl].double().numpy()
+        t = time.perf_counter()
+        Hb, gb, c, nv = oracle.linearize_edge(T[i], T[j], w.X_canon[w.kf_slice(i)], w.X_canon[w.kf_slice(j)], idx,
+                                              q, **par)
+        t_gn += time.perf_counter() - t
+        n_px_it += nv
+        H14.append(Hb)
+        g14.append(gb)
+        e += 1
+    t = time.perf_counter()
+    oracle.gn_solve(w.N, w.edges.numpy()[:e], np.array(H14), np.array(g14), T)
+    t_solve = time.perf_counter() - t
+    t_match_px = t_match / max(n_match, 1)
+    t_gn_px = t_gn / max(n_px_it, 1)
+    return t_match_px, t_gn_px, t_solve, dict(match_pixels=n_match, gn_pixel_iters=n_px_it, edges_linearised=e)
+
+
+def cpu_baseline(w, seconds, n_matched_total, n_query_total, iters, par):
+    import oracle
+    tm, tg, ts, det = oracle_sample(w, seconds, iters, par)
+    step_s = n_query_total * tm + n_matched_total * iters * tg + iters * ts
+    val = n_matched_total * iters / step_s
+    return {"value": val, "unit": "matched-pixel GN iters/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": (f"FP64 C oracle (OpenMP): matching of {det['match_pixels']} sampled query pixels and "
+                       f"linearisation of {det['edges_linearised']} whole edges ({det['gn_pixel_iters']} matched "
+                       f"pixel-iterations) plus one solve, scaled to the full step's pixel counts"),
+            "matches_per_s": 1.0 / tm}
+
+
+def run_reference(args, world, rank):
+    """The oracle as the reference arm, on the host cores."""
+    if rank != 0:
+        return None
+    import oracle
+    import synth
+    from paper_2412_12392_gb300 import _lib  # noqa: F401  (only for the parameter defaults below)
+    oracle.build()
+    w = make_workload(args, 0, "cpu")
+    par = dict(oracle.DEFAULT_PARAMS)
+    n_query = int(w.e_off[-1])
+    n_matched = int((w.gt_match >= 0).sum())
+    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_sample(w, per_step, w.n_gn_iters, par)
+    times = []
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        tm, tg, ts, det = oracle_sample(w, per_step, w.n_gn_iters, par, seed=k)
+        times.append(n_query * tm + n_matched * w.n_gn_iters * tg + w.n_gn_iters * ts)
+    wall = time.perf_counter() - t0
+    step_s = float(np.mean(times))
+    val = n_matched * w.n_gn_iters / step_s
+    cb = {"value": val, "unit": "matched-pixel GN iters/s", "cores": oracle.num_threads(), "kind": "oracle",
+          "sample": f"each step: about {per_step:.0f} s of FP64 oracle matching and linearisation on sampled "
+                    f"pixels/edges, scaled to the full step"}
+    return {"metric": METRIC, "value": val, "unit": "matched-pixel GN iters/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{w.name}: {w.N} keyframes, {w.E} directed edges, "
+                                   f"{int(w.kf_hw[0, 1])}x{int(w.kf_hw[0, 0])}, d={w.d}",
+                       "parallelism": "host cores (OpenMP)"},
+            "impl": "reference", "cpu_baseline": cb,
+            "e2e": {"value": val, "unit": "matched-pixel GN iters/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}, "wall_s": wall}
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        out = run_reference(args, world, rank)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    out, arm, w = run_gpu(args, world, rank, local)
+    import paper_2412_12392_gb300 as M
+    if not args.no_plain and args.form == "batched":
+        plain = Arm(M, w, torch.float32, per_edge=True)
+        pms, pstats, _ = time_steps(plain, max(2, args.steps // 3), 1, world)
+        pms = max_over_ranks(pms, world)
+        n_m = int(((plain.idx >= 0) & (plain.q > plain.P.q_min)).sum())
+        out["plain_fp32_per_edge"] = {
+            "value": sum_over_ranks(n_m, world) * plain.iters / (pms * 1e-3), "ms_per_step": pms,
+            "stage_ms": {k: round(v, 4) for k, v in pstats.items()},
+            "speedup_of_batched": pms / out["ms_per_step"]}
+        del plain
+    if not args.no_e2e:
+        out["e2e"] = e2e_measure(args, M, w, arm.wd.X_canon.dtype, world, rank, local)
+    if rank == 0 and not args.no_cpu:
+        wc = w.to_storage(arm.wd.X_canon.dtype).to("cpu")
+        out["cpu_baseline"] = cpu_baseline(wc, args.cpu_seconds, out["matched_pixels"], out["query_pixels"],
+                                           w.n_gn_iters, M.params_dict(arm.P))
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -25,7 +25,7 @@
  *   matches) are concatenated in edge order, H_j W_j pixels per edge ("edge
  *   pool").  Pixels are row-major (n = v W + u).
  * - Pointmaps are [pixels, 3] (x, y, z) of the storage dtype; descriptors
- *   [pixels, d]; confidences [pixels].  MSLAM_F32 stores float, MSLAM_F16
+ *   chunk-planar [d / c, pixels, c] (see mslam_match); confidences [pixels].  MSLAM_F32 stores float, MSLAM_F16
  *   stores IEEE half; all arithmetic is float (FP32) except the pose algebra,
  *   the per-edge block assembly and the Cholesky solve, which are FP64.
  * - Poses T_wc are [N, 8] FP64: translation (3), unit quaternion x y z w (4),
@@ -65,6 +65,8 @@ typedef enum { MSLAM_F32 = 0, MSLAM_F16 = 1 } mslam_dtype;
 #define MSLAM_OP_LINEARIZE 1
 #define MSLAM_OP_SOLVE 2
 #define MSLAM_OP_BACKWARD 3
+#define MSLAM_OP_PACK_F32 4 /* packed-match buffer of mslam_gn_pack, FP32 storage */
+#define MSLAM_OP_PACK_F16 5 /* packed-match buffer of mslam_gn_pack, FP16 storage */
 
 /* Constants of the method.  The paper names these quantities without values
  * where marked "reading"; defaults are set by mslam_default_params. */
@@ -154,8 +156,11 @@ size_t mslam_workspace_bytes(const mslam_plan* plan, int32_t op);
  *       maximum descriptor dot product <D_qry[n], D_ref[c]> (first maximum in
  *       row-major order), and invalidated if x is zero/non-finite or
  *       |X_ref[m] - x| > max_rel_dist3d |x|; q = sqrt(Q_ref[m] Q_qry[n]).
- * Arguments (edge pools, dtype dt): X_ref, X_qry [P, 3]; D_ref, D_qry [P, d]
- * with d in {16, 24, 32}, 16-byte aligned; Q_ref, Q_qry [P]; init_idx [P]
+ * Arguments (edge pools, dtype dt): X_ref, X_qry [P, 3]; D_ref, D_qry in the
+ * chunk-planar layout [d / c, P, c] with c = 16 bytes of elements (8 halves
+ * or 4 floats): channel k of pool pixel p is element ((k / c) P + p) c + k % c
+ * (so a warp reading one chunk of neighbouring pixels reads contiguous
+ * memory); d in {16, 24, 32}, 16-byte aligned; Q_ref, Q_qry [P]; init_idx [P]
  * int32 or NULL; outputs idx_out [P] int32 (m within the reference image,
  * -1 = invalid) and q_out [P] (dt; 0 where invalid).
  * flags: MSLAM_FLAG_PER_EDGE = one launch per edge, else one launch.
@@ -191,6 +196,26 @@ mslam_status mslam_gn_linearize(const mslam_params* p, const mslam_plan* plan, m
                                 const void* X_canon, const int32_t* idx, const void* q, float* H_blocks,
                                 float* g_blocks, double* cost, int32_t* n_valid, void* workspace,
                                 size_t ws_bytes, uint32_t flags, void* stream);
+
+/* Packed form of the same linearisation.  The matches and the canonical
+ * pointmaps do not change during the Gauss-Newton iterations of Sec. 3.5,
+ * so mslam_gn_pack gathers, once, the inputs of every match used by
+ * Eq. backend_ray (idx[n] >= 0 and q[n] > q_min): per work tile of the plan,
+ * in pixel order, one record {X_j[n], X_i[m], q[n]} of the storage dtype
+ * (16 bytes in FP16, 32 in FP32) plus a per-tile count.  The values are
+ * copied bit for bit, so mslam_gn_linearize_packed computes exactly the sums
+ * of mslam_gn_linearize (up to FP32 summation order) while streaming the
+ * records with coalesced loads.  packed: caller device buffer of at least
+ * mslam_workspace_bytes(plan, MSLAM_OP_PACK_F16 or _F32) bytes, 256-byte
+ * aligned; it must be re-packed whenever X_canon, idx or q change.  Other
+ * arguments and outputs as mslam_gn_linearize.
+ * Errors: MSLAM_ERR_ARG, MSLAM_ERR_CUDA. */
+mslam_status mslam_gn_pack(const mslam_params* p, const mslam_plan* plan, mslam_dtype dt, const void* X_canon,
+                           const int32_t* idx, const void* q, void* packed, size_t packed_bytes, void* stream);
+mslam_status mslam_gn_linearize_packed(const mslam_params* p, const mslam_plan* plan, mslam_dtype dt,
+                                       const double* T_wc, const void* packed, size_t packed_bytes, float* H_blocks,
+                                       float* g_blocks, double* cost, int32_t* n_valid, void* workspace,
+                                       size_t ws_bytes, uint32_t flags, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* (a6-a8) Gauss-Newton solve with the first pose fixed, Sec. 3.5.           */

@@ -6,8 +6,8 @@ The kernels live in libmslam.so behind the C ABI of include/mslam.h; this
 package holds its build script and a thin ctypes binding.
 """
 from . import _lib  # noqa: F401
-from .api import (GaussNewton, Plan, default_params, gn_backward, gn_linearize, gn_solve,  # noqa: F401
-                  match, params_dict)
+from .api import (GaussNewton, Plan, chunk_descriptors, default_params, gn_backward, gn_linearize,  # noqa: F401
+                  gn_linearize_packed, gn_pack, gn_solve, match, pack_bytes, params_dict)
 
-__all__ = ["Plan", "GaussNewton", "default_params", "params_dict", "match", "gn_linearize", "gn_solve",
-           "gn_backward"]
+__all__ = ["Plan", "GaussNewton", "chunk_descriptors", "default_params", "params_dict", "match", "gn_linearize", "gn_solve",
+           "gn_backward", "gn_pack", "gn_linearize_packed", "pack_bytes"]

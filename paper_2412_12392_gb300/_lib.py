@@ -23,6 +23,8 @@ MSLAM_FLAG_PER_EDGE = 1
 MSLAM_OP_LINEARIZE = 1
 MSLAM_OP_SOLVE = 2
 MSLAM_OP_BACKWARD = 3
+MSLAM_OP_PACK_F32 = 4
+MSLAM_OP_PACK_F16 = 5
 
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_NOT_PD", 4: "ERR_TIMEOUT", 5: "ERR_NONFINITE",
                 6: "ERR_RANGE"}
@@ -68,6 +70,8 @@ SIGNATURES = {
     "mslam_workspace_bytes": ([vp, i32], sz),
     "mslam_match": ([vp, vp, C.c_int, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, i32, u32, vp], C.c_int),
     "mslam_gn_linearize": ([vp, vp, C.c_int, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, u32, vp], C.c_int),
+    "mslam_gn_pack": ([vp, vp, C.c_int, vp, vp, vp, vp, sz, vp], C.c_int),
+    "mslam_gn_linearize_packed": ([vp, vp, C.c_int, vp, vp, sz, vp, vp, vp, vp, vp, sz, u32, vp], C.c_int),
     "mslam_gn_solve": ([vp, vp, vp, vp, vp, vp, vp, vp, sz, vp], C.c_int),
     "mslam_gn_backward": ([vp, vp, C.c_int, vp, vp, vp, vp, vp, vp, vp, C.c_double, vp, vp, vp, vp, sz, vp],
                           C.c_int),

@@ -114,14 +114,28 @@ class Plan:
             pass
 
 
+def chunk_descriptors(D: torch.Tensor) -> torch.Tensor:
+    """[P, d] descriptors -> the chunk-planar [d / c, P, c] layout of
+    mslam_match (c = 16 bytes of elements).  A layout change only."""
+    c = 16 // D.element_size()
+    P, d = D.shape
+    if d % c:
+        raise ValueError(f"descriptor dimension {d} is not a multiple of {c}")
+    return D.reshape(P, d // c, c).permute(1, 0, 2).contiguous()
+
+
 def match(plan: Plan, params: Params, X_ref, X_qry, D_ref, D_qry, Q_ref, Q_qry, init_idx=None, idx_out=None,
           q_out=None, edge_range: Tuple[int, int] = (-1, -1), per_edge: bool = False):
-    """mslam_match (Sec. 3.2): returns (idx int32 [P], q [P])."""
+    """mslam_match (Sec. 3.2): returns (idx int32 [P], q [P]).  D_ref and
+    D_qry are chunk-planar [d / c, P, c] (see chunk_descriptors)."""
     dt = X_ref.dtype
     if dt not in DTYPES:
         raise ValueError(f"unsupported storage dtype {dt}")
     P = plan.edge_pixels
-    d = D_ref.shape[-1]
+    c = 16 // X_ref.element_size()
+    if D_ref.dim() != 3 or D_ref.shape[1] != P or D_ref.shape[2] != c or D_qry.shape != D_ref.shape:
+        raise ValueError(f"descriptors must be chunk-planar [d/{c}, {P}, {c}] (got {tuple(D_ref.shape)})")
+    d = D_ref.shape[0] * c
     for t, nm, ne in ((X_ref, "X_ref", 3 * P), (X_qry, "X_qry", 3 * P), (D_ref, "D_ref", d * P),
                       (D_qry, "D_qry", d * P), (Q_ref, "Q_ref", P), (Q_qry, "Q_qry", P)):
         _need(t, nm, dt, ne)
@@ -167,6 +181,54 @@ def gn_linearize(plan: Plan, params: Params, T_wc, X_canon, idx, q, H=None, g=No
                                    idx.data_ptr(), q.data_ptr(), H.data_ptr(), g.data_ptr(), cost.data_ptr(),
                                    n_valid.data_ptr(), ws.data_ptr(), ws.numel(),
                                    _lib.MSLAM_FLAG_PER_EDGE if per_edge else 0, _stream(dev)), "mslam_gn_linearize")
+    return H, g, cost, n_valid
+
+
+def pack_bytes(plan: Plan, dtype) -> int:
+    op = _lib.MSLAM_OP_PACK_F16 if dtype == torch.float16 else _lib.MSLAM_OP_PACK_F32
+    return plan.workspace_bytes(op)
+
+
+def gn_pack(plan: Plan, params: Params, X_canon, idx, q, packed=None):
+    """mslam_gn_pack: gather the inputs of every used match once (the
+    matches are fixed during the Gauss-Newton loop).  Returns the packed
+    buffer (uint8 device tensor)."""
+    dt = X_canon.dtype
+    if dt not in DTYPES:
+        raise ValueError(f"unsupported storage dtype {dt}")
+    _need(X_canon, "X_canon", dt, 3 * plan.kf_pixels)
+    _need(idx, "idx", torch.int32, plan.edge_pixels)
+    _need(q, "q", dt, plan.edge_pixels)
+    nb = pack_bytes(plan, dt)
+    if packed is None:
+        packed = torch.empty(max(nb, 256), dtype=torch.uint8, device=X_canon.device)
+    _need(packed, "packed", torch.uint8)
+    check(lib().mslam_gn_pack(C.byref(params), plan.handle, DTYPES[dt], X_canon.data_ptr(), idx.data_ptr(),
+                              q.data_ptr(), packed.data_ptr(), packed.numel(), _stream(X_canon.device)),
+          "mslam_gn_pack")
+    return packed
+
+
+def gn_linearize_packed(plan: Plan, params: Params, dtype, T_wc, packed, H=None, g=None, cost=None, n_valid=None,
+                        workspace=None, per_edge: bool = False):
+    """mslam_gn_linearize_packed: the linearisation of gn_linearize from the
+    records of gn_pack."""
+    if dtype not in DTYPES:
+        raise ValueError(f"unsupported storage dtype {dtype}")
+    dev = packed.device
+    _need(T_wc, "T_wc", torch.float64, 8 * plan.N)
+    _need(packed, "packed", torch.uint8)
+    E = plan.E
+    H = torch.empty(E, 14, 14, dtype=torch.float32, device=dev) if H is None else H
+    g = torch.empty(E, 14, dtype=torch.float32, device=dev) if g is None else g
+    cost = torch.empty(E, dtype=torch.float64, device=dev) if cost is None else cost
+    n_valid = torch.empty(E, dtype=torch.int32, device=dev) if n_valid is None else n_valid
+    ws = plan.workspace(_lib.MSLAM_OP_LINEARIZE) if workspace is None else workspace
+    check(lib().mslam_gn_linearize_packed(C.byref(params), plan.handle, DTYPES[dtype], T_wc.data_ptr(),
+                                          packed.data_ptr(), packed.numel(), H.data_ptr(), g.data_ptr(),
+                                          cost.data_ptr(), n_valid.data_ptr(), ws.data_ptr(), ws.numel(),
+                                          _lib.MSLAM_FLAG_PER_EDGE if per_edge else 0, _stream(dev)),
+          "mslam_gn_linearize_packed")
     return H, g, cost, n_valid
 
 
@@ -216,10 +278,12 @@ def gn_backward(plan: Plan, params: Params, T_wc, X_canon, idx, q, H=None, g=Non
 
 class GaussNewton:
     """Device-resident Gauss-Newton loop over a plan (Sec. 3.5): buffers are
-    allocated once, so the loop can be captured into a CUDA graph."""
+    allocated once, so the loop can be captured into a CUDA graph.  With
+    packed=True the used matches are gathered once per run (mslam_gn_pack)
+    and every iteration streams them (mslam_gn_linearize_packed)."""
 
-    def __init__(self, plan: Plan, params: Params, X_canon, idx, q, per_edge: bool = False):
-        self.plan, self.params, self.per_edge = plan, params, per_edge
+    def __init__(self, plan: Plan, params: Params, X_canon, idx, q, per_edge: bool = False, packed: bool = False):
+        self.plan, self.params, self.per_edge, self.packed = plan, params, per_edge, packed
         self.X, self.idx, self.q = X_canon, idx, q
         dev = X_canon.device
         E, N = plan.E, plan.N
@@ -231,30 +295,50 @@ class GaussNewton:
         self.status = torch.zeros(plan.G, dtype=torch.int32, device=dev)
         self.ws_lin = plan.workspace(_lib.MSLAM_OP_LINEARIZE)
         self.ws_solve = plan.workspace(_lib.MSLAM_OP_SOLVE)
+        self.pack_buf = (torch.empty(max(pack_bytes(plan, X_canon.dtype), 256), dtype=torch.uint8, device=dev)
+                         if packed else None)
         self.T = torch.empty(N, 8, dtype=torch.float64, device=dev)
         self.graph = None
 
-    def step(self):
-        gn_linearize(self.plan, self.params, self.T, self.X, self.idx, self.q, self.H, self.g, self.cost,
-                     self.n_valid, self.ws_lin, self.per_edge)
+    def pack(self):
+        if self.packed:
+            gn_pack(self.plan, self.params, self.X, self.idx, self.q, self.pack_buf)
+
+    def linearize(self):
+        if self.packed:
+            gn_linearize_packed(self.plan, self.params, self.X.dtype, self.T, self.pack_buf, self.H, self.g,
+                                self.cost, self.n_valid, self.ws_lin, self.per_edge)
+        else:
+            gn_linearize(self.plan, self.params, self.T, self.X, self.idx, self.q, self.H, self.g, self.cost,
+                         self.n_valid, self.ws_lin, self.per_edge)
+
+    def solve(self):
         gn_solve(self.plan, self.params, self.H, self.g, self.T, self.tau, self.status, self.ws_solve)
 
+    def step(self):
+        self.linearize()
+        self.solve()
+
     def run(self, T_init, iters: int):
+        """Pack (if packed) and run `iters` iterations from T_init."""
         self.T.copy_(T_init)
         self.status.zero_()
+        self.pack()
         for _ in range(iters):
             self.step()
         return self.T
 
     def capture(self, iters: int):
-        """Capture `iters` steps (on the current buffers) into a CUDA graph."""
+        """Capture pack + `iters` steps (on the current buffers) into a CUDA graph."""
         s = torch.cuda.Stream(self.X.device)
         s.wait_stream(torch.cuda.current_stream(self.X.device))
         with torch.cuda.stream(s):
+            self.pack()
             self.step()  # warm-up outside capture (lazy module loading)
         torch.cuda.current_stream(self.X.device).wait_stream(s)
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
+            self.pack()
             for _ in range(iters):
                 self.step()
         self.graph = g

@@ -31,6 +31,31 @@ def _flags(extra=()):
                    "-I", os.path.join(HERE, "..", "include")] + list(extra)
 
 
+def build_variant(out_dir: str, defines=()) -> str:
+    """Build a copy of the library with extra -D tuning macros into out_dir
+    (used by tuning sweeps; the default build uses the macros' defaults)."""
+    os.makedirs(out_dir, exist_ok=True)
+    nv = nvcc()
+    dflags = [f"-D{d}" for d in defines]
+    objs = []
+
+    def one(src):
+        o = os.path.join(out_dir, src.replace(".cu", ".o"))
+        r = subprocess.run([nv, "-c", os.path.join(CSRC, src), "-o", o] + _flags(dflags), capture_output=True,
+                           text=True)
+        if r.returncode != 0:
+            raise RuntimeError(r.stderr)
+        return o
+
+    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+        objs = list(ex.map(one, SOURCES))
+    lib = os.path.join(out_dir, "libmslam.so")
+    r = subprocess.run([nv, "-shared", "-o", lib] + objs + ARCH, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr)
+    return lib
+
+
 def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True

@@ -11,7 +11,10 @@
 
 namespace mslam {
 
-constexpr int kLinTile = 4096;       // pixels per linearisation work tile
+#ifndef MSLAM_LIN_TILE
+#define MSLAM_LIN_TILE 8192
+#endif
+constexpr int kLinTile = MSLAM_LIN_TILE;  // pixels per linearisation work tile
 constexpr int kLinThreads = 256;     // threads per linearisation block
 constexpr int kNumAcc = 30;          // accumulators of the relative 7x7 system
 constexpr int kAccStride = 32;       // floats per tile partial in the workspace
@@ -54,13 +57,23 @@ struct DevGraph {
   int32_t off_asment; // -> asm entries: edge * 4 + quadrant
   int32_t off_gasm;   // -> gasm_ptr [m + 1]
   int32_t off_gasment;// -> gasm entries: edge * 2 + side
-  int32_t pad1;
+  int32_t n_levels;   // levels of the elimination dependency schedule
+  int32_t off_lev;    // -> lev_ptr [n_levels + 1] into lev_cols
+  int32_t off_levcols;// -> positions ordered by level
+  int32_t off_levtgt; // -> [n_levels + 1] into the per-level target-block list
+  int32_t off_tgtlist;// -> target blocks of each level (diagonal, then column blocks, per column)
+  int32_t off_tptr;   // -> tptr [n_blocks + 1] into pairs
+  int32_t off_pairs;  // -> (row block, column block) source pairs of each target, in column order
+  int32_t off_rsptr;  // -> rsptr [m + 1] into row structure
+  int32_t off_rs;     // -> (column c, block L(p, c)) of each position p, in column order
+  int32_t off_blkcol; // -> [n_blocks] column position of each block
   int64_t ws_off;     // offset (doubles) of this graph's numeric workspace
 };
 
 // Device view of a plan (pointers into the uploaded table blob).
 struct PlanView {
   int32_t N, E, G, n_tiles, n_mblocks;
+  int64_t P;  // pixels of the edge pools
   const DevEdge* edges;
   const DevTile* tiles;
   const DevGraph* graphs;
@@ -250,13 +263,38 @@ __device__ __forceinline__ Sim3d sim3_exp(const double tau[7]) {
   return e;
 }
 
+// 1/sqrt(d) in FP64 by Newton-Raphson iteration for the inverse square root,
+// y <- y (3 - d y^2) / 2, seeded with the single-precision hardware estimate:
+// two iterations take the ~23-bit seed past FP64 precision.  On this GPU a
+// dependent FP64 operation costs ~64 cycles and FP64 sqrt + reciprocal
+// ~1080, so the diagonal pivots of the factorisation use this (~8 dependent
+// operations); outside the single-precision range it falls back to
+// 1.0 / sqrt(d).
+__device__ __forceinline__ double rsqrt_newton(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+  double y = (double)rsqrtf((float)d);
+  const double hd = 0.5 * d;
+  y = y * fma(-hd * y, y, 1.5);
+  y = y * fma(-hd * y, y, 1.5);
+  return y;
+}
+
 // ---------------------------------------------------------------- host errors
 void set_error(const char* fmt, ...);
 mslam_status cuda_check(cudaError_t e, const char* what);
 bool check_plan_uploaded(const mslam_plan* plan);
 PlanView plan_view(const mslam_plan* plan);
+// Linearisation workspace: tile partials (256-byte aligned), then the
+// per-edge relative poses (16 floats each).
+inline size_t lin_partials_bytes(int n_tiles) {
+  return ((sizeof(float) * kAccStride * (size_t)(n_tiles > 0 ? n_tiles : 1)) + 255) & ~size_t(255);
+}
+// Packed-match buffer size (records of every tile, then per-tile counts).
+size_t pack_bytes(int n_tiles, mslam_dtype dt);
 // Host-side per-edge ranges: linearisation tiles [t0, t1), match blocks [b0, b1).
 void plan_edge_tiles(const mslam_plan* plan, int e, int* t0, int* t1);
 void plan_edge_mblocks(const mslam_plan* plan, int e, int* b0, int* b1);
+// Largest per-graph numeric solve workspace (doubles).
+int64_t plan_max_graph_doubles(const mslam_plan* plan);
 
 }  // namespace mslam

@@ -32,64 +32,66 @@ __device__ __forceinline__ float3 ray_at(const T* X, int64_t pix) {
   return make_float3(a.x * inv, a.y * inv, a.z * inv);
 }
 
-// descriptor row loads: D floats of a row into registers
-template <typename T, int D> struct DescRow;
+// Descriptors are stored chunk-planar: [d / C][P][C] with C = 16 bytes of
+// elements (8 halves or 4 floats), P = pixels of the whole edge pool, so that
+// a warp reading one chunk of 32 neighbouring pixels reads 512 contiguous
+// bytes.  Dot products accumulate in FP32 in channel order.
+template <typename T, int D> struct Desc;
 
-template <int D> struct DescRow<float, D> {
-  static __device__ __forceinline__ void load(const float* row, float* out) {
-    const float4* r4 = reinterpret_cast<const float4*>(row);
+template <int D> struct Desc<float, D> {
+  using Q = float4;  // query descriptor kept as D / 4 float4
+  static constexpr int NQ = D / 4;
+  static __device__ __forceinline__ void load(const float* base, int64_t P, int64_t pix, Q* q) {
+    const float4* b = reinterpret_cast<const float4*>(base);
 #pragma unroll
-    for (int k = 0; k < D / 4; ++k) {
-      const float4 v = __ldg(r4 + k);
-      out[4 * k] = v.x;
-      out[4 * k + 1] = v.y;
-      out[4 * k + 2] = v.z;
-      out[4 * k + 3] = v.w;
-    }
+    for (int k = 0; k < NQ; ++k) q[k] = __ldg(b + (int64_t)k * P + pix);
   }
-  static __device__ __forceinline__ float dot(const float* row, const float* q) {
-    const float4* r4 = reinterpret_cast<const float4*>(row);
+  static __device__ __forceinline__ float dot(const float* base, int64_t P, int64_t pix, const Q* q) {
+    const float4* b = reinterpret_cast<const float4*>(base);
     float s = 0.0f;
 #pragma unroll
-    for (int k = 0; k < D / 4; ++k) {
-      const float4 v = __ldg(r4 + k);
-      s = fmaf(q[4 * k], v.x, s);
-      s = fmaf(q[4 * k + 1], v.y, s);
-      s = fmaf(q[4 * k + 2], v.z, s);
-      s = fmaf(q[4 * k + 3], v.w, s);
+    for (int k = 0; k < NQ; ++k) {
+      const float4 v = __ldg(b + (int64_t)k * P + pix);
+      s = fmaf(q[k].x, v.x, s);
+      s = fmaf(q[k].y, v.y, s);
+      s = fmaf(q[k].z, v.z, s);
+      s = fmaf(q[k].w, v.w, s);
     }
     return s;
   }
 };
 
-template <int D> struct DescRow<__half, D> {
-  static __device__ __forceinline__ void load(const __half* row, float* out) {
-    const uint4* r4 = reinterpret_cast<const uint4*>(row);
+// s += lo(a) lo(b); s += hi(a) hi(b) with the FP16 x FP16 -> FP32 fused
+// multiply-add (the product of two halves is exact in FP32, so this equals
+// converting both to float and using fmaf)
+__device__ __forceinline__ void fma_h2(float& s, uint32_t a, uint32_t b) {
+  asm("{\n\t.reg .b16 a0, a1, b0, b1;\n\t"
+      "mov.b32 {a0, a1}, %1;\n\t"
+      "mov.b32 {b0, b1}, %2;\n\t"
+      "fma.rn.f32.f16 %0, a0, b0, %0;\n\t"
+      "fma.rn.f32.f16 %0, a1, b1, %0;\n\t}"
+      : "+f"(s)
+      : "r"(a), "r"(b));
+}
+
+template <int D> struct Desc<__half, D> {
+  using Q = uint4;  // query descriptor kept as D / 8 packed uint4 (8 halves each)
+  static constexpr int NQ = D / 8;
+  static __device__ __forceinline__ void load(const __half* base, int64_t P, int64_t pix, Q* q) {
+    const uint4* b = reinterpret_cast<const uint4*>(base);
 #pragma unroll
-    for (int k = 0; k < D / 8; ++k) {
-      const uint4 v = __ldg(r4 + k);
-      const __half2* h = reinterpret_cast<const __half2*>(&v);
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const float2 f = __half22float2(h[c]);
-        out[8 * k + 2 * c] = f.x;
-        out[8 * k + 2 * c + 1] = f.y;
-      }
-    }
+    for (int k = 0; k < NQ; ++k) q[k] = __ldg(b + (int64_t)k * P + pix);
   }
-  static __device__ __forceinline__ float dot(const __half* row, const float* q) {
-    const uint4* r4 = reinterpret_cast<const uint4*>(row);
+  static __device__ __forceinline__ float dot(const __half* base, int64_t P, int64_t pix, const Q* q) {
+    const uint4* b = reinterpret_cast<const uint4*>(base);
     float s = 0.0f;
 #pragma unroll
-    for (int k = 0; k < D / 8; ++k) {
-      const uint4 v = __ldg(r4 + k);
-      const __half2* h = reinterpret_cast<const __half2*>(&v);
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const float2 f = __half22float2(h[c]);
-        s = fmaf(q[8 * k + 2 * c], f.x, s);
-        s = fmaf(q[8 * k + 2 * c + 1], f.y, s);
-      }
+    for (int k = 0; k < NQ; ++k) {
+      const uint4 v = __ldg(b + (int64_t)k * P + pix);
+      fma_h2(s, q[k].x, v.x);
+      fma_h2(s, q[k].y, v.y);
+      fma_h2(s, q[k].z, v.z);
+      fma_h2(s, q[k].w, v.w);
     }
     return s;
   }
@@ -167,9 +169,8 @@ __global__ void __launch_bounds__(kMatchBX* kMatchBY) match_kernel(
   }
   int cu = min((int)floorf(pu + 0.5f), W - 1), cv = min((int)floorf(pv_ + 0.5f), H - 1);
   // coarse-to-fine refinement: maximum descriptor similarity in a window
-  float dq[D];
-  DescRow<T, D>::load(Dq + (o + n) * D, dq);
-  const T* Dr_e = Dr + o * D;
+  typename Desc<T, D>::Q dq[Desc<T, D>::NQ];
+  Desc<T, D>::load(Dq, pv.P, o + n, dq);
   const int r = mc.radius;
   for (int lev = 0; lev < mc.n_levels; ++lev) {
     const int dil = mc.dil[lev];
@@ -181,7 +182,7 @@ __global__ void __launch_bounds__(kMatchBX* kMatchBY) match_kernel(
       for (int dx = -r; dx <= r; ++dx) {
         const int uu = cu + dx * dil;
         if (uu < 0 || uu >= W) continue;
-        const float s = DescRow<T, D>::dot(Dr_e + ((int64_t)vv * W + uu) * D, dq);
+        const float s = Desc<T, D>::dot(Dr, pv.P, o + (int64_t)vv * W + uu, dq);
         if (s > best) {
           best = s;
           bu = uu;
@@ -232,6 +233,7 @@ extern "C" mslam_status mslam_match(const mslam_params* p, const mslam_plan* pla
     set_error("descriptor dimension %d not supported (16, 24 or 32)", d);
     return MSLAM_ERR_ARG;
   }
+  if (plan_view(plan).E == 0) return MSLAM_OK;  // no edges: empty pools, nothing to match
   if (!X_ref || !X_qry || !D_ref || !D_qry || !Q_ref || !Q_qry || !idx_out || !q_out) {
     set_error("match: NULL device pointer");
     return MSLAM_ERR_ARG;

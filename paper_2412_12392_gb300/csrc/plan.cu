@@ -21,7 +21,8 @@ struct mslam_plan {
   std::vector<mslam::DevGraph> graphs;
   std::vector<int32_t> ints;
   std::vector<int32_t> order;
-  int64_t n_blocks_total = 0, n_trips_total = 0, solve_ws_doubles = 0;
+  int64_t n_blocks_total = 0, n_trips_total = 0, solve_ws_doubles = 0, max_graph_doubles = 0;
+  int32_t max_levels = 0;
   int32_t n_mblocks = 0;
   void* dev = nullptr;
   size_t dev_bytes = 0;
@@ -65,6 +66,7 @@ PlanView plan_view(const mslam_plan* plan) {
   v.G = plan->G;
   v.n_tiles = (int32_t)plan->tiles.size();
   v.n_mblocks = plan->n_mblocks;
+  v.P = plan->e_off.back();
   v.edges = reinterpret_cast<const DevEdge*>(base + plan->off_edges);
   v.tiles = reinterpret_cast<const DevTile*>(base + plan->off_tiles);
   v.graphs = reinterpret_cast<const DevGraph*>(base + plan->off_graphs);
@@ -81,6 +83,8 @@ void plan_edge_mblocks(const mslam_plan* plan, int e, int* b0, int* b1) {
   *b0 = plan->dedges[e].mblock_begin;
   *b1 = (e + 1 < plan->E) ? plan->dedges[e + 1].mblock_begin : plan->n_mblocks;
 }
+
+int64_t plan_max_graph_doubles(const mslam_plan* plan) { return plan->max_graph_doubles; }
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -186,6 +190,92 @@ static void build_graph(mslam_plan* P, int g, const std::vector<int>& kfs) {
   dg.off_tripent = (int32_t)I.size();
   I.insert(I.end(), trips.begin(), trips.end());
 
+  // ---- level schedule for the left-looking factorisation.  Column p depends
+  // on every column c with p in rows(c); lev(p) = 1 + max lev(c).  Columns of
+  // one level touch disjoint blocks, so a level is processed in parallel.
+  std::vector<int> lev(m, 0);
+  int n_lev = 0;
+  for (int c = 0; c < m; ++c)
+    for (int r : rows[c]) lev[r] = std::max(lev[r], lev[c] + 1);
+  for (int c = 0; c < m; ++c) n_lev = std::max(n_lev, lev[c] + 1);
+  std::vector<std::vector<int>> cols_of(n_lev);
+  for (int c = 0; c < m; ++c) cols_of[lev[c]].push_back(c);
+  // update pairs grouped by target block: A_t -= L_b L_a^T in increasing c
+  std::vector<std::vector<std::pair<int, int>>> by_target(nb_total);
+  std::vector<std::vector<std::pair<int, int>>> rowstruct(m);  // p -> (c, block L(p, c))
+  for (int c = 0; c < m; ++c) {
+    const auto& R = rows[c];
+    for (size_t a = 0; a < R.size(); ++a) {
+      rowstruct[R[a]].push_back({c, blk.at({R[a], c})});
+      for (size_t b = a; b < R.size(); ++b) {
+        const int ra = R[a], rb = R[b];
+        const int target = (ra == rb) ? ra : blk.at({rb, ra});
+        by_target[target].push_back({blk.at({rb, c}), blk.at({ra, c})});
+      }
+    }
+  }
+  dg.n_levels = n_lev;
+  dg.off_lev = (int32_t)I.size();  // lev_ptr [n_lev + 1] into lev_cols
+  {
+    int acc = 0;
+    for (int l = 0; l <= n_lev; ++l) {
+      I.push_back(acc);
+      if (l < n_lev) acc += (int)cols_of[l].size();
+    }
+  }
+  dg.off_levcols = (int32_t)I.size();
+  for (auto& v : cols_of) I.insert(I.end(), v.begin(), v.end());
+  // per level: target blocks (diagonal then column blocks of each column)
+  dg.off_levtgt = (int32_t)I.size();  // [n_lev + 1] pointers into the target list
+  std::vector<int32_t> tg_list;
+  {
+    std::vector<int32_t> ptr;
+    for (int l = 0; l < n_lev; ++l) {
+      ptr.push_back((int32_t)tg_list.size());
+      for (int c : cols_of[l]) {
+        tg_list.push_back(c);
+        for (int r : rows[c]) tg_list.push_back(blk.at({r, c}));
+      }
+    }
+    ptr.push_back((int32_t)tg_list.size());
+    I.insert(I.end(), ptr.begin(), ptr.end());
+  }
+  dg.off_tgtlist = (int32_t)I.size();
+  I.insert(I.end(), tg_list.begin(), tg_list.end());
+  dg.off_tptr = (int32_t)I.size();  // [n_blocks + 1] into pairs
+  {
+    int acc = 0;
+    for (int b = 0; b <= nb_total; ++b) {
+      I.push_back(acc);
+      if (b < nb_total) acc += (int)by_target[b].size();
+    }
+  }
+  dg.off_pairs = (int32_t)I.size();
+  for (auto& v : by_target)
+    for (auto& pr : v) {
+      I.push_back(pr.first);
+      I.push_back(pr.second);
+    }
+  dg.off_rsptr = (int32_t)I.size();  // [m + 1] row structure (c, block) per position
+  {
+    int acc = 0;
+    for (int q = 0; q <= m; ++q) {
+      I.push_back(acc);
+      if (q < m) acc += (int)rowstruct[q].size();
+    }
+  }
+  dg.off_rs = (int32_t)I.size();
+  for (auto& v : rowstruct)
+    for (auto& pr : v) {
+      I.push_back(pr.first);
+      I.push_back(pr.second);
+    }
+  dg.off_blkcol = (int32_t)I.size();  // [n_blocks] column position of each block
+  for (int b = 0; b < m; ++b) I.push_back(b);
+  for (int c = 0; c < m; ++c)
+    for (size_t k = 0; k < rows[c].size(); ++k) I.push_back(c);
+  P->max_levels = std::max(P->max_levels, n_lev);
+
   // assembly lists (edge order): quadrant 0 = H_ii, 1 = H_jj, 2 = rows i cols j, 3 = rows j cols i
   std::vector<std::vector<int>> asml(nb_total), gasm(m);
   for (int e = 0; e < P->E; ++e) {
@@ -229,8 +319,11 @@ static void build_graph(mslam_plan* P, int g, const std::vector<int>& kfs) {
   for (auto& v : gasm) I.insert(I.end(), v.begin(), v.end());
 
   dg.ws_off = P->solve_ws_doubles;
-  // numeric workspace: blocks (49 each), rhs (7 m), assembled diagonal (7 m)
-  P->solve_ws_doubles += (int64_t)nb_total * 49 + 14 * (int64_t)m;
+  // numeric workspace: blocks (49 each), rhs (7 m), assembled diagonal (7 m),
+  // reciprocal pivots (7 m)
+  const int64_t need = (int64_t)nb_total * 49 + 21 * (int64_t)m;
+  P->solve_ws_doubles += need;
+  P->max_graph_doubles = std::max(P->max_graph_doubles, need);
   P->n_blocks_total += nb_total;
   P->graphs.push_back(dg);
 }
@@ -403,9 +496,13 @@ size_t mslam_workspace_bytes(const mslam_plan* plan, int32_t op) {
   if (!plan) return 0;
   switch (op) {
     case MSLAM_OP_LINEARIZE:
-      return align256(sizeof(float) * kAccStride * std::max<size_t>(plan->tiles.size(), 1));
+      return lin_partials_bytes((int)plan->tiles.size()) + align256(sizeof(float) * 16 * std::max(plan->E, 1));
     case MSLAM_OP_SOLVE:
       return align256(sizeof(double) * std::max<int64_t>(plan->solve_ws_doubles, 1));
+    case MSLAM_OP_PACK_F32:
+      return pack_bytes((int)plan->tiles.size(), MSLAM_F32);
+    case MSLAM_OP_PACK_F16:
+      return pack_bytes((int)plan->tiles.size(), MSLAM_F16);
     case MSLAM_OP_BACKWARD:
       return align256(sizeof(double) * std::max<int64_t>(plan->solve_ws_doubles, 1)) +
              align256(sizeof(double) * 7 * (size_t)plan->N) * 2;

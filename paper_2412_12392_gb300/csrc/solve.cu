@@ -2,12 +2,18 @@
 //
 // One CTA per graph.  The 14x14 edge blocks are assembled in FP64 into the
 // 7x7 blocks of the gauge-reduced system (first keyframe dropped), each
-// block summed in edge order from a host-built list; a right-looking block
-// Cholesky then runs in the plan's minimum-degree elimination order over the
-// symbolic fill pattern (diagonal factor by one warp, column panel and the
-// (target, row, column) update triples spread over the CTA); forward and
-// back substitution give tau = -H^-1 g, and every non-fixed pose is retracted
-// T <- Exp(tau) o T in FP64 (Eq. 1, Eq. gauss_newton).
+// block summed in edge order from a host-built list.  The block Cholesky is
+// left-looking and scheduled by levels of the elimination dependencies in
+// the plan's minimum-degree order (21 levels for the 63 columns of the
+// 64-keyframe loop graph): per level, (A) every target block and right-hand
+// side row of the level's columns gathers its updates from lower levels in a
+// fixed order, (B) one warp per column factors the diagonal block (reciprocal
+// pivots kept) and forward-substitutes y_p, (C) the column panels
+// L_rp = A_rp L_pp^-T are formed.  Back substitution runs the levels in
+// reverse, one warp per column, and every non-fixed pose is retracted
+// T <- Exp(tau) o T in FP64 (Eq. 1, Eq. gauss_newton).  The numeric factor
+// lives in shared memory when the graph fits (the 64-keyframe graph needs
+// 151 KB), else in the caller's workspace.
 #include <algorithm>
 
 #include "common.cuh"
@@ -16,7 +22,8 @@ namespace mslam {
 
 struct SolveConst {
   double conv_tol;
-  int factor_only;  // 1: factor and write tau, never touch poses or the converged flag
+  int factor_only;      // 1: factor and write tau, never touch poses or the converged flag
+  int smem_doubles;     // dynamic shared memory available per CTA (doubles)
 };
 
 __global__ void __launch_bounds__(kSolveThreads) solve_kernel(PlanView pv, SolveConst sc,
@@ -25,11 +32,11 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(PlanView pv, Solve
                                                               double* __restrict__ T_wc, double* __restrict__ tau_out,
                                                               int32_t* __restrict__ dev_status,
                                                               double* __restrict__ ws) {
+  extern __shared__ double smem[];
   const int g = blockIdx.x;
   const DevGraph G = pv.graphs[g];
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
   __shared__ int s_fail;
-  __shared__ double s_y[7];
   __shared__ double s_max;
   __shared__ int s_nonfinite;
   // converged (1) or failed (> 1) earlier: no more updates; a factor-only
@@ -48,25 +55,28 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(PlanView pv, Solve
   const int32_t* pose_of_pos = I + G.off_pose;
   const int32_t* col_ptr = I + G.off_col;
   const int32_t* colent = I + G.off_colent;
-  const int32_t* trip_ptr = I + G.off_trip;
-  const int32_t* trips = I + G.off_tripent;
   const int32_t* asm_ptr = I + G.off_asm;
   const int32_t* asment = I + G.off_asment;
   const int32_t* gasm_ptr = I + G.off_gasm;
   const int32_t* gasment = I + G.off_gasment;
-  double* L = ws + G.ws_off;
+  const int64_t need = (int64_t)G.n_blocks * 49 + 21 * (int64_t)m;
+  const bool in_smem = need <= sc.smem_doubles;
+  double* gws = ws + G.ws_off;
+  double* L = in_smem ? smem : gws;
   double* rhs = L + (size_t)G.n_blocks * 49;
   double* diag0 = rhs + 7 * (size_t)m;
+  double* invd = diag0 + 7 * (size_t)m;
 
   // ---- assembly (FP64, fixed order)
   for (int t = tid; t < G.n_blocks * 49; t += nth) {
     const int b = t / 49, e = t % 49, r = e / 7, c = e % 7;
     double s = 0.0;
-    for (int k = asm_ptr[b]; k < asm_ptr[b + 1]; ++k) {
-      const int code = asment[k], edge = code >> 2, quad = code & 3;
+    const int k1 = __ldg(asm_ptr + b + 1);
+    for (int k = __ldg(asm_ptr + b); k < k1; ++k) {
+      const int code = __ldg(asment + k), edge = code >> 2, quad = code & 3;
       const int r0 = (quad == 0 || quad == 2) ? 0 : 7;
       const int c0 = (quad == 0 || quad == 3) ? 0 : 7;
-      s += (double)H14[(size_t)edge * 196 + (r0 + r) * 14 + c0 + c];
+      s += (double)__ldg(H14 + (size_t)edge * 196 + (r0 + r) * 14 + c0 + c);
     }
     L[t] = s;
     if (b < m && r == c) diag0[7 * b + r] = s;
@@ -74,9 +84,10 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(PlanView pv, Solve
   for (int t = tid; t < 7 * m; t += nth) {
     const int p = t / 7, a = t % 7;
     double s = 0.0;
-    for (int k = gasm_ptr[p]; k < gasm_ptr[p + 1]; ++k) {
-      const int code = gasment[k], edge = code >> 1, side = code & 1;
-      s += (double)g14[(size_t)edge * 14 + 7 * side + a];
+    const int k1 = __ldg(gasm_ptr + p + 1);
+    for (int k = __ldg(gasm_ptr + p); k < k1; ++k) {
+      const int code = __ldg(gasment + k), edge = code >> 1, side = code & 1;
+      s += (double)__ldg(g14 + (size_t)edge * 14 + 7 * side + a);
     }
     rhs[t] = -s;
   }
@@ -87,55 +98,116 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(PlanView pv, Solve
   }
   __syncthreads();
 
-  // ---- numeric factorisation, right-looking over block columns
-  for (int p = 0; p < m; ++p) {
-    double* D = L + 49 * (size_t)p;
-    if (warp == 0) {
-      for (int j = 0; j < 7; ++j) {
-        if (lane == 0) {
-          double d = D[7 * j + j];
-          for (int k = 0; k < j; ++k) d -= D[7 * j + k] * D[7 * j + k];
-          const double ref = diag0[7 * p + j];
-          if (!(d > 1e-12 * ref) || !isfinite(d)) {
-            s_fail = 1;
-            d = 1.0;
-          }
-          D[7 * j + j] = sqrt(d);
+  // ---- numeric factorisation, left-looking, one elimination level at a time.
+  // Level l holds columns whose dependencies all lie in lower levels; its
+  // columns write disjoint blocks, so each phase runs over the whole level.
+  const int32_t* lev_ptr = I + G.off_lev;
+  const int32_t* lev_cols = I + G.off_levcols;
+  const int32_t* levtgt = I + G.off_levtgt;
+  const int32_t* tgtlist = I + G.off_tgtlist;
+  const int32_t* tptr = I + G.off_tptr;
+  const int32_t* pairs = I + G.off_pairs;
+  const int32_t* rsptr = I + G.off_rsptr;
+  const int32_t* rs = I + G.off_rs;
+  const int32_t* blkcol = I + G.off_blkcol;
+  const int nwarps = nth >> 5;
+  for (int l = 0; l < G.n_levels; ++l) {
+    const int q0 = __ldg(lev_ptr + l), q1 = __ldg(lev_ptr + l + 1);
+    const int g0 = __ldg(levtgt + l), g1 = __ldg(levtgt + l + 1);
+    // (A) updates from lower levels: A_t -= sum_c L_(r,c) L_(p,c)^T for every
+    //     target block of the level, and rhs_p -= sum_c L_(p,c) y_c
+    const int nA = (g1 - g0) * 49;
+    for (int w = tid; w < nA + (q1 - q0) * 7; w += nth) {
+      if (w < nA) {
+        const int t = __ldg(tgtlist + g0 + w / 49), e = w % 49, r = e / 7, c = e % 7;
+        const int k1 = __ldg(tptr + t + 1);
+        double ps[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // independent chains (FP64 latency)
+        for (int k = __ldg(tptr + t); k < k1; ++k) {
+          const double* Lb = L + 49 * (size_t)__ldg(pairs + 2 * k) + 7 * r;
+          const double* La = L + 49 * (size_t)__ldg(pairs + 2 * k + 1) + 7 * c;
+#pragma unroll
+          for (int kk = 0; kk < 7; ++kk) ps[kk] = fma(Lb[kk], La[kk], ps[kk]);
         }
-        __syncwarp();
-        if (lane > j && lane < 7) {
-          double v = D[7 * lane + j];
-          for (int k = 0; k < j; ++k) v -= D[7 * lane + k] * D[7 * j + k];
-          D[7 * lane + j] = v / D[7 * j + j];
+        L[49 * (size_t)t + e] -= ((ps[0] + ps[1]) + (ps[2] + ps[3])) + ((ps[4] + ps[5]) + ps[6]);
+      } else {
+        const int ww = w - nA, p = __ldg(lev_cols + q0 + ww / 7), a = ww % 7;
+        const int k1 = __ldg(rsptr + p + 1);
+        double ps[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int k = __ldg(rsptr + p); k < k1; ++k) {
+          const double* Lpc = L + 49 * (size_t)__ldg(rs + 2 * k + 1) + 7 * a;
+          const double* yc = rhs + 7 * __ldg(rs + 2 * k);
+#pragma unroll
+          for (int kk = 0; kk < 7; ++kk) ps[kk] = fma(Lpc[kk], yc[kk], ps[kk]);
         }
-        __syncwarp();
+        rhs[7 * p + a] -= ((ps[0] + ps[1]) + (ps[2] + ps[3])) + ((ps[4] + ps[5]) + ps[6]);
       }
+    }
+    __syncthreads();
+    // (B) diagonal factor and y_p = L_pp^-1 rhs_p, one warp per column: lane
+    //     i < 7 owns row i of the block and y_i; column-oriented inside the
+    //     block, so each step is a few dependent FP64 operations.  All lanes
+    //     execute every shuffle (full mask); lanes >= 7 carry dummies.
+    for (int qi = q0 + warp; qi < q1; qi += nwarps) {
+      const int p = __ldg(lev_cols + qi);
+      double* D = L + 49 * (size_t)p;
+      double* iv = invd + 7 * p;
+      const bool mine = lane < 7;
+      const int li = mine ? lane : 0;
+      double row[7], yv = mine ? rhs[7 * p + li] : 0.0;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) row[k] = D[7 * li + k];
+      bool bad = false;
+#pragma unroll
+      for (int j = 0; j < 7; ++j) {
+        const double djj = __shfl_sync(0xffffffffu, row[j], j);  // A_jj after earlier steps
+        const bool okj = (djj > 1e-12 * diag0[7 * p + j]) && isfinite(djj);
+        bad |= !okj;
+        const double ivj = rsqrt_newton(okj ? djj : 1.0);    // 1 / L_jj
+        const double yj = __shfl_sync(0xffffffffu, yv, j) * ivj;
+        // lane j: row[j] = A_jj / sqrt(A_jj) = L_jj; lanes > j: L_ij = A_ij / L_jj
+        const double lij = (lane == j && !okj) ? 1.0 : row[j] * ivj;
+        if (mine && lane >= j) row[j] = lij;
+        if (lane == j) {
+          iv[j] = ivj;
+          yv = yj;
+        } else if (mine && lane > j) {
+          yv = fma(-lij, yj, yv);
+        }
+        // trailing update inside the block: A_ik -= L_ij L_kj for j < k <= i
+#pragma unroll
+        for (int k = j + 1; k < 7; ++k) {
+          const double lkj = __shfl_sync(0xffffffffu, row[j], k);
+          if (mine && lane >= k) row[k] = fma(-lij, lkj, row[k]);
+        }
+      }
+      if (mine) {
+#pragma unroll
+        for (int k = 0; k < 7; ++k)
+          if (k <= lane) D[7 * lane + k] = row[k];
+        rhs[7 * p + lane] = yv;
+      }
+      if (bad && lane == 0) s_fail = 1;
+      __syncwarp();
     }
     __syncthreads();
     if (s_fail) break;
-    // panel: L_rp = A_rp L_pp^-T, one thread per (block, row)
-    const int c0 = col_ptr[p], c1 = col_ptr[p + 1];
-    for (int w = tid; w < (c1 - c0) * 7; w += nth) {
-      const int ent = c0 + w / 7, a = w % 7;
-      double* row = L + 49 * (size_t)colent[2 * ent + 1] + 7 * a;
+    // (C) panel: L_rp = A_rp L_pp^-T for the column blocks of the level
+    for (int w = tid; w < (g1 - g0) * 7; w += nth) {
+      const int t = __ldg(tgtlist + g0 + w / 7), a = w % 7;
+      if (t < m) continue;  // a diagonal block
+      const int p = __ldg(blkcol + t);
+      const double* D = L + 49 * (size_t)p;
+      const double* iv = invd + 7 * p;
+      double* row = L + 49 * (size_t)t + 7 * a;
       double x[7];
+#pragma unroll
       for (int k = 0; k < 7; ++k) {
         double v = row[k];
-        for (int l = 0; l < k; ++l) v -= x[l] * D[7 * k + l];
-        x[k] = v / D[7 * k + k];
+        for (int l2 = 0; l2 < k; ++l2) v -= x[l2] * D[7 * k + l2];
+        x[k] = v * iv[k];
       }
+#pragma unroll
       for (int k = 0; k < 7; ++k) row[k] = x[k];
-    }
-    __syncthreads();
-    // trailing update: A_t -= L_b L_a^T for each triple of this column
-    const int t0 = trip_ptr[p], t1 = trip_ptr[p + 1];
-    for (int w = tid; w < (t1 - t0) * 49; w += nth) {
-      const int tr = t0 + w / 49, e = w % 49, r = e / 7, c = e % 7;
-      const double* Lb = L + 49 * (size_t)trips[3 * tr + 1] + 7 * r;
-      const double* La = L + 49 * (size_t)trips[3 * tr + 2] + 7 * c;
-      double s = 0.0;
-      for (int k = 0; k < 7; ++k) s += Lb[k] * La[k];
-      L[49 * (size_t)trips[3 * tr] + e] -= s;
     }
     __syncthreads();
   }
@@ -144,53 +216,45 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(PlanView pv, Solve
     return;
   }
 
-  // ---- forward substitution L y = -g
-  for (int p = 0; p < m; ++p) {
-    const double* D = L + 49 * (size_t)p;
-    if (tid == 0) {
-      double* y = rhs + 7 * p;
-      for (int k = 0; k < 7; ++k) {
-        double v = y[k];
-        for (int l = 0; l < k; ++l) v -= D[7 * k + l] * y[l];
-        y[k] = v / D[7 * k + k];
-        s_y[k] = y[k];
-      }
-    }
-    __syncthreads();
-    const int c0 = col_ptr[p], c1 = col_ptr[p + 1];
-    for (int w = tid; w < (c1 - c0) * 7; w += nth) {
-      const int ent = c0 + w / 7, a = w % 7;
-      const double* row = L + 49 * (size_t)colent[2 * ent + 1] + 7 * a;
+  // ---- back substitution L^T x = y, levels in reverse (a column's rows all
+  // lie in higher levels), one warp per column
+  for (int l = G.n_levels - 1; l >= 0; --l) {
+    const int q0 = __ldg(lev_ptr + l), q1 = __ldg(lev_ptr + l + 1);
+    for (int qi = q0 + warp; qi < q1; qi += nwarps) {
+      const int p = __ldg(lev_cols + qi);
+      const double* D = L + 49 * (size_t)p;
+      const int c0 = __ldg(col_ptr + p), c1 = __ldg(col_ptr + p + 1);
       double s = 0.0;
-      for (int k = 0; k < 7; ++k) s += row[k] * s_y[k];
-      rhs[7 * colent[2 * ent] + a] -= s;
+      if (lane < 7) {
+        double ps[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // independent chains
+        for (int ent = c0; ent < c1; ++ent) {
+          const double* Lr = L + 49 * (size_t)__ldg(colent + 2 * ent + 1);
+          const double* xr = rhs + 7 * __ldg(colent + 2 * ent);
+#pragma unroll
+          for (int k = 0; k < 7; ++k) ps[k] = fma(Lr[7 * k + lane], xr[k], ps[k]);
+        }
+        s = rhs[7 * p + lane] - (((ps[0] + ps[1]) + (ps[2] + ps[3])) + ((ps[4] + ps[5]) + ps[6]));
+      }
+      double sv[7];
+#pragma unroll
+      for (int k = 0; k < 7; ++k) sv[k] = __shfl_sync(0xffffffffu, s, k);
+      if (lane == 0) {
+        const double* iv = invd + 7 * p;
+        double x[7];
+        for (int k = 6; k >= 0; --k) {
+          double v = sv[k];
+          for (int l2 = k + 1; l2 < 7; ++l2) v -= D[7 * l2 + k] * x[l2];
+          x[k] = v * iv[k];
+        }
+        for (int k = 0; k < 7; ++k) rhs[7 * p + k] = x[k];
+      }
+      __syncwarp();
     }
     __syncthreads();
   }
-  // ---- back substitution L^T x = y
-  for (int p = m - 1; p >= 0; --p) {
-    const double* D = L + 49 * (size_t)p;
-    const int c0 = col_ptr[p], c1 = col_ptr[p + 1];
-    if (tid < 7) {
-      double s = rhs[7 * p + tid];
-      for (int ent = c0; ent < c1; ++ent) {
-        const double* Lr = L + 49 * (size_t)colent[2 * ent + 1];
-        const double* xr = rhs + 7 * colent[2 * ent];
-        for (int k = 0; k < 7; ++k) s -= Lr[7 * k + tid] * xr[k];
-      }
-      s_y[tid] = s;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      double x[7];
-      for (int k = 6; k >= 0; --k) {
-        double v = s_y[k];
-        for (int l = k + 1; l < 7; ++l) v -= D[7 * l + k] * x[l];
-        x[k] = v / D[7 * k + k];
-      }
-      for (int k = 0; k < 7; ++k) rhs[7 * p + k] = x[k];
-    }
-    __syncthreads();
+  if (sc.factor_only && in_smem) {
+    // the adjoint reuses the factor: leave it in the workspace
+    for (size_t t = tid; t < (size_t)need; t += nth) gws[t] = L[t];
   }
   // ---- step statistics, tau, retraction
   for (int t = tid; t < 7 * m; t += nth) {
@@ -209,7 +273,7 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(PlanView pv, Solve
     if (lane == 0) s_max = mx;
   }
   for (int p = tid; p < m; p += nth) {
-    const int k = pose_of_pos[p];
+    const int k = __ldg(pose_of_pos + p);
     double tau[7];
     for (int a = 0; a < 7; ++a) tau[a] = rhs[7 * p + a];
     if (tau_out)
@@ -223,6 +287,21 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(PlanView pv, Solve
   if (tid == 0 && !sc.factor_only && s_max < sc.conv_tol) dev_status[g] = 1;
 }
 
+// Dynamic shared memory for the solve: the largest graph's factor if it fits
+// in the opt-in per-CTA limit, else none (all graphs then use the workspace).
+static int solve_smem_doubles(const mslam_plan* plan) {
+  static int limit = -1;
+  if (limit < 0) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    limit = std::max(0, optin - 1024);  // headroom for the static shared variables
+    cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
+  }
+  const int64_t need = plan_max_graph_doubles(plan);
+  return (need * (int64_t)sizeof(double) <= limit) ? (int)need : 0;
+}
+
 }  // namespace mslam
 
 using namespace mslam;
@@ -234,7 +313,8 @@ extern "C" mslam_status mslam_gn_solve(const mslam_params* p, const mslam_plan* 
     if (!p) set_error("params is NULL");
     return MSLAM_ERR_ARG;
   }
-  if (!H_blocks || !g_blocks || !T_wc || !dev_status || !workspace) {
+  // with no edges the block arrays are empty and may be NULL
+  if ((plan_view(plan).E > 0 && (!H_blocks || !g_blocks)) || !T_wc || !dev_status || !workspace) {
     set_error("gn_solve: NULL device pointer");
     return MSLAM_ERR_ARG;
   }
@@ -247,9 +327,10 @@ extern "C" mslam_status mslam_gn_solve(const mslam_params* p, const mslam_plan* 
   SolveConst sc;
   sc.conv_tol = p->conv_tol;
   sc.factor_only = 0;
+  sc.smem_doubles = solve_smem_doubles(plan);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  solve_kernel<<<pv.G, kSolveThreads, 0, s>>>(pv, sc, H_blocks, g_blocks, T_wc, tau, dev_status,
-                                              static_cast<double*>(workspace));
+  solve_kernel<<<pv.G, kSolveThreads, sizeof(double) * sc.smem_doubles, s>>>(
+      pv, sc, H_blocks, g_blocks, T_wc, tau, dev_status, static_cast<double*>(workspace));
   return cuda_check(cudaGetLastError(), "gn_solve launch");
 }
 
@@ -261,6 +342,8 @@ mslam_status mslam_factor_only(const mslam_plan* plan, const float* H_blocks, co
   SolveConst sc;
   sc.conv_tol = 0.0;
   sc.factor_only = 1;
-  solve_kernel<<<pv.G, kSolveThreads, 0, s>>>(pv, sc, H_blocks, g_blocks, nullptr, tau, dev_status, ws);
+  sc.smem_doubles = solve_smem_doubles(plan);
+  solve_kernel<<<pv.G, kSolveThreads, sizeof(double) * sc.smem_doubles, s>>>(pv, sc, H_blocks, g_blocks, nullptr,
+                                                                             tau, dev_status, ws);
   return cuda_check(cudaGetLastError(), "factor launch");
 }

@@ -32,7 +32,8 @@ def to_dev(w, dtype=torch.float32):
 
 
 def gpu_match(M, plan, P, wd, **kw):
-    return M.match(plan, P, wd.X_ref, wd.X_qry, wd.D_ref, wd.D_qry, wd.Q_ref, wd.Q_qry, **kw)
+    return M.match(plan, P, wd.X_ref, wd.X_qry, M.chunk_descriptors(wd.D_ref), M.chunk_descriptors(wd.D_qry),
+                   wd.Q_ref, wd.Q_qry, **kw)
 
 
 def oracle_match_all(w, par, diag=True):
@@ -110,7 +111,8 @@ def test_match_invalid_and_edge_pixels(M):
     plan = M.Plan([[H, W], [H, W]], [[0, 1]])
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     P = M.default_params()
-    idx_g, q_g = M.match(plan, P, t(X), t(Xq), t(D), t(D), t(Q), t(Q), init_idx=t(init))
+    Dc = M.chunk_descriptors(t(D))
+    idx_g, q_g = M.match(plan, P, t(X), t(Xq), Dc, Dc, t(Q), t(Q), init_idx=t(init))
     par = M.params_dict(P)
     idx_r, q_r, dg = oracle.match(H, W, X, Xq, D, D, Q, Q, init_idx=np.where((init >= 0) & (init < H * W), init, -1),
                                   diag=True, **par)
@@ -305,8 +307,8 @@ def test_argument_errors_do_not_launch(M, tiny_wl):
     wd = to_dev(tiny_wl)
     plan = M.Plan(tiny_wl.kf_hw.numpy(), tiny_wl.edges.numpy())
     with pytest.raises(_lib.MslamError) as ei:
-        M.match(plan, P, wd.X_ref, wd.X_qry, wd.D_ref[:, :12].contiguous(), wd.D_qry[:, :12].contiguous(),
-                wd.Q_ref, wd.Q_qry)
+        M.match(plan, P, wd.X_ref, wd.X_qry, M.chunk_descriptors(wd.D_ref)[:3].contiguous(),
+                M.chunk_descriptors(wd.D_qry)[:3].contiguous(), wd.Q_ref, wd.Q_qry)
     assert ei.value.status == _lib.MSLAM_ERR_ARG
     bad = M.default_params(sigma_ray=0.0)
     idx, q = gpu_match(M, plan, P, wd)
@@ -314,3 +316,54 @@ def test_argument_errors_do_not_launch(M, tiny_wl):
         M.gn_linearize(plan, bad, tiny_wl.T_init.cuda(), wd.X_canon, idx, q)
     with pytest.raises(_lib.MslamError):
         M.Plan([[16, 16], [16, 16]], [[0, 0]])
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
+def test_packed_linearize_parity(M, tiny_wl, dtype):
+    """Packed form (gather once, stream records) against the oracle, and the
+    plain per-edge and batched packed launches agree bitwise."""
+    P = M.default_params()
+    par = M.params_dict(P)
+    ws = tiny_wl.to_storage(dtype)
+    idx_r, q_r, _ = oracle_match_all(ws, par, diag=False)
+    q_s = torch.from_numpy(q_r).to(dtype)
+    wd = ws.to("cuda")
+    plan = M.Plan(ws.kf_hw.numpy(), ws.edges.numpy())
+    T = ws.T_init.clone()
+    idx_d, q_d = torch.from_numpy(idx_r).cuda(), q_s.cuda()
+    packed = M.gn_pack(plan, P, wd.X_canon, idx_d, q_d)
+    H, g, c, nv = M.gn_linearize_packed(plan, P, dtype, T.cuda(), packed)
+    torch.cuda.synchronize()
+    Hr, gr, cr, nvr = oracle_blocks(ws, T.numpy(), idx_r, q_s, par)
+    eh, eg = block_rel_err(H, Hr), block_rel_err(g, gr)
+    print(f"packed linearize {dtype}: max H rel {eh.max():.2e}, g rel {eg.max():.2e}")
+    assert eh.max() <= BLOCK_RTOL and eg.max() <= BLOCK_RTOL
+    assert np.allclose(f64(c), cr, rtol=1e-5)
+    assert np.array_equal(nv.cpu().numpy(), nvr)
+    H2, g2, c2, nv2 = M.gn_linearize_packed(plan, P, dtype, T.cuda(), packed, per_edge=True)
+    assert torch.equal(H, H2) and torch.equal(g, g2) and torch.equal(c, c2)
+    # against the gathering form: same sums up to FP32 summation order
+    H3, g3, c3, nv3 = M.gn_linearize(plan, P, T.cuda(), wd.X_canon, idx_d, q_d)
+    assert block_rel_err(H, H3).max() <= 1e-6 and torch.equal(nv, nv3)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
+def test_packed_gauss_newton_parity(M, tiny_wl, dtype):
+    P = M.default_params()
+    par = M.params_dict(P)
+    ws = tiny_wl.to_storage(dtype)
+    idx_r, q_r, _ = oracle_match_all(ws, par, diag=False)
+    q_s = torch.from_numpy(q_r).to(dtype)
+    wd = ws.to("cuda")
+    plan = M.Plan(ws.kf_hw.numpy(), ws.edges.numpy())
+    gn = M.GaussNewton(plan, P, wd.X_canon, torch.from_numpy(idx_r).cuda(), q_s.cuda(), packed=True)
+    T_g = gn.run(ws.T_init.cuda(), ws.n_gn_iters).cpu()
+    st, T_r, hist, done = oracle.gauss_newton(ws.N, ws.edges.numpy(), ws.kf_off.numpy(), ws.e_off.numpy(),
+                                              ws.X_canon, idx_r, q_s, ws.T_init.numpy(), ws.n_gn_iters, **par)
+    assert st == 0
+    assert_poses_close(T_g, T_r)
+    # CUDA-graph capture of pack + iterations replays to the same poses
+    T_e = T_g.clone()
+    gn.capture(ws.n_gn_iters)
+    T_c = gn.replay(ws.T_init.cuda()).cpu()
+    assert torch.equal(T_e, T_c)

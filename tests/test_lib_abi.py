@@ -54,7 +54,7 @@ def test_plan_offsets_and_tiles(L):
     assert p.G == 2
     assert list(p.kf_off) == [0, 12288, 24576, 36864, 39936, 43008]
     assert list(p.e_off) == [0, 12288, 24576, 36864, 39936, 43008]
-    tiles = sum((h * w + 4095) // 4096 for h, w in [kf[j] for _, j in edges])
+    tiles = sum((h * w + 8191) // 8192 for h, w in [kf[j] for _, j in edges])  # 8192-pixel tiles
     assert p.counts[2] == tiles
     mblocks = sum(((w + 31) // 32) * ((h + 7) // 8) for h, w in [kf[j] for _, j in edges])
     assert p.counts[3] == mblocks

@@ -49,10 +49,14 @@ __device__ __forceinline__ float huber_c(float e, float delta) {
 }
 
 struct LinConst {
-  float inv_sr2, inv_sd2, delta, q_min;
+  float inv_sr2, inv_sd2, delta, delta2, q_min;
 };
 
-// Accumulate one match into acc[30].
+// Accumulate one match into acc[30].  Normalisation uses the hardware
+// reciprocal square root (max error 2 ulp) and the Huber branch needs no
+// square root in its quadratic region; the errors this adds are far below
+// the FP32 rounding of the residual itself.
+template <bool kCheckFinite>
 __device__ __forceinline__ void accumulate(float acc[kNumAcc], const RelPose& P, float3 Xj, float3 y, float qq,
                                            const LinConst& c) {
   const float x0 = fmaf(P.R[0], Xj.x, fmaf(P.R[1], Xj.y, fmaf(P.R[2], Xj.z, P.t[0])));
@@ -60,16 +64,31 @@ __device__ __forceinline__ void accumulate(float acc[kNumAcc], const RelPose& P,
   const float x2 = fmaf(P.R[6], Xj.x, fmaf(P.R[7], Xj.y, fmaf(P.R[8], Xj.z, P.t[2])));
   const float d2 = fmaf(x0, x0, fmaf(x1, x1, x2 * x2));
   const float dy2 = fmaf(y.x, y.x, fmaf(y.y, y.y, y.z * y.z));
-  if (!(d2 > 0.0f && dy2 > 0.0f && d2 < INFINITY && dy2 < INFINITY)) return;
-  const float d = sqrtf(d2), dy = sqrtf(dy2);
-  const float id = 1.0f / d, idy = 1.0f / dy;
+  if (kCheckFinite) {
+    if (!(d2 > 0.0f && dy2 > 0.0f && d2 < INFINITY && dy2 < INFINITY)) return;
+  } else {
+    if (!(d2 > 0.0f)) return;  // packed records are finite and non-zero already
+  }
+  const float id = rsqrtf(d2), idy = rsqrtf(dy2);
+  const float d = d2 * id, dy = dy2 * idy;
   const float u0 = x0 * id, u1 = x1 * id, u2 = x2 * id;
   const float r0 = u0 - y.x * idy, r1 = u1 - y.y * idy, r2 = u2 - y.z * idy;
   const float rd = d - dy;
   const float lr = qq * c.inv_sr2, ld = qq * c.inv_sd2;
-  const float er = sqrtf(lr * fmaf(r0, r0, fmaf(r1, r1, r2 * r2)));
-  const float ed = sqrtf(ld) * fabsf(rd);
-  const float wr = lr * huber_w(er, c.delta), wd = ld * huber_w(ed, c.delta);
+  const float er2 = lr * fmaf(r0, r0, fmaf(r1, r1, r2 * r2));
+  const float ed2 = ld * rd * rd;
+  // Huber: e <= delta -> weight 1, cost e^2/2; else weight delta/e, cost delta (e - delta/2)
+  float wr = lr, wd = ld, cost = 0.5f * (er2 + ed2);
+  if (er2 > c.delta2) {
+    const float ir = rsqrtf(er2);
+    wr = lr * c.delta * ir;
+    cost += c.delta * (er2 * ir - 0.5f * c.delta) - 0.5f * er2;
+  }
+  if (ed2 > c.delta2) {
+    const float ie = rsqrtf(ed2);
+    wd = ld * c.delta * ie;
+    cost += c.delta * (ed2 * ie - 0.5f * c.delta) - 0.5f * ed2;
+  }
   const float A = wr * id * id;
   acc[0] += A;
   const float cc = wd - A;
@@ -104,7 +123,7 @@ __device__ __forceinline__ void accumulate(float acc[kNumAcc], const RelPose& P,
   acc[25] = fmaf(ad, x2 * r0 - x0 * r2, acc[25]);
   acc[26] = fmaf(ad, x0 * r1 - x1 * r0, acc[26]);
   acc[27] = fmaf(wdr, d, acc[27]);
-  acc[28] += huber_c(er, c.delta) + huber_c(ed, c.delta);
+  acc[28] += cost;
   acc[29] += 1.0f;
 }
 
@@ -171,7 +190,7 @@ __global__ void __launch_bounds__(kLinThreads, MSLAM_LIN_MINBLOCKS)
       }
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u)
-        if (mm[u] >= 0 && qq[u] > lc.q_min) accumulate(acc, P, xj[u], yy[u], qq[u], lc);
+        if (mm[u] >= 0 && qq[u] > lc.q_min) accumulate<true>(acc, P, xj[u], yy[u], qq[u], lc);
     }
     // fixed-order tree: warp shuffles, then the 8 warp sums in order
 #pragma unroll
@@ -273,11 +292,14 @@ __global__ void __launch_bounds__(kLinThreads) pack_kernel(PlanView pv, float q_
         m = __ldg(idx_e + n);
         if (m >= 0) qq = ldf(q_e + n);
       }
-      const bool valid = m >= 0 && qq > q_min;
+      bool valid = m >= 0 && qq > q_min;
       float3 xj = make_float3(0.f, 0.f, 0.f), y = xj;
       if (valid) {
         xj = ld3(Xj, n);
         y = ld3(Xi, m);
+        // a degenerate point contributes nothing (as in the gathering form)
+        const float a2 = xj.x * xj.x + xj.y * xj.y + xj.z * xj.z, b2 = y.x * y.x + y.y * y.y + y.z * y.z;
+        valid = a2 > 0.0f && b2 > 0.0f && a2 < INFINITY && b2 < INFINITY;
       }
       const unsigned bal = __ballot_sync(0xffffffffu, valid);
       const int rank = __popc(bal & ((1u << lane) - 1u));
@@ -332,7 +354,7 @@ __global__ void __launch_bounds__(kLinThreads, MSLAM_PACKED_MINBLOCKS) lin_packe
       }
 #pragma unroll
       for (int u = 0; u < U; ++u)
-        if (r0 + u * kLinThreads < cnt) accumulate(acc, P, xj[u], yy[u], qq[u], lc);
+        if (r0 + u * kLinThreads < cnt) accumulate<false>(acc, P, xj[u], yy[u], qq[u], lc);
     }
 #pragma unroll
     for (int a = 0; a < kNumAcc; ++a) {
@@ -479,6 +501,7 @@ extern "C" mslam_status mslam_gn_linearize(const mslam_params* p, const mslam_pl
   lc.inv_sr2 = 1.0f / (p->sigma_ray * p->sigma_ray);
   lc.inv_sd2 = 1.0f / (p->sigma_dist * p->sigma_dist);
   lc.delta = p->huber_delta;
+  lc.delta2 = p->huber_delta * p->huber_delta;
   lc.q_min = p->q_min;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   float* partials = static_cast<float*>(workspace);
@@ -593,6 +616,7 @@ extern "C" mslam_status mslam_gn_linearize_packed(const mslam_params* p, const m
   lc.inv_sr2 = 1.0f / (p->sigma_ray * p->sigma_ray);
   lc.inv_sd2 = 1.0f / (p->sigma_dist * p->sigma_dist);
   lc.delta = p->huber_delta;
+  lc.delta2 = p->huber_delta * p->huber_delta;
   lc.q_min = p->q_min;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   float* partials = static_cast<float*>(workspace);

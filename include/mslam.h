@@ -217,6 +217,27 @@ mslam_status mslam_gn_linearize_packed(const mslam_params* p, const mslam_plan* 
                                        float* g_blocks, double* cost, int32_t* n_valid, void* workspace,
                                        size_t ws_bytes, uint32_t flags, void* stream);
 
+/* mslam_gn_linearize without a workspace argument.  The paper has no
+ * counterpart: this exists for callers that cannot allocate device memory --
+ * e.g. a tracking loop with a fixed per-frame time budget, where cudaMalloc
+ * may synchronise the device and stall the frame, or host code whose device
+ * memory is owned by another allocator that hands out no raw scratch
+ * buffers.  It uses a scratch array built into the library (4 MiB, held on
+ * every GPU that loads the library until the process exits) and allocates
+ * nothing; inputs and outputs are the caller's, exactly as in
+ * mslam_gn_linearize.  The first call on a device looks up that device's
+ * address of the array (cudaGetSymbolAddress) and so should come before any
+ * stream capture on that device.  All calls on a device share the array and
+ * every call rewrites what it reads, so nothing needs clearing; calls whose
+ * GPU work overlaps (e.g. on two streams) race on it and must be serialised.
+ * Errors: MSLAM_ERR_RANGE if the plan needs more scratch than the array
+ * holds (about 32,768 work tiles of 8,192 pixels), otherwise as
+ * mslam_gn_linearize. */
+mslam_status mslam_gn_linearize_noalloc(const mslam_params* p, const mslam_plan* plan, mslam_dtype dt,
+                                        const double* T_wc, const void* X_canon, const int32_t* idx, const void* q,
+                                        float* H_blocks, float* g_blocks, double* cost, int32_t* n_valid,
+                                        uint32_t flags, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* (a6-a8) Gauss-Newton solve with the first pose fixed, Sec. 3.5.           */
 /* ------------------------------------------------------------------------ */

@@ -70,6 +70,7 @@ SIGNATURES = {
     "mslam_workspace_bytes": ([vp, i32], sz),
     "mslam_match": ([vp, vp, C.c_int, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, i32, u32, vp], C.c_int),
     "mslam_gn_linearize": ([vp, vp, C.c_int, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, u32, vp], C.c_int),
+    "mslam_gn_linearize_noalloc": ([vp, vp, C.c_int, vp, vp, vp, vp, vp, vp, vp, vp, u32, vp], C.c_int),
     "mslam_gn_pack": ([vp, vp, C.c_int, vp, vp, vp, vp, sz, vp], C.c_int),
     "mslam_gn_linearize_packed": ([vp, vp, C.c_int, vp, vp, sz, vp, vp, vp, vp, vp, sz, u32, vp], C.c_int),
     "mslam_gn_solve": ([vp, vp, vp, vp, vp, vp, vp, vp, sz, vp], C.c_int),

@@ -74,6 +74,8 @@ def lib():
             ("orc_gauss_newton", [pp, C.c_int, C.c_int, ip, lp, lp, dp, ip, dp, C.c_int, C.c_int, dp, dp,
                                   C.POINTER(C.c_int)], C.c_int),
             ("orc_cost_grad", [pp, C.c_int, C.c_int, ip, lp, lp, dp, dp, ip, dp, dp, dp, dp], None),
+            ("orc_gn_step_grad", [pp, C.c_int, C.c_int, ip, lp, lp, dp, dp, ip, dp, dp, C.c_double, dp, dp, dp],
+             C.c_int),
             ("orc_num_threads", [], C.c_int),
         ]:
             f = getattr(L, name)
@@ -288,6 +290,25 @@ def cost_grad(N, edges, kf_off, e_off, T, X_canon, idx, q, **par):
     lib().orc_cost_grad(C.byref(params(**par)), N, edges.shape[0], _p(edges, C.c_int32), _p(kf_off, C.c_int64),
                         _p(e_off, C.c_int64), _p(T), _p(X), _p(idx, C.c_int32), _p(q), _p(dX), _p(dq), _p(c))
     return float(c[0]), dX, dq
+
+
+def gn_step_grad(N, edges, kf_off, e_off, T, X_canon, idx, q, dL_dtau=None, dL_dcost=1.0, **par):
+    """Gradient of dL_dcost * E + dL_dtau . tau (one GN step) w.r.t. X_canon
+    and q.  Returns (status, dX [P, 3], dq [P_e], tau [N, 7])."""
+    edges = _i32(edges).reshape(-1, 2)
+    kf_off, e_off = _i64(kf_off), _i64(e_off)
+    X = _d(X_canon).reshape(-1, 3)
+    idx = _i32(idx).reshape(-1)
+    q = _d(q).reshape(-1)
+    T = _d(T).reshape(N, 8)
+    a = None if dL_dtau is None else _d(dL_dtau).reshape(N * 7)
+    dX = np.zeros_like(X)
+    dq = np.zeros_like(q)
+    tau = np.zeros((N, 7))
+    st = lib().orc_gn_step_grad(C.byref(params(**par)), N, edges.shape[0], _p(edges, C.c_int32),
+                                _p(kf_off, C.c_int64), _p(e_off, C.c_int64), _p(T), _p(X), _p(idx, C.c_int32), _p(q),
+                                _p(a) if a is not None else None, float(dL_dcost), _p(dX), _p(dq), _p(tau))
+    return st, dX, dq, tau
 
 
 def num_threads() -> int:

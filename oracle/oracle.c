@@ -11,6 +11,7 @@
  */
 #include "oracle.h"
 
+#include <complex.h>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -86,9 +87,9 @@ static double int_xn_exp(int n, double s) {
     }
     return sum;
   }
-  double I = expm1(s) / s, es = exp(s);
-  for (int k = 1; k <= n; ++k) I = (es - k * I) / s;
-  return I;
+  double mom = expm1(s) / s, es = exp(s);
+  for (int k = 1; k <= n; ++k) mom = (es - k * mom) / s;
+  return mom;
 }
 
 /* V = integral_0^1 exp(x ([phi]x + sigma I)) dx = A0 I + B [phi]x + C [phi]x^2,
@@ -622,4 +623,201 @@ void orc_cost_grad(const orc_params* P, int N, int E, const int32_t* edges, cons
     }
   }
   if (cost) *cost = c;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Adjoint of one Gauss-Newton step (project form; not in the paper).        */
+/* tau = -H^-1 g (Eq. gauss_newton, gauge pose removed).  For L = a . tau,    */
+/* dL = -b^T (dH tau + dg) with b = H^-1 a, i.e. dL/dtheta = -d phi/d theta   */
+/* at fixed b and tau, phi = sum over matches of (J b)^T W (J tau + r), J the */
+/* 4 x 14 global Jacobian.  Each match's phi depends on X_j[n], X_i[m], q[n]; */
+/* its seven partial derivatives are taken by complex-step differentiation   */
+/* (Squire & Trapp 1998): phi(v + i h e_k) with h = 1e-30, derivative =       */
+/* Im / h, exact to rounding.  The complex evaluation below restates the      */
+/* literal residual and Jacobian of residual_jacobian_rel.                    */
+/* ------------------------------------------------------------------------ */
+typedef double complex cplx;
+
+static cplx huber_weight_c(cplx e, double delta) { return creal(e) <= delta ? 1.0 : delta / e; }
+
+/* phi of one match with complex inputs xj (point in frame j), y (point X_i[m]), q */
+static cplx match_phi_c(const orc_params* P, const double Tij[8], const double Ad[49], const double b14[14],
+                        const double t14[14], const cplx xj[3], const cplx y[3], cplx q) {
+  double R[9];
+  quat_to_rot(Tij + 3, R);
+  cplx x[3];
+  for (int r = 0; r < 3; ++r) x[r] = Tij[7] * (R[3 * r] * xj[0] + R[3 * r + 1] * xj[1] + R[3 * r + 2] * xj[2]) + Tij[r];
+  cplx d = csqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  cplx dy = csqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
+  cplx r4[4];
+  for (int c = 0; c < 3; ++c) r4[c] = x[c] / d - y[c] / dy;
+  r4[3] = d - dy;
+  /* dx/dtau = [I, -[x]x, x]; dr/dx = (I - x x^T/d^2)/d (ray), x^T/d (distance) */
+  cplx Dx[21], Dr[12], J[28];
+  cplx S[9] = {0, -x[2], x[1], x[2], 0, -x[0], -x[1], x[0], 0};
+  for (int rr = 0; rr < 3; ++rr) {
+    for (int c = 0; c < 3; ++c) {
+      Dx[7 * rr + c] = (rr == c) ? 1.0 : 0.0;
+      Dx[7 * rr + 3 + c] = -S[3 * rr + c];
+      Dr[3 * rr + c] = ((rr == c ? 1.0 : 0.0) - x[rr] * x[c] / (d * d)) / d;
+    }
+    Dx[7 * rr + 6] = x[rr];
+  }
+  for (int c = 0; c < 3; ++c) Dr[9 + c] = x[c] / d;
+  for (int rr = 0; rr < 4; ++rr)
+    for (int c = 0; c < 7; ++c) {
+      cplx acc = 0;
+      for (int k = 0; k < 3; ++k) acc += Dr[3 * rr + k] * Dx[7 * k + c];
+      J[7 * rr + c] = acc;
+    }
+  /* global Jacobian [-J Ad, J Ad] applied to b and tau */
+  cplx Jb[4], Jt[4];
+  for (int rr = 0; rr < 4; ++rr) {
+    cplx sb = 0, st = 0;
+    for (int c = 0; c < 7; ++c) {
+      cplx ja = 0;
+      for (int k = 0; k < 7; ++k) ja += J[7 * rr + k] * Ad[7 * k + c];
+      sb += -ja * b14[c] + ja * b14[7 + c];
+      st += -ja * t14[c] + ja * t14[7 + c];
+    }
+    Jb[rr] = sb;
+    Jt[rr] = st;
+  }
+  cplx lr = q / (P->sigma_ray * P->sigma_ray), ld = q / (P->sigma_dist * P->sigma_dist);
+  cplx er = csqrt(lr * (r4[0] * r4[0] + r4[1] * r4[1] + r4[2] * r4[2]));
+  cplx ed = csqrt(ld * r4[3] * r4[3]);
+  cplx wr = lr * huber_weight_c(er, P->huber_delta), wd = ld * huber_weight_c(ed, P->huber_delta);
+  return wr * (Jb[0] * (Jt[0] + r4[0]) + Jb[1] * (Jt[1] + r4[1]) + Jb[2] * (Jt[2] + r4[2])) +
+         wd * Jb[3] * (Jt[3] + r4[3]);
+}
+
+/* Solve the gauge-reduced dense system H x = rhs (Cholesky); returns 0 or 3. */
+static int dense_spd_solve(int m, const double* A, const double* rhs, double* x) {
+  double* L = (double*)calloc((size_t)m * m, sizeof(double));
+  int st = 0;
+  for (int j = 0; j < m && !st; ++j)
+    for (int i = j; i < m; ++i) {
+      double s = A[(size_t)i * m + j];
+      for (int k = 0; k < j; ++k) s -= L[(size_t)i * m + k] * L[(size_t)j * m + k];
+      if (i == j) {
+        if (!(s > 1e-12 * A[(size_t)j * m + j]) || !isfinite(s)) { st = 3; break; }
+        L[(size_t)j * m + j] = sqrt(s);
+      } else {
+        L[(size_t)i * m + j] = s / L[(size_t)j * m + j];
+      }
+    }
+  if (!st) {
+    for (int i = 0; i < m; ++i) {
+      double s = rhs[i];
+      for (int k = 0; k < i; ++k) s -= L[(size_t)i * m + k] * x[k];
+      x[i] = s / L[(size_t)i * m + i];
+    }
+    for (int i = m - 1; i >= 0; --i) {
+      double s = x[i];
+      for (int k = i + 1; k < m; ++k) s -= L[(size_t)k * m + i] * x[k];
+      x[i] = s / L[(size_t)i * m + i];
+    }
+  }
+  free(L);
+  return st;
+}
+
+int orc_gn_step_grad(const orc_params* P, int N, int E, const int32_t* edges, const int64_t* kf_off,
+                     const int64_t* e_off, const double* T, const double* X_canon, const int32_t* idx, const double* q,
+                     const double* dL_dtau, double dL_dcost, double* dX, double* dq, double* tau_out) {
+  /* linearise every edge and assemble the dense 7N system */
+  int n = 7 * N, gauge = 0, m = 7 * (N - 1);
+  double* H14 = (double*)malloc(sizeof(double) * 196 * (size_t)(E > 0 ? E : 1));
+  double* g14 = (double*)malloc(sizeof(double) * 14 * (size_t)(E > 0 ? E : 1));
+  double cost;
+  for (int e = 0; e < E; ++e) {
+    int i = edges[2 * e], j = edges[2 * e + 1];
+    orc_linearize_edge(P, T + 8 * i, T + 8 * j, e_off[e + 1] - e_off[e], X_canon + 3 * kf_off[i],
+                       X_canon + 3 * kf_off[j], idx + e_off[e], q + e_off[e], H14 + 196 * (size_t)e,
+                       g14 + 14 * (size_t)e, &cost, NULL);
+  }
+  double* A = (double*)calloc((size_t)n * n, sizeof(double));
+  double* g = (double*)calloc((size_t)n, sizeof(double));
+  for (int e = 0; e < E; ++e) {
+    int pose[2] = {edges[2 * e], edges[2 * e + 1]};
+    for (int a = 0; a < 14; ++a) {
+      int ia = 7 * pose[a / 7] + a % 7;
+      g[ia] += g14[14 * e + a];
+      for (int bb = 0; bb < 14; ++bb) A[(size_t)ia * n + 7 * pose[bb / 7] + bb % 7] += H14[196 * (size_t)e + 14 * a + bb];
+    }
+  }
+  double* Ar = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1) * (m > 0 ? m : 1));
+  double* rg = (double*)malloc(sizeof(double) * (m > 0 ? m : 1));
+  double* ra = (double*)malloc(sizeof(double) * (m > 0 ? m : 1));
+  double* tr = (double*)malloc(sizeof(double) * (m > 0 ? m : 1));
+  double* br = (double*)malloc(sizeof(double) * (m > 0 ? m : 1));
+  for (int i = 0; i < m; ++i) {
+    rg[i] = -g[7 + i];
+    ra[i] = dL_dtau ? dL_dtau[7 + i] : 0.0;
+    for (int k = 0; k < m; ++k) Ar[(size_t)i * m + k] = A[(size_t)(7 + i) * n + 7 + k];
+  }
+  int st = dense_spd_solve(m, Ar, rg, tr);
+  if (!st) st = dense_spd_solve(m, Ar, ra, br);
+  double* tau = (double*)calloc((size_t)n, sizeof(double));
+  double* b = (double*)calloc((size_t)n, sizeof(double));
+  if (!st)
+    for (int i = 0; i < m; ++i) {
+      tau[7 + i] = tr[i];
+      b[7 + i] = br[i];
+    }
+  if (tau_out) memcpy(tau_out, tau, sizeof(double) * n);
+  (void)gauge;
+  /* cost term */
+  double c;
+  orc_cost_grad(P, N, E, edges, kf_off, e_off, T, X_canon, idx, q, dX, dq, &c);
+  if (dL_dcost != 1.0) {
+    /* orc_cost_grad accumulated the unit-weight gradient: rescale it */
+    for (int64_t k = 0; k < 3 * kf_off[N]; ++k) dX[k] *= dL_dcost;
+    for (int64_t k = 0; k < e_off[E]; ++k) dq[k] *= dL_dcost;
+  }
+  /* step term by complex-step differentiation of phi */
+  if (dL_dtau && !st) {
+    const double h = 1e-30;
+    for (int e = 0; e < E; ++e) {
+      int i = edges[2 * e], j = edges[2 * e + 1];
+      double Tii[8], Tij[8], Ad[49], b14[14], t14[14];
+      orc_sim3_inv(T + 8 * i, Tii);
+      orc_sim3_mul(Tii, T + 8 * j, Tij);
+      orc_sim3_adjoint(Tii, Ad);
+      for (int k = 0; k < 7; ++k) {
+        b14[k] = b[7 * i + k];
+        b14[7 + k] = b[7 * j + k];
+        t14[k] = tau[7 * i + k];
+        t14[7 + k] = tau[7 * j + k];
+      }
+      const double* Xi = X_canon + 3 * kf_off[i];
+      const double* Xj = X_canon + 3 * kf_off[j];
+      int64_t np = e_off[e + 1] - e_off[e];
+      for (int64_t nn = 0; nn < np; ++nn) {
+        int32_t mm = idx[e_off[e] + nn];
+        double qq = q[e_off[e] + nn];
+        if (mm < 0 || !(qq > P->q_min)) continue;
+        const double* xj = Xj + 3 * nn;
+        const double* y = Xi + 3 * (int64_t)mm;
+        double xw[3];
+        orc_sim3_act(Tij, xj, xw);
+        if (!(finite3(xw) && finite3(y) && norm3(xw) > 0 && norm3(y) > 0)) continue;
+        double grad[7];
+        for (int k = 0; k < 7; ++k) {
+          cplx xc[3] = {xj[0], xj[1], xj[2]}, yc[3] = {y[0], y[1], y[2]}, qc = qq;
+          if (k < 3) xc[k] += _Complex_I * h;
+          else if (k < 6) yc[k - 3] += _Complex_I * h;
+          else qc += _Complex_I * h;
+          grad[k] = cimag(match_phi_c(P, Tij, Ad, b14, t14, xc, yc, qc)) / h;
+        }
+        for (int k = 0; k < 3; ++k) {
+          dX[3 * (kf_off[j] + nn) + k] -= grad[k];
+          dX[3 * (kf_off[i] + mm) + k] -= grad[3 + k];
+        }
+        dq[e_off[e] + nn] -= grad[6];
+      }
+    }
+  }
+  free(b); free(tau); free(br); free(tr); free(ra); free(rg); free(Ar); free(g); free(A); free(g14); free(H14);
+  return st;
 }

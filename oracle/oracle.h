@@ -99,6 +99,14 @@ void orc_cost_grad(const orc_params* P, int N, int E, const int32_t* edges,
                    const double* X_canon, const int32_t* idx, const double* q,
                    double* dX, double* dq, double* cost);
 
+/* Gradient of L = dL_dcost * E_g + dL_dtau . tau, tau = -H^-1 g the Gauss-
+ * Newton step at T with the first pose fixed, with respect to X_canon and q
+ * (dX, dq overwritten).  The step term is differentiated by complex step.
+ * tau_out [N, 7] may be NULL.  Returns 0, or 3 if H is not positive definite. */
+int orc_gn_step_grad(const orc_params* P, int N, int E, const int32_t* edges, const int64_t* kf_off,
+                     const int64_t* e_off, const double* T, const double* X_canon, const int32_t* idx, const double* q,
+                     const double* dL_dtau, double dL_dcost, double* dX, double* dq, double* tau_out);
+
 int orc_num_threads(void);
 
 #ifdef __cplusplus

@@ -14,6 +14,8 @@
 // T <- Exp(tau) o T in FP64 (Eq. 1, Eq. gauss_newton).  The numeric factor
 // lives in shared memory when the graph fits (the 64-keyframe graph needs
 // 151 KB), else in the caller's workspace.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "common.cuh"
@@ -235,19 +237,17 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(PlanView pv, Solve
         }
         s = rhs[7 * p + lane] - (((ps[0] + ps[1]) + (ps[2] + ps[3])) + ((ps[4] + ps[5]) + ps[6]));
       }
-      double sv[7];
+      // L_pp^T x = s, column-oriented across lanes 0..6: x_k = s_k / L_kk,
+      // then s_l -= L_kl x_k for l < k (a few dependent operations per k)
+      const double* iv = invd + 7 * p;
+      double xl = 0.0;
 #pragma unroll
-      for (int k = 0; k < 7; ++k) sv[k] = __shfl_sync(0xffffffffu, s, k);
-      if (lane == 0) {
-        const double* iv = invd + 7 * p;
-        double x[7];
-        for (int k = 6; k >= 0; --k) {
-          double v = sv[k];
-          for (int l2 = k + 1; l2 < 7; ++l2) v -= D[7 * l2 + k] * x[l2];
-          x[k] = v * iv[k];
-        }
-        for (int k = 0; k < 7; ++k) rhs[7 * p + k] = x[k];
+      for (int k = 6; k >= 0; --k) {
+        const double xk = __shfl_sync(0xffffffffu, s, k) * iv[k];
+        if (lane == k) xl = xk;
+        if (lane < k) s = fma(-D[7 * k + lane], xk, s);
       }
+      if (lane < 7) rhs[7 * p + lane] = xl;
       __syncwarp();
     }
     __syncthreads();
@@ -287,19 +287,341 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(PlanView pv, Solve
   if (tid == 0 && !sc.factor_only && s_max < sc.conv_tol) dev_status[g] = 1;
 }
 
+// ---------------------------------------------------------------- cluster form
+// The same factorisation spread over a thread-block cluster of kClusterSize
+// CTAs (one cluster per graph).  Every CTA keeps a full replica of the
+// factor, right-hand side, assembled diagonal and reciprocal pivots in its
+// shared memory, so all reads are local; each value is computed by one
+// thread of the cluster and written to all replicas through distributed
+// shared memory, and a cluster barrier (release / acquire) separates the
+// phases.  Control flow is uniform across the cluster: no CTA leaves early
+// between barriers (a failed pivot only marks the status).
+constexpr int kClusterSize = 2;  // measured fastest of 1, 2, 4, 8 on the 64-keyframe graph
+
+__global__ void __launch_bounds__(kSolveThreads) solve_cluster_kernel(PlanView pv, SolveConst sc,
+                                                                      const float* __restrict__ H14,
+                                                                      const float* __restrict__ g14,
+                                                                      double* __restrict__ T_wc,
+                                                                      double* __restrict__ tau_out,
+                                                                      int32_t* __restrict__ dev_status,
+                                                                      double* __restrict__ ws) {
+  namespace cg = cooperative_groups;
+  extern __shared__ double smem[];
+  __shared__ double* rbase[kClusterSize];
+  __shared__ int* rfail[kClusterSize];
+  __shared__ int s_fail;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int g = blockIdx.x / kClusterSize;
+  const DevGraph G = pv.graphs[g];
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int ctid = rank * nth + tid, cnth = kClusterSize * nth;            // cluster-wide thread index
+  const int nwarps = nth >> 5, cwarp = rank * nwarps + warp, cnwarps = kClusterSize * nwarps;
+  // uniform across the cluster (all CTAs read the same status)
+  if (dev_status[g] > (sc.factor_only ? 1 : 0)) return;
+  const int m = G.m;
+  if (m == 0) {
+    if (rank == 0 && tid == 0 && !sc.factor_only) dev_status[g] = 1;
+    if (rank == 0 && tau_out && tid < 7) tau_out[7 * G.gauge + tid] = 0.0;
+    return;
+  }
+  if (tid < kClusterSize) {
+    rbase[tid] = cl.map_shared_rank(smem, tid);
+    rfail[tid] = cl.map_shared_rank(&s_fail, tid);
+  }
+  if (tid == 0) s_fail = 0;
+  cl.sync();  // every CTA of the cluster is running and initialised
+  const int32_t* I = pv.ints;
+  const int32_t* pose_of_pos = I + G.off_pose;
+  const int32_t* col_ptr = I + G.off_col;
+  const int32_t* colent = I + G.off_colent;
+  const int32_t* asm_ptr = I + G.off_asm;
+  const int32_t* asment = I + G.off_asment;
+  const int32_t* gasm_ptr = I + G.off_gasm;
+  const int32_t* gasment = I + G.off_gasment;
+  const int32_t* lev_ptr = I + G.off_lev;
+  const int32_t* lev_cols = I + G.off_levcols;
+  const int32_t* levtgt = I + G.off_levtgt;
+  const int32_t* tgtlist = I + G.off_tgtlist;
+  const int32_t* tptr = I + G.off_tptr;
+  const int32_t* pairs = I + G.off_pairs;
+  const int32_t* rsptr = I + G.off_rsptr;
+  const int32_t* rs = I + G.off_rs;
+  const int32_t* blkcol = I + G.off_blkcol;
+  const size_t need = (size_t)G.n_blocks * 49 + 21 * (size_t)m;
+  double* L = smem;
+  const size_t off_rhs = (size_t)G.n_blocks * 49, off_d0 = off_rhs + 7 * (size_t)m, off_iv = off_d0 + 7 * (size_t)m;
+  double* rhs = L + off_rhs;
+  double* diag0 = L + off_d0;
+  double* invd = L + off_iv;
+  auto put = [&](size_t off, double v) {
+#pragma unroll
+    for (int r = 0; r < kClusterSize; ++r) rbase[r][off] = v;
+  };
+
+  // ---- assembly
+  for (int t = ctid; t < G.n_blocks * 49; t += cnth) {
+    const int b = t / 49, e = t % 49, r = e / 7, c = e % 7;
+    double s = 0.0;
+    const int k1 = __ldg(asm_ptr + b + 1);
+    for (int k = __ldg(asm_ptr + b); k < k1; ++k) {
+      const int code = __ldg(asment + k), edge = code >> 2, quad = code & 3;
+      const int r0 = (quad == 0 || quad == 2) ? 0 : 7;
+      const int c0 = (quad == 0 || quad == 3) ? 0 : 7;
+      s += (double)__ldg(H14 + (size_t)edge * 196 + (r0 + r) * 14 + c0 + c);
+    }
+    put(t, s);
+    if (b < m && r == c) put(off_d0 + 7 * b + r, s);
+  }
+  for (int t = ctid; t < 7 * m; t += cnth) {
+    const int p = t / 7, a = t % 7;
+    double s = 0.0;
+    const int k1 = __ldg(gasm_ptr + p + 1);
+    for (int k = __ldg(gasm_ptr + p); k < k1; ++k) {
+      const int code = __ldg(gasment + k), edge = code >> 1, side = code & 1;
+      s += (double)__ldg(g14 + (size_t)edge * 14 + 7 * side + a);
+    }
+    put(off_rhs + t, -s);
+  }
+  cl.sync();
+
+  // ---- factorisation by levels
+  for (int l = 0; l < G.n_levels; ++l) {
+    const int q0 = __ldg(lev_ptr + l), q1 = __ldg(lev_ptr + l + 1);
+    const int g0 = __ldg(levtgt + l), g1 = __ldg(levtgt + l + 1);
+    const int nA = (g1 - g0) * 49;
+    for (int w = ctid; w < nA + (q1 - q0) * 7; w += cnth) {
+      if (w < nA) {
+        const int t = __ldg(tgtlist + g0 + w / 49), e = w % 49, r = e / 7, c = e % 7;
+        const int k1 = __ldg(tptr + t + 1);
+        double ps[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int k = __ldg(tptr + t); k < k1; ++k) {
+          const double* Lb = L + 49 * (size_t)__ldg(pairs + 2 * k) + 7 * r;
+          const double* La = L + 49 * (size_t)__ldg(pairs + 2 * k + 1) + 7 * c;
+#pragma unroll
+          for (int kk = 0; kk < 7; ++kk) ps[kk] = fma(Lb[kk], La[kk], ps[kk]);
+        }
+        const size_t off = 49 * (size_t)t + e;
+        put(off, L[off] - (((ps[0] + ps[1]) + (ps[2] + ps[3])) + ((ps[4] + ps[5]) + ps[6])));
+      } else {
+        const int ww = w - nA, p = __ldg(lev_cols + q0 + ww / 7), a = ww % 7;
+        const int k1 = __ldg(rsptr + p + 1);
+        double ps[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int k = __ldg(rsptr + p); k < k1; ++k) {
+          const double* Lpc = L + 49 * (size_t)__ldg(rs + 2 * k + 1) + 7 * a;
+          const double* yc = rhs + 7 * __ldg(rs + 2 * k);
+#pragma unroll
+          for (int kk = 0; kk < 7; ++kk) ps[kk] = fma(Lpc[kk], yc[kk], ps[kk]);
+        }
+        const size_t off = off_rhs + 7 * (size_t)p + a;
+        put(off, L[off] - (((ps[0] + ps[1]) + (ps[2] + ps[3])) + ((ps[4] + ps[5]) + ps[6])));
+      }
+    }
+    cl.sync();
+    for (int qi = q0 + cwarp; qi < q1; qi += cnwarps) {
+      const int p = __ldg(lev_cols + qi);
+      const double* D = L + 49 * (size_t)p;
+      const bool mine = lane < 7;
+      const int li = mine ? lane : 0;
+      double row[7], yv = mine ? rhs[7 * p + li] : 0.0;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) row[k] = D[7 * li + k];
+      bool bad = false;
+#pragma unroll
+      for (int j = 0; j < 7; ++j) {
+        const double djj = __shfl_sync(0xffffffffu, row[j], j);
+        const bool okj = (djj > 1e-12 * diag0[7 * p + j]) && isfinite(djj);
+        bad |= !okj;
+        const double ivj = rsqrt_newton(okj ? djj : 1.0);
+        const double yj = __shfl_sync(0xffffffffu, yv, j) * ivj;
+        const double lij = (lane == j && !okj) ? 1.0 : row[j] * ivj;
+        if (mine && lane >= j) row[j] = lij;
+        if (lane == j) {
+          put(off_iv + 7 * (size_t)p + j, ivj);
+          yv = yj;
+        } else if (mine && lane > j) {
+          yv = fma(-lij, yj, yv);
+        }
+#pragma unroll
+        for (int k = j + 1; k < 7; ++k) {
+          const double lkj = __shfl_sync(0xffffffffu, row[j], k);
+          if (mine && lane >= k) row[k] = fma(-lij, lkj, row[k]);
+        }
+      }
+      if (mine) {
+#pragma unroll
+        for (int k = 0; k < 7; ++k)
+          if (k <= lane) put(49 * (size_t)p + 7 * lane + k, row[k]);
+        put(off_rhs + 7 * (size_t)p + lane, yv);
+      }
+      if (bad && lane == 0)
+        for (int r = 0; r < kClusterSize; ++r) *rfail[r] = 1;
+    }
+    cl.sync();
+    for (int w = ctid; w < (g1 - g0) * 7; w += cnth) {
+      const int t = __ldg(tgtlist + g0 + w / 7), a = w % 7;
+      if (t < m) continue;
+      const int p = __ldg(blkcol + t);
+      const double* D = L + 49 * (size_t)p;
+      const double* iv = invd + 7 * p;
+      const double* row = L + 49 * (size_t)t + 7 * a;
+      double x[7];
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        double v = row[k];
+        for (int l2 = 0; l2 < k; ++l2) v -= x[l2] * D[7 * k + l2];
+        x[k] = v * iv[k];
+      }
+#pragma unroll
+      for (int k = 0; k < 7; ++k) put(49 * (size_t)t + 7 * a + k, x[k]);
+    }
+    cl.sync();
+  }
+
+  // ---- back substitution by levels (reverse)
+  for (int l = G.n_levels - 1; l >= 0; --l) {
+    const int q0 = __ldg(lev_ptr + l), q1 = __ldg(lev_ptr + l + 1);
+    for (int qi = q0 + cwarp; qi < q1; qi += cnwarps) {
+      const int p = __ldg(lev_cols + qi);
+      const double* D = L + 49 * (size_t)p;
+      const int c0 = __ldg(col_ptr + p), c1 = __ldg(col_ptr + p + 1);
+      double s = 0.0;
+      if (lane < 7) {
+        double ps[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int ent = c0; ent < c1; ++ent) {
+          const double* Lr = L + 49 * (size_t)__ldg(colent + 2 * ent + 1);
+          const double* xr = rhs + 7 * __ldg(colent + 2 * ent);
+#pragma unroll
+          for (int k = 0; k < 7; ++k) ps[k] = fma(Lr[7 * k + lane], xr[k], ps[k]);
+        }
+        s = rhs[7 * p + lane] - (((ps[0] + ps[1]) + (ps[2] + ps[3])) + ((ps[4] + ps[5]) + ps[6]));
+      }
+      const double* iv = invd + 7 * p;
+      double xl = 0.0;
+#pragma unroll
+      for (int k = 6; k >= 0; --k) {
+        const double xk = __shfl_sync(0xffffffffu, s, k) * iv[k];
+        if (lane == k) xl = xk;
+        if (lane < k) s = fma(-D[7 * k + lane], xk, s);
+      }
+      if (lane < 7) put(off_rhs + 7 * (size_t)p + lane, xl);
+      __syncwarp();
+    }
+    cl.sync();
+  }
+  // every replica now holds tau in rhs; the failure flag is the same in all CTAs
+  const bool failed = s_fail != 0;
+  if (sc.factor_only && rank == 0 && !failed) {
+    for (size_t t = tid; t < need; t += nth) ws[G.ws_off + t] = L[t];  // the adjoint reuses the factor
+  }
+  if (failed) {
+    if (rank == 0 && tid == 0) dev_status[g] = MSLAM_ERR_NOT_PD;
+    cl.sync();  // keep every replica alive until all remote writes are done
+    return;
+  }
+  // max |tau| and finiteness over the replica (the same in every CTA)
+  __shared__ double s_wmax[kSolveThreads / 32];
+  __shared__ int s_nf;
+  if (tid == 0) s_nf = 0;
+  __syncthreads();
+  double mx = 0.0;
+  for (int t = tid; t < 7 * m; t += nth) {
+    const double v = rhs[t];
+    if (!isfinite(v)) s_nf = 1;
+    mx = fmax(mx, fabs(v));
+  }
+  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  if (lane == 0) s_wmax[warp] = mx;
+  __syncthreads();
+  mx = 0.0;
+  for (int w = 0; w < nwarps; ++w) mx = fmax(mx, s_wmax[w]);
+  const bool nonfinite = s_nf != 0;
+  if (tau_out && rank == 0 && tid < 7) tau_out[7 * G.gauge + tid] = 0.0;
+  if (!nonfinite) {
+    for (int p = ctid; p < m; p += cnth) {
+      const int k = __ldg(pose_of_pos + p);
+      double tau[7];
+      for (int a = 0; a < 7; ++a) tau[a] = rhs[7 * p + a];
+      if (tau_out)
+        for (int a = 0; a < 7; ++a) tau_out[7 * k + a] = tau[a];
+      if (sc.factor_only) continue;
+      const Sim3d E = sim3_exp(tau);
+      store_pose(compose(E, load_pose(T_wc + 8 * k)), T_wc + 8 * k);
+    }
+  }
+  if (rank == 0 && tid == 0) {
+    if (nonfinite) dev_status[g] = MSLAM_ERR_NONFINITE;
+    else if (!sc.factor_only && mx < sc.conv_tol) dev_status[g] = 1;
+  }
+  cl.sync();  // no CTA exits while others may still read its shared memory
+}
+
 // Dynamic shared memory for the solve: the largest graph's factor if it fits
 // in the opt-in per-CTA limit, else none (all graphs then use the workspace).
-static int solve_smem_doubles(const mslam_plan* plan) {
+static int smem_limit_bytes() {
   static int limit = -1;
   if (limit < 0) {
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    limit = std::max(0, optin - 1024);  // headroom for the static shared variables
+    limit = std::max(0, optin - 2048);  // headroom for the static shared variables
     cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
+    cudaFuncSetAttribute(solve_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
   }
+  return limit;
+}
+
+static int solve_smem_doubles(const mslam_plan* plan) {
   const int64_t need = plan_max_graph_doubles(plan);
-  return (need * (int64_t)sizeof(double) <= limit) ? (int)need : 0;
+  return (need * (int64_t)sizeof(double) <= smem_limit_bytes()) ? (int)need : 0;
+}
+
+// Whether one cluster of kClusterSize CTAs with this much shared memory can
+// be resident (asked once per size, outside any stream capture).
+static bool cluster_fits(int smem_bytes) {
+  static int cached_bytes = -1;
+  static bool cached_ok = false;
+  if (smem_bytes == cached_bytes) return cached_ok;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kClusterSize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(kClusterSize);
+  cfg.blockDim = dim3(kSolveThreads);
+  cfg.dynamicSmemBytes = smem_bytes;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  const cudaError_t e = cudaOccupancyMaxActiveClusters(&n, solve_cluster_kernel, &cfg);
+  cudaGetLastError();  // clear a refusal: the single-CTA form is used instead
+  cached_bytes = smem_bytes;
+  cached_ok = (e == cudaSuccess && n >= 1);
+  return cached_ok;
+}
+
+static mslam_status launch_solve(const PlanView& pv, SolveConst sc, const float* H, const float* g, double* T,
+                                 double* tau, int32_t* st, double* ws, cudaStream_t s) {
+  smem_limit_bytes();
+  if (sc.smem_doubles > 0 && cluster_fits((int)(sizeof(double) * sc.smem_doubles))) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kClusterSize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(pv.G * kClusterSize);
+    cfg.blockDim = dim3(kSolveThreads);
+    cfg.dynamicSmemBytes = sizeof(double) * sc.smem_doubles;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cuda_check(cudaLaunchKernelEx(&cfg, solve_cluster_kernel, pv, sc, H, g, T, tau, st, ws),
+                      "gn_solve cluster launch");
+  }
+  solve_kernel<<<pv.G, kSolveThreads, sizeof(double) * sc.smem_doubles, s>>>(pv, sc, H, g, T, tau, st, ws);
+  return cuda_check(cudaGetLastError(), "gn_solve launch");
 }
 
 }  // namespace mslam
@@ -329,9 +651,7 @@ extern "C" mslam_status mslam_gn_solve(const mslam_params* p, const mslam_plan* 
   sc.factor_only = 0;
   sc.smem_doubles = solve_smem_doubles(plan);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  solve_kernel<<<pv.G, kSolveThreads, sizeof(double) * sc.smem_doubles, s>>>(
-      pv, sc, H_blocks, g_blocks, T_wc, tau, dev_status, static_cast<double*>(workspace));
-  return cuda_check(cudaGetLastError(), "gn_solve launch");
+  return launch_solve(pv, sc, H_blocks, g_blocks, T_wc, tau, dev_status, static_cast<double*>(workspace), s);
 }
 
 // Factor every graph's system and write tau = -H^-1 g without updating poses
@@ -343,7 +663,5 @@ mslam_status mslam_factor_only(const mslam_plan* plan, const float* H_blocks, co
   sc.conv_tol = 0.0;
   sc.factor_only = 1;
   sc.smem_doubles = solve_smem_doubles(plan);
-  solve_kernel<<<pv.G, kSolveThreads, sizeof(double) * sc.smem_doubles, s>>>(pv, sc, H_blocks, g_blocks, nullptr,
-                                                                             tau, dev_status, ws);
-  return cuda_check(cudaGetLastError(), "factor launch");
+  return launch_solve(pv, sc, H_blocks, g_blocks, nullptr, tau, dev_status, ws, s);
 }

@@ -295,3 +295,51 @@ def test_cost_gradient_wrt_points_and_confidence(tiny_wl):
         tot += oracle.linearize_edge(T[i], T[j], X[w.kf_slice(i)], X[w.kf_slice(j)], idx[w.edge_slice(e)],
                                      q[w.edge_slice(e)], **PAR)[2]
     assert abs(tot - c0) <= 1e-12 * abs(c0)
+
+
+def test_step_gradient_against_finite_differences():
+    """The oracle's adjoint of one Gauss-Newton step (complex step on the
+    per-match terms, dL = -b^T (dH tau + dg)) equals central differences of
+    L(X, q) = c E(X, q) + a . tau(X, q), tau the oracle's own step."""
+    rng = np.random.default_rng(6)
+    import synth
+    w = synth.global_graph(N=4, n_pairs=5, H=12, W=16, seed=5)
+    N = w.N
+    edges = w.edges.numpy()
+    kf_off, e_off = w.kf_off.numpy(), w.e_off.numpy()
+    X = w.X_canon.double().numpy().copy()
+    idx = w.gt_match.numpy()
+    q = w.Q_qry.double().numpy() * 0.5 + 1.0
+    T = w.T_init.numpy()
+    a = rng.normal(size=(N, 7))
+    a[0] = 0.0
+    c = 0.7
+    st, dX, dq, tau = oracle.gn_step_grad(N, edges, kf_off, e_off, T, X, idx, q, dL_dtau=a, dL_dcost=c, **PAR)
+    assert st == 0
+
+    def L(Xv, qv):
+        s2, _, _, t2 = oracle.gn_step_grad(N, edges, kf_off, e_off, T, Xv, idx, qv, dL_dtau=a, dL_dcost=1.0, **PAR)
+        cost = oracle.cost_grad(N, edges, kf_off, e_off, T, Xv, idx, qv, **PAR)[0]
+        return c * cost + float((a * t2).sum())
+
+    used = np.nonzero((idx >= 0) & (q > PAR["q_min"]))[0]
+    checked = 0
+    for p in rng.choice(X.shape[0], 40, replace=False):
+        k = int(rng.integers(0, 3))
+        if dX[p, k] == 0.0:
+            continue
+        h = 1e-5 * max(1.0, abs(X[p, k]))
+        Xp, Xm = X.copy(), X.copy()
+        Xp[p, k] += h
+        Xm[p, k] -= h
+        fd = (L(Xp, q) - L(Xm, q)) / (2 * h)
+        assert abs(fd - dX[p, k]) <= 2e-5 * max(1.0, abs(dX[p, k])), (p, k, fd, dX[p, k])
+        checked += 1
+    for p in rng.choice(used, 10, replace=False):
+        h = 1e-6 * q[p]
+        qp, qm = q.copy(), q.copy()
+        qp[p] += h
+        qm[p] -= h
+        fd = (L(X, qp) - L(X, qm)) / (2 * h)
+        assert abs(fd - dq[p]) <= 2e-5 * max(1.0, abs(dq[p])), (p, fd, dq[p])
+    assert checked >= 10

@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--small", action="store_true", help="a reduced graph (8 keyframes) for profiling")
+    ap.add_argument("--hw", default="384x512", help="image size HxW (smaller sizes keep the graph for profiling)")
+    ap.add_argument("--no-autotune", action="store_true", help="default launch shapes instead of the autotuner's")
     return ap.parse_args()
 
 
@@ -120,7 +122,7 @@ class ClockSampler:
         try:
             self.out = open(os.path.join(ROOT, f".clocks_{os.getpid()}.csv"), "w+")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.out,
+                                          "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.out,
                                          stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -162,14 +164,21 @@ class ClockSampler:
 class Arm:
     """Device-resident inputs and buffers of one launch form."""
 
-    def __init__(self, M, w, dtype, per_edge: bool):
+    def __init__(self, M, w, dtype, per_edge: bool, autotune: bool = False, opts=None):
         self.M, self.w, self.per_edge = M, w, per_edge
         self.P = M.default_params()
         self.wd = w.to_storage(dtype)
         # descriptors in the kernel's chunk-planar layout (a one-off layout change)
         self.Dr = M.chunk_descriptors(self.wd.D_ref)
         self.Dq = M.chunk_descriptors(self.wd.D_qry)
-        self.plan = M.Plan(w.kf_hw.numpy(), w.edges.numpy())
+        self.tuning = None
+        if autotune:
+            from paper_2412_12392_gb300.autotune import autotune as tune
+            wd = self.wd
+            self.tuning = tune(w.kf_hw.numpy(), w.edges.numpy(), None, self.P, wd.X_ref, wd.X_qry, self.Dr, self.Dq,
+                               wd.Q_ref, wd.Q_qry, wd.X_canon, w.T_init.to(wd.X_canon.device))
+            opts = self.tuning["opts"]
+        self.plan = M.Plan(w.kf_hw.numpy(), w.edges.numpy(), opts=opts)
         dev = self.wd.X_canon.device
         self.idx = torch.empty(self.plan.edge_pixels, dtype=torch.int32, device=dev)
         self.q = torch.empty(self.plan.edge_pixels, dtype=dtype, device=dev)
@@ -259,9 +268,10 @@ def run_gpu(args, world, rank, local):
     build.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = make_workload(args, rank, dev)
+    hw = tuple(int(v) for v in args.hw.lower().split("x"))
+    w = make_workload(args, rank, dev, hw=hw)
     dtype = torch.float16 if args.form == "batched" else torch.float32
-    arm = Arm(M, w, dtype, per_edge=(args.form == "plain"))
+    arm = Arm(M, w, dtype, per_edge=(args.form == "plain"), autotune=(args.form == "batched" and not args.no_autotune))
     arm.step()
     torch.cuda.synchronize()
     n_matched = int(((arm.idx >= 0) & (arm.q.float() > arm.P.q_min)).sum())
@@ -305,7 +315,8 @@ def run_gpu(args, world, rank, local):
         "f32/f64-solve", "data": "synthetic (seeded box-room pointmaps, no network or dataset)",
         "config": {"workload": f"{w.name}: {w.N} keyframes, {w.E} directed edges, "
                                f"{int(w.kf_hw[0, 1])}x{int(w.kf_hw[0, 0])}, d={d}, {w.n_gn_iters} GN iters",
-                   "form": args.form, "global_batch": w.E, "seq_len": None, "parallelism": f"replicas x{world}",
+                   "form": args.form, "launch_shapes": arm.plan.opts, "global_batch": w.E, "seq_len": None,
+                   "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (per-step edge pools of several GB)"},
         "matches_per_s": tot_query / (stats["match_ms"] * 1e-3) if stats else None,
         "gn_iters_per_s_gn_only": tot_matched * arm.iters / (((stats["lin_ms"] + stats["solve_ms"]) * arm.iters
@@ -319,7 +330,7 @@ def run_gpu(args, world, rank, local):
     return out, arm, w
 
 
-def e2e_measure(args, M, w, dtype, world, rank, local):
+def e2e_measure(args, M, w, dtype, world, rank, local, opts=None):
     """Same metric through the public API with host (pinned) inputs copied in
     and the poses copied out inside the timed region."""
     dev = torch.device("cuda", local)
@@ -329,7 +340,7 @@ def e2e_measure(args, M, w, dtype, world, rank, local):
     host = {k: (M.chunk_descriptors(getattr(wh, k)) if k.startswith("D_") else getattr(wh, k)).pin_memory()
             for k in names}
     T_host = w.T_init.cpu().pin_memory()
-    arm = Arm(M, w, dtype, per_edge=False)
+    arm = Arm(M, w, dtype, per_edge=False, opts=opts)
     dbuf = {k: getattr(arm.wd, k) for k in names}
     dbuf["D_ref"], dbuf["D_qry"] = arm.Dr, arm.Dq
     T_out = torch.empty_like(T_host).pin_memory()
@@ -480,7 +491,10 @@ def main():
             "speedup_of_batched": pms / out["ms_per_step"]}
         del plain
     if not args.no_e2e:
-        out["e2e"] = e2e_measure(args, M, w, arm.wd.X_canon.dtype, world, rank, local)
+        out["e2e"] = e2e_measure(args, M, w, arm.wd.X_canon.dtype, world, rank, local, opts=arm.plan.opts)
+    if arm.tuning is not None:
+        out["autotune"] = {"opts": arm.tuning["opts"], "match_ms": arm.tuning["match_ms"],
+                           "lin_ms": arm.tuning["lin_ms"]}
     if rank == 0 and not args.no_cpu:
         wc = w.to_storage(arm.wd.X_canon.dtype).to("cpu")
         out["cpu_baseline"] = cpu_baseline(wc, args.cpu_seconds, out["matched_pixels"], out["query_pixels"],

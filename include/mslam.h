@@ -116,6 +116,27 @@ mslam_status mslam_plan_create(int32_t N, const int32_t* kf_hw, int32_t E, const
                                const int32_t* graph_of_kf, mslam_plan** out);
 void mslam_plan_destroy(mslam_plan* plan);
 
+/* Launch-shape options of a plan (no effect on results beyond FP32
+ * summation order), chosen by the caller or an autotuner:
+ *   lin_tile           pixels per linearisation work tile: a multiple of 256
+ *                      in [1024, 65536] (default 8192)
+ *   lin_blocks_per_sm  resident blocks per SM of the persistent
+ *                      linearisation launches, 1..32, or 0 for the
+ *                      occupancy maximum (default 0)
+ *   match_block_w      width of a 256-pixel match block: 16, 32, 64, 128 or
+ *                      256 (default 32, i.e. 32 x 8 pixels)
+ * mslam_plan_create uses the defaults; mslam_plan_create_ex takes options
+ * (NULL = defaults).  Errors: MSLAM_ERR_ARG for an option out of range. */
+typedef struct {
+  int32_t lin_tile;
+  int32_t lin_blocks_per_sm;
+  int32_t match_block_w;
+  int32_t reserved; /* set to 0 */
+} mslam_plan_opts;
+void mslam_default_plan_opts(mslam_plan_opts* opts);
+mslam_status mslam_plan_create_ex(int32_t N, const int32_t* kf_hw, int32_t E, const int32_t* edges,
+                                  const int32_t* graph_of_kf, const mslam_plan_opts* opts, mslam_plan** out);
+
 /* Bytes of device memory the plan's tables need, and their upload into a
  * caller-owned device buffer `dev` (>= 256-byte aligned) on `stream`.  The
  * buffer must outlive every call that uses the plan.  The host staging copy

@@ -39,6 +39,12 @@ class Params(C.Structure):
     ]
 
 
+class PlanOpts(C.Structure):
+    """Mirror of mslam_plan_opts."""
+    _fields_ = [("lin_tile", C.c_int32), ("lin_blocks_per_sm", C.c_int32), ("match_block_w", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
 class MslamError(RuntimeError):
     def __init__(self, status: int, what: str):
         super().__init__(f"{what}: {STATUS_NAMES.get(status, status)}: {last_error()}")
@@ -60,6 +66,8 @@ SIGNATURES = {
     "mslam_version": ([], C.c_char_p),
     "mslam_plan_create": ([i32, vp, i32, vp, vp, C.POINTER(vp)], C.c_int),
     "mslam_plan_destroy": ([vp], None),
+    "mslam_default_plan_opts": ([C.POINTER(PlanOpts)], None),
+    "mslam_plan_create_ex": ([i32, vp, i32, vp, vp, C.POINTER(PlanOpts), C.POINTER(vp)], C.c_int),
     "mslam_plan_device_bytes": ([vp], sz),
     "mslam_plan_upload": ([vp, vp, sz, vp], C.c_int),
     "mslam_plan_kf_pixels": ([vp], i64),

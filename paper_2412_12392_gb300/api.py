@@ -15,7 +15,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import Params, check, lib
+from ._lib import Params, PlanOpts, check, lib
 
 DTYPES = {torch.float32: _lib.MSLAM_F32, torch.float16: _lib.MSLAM_F16}
 
@@ -65,14 +65,21 @@ class Plan:
     """mslam_plan: the static structure of one or more keyframe graphs,
     uploaded to a torch-owned device buffer."""
 
-    def __init__(self, kf_hw, edges, graph_of_kf=None, device="cuda"):
+    def __init__(self, kf_hw, edges, graph_of_kf=None, device="cuda", opts: Optional[dict] = None):
         kf = np.ascontiguousarray(np.asarray(kf_hw, dtype=np.int32).reshape(-1, 2))
         ed = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
         gk = None if graph_of_kf is None else np.ascontiguousarray(np.asarray(graph_of_kf, dtype=np.int32))
         self.N, self.E = kf.shape[0], ed.shape[0]
+        o = PlanOpts()
+        lib().mslam_default_plan_opts(C.byref(o))
+        for k, v in (opts or {}).items():
+            setattr(o, k, int(v))
+        self.opts = {k: getattr(o, k) for k in ("lin_tile", "lin_blocks_per_sm", "match_block_w")}
+        self.graph_of_kf = gk
         h = C.c_void_p()
-        check(lib().mslam_plan_create(self.N, kf.ctypes.data, self.E, ed.ctypes.data if self.E else None,
-                                      gk.ctypes.data if gk is not None else None, C.byref(h)), "mslam_plan_create")
+        check(lib().mslam_plan_create_ex(self.N, kf.ctypes.data, self.E, ed.ctypes.data if self.E else None,
+                                         gk.ctypes.data if gk is not None else None, C.byref(o), C.byref(h)),
+              "mslam_plan_create_ex")
         self._h = h
         self.kf_hw, self.edges = kf, ed
         self.kf_pixels = int(lib().mslam_plan_kf_pixels(h))

@@ -1,0 +1,69 @@
+"""Autotuner for the plan's launch shapes (spec: tile and pixels-per-
+thread choices made by the project's own tuner).
+
+Each candidate is timed on the caller's device-resident inputs with CUDA
+events -- the match block shape on mslam_match, the linearisation tile size
+and persistent-grid blocks per SM on mslam_gn_pack + mslam_gn_linearize_packed
+-- and the fastest of each stage is kept.  Results are identical for every
+shape up to FP32 summation order.
+"""
+from __future__ import annotations
+
+import itertools
+from typing import Dict, Optional, Sequence
+
+import torch
+
+from . import api
+
+MATCH_WIDTHS = (16, 32, 64, 128)
+LIN_TILES = (4096, 8192, 16384)
+LIN_BLOCKS = (0, 2, 3, 4)
+
+
+def _time(fn, reps: int) -> float:
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def autotune(kf_hw, edges, graph_of_kf, params, X_ref, X_qry, D_ref, D_qry, Q_ref, Q_qry, X_canon, T_wc,
+             match_widths: Sequence[int] = MATCH_WIDTHS, lin_tiles: Sequence[int] = LIN_TILES,
+             lin_blocks: Sequence[int] = LIN_BLOCKS, reps: int = 3) -> Dict:
+    """Returns {"opts": best plan options, "match_ms": {...}, "lin_ms": {...}}.
+    D_ref / D_qry are chunk-planar (api.chunk_descriptors)."""
+    report = {"match_ms": {}, "lin_ms": {}}
+    best_w, best_t = None, float("inf")
+    idx = q = None
+    for wdt in match_widths:
+        plan = api.Plan(kf_hw, edges, graph_of_kf, opts={"match_block_w": wdt})
+
+        def run_match():
+            return api.match(plan, params, X_ref, X_qry, D_ref, D_qry, Q_ref, Q_qry)
+
+        ms = _time(run_match, reps)
+        report["match_ms"][wdt] = ms
+        if ms < best_t:
+            best_w, best_t = wdt, ms
+    idx, q = api.match(api.Plan(kf_hw, edges, graph_of_kf), params, X_ref, X_qry, D_ref, D_qry, Q_ref, Q_qry)
+    best_lin, best_lt = None, float("inf")
+    for tile, bps in itertools.product(lin_tiles, lin_blocks):
+        plan = api.Plan(kf_hw, edges, graph_of_kf, opts={"lin_tile": tile, "lin_blocks_per_sm": bps})
+        packed = api.gn_pack(plan, params, X_canon, idx, q)
+        ws = plan.workspace(api._lib.MSLAM_OP_LINEARIZE)
+
+        def run_lin():
+            api.gn_linearize_packed(plan, params, X_canon.dtype, T_wc, packed, workspace=ws)
+
+        ms = _time(run_lin, reps)
+        report["lin_ms"][f"{tile}/{bps}"] = ms
+        if ms < best_lt:
+            best_lin, best_lt = (tile, bps), ms
+    report["opts"] = {"match_block_w": best_w, "lin_tile": best_lin[0], "lin_blocks_per_sm": best_lin[1]}
+    return report

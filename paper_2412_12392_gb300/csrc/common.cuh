@@ -14,12 +14,12 @@ namespace mslam {
 #ifndef MSLAM_LIN_TILE
 #define MSLAM_LIN_TILE 8192
 #endif
-constexpr int kLinTile = MSLAM_LIN_TILE;  // pixels per linearisation work tile
+constexpr int kLinTile = MSLAM_LIN_TILE;  // default pixels per linearisation work tile
 constexpr int kLinThreads = 256;     // threads per linearisation block
 constexpr int kNumAcc = 30;          // accumulators of the relative 7x7 system
 constexpr int kAccStride = 32;       // floats per tile partial in the workspace
-constexpr int kMatchBX = 32;         // match block: 32 x 8 query pixels
-constexpr int kMatchBY = 8;
+constexpr int kMatchThreads = 256;   // match block: 256 query pixels (default 32 x 8)
+constexpr int kMatchBX = 32;
 constexpr int kSolveThreads = 512;
 
 // One directed edge as seen by the kernels.
@@ -74,6 +74,8 @@ struct DevGraph {
 struct PlanView {
   int32_t N, E, G, n_tiles, n_mblocks;
   int64_t P;  // pixels of the edge pools
+  int32_t lin_tile;           // pixels per linearisation tile
+  int32_t match_bx, match_by; // match block shape (match_bx * match_by = 256)
   const DevEdge* edges;
   const DevTile* tiles;
   const DevGraph* graphs;
@@ -300,7 +302,9 @@ inline size_t lin_partials_bytes(int n_tiles) {
   return ((sizeof(float) * kAccStride * (size_t)(n_tiles > 0 ? n_tiles : 1)) + 255) & ~size_t(255);
 }
 // Packed-match buffer size (records of every tile, then per-tile counts).
-size_t pack_bytes(int n_tiles, mslam_dtype dt);
+size_t pack_bytes(int n_tiles, int lin_tile, mslam_dtype dt);
+// Persistent-grid size of the linearisation launches (0 = occupancy maximum).
+int plan_lin_blocks_per_sm(const mslam_plan* plan);
 // Host-side per-edge ranges: linearisation tiles [t0, t1), match blocks [b0, b1).
 void plan_edge_tiles(const mslam_plan* plan, int e, int* t0, int* t1);
 void plan_edge_mblocks(const mslam_plan* plan, int e, int* b0, int* b1);

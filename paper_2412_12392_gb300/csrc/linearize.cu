@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(kLinThreads) pack_kernel(PlanView pv, float q_
     const T* q_e = q + ed.off_e;
     const T* Xj = X + 3 * ed.off_j;
     const T* Xi = X + 3 * ed.off_i;
-    uint4* out = recs + (size_t)tile * kLinTile * W;
+    uint4* out = recs + (size_t)tile * pv.lin_tile * W;
     int base_count = 0;
     for (int base = tl.begin; base < tl.end; base += kLinThreads) {
       const int n = base + tid;
@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(kLinThreads, MSLAM_PACKED_MINBLOCKS) lin_packe
 #pragma unroll
     for (int a = 0; a < kNumAcc; ++a) acc[a] = 0.0f;
     const int cnt = __ldg(counts + tile);
-    const uint4* in = recs + (size_t)tile * kLinTile * W;
+    const uint4* in = recs + (size_t)tile * pv.lin_tile * W;
     for (int r0 = tid; r0 < cnt; r0 += U * kLinThreads) {
       float3 xj[U], yy[U];
       float qq[U];
@@ -451,16 +451,17 @@ __global__ void __launch_bounds__(64) lin_finalize_kernel(PlanView pv, const dou
   }
 }
 
-static int lin_grid_blocks() {
-  static int cached = 0;
-  if (!cached) {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, lin_tiles_kernel<float>, kLinThreads, 0);
-    cached = std::max(1, sms) * std::max(1, per);
-  }
-  return cached;
+// Blocks of a persistent linearisation launch: the plan's blocks per SM, or
+// the occupancy maximum of the kernel.
+template <typename K>
+static int persistent_grid(const mslam_plan* plan, K kernel) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kLinThreads, 0);
+  const int want = plan_lin_blocks_per_sm(plan);
+  if (want > 0) per = std::min(std::max(per, 1), want);
+  return std::max(1, sms) * std::max(1, per);
 }
 
 }  // namespace mslam
@@ -522,7 +523,7 @@ extern "C" mslam_status mslam_gn_linearize(const mslam_params* p, const mslam_pl
       lin_finalize_kernel<<<1, 64, 0, s>>>(pv, T_wc, partials, H_blocks, g_blocks, cost, n_valid, e);
     }
   } else {
-    const int grid = std::min(pv.n_tiles, lin_grid_blocks());
+    const int grid = std::min(pv.n_tiles, persistent_grid(plan, lin_tiles_kernel<float>));
     if (dt == MSLAM_F32)
       lin_tiles_kernel<float><<<grid, kLinThreads, 0, s>>>(pv, lc, rel, static_cast<const float*>(X_canon), idx,
                                                           static_cast<const float*>(q), partials, 0, pv.n_tiles);
@@ -538,8 +539,8 @@ extern "C" mslam_status mslam_gn_linearize(const mslam_params* p, const mslam_pl
 static size_t pack_record_bytes(mslam_dtype dt) { return dt == MSLAM_F16 ? 16 : 32; }
 
 namespace mslam {
-size_t pack_bytes(int n_tiles, mslam_dtype dt) {
-  const size_t recs = ((size_t)(n_tiles > 0 ? n_tiles : 1) * kLinTile * pack_record_bytes(dt) + 255) & ~size_t(255);
+size_t pack_bytes(int n_tiles, int lin_tile, mslam_dtype dt) {
+  const size_t recs = ((size_t)(n_tiles > 0 ? n_tiles : 1) * lin_tile * pack_record_bytes(dt) + 255) & ~size_t(255);
   const size_t cnts = ((size_t)(n_tiles > 0 ? n_tiles : 1) * sizeof(int32_t) + 255) & ~size_t(255);
   return recs + cnts;
 }
@@ -562,13 +563,13 @@ extern "C" mslam_status mslam_gn_pack(const mslam_params* p, const mslam_plan* p
     set_error("gn_pack: NULL device pointer");
     return MSLAM_ERR_ARG;
   }
-  if (packed_bytes < pack_bytes(pv.n_tiles, dt) || (reinterpret_cast<uintptr_t>(packed) & 255)) {
-    set_error("gn_pack: packed buffer smaller than %zu bytes or not 256-byte aligned", pack_bytes(pv.n_tiles, dt));
+  if (packed_bytes < pack_bytes(pv.n_tiles, pv.lin_tile, dt) || (reinterpret_cast<uintptr_t>(packed) & 255)) {
+    set_error("gn_pack: packed buffer smaller than %zu bytes or not 256-byte aligned", pack_bytes(pv.n_tiles, pv.lin_tile, dt));
     return MSLAM_ERR_ARG;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   uint4* recs = static_cast<uint4*>(packed);
-  int32_t* counts = reinterpret_cast<int32_t*>(static_cast<char*>(packed) + pack_bytes(pv.n_tiles, dt) -
+  int32_t* counts = reinterpret_cast<int32_t*>(static_cast<char*>(packed) + pack_bytes(pv.n_tiles, pv.lin_tile, dt) -
                                                (((size_t)pv.n_tiles * sizeof(int32_t) + 255) & ~size_t(255)));
   if (dt == MSLAM_F32)
     pack_kernel<float><<<pv.n_tiles, kLinThreads, 0, s>>>(pv, p->q_min, static_cast<const float*>(X_canon), idx,
@@ -597,9 +598,9 @@ extern "C" mslam_status mslam_gn_linearize_packed(const mslam_params* p, const m
     set_error("gn_linearize_packed: NULL device pointer");
     return MSLAM_ERR_ARG;
   }
-  if (packed_bytes < pack_bytes(pv.n_tiles, dt) || (reinterpret_cast<uintptr_t>(packed) & 255)) {
+  if (packed_bytes < pack_bytes(pv.n_tiles, pv.lin_tile, dt) || (reinterpret_cast<uintptr_t>(packed) & 255)) {
     set_error("gn_linearize_packed: packed buffer smaller than %zu bytes or not 256-byte aligned",
-              pack_bytes(pv.n_tiles, dt));
+              pack_bytes(pv.n_tiles, pv.lin_tile, dt));
     return MSLAM_ERR_ARG;
   }
   if (ws_bytes < mslam_workspace_bytes(plan, MSLAM_OP_LINEARIZE) ||
@@ -623,7 +624,7 @@ extern "C" mslam_status mslam_gn_linearize_packed(const mslam_params* p, const m
   RelPose* rel = reinterpret_cast<RelPose*>(static_cast<char*>(workspace) + lin_partials_bytes(pv.n_tiles));
   const uint4* recs = static_cast<const uint4*>(packed);
   const int32_t* counts = reinterpret_cast<const int32_t*>(
-      static_cast<const char*>(packed) + pack_bytes(pv.n_tiles, dt) -
+      static_cast<const char*>(packed) + pack_bytes(pv.n_tiles, pv.lin_tile, dt) -
       (((size_t)pv.n_tiles * sizeof(int32_t) + 255) & ~size_t(255)));
   rel_pose_kernel<<<(pv.E + 127) / 128, 128, 0, s>>>(pv, T_wc, rel);
   auto launch = [&](int grid, int t0, int t1) {
@@ -640,15 +641,7 @@ extern "C" mslam_status mslam_gn_linearize_packed(const mslam_params* p, const m
       lin_finalize_kernel<<<1, 64, 0, s>>>(pv, T_wc, partials, H_blocks, g_blocks, cost, n_valid, e);
     }
   } else {
-    static int cached = 0;
-    if (!cached) {
-      int dev = 0, sms = 0, per = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, lin_packed_kernel<__half>, kLinThreads, 0);
-      cached = std::max(1, sms) * std::max(1, per);
-    }
-    launch(std::min(pv.n_tiles, cached), 0, pv.n_tiles);
+    launch(std::min(pv.n_tiles, persistent_grid(plan, lin_packed_kernel<__half>)), 0, pv.n_tiles);
     lin_finalize_kernel<<<pv.E, 64, 0, s>>>(pv, T_wc, partials, H_blocks, g_blocks, cost, n_valid, 0);
   }
   return cuda_check(cudaGetLastError(), "gn_linearize_packed launch");

@@ -1,6 +1,7 @@
 // (a1-a3) Iterative projective matching with feature refinement, Sec. 3.2.
 //
-// One thread per query pixel, blocks of 32 x 8 query pixels so that a
+// One thread per query pixel, blocks of 256 query pixels (32 x 8 by default,
+// a plan option) so that a
 // block's bilinear taps and refinement windows fall in a compact region of
 // the reference image (served from L1/L2).  Per pixel:
 //   a1  the reference camera model psi(X_ref) is evaluated at the four
@@ -98,7 +99,7 @@ template <int D> struct Desc<__half, D> {
 };
 
 template <typename T, int D>
-__global__ void __launch_bounds__(kMatchBX* kMatchBY) match_kernel(
+__global__ void __launch_bounds__(kMatchThreads) match_kernel(
     PlanView pv, MatchConst mc, const T* __restrict__ Xr, const T* __restrict__ Xq, const T* __restrict__ Dr,
     const T* __restrict__ Dq, const T* __restrict__ Qr, const T* __restrict__ Qq, const int32_t* __restrict__ init,
     int32_t* __restrict__ out_idx, T* __restrict__ out_q, int e_begin, int e_end, int block_base) {
@@ -113,9 +114,10 @@ __global__ void __launch_bounds__(kMatchBX* kMatchBY) match_kernel(
   const DevEdge ed = pv.edges[lo];
   const int W = ed.W, H = ed.H;
   const int local = gb - ed.mblock_begin;
-  const int nbx = (W + kMatchBX - 1) / kMatchBX;
-  const int u = (local % nbx) * kMatchBX + (threadIdx.x % kMatchBX);
-  const int v = (local / nbx) * kMatchBY + (threadIdx.x / kMatchBX);
+  const int bx = pv.match_bx, by = pv.match_by;
+  const int nbx = (W + bx - 1) / bx;
+  const int u = (local % nbx) * bx + (threadIdx.x % bx);
+  const int v = (local / nbx) * by + (threadIdx.x / bx);
   if (u >= W || v >= H) return;
   const int64_t HW = (int64_t)H * W;
   const int n = v * W + u;
@@ -206,7 +208,7 @@ template <typename T, int D>
 static void launch_match(const PlanView& pv, const MatchConst& mc, const void* Xr, const void* Xq, const void* Dr,
                          const void* Dq, const void* Qr, const void* Qq, const int32_t* init, int32_t* out_idx,
                          void* out_q, int e0, int e1, int b0, int nblocks, cudaStream_t s) {
-  match_kernel<T, D><<<nblocks, kMatchBX * kMatchBY, 0, s>>>(
+  match_kernel<T, D><<<nblocks, kMatchThreads, 0, s>>>(
       pv, mc, static_cast<const T*>(Xr), static_cast<const T*>(Xq), static_cast<const T*>(Dr),
       static_cast<const T*>(Dq), static_cast<const T*>(Qr), static_cast<const T*>(Qq), init, out_idx,
       static_cast<T*>(out_q), e0, e1, b0);

@@ -23,6 +23,7 @@ struct mslam_plan {
   std::vector<int32_t> order;
   int64_t n_blocks_total = 0, n_trips_total = 0, solve_ws_doubles = 0, max_graph_doubles = 0;
   int32_t max_levels = 0;
+  int32_t lin_tile = 0, lin_blocks_per_sm = 0, match_bx = 0, match_by = 0;
   int32_t n_mblocks = 0;
   void* dev = nullptr;
   size_t dev_bytes = 0;
@@ -67,6 +68,9 @@ PlanView plan_view(const mslam_plan* plan) {
   v.n_tiles = (int32_t)plan->tiles.size();
   v.n_mblocks = plan->n_mblocks;
   v.P = plan->e_off.back();
+  v.lin_tile = plan->lin_tile;
+  v.match_bx = plan->match_bx;
+  v.match_by = plan->match_by;
   v.edges = reinterpret_cast<const DevEdge*>(base + plan->off_edges);
   v.tiles = reinterpret_cast<const DevTile*>(base + plan->off_tiles);
   v.graphs = reinterpret_cast<const DevGraph*>(base + plan->off_graphs);
@@ -85,6 +89,7 @@ void plan_edge_mblocks(const mslam_plan* plan, int e, int* b0, int* b1) {
 }
 
 int64_t plan_max_graph_doubles(const mslam_plan* plan) { return plan->max_graph_doubles; }
+int plan_lin_blocks_per_sm(const mslam_plan* plan) { return plan->lin_blocks_per_sm; }
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -356,8 +361,33 @@ const char* mslam_last_error(void) { return g_err; }
 
 const char* mslam_version(void) { return "mslam-gb300 0.1 (sm_103a)"; }
 
+void mslam_default_plan_opts(mslam_plan_opts* o) {
+  if (!o) return;
+  o->lin_tile = kLinTile;
+  o->lin_blocks_per_sm = 0;
+  o->match_block_w = kMatchBX;
+  o->reserved = 0;
+}
+
 mslam_status mslam_plan_create(int32_t N, const int32_t* kf_hw, int32_t E, const int32_t* edges,
                                const int32_t* graph_of_kf, mslam_plan** out) {
+  return mslam_plan_create_ex(N, kf_hw, E, edges, graph_of_kf, nullptr, out);
+}
+
+mslam_status mslam_plan_create_ex(int32_t N, const int32_t* kf_hw, int32_t E, const int32_t* edges,
+                                  const int32_t* graph_of_kf, const mslam_plan_opts* opts, mslam_plan** out) {
+  mslam_plan_opts o;
+  mslam_default_plan_opts(&o);
+  if (opts) o = *opts;
+  if (o.lin_tile < 1024 || o.lin_tile > 65536 || (o.lin_tile % kLinThreads) != 0 || o.lin_blocks_per_sm < 0 ||
+      o.lin_blocks_per_sm > 32 || (o.match_block_w != 16 && o.match_block_w != 32 && o.match_block_w != 64 &&
+                                   o.match_block_w != 128 && o.match_block_w != 256)) {
+    set_error("plan options: lin_tile %d (multiple of %d in [1024, 65536]), lin_blocks_per_sm %d (0..32), "
+              "match_block_w %d (16, 32, 64, 128 or 256)", o.lin_tile, kLinThreads, o.lin_blocks_per_sm,
+              o.match_block_w);
+    if (out) *out = nullptr;
+    return MSLAM_ERR_ARG;
+  }
   if (!out) {
     set_error("out is NULL");
     return MSLAM_ERR_ARG;
@@ -368,6 +398,10 @@ mslam_status mslam_plan_create(int32_t N, const int32_t* kf_hw, int32_t E, const
     return MSLAM_ERR_ARG;
   }
   mslam_plan* P = new mslam_plan();
+  P->lin_tile = o.lin_tile;
+  P->lin_blocks_per_sm = o.lin_blocks_per_sm;
+  P->match_bx = o.match_block_w;
+  P->match_by = kMatchThreads / o.match_block_w;
   P->N = N;
   P->E = E;
   P->kf_hw.assign(kf_hw, kf_hw + 2 * N);
@@ -416,16 +450,16 @@ mslam_status mslam_plan_create(int32_t N, const int32_t* kf_hw, int32_t E, const
     d.off_j = P->kf_off[j];
     d.graph = P->graph_of_kf[i];
     d.tile_begin = (int32_t)P->tiles.size();
-    for (int b = 0; b < H * W; b += kLinTile) {
+    for (int b = 0; b < H * W; b += P->lin_tile) {
       DevTile t{};
       t.edge = e;
       t.begin = b;
-      t.end = std::min(H * W, b + kLinTile);
+      t.end = std::min(H * W, b + P->lin_tile);
       P->tiles.push_back(t);
     }
     d.tile_end = (int32_t)P->tiles.size();
     d.mblock_begin = P->n_mblocks;
-    P->n_mblocks += ((W + kMatchBX - 1) / kMatchBX) * ((H + kMatchBY - 1) / kMatchBY);
+    P->n_mblocks += ((W + P->match_bx - 1) / P->match_bx) * ((H + P->match_by - 1) / P->match_by);
     P->dedges.push_back(d);
   }
   P->order.assign(N, -1);
@@ -500,9 +534,9 @@ size_t mslam_workspace_bytes(const mslam_plan* plan, int32_t op) {
     case MSLAM_OP_SOLVE:
       return align256(sizeof(double) * std::max<int64_t>(plan->solve_ws_doubles, 1));
     case MSLAM_OP_PACK_F32:
-      return pack_bytes((int)plan->tiles.size(), MSLAM_F32);
+      return pack_bytes((int)plan->tiles.size(), plan->lin_tile, MSLAM_F32);
     case MSLAM_OP_PACK_F16:
-      return pack_bytes((int)plan->tiles.size(), MSLAM_F16);
+      return pack_bytes((int)plan->tiles.size(), plan->lin_tile, MSLAM_F16);
     case MSLAM_OP_BACKWARD:
       return align256(sizeof(double) * std::max<int64_t>(plan->solve_ws_doubles, 1)) +
              align256(sizeof(double) * 7 * (size_t)plan->N) * 2;

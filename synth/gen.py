@@ -598,3 +598,37 @@ def batched(device="cpu", scale: int = 1) -> List[Workload]:
 def differentiation(device="cpu", seed: int = 3, H: int = 384, W: int = 512) -> Workload:
     """32 keyframes, 96 directed edges at 512 x 384, log-normal confidences."""
     return global_graph(device, seed, 32, 48, H, W, name="diff")
+
+
+def merge(workloads: List[Workload], name: str = "merged") -> Workload:
+    """Concatenate independent graphs into one set of pools: keyframes and
+    edges are renumbered, graph_of_kf records each keyframe's graph, and the
+    pools are concatenated in order (pool layout only; no arithmetic)."""
+    kf_hw, edges, gof, T_gt, T_init = [], [], [], [], []
+    pools = {k: [] for k in ("X_canon", "C_canon", "X_ref", "X_qry", "D_ref", "D_qry", "Q_ref", "Q_qry", "gt_match")}
+    kf_base = 0
+    for g, w in enumerate(workloads):
+        kf_hw.append(w.kf_hw)
+        edges.append(w.edges + kf_base)
+        gof.append(torch.full((w.N,), g, dtype=torch.int32))
+        T_gt.append(w.T_gt)
+        T_init.append(w.T_init)
+        for k in pools:
+            pools[k].append(getattr(w, k))
+        kf_base += w.N
+    kf_hw = torch.cat(kf_hw)
+    edges = torch.cat(edges)
+    N, E = kf_hw.shape[0], edges.shape[0]
+    sizes = (kf_hw[:, 0].to(torch.int64) * kf_hw[:, 1].to(torch.int64))
+    kf_off = torch.zeros(N + 1, dtype=torch.int64)
+    kf_off[1:] = torch.cumsum(sizes, 0)
+    esz = sizes[edges[:, 1].to(torch.int64)]
+    e_off = torch.zeros(E + 1, dtype=torch.int64)
+    e_off[1:] = torch.cumsum(esz, 0)
+    d = workloads[0].d
+    return Workload(name=name, N=N, E=E, d=d, kf_hw=kf_hw, edges=edges, graph_of_kf=torch.cat(gof), kf_off=kf_off,
+                    e_off=e_off, T_gt=torch.cat(T_gt), T_init=torch.cat(T_init),
+                    **{k: torch.cat(v) for k, v in pools.items()},
+                    n_match_iters=workloads[0].n_match_iters, n_gn_iters=workloads[0].n_gn_iters,
+                    meta=dict(graphs=[w.name for w in workloads], graph_kf=[w.N for w in workloads],
+                              graph_edges=[w.E for w in workloads]))

@@ -1,0 +1,141 @@
+"""Parity at the benchmark's full sizes and in its launch configuration.
+
+* tracking (one frame against one keyframe, 512 x 384, radial camera, FP16
+  storage, 10 % occluded query pixels): every pixel's match and the poses
+  after 20 Gauss-Newton iterations against the oracle;
+* global graph (64 keyframes, 256 directed edges, 512 x 384, FP16 storage):
+  the batched matching launch on sampled query pixels of sampled edges, and
+  the packed linearisation of sampled edges (fed the oracle's own matches),
+  against the oracle computed one edge at a time;
+* the 64-keyframe graph's solve (same plan structure as the benchmark) on
+  oracle blocks.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from parity import BLOCK_RTOL, MATCH_AGREE, assert_poses_close, block_rel_err, f64, match_agreement
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    assert torch.cuda.is_available()
+    from paper_2412_12392_gb300 import build
+    build.build()
+    import paper_2412_12392_gb300 as M
+    return M
+
+
+def test_tracking_full_size(M):
+    w = synth.tracking().to_storage(torch.float16)
+    wd = w.to("cuda")
+    P = M.default_params()
+    par = M.params_dict(P)
+    plan = M.Plan(w.kf_hw.numpy(), w.edges.numpy())
+    idx_g, q_g = M.match(plan, P, wd.X_ref, wd.X_qry, M.chunk_descriptors(wd.D_ref), M.chunk_descriptors(wd.D_qry),
+                         wd.Q_ref, wd.Q_qry)
+    gn = M.GaussNewton(plan, P, wd.X_canon, idx_g, q_g, packed=True)
+    T_g = gn.run(w.T_init.cuda(), w.n_gn_iters).cpu()
+    idx_r, q_r, dg = oracle.match_workload(w, 0, diag=True, **par)
+    agree, ndis, nunion, expl = match_agreement(idx_g, idx_r, dg, par)
+    print(f"tracking match: agree {agree:.6f} ({ndis} of {nunion}), explained {expl:.3f}")
+    assert agree >= MATCH_AGREE
+    occ = w.meta["occluded"].numpy()
+    assert (idx_g.cpu().numpy()[occ] == -1).mean() >= 0.99
+    q16 = torch.from_numpy(q_r).to(torch.float16)
+    st, T_r, hist, done = oracle.gauss_newton(w.N, w.edges.numpy(), w.kf_off.numpy(), w.e_off.numpy(), w.X_canon,
+                                              idx_r, q16, w.T_init.numpy(), w.n_gn_iters, **par)
+    assert st == 0
+    e = assert_poses_close(T_g, T_r)
+    print(f"tracking poses vs oracle (rot, trans, scale): {e.max(axis=0)}")
+
+
+@pytest.fixture(scope="module")
+def global_wl():
+    return synth.global_graph(device="cuda").to_storage(torch.float16)
+
+
+def test_global_full_size_sampled(M, global_wl):
+    w = global_wl
+    P = M.default_params()
+    par = M.params_dict(P)
+    plan = M.Plan(w.kf_hw.numpy(), w.edges.numpy())
+    Dr, Dq = M.chunk_descriptors(w.D_ref), M.chunk_descriptors(w.D_qry)
+    idx_g, q_g = M.match(plan, P, w.X_ref, w.X_qry, Dr, Dq, w.Q_ref, w.Q_qry)  # batched launch
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(0)
+    match_edges = rng.choice(w.E, 12, replace=False)
+    edges = match_edges[:4]
+    H, W = int(w.kf_hw[0, 0]), int(w.kf_hw[0, 1])
+    idx_sub, q_sub = idx_g.clone(), q_g.clone()
+    tot_dis, tot_union, tot_expl = 0, 0, 0.0
+    for e in match_edges:
+        sl = w.edge_slice(int(e))
+        cpu = {k: getattr(w, k)[sl].cpu() for k in ("X_ref", "X_qry", "D_ref", "D_qry", "Q_ref", "Q_qry")}
+        pix = np.sort(rng.choice(H * W, 16384, replace=False))
+        idx_r, q_r, dg = oracle.match(H, W, cpu["X_ref"], cpu["X_qry"], cpu["D_ref"], cpu["D_qry"], cpu["Q_ref"],
+                                      cpu["Q_qry"], pix=pix, diag=True, **par)
+        agree, ndis, nunion, expl = match_agreement(idx_g[sl].cpu().numpy()[pix], idx_r, dg, par)
+        print(f"edge {e}: agree {agree:.5f} ({ndis} of {nunion}) explained {expl:.3f}")
+        tot_dis += ndis
+        tot_union += nunion
+        tot_expl += expl * ndis
+        if e in edges:
+            # the oracle's matches of the whole edge feed both linearisations
+            idx_full, q_full = oracle.match(H, W, cpu["X_ref"], cpu["X_qry"], cpu["D_ref"], cpu["D_qry"],
+                                            cpu["Q_ref"], cpu["Q_qry"], **par)
+            idx_sub[sl] = torch.from_numpy(idx_full).cuda()
+            q_sub[sl] = torch.from_numpy(q_full).to(torch.float16).cuda()
+    # the bar is on all sampled valid pixels together; every disagreement must
+    # be a near tie of an FP32-versus-FP64 decision
+    print(f"sampled total: agree {1 - tot_dis / tot_union:.6f} ({tot_dis} of {tot_union})")
+    assert 1 - tot_dis / tot_union >= MATCH_AGREE
+    assert tot_dis == 0 or tot_expl / tot_dis >= 0.9
+    packed = M.gn_pack(plan, P, w.X_canon, idx_sub, q_sub)
+    T0 = w.T_init.cuda()
+    Hb, gb, cb, nv = M.gn_linearize_packed(plan, P, torch.float16, T0, packed)
+    torch.cuda.synchronize()
+    Xc = w.X_canon.cpu()
+    for e in edges:
+        i, j = int(w.edges[e, 0]), int(w.edges[e, 1])
+        sl = w.edge_slice(int(e))
+        Hr, gr, cr, nvr = oracle.linearize_edge(w.T_init[i], w.T_init[j], Xc[w.kf_slice(i)], Xc[w.kf_slice(j)],
+                                                idx_sub[sl].cpu(), q_sub[sl].cpu(), **par)
+        eh = block_rel_err(Hb[e:e + 1], Hr[None])[0]
+        eg = block_rel_err(gb[e:e + 1], gr[None])[0]
+        print(f"edge {e}: H rel {eh:.2e}, g rel {eg:.2e}, matches {int(nv[e])}")
+        assert eh <= BLOCK_RTOL and eg <= BLOCK_RTOL and int(nv[e]) == nvr
+
+
+def test_global_graph_solve_structure(M):
+    """The 64-keyframe / 256-edge plan of the benchmark (small images, same
+    graph structure and hence the same symbolic factorisation): the solve on
+    oracle blocks against the oracle's dense solve."""
+    w = synth.global_graph(H=24, W=32)
+    P = M.default_params()
+    par = M.params_dict(P)
+    plan = M.Plan(w.kf_hw.numpy(), w.edges.numpy())
+    Hr, gr = [], []
+    idx = w.gt_match.numpy()
+    q = w.Q_qry.double().numpy()
+    T0 = w.T_init.numpy()
+    for e in range(w.E):
+        i, j = int(w.edges[e, 0]), int(w.edges[e, 1])
+        sl = w.edge_slice(e)
+        Hb, gb, _, _ = oracle.linearize_edge(T0[i], T0[j], w.X_canon[w.kf_slice(i)], w.X_canon[w.kf_slice(j)], idx[sl],
+                                             q[sl], **par)
+        Hr.append(Hb)
+        gr.append(gb)
+    H32, g32 = torch.from_numpy(np.array(Hr)).float(), torch.from_numpy(np.array(gr)).float()
+    T = w.T_init.clone().cuda()
+    tau = torch.zeros(w.N, 7, dtype=torch.float64, device="cuda")
+    tau, st = M.gn_solve(plan, P, H32.cuda(), g32.cuda(), T, tau=tau)
+    torch.cuda.synchronize()
+    s, T_r, tau_r = oracle.gn_solve(w.N, w.edges.numpy(), H32.double(), g32.double(), T0)
+    assert s == 0 and int(st[0]) in (0, 1)
+    assert np.abs(f64(tau) - tau_r).max() <= 1e-8 * max(1.0, np.abs(tau_r).max())
+    assert_poses_close(T, T_r, 1e-8)

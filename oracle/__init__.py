@@ -24,7 +24,10 @@ DEFAULT_PARAMS: Dict = dict(
     sigma_ray=0.01, sigma_dist=0.1, huber_delta=1.345, q_min=1.5,
     lm_lambda=1e-8, lm_iters=10, win_radius=3, n_levels=2, win_dilation=(2, 1, 1, 1),
     max_rel_dist3d=0.1, conv_tol=1e-10,
+    residual=0, sigma_point=0.05, sigma_pixel=1.0, sigma_depth=0.1, fx=0.0, fy=0.0, cx=0.0, cy=0.0, img_w=0,
 )
+
+RES_RAY, RES_POINT, RES_PIXEL = 0, 1, 2
 
 
 class _Params(C.Structure):
@@ -33,6 +36,9 @@ class _Params(C.Structure):
         ("q_min", C.c_double), ("lm_lambda", C.c_double), ("lm_iters", C.c_int),
         ("win_radius", C.c_int), ("n_levels", C.c_int), ("win_dilation", C.c_int * 4),
         ("max_rel_dist3d", C.c_double), ("conv_tol", C.c_double),
+        ("residual", C.c_int), ("sigma_point", C.c_double), ("sigma_pixel", C.c_double),
+        ("sigma_depth", C.c_double), ("fx", C.c_double), ("fy", C.c_double), ("cx", C.c_double),
+        ("cy", C.c_double), ("img_w", C.c_int),
     ]
 
 
@@ -69,6 +75,7 @@ def lib():
             ("orc_match", [pp, C.c_int, C.c_int, C.c_int, dp, dp, dp, dp, dp, dp, ip, lp, C.c_int64, ip, dp, dp],
              None),
             ("orc_residual_jacobian", [dp, dp, dp, dp, dp, dp], C.c_int),
+            ("orc_residual_jacobian_p", [pp, dp, dp, dp, dp, C.c_int32, dp, dp], C.c_int),
             ("orc_linearize_edge", [pp, dp, dp, C.c_int64, dp, dp, ip, dp, dp, dp, dp, lp], None),
             ("orc_gn_solve", [C.c_int, C.c_int, ip, dp, dp, C.c_int, dp, dp], C.c_int),
             ("orc_gauss_newton", [pp, C.c_int, C.c_int, ip, lp, lp, dp, ip, dp, C.c_int, C.c_int, dp, dp,
@@ -76,6 +83,10 @@ def lib():
             ("orc_cost_grad", [pp, C.c_int, C.c_int, ip, lp, lp, dp, dp, ip, dp, dp, dp, dp], None),
             ("orc_gn_step_grad", [pp, C.c_int, C.c_int, ip, lp, lp, dp, dp, ip, dp, dp, C.c_double, dp, dp, dp],
              C.c_int),
+            ("orc_fuse", [dp, C.c_int64, dp, dp, dp, dp], None),
+            ("orc_match_stats", [C.c_int64, C.c_int64, ip, lp, lp], None),
+            ("orc_calib_backproject", [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, dp],
+             None),
             ("orc_num_threads", [], C.c_int),
         ]:
             f = getattr(L, name)
@@ -238,6 +249,17 @@ def residual_jacobian(Ti, Tj, Xj_n, Xi_m):
     return bool(ok), r, J.reshape(4, 14)
 
 
+def residual_jacobian_p(Ti, Tj, Xj_n, Xi_m, m=0, **par):
+    """Any residual family (par["residual"]): (rows, r [rows], J [rows, 14]);
+    rows = 0 for a degenerate match."""
+    Ti, Tj, a, b = _d(Ti).reshape(8), _d(Tj).reshape(8), _d(Xj_n).reshape(3), _d(Xi_m).reshape(3)
+    r = np.zeros(4)
+    J = np.zeros(56)
+    rows = lib().orc_residual_jacobian_p(C.byref(params(**par)), _p(Ti), _p(Tj), _p(a), _p(b), int(m), _p(r),
+                                         _p(J))
+    return rows, r[:rows], J.reshape(4, 14)[:rows]
+
+
 def linearize_edge(Ti, Tj, X_i, X_j, idx, q, **par):
     Ti, Tj = _d(Ti).reshape(8), _d(Tj).reshape(8)
     Xi, Xj = _d(X_i).reshape(-1, 3), _d(X_j).reshape(-1, 3)
@@ -311,5 +333,32 @@ def gn_step_grad(N, edges, kf_off, e_off, T, X_canon, idx, q, dL_dtau=None, dL_d
     return st, dX, dq, tau
 
 
+def fuse(T_kf, X_canon, C_canon, X_kf, C_kf):
+    """Pointmap fusion (Sec. 3.3); returns the updated (X_canon, C_canon)."""
+    T = _d(T_kf).reshape(8)
+    X = _d(X_canon).reshape(-1, 3).copy()
+    Cc = _d(C_canon).reshape(-1).copy()
+    Xk = _d(X_kf).reshape(-1, 3)
+    Ck = _d(C_kf).reshape(-1)
+    lib().orc_fuse(_p(T), X.shape[0], _p(X), _p(Cc), _p(Xk), _p(Ck))
+    return X, Cc
+
+
+def match_stats(idx, n_ref: int):
+    """(valid matches, distinct reference pixels) of one edge (Sec. 3.4)."""
+    idx = _i32(idx).reshape(-1)
+    v = np.zeros(1, dtype=np.int64)
+    u = np.zeros(1, dtype=np.int64)
+    lib().orc_match_stats(idx.shape[0], int(n_ref), _p(idx, C.c_int32), _p(v, C.c_int64), _p(u, C.c_int64))
+    return int(v[0]), int(u[0])
+
+
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def calib_backproject(H, W, fx, fy, cx, cy, X):
+    """Sec. 3.6: keep the depth, rebuild each point on its pixel's pinhole ray."""
+    X = _d(X).reshape(H * W, 3).copy()
+    lib().orc_calib_backproject(H, W, fx, fy, cx, cy, _p(X))
+    return X

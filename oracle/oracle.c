@@ -426,6 +426,69 @@ int orc_residual_jacobian(const double Ti[8], const double Tj[8], const double X
   return residual_jacobian_rel(Tij, Ad, Xj_n, Xi_m, r, J);
 }
 
+/* The other residual families, formed the same literal way: r and dr/dx of
+ * the family, times dx/dtau = [I, -[x]x, x] (Eq. point_jac), times the
+ * global map.  Point family (Supp. S1.1, Eq. track_point in backend
+ * notation): r = T_ij X_j,n - X_i,m, dr/dx = I.  Pixel family with known
+ * pinhole calibration (Sec. 3.6, Supp. S1.3): r = Pi(x) - p_m with
+ * Pi(x) = (fx x/z + cx, fy y/z + cy) and p_m the reference pixel m, plus the
+ * depth residual x_z - (X_i,m)_z that replaces the distance term.  A pixel
+ * residual needs the point in front of the camera: z > 1e-3 |x|.  Returns
+ * the number of rows, or 0 for a degenerate match. */
+static int residual_jacobian_family(const orc_params* P, const double Tij[8], const double Ad[49],
+                                    const double Xj_n[3], const double Xi_m[3], int32_t m, double r[4],
+                                    double J[56]) {
+  if (P->residual == ORC_RES_RAY) return residual_jacobian_rel(Tij, Ad, Xj_n, Xi_m, r, J) ? 4 : 0;
+  double x[3];
+  orc_sim3_act(Tij, Xj_n, x);
+  if (!(finite3(x) && finite3(Xi_m) && norm3(x) > 0.0 && norm3(Xi_m) > 0.0)) return 0;
+  double Dr[9];
+  if (P->residual == ORC_RES_POINT) {
+    for (int c = 0; c < 3; ++c) r[c] = x[c] - Xi_m[c];
+    for (int k = 0; k < 9; ++k) Dr[k] = (k % 4 == 0) ? 1.0 : 0.0;
+  } else if (P->residual == ORC_RES_PIXEL) {
+    const double z = x[2];
+    if (!(z > 1e-3 * norm3(x)) || P->img_w <= 0) return 0;
+    const double u_m = (double)(m % P->img_w), v_m = (double)(m / P->img_w);
+    r[0] = P->fx * x[0] / z + P->cx - u_m;
+    r[1] = P->fy * x[1] / z + P->cy - v_m;
+    r[2] = z - Xi_m[2];
+    /* d Pi / dx = (1/z) [[fx, 0, -fx x/z], [0, fy, -fy y/z]] (Supp. S1.3); d z / dx = e_z^T */
+    Dr[0] = P->fx / z; Dr[1] = 0.0; Dr[2] = -P->fx * x[0] / (z * z);
+    Dr[3] = 0.0; Dr[4] = P->fy / z; Dr[5] = -P->fy * x[1] / (z * z);
+    Dr[6] = 0.0; Dr[7] = 0.0; Dr[8] = 1.0;
+  } else {
+    return 0;
+  }
+  double Dx[21], S[9];
+  skew(x, S);
+  for (int rr = 0; rr < 3; ++rr) {
+    for (int c = 0; c < 3; ++c) {
+      Dx[7 * rr + c] = (rr == c) ? 1.0 : 0.0;
+      Dx[7 * rr + 3 + c] = -S[3 * rr + c];
+    }
+    Dx[7 * rr + 6] = x[rr];
+  }
+  double Jrel[21], JA[21];
+  matmul(Dr, Dx, Jrel, 3, 3, 7);
+  matmul(Jrel, Ad, JA, 3, 7, 7);
+  for (int rr = 0; rr < 3; ++rr)
+    for (int c = 0; c < 7; ++c) {
+      J[14 * rr + c] = -JA[7 * rr + c];
+      J[14 * rr + 7 + c] = JA[7 * rr + c];
+    }
+  return 3;
+}
+
+int orc_residual_jacobian_p(const orc_params* P, const double Ti[8], const double Tj[8], const double Xj_n[3],
+                            const double Xi_m[3], int32_t m, double r[4], double J[56]) {
+  double Tii[8], Tij[8], Ad[49];
+  orc_sim3_inv(Ti, Tii);
+  orc_sim3_mul(Tii, Tj, Tij);
+  orc_sim3_adjoint(Tii, Ad);
+  return residual_jacobian_family(P, Tij, Ad, Xj_n, Xi_m, m, r, J);
+}
+
 /* Huber cost and IRLS weight of a whitened residual norm e */
 static double huber_cost(double e, double delta) { return e <= delta ? 0.5 * e * e : delta * (e - 0.5 * delta); }
 static double huber_weight(double e, double delta) { return e <= delta ? 1.0 : delta / e; }
@@ -448,24 +511,40 @@ void orc_linearize_edge(const orc_params* P, const double Ti[8], const double Tj
   for (int64_t n = 0; n < n_pix; ++n) {
     int32_t m = idx[n];
     if (m < 0 || !(q[n] > P->q_min)) continue;
-    double r[4], J[56];
-    if (!residual_jacobian_rel(Tij, Ad, X_j + 3 * n, X_i + 3 * (int64_t)m, r, J)) continue;
-    double lr = q[n] / (P->sigma_ray * P->sigma_ray), ld = q[n] / (P->sigma_dist * P->sigma_dist);
-    double er = sqrt(lr * dot3(r, r)), ed = sqrt(ld) * fabs(r[3]);
-    double w[4];
-    w[0] = w[1] = w[2] = lr * huber_weight(er, P->huber_delta);
-    w[3] = ld * huber_weight(ed, P->huber_delta);
+    double r[4], J[56], w[4];
+    const int rows = residual_jacobian_family(P, Tij, Ad, X_j + 3 * n, X_i + 3 * (int64_t)m, m, r, J);
+    if (!rows) continue;
+    if (P->residual == ORC_RES_RAY) {
+      /* one Huber norm on the ray residual, one on the distance residual */
+      double lr = q[n] / (P->sigma_ray * P->sigma_ray), ld = q[n] / (P->sigma_dist * P->sigma_dist);
+      double er = sqrt(lr * dot3(r, r)), ed = sqrt(ld) * fabs(r[3]);
+      w[0] = w[1] = w[2] = lr * huber_weight(er, P->huber_delta);
+      w[3] = ld * huber_weight(ed, P->huber_delta);
+      c += huber_cost(er, P->huber_delta) + huber_cost(ed, P->huber_delta);
+    } else if (P->residual == ORC_RES_POINT) {
+      /* one Huber norm on the 3D point residual */
+      double lp = q[n] / (P->sigma_point * P->sigma_point);
+      double ep = sqrt(lp * dot3(r, r));
+      w[0] = w[1] = w[2] = lp * huber_weight(ep, P->huber_delta);
+      c += huber_cost(ep, P->huber_delta);
+    } else {
+      /* one Huber norm on the 2D pixel residual, one on the depth residual */
+      double lp = q[n] / (P->sigma_pixel * P->sigma_pixel), lz = q[n] / (P->sigma_depth * P->sigma_depth);
+      double ep = sqrt(lp * (r[0] * r[0] + r[1] * r[1])), ez = sqrt(lz) * fabs(r[2]);
+      w[0] = w[1] = lp * huber_weight(ep, P->huber_delta);
+      w[2] = lz * huber_weight(ez, P->huber_delta);
+      c += huber_cost(ep, P->huber_delta) + huber_cost(ez, P->huber_delta);
+    }
     for (int a = 0; a < 14; ++a) {
       for (int b = 0; b < 14; ++b) {
         double s = 0.0;
-        for (int k = 0; k < 4; ++k) s += J[14 * k + a] * w[k] * J[14 * k + b];
+        for (int k = 0; k < rows; ++k) s += J[14 * k + a] * w[k] * J[14 * k + b];
         H14[14 * a + b] += s;
       }
       double s = 0.0;
-      for (int k = 0; k < 4; ++k) s += J[14 * k + a] * w[k] * r[k];
+      for (int k = 0; k < rows; ++k) s += J[14 * k + a] * w[k] * r[k];
       g14[a] += s;
     }
-    c += huber_cost(er, P->huber_delta) + huber_cost(ed, P->huber_delta);
     ++nv;
   }
   *cost = c;
@@ -820,4 +899,59 @@ int orc_gn_step_grad(const orc_params* P, int N, int E, const int32_t* edges, co
   }
   free(b); free(tau); free(br); free(tr); free(ra); free(rg); free(Ar); free(g); free(A); free(g14); free(H14);
   return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.3 pointmap fusion: the keyframe's canonical pointmap and confidence */
+/* are updated by a running weighted average with the new prediction of the  */
+/* keyframe's points (made with the current frame) moved into the keyframe  */
+/* frame by T_kf:  X~ <- (C~ X~ + C (T_kf X)) / (C~ + C),  C~ <- C~ + C.       */
+/* Reading: a prediction with a non-finite or zero point, or a confidence    */
+/* that is not positive, leaves the pixel unchanged.                         */
+/* ------------------------------------------------------------------------ */
+void orc_fuse(const double T_kf[8], int64_t n, double* X_canon, double* C_canon, const double* X_kf,
+              const double* C_kf) {
+  for (int64_t p = 0; p < n; ++p) {
+    const double* x = X_kf + 3 * p;
+    double c = C_kf[p];
+    if (!(finite3(x) && norm3(x) > 0.0 && c > 0.0 && isfinite(c))) continue;
+    double y[3];
+    orc_sim3_act(T_kf, x, y);
+    double cc = C_canon[p];
+    for (int k = 0; k < 3; ++k) X_canon[3 * p + k] = (cc * X_canon[3 * p + k] + c * y[k]) / (cc + c);
+    C_canon[p] = cc + c;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.4 keyframe criterion counts for one edge's matches: the number of  */
+/* valid matches and the number of distinct reference (keyframe) pixels they */
+/* hit.  A new keyframe is added when either fraction falls below omega_k.  */
+/* ------------------------------------------------------------------------ */
+void orc_match_stats(int64_t n_qry, int64_t n_ref, const int32_t* idx, int64_t* n_valid, int64_t* n_unique) {
+  unsigned char* seen = (unsigned char*)calloc((size_t)(n_ref > 0 ? n_ref : 1), 1);
+  int64_t v = 0, u = 0;
+  for (int64_t p = 0; p < n_qry; ++p) {
+    int32_t m = idx[p];
+    if (m < 0 || m >= n_ref) continue;
+    ++v;
+    if (!seen[m]) {
+      seen[m] = 1;
+      ++u;
+    }
+  }
+  free(seen);
+  *n_valid = v;
+  *n_unique = u;
+}
+
+/* Sec. 3.6, first change for a known camera: the prediction contributes only
+ * its depth; the point is rebuilt on the pixel's ray of the pinhole model. */
+void orc_calib_backproject(int H, int W, double fx, double fy, double cx, double cy, double* X) {
+  for (int64_t p = 0; p < (int64_t)H * W; ++p) {
+    const double u = (double)(p % W), v = (double)(p / W), z = X[3 * p + 2];
+    X[3 * p + 0] = z * (u - cx) / fx;
+    X[3 * p + 1] = z * (v - cy) / fy;
+    X[3 * p + 2] = z;
+  }
 }

@@ -32,7 +32,19 @@ typedef struct {
   int win_dilation[4];   /* candidate spacing per level, coarse first */
   double max_rel_dist3d; /* invalidate a match if |X_ref[m] - x| > this * |x| */
   double conv_tol;       /* GN stops once max|tau| < conv_tol */
+  /* residual family of the Gauss-Newton cost */
+  int residual;          /* 0: ray + distance (Eq. backend_ray); 1: 3D point (Eq. track_point);
+                            2: pixel + depth with known pinhole calibration (Eq. backend_pixel) */
+  double sigma_point;    /* sigma_p of the point error */
+  double sigma_pixel;    /* sigma_Pi of the pixel error (pixels) */
+  double sigma_depth;    /* sigma of the small-weight depth term of the pixel family */
+  double fx, fy, cx, cy; /* pinhole calibration K of the pixel family (Supp. S1.3) */
+  int img_w;             /* reference image width: pixel m sits at (m mod W, m div W) */
 } orc_params;
+
+#define ORC_RES_RAY 0
+#define ORC_RES_POINT 1
+#define ORC_RES_PIXEL 2
 
 /* --- Sim(3), Eq. 1 -------------------------------------------------------- */
 void orc_sim3_exp(const double tau[7], double T[8]);
@@ -67,6 +79,12 @@ void orc_match(const orc_params* P, int H, int W, int d,
  * (cols 7..13).  Returns 0 if the match is degenerate. */
 int orc_residual_jacobian(const double Ti[8], const double Tj[8], const double Xj_n[3],
                           const double Xi_m[3], double r[4], double J[56]);
+
+/* Any residual family of P->residual: returns the number of residual rows
+ * (4 ray, 3 point, 3 pixel) or 0 if the match is degenerate; m is the
+ * reference pixel index (used by the pixel family). */
+int orc_residual_jacobian_p(const orc_params* P, const double Ti[8], const double Tj[8], const double Xj_n[3],
+                            const double Xi_m[3], int32_t m, double r[4], double J[56]);
 
 /* --- per-edge linearisation (Eq. backend_ray and Eq. gauss_newton) -------- */
 /* Edge (i, j): X_i is keyframe i's canonical pointmap (gathered at m), X_j
@@ -106,6 +124,22 @@ void orc_cost_grad(const orc_params* P, int N, int E, const int32_t* edges,
 int orc_gn_step_grad(const orc_params* P, int N, int E, const int32_t* edges, const int64_t* kf_off,
                      const int64_t* e_off, const double* T, const double* X_canon, const int32_t* idx, const double* q,
                      const double* dL_dtau, double dL_dcost, double* dX, double* dq, double* tau_out);
+
+/* --- pointmap fusion, Sec. 3.3 -------------------------------------------- */
+/* X_canon [n, 3] and C_canon [n] updated in place with the prediction X_kf
+ * (keyframe points predicted with the current frame, in the frame's
+ * coordinates) and its confidence C_kf, moved by T_kf (frame -> keyframe). */
+void orc_fuse(const double T_kf[8], int64_t n, double* X_canon, double* C_canon, const double* X_kf,
+              const double* C_kf);
+
+/* --- known calibration, Sec. 3.6 ----------------------------------------- */
+/* X [H*W, 3] in place: only the depth z of each point is kept and the point
+ * is placed on its pixel's ray under the pinhole K,
+ * X[p] = z ((u - cx) / fx, (v - cy) / fy, 1), (u, v) = (p mod W, p div W). */
+void orc_calib_backproject(int H, int W, double fx, double fy, double cx, double cy, double* X);
+
+/* --- keyframe criterion counts, Sec. 3.4 ---------------------------------- */
+void orc_match_stats(int64_t n_qry, int64_t n_ref, const int32_t* idx, int64_t* n_valid, int64_t* n_unique);
 
 int orc_num_threads(void);
 

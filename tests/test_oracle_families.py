@@ -1,0 +1,193 @@
+"""Pins of the oracle's other residual families, written from their
+definitions and checked against facts fixed by the mathematics:
+
+* point family (Eq. track_point, Supp. S1.1): r = T_ij X_j,n - X_i,m; the
+  relative Jacobian is exactly [I, -[x]x, x] (Eq. point_jac);
+* pixel family with known pinhole calibration (Sec. 3.6, Eq. backend_pixel,
+  Supp. S1.3): r = Pi(T_ij X_j,n) - p_m plus a depth residual; its pixel rows
+  have a zero scale column (a projection does not see scale);
+* both: analytic Jacobians against central differences under expm-based left
+  perturbations, g = dE/dtau of the reported cost, and exact pose recovery
+  from noise-free pixel-exact correspondences;
+* the calibrated back-projection keeps the depth and puts every point on its
+  pixel's ray: projecting it gives back the pixel.
+"""
+import numpy as np
+import pytest
+from scipy.linalg import expm
+
+import oracle
+from test_oracle_gn import perturbed
+from test_oracle_sim3 import hat
+
+PAR = dict(oracle.DEFAULT_PARAMS)
+H, W = 24, 32
+CAM = dict(fx=0.8 * W, fy=0.8 * W, cx=(W - 1) / 2.0, cy=(H - 1) / 2.0)
+
+
+def pix_par(**kw):
+    return {**PAR, "residual": oracle.RES_PIXEL, "img_w": W, **CAM, **kw}
+
+
+def point_par(**kw):
+    return {**PAR, "residual": oracle.RES_POINT, **kw}
+
+
+def residual_np(fam, Mi, Mj, Xj, Xi, m):
+    """The two residuals restated with 4x4 matrices."""
+    x = (np.linalg.inv(Mi) @ Mj @ np.r_[Xj, 1.0])[:3]
+    if fam == oracle.RES_POINT:
+        return x - Xi
+    u, v = m % W, m // W
+    return np.array([CAM["fx"] * x[0] / x[2] + CAM["cx"] - u, CAM["fy"] * x[1] / x[2] + CAM["cy"] - v, x[2] - Xi[2]])
+
+
+def fd_jacobian(fam, Ti, Tj, Xj, Xi, m, h=1e-6):
+    Mi, Mj = oracle.sim3_matrix(Ti), oracle.sim3_matrix(Tj)
+    J = np.zeros((3, 14))
+    for k in range(14):
+        e = np.zeros(7)
+        e[k % 7] = h
+        P, Mn = expm(hat(e)), expm(hat(-e))
+        if k < 7:
+            rp, rm = residual_np(fam, P @ Mi, Mj, Xj, Xi, m), residual_np(fam, Mn @ Mi, Mj, Xj, Xi, m)
+        else:
+            rp, rm = residual_np(fam, Mi, P @ Mj, Xj, Xi, m), residual_np(fam, Mi, Mn @ Mj, Xj, Xi, m)
+        J[:, k] = (rp - rm) / (2 * h)
+    return J
+
+
+@pytest.mark.parametrize("fam", [oracle.RES_POINT, oracle.RES_PIXEL])
+def test_family_jacobians_vs_fd(fam):
+    rng = np.random.default_rng(10 + fam)
+    par = point_par() if fam == oracle.RES_POINT else pix_par()
+    for _ in range(30):
+        Ti = oracle.sim3_exp(rng.normal(size=7) * 0.2)
+        Tj = oracle.sim3_exp(rng.normal(size=7) * 0.2)
+        Xj = rng.normal(size=3) * 0.5 + np.array([0, 0, 4.0])
+        Xi = rng.normal(size=3) * 0.5 + np.array([0, 0, 4.0])
+        m = int(rng.integers(H * W))
+        rows, r, J = oracle.residual_jacobian_p(Ti, Tj, Xj, Xi, m, **par)
+        assert rows == 3
+        Mi, Mj = oracle.sim3_matrix(Ti), oracle.sim3_matrix(Tj)
+        assert np.allclose(r, residual_np(fam, Mi, Mj, Xj, Xi, m), atol=1e-12)
+        Jfd = fd_jacobian(fam, Ti, Tj, Xj, Xi, m)
+        assert np.abs(J - Jfd).max() <= 1e-6 * max(1.0, np.abs(J).max()), np.abs(J - Jfd).max()
+
+
+def test_point_family_relative_jacobian_is_point_jac():
+    """With T_i = I, the j-block is (dr/dx)[I, -[x]x, x] with dr/dx = I."""
+    rng = np.random.default_rng(3)
+    I8 = np.array([0, 0, 0, 0, 0, 0, 1.0, 1.0])
+    for _ in range(10):
+        Tj = oracle.sim3_exp(rng.normal(size=7) * 0.3)
+        Xj = rng.normal(size=3) + np.array([0, 0, 3.0])
+        Xi = rng.normal(size=3) + np.array([0, 0, 3.0])
+        rows, r, J = oracle.residual_jacobian_p(I8, Tj, Xj, Xi, 0, **point_par())
+        x = oracle.sim3_act(Tj, Xj)
+        expect = np.c_[np.eye(3), -hat(np.r_[np.zeros(3), x, 0.0])[:3, :3], x]
+        assert np.abs(J[:, 7:] - expect).max() <= 1e-14
+        assert np.abs(J[:, :7] + expect).max() <= 1e-14
+
+
+def test_pixel_family_structure():
+    """Pixel rows carry no scale derivative (the projection is invariant to
+    scaling x); the depth row of the j-block is [e_z^T, (y, -x, 0), z]."""
+    rng = np.random.default_rng(4)
+    I8 = np.array([0, 0, 0, 0, 0, 0, 1.0, 1.0])
+    for _ in range(10):
+        Tj = oracle.sim3_exp(rng.normal(size=7) * 0.2)
+        Xj = rng.normal(size=3) * 0.5 + np.array([0, 0, 3.0])
+        Xi = rng.normal(size=3) * 0.5 + np.array([0, 0, 3.0])
+        rows, r, J = oracle.residual_jacobian_p(I8, Tj, Xj, Xi, 5, **pix_par())
+        x = oracle.sim3_act(Tj, Xj)
+        assert np.abs(J[:2, 13]).max() <= 1e-12 * np.abs(J[:2]).max()
+        assert np.allclose(J[2, 7:], [0, 0, 1, x[1], -x[0], 0, x[2]], atol=1e-13)
+    # a point behind the camera is degenerate for the pixel family
+    rows, _, _ = oracle.residual_jacobian_p(I8, I8, np.array([0.1, 0.2, -2.0]), np.array([0, 0, 2.0]), 0, **pix_par())
+    assert rows == 0
+
+
+def calibrated_keyframe(rng):
+    """Keyframe 0 predicted with the known camera: random depths on its
+    pixels' pinhole rays."""
+    z = rng.uniform(2.0, 6.0, H * W)
+    X = np.c_[rng.normal(size=(H * W, 2)), z]
+    return oracle.calib_backproject(H, W, CAM["fx"], CAM["fy"], CAM["cx"], CAM["cy"], X)
+
+
+def test_calib_backproject_reprojects_to_pixel():
+    rng = np.random.default_rng(5)
+    X = calibrated_keyframe(rng)
+    u = CAM["fx"] * X[:, 0] / X[:, 2] + CAM["cx"]
+    v = CAM["fy"] * X[:, 1] / X[:, 2] + CAM["cy"]
+    p = np.arange(H * W)
+    assert np.abs(u - p % W).max() <= 1e-12 and np.abs(v - p // W).max() <= 1e-12
+    # idempotent, and it keeps the depth
+    X2 = oracle.calib_backproject(H, W, CAM["fx"], CAM["fy"], CAM["cx"], CAM["cy"], X)
+    assert np.array_equal(X2, X)
+
+
+def family_edge(fam, rng, noise=0.0):
+    """One edge (i = 0, j = 1): keyframe i's points (calibrated for the pixel
+    family), keyframe j's points mapped from them by T_ji, idx = identity."""
+    Xi = calibrated_keyframe(rng) if fam == oracle.RES_PIXEL else np.c_[
+        rng.uniform(-2, 2, H * W), rng.uniform(-1.5, 1.5, H * W), rng.uniform(2, 8, H * W)]
+    Ti = np.array([0, 0, 0, 0, 0, 0, 1.0, 1.0])
+    Tj = oracle.sim3_exp(np.r_[rng.normal(size=3) * 0.1, rng.normal(size=3) * 0.05, 0.05])
+    Tji = oracle.sim3_mul(oracle.sim3_inv(Tj), Ti)
+    Xj = np.array([oracle.sim3_act(Tji, x) for x in Xi])
+    Xj = Xj * (1.0 + noise * rng.normal(size=(H * W, 1)))
+    idx = np.arange(H * W, dtype=np.int32)
+    q = rng.uniform(2, 10, H * W)
+    return Ti, Tj, Xi, Xj, idx, q
+
+
+@pytest.mark.parametrize("fam", [oracle.RES_POINT, oracle.RES_PIXEL])
+@pytest.mark.parametrize("delta", [1.345, 1e9])
+def test_family_gradient_is_derivative_of_cost(fam, delta):
+    rng = np.random.default_rng(20 + fam)
+    Ti, Tj, Xi, Xj, idx, q = family_edge(fam, rng, noise=0.02)
+    Tj = oracle.sim3_mul(oracle.sim3_exp(np.r_[0.02, -0.01, 0.03, 0.01, 0.02, -0.01, 0.02]), Tj)
+    par = (point_par if fam == oracle.RES_POINT else pix_par)(huber_delta=delta)
+    Hb, g, c, nv = oracle.linearize_edge(Ti, Tj, Xi, Xj, idx, q, **par)
+    assert nv == H * W
+    h = 1e-6
+    fd = np.zeros(14)
+    for k in range(14):
+        def cost(sgn):
+            if k < 7:
+                return oracle.linearize_edge(perturbed(Ti, k, sgn * h), Tj, Xi, Xj, idx, q, **par)[2]
+            return oracle.linearize_edge(Ti, perturbed(Tj, k - 7, sgn * h), Xi, Xj, idx, q, **par)[2]
+        fd[k] = (cost(1) - cost(-1)) / (2 * h)
+    assert np.abs(g - fd).max() <= 1e-5 * np.abs(g).max(), (g, fd)
+    assert np.abs(g[:7] + g[7:]).max() <= 1e-12 * np.abs(g).max()
+    assert np.allclose(Hb, Hb.T, rtol=1e-12, atol=1e-9 * np.abs(Hb).max())
+
+
+@pytest.mark.parametrize("fam", [oracle.RES_POINT, oracle.RES_PIXEL])
+def test_family_exact_pose_recovery(fam):
+    """Two edges from the fixed keyframe 0 to keyframes 1 and 2 with
+    noise-free pixel-exact correspondences: GN recovers both poses to 1e-10."""
+    rng = np.random.default_rng(30 + fam)
+    _, T1, X0, X1, idx, q1 = family_edge(fam, rng)
+    T2 = oracle.sim3_exp(np.r_[rng.normal(size=3) * 0.1, rng.normal(size=3) * 0.05, -0.03])
+    X2 = np.array([oracle.sim3_act(oracle.sim3_inv(T2), x) for x in X0])
+    T_gt = np.array([[0, 0, 0, 0, 0, 0, 1.0, 1.0], T1, T2])
+    X = np.concatenate([X0, X1, X2])
+    edges = np.array([[0, 1], [0, 2]], dtype=np.int32)
+    kf_off = np.arange(4) * H * W
+    e_off = np.arange(3) * H * W
+    idx2 = np.tile(idx, 2)
+    q = np.r_[q1, rng.uniform(2, 10, H * W)]
+    T0 = T_gt.copy()
+    for k in (1, 2):
+        T0[k] = oracle.sim3_mul(oracle.sim3_exp(np.r_[rng.normal(size=3) * 0.03, rng.normal(size=3) * 0.02, 0.03]),
+                                T_gt[k])
+    par = point_par() if fam == oracle.RES_POINT else pix_par()
+    st, T, hist, done = oracle.gauss_newton(3, edges, kf_off, e_off, X, idx2, q, T0, 30, **par)
+    assert st == 0
+    for k in range(3):
+        err = oracle.sim3_log(oracle.sim3_mul(T[k], oracle.sim3_inv(T_gt[k])))
+        assert np.abs(err).max() <= 1e-10, (k, err)
+    assert hist[0] > hist[-1]

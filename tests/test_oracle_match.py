@@ -205,3 +205,45 @@ def test_init_from_previous_matches(tiny_wl):
     idx1, q1 = oracle.match_workload(w, 1, init_idx=init, **PAR)
     agree = np.mean(idx0 == idx1)
     assert agree > 0.99, agree
+
+
+def test_fusion_weighted_average():
+    """Sec. 3.3 fusion: with equal confidences and the same prediction twice
+    the canonical pointmap becomes the mean of the three; a prediction moved
+    by T_kf lands where the transform puts it; invalid predictions change
+    nothing; the confidence accumulates."""
+    rng = np.random.default_rng(0)
+    n = 500
+    X0 = np.c_[rng.uniform(-1, 1, n), rng.uniform(-1, 1, n), rng.uniform(2, 5, n)]
+    C0 = np.full(n, 2.0)
+    Xf = X0 + rng.normal(size=X0.shape) * 0.05
+    Cf = np.full(n, 2.0)
+    I8 = np.array([0, 0, 0, 0, 0, 0, 1.0, 1.0])
+    X1, C1 = oracle.fuse(I8, X0, C0, Xf, Cf)
+    X2, C2 = oracle.fuse(I8, X1, C1, Xf, Cf)
+    assert np.allclose(X2, (X0 + 2 * Xf) / 3, atol=1e-14) and np.allclose(C2, 6.0)
+    # a transformed prediction: fusing T X (with T the inverse of a known
+    # motion) of the keyframe's own points reproduces them
+    T = oracle.sim3_exp(np.array([0.1, -0.2, 0.05, 0.02, 0.03, -0.01, 0.01]))
+    Ti = oracle.sim3_inv(T)
+    Xp = np.array([oracle.sim3_act(Ti, x) for x in X0])
+    X3, C3 = oracle.fuse(T, X0, C0, Xp, np.full(n, 5.0))
+    assert np.allclose(X3, X0, atol=1e-12) and np.allclose(C3, 7.0)
+    Xbad = Xf.copy()
+    Xbad[::3] = 0.0
+    Cbad = Cf.copy()
+    Cbad[1::3] = -1.0
+    X4, C4 = oracle.fuse(I8, X0, C0, Xbad, Cbad)
+    untouched = np.zeros(n, bool)
+    untouched[::3] = True
+    untouched[1::3] = True
+    assert np.array_equal(X4[untouched], X0[untouched]) and np.array_equal(C4[untouched], C0[untouched])
+
+
+def test_match_stats_counts():
+    """Sec. 3.4 counts against numpy's unique (brute force)."""
+    rng = np.random.default_rng(2)
+    idx = rng.integers(-1, 300, 5000).astype(np.int32)
+    v, u = oracle.match_stats(idx, 300)
+    assert v == int((idx >= 0).sum()) and u == len(np.unique(idx[idx >= 0]))
+    assert oracle.match_stats(np.full(10, -1, np.int32), 5) == (0, 0)

@@ -67,6 +67,7 @@ typedef enum { MSLAM_F32 = 0, MSLAM_F16 = 1 } mslam_dtype;
 #define MSLAM_OP_BACKWARD 3
 #define MSLAM_OP_PACK_F32 4 /* packed-match buffer of mslam_gn_pack, FP32 storage */
 #define MSLAM_OP_PACK_F16 5 /* packed-match buffer of mslam_gn_pack, FP16 storage */
+#define MSLAM_OP_STATS 6    /* reference-pixel bitmap of mslam_match_stats */
 
 /* Constants of the method.  The paper names these quantities without values
  * where marked "reading"; defaults are set by mslam_default_params. */
@@ -82,7 +83,23 @@ typedef struct {
   int32_t win_dilation[4]; /* candidate spacing per level, coarse first; reading {2, 1} */
   float max_rel_dist3d;  /* match invalid if |X_ref[m] - x| > this * |x| (Sec. 3.2 "large distances in 3D"); reading 0.1 */
   double conv_tol;       /* a graph stops updating once max|tau| < conv_tol (Sec. 3.5 "terminates upon convergence") */
+  /* Residual family of the Gauss-Newton cost (MSLAM_RES_*):
+   *   RAY   ray + distance errors, Eq. backend_ray / Eq. track_ray (default);
+   *   POINT 3D point error r = T_ij X_j,n - X_i,m, Eq. track_point, Supp. S1.1;
+   *   PIXEL known pinhole calibration, Sec. 3.6: pixel error Pi(T_ij X_j,n) - p_m
+   *         (Eq. backend_pixel, Supp. S1.3) plus the depth error
+   *         (T_ij X_j,n)_z - (X_i,m)_z; p_m = (m mod W, m div W) of the reference
+   *         image; a match counts only if (T_ij X_j,n)_z > 1e-3 |T_ij X_j,n|. */
+  int32_t residual;
+  float sigma_point;     /* sigma_p of the point error; reading 0.05 */
+  float sigma_pixel;     /* sigma_Pi of the pixel error, pixels; reading 1.0 */
+  float sigma_depth;     /* sigma of the small-weight depth term of PIXEL; reading 0.1 */
+  float fx, fy, cx, cy;  /* pinhole calibration K of PIXEL (pixels; centre of pixel (u, v) at (u, v)) */
 } mslam_params;
+
+#define MSLAM_RES_RAY 0
+#define MSLAM_RES_POINT 1
+#define MSLAM_RES_PIXEL 2
 
 /* Fill `p` with the default readings listed above. */
 void mslam_default_params(mslam_params* p);
@@ -131,7 +148,8 @@ typedef struct {
   int32_t lin_tile;
   int32_t lin_blocks_per_sm;
   int32_t match_block_w;
-  int32_t reserved; /* set to 0 */
+  int32_t lin_form;  /* packed ray-family linearisation: 0 = records streamed through shared memory by
+                        bulk asynchronous copies (default), 1 = per-thread register pipeline */
 } mslam_plan_opts;
 void mslam_default_plan_opts(mslam_plan_opts* opts);
 mslam_status mslam_plan_create_ex(int32_t N, const int32_t* kf_hw, int32_t E, const int32_t* edges,
@@ -191,6 +209,17 @@ mslam_status mslam_match(const mslam_params* p, const mslam_plan* plan, mslam_dt
                          const void* X_ref, const void* X_qry, const void* D_ref, const void* D_qry,
                          const void* Q_ref, const void* Q_qry, const int32_t* init_idx, int32_t* idx_out,
                          void* q_out, int32_t edge_begin, int32_t edge_end, uint32_t flags, void* stream);
+
+/* Keyframe criterion of Sec. 3.4 (next stage after matching): per edge, the
+ * number of valid matches (idx >= 0) and the number of distinct reference
+ * (keyframe) pixels they hit; tracking adds a keyframe when either, as a
+ * fraction of the image, falls below omega_k (0.333 in the paper's setup).
+ * idx: edge pool [P] int32 from mslam_match; outputs n_valid [E] and
+ * n_unique [E] int32 (exact integer counts).  workspace >=
+ * mslam_workspace_bytes(plan, MSLAM_OP_STATS), 256-byte aligned (a bitmap,
+ * cleared by the call).  Errors: MSLAM_ERR_ARG, MSLAM_ERR_CUDA. */
+mslam_status mslam_match_stats(const mslam_plan* plan, const int32_t* idx, int32_t* n_valid, int32_t* n_unique,
+                               void* workspace, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* (a4-a5) Linearisation of the ray-error cost, Eq. backend_ray, Supp. S1.   */
@@ -300,6 +329,34 @@ mslam_status mslam_gn_backward(const mslam_params* p, const mslam_plan* plan, ms
                                const float* g_blocks, const double* dL_dtau, double dL_dcost, float* dL_dX,
                                float* dL_dq, int32_t* dev_status, void* workspace, size_t ws_bytes,
                                void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Pointmap fusion, Sec. 3.3 (next stage after tracking).                    */
+/* ------------------------------------------------------------------------ */
+/* Running weighted average of the keyframe's canonical pointmap:
+ *   X~ <- (C~ X~ + C (T_kf X)) / (C~ + C),  C~ <- C~ + C,
+ * per pixel, T_kf = T_wc[k]^-1 T_wc[f] computed on the device from the pose
+ * array (no host round trip after the tracking solve).  X_canon_k [n_pix, 3]
+ * and C_canon_k [n_pix] are keyframe k's canonical pointmap and confidence
+ * (updated in place); X_kf [n_pix, 3] and C_kf [n_pix] the keyframe's points
+ * as predicted with frame f, in frame f's coordinates, and their
+ * confidences; all of dtype dt, pixel-aligned with the keyframe.  A pixel
+ * whose prediction is non-finite, zero or has a confidence that is not
+ * positive is left unchanged.  Errors: MSLAM_ERR_ARG (NULL pointer, k == f,
+ * negative size), MSLAM_ERR_CUDA. */
+mslam_status mslam_fuse(mslam_dtype dt, const double* T_wc, int32_t k, int32_t f, int64_t n_pix, void* X_canon_k,
+                        void* C_canon_k, const void* X_kf, const void* C_kf, void* stream);
+
+/* Known calibration, Sec. 3.6 (first of its two changes): before a
+ * canonical pointmap is used, keep only the depth z of each point and place
+ * the point on its pixel's ray of the pinhole camera,
+ *   X[p] <- z ((u - cx) / fx, (v - cy) / fy, 1),  (u, v) = (p mod W, p div W).
+ * X: [n_images, H, W, 3] of dt (FP32 or FP16), in place, device memory.
+ * Pairs with residual = MSLAM_RES_PIXEL and the same fx, fy, cx, cy.
+ * Errors: MSLAM_ERR_ARG (NULL pointer, negative size, fx or fy not positive
+ * or a non-finite calibration), MSLAM_ERR_CUDA. */
+mslam_status mslam_calib_backproject(mslam_dtype dt, int32_t n_images, int32_t H, int32_t W, float fx, float fy,
+                                     float cx, float cy, void* X, void* stream);
 
 #ifdef __cplusplus
 }

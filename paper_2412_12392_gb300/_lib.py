@@ -25,6 +25,8 @@ MSLAM_OP_SOLVE = 2
 MSLAM_OP_BACKWARD = 3
 MSLAM_OP_PACK_F32 = 4
 MSLAM_OP_PACK_F16 = 5
+MSLAM_OP_STATS = 6
+MSLAM_RES_RAY, MSLAM_RES_POINT, MSLAM_RES_PIXEL = 0, 1, 2
 
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_NOT_PD", 4: "ERR_TIMEOUT", 5: "ERR_NONFINITE",
                 6: "ERR_RANGE"}
@@ -36,13 +38,15 @@ class Params(C.Structure):
         ("sigma_ray", C.c_float), ("sigma_dist", C.c_float), ("huber_delta", C.c_float), ("q_min", C.c_float),
         ("lm_lambda", C.c_float), ("lm_iters", C.c_int32), ("win_radius", C.c_int32), ("n_levels", C.c_int32),
         ("win_dilation", C.c_int32 * 4), ("max_rel_dist3d", C.c_float), ("conv_tol", C.c_double),
+        ("residual", C.c_int32), ("sigma_point", C.c_float), ("sigma_pixel", C.c_float), ("sigma_depth", C.c_float),
+        ("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float), ("cy", C.c_float),
     ]
 
 
 class PlanOpts(C.Structure):
     """Mirror of mslam_plan_opts."""
     _fields_ = [("lin_tile", C.c_int32), ("lin_blocks_per_sm", C.c_int32), ("match_block_w", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("lin_form", C.c_int32)]
 
 
 class MslamError(RuntimeError):
@@ -82,6 +86,10 @@ SIGNATURES = {
     "mslam_gn_pack": ([vp, vp, C.c_int, vp, vp, vp, vp, sz, vp], C.c_int),
     "mslam_gn_linearize_packed": ([vp, vp, C.c_int, vp, vp, sz, vp, vp, vp, vp, vp, sz, u32, vp], C.c_int),
     "mslam_gn_solve": ([vp, vp, vp, vp, vp, vp, vp, vp, sz, vp], C.c_int),
+    "mslam_match_stats": ([vp, vp, vp, vp, vp, sz, vp], C.c_int),
+    "mslam_calib_backproject": ([C.c_int, i32, i32, i32, C.c_float, C.c_float, C.c_float, C.c_float, vp, vp],
+                                C.c_int),
+    "mslam_fuse": ([C.c_int, vp, i32, i32, i64, vp, vp, vp, vp, vp], C.c_int),
     "mslam_gn_backward": ([vp, vp, C.c_int, vp, vp, vp, vp, vp, vp, vp, C.c_double, vp, vp, vp, vp, sz, vp],
                           C.c_int),
 }

@@ -37,7 +37,9 @@ def params_dict(p: Params) -> dict:
     """The parameter block as a plain dict (for the oracle)."""
     return dict(sigma_ray=p.sigma_ray, sigma_dist=p.sigma_dist, huber_delta=p.huber_delta, q_min=p.q_min,
                 lm_lambda=p.lm_lambda, lm_iters=p.lm_iters, win_radius=p.win_radius, n_levels=p.n_levels,
-                win_dilation=tuple(p.win_dilation), max_rel_dist3d=p.max_rel_dist3d, conv_tol=p.conv_tol)
+                win_dilation=tuple(p.win_dilation), max_rel_dist3d=p.max_rel_dist3d, conv_tol=p.conv_tol,
+                residual=p.residual, sigma_point=p.sigma_point, sigma_pixel=p.sigma_pixel,
+                sigma_depth=p.sigma_depth, fx=p.fx, fy=p.fy, cx=p.cx, cy=p.cy)
 
 
 def _stream(device=None) -> int:
@@ -74,7 +76,7 @@ class Plan:
         lib().mslam_default_plan_opts(C.byref(o))
         for k, v in (opts or {}).items():
             setattr(o, k, int(v))
-        self.opts = {k: getattr(o, k) for k in ("lin_tile", "lin_blocks_per_sm", "match_block_w")}
+        self.opts = {k: getattr(o, k) for k in ("lin_tile", "lin_blocks_per_sm", "match_block_w", "lin_form")}
         self.graph_of_kf = gk
         h = C.c_void_p()
         check(lib().mslam_plan_create_ex(self.N, kf.ctypes.data, self.E, ed.ctypes.data if self.E else None,
@@ -160,6 +162,28 @@ def match(plan: Plan, params: Params, X_ref, X_qry, D_ref, D_qry, Q_ref, Q_qry, 
                             int(edge_range[1]), _lib.MSLAM_FLAG_PER_EDGE if per_edge else 0,
                             _stream(X_ref.device)), "mslam_match")
     return idx_out, q_out
+
+
+def match_stats(plan: Plan, idx, workspace=None):
+    """mslam_match_stats (Sec. 3.4): (n_valid [E], n_unique [E]) int32."""
+    _need(idx, "idx", torch.int32, plan.edge_pixels)
+    dev = idx.device
+    nv = torch.empty(plan.E, dtype=torch.int32, device=dev)
+    nu = torch.empty(plan.E, dtype=torch.int32, device=dev)
+    ws = plan.workspace(_lib.MSLAM_OP_STATS) if workspace is None else workspace
+    check(lib().mslam_match_stats(plan.handle, idx.data_ptr(), nv.data_ptr(), nu.data_ptr(), ws.data_ptr(),
+                                  ws.numel(), _stream(dev)), "mslam_match_stats")
+    return nv, nu
+
+
+def calib_backproject(X: torch.Tensor, fx: float, fy: float, cx: float, cy: float) -> torch.Tensor:
+    """mslam_calib_backproject (Sec. 3.6), in place on X [n, H, W, 3] (FP32 or
+    FP16, CUDA); returns X."""
+    if X.dim() != 4 or X.shape[-1] != 3 or not X.is_contiguous() or not X.is_cuda:
+        raise ValueError("X must be a contiguous CUDA tensor of shape [n, H, W, 3]")
+    check(lib().mslam_calib_backproject(DTYPES[X.dtype], X.shape[0], X.shape[1], X.shape[2], fx, fy, cx, cy, X.data_ptr(),
+                                        _stream(X.device)), "mslam_calib_backproject")
+    return X
 
 
 def gn_linearize(plan: Plan, params: Params, T_wc, X_canon, idx, q, H=None, g=None, cost=None, n_valid=None,
@@ -281,6 +305,25 @@ def gn_backward(plan: Plan, params: Params, T_wc, X_canon, idx, q, H=None, g=Non
                                   dL_dX.data_ptr(), dL_dq.data_ptr(), dev_status.data_ptr(), ws.data_ptr(),
                                   ws.numel(), _stream(dev)), "mslam_gn_backward")
     return dL_dX, dL_dq, dev_status
+
+
+def fuse(T_wc, k: int, f: int, X_canon_k, C_canon_k, X_kf, C_kf):
+    """mslam_fuse (Sec. 3.3): update keyframe k's canonical pointmap and
+    confidence in place with the prediction made together with frame f."""
+    dt = X_canon_k.dtype
+    if dt not in DTYPES:
+        raise ValueError(f"unsupported storage dtype {dt}")
+    n = C_canon_k.numel()
+    for t, nm, ne in ((X_canon_k, "X_canon_k", 3 * n), (C_canon_k, "C_canon_k", n), (X_kf, "X_kf", 3 * n),
+                      (C_kf, "C_kf", n)):
+        _need(t, nm, dt, ne)
+    _need(T_wc, "T_wc", torch.float64)
+    if max(k, f) >= T_wc.numel() // 8:
+        raise ValueError("pose index out of range")
+    check(lib().mslam_fuse(DTYPES[dt], T_wc.data_ptr(), int(k), int(f), n, X_canon_k.data_ptr(),
+                           C_canon_k.data_ptr(), X_kf.data_ptr(), C_kf.data_ptr(), _stream(X_canon_k.device)),
+          "mslam_fuse")
+    return X_canon_k, C_canon_k
 
 
 class GaussNewton:

@@ -53,8 +53,11 @@ def autotune(kf_hw, edges, graph_of_kf, params, X_ref, X_qry, D_ref, D_qry, Q_re
             best_w, best_t = wdt, ms
     idx, q = api.match(api.Plan(kf_hw, edges, graph_of_kf), params, X_ref, X_qry, D_ref, D_qry, Q_ref, Q_qry)
     best_lin, best_lt = None, float("inf")
-    for tile, bps in itertools.product(lin_tiles, lin_blocks):
-        plan = api.Plan(kf_hw, edges, graph_of_kf, opts={"lin_tile": tile, "lin_blocks_per_sm": bps})
+    shapes = [(tile, bps, 1) for tile, bps in itertools.product(lin_tiles, lin_blocks)]
+    shapes += [(tile, 0, 0) for tile in lin_tiles]  # the streamed form runs one CTA per SM
+    for tile, bps, form in shapes:
+        plan = api.Plan(kf_hw, edges, graph_of_kf, opts={"lin_tile": tile, "lin_blocks_per_sm": bps,
+                                                        "lin_form": form})
         packed = api.gn_pack(plan, params, X_canon, idx, q)
         ws = plan.workspace(api._lib.MSLAM_OP_LINEARIZE)
 
@@ -62,8 +65,9 @@ def autotune(kf_hw, edges, graph_of_kf, params, X_ref, X_qry, D_ref, D_qry, Q_re
             api.gn_linearize_packed(plan, params, X_canon.dtype, T_wc, packed, workspace=ws)
 
         ms = _time(run_lin, reps)
-        report["lin_ms"][f"{tile}/{bps}"] = ms
+        report["lin_ms"][f"{tile}/{bps}/{'stream' if form == 0 else 'regs'}"] = ms
         if ms < best_lt:
-            best_lin, best_lt = (tile, bps), ms
-    report["opts"] = {"match_block_w": best_w, "lin_tile": best_lin[0], "lin_blocks_per_sm": best_lin[1]}
+            best_lin, best_lt = (tile, bps, form), ms
+    report["opts"] = {"match_block_w": best_w, "lin_tile": best_lin[0], "lin_blocks_per_sm": best_lin[1],
+                      "lin_form": best_lin[2]}
     return report

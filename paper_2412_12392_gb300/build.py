@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmslam.so")
-SOURCES = ["plan.cu", "match.cu", "linearize.cu", "solve.cu", "backward.cu", "noalloc.cu"]
+SOURCES = ["plan.cu", "match.cu", "linearize.cu", "solve.cu", "backward.cu", "noalloc.cu", "fuse.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -289,6 +289,10 @@ extern "C" mslam_status mslam_gn_backward(const mslam_params* p, const mslam_pla
     set_error("unsupported dtype %d", (int)dt);
     return MSLAM_ERR_ARG;
   }
+  if (p->residual != MSLAM_RES_RAY) {
+    set_error("gn_backward: the adjoint covers the ray-error cost only (residual = MSLAM_RES_RAY)");
+    return MSLAM_ERR_ARG;
+  }
   if (!T_wc || !X_canon || !idx || !q || !dL_dX || !dL_dq || !workspace) {
     set_error("gn_backward: NULL device pointer");
     return MSLAM_ERR_ARG;

@@ -16,8 +16,9 @@ namespace mslam {
 #endif
 constexpr int kLinTile = MSLAM_LIN_TILE;  // default pixels per linearisation work tile
 constexpr int kLinThreads = 256;     // threads per linearisation block
-constexpr int kNumAcc = 30;          // accumulators of the relative 7x7 system
-constexpr int kAccStride = 32;       // floats per tile partial in the workspace
+constexpr int kNumAcc = 30;          // accumulators of the ray family's relative 7x7 system
+constexpr int kFamAcc = 37;          // accumulators of the point / pixel families (28 + 7 + 2)
+constexpr int kAccStride = 40;       // floats per tile partial in the workspace
 constexpr int kMatchThreads = 256;   // match block: 256 query pixels (default 32 x 8)
 constexpr int kMatchBX = 32;
 constexpr int kSolveThreads = 512;
@@ -305,6 +306,10 @@ inline size_t lin_partials_bytes(int n_tiles) {
 size_t pack_bytes(int n_tiles, int lin_tile, mslam_dtype dt);
 // Persistent-grid size of the linearisation launches (0 = occupancy maximum).
 int plan_lin_blocks_per_sm(const mslam_plan* plan);
+int plan_lin_form(const mslam_plan* plan);  // 0 streamed, 1 register pipeline
+int64_t plan_max_mixed_bytes(const mslam_plan* plan);  // shared memory of the mixed-precision solve
+int64_t plan_solve_ws_doubles(const mslam_plan* plan);    // FP64 solve workspace of all graphs (doubles)
+int plan_max_image_dim(const mslam_plan* plan);  // largest H or W of the plan's keyframes
 // Host-side per-edge ranges: linearisation tiles [t0, t1), match blocks [b0, b1).
 void plan_edge_tiles(const mslam_plan* plan, int e, int* t0, int* t1);
 void plan_edge_mblocks(const mslam_plan* plan, int e, int* b0, int* b1);

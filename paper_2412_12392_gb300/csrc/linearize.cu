@@ -15,6 +15,9 @@
 // 7x7 system to the 14x14 block with Ad_{T_i^-1} (Supp. S1.4).  No atomics:
 // the result is bitwise reproducible.
 #include <algorithm>
+#include <cmath>
+#include <mutex>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -50,6 +53,8 @@ __device__ __forceinline__ float huber_c(float e, float delta) {
 
 struct LinConst {
   float inv_sr2, inv_sd2, delta, delta2, q_min;
+  float inv_s1, inv_s2;  // point: 1/sigma_p^2; pixel: 1/sigma_Pi^2 and 1/sigma_depth^2
+  float fx, fy, cx, cy;  // pinhole K of the pixel family
 };
 
 // Accumulate one match into acc[30].  Normalisation uses the hardware
@@ -127,6 +132,135 @@ __device__ __forceinline__ void accumulate(float acc[kNumAcc], const RelPose& P,
   acc[29] += 1.0f;
 }
 
+// ------------------------------------------------------------ other families
+// Point (Eq. track_point, Supp. S1.1) and calibrated pixel + depth (Sec. 3.6,
+// Eq. backend_pixel, Supp. S1.3) residuals: three rows J_k of the relative
+// Jacobian (dr/dx)[I, -[x]x, x], each a 3-vector a and its rotation part
+// x cross a, with weights w_k, accumulated as the 28 upper-triangle entries
+// of sum w_k J_k^T J_k, the 7 entries of sum w_k J_k r_k, the cost and the
+// count.  For the pixel family y = (u_m, v_m, depth of X_i[m]).
+__device__ __forceinline__ void add_rows(float acc[kFamAcc], const float J[3][7], const float w[3], const float r[3]) {
+  float wJ[3][7];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int a = 0; a < 7; ++a) wJ[k][a] = w[k] * J[k][a];
+  int t = 0;
+#pragma unroll
+  for (int a = 0; a < 7; ++a)
+#pragma unroll
+    for (int b = a; b < 7; ++b, ++t) acc[t] = fmaf(wJ[0][a], J[0][b], fmaf(wJ[1][a], J[1][b], fmaf(wJ[2][a], J[2][b], acc[t])));
+#pragma unroll
+  for (int a = 0; a < 7; ++a) acc[28 + a] = fmaf(wJ[0][a], r[0], fmaf(wJ[1][a], r[1], fmaf(wJ[2][a], r[2], acc[28 + a])));
+}
+
+__device__ __forceinline__ void row_of(float J[7], float a0, float a1, float a2, float x0, float x1, float x2, float s) {
+  J[0] = a0;
+  J[1] = a1;
+  J[2] = a2;
+  J[3] = x1 * a2 - x2 * a1;  // x cross a
+  J[4] = x2 * a0 - x0 * a2;
+  J[5] = x0 * a1 - x1 * a0;
+  J[6] = s;
+}
+
+__device__ __forceinline__ float huber_apply(float e2, float lam, const LinConst& c, float* cost) {
+  // Huber on a whitened squared norm e2: returns the IRLS weight times lam
+  if (e2 <= c.delta2) {
+    *cost += 0.5f * e2;
+    return lam;
+  }
+  const float ie = rsqrtf(e2);
+  *cost += c.delta * (e2 * ie - 0.5f * c.delta);
+  return lam * c.delta * ie;
+}
+
+template <int kKind>
+__device__ __forceinline__ void accumulate_family(float acc[kFamAcc], const RelPose& P, float3 Xj, float3 y, float qq,
+                                                  const LinConst& c) {
+  const float x0 = fmaf(P.R[0], Xj.x, fmaf(P.R[1], Xj.y, fmaf(P.R[2], Xj.z, P.t[0])));
+  const float x1 = fmaf(P.R[3], Xj.x, fmaf(P.R[4], Xj.y, fmaf(P.R[5], Xj.z, P.t[1])));
+  const float x2 = fmaf(P.R[6], Xj.x, fmaf(P.R[7], Xj.y, fmaf(P.R[8], Xj.z, P.t[2])));
+  const float d2 = fmaf(x0, x0, fmaf(x1, x1, x2 * x2));
+  if (!(d2 > 0.0f && d2 < INFINITY)) return;
+  float J[3][7], r[3], w[3], cost = 0.0f;
+  if (kKind == MSLAM_RES_POINT) {
+    r[0] = x0 - y.x;
+    r[1] = x1 - y.y;
+    r[2] = x2 - y.z;
+    const float lp = qq * c.inv_s1;
+    w[0] = w[1] = w[2] = huber_apply(lp * fmaf(r[0], r[0], fmaf(r[1], r[1], r[2] * r[2])), lp, c, &cost);
+    row_of(J[0], 1.0f, 0.0f, 0.0f, x0, x1, x2, x0);
+    row_of(J[1], 0.0f, 1.0f, 0.0f, x0, x1, x2, x1);
+    row_of(J[2], 0.0f, 0.0f, 1.0f, x0, x1, x2, x2);
+  } else {
+    if (!(x2 > 0.0f && x2 * x2 > 1e-6f * d2)) return;  // not in front of the camera
+    const float iz = 1.0f / x2;
+    const float a = c.fx * iz, b = c.fy * iz;
+    r[0] = fmaf(a, x0, c.cx) - y.x;
+    r[1] = fmaf(b, x1, c.cy) - y.y;
+    r[2] = x2 - y.z;
+    const float lp = qq * c.inv_s1, lz = qq * c.inv_s2;
+    w[0] = w[1] = huber_apply(lp * fmaf(r[0], r[0], r[1] * r[1]), lp, c, &cost);
+    w[2] = huber_apply(lz * r[2] * r[2], lz, c, &cost);
+    // dPi/dx = (1/z) [[fx, 0, -fx x/z], [0, fy, -fy y/z]]; the scale column is zero
+    row_of(J[0], a, 0.0f, -a * x0 * iz, x0, x1, x2, 0.0f);
+    row_of(J[1], 0.0f, b, -b * x1 * iz, x0, x1, x2, 0.0f);
+    row_of(J[2], 0.0f, 0.0f, 1.0f, x0, x1, x2, x2);
+  }
+  add_rows(acc, J, w, r);
+  acc[35] += cost;
+  acc[36] += 1.0f;
+}
+
+template <int kKind> struct FamilyAcc { static constexpr int N = kKind == MSLAM_RES_RAY ? kNumAcc : kFamAcc; };
+
+template <int kKind, bool kCheckFinite>
+__device__ __forceinline__ void accumulate_any(float* acc, const RelPose& P, float3 Xj, float3 y, float qq,
+                                               const LinConst& c) {
+  if constexpr (kKind == MSLAM_RES_RAY)
+    accumulate<kCheckFinite>(acc, P, Xj, y, qq, c);
+  else
+    accumulate_family<kKind>(acc, P, Xj, y, qq, c);
+}
+
+// The reference-side value a family consumes: the ray and point families use
+// X_i[m] (checked inside the ray accumulation, here for the point family);
+// the pixel family uses the pixel of m and the depth of X_i[m].  Returns
+// false for a degenerate (non-finite or zero) X_i[m].
+template <int kKind>
+__device__ __forceinline__ bool family_y(float3& y, int m, int W) {
+  if constexpr (kKind == MSLAM_RES_RAY) {
+    return true;
+  } else {
+    const float b2 = y.x * y.x + y.y * y.y + y.z * y.z;
+    if (!(b2 > 0.0f && b2 < INFINITY)) return false;
+    if (kKind == MSLAM_RES_PIXEL) y = make_float3((float)(m % W), (float)(m / W), y.z);
+    return true;
+  }
+}
+
+// Fixed-order block reduction of NA accumulators into the tile's partial slot.
+template <int NA>
+__device__ __forceinline__ void reduce_store(const float* acc, float (*red)[kFamAcc], float* partials, int tile) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int a = 0; a < NA; ++a) {
+    float v = acc[a];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) red[warp][a] = v;
+  }
+  __syncthreads();
+  if (tid < NA) {
+    float s = red[0][tid];
+#pragma unroll
+    for (int w = 1; w < kLinThreads / 32; ++w) s += red[w][tid];
+    partials[(size_t)tile * kAccStride + tid] = s;
+  }
+  __syncthreads();
+}
+
 #ifndef MSLAM_LIN_UNROLL
 #define MSLAM_LIN_UNROLL 4
 #endif
@@ -135,13 +269,14 @@ __device__ __forceinline__ void accumulate(float acc[kNumAcc], const RelPose& P,
 #endif
 constexpr int kUnroll = MSLAM_LIN_UNROLL;  // pixels per thread in flight
 
-template <typename T>
+template <typename T, int kKind>
 __global__ void __launch_bounds__(kLinThreads, MSLAM_LIN_MINBLOCKS)
     lin_tiles_kernel(PlanView pv, LinConst lc, const RelPose* __restrict__ rel, const T* __restrict__ X,
                      const int32_t* __restrict__ idx, const T* __restrict__ q, float* __restrict__ partials,
                      int tile_begin, int tile_end) {
-  __shared__ float red[kLinThreads / 32][kNumAcc];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NA = FamilyAcc<kKind>::N;
+  __shared__ float red[kLinThreads / 32][kFamAcc];
+  const int tid = threadIdx.x;
   for (int tile = tile_begin + blockIdx.x; tile < tile_end; tile += gridDim.x) {
     const DevTile tl = pv.tiles[tile];
     const DevEdge ed = pv.edges[tl.edge];
@@ -153,9 +288,9 @@ __global__ void __launch_bounds__(kLinThreads, MSLAM_LIN_MINBLOCKS)
       P.R[4] = b.x; P.R[5] = b.y; P.R[6] = b.z; P.R[7] = b.w;
       P.R[8] = c.x; P.t[0] = c.y; P.t[1] = c.z; P.t[2] = c.w;
     }
-    float acc[kNumAcc];
+    float acc[NA];
 #pragma unroll
-    for (int a = 0; a < kNumAcc; ++a) acc[a] = 0.0f;
+    for (int a = 0; a < NA; ++a) acc[a] = 0.0f;
     const int32_t* idx_e = idx + ed.off_e;
     const T* q_e = q + ed.off_e;
     const T* Xj = X + 3 * ed.off_j;
@@ -190,24 +325,11 @@ __global__ void __launch_bounds__(kLinThreads, MSLAM_LIN_MINBLOCKS)
       }
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u)
-        if (mm[u] >= 0 && qq[u] > lc.q_min) accumulate<true>(acc, P, xj[u], yy[u], qq[u], lc);
+        if (mm[u] >= 0 && qq[u] > lc.q_min && family_y<kKind>(yy[u], mm[u], ed.W))
+          accumulate_any<kKind, true>(acc, P, xj[u], yy[u], qq[u], lc);
     }
     // fixed-order tree: warp shuffles, then the 8 warp sums in order
-#pragma unroll
-    for (int a = 0; a < kNumAcc; ++a) {
-      float v = acc[a];
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-      if (lane == 0) red[warp][a] = v;
-    }
-    __syncthreads();
-    if (tid < kNumAcc) {
-      float s = red[0][tid];
-#pragma unroll
-      for (int w = 1; w < kLinThreads / 32; ++w) s += red[w][tid];
-      partials[(size_t)tile * kAccStride + tid] = s;
-    }
-    __syncthreads();
+    reduce_store<NA>(acc, red, partials, tile);
   }
 }
 
@@ -269,7 +391,7 @@ template <> struct PackRec<float> {
 
 // The storage values are copied bit for bit (FP16 -> float -> FP16 is exact).
 template <typename T>
-__global__ void __launch_bounds__(kLinThreads) pack_kernel(PlanView pv, float q_min, const T* __restrict__ X,
+__global__ void __launch_bounds__(kLinThreads) pack_kernel(PlanView pv, float q_min, int kind, const T* __restrict__ X,
                                                            const int32_t* __restrict__ idx, const T* __restrict__ q,
                                                            uint4* __restrict__ recs, int32_t* __restrict__ counts) {
   __shared__ int warp_tot[kLinThreads / 32];
@@ -300,6 +422,8 @@ __global__ void __launch_bounds__(kLinThreads) pack_kernel(PlanView pv, float q_
         // a degenerate point contributes nothing (as in the gathering form)
         const float a2 = xj.x * xj.x + xj.y * xj.y + xj.z * xj.z, b2 = y.x * y.x + y.y * y.y + y.z * y.z;
         valid = a2 > 0.0f && b2 > 0.0f && a2 < INFINITY && b2 < INFINITY;
+        // the pixel family stores the reference pixel of m and its depth
+        if (kind == MSLAM_RES_PIXEL) y = make_float3((float)(m % ed.W), (float)(m / ed.W), y.z);
       }
       const unsigned bal = __ballot_sync(0xffffffffu, valid);
       const int rank = __popc(bal & ((1u << lane) - 1u));
@@ -317,15 +441,16 @@ __global__ void __launch_bounds__(kLinThreads) pack_kernel(PlanView pv, float q_
   }
 }
 
-template <typename T>
+template <typename T, int kKind>
 __global__ void __launch_bounds__(kLinThreads, MSLAM_PACKED_MINBLOCKS) lin_packed_kernel(PlanView pv, LinConst lc,
                                                                    const RelPose* __restrict__ rel,
                                                                    const uint4* __restrict__ recs,
                                                                    const int32_t* __restrict__ counts,
                                                                    float* __restrict__ partials, int tile_begin,
                                                                    int tile_end) {
-  __shared__ float red[kLinThreads / 32][kNumAcc];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NA = FamilyAcc<kKind>::N;
+  __shared__ float red[kLinThreads / 32][kFamAcc];
+  const int tid = threadIdx.x;
   constexpr int W = PackRec<T>::kWords;
   constexpr int U = MSLAM_PACKED_UNROLL;
   for (int tile = tile_begin + blockIdx.x; tile < tile_end; tile += gridDim.x) {
@@ -338,9 +463,9 @@ __global__ void __launch_bounds__(kLinThreads, MSLAM_PACKED_MINBLOCKS) lin_packe
       P.R[4] = b.x; P.R[5] = b.y; P.R[6] = b.z; P.R[7] = b.w;
       P.R[8] = c.x; P.t[0] = c.y; P.t[1] = c.z; P.t[2] = c.w;
     }
-    float acc[kNumAcc];
+    float acc[NA];
 #pragma unroll
-    for (int a = 0; a < kNumAcc; ++a) acc[a] = 0.0f;
+    for (int a = 0; a < NA; ++a) acc[a] = 0.0f;
     const int cnt = __ldg(counts + tile);
     const uint4* in = recs + (size_t)tile * pv.lin_tile * W;
     for (int r0 = tid; r0 < cnt; r0 += U * kLinThreads) {
@@ -354,22 +479,313 @@ __global__ void __launch_bounds__(kLinThreads, MSLAM_PACKED_MINBLOCKS) lin_packe
       }
 #pragma unroll
       for (int u = 0; u < U; ++u)
-        if (r0 + u * kLinThreads < cnt) accumulate<false>(acc, P, xj[u], yy[u], qq[u], lc);
+        if (r0 + u * kLinThreads < cnt) accumulate_any<kKind, false>(acc, P, xj[u], yy[u], qq[u], lc);
     }
-#pragma unroll
-    for (int a = 0; a < kNumAcc; ++a) {
-      float v = acc[a];
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-      if (lane == 0) red[warp][a] = v;
+    reduce_store<NA>(acc, red, partials, tile);
+  }
+}
+
+// ---------------------------------------------------------- streamed form
+// The packed records of the ray family streamed through shared memory: one
+// persistent CTA per SM walks its tiles' records in 16 KB chunks, which one
+// thread copies ahead with bulk asynchronous copies (TMA, completion counted
+// on an mbarrier per stage), so the loads need no registers and the copies
+// of later chunks overlap the arithmetic of the current one.  Each thread
+// takes two records at a time (r and r + 512 of a chunk) and evaluates both
+// with paired FP32 instructions (__ffma2_rn / __fmul2_rn / __fadd2_rn: one
+// instruction per two lanes of work), which halves the instruction count of the per-match math
+// that otherwise bounds this kernel.  Every paired operation rounds exactly
+// like its scalar form; only the summation order of the per-thread sums
+// differs from lin_packed_kernel.
+
+constexpr int kStreamThreads = 512;
+constexpr int kStreamStages = 4;
+constexpr int kStreamChunkBytes = 16384;
+constexpr uint32_t kSpinLimit = 1u << 24;  // bounded mbarrier waits (non-blocking polls, about a second)
+
+// Paired FP32 arithmetic (one instruction for two lanes of work).
+using f2 = float2;
+__device__ __forceinline__ f2 mk2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ f2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ void un2(f2 x, float& a, float& b) {
+  a = x.x;
+  b = x.y;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for the phase of `parity` to complete; false after kSpinLimit polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (uint32_t it = 0; it < kSpinLimit; ++it)
+    if (mbar_test_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "{\n .reg .u64 g;\n cvta.to.global.u64 g, %1;\n"
+      " cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [g], %2, [%3];\n}\n" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Two records (lanes a and b of every pair) of the ray family.  va / vb:
+// whether the lane holds a record; an empty lane gets zero weights.
+__device__ __forceinline__ void accumulate_pair(f2 acc[kNumAcc], const f2 Rp[12], f2 X0, f2 X1, f2 X2, f2 Y0, f2 Y1,
+                                                f2 Y2, f2 Q, bool va, bool vb, const LinConst& c) {
+  const f2 x0 = fma2(Rp[0], X0, fma2(Rp[1], X1, fma2(Rp[2], X2, Rp[9])));
+  const f2 x1 = fma2(Rp[3], X0, fma2(Rp[4], X1, fma2(Rp[5], X2, Rp[10])));
+  const f2 x2 = fma2(Rp[6], X0, fma2(Rp[7], X1, fma2(Rp[8], X2, Rp[11])));
+  const f2 d2 = fma2(x0, x0, fma2(x1, x1, mul2(x2, x2)));
+  const f2 dy2 = fma2(Y0, Y0, fma2(Y1, Y1, mul2(Y2, Y2)));
+  float d2a, d2b, dy2a, dy2b;
+  un2(d2, d2a, d2b);
+  un2(dy2, dy2a, dy2b);
+  // a lane without a record, or with x = 0, contributes nothing; keep its
+  // arithmetic finite so that zero weights give exact zeros
+  va = va && d2a > 0.0f;
+  vb = vb && d2b > 0.0f;
+  const f2 id = mk2(rsqrtf(va ? d2a : 1.0f), rsqrtf(vb ? d2b : 1.0f));
+  const f2 idy = mk2(rsqrtf(va ? dy2a : 1.0f), rsqrtf(vb ? dy2b : 1.0f));
+  const f2 m1 = bc2(-1.0f);
+  const f2 d = mul2(d2, id), dy = mul2(dy2, idy);
+  const f2 u0 = mul2(x0, id), u1 = mul2(x1, id), u2 = mul2(x2, id);
+  const f2 nidy = mul2(idy, m1);
+  const f2 r0 = fma2(Y0, nidy, u0), r1 = fma2(Y1, nidy, u1), r2 = fma2(Y2, nidy, u2);
+  const f2 rd = fma2(dy, m1, d);
+  const f2 lr = mul2(Q, bc2(c.inv_sr2)), ld = mul2(Q, bc2(c.inv_sd2));
+  const f2 er2 = mul2(lr, fma2(r0, r0, fma2(r1, r1, mul2(r2, r2))));
+  const f2 ed2 = mul2(ld, mul2(rd, rd));
+  // Huber weights and cost per lane (the quadratic region needs no root)
+  float er2a, er2b, ed2a, ed2b, lra, lrb, lda, ldb;
+  un2(er2, er2a, er2b);
+  un2(ed2, ed2a, ed2b);
+  un2(lr, lra, lrb);
+  un2(ld, lda, ldb);
+  float ca = 0.5f * (er2a + ed2a), cb = 0.5f * (er2b + ed2b);
+  float wra = lra, wrb = lrb, wda = lda, wdb = ldb;
+  if (er2a > c.delta2) {
+    const float ir = rsqrtf(er2a);
+    wra = lra * c.delta * ir;
+    ca += c.delta * (er2a * ir - 0.5f * c.delta) - 0.5f * er2a;
+  }
+  if (er2b > c.delta2) {
+    const float ir = rsqrtf(er2b);
+    wrb = lrb * c.delta * ir;
+    cb += c.delta * (er2b * ir - 0.5f * c.delta) - 0.5f * er2b;
+  }
+  if (ed2a > c.delta2) {
+    const float ie = rsqrtf(ed2a);
+    wda = lda * c.delta * ie;
+    ca += c.delta * (ed2a * ie - 0.5f * c.delta) - 0.5f * ed2a;
+  }
+  if (ed2b > c.delta2) {
+    const float ie = rsqrtf(ed2b);
+    wdb = ldb * c.delta * ie;
+    cb += c.delta * (ed2b * ie - 0.5f * c.delta) - 0.5f * ed2b;
+  }
+  const f2 wr = mk2(va ? wra : 0.0f, vb ? wrb : 0.0f);
+  const f2 wd = mk2(va ? wda : 0.0f, vb ? wdb : 0.0f);
+  const f2 A = mul2(wr, mul2(id, id));
+  acc[0] = add2(acc[0], A);
+  const f2 cc = fma2(A, m1, wd);
+  const f2 cu0 = mul2(cc, u0), cu1 = mul2(cc, u1), cu2 = mul2(cc, u2);
+  acc[1] = fma2(cu0, u0, acc[1]);
+  acc[2] = fma2(cu0, u1, acc[2]);
+  acc[3] = fma2(cu0, u2, acc[3]);
+  acc[4] = fma2(cu1, u1, acc[4]);
+  acc[5] = fma2(cu1, u2, acc[5]);
+  acc[6] = fma2(cu2, u2, acc[6]);
+  acc[7] = fma2(A, x0, acc[7]);
+  acc[8] = fma2(A, x1, acc[8]);
+  acc[9] = fma2(A, x2, acc[9]);
+  acc[10] = fma2(wd, x0, acc[10]);
+  acc[11] = fma2(wd, x1, acc[11]);
+  acc[12] = fma2(wd, x2, acc[12]);
+  acc[13] = add2(acc[13], wr);
+  const f2 wu0 = mul2(wr, u0), wu1 = mul2(wr, u1), wu2 = mul2(wr, u2);
+  acc[14] = fma2(wu0, u0, acc[14]);
+  acc[15] = fma2(wu0, u1, acc[15]);
+  acc[16] = fma2(wu0, u2, acc[16]);
+  acc[17] = fma2(wu1, u1, acc[17]);
+  acc[18] = fma2(wu1, u2, acc[18]);
+  acc[19] = fma2(wu2, u2, acc[19]);
+  acc[20] = fma2(wd, d2, acc[20]);
+  const f2 nur = mul2(fma2(u0, r0, fma2(u1, r1, mul2(u2, r2))), m1);
+  const f2 ad = mul2(wr, id), wdr = mul2(wd, rd);
+  acc[21] = fma2(ad, fma2(u0, nur, r0), fma2(wdr, u0, acc[21]));
+  acc[22] = fma2(ad, fma2(u1, nur, r1), fma2(wdr, u1, acc[22]));
+  acc[23] = fma2(ad, fma2(u2, nur, r2), fma2(wdr, u2, acc[23]));
+  const f2 nx0 = mul2(x0, m1), nx1 = mul2(x1, m1), nx2 = mul2(x2, m1);
+  acc[24] = fma2(ad, fma2(nx2, r1, mul2(x1, r2)), acc[24]);
+  acc[25] = fma2(ad, fma2(nx0, r2, mul2(x2, r0)), acc[25]);
+  acc[26] = fma2(ad, fma2(nx1, r0, mul2(x0, r1)), acc[26]);
+  acc[27] = fma2(wdr, d, acc[27]);
+  acc[28] = add2(acc[28], mk2(va ? ca : 0.0f, vb ? cb : 0.0f));
+  acc[29] = add2(acc[29], mk2(va ? 1.0f : 0.0f, vb ? 1.0f : 0.0f));
+}
+
+template <typename T> struct StreamRec;
+template <> struct StreamRec<__half> {
+  static constexpr int kBytes = 16;
+  static __device__ __forceinline__ void load(const unsigned char* base, int r, float v[7]) {
+    const uint4 w = *reinterpret_cast<const uint4*>(base + 16 * r);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&w.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&w.y));
+    const float2 cc = __half22float2(*reinterpret_cast<const __half2*>(&w.z));
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = cc.x; v[5] = cc.y;
+    v[6] = __half2float(*reinterpret_cast<const __half*>(&w.w));
+  }
+};
+template <> struct StreamRec<float> {
+  static constexpr int kBytes = 32;
+  static __device__ __forceinline__ void load(const unsigned char* base, int r, float v[7]) {
+    const float4 a = *reinterpret_cast<const float4*>(base + 32 * r);
+    const float4 b = *reinterpret_cast<const float4*>(base + 32 * r + 16);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z;
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kStreamThreads, 1)
+    lin_stream_kernel(PlanView pv, LinConst lc, const RelPose* __restrict__ rel, const unsigned char* __restrict__ recs,
+                      const int32_t* __restrict__ counts, float* __restrict__ partials, int tile_begin, int tile_end) {
+  constexpr int RB = StreamRec<T>::kBytes;
+  constexpr int CR = kStreamChunkBytes / RB;  // records per chunk
+  extern __shared__ __align__(128) unsigned char stage[];
+  __shared__ __align__(8) uint64_t full[kStreamStages];
+  __shared__ int m_tile[kStreamStages], m_n[kStreamStages], m_last[kStreamStages];
+  __shared__ float red[kStreamThreads / 32][kNumAcc];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  // producer state (thread 0): the next chunk to copy
+  int p_tile = tile_begin + blockIdx.x, p_off = 0;
+  auto issue = [&](int slot) {
+    if (p_tile >= tile_end) {  // end marker
+      m_tile[slot] = -1;
+      mbar_arrive(&full[slot]);
+      return;
     }
-    __syncthreads();
-    if (tid < kNumAcc) {
-      float sum = red[0][tid];
-#pragma unroll
-      for (int w = 1; w < kLinThreads / 32; ++w) sum += red[w][tid];
-      partials[(size_t)tile * kAccStride + tid] = sum;
+    const int cnt = __ldg(counts + p_tile);
+    const int n = min(CR, cnt - p_off);
+    m_tile[slot] = p_tile;
+    m_n[slot] = n;
+    m_last[slot] = (p_off + n >= cnt);
+    if (n > 0) {
+      mbar_arrive_tx(&full[slot], (uint32_t)(n * RB));
+      bulk_g2s(stage + slot * kStreamChunkBytes, recs + ((size_t)p_tile * pv.lin_tile + p_off) * RB,
+               (uint32_t)(n * RB), &full[slot]);
+    } else {
+      mbar_arrive(&full[slot]);
     }
+    p_off += n;
+    if (p_off >= cnt) {
+      p_tile += gridDim.x;
+      p_off = 0;
+    }
+  };
+  if (tid == 0) {
+    for (int sl = 0; sl < kStreamStages; ++sl) mbar_init(&full[sl], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int sl = 0; sl < kStreamStages; ++sl) issue(sl);
+  }
+  __syncthreads();
+
+  f2 acc[kNumAcc];
+#pragma unroll
+  for (int a = 0; a < kNumAcc; ++a) acc[a] = mk2(0.0f, 0.0f);
+  int cur_tile = -1;
+  f2 Rp[12];
+  bool aborted = false;
+  for (int k = 0;; ++k) {
+    const int slot = k % kStreamStages;
+    const uint32_t parity = (uint32_t)((k / kStreamStages) & 1);
+    const bool ok = mbar_wait_bounded(&full[slot], parity);
+    if (__syncthreads_or(!ok)) {
+      aborted = true;
+      break;
+    }
+    const int tile = m_tile[slot];
+    if (tile < 0) break;
+    const int n = m_n[slot];
+    if (tile != cur_tile) {
+      const float4* src = reinterpret_cast<const float4*>(rel + pv.tiles[tile].edge);
+      const float4 a = __ldg(src), b = __ldg(src + 1), c4 = __ldg(src + 2);
+      Rp[0] = bc2(a.x); Rp[1] = bc2(a.y); Rp[2] = bc2(a.z); Rp[3] = bc2(a.w);
+      Rp[4] = bc2(b.x); Rp[5] = bc2(b.y); Rp[6] = bc2(b.z); Rp[7] = bc2(b.w);
+      Rp[8] = bc2(c4.x); Rp[9] = bc2(c4.y); Rp[10] = bc2(c4.z); Rp[11] = bc2(c4.w);
+      cur_tile = tile;
+    }
+    const unsigned char* base = stage + slot * kStreamChunkBytes;
+    for (int r0 = 0; r0 < n; r0 += 2 * kStreamThreads) {
+      const int ra = r0 + tid, rb = r0 + kStreamThreads + tid;
+      const bool va = ra < n, vb = rb < n;
+      if (!va) continue;
+      float A[7], B[7];
+      StreamRec<T>::load(base, ra, A);
+      if (vb)
+        StreamRec<T>::load(base, rb, B);
+      else
+#pragma unroll
+        for (int e = 0; e < 7; ++e) B[e] = A[e];
+      accumulate_pair(acc, Rp, mk2(A[0], B[0]), mk2(A[1], B[1]), mk2(A[2], B[2]), mk2(A[3], B[3]), mk2(A[4], B[4]),
+                      mk2(A[5], B[5]), mk2(A[6], B[6]), true, vb, lc);
+    }
+    if (m_last[slot]) {
+      // the tile is complete: fixed-order reduction into its partial slot
+#pragma unroll
+      for (int a = 0; a < kNumAcc; ++a) {
+        float lo, hi;
+        un2(acc[a], lo, hi);
+        float v = lo + hi;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) red[warp][a] = v;
+        acc[a] = mk2(0.0f, 0.0f);
+      }
+      __syncthreads();
+      if (tid < kNumAcc) {
+        float sum = red[0][tid];
+#pragma unroll
+        for (int w = 1; w < kStreamThreads / 32; ++w) sum += red[w][tid];
+        partials[(size_t)tile * kAccStride + tid] = sum;
+      }
+    }
+    __syncthreads();  // every thread is done with this slot
+    if (tid == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(slot);
+    }
+  }
+  if (aborted) {
+    // a copy did not complete in time: poison this CTA's tiles (the solve
+    // then reports a non-finite system) and let in-flight copies land
+    // before the CTA's shared memory is released
+    for (int t = tile_begin + blockIdx.x + tid * (int)gridDim.x; t < tile_end; t += kStreamThreads * (int)gridDim.x)
+      partials[(size_t)t * kAccStride] = __int_as_float(0x7fc00000);
+    if (tid == 0)
+      for (int sl = 0; sl < kStreamStages; ++sl) mbar_wait_bounded(&full[sl], 0), mbar_wait_bounded(&full[sl], 1);
     __syncthreads();
   }
 }
@@ -379,13 +795,14 @@ __global__ void __launch_bounds__(64) lin_finalize_kernel(PlanView pv, const dou
                                                           const float* __restrict__ partials,
                                                           float* __restrict__ H14, float* __restrict__ g14,
                                                           double* __restrict__ cost, int32_t* __restrict__ n_valid,
-                                                          int e_begin) {
+                                                          int e_begin, int kind) {
   const int e = e_begin + blockIdx.x;
   const DevEdge ed = pv.edges[e];
-  __shared__ double S[kNumAcc];
+  __shared__ double S[kFamAcc];
   __shared__ double Hr[49], A[49], C[49], g[7];
   const int tid = threadIdx.x;
-  if (tid < kNumAcc) {
+  const int NA = kind == MSLAM_RES_RAY ? kNumAcc : kFamAcc;
+  if (tid < NA) {
     double s = 0.0;
     for (int t = ed.tile_begin; t < ed.tile_end; ++t) s += (double)partials[(size_t)t * kAccStride + tid];
     S[tid] = s;
@@ -395,7 +812,16 @@ __global__ void __launch_bounds__(64) lin_finalize_kernel(PlanView pv, const dou
     adjoint_of(inverse(Ti), A);
   }
   __syncthreads();
-  if (tid == 0) {
+  if (tid == 0 && kind != MSLAM_RES_RAY) {
+    // other families: the 28 upper-triangle sums, then g, cost and count
+    int t = 0;
+    for (int a = 0; a < 7; ++a)
+      for (int b = a; b < 7; ++b, ++t) Hr[7 * a + b] = Hr[7 * b + a] = S[t];
+    for (int a = 0; a < 7; ++a) g[a] = S[28 + a];
+    cost[e] = S[35];
+    if (n_valid) n_valid[e] = (int32_t)S[36];
+  }
+  if (tid == 0 && kind == MSLAM_RES_RAY) {
     for (int k = 0; k < 49; ++k) Hr[k] = 0.0;
     // H_tt = S1 I + S2
     const double s2[6] = {S[1], S[2], S[3], S[4], S[5], S[6]};
@@ -468,6 +894,68 @@ static int persistent_grid(const mslam_plan* plan, K kernel) {
 
 using namespace mslam;
 
+// Opt the streamed kernels into their dynamic shared memory, once per device.
+static mslam_status stream_kernel_setup(size_t smem) {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  mslam_status st = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+  if (st != MSLAM_OK) return st;
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev >= 0 && dev < 64 && done[dev]) return MSLAM_OK;
+  st = cuda_check(cudaFuncSetAttribute(lin_stream_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                  "cudaFuncSetAttribute");
+  if (st != MSLAM_OK) return st;
+  st = cuda_check(cudaFuncSetAttribute(lin_stream_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                  "cudaFuncSetAttribute");
+  if (st != MSLAM_OK) return st;
+  if (dev >= 0 && dev < 64) done[dev] = true;
+  return MSLAM_OK;
+}
+
+// Weights and constants of the residual family chosen in the parameters.
+static mslam_status make_lin_const(const mslam_params* p, LinConst* lc, const char* who) {
+  if (p->residual < MSLAM_RES_RAY || p->residual > MSLAM_RES_PIXEL) {
+    set_error("%s: unknown residual family %d", who, (int)p->residual);
+    return MSLAM_ERR_ARG;
+  }
+  bool ok = p->huber_delta > 0.0f;
+  if (p->residual == MSLAM_RES_RAY) ok = ok && p->sigma_ray > 0.0f && p->sigma_dist > 0.0f;
+  if (p->residual == MSLAM_RES_POINT) ok = ok && p->sigma_point > 0.0f;
+  if (p->residual == MSLAM_RES_PIXEL)
+    ok = ok && p->sigma_pixel > 0.0f && p->sigma_depth > 0.0f && p->fx > 0.0f && p->fy > 0.0f &&
+         std::isfinite(p->fx) && std::isfinite(p->fy) && std::isfinite(p->cx) && std::isfinite(p->cy);
+  if (!ok) {
+    set_error("%s: the sigmas of the residual family and huber_delta must be positive (and fx, fy > 0 for the "
+              "pixel family)", who);
+    return MSLAM_ERR_ARG;
+  }
+  lc->inv_sr2 = 1.0f / (p->sigma_ray * p->sigma_ray);
+  lc->inv_sd2 = 1.0f / (p->sigma_dist * p->sigma_dist);
+  lc->delta = p->huber_delta;
+  lc->delta2 = p->huber_delta * p->huber_delta;
+  lc->q_min = p->q_min;
+  lc->inv_s1 = p->residual == MSLAM_RES_POINT ? 1.0f / (p->sigma_point * p->sigma_point)
+                                              : 1.0f / (p->sigma_pixel * p->sigma_pixel);
+  lc->inv_s2 = 1.0f / (p->sigma_depth * p->sigma_depth);
+  lc->fx = p->fx;
+  lc->fy = p->fy;
+  lc->cx = p->cx;
+  lc->cy = p->cy;
+  return MSLAM_OK;
+}
+
+// Calls f with the residual family as a compile-time constant.
+template <typename F>
+static void with_family(int kind, F&& f) {
+  if (kind == MSLAM_RES_POINT)
+    f(std::integral_constant<int, MSLAM_RES_POINT>{});
+  else if (kind == MSLAM_RES_PIXEL)
+    f(std::integral_constant<int, MSLAM_RES_PIXEL>{});
+  else
+    f(std::integral_constant<int, MSLAM_RES_RAY>{});
+}
+
 extern "C" mslam_status mslam_gn_linearize(const mslam_params* p, const mslam_plan* plan, mslam_dtype dt,
                                            const double* T_wc, const void* X_canon, const int32_t* idx,
                                            const void* q, float* H_blocks, float* g_blocks, double* cost,
@@ -492,47 +980,38 @@ extern "C" mslam_status mslam_gn_linearize(const mslam_params* p, const mslam_pl
               mslam_workspace_bytes(plan, MSLAM_OP_LINEARIZE));
     return MSLAM_ERR_ARG;
   }
-  if (!(p->sigma_ray > 0.0f) || !(p->sigma_dist > 0.0f) || !(p->huber_delta > 0.0f)) {
-    set_error("gn_linearize: sigma_ray, sigma_dist and huber_delta must be positive");
-    return MSLAM_ERR_ARG;
-  }
-  const PlanView pv = plan_view(plan);
-  if (pv.E == 0) return MSLAM_OK;
   LinConst lc;
-  lc.inv_sr2 = 1.0f / (p->sigma_ray * p->sigma_ray);
-  lc.inv_sd2 = 1.0f / (p->sigma_dist * p->sigma_dist);
-  lc.delta = p->huber_delta;
-  lc.delta2 = p->huber_delta * p->huber_delta;
-  lc.q_min = p->q_min;
+  const mslam_status st = make_lin_const(p, &lc, "gn_linearize");
+  if (st != MSLAM_OK) return st;
+  const PlanView pv = plan_view(plan);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   float* partials = static_cast<float*>(workspace);
   RelPose* rel = reinterpret_cast<RelPose*>(static_cast<char*>(workspace) + lin_partials_bytes(pv.n_tiles));
   rel_pose_kernel<<<(pv.E + 127) / 128, 128, 0, s>>>(pv, T_wc, rel);
-  if (flags & MSLAM_FLAG_PER_EDGE) {
-    // plain form: a host loop of per-edge launches
-    for (int e = 0; e < pv.E; ++e) {
-      int t0, t1;
-      plan_edge_tiles(plan, e, &t0, &t1);
+  with_family(p->residual, [&](auto K) {
+    constexpr int kK = decltype(K)::value;
+    auto launch = [&](int grid, int t0, int t1) {
       if (dt == MSLAM_F32)
-        lin_tiles_kernel<float><<<t1 - t0, kLinThreads, 0, s>>>(pv, lc, rel, static_cast<const float*>(X_canon),
-                                                               idx, static_cast<const float*>(q), partials, t0, t1);
+        lin_tiles_kernel<float, kK><<<grid, kLinThreads, 0, s>>>(pv, lc, rel, static_cast<const float*>(X_canon),
+                                                                idx, static_cast<const float*>(q), partials, t0, t1);
       else
-        lin_tiles_kernel<__half><<<t1 - t0, kLinThreads, 0, s>>>(pv, lc, rel,
-                                                                static_cast<const __half*>(X_canon), idx,
-                                                                static_cast<const __half*>(q), partials, t0, t1);
-      lin_finalize_kernel<<<1, 64, 0, s>>>(pv, T_wc, partials, H_blocks, g_blocks, cost, n_valid, e);
+        lin_tiles_kernel<__half, kK><<<grid, kLinThreads, 0, s>>>(pv, lc, rel, static_cast<const __half*>(X_canon),
+                                                                 idx, static_cast<const __half*>(q), partials, t0,
+                                                                 t1);
+    };
+    if (flags & MSLAM_FLAG_PER_EDGE) {
+      // plain form: a host loop of per-edge launches
+      for (int e = 0; e < pv.E; ++e) {
+        int t0, t1;
+        plan_edge_tiles(plan, e, &t0, &t1);
+        launch(t1 - t0, t0, t1);
+        lin_finalize_kernel<<<1, 64, 0, s>>>(pv, T_wc, partials, H_blocks, g_blocks, cost, n_valid, e, kK);
+      }
+    } else {
+      launch(std::min(pv.n_tiles, persistent_grid(plan, lin_tiles_kernel<float, kK>)), 0, pv.n_tiles);
+      lin_finalize_kernel<<<pv.E, 64, 0, s>>>(pv, T_wc, partials, H_blocks, g_blocks, cost, n_valid, 0, kK);
     }
-  } else {
-    const int grid = std::min(pv.n_tiles, persistent_grid(plan, lin_tiles_kernel<float>));
-    if (dt == MSLAM_F32)
-      lin_tiles_kernel<float><<<grid, kLinThreads, 0, s>>>(pv, lc, rel, static_cast<const float*>(X_canon), idx,
-                                                          static_cast<const float*>(q), partials, 0, pv.n_tiles);
-    else
-      lin_tiles_kernel<__half><<<grid, kLinThreads, 0, s>>>(pv, lc, rel, static_cast<const __half*>(X_canon),
-                                                           idx, static_cast<const __half*>(q), partials, 0,
-                                                           pv.n_tiles);
-    lin_finalize_kernel<<<pv.E, 64, 0, s>>>(pv, T_wc, partials, H_blocks, g_blocks, cost, n_valid, 0);
-  }
+  });
   return cuda_check(cudaGetLastError(), "gn_linearize launch");
 }
 
@@ -567,15 +1046,23 @@ extern "C" mslam_status mslam_gn_pack(const mslam_params* p, const mslam_plan* p
     set_error("gn_pack: packed buffer smaller than %zu bytes or not 256-byte aligned", pack_bytes(pv.n_tiles, pv.lin_tile, dt));
     return MSLAM_ERR_ARG;
   }
+  if (p->residual < MSLAM_RES_RAY || p->residual > MSLAM_RES_PIXEL) {
+    set_error("gn_pack: unknown residual family %d", (int)p->residual);
+    return MSLAM_ERR_ARG;
+  }
+  if (p->residual == MSLAM_RES_PIXEL && dt == MSLAM_F16 && plan_max_image_dim(plan) > 2048) {
+    set_error("gn_pack: FP16 records hold pixel coordinates exactly only up to 2048; use MSLAM_F32");
+    return MSLAM_ERR_ARG;
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   uint4* recs = static_cast<uint4*>(packed);
   int32_t* counts = reinterpret_cast<int32_t*>(static_cast<char*>(packed) + pack_bytes(pv.n_tiles, pv.lin_tile, dt) -
                                                (((size_t)pv.n_tiles * sizeof(int32_t) + 255) & ~size_t(255)));
   if (dt == MSLAM_F32)
-    pack_kernel<float><<<pv.n_tiles, kLinThreads, 0, s>>>(pv, p->q_min, static_cast<const float*>(X_canon), idx,
+    pack_kernel<float><<<pv.n_tiles, kLinThreads, 0, s>>>(pv, p->q_min, p->residual, static_cast<const float*>(X_canon), idx,
                                                           static_cast<const float*>(q), recs, counts);
   else
-    pack_kernel<__half><<<pv.n_tiles, kLinThreads, 0, s>>>(pv, p->q_min, static_cast<const __half*>(X_canon), idx,
+    pack_kernel<__half><<<pv.n_tiles, kLinThreads, 0, s>>>(pv, p->q_min, p->residual, static_cast<const __half*>(X_canon), idx,
                                                            static_cast<const __half*>(q), recs, counts);
   return cuda_check(cudaGetLastError(), "gn_pack launch");
 }
@@ -609,16 +1096,9 @@ extern "C" mslam_status mslam_gn_linearize_packed(const mslam_params* p, const m
               mslam_workspace_bytes(plan, MSLAM_OP_LINEARIZE));
     return MSLAM_ERR_ARG;
   }
-  if (!(p->sigma_ray > 0.0f) || !(p->sigma_dist > 0.0f) || !(p->huber_delta > 0.0f)) {
-    set_error("gn_linearize_packed: sigma_ray, sigma_dist and huber_delta must be positive");
-    return MSLAM_ERR_ARG;
-  }
   LinConst lc;
-  lc.inv_sr2 = 1.0f / (p->sigma_ray * p->sigma_ray);
-  lc.inv_sd2 = 1.0f / (p->sigma_dist * p->sigma_dist);
-  lc.delta = p->huber_delta;
-  lc.delta2 = p->huber_delta * p->huber_delta;
-  lc.q_min = p->q_min;
+  const mslam_status st = make_lin_const(p, &lc, "gn_linearize_packed");
+  if (st != MSLAM_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   float* partials = static_cast<float*>(workspace);
   RelPose* rel = reinterpret_cast<RelPose*>(static_cast<char*>(workspace) + lin_partials_bytes(pv.n_tiles));
@@ -627,22 +1107,47 @@ extern "C" mslam_status mslam_gn_linearize_packed(const mslam_params* p, const m
       static_cast<const char*>(packed) + pack_bytes(pv.n_tiles, pv.lin_tile, dt) -
       (((size_t)pv.n_tiles * sizeof(int32_t) + 255) & ~size_t(255)));
   rel_pose_kernel<<<(pv.E + 127) / 128, 128, 0, s>>>(pv, T_wc, rel);
-  auto launch = [&](int grid, int t0, int t1) {
-    if (dt == MSLAM_F32)
-      lin_packed_kernel<float><<<grid, kLinThreads, 0, s>>>(pv, lc, rel, recs, counts, partials, t0, t1);
-    else
-      lin_packed_kernel<__half><<<grid, kLinThreads, 0, s>>>(pv, lc, rel, recs, counts, partials, t0, t1);
-  };
-  if (flags & MSLAM_FLAG_PER_EDGE) {
-    for (int e = 0; e < pv.E; ++e) {
-      int t0, t1;
-      plan_edge_tiles(plan, e, &t0, &t1);
-      launch(t1 - t0, t0, t1);
-      lin_finalize_kernel<<<1, 64, 0, s>>>(pv, T_wc, partials, H_blocks, g_blocks, cost, n_valid, e);
-    }
-  } else {
-    launch(std::min(pv.n_tiles, persistent_grid(plan, lin_packed_kernel<__half>)), 0, pv.n_tiles);
-    lin_finalize_kernel<<<pv.E, 64, 0, s>>>(pv, T_wc, partials, H_blocks, g_blocks, cost, n_valid, 0);
+  const size_t stream_smem = (size_t)kStreamStages * kStreamChunkBytes;
+  const bool streamed = p->residual == MSLAM_RES_RAY && plan_lin_form(plan) == 0;
+  if (streamed) {
+    mslam_status st2 = stream_kernel_setup(stream_smem);
+    if (st2 != MSLAM_OK) return st2;
   }
+  with_family(p->residual, [&](auto K) {
+    constexpr int kK = decltype(K)::value;
+    auto launch = [&](int grid, int t0, int t1) {
+      if (kK == MSLAM_RES_RAY && streamed) {
+        // the ray family streams its records through shared memory
+        const unsigned char* rb = static_cast<const unsigned char*>(packed);
+        if (dt == MSLAM_F32)
+          lin_stream_kernel<float><<<grid, kStreamThreads, stream_smem, s>>>(pv, lc, rel, rb, counts, partials, t0, t1);
+        else
+          lin_stream_kernel<__half><<<grid, kStreamThreads, stream_smem, s>>>(pv, lc, rel, rb, counts, partials, t0, t1);
+        return;
+      }
+      if (dt == MSLAM_F32)
+        lin_packed_kernel<float, kK><<<grid, kLinThreads, 0, s>>>(pv, lc, rel, recs, counts, partials, t0, t1);
+      else
+        lin_packed_kernel<__half, kK><<<grid, kLinThreads, 0, s>>>(pv, lc, rel, recs, counts, partials, t0, t1);
+    };
+    if (flags & MSLAM_FLAG_PER_EDGE) {
+      for (int e = 0; e < pv.E; ++e) {
+        int t0, t1;
+        plan_edge_tiles(plan, e, &t0, &t1);
+        launch(t1 - t0, t0, t1);
+        lin_finalize_kernel<<<1, 64, 0, s>>>(pv, T_wc, partials, H_blocks, g_blocks, cost, n_valid, e, kK);
+      }
+    } else {
+      int grid = persistent_grid(plan, lin_packed_kernel<__half, kK>);
+      if (kK == MSLAM_RES_RAY && streamed) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        grid = std::max(1, sms);  // one streaming CTA per SM
+      }
+      launch(std::min(pv.n_tiles, grid), 0, pv.n_tiles);
+      lin_finalize_kernel<<<pv.E, 64, 0, s>>>(pv, T_wc, partials, H_blocks, g_blocks, cost, n_valid, 0, kK);
+    }
+  });
   return cuda_check(cudaGetLastError(), "gn_linearize_packed launch");
 }

@@ -304,3 +304,88 @@ extern "C" mslam_status mslam_match(const mslam_params* p, const mslam_plan* pla
   }
   return cuda_check(cudaGetLastError(), "match launch");
 }
+
+// ---------------------------------------------------------------- Sec. 3.4 counts
+namespace mslam {
+
+// Mark every valid match's reference pixel in a pool-wide bitmap (bit
+// e_off[e] + m) and count valid matches per edge (integer atomics: exact).
+__global__ void __launch_bounds__(256) stats_mark_kernel(PlanView pv, const int32_t* __restrict__ idx,
+                                                         uint32_t* __restrict__ bits, int32_t* __restrict__ n_valid) {
+  __shared__ int s_cnt;
+  for (int tile = blockIdx.x; tile < pv.n_tiles; tile += gridDim.x) {
+    const DevTile tl = pv.tiles[tile];
+    const DevEdge ed = pv.edges[tl.edge];
+    const int HW = ed.H * ed.W;
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    int cnt = 0;
+    for (int n = tl.begin + threadIdx.x; n < tl.end; n += blockDim.x) {
+      const int m = __ldg(idx + ed.off_e + n);
+      if (m < 0 || m >= HW) continue;
+      ++cnt;
+      const int64_t b = ed.off_e + m;
+      atomicOr(bits + (b >> 5), 1u << (b & 31));
+    }
+    for (int off = 16; off > 0; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&s_cnt, cnt);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_cnt) atomicAdd(n_valid + tl.edge, s_cnt);
+    __syncthreads();
+  }
+}
+
+// Distinct reference pixels per edge: popcount of the edge's bit range.
+__global__ void __launch_bounds__(256) stats_count_kernel(PlanView pv, const uint32_t* __restrict__ bits,
+                                                          int32_t* __restrict__ n_unique) {
+  const int e = blockIdx.x;
+  const DevEdge ed = pv.edges[e];
+  const int64_t b0 = ed.off_e, b1 = ed.off_e + (int64_t)ed.H * ed.W;  // [b0, b1)
+  const int64_t w0 = b0 >> 5, w1 = (b1 - 1) >> 5;
+  int cnt = 0;
+  for (int64_t wd = w0 + threadIdx.x; wd <= w1; wd += blockDim.x) {
+    uint32_t v = bits[wd];
+    if (wd == w0) v &= ~0u << (b0 & 31);
+    if (wd == w1 && ((b1 & 31) != 0)) v &= (1u << (b1 & 31)) - 1u;
+    cnt += __popc(v);
+  }
+  __shared__ int s[8];
+  for (int off = 16; off > 0; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < 8; ++w) t += s[w];
+    n_unique[e] = t;
+  }
+}
+
+}  // namespace mslam
+
+extern "C" mslam_status mslam_match_stats(const mslam_plan* plan, const int32_t* idx, int32_t* n_valid,
+                                          int32_t* n_unique, void* workspace, size_t ws_bytes, void* stream) {
+  if (!check_plan_uploaded(plan)) return MSLAM_ERR_ARG;
+  const PlanView pv = plan_view(plan);
+  if (pv.E == 0) return MSLAM_OK;
+  if (!idx || !n_valid || !n_unique || !workspace) {
+    set_error("match_stats: NULL device pointer");
+    return MSLAM_ERR_ARG;
+  }
+  const size_t need = mslam_workspace_bytes(plan, MSLAM_OP_STATS);
+  if (ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) {
+    set_error("match_stats: workspace smaller than %zu bytes or not 256-byte aligned", need);
+    return MSLAM_ERR_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  mslam_status st = cuda_check(cudaMemsetAsync(workspace, 0, need, s), "match_stats memset");
+  if (st != MSLAM_OK) return st;
+  st = cuda_check(cudaMemsetAsync(n_valid, 0, sizeof(int32_t) * pv.E, s), "match_stats memset");
+  if (st != MSLAM_OK) return st;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  stats_mark_kernel<<<std::min(pv.n_tiles, std::max(1, sms) * 8), 256, 0, s>>>(pv, idx,
+                                                                             static_cast<uint32_t*>(workspace), n_valid);
+  stats_count_kernel<<<pv.E, 256, 0, s>>>(pv, static_cast<const uint32_t*>(workspace), n_unique);
+  return cuda_check(cudaGetLastError(), "match_stats launch");
+}

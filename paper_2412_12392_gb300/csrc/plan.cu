@@ -22,8 +22,9 @@ struct mslam_plan {
   std::vector<int32_t> ints;
   std::vector<int32_t> order;
   int64_t n_blocks_total = 0, n_trips_total = 0, solve_ws_doubles = 0, max_graph_doubles = 0;
+  int64_t max_mixed_bytes = 0;  // shared memory of the mixed-precision solve for the largest graph
   int32_t max_levels = 0;
-  int32_t lin_tile = 0, lin_blocks_per_sm = 0, match_bx = 0, match_by = 0;
+  int32_t lin_tile = 0, lin_blocks_per_sm = 0, match_bx = 0, match_by = 0, lin_form = 0;
   int32_t n_mblocks = 0;
   void* dev = nullptr;
   size_t dev_bytes = 0;
@@ -89,7 +90,15 @@ void plan_edge_mblocks(const mslam_plan* plan, int e, int* b0, int* b1) {
 }
 
 int64_t plan_max_graph_doubles(const mslam_plan* plan) { return plan->max_graph_doubles; }
+int64_t plan_max_mixed_bytes(const mslam_plan* plan) { return plan->max_mixed_bytes; }
+int64_t plan_solve_ws_doubles(const mslam_plan* plan) { return plan->solve_ws_doubles; }
 int plan_lin_blocks_per_sm(const mslam_plan* plan) { return plan->lin_blocks_per_sm; }
+int plan_lin_form(const mslam_plan* plan) { return plan->lin_form; }
+int plan_max_image_dim(const mslam_plan* plan) {
+  int m = 0;
+  for (int v : plan->kf_hw) m = std::max(m, v);
+  return m;
+}
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -329,6 +338,8 @@ static void build_graph(mslam_plan* P, int g, const std::vector<int>& kfs) {
   const int64_t need = (int64_t)nb_total * 49 + 21 * (int64_t)m;
   P->solve_ws_doubles += need;
   P->max_graph_doubles = std::max(P->max_graph_doubles, need);
+  // mixed-precision solve: S, x, b (FP64), the FP32 factor, y and pivots, block rows
+  P->max_mixed_bytes = std::max(P->max_mixed_bytes, (int64_t)(32 * 7 * (int64_t)m + 4 * 50 * (int64_t)nb_total));
   P->n_blocks_total += nb_total;
   P->graphs.push_back(dg);
 }
@@ -355,6 +366,11 @@ void mslam_default_params(mslam_params* p) {
   p->win_dilation[3] = 1;
   p->max_rel_dist3d = 0.1f;
   p->conv_tol = 1e-10;
+  p->residual = MSLAM_RES_RAY;
+  p->sigma_point = 0.05f;
+  p->sigma_pixel = 1.0f;
+  p->sigma_depth = 0.1f;
+  p->fx = p->fy = p->cx = p->cy = 0.0f;
 }
 
 const char* mslam_last_error(void) { return g_err; }
@@ -366,7 +382,7 @@ void mslam_default_plan_opts(mslam_plan_opts* o) {
   o->lin_tile = kLinTile;
   o->lin_blocks_per_sm = 0;
   o->match_block_w = kMatchBX;
-  o->reserved = 0;
+  o->lin_form = 0;
 }
 
 mslam_status mslam_plan_create(int32_t N, const int32_t* kf_hw, int32_t E, const int32_t* edges,
@@ -381,10 +397,11 @@ mslam_status mslam_plan_create_ex(int32_t N, const int32_t* kf_hw, int32_t E, co
   if (opts) o = *opts;
   if (o.lin_tile < 1024 || o.lin_tile > 65536 || (o.lin_tile % kLinThreads) != 0 || o.lin_blocks_per_sm < 0 ||
       o.lin_blocks_per_sm > 32 || (o.match_block_w != 16 && o.match_block_w != 32 && o.match_block_w != 64 &&
-                                   o.match_block_w != 128 && o.match_block_w != 256)) {
+                                   o.match_block_w != 128 && o.match_block_w != 256) ||
+      (o.lin_form != 0 && o.lin_form != 1)) {
     set_error("plan options: lin_tile %d (multiple of %d in [1024, 65536]), lin_blocks_per_sm %d (0..32), "
-              "match_block_w %d (16, 32, 64, 128 or 256)", o.lin_tile, kLinThreads, o.lin_blocks_per_sm,
-              o.match_block_w);
+              "match_block_w %d (16, 32, 64, 128 or 256), lin_form %d (0 or 1)", o.lin_tile, kLinThreads,
+              o.lin_blocks_per_sm, o.match_block_w, o.lin_form);
     if (out) *out = nullptr;
     return MSLAM_ERR_ARG;
   }
@@ -400,6 +417,7 @@ mslam_status mslam_plan_create_ex(int32_t N, const int32_t* kf_hw, int32_t E, co
   mslam_plan* P = new mslam_plan();
   P->lin_tile = o.lin_tile;
   P->lin_blocks_per_sm = o.lin_blocks_per_sm;
+  P->lin_form = o.lin_form;
   P->match_bx = o.match_block_w;
   P->match_by = kMatchThreads / o.match_block_w;
   P->N = N;
@@ -531,15 +549,17 @@ size_t mslam_workspace_bytes(const mslam_plan* plan, int32_t op) {
   switch (op) {
     case MSLAM_OP_LINEARIZE:
       return lin_partials_bytes((int)plan->tiles.size()) + align256(sizeof(float) * 16 * std::max(plan->E, 1));
-    case MSLAM_OP_SOLVE:
-      return align256(sizeof(double) * std::max<int64_t>(plan->solve_ws_doubles, 1));
+    case MSLAM_OP_SOLVE:  // per-graph FP64 blocks and vectors, then one flag per graph
+      return align256(sizeof(double) * std::max<int64_t>(plan->solve_ws_doubles, 1)) +
+             align256(sizeof(int32_t) * std::max<size_t>(plan->graphs.size(), 1));
     case MSLAM_OP_PACK_F32:
       return pack_bytes((int)plan->tiles.size(), plan->lin_tile, MSLAM_F32);
     case MSLAM_OP_PACK_F16:
       return pack_bytes((int)plan->tiles.size(), plan->lin_tile, MSLAM_F16);
+    case MSLAM_OP_STATS:
+      return align256(sizeof(uint32_t) * (size_t)((plan->e_off.back() + 31) / 32 + 1));
     case MSLAM_OP_BACKWARD:
-      return align256(sizeof(double) * std::max<int64_t>(plan->solve_ws_doubles, 1)) +
-             align256(sizeof(double) * 7 * (size_t)plan->N) * 2;
+      return mslam_workspace_bytes(plan, MSLAM_OP_SOLVE) + align256(sizeof(double) * 7 * (size_t)plan->N) * 2;
     default:
       return 0;
   }

@@ -26,6 +26,7 @@ struct SolveConst {
   double conv_tol;
   int factor_only;      // 1: factor and write tau, never touch poses or the converged flag
   int smem_doubles;     // dynamic shared memory available per CTA (doubles)
+  const int32_t* skip;  // per graph: 1 = already solved by the mixed-precision kernel (may be NULL)
 };
 
 __global__ void __launch_bounds__(kSolveThreads) solve_kernel(PlanView pv, SolveConst sc,
@@ -41,6 +42,7 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(PlanView pv, Solve
   __shared__ int s_fail;
   __shared__ double s_max;
   __shared__ int s_nonfinite;
+  if (sc.skip && sc.skip[g]) return;
   // converged (1) or failed (> 1) earlier: no more updates; a factor-only
   // call still factors a converged graph
   if (dev_status[g] > (sc.factor_only ? 1 : 0)) return;
@@ -317,7 +319,8 @@ __global__ void __launch_bounds__(kSolveThreads) solve_cluster_kernel(PlanView p
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
   const int ctid = rank * nth + tid, cnth = kClusterSize * nth;            // cluster-wide thread index
   const int nwarps = nth >> 5, cwarp = rank * nwarps + warp, cnwarps = kClusterSize * nwarps;
-  // uniform across the cluster (all CTAs read the same status)
+  // uniform across the cluster (all CTAs read the same flags and status)
+  if (sc.skip && sc.skip[g]) return;
   if (dev_status[g] > (sc.factor_only ? 1 : 0)) return;
   const int m = G.m;
   if (m == 0) {
@@ -556,6 +559,366 @@ __global__ void __launch_bounds__(kSolveThreads) solve_cluster_kernel(PlanView p
   cl.sync();  // no CTA exits while others may still read its shared memory
 }
 
+// ------------------------------------------------------- mixed-precision form
+// The same system solved by a factorisation in FP32 and iterative refinement
+// in FP64.  With D the assembled diagonal and S = D^-1/2, the scaled matrix
+// S H S (unit diagonal) is factored in FP32 with the level schedule above;
+// then x <- x + S (L L^T)^-1 S (b - H x), the residual b - H x formed in FP64
+// from the assembled FP64 blocks, until the predicted next correction
+// (the last correction times the observed contraction rate) is below 1e-10
+// of |x|.  Each FP32 operation has a latency of a few cycles instead of about
+// 64 for FP64 on this GPU, which shortens the solve's dependent chains; the
+// refined solution is the FP64 solution of the same system.  A graph whose
+// FP32 factorisation meets a pivot below 2^-20 of its unit diagonal, or
+// whose refinement stalls, is left to the FP64 kernel (flag handled[g] = 0),
+// which applies the exact not-positive-definite rule.
+constexpr int kMixThreads = 512;
+constexpr int kMixMaxIters = 10;
+
+__global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, SolveConst sc,
+                                                                  const float* __restrict__ H14,
+                                                                  const float* __restrict__ g14,
+                                                                  double* __restrict__ T_wc,
+                                                                  double* __restrict__ tau_out,
+                                                                  int32_t* __restrict__ dev_status,
+                                                                  double* __restrict__ ws,
+                                                                  int32_t* __restrict__ handled) {
+  extern __shared__ double smem[];
+  const int g = blockIdx.x;
+  const DevGraph G = pv.graphs[g];
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
+  __shared__ int s_fail, s_done, s_nonfinite;
+  __shared__ double s_zmax, s_xmax, s_zprev, s_max;
+  const int m = G.m, nb = G.n_blocks;
+  if (dev_status[g] > 0 || m == 0) {
+    // converged or failed earlier, or nothing to solve: the FP64 kernel
+    // handles these cases exactly as before
+    if (tid == 0) handled[g] = 0;
+    return;
+  }
+  const int32_t* I = pv.ints;
+  const int32_t* pose_of_pos = I + G.off_pose;
+  const int32_t* col_ptr = I + G.off_col;
+  const int32_t* colent = I + G.off_colent;
+  const int32_t* asm_ptr = I + G.off_asm;
+  const int32_t* asment = I + G.off_asment;
+  const int32_t* gasm_ptr = I + G.off_gasm;
+  const int32_t* gasment = I + G.off_gasment;
+  const int32_t* lev_ptr = I + G.off_lev;
+  const int32_t* lev_cols = I + G.off_levcols;
+  const int32_t* levtgt = I + G.off_levtgt;
+  const int32_t* tgtlist = I + G.off_tgtlist;
+  const int32_t* tptr = I + G.off_tptr;
+  const int32_t* pairs = I + G.off_pairs;
+  const int32_t* rsptr = I + G.off_rsptr;
+  const int32_t* rs = I + G.off_rs;
+  const int32_t* blkcol = I + G.off_blkcol;
+  const int n7 = 7 * m;
+  // shared memory: FP64 vectors first, then the FP32 factor and vectors
+  double* scl = smem;          // S = D^-1/2
+  double* xv = scl + n7;       // solution
+  double* bv = xv + n7;        // right-hand side -g
+  float* Lf = reinterpret_cast<float*>(bv + n7);  // scaled factor, FP32
+  float* yv = Lf + (size_t)nb * 49;               // work vector
+  float* ivf = yv + n7;                           // reciprocal pivots
+  int* blkrow = reinterpret_cast<int*>(ivf + n7);  // row position of each block
+  double* H64 = ws + G.ws_off;  // assembled FP64 blocks (global, L2-resident)
+
+  // ---- assembly (FP64, fixed order), as in the FP64 kernel
+  for (int t = tid; t < nb * 49; t += nth) {
+    const int b = t / 49, e = t % 49, r = e / 7, c = e % 7;
+    double s = 0.0;
+    const int k1 = __ldg(asm_ptr + b + 1);
+    for (int k = __ldg(asm_ptr + b); k < k1; ++k) {
+      const int code = __ldg(asment + k), edge = code >> 2, quad = code & 3;
+      const int r0 = (quad == 0 || quad == 2) ? 0 : 7;
+      const int c0 = (quad == 0 || quad == 3) ? 0 : 7;
+      s += (double)__ldg(H14 + (size_t)edge * 196 + (r0 + r) * 14 + c0 + c);
+    }
+    H64[t] = s;
+  }
+  for (int t = tid; t < n7; t += nth) {
+    const int p = t / 7, a = t % 7;
+    double s = 0.0;
+    const int k1 = __ldg(gasm_ptr + p + 1);
+    for (int k = __ldg(gasm_ptr + p); k < k1; ++k) {
+      const int code = __ldg(gasment + k), edge = code >> 1, side = code & 1;
+      s += (double)__ldg(g14 + (size_t)edge * 14 + 7 * side + a);
+    }
+    bv[t] = -s;
+    xv[t] = 0.0;
+  }
+  for (int p = tid; p < m; p += nth) {
+    blkrow[p] = p;
+    for (int ent = __ldg(col_ptr + p); ent < __ldg(col_ptr + p + 1); ++ent)
+      blkrow[__ldg(colent + 2 * ent + 1)] = __ldg(colent + 2 * ent);
+  }
+  if (tid == 0) {
+    s_fail = 0;
+    s_done = 0;
+    s_nonfinite = 0;
+    s_zprev = 0.0;
+  }
+  __syncthreads();
+  // ---- scaling S = D^-1/2 from the assembled diagonal
+  for (int k = tid; k < n7; k += nth) {
+    const double d = H64[49 * (k / 7) + 8 * (k % 7)];
+    if (!(d > 0.0) || !isfinite(d)) {
+      s_fail = 1;
+      scl[k] = 1.0;
+    } else {
+      scl[k] = rsqrt_newton(d);
+    }
+  }
+  __syncthreads();
+  if (s_fail) {
+    if (tid == 0) handled[g] = 0;
+    return;
+  }
+  for (int t = tid; t < nb * 49; t += nth) {
+    const int b = t / 49, e = t % 49;
+    Lf[t] = (float)(H64[t] * scl[7 * blkrow[b] + e / 7] * scl[7 * __ldg(blkcol + b) + e % 7]);
+  }
+  __syncthreads();
+
+  // ---- FP32 factorisation of S H S by levels
+  for (int l = 0; l < G.n_levels; ++l) {
+    const int q0 = __ldg(lev_ptr + l), q1 = __ldg(lev_ptr + l + 1);
+    const int g0 = __ldg(levtgt + l), g1 = __ldg(levtgt + l + 1);
+    for (int w = tid; w < (g1 - g0) * 49; w += nth) {
+      const int t = __ldg(tgtlist + g0 + w / 49), e = w % 49, r = e / 7, c = e % 7;
+      const int k1 = __ldg(tptr + t + 1);
+      float ps[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      for (int k = __ldg(tptr + t); k < k1; ++k) {
+        const float* Lb = Lf + 49 * (size_t)__ldg(pairs + 2 * k) + 7 * r;
+        const float* La = Lf + 49 * (size_t)__ldg(pairs + 2 * k + 1) + 7 * c;
+#pragma unroll
+        for (int kk = 0; kk < 7; ++kk) ps[kk] = fmaf(Lb[kk], La[kk], ps[kk]);
+      }
+      Lf[49 * (size_t)t + e] -= ((ps[0] + ps[1]) + (ps[2] + ps[3])) + ((ps[4] + ps[5]) + ps[6]);
+    }
+    __syncthreads();
+    for (int qi = q0 + warp; qi < q1; qi += nwarps) {
+      const int p = __ldg(lev_cols + qi);
+      float* D = Lf + 49 * (size_t)p;
+      const bool mine = lane < 7;
+      const int li = mine ? lane : 0;
+      float row[7];
+#pragma unroll
+      for (int k = 0; k < 7; ++k) row[k] = D[7 * li + k];
+      bool bad = false;
+#pragma unroll
+      for (int j = 0; j < 7; ++j) {
+        const float djj = __shfl_sync(0xffffffffu, row[j], j);
+        const bool okj = djj > 9.5367431640625e-7f && djj < INFINITY;  // 2^-20 of the unit diagonal
+        bad |= !okj;
+        const float ivj = rsqrtf(okj ? djj : 1.0f);
+        const float lij = (lane == j && !okj) ? 1.0f : row[j] * ivj;
+        if (mine && lane >= j) row[j] = lij;
+        if (lane == j) ivf[7 * p + j] = ivj;
+#pragma unroll
+        for (int k = j + 1; k < 7; ++k) {
+          const float lkj = __shfl_sync(0xffffffffu, row[j], k);
+          if (mine && lane >= k) row[k] = fmaf(-lij, lkj, row[k]);
+        }
+      }
+      if (mine) {
+#pragma unroll
+        for (int k = 0; k < 7; ++k)
+          if (k <= lane) D[7 * lane + k] = row[k];
+      }
+      if (bad && lane == 0) s_fail = 1;
+      __syncwarp();
+    }
+    __syncthreads();
+    if (s_fail) break;
+    for (int w = tid; w < (g1 - g0) * 7; w += nth) {
+      const int t = __ldg(tgtlist + g0 + w / 7), a = w % 7;
+      if (t < m) continue;
+      const int p = __ldg(blkcol + t);
+      const float* D = Lf + 49 * (size_t)p;
+      const float* iv = ivf + 7 * p;
+      float* row = Lf + 49 * (size_t)t + 7 * a;
+      float x[7];
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        float v = row[k];
+        for (int l2 = 0; l2 < k; ++l2) v = fmaf(-x[l2], D[7 * k + l2], v);
+        x[k] = v * iv[k];
+      }
+#pragma unroll
+      for (int k = 0; k < 7; ++k) row[k] = x[k];
+    }
+    __syncthreads();
+  }
+  if (s_fail) {
+    if (tid == 0) handled[g] = 0;
+    return;
+  }
+
+  // ---- iterative refinement
+  for (int t = tid; t < n7; t += nth) yv[t] = (float)(scl[t] * bv[t]);
+  __syncthreads();
+  for (int it = 0; it < kMixMaxIters; ++it) {
+    // forward substitution L y' = y, levels ascending, one warp per column
+    for (int l = 0; l < G.n_levels; ++l) {
+      const int q0 = __ldg(lev_ptr + l), q1 = __ldg(lev_ptr + l + 1);
+      for (int qi = q0 + warp; qi < q1; qi += nwarps) {
+        const int p = __ldg(lev_cols + qi);
+        float s = 0.0f;
+        if (lane < 7) {
+          float ps[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+          for (int k = __ldg(rsptr + p); k < __ldg(rsptr + p + 1); ++k) {
+            const float* Lpc = Lf + 49 * (size_t)__ldg(rs + 2 * k + 1) + 7 * lane;
+            const float* yc = yv + 7 * __ldg(rs + 2 * k);
+#pragma unroll
+            for (int kk = 0; kk < 7; ++kk) ps[kk] = fmaf(Lpc[kk], yc[kk], ps[kk]);
+          }
+          s = yv[7 * p + lane] - (((ps[0] + ps[1]) + (ps[2] + ps[3])) + ((ps[4] + ps[5]) + ps[6]));
+        }
+        const float* D = Lf + 49 * (size_t)p;
+        float out = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 7; ++j) {
+          const float yj = __shfl_sync(0xffffffffu, s, j) * ivf[7 * p + j];
+          if (lane == j) out = yj;
+          if (lane > j && lane < 7) s = fmaf(-D[7 * lane + j], yj, s);
+        }
+        if (lane < 7) yv[7 * p + lane] = out;
+        __syncwarp();
+      }
+      __syncthreads();
+    }
+    // back substitution L^T z = y', levels descending
+    for (int l = G.n_levels - 1; l >= 0; --l) {
+      const int q0 = __ldg(lev_ptr + l), q1 = __ldg(lev_ptr + l + 1);
+      for (int qi = q0 + warp; qi < q1; qi += nwarps) {
+        const int p = __ldg(lev_cols + qi);
+        const float* D = Lf + 49 * (size_t)p;
+        float s = 0.0f;
+        if (lane < 7) {
+          float ps[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+          for (int ent = __ldg(col_ptr + p); ent < __ldg(col_ptr + p + 1); ++ent) {
+            const float* Lr = Lf + 49 * (size_t)__ldg(colent + 2 * ent + 1);
+            const float* xr = yv + 7 * __ldg(colent + 2 * ent);
+#pragma unroll
+            for (int k = 0; k < 7; ++k) ps[k] = fmaf(Lr[7 * k + lane], xr[k], ps[k]);
+          }
+          s = yv[7 * p + lane] - (((ps[0] + ps[1]) + (ps[2] + ps[3])) + ((ps[4] + ps[5]) + ps[6]));
+        }
+        float xl = 0.0f;
+#pragma unroll
+        for (int k = 6; k >= 0; --k) {
+          const float xk = __shfl_sync(0xffffffffu, s, k) * ivf[7 * p + k];
+          if (lane == k) xl = xk;
+          if (lane < k) s = fmaf(-D[7 * k + lane], xk, s);
+        }
+        if (lane < 7) yv[7 * p + lane] = xl;
+        __syncwarp();
+      }
+      __syncthreads();
+    }
+    // x += S z; the sizes of the correction and of x
+    double zmax = 0.0, xmax = 0.0;
+    for (int t = tid; t < n7; t += nth) {
+      const double z = scl[t] * (double)yv[t];
+      const double xn = xv[t] + z;
+      xv[t] = xn;
+      zmax = fmax(zmax, fabs(z));
+      xmax = fmax(xmax, fabs(xn));
+      if (!isfinite(z)) s_nonfinite = 1;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      zmax = fmax(zmax, __shfl_xor_sync(0xffffffffu, zmax, off));
+      xmax = fmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, off));
+    }
+    if (tid == 0) {
+      s_zmax = 0.0;
+      s_xmax = 0.0;
+    }
+    __syncthreads();
+    if (lane == 0) {
+      // non-negative doubles order like their bit patterns
+      atomicMax(reinterpret_cast<unsigned long long*>(&s_zmax), (unsigned long long)__double_as_longlong(zmax));
+      atomicMax(reinterpret_cast<unsigned long long*>(&s_xmax), (unsigned long long)__double_as_longlong(xmax));
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const double zm = s_zmax, xm = s_xmax;
+      if (s_nonfinite) {
+        s_fail = 1;
+      } else if (it > 0) {
+        const double rho = s_zprev > 0.0 ? zm / s_zprev : 0.0;
+        if (zm == 0.0 || rho * zm <= 1e-10 * xm) s_done = 1;
+        else if (it > 1 && rho > 0.5) s_fail = 1;  // stalled: leave it to FP64
+      } else if (zm == 0.0) {
+        s_done = 1;  // b = 0
+      }
+      s_zprev = zm;
+    }
+    __syncthreads();
+    if (s_done || s_fail) break;
+    // residual b - H x in FP64 over the nonzero blocks of H, scaled into y
+    for (int i = tid; i < n7; i += nth) {
+      const int p = i / 7, a = i % 7;
+      double ps[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      {
+        const double* Hd = H64 + 49 * (size_t)p + 7 * a;
+        const double* xp = xv + 7 * p;
+#pragma unroll
+        for (int kk = 0; kk < 7; ++kk) ps[kk] = fma(Hd[kk], xp[kk], ps[kk]);
+      }
+      for (int k = __ldg(rsptr + p); k < __ldg(rsptr + p + 1); ++k) {
+        const int blk = __ldg(rs + 2 * k + 1);
+        if (__ldg(asm_ptr + blk) == __ldg(asm_ptr + blk + 1)) continue;  // fill: zero in H
+        const double* Hb = H64 + 49 * (size_t)blk + 7 * a;
+        const double* xc = xv + 7 * __ldg(rs + 2 * k);
+#pragma unroll
+        for (int kk = 0; kk < 7; ++kk) ps[kk] = fma(Hb[kk], xc[kk], ps[kk]);
+      }
+      for (int ent = __ldg(col_ptr + p); ent < __ldg(col_ptr + p + 1); ++ent) {
+        const int blk = __ldg(colent + 2 * ent + 1);
+        if (__ldg(asm_ptr + blk) == __ldg(asm_ptr + blk + 1)) continue;
+        const double* Hb = H64 + 49 * (size_t)blk + a;  // H_(p,r) = H_(r,p)^T
+        const double* xr = xv + 7 * __ldg(colent + 2 * ent);
+#pragma unroll
+        for (int kk = 0; kk < 7; ++kk) ps[kk] = fma(Hb[7 * kk], xr[kk], ps[kk]);
+      }
+      const double r = bv[i] - (((ps[0] + ps[1]) + (ps[2] + ps[3])) + ((ps[4] + ps[5]) + ps[6]));
+      yv[i] = (float)(scl[i] * r);
+    }
+    __syncthreads();
+  }
+  if (!s_done) {
+    if (tid == 0) handled[g] = 0;
+    return;
+  }
+
+  // ---- step statistics, tau, retraction (as in the FP64 kernel)
+  if (warp == 0) {
+    double mx = 0.0;
+    for (int t = lane; t < n7; t += 32) mx = fmax(mx, fabs(xv[t]));
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (lane == 0) s_max = mx;
+  }
+  if (tau_out && tid < 7) tau_out[7 * G.gauge + tid] = 0.0;
+  for (int p = tid; p < m; p += nth) {
+    const int k = __ldg(pose_of_pos + p);
+    double tau[7];
+    for (int a = 0; a < 7; ++a) tau[a] = xv[7 * p + a];
+    if (tau_out)
+      for (int a = 0; a < 7; ++a) tau_out[7 * k + a] = tau[a];
+    const Sim3d E = sim3_exp(tau);
+    const Sim3d Tn = compose(E, load_pose(T_wc + 8 * k));
+    store_pose(Tn, T_wc + 8 * k);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    if (s_max < sc.conv_tol) dev_status[g] = 1;
+    handled[g] = 1;
+  }
+}
+
 // Dynamic shared memory for the solve: the largest graph's factor if it fits
 // in the opt-in per-CTA limit, else none (all graphs then use the workspace).
 static int smem_limit_bytes() {
@@ -567,6 +930,7 @@ static int smem_limit_bytes() {
     limit = std::max(0, optin - 2048);  // headroom for the static shared variables
     cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
     cudaFuncSetAttribute(solve_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
+    cudaFuncSetAttribute(solve_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
   }
   return limit;
 }
@@ -599,6 +963,14 @@ static bool cluster_fits(int smem_bytes) {
   cached_bytes = smem_bytes;
   cached_ok = (e == cudaSuccess && n >= 1);
   return cached_ok;
+}
+
+// Shared memory of the mixed-precision solve if the plan's largest graph fits
+// (0: use the FP64 kernels alone).
+static int mixed_smem_bytes(const mslam_plan* plan) {
+  const int64_t need = plan_max_mixed_bytes(plan);
+  const int limit = smem_limit_bytes();
+  return (need > 0 && need <= limit) ? (int)need : 0;
 }
 
 static mslam_status launch_solve(const PlanView& pv, SolveConst sc, const float* H, const float* g, double* T,
@@ -650,8 +1022,22 @@ extern "C" mslam_status mslam_gn_solve(const mslam_params* p, const mslam_plan* 
   sc.conv_tol = p->conv_tol;
   sc.factor_only = 0;
   sc.smem_doubles = solve_smem_doubles(plan);
+  sc.skip = nullptr;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  return launch_solve(pv, sc, H_blocks, g_blocks, T_wc, tau, dev_status, static_cast<double*>(workspace), s);
+  double* ws = static_cast<double*>(workspace);
+  const int mixed = mixed_smem_bytes(plan);
+  if (mixed > 0 && pv.E > 0) {
+    // FP32 factorisation + FP64 refinement first; graphs it declines (or
+    // that need no solve) go through the FP64 kernel, which skips the rest
+    int32_t* handled = reinterpret_cast<int32_t*>(static_cast<char*>(workspace) +
+                                                  ((sizeof(double) * std::max<int64_t>(plan_solve_ws_doubles(plan), 1) + 255) &
+                                                   ~size_t(255)));
+    solve_mixed_kernel<<<pv.G, kMixThreads, mixed, s>>>(pv, sc, H_blocks, g_blocks, T_wc, tau, dev_status, ws, handled);
+    mslam_status st = cuda_check(cudaGetLastError(), "gn_solve mixed launch");
+    if (st != MSLAM_OK) return st;
+    sc.skip = handled;
+  }
+  return launch_solve(pv, sc, H_blocks, g_blocks, T_wc, tau, dev_status, ws, s);
 }
 
 // Factor every graph's system and write tau = -H^-1 g without updating poses
@@ -663,5 +1049,6 @@ mslam_status mslam_factor_only(const mslam_plan* plan, const float* H_blocks, co
   sc.conv_tol = 0.0;
   sc.factor_only = 1;
   sc.smem_doubles = solve_smem_doubles(plan);
+  sc.skip = nullptr;
   return launch_solve(pv, sc, H_blocks, g_blocks, nullptr, tau, dev_status, ws, s);
 }

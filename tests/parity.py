@@ -66,3 +66,13 @@ def match_agreement(idx_gpu, idx_ref, diag_ref=None, params=None):
         ok = (d[:, 5] < 2e-3) | (d[:, 3] < 1e-4) | (d[:, 4] < 1e-4) | (np.abs(d[:, 6] - thr) < 1e-4) | (d[:, 2] > 1e-3)
         explained = ok.mean()
     return agree, int(dis.sum()), int(union.sum()), explained
+
+
+def solve_flags(plan, ws):
+    """Per-graph flags the mixed-precision solve leaves at the end of the
+    solve workspace: 1 = solved by FP32 factorisation + FP64 refinement,
+    0 = left to the FP64 kernel."""
+    import torch
+    n = 4 * plan.G
+    off = ws.numel() - ((n + 255) // 256) * 256
+    return ws[off:off + n].view(torch.int32).cpu()

@@ -1,0 +1,184 @@
+"""NEXT-stage kernels against the oracle: pointmap fusion (Sec. 3.3), the
+keyframe-criterion counts (Sec. 3.4), the point residual family (Eq.
+track_point) and the known-calibration pixel + depth family with its
+back-projection (Sec. 3.6, Eq. backend_pixel)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from parity import BLOCK_RTOL, assert_poses_close, block_rel_err, f64
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    assert torch.cuda.is_available()
+    from paper_2412_12392_gb300 import build
+    build.build()
+    import paper_2412_12392_gb300 as M
+    return M
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
+def test_fusion_matches_oracle(M, dtype):
+    w = synth.tracking(H=96, W=128)
+    rng = np.random.default_rng(1)
+    n = int(w.kf_off[1])
+    Xc = w.X_canon[:n].to(dtype)
+    Cc = w.C_canon[:n].to(dtype)
+    # the keyframe's points predicted with the frame, in the frame's
+    # coordinates: the canonical points moved by T_fk plus noise
+    Tk, Tf = w.T_init[0].numpy(), w.T_init[1].numpy()
+    Tfk = oracle.sim3_mul(oracle.sim3_inv(Tf), Tk)
+    Xkf = np.array([oracle.sim3_act(Tfk, x) for x in w.X_canon[:n].double().numpy()])
+    Xkf += rng.normal(size=Xkf.shape) * 0.01
+    Xkf[::17] = 0.0
+    Ckf = rng.uniform(1, 10, n)
+    Ckf[5::23] = -1.0
+    Xkf_t = torch.from_numpy(Xkf).to(dtype)
+    Ckf_t = torch.from_numpy(Ckf).to(dtype)
+    T = w.T_init.cuda()
+    Xg, Cg = Xc.cuda().clone(), Cc.cuda().clone()
+    M.fuse(T, 0, 1, Xg, Cg, Xkf_t.cuda(), Ckf_t.cuda())
+    torch.cuda.synchronize()
+    Xr, Cr = oracle.fuse(oracle.sim3_mul(oracle.sim3_inv(Tk), Tf), Xc, Cc, Xkf_t, Ckf_t)
+    tol = 2e-6 if dtype == torch.float32 else 2e-3
+    assert np.abs(Xg.double().cpu().numpy() - Xr).max() <= tol * np.abs(Xr).max()
+    assert np.abs(Cg.double().cpu().numpy() - Cr).max() <= tol * np.abs(Cr).max()
+    # untouched pixels are bit-identical
+    bad = np.zeros(n, bool)
+    bad[::17] = True
+    bad[5::23] = True
+    assert torch.equal(Xg.cpu()[torch.from_numpy(bad)], Xc[torch.from_numpy(bad)])
+
+
+def test_match_stats_match_oracle(M):
+    """Sec. 3.4 keyframe-criterion counts on the GPU's matches equal the
+    oracle's counts of the same indices (exact integers)."""
+    w = synth.global_graph(N=6, n_pairs=8, H=48, W=64, seed=4)
+    wd = w.to("cuda")
+    P = M.default_params()
+    plan = M.Plan(w.kf_hw.numpy(), w.edges.numpy())
+    idx, q = M.match(plan, P, wd.X_ref, wd.X_qry, M.chunk_descriptors(wd.D_ref), M.chunk_descriptors(wd.D_qry),
+                     wd.Q_ref, wd.Q_qry)
+    nv, nu = M.match_stats(plan, idx)
+    torch.cuda.synchronize()
+    idx_c = idx.cpu().numpy()
+    for e in range(w.E):
+        v, u = oracle.match_stats(idx_c[w.edge_slice(e)], 48 * 64)
+        assert (int(nv[e]), int(nu[e])) == (v, u), e
+    # a second call gives the same counts (the bitmap is cleared each call)
+    nv2, nu2 = M.match_stats(plan, idx)
+    assert torch.equal(nv, nv2) and torch.equal(nu, nu2)
+
+
+def calibration(w):
+    """The generator's pinhole camera (tiny workload: k1 = 0)."""
+    H, W = int(w.kf_hw[0, 0]), int(w.kf_hw[0, 1])
+    return dict(fx=0.8 * W, fy=0.8 * W, cx=(W - 1) / 2.0, cy=(H - 1) / 2.0)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
+def test_calib_backproject_matches_oracle(M, tiny_wl, dtype):
+    w = tiny_wl
+    H, W = int(w.kf_hw[0, 0]), int(w.kf_hw[0, 1])
+    K = calibration(w)
+    X = w.X_canon.to(dtype).view(w.N, H, W, 3)
+    Xg = M.calib_backproject(X.cuda().clone(), **K).cpu()
+    for k in range(w.N):
+        Xr = oracle.calib_backproject(H, W, K["fx"], K["fy"], K["cx"], K["cy"], X[k].reshape(-1, 3))
+        err = np.abs(Xg[k].reshape(-1, 3).double().numpy() - Xr)
+        tol = 1e-6 if dtype == torch.float32 else 1e-3
+        assert (err <= tol * (np.abs(Xr) + 1e-3)).all(), err.max()
+        # the depth is kept bit for bit
+        assert torch.equal(Xg[k][..., 2], X[k][..., 2])
+
+
+def family_params(M, w, fam):
+    if fam == "point":
+        return M.default_params(residual=M._lib.MSLAM_RES_POINT)
+    return M.default_params(residual=M._lib.MSLAM_RES_PIXEL, **calibration(w))
+
+
+def family_inputs(M, w, fam, dtype):
+    """Storage-dtype inputs; the pixel family's keyframes are back-projected
+    on the GPU first and both sides consume the stored result."""
+    ws = w.to_storage(dtype)
+    X = ws.X_canon.cuda().clone()
+    if fam == "pixel":
+        H, W = int(w.kf_hw[0, 0]), int(w.kf_hw[0, 1])
+        M.calib_backproject(X.view(w.N, H, W, 3), **calibration(w))
+    idx = ws.gt_match.clone()
+    q = (ws.Q_qry.float() * 0.5 + 1.0).to(dtype)
+    return ws, X, idx, q
+
+
+@pytest.mark.parametrize("fam", ["point", "pixel"])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
+def test_family_linearize_matches_oracle(M, tiny_wl, fam, dtype):
+    w = tiny_wl
+    P = family_params(M, w, fam)
+    par = M.params_dict(P)
+    ws, X, idx, q = family_inputs(M, w, fam, dtype)
+    plan = M.Plan(w.kf_hw.numpy(), w.edges.numpy())
+    T = ws.T_init.clone()
+    H, g, c, nv = M.gn_linearize(plan, P, T.cuda(), X, idx.cuda(), q.cuda())
+    packed = M.gn_pack(plan, P, X, idx.cuda(), q.cuda())
+    Hp, gp, cp, nvp = M.gn_linearize_packed(plan, P, dtype, T.cuda(), packed)
+    torch.cuda.synchronize()
+    Xc = X.cpu()
+    W = int(w.kf_hw[0, 1])
+    Hr, gr, cr, nvr = [], [], [], []
+    for e in range(w.E):
+        i, j = int(w.edges[e, 0]), int(w.edges[e, 1])
+        sl = w.edge_slice(e)
+        out = oracle.linearize_edge(T[i], T[j], Xc[w.kf_slice(i)], Xc[w.kf_slice(j)], idx[sl], q[sl], img_w=W, **par)
+        Hr.append(out[0]), gr.append(out[1]), cr.append(out[2]), nvr.append(out[3])
+    Hr, gr = np.array(Hr), np.array(gr)
+    for name, (Hg, gg, cg, ng) in {"gather": (H, g, c, nv), "packed": (Hp, gp, cp, nvp)}.items():
+        eh, eg = block_rel_err(Hg, Hr), block_rel_err(gg, gr)
+        print(f"{fam} {dtype} {name}: H rel {eh.max():.2e}, g rel {eg.max():.2e}, matches {ng.tolist()}")
+        assert eh.max() <= BLOCK_RTOL and eg.max() <= BLOCK_RTOL
+        assert np.allclose(f64(cg), cr, rtol=1e-5)
+        assert ng.cpu().tolist() == nvr
+        assert min(nvr) > 1000
+
+
+@pytest.mark.parametrize("fam", ["point", "pixel"])
+def test_family_gauss_newton_matches_oracle(M, tiny_wl, fam):
+    w = tiny_wl
+    dtype = torch.float16
+    P = family_params(M, w, fam)
+    par = M.params_dict(P)
+    ws, X, idx, q = family_inputs(M, w, fam, dtype)
+    plan = M.Plan(w.kf_hw.numpy(), w.edges.numpy())
+    gn = M.GaussNewton(plan, P, X, idx.cuda(), q.cuda(), packed=True)
+    T_g = gn.run(ws.T_init.cuda(), ws.n_gn_iters).cpu()
+    W = int(w.kf_hw[0, 1])
+    st, T_r, hist, done = oracle.gauss_newton(w.N, w.edges.numpy(), w.kf_off.numpy(), w.e_off.numpy(), X.cpu(),
+                                              idx, q, ws.T_init.numpy(), ws.n_gn_iters, img_w=W, **par)
+    assert st == 0
+    e = assert_poses_close(T_g, T_r)
+    print(f"{fam} GN vs oracle (rot, trans, scale): {e.max(axis=0)}")
+
+
+def test_family_argument_errors(M, tiny_wl):
+    w = tiny_wl
+    plan = M.Plan(w.kf_hw.numpy(), w.edges.numpy())
+    ws, X, idx, q = family_inputs(M, w, "point", torch.float32)
+    T = ws.T_init.cuda()
+    with pytest.raises(M._lib.MslamError):
+        M.gn_linearize(plan, M.default_params(residual=7), T, X, idx.cuda(), q.cuda())
+    with pytest.raises(M._lib.MslamError):  # the pixel family needs a calibration
+        M.gn_linearize(plan, M.default_params(residual=M._lib.MSLAM_RES_PIXEL), T, X, idx.cuda(), q.cuda())
+    with pytest.raises(M._lib.MslamError):  # the adjoint covers the ray family only
+        M.gn_backward(plan, family_params(M, w, "point"), T, X, idx.cuda(), q.cuda(), dL_dcost=1.0)
+    # FP16 records carry pixel coordinates exactly only up to 2048
+    big = M.Plan(np.array([[2, 4096], [2, 4096]], np.int32), np.array([[0, 1]], np.int32))
+    Xb = torch.ones(2 * 8192, 3, dtype=torch.float16, device="cuda")
+    with pytest.raises(M._lib.MslamError):
+        M.gn_pack(big, family_params(M, w, "pixel"), Xb, torch.zeros(8192, dtype=torch.int32, device="cuda"),
+                  torch.full((8192,), 5.0, dtype=torch.float16, device="cuda"))

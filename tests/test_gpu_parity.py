@@ -13,7 +13,7 @@ import torch
 import oracle
 import synth
 from parity import (BLOCK_RTOL, MATCH_AGREE, assert_poses_close, block_rel_err, f64, match_agreement,
-                    pose_errors)
+                    pose_errors, solve_flags)
 
 pytestmark = pytest.mark.gpu
 
@@ -266,10 +266,15 @@ def test_disconnected_graph_not_pd(M):
     q2 = torch.from_numpy(np.concatenate([q, q]).astype(np.float32)).cuda()
     H, g, c, nv = M.gn_linearize(plan, P, T0, torch.from_numpy(X).cuda(), idx2, q2)
     T = T0.clone()
-    tau, st = M.gn_solve(plan, P, H, g, T)
+    ws = plan.workspace(M._lib.MSLAM_OP_SOLVE)
+    tau, st = M.gn_solve(plan, P, H, g, T, workspace=ws)
     torch.cuda.synchronize()
     assert int(st[0]) == 3
     assert torch.equal(T, T0)
+    # the mixed-precision kernel declined the singular system (FP32 pivots at
+    # rounding level) and the FP64 kernel reported it
+    assert solve_flags(plan, ws).tolist() == [0]
+
 
 
 def test_degenerate_plans(M):

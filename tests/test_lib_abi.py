@@ -38,8 +38,10 @@ def test_params_struct_layout(L):
     from paper_2412_12392_gb300 import _lib
     p = _lib.Params()
     L.mslam_default_params(C.byref(p))
-    assert C.sizeof(p) == 64
+    assert C.sizeof(p) == 96
+    assert _lib.Params.conv_tol.offset == 56 and _lib.Params.residual.offset == 64 and _lib.Params.cy.offset == 92
     assert abs(p.sigma_ray - 0.01) < 1e-8 and p.lm_iters == 10 and list(p.win_dilation)[:2] == [2, 1]
+    assert p.residual == _lib.MSLAM_RES_RAY and abs(p.sigma_point - 0.05) < 1e-8 and p.sigma_pixel == 1.0
 
 
 def plan(kf_hw, edges, graph=None):

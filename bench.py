@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--small", action="store_true", help="a reduced graph (8 keyframes) for profiling")
     ap.add_argument("--hw", default="384x512", help="image size HxW (smaller sizes keep the graph for profiling)")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes instead of the autotuner's")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the tracking-frame and adjoint measurements reported beside the headline")
     return ap.parse_args()
 
 
@@ -229,19 +231,42 @@ class Arm:
             lins.append((a, b, c))
         ev.append((e[0], e[1], e[2], lins))
 
+    def capture(self):
+        """Capture one whole step (pose reset, matching, packing and the GN
+        iterations) into a CUDA graph; step_graph() replays it."""
+        dev = self.wd.X_canon.device
+        s = torch.cuda.Stream(dev)
+        s.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(s):
+            self.step()  # warm-up outside capture
+        torch.cuda.current_stream(dev).wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.step()
+        self.graph = g
+
+    def step_graph(self, ev=None):
+        self.graph.replay()
+
     def launches_per_step(self) -> int:
         """Kernels of this library launched per step: match; (batched) pack;
         per iteration the relative-pose, tile and finalize kernels of the
         linearisation (per edge in the plain form) and the solve."""
         E = self.plan.E
+        sl = self.plan.solve_launches
         if self.per_edge:
-            return E + self.iters * (1 + 2 * E + 1)
-        return 1 + 1 + self.iters * 4
+            return E + self.iters * (1 + 2 * E + sl)
+        return 1 + 1 + self.iters * (3 + sl)
 
 
-def time_steps(arm, steps, warmup, world, sampler=None, with_events=True):
+def time_steps(arm, steps, warmup, world, sampler=None, with_events=True, graph=False):
+    """Mean time of a step over `steps` steps after `warmup` untimed steps;
+    with events, also the mean time of each stage (eager launches); with
+    graph, the steps are replays of the captured CUDA graph."""
+    step = arm.step_graph if graph else arm.step
     for _ in range(warmup):
-        arm.step()
+        step()
     torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
@@ -252,7 +277,7 @@ def time_steps(arm, steps, warmup, world, sampler=None, with_events=True):
         sampler.start()
     t0.record()
     for _ in range(steps):
-        arm.step(ev)
+        step(ev)
     t1.record()
     torch.cuda.synchronize()
     clocks = sampler.stop() if sampler else None
@@ -287,6 +312,12 @@ def run_gpu(args, world, rank, local):
     sampler = ClockSampler(local) if rank == 0 else None
     ms, stats, clocks = time_steps(arm, args.steps, args.warmup, world, sampler)
     ms = max_over_ranks(ms, world)
+    graph_ms = None
+    if args.form == "batched":
+        # the same step captured once as a CUDA graph and replayed
+        arm.capture()
+        graph_ms, _, _ = time_steps(arm, args.steps, args.warmup, world, None, with_events=False, graph=True)
+        graph_ms = max_over_ranks(graph_ms, world)
     tot_matched = sum_over_ranks(n_matched, world)
     tot_query = sum_over_ranks(n_query, world)
     value = tot_matched * arm.iters / (ms * 1e-3)
@@ -333,6 +364,9 @@ def run_gpu(args, world, rank, local):
         "stage_ms": {k: round(v, 4) for k, v in stats.items()},
         "matched_pixels": n_matched, "query_pixels": n_query,
         "roofline": dominant, "roofline_kernels": [rl_match, rl_lin],
+        "cuda_graph": None if graph_ms is None else {
+            "ms_per_step": graph_ms, "value": tot_matched * arm.iters / (graph_ms * 1e-3),
+            "note": "the whole step captured once as a CUDA graph and replayed"},
         "gpu_launches": arm.launches_per_step() * args.steps,
         "clocks": clocks,
     }
@@ -362,7 +396,8 @@ def e2e_measure(args, M, w, dtype, world, rank, local, opts=None, n_chunks: int 
     e_off = w.e_off.numpy()
     bounds = np.linspace(0, w.E, n_chunks + 1).round().astype(int)
     chunks = [(int(a), int(b)) for a, b in zip(bounds[:-1], bounds[1:]) if b > a]
-    copy_stream = torch.cuda.Stream(device=dev)
+    # two copy streams take alternate chunks, so that two copy engines run
+    copy_streams = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)]
     compute = torch.cuda.current_stream(dev)
     free = [torch.cuda.Event(), torch.cuda.Event()]  # a set's inputs are no longer read
     for ev in free:
@@ -372,22 +407,29 @@ def e2e_measure(args, M, w, dtype, world, rank, local, opts=None, n_chunks: int 
         """Copy stream: one step's inputs into set si, chunk by chunk."""
         dst = sets[si]
         done = []
-        with torch.cuda.stream(copy_stream):
-            copy_stream.wait_event(free[si])
+        for cs in copy_streams:
+            cs.wait_event(free[si])
+        with torch.cuda.stream(copy_streams[1]):
             dst["X_canon"].copy_(host["X_canon"], non_blocking=True)
-            for e0, e1 in chunks:
+            xev = torch.cuda.Event()
+            xev.record(copy_streams[1])
+        for ci, (e0, e1) in enumerate(chunks):
+            cs = copy_streams[ci % 2]
+            with torch.cuda.stream(cs):
                 p0, p1 = int(e_off[e0]), int(e_off[e1])
                 for k in pools:
                     if k.startswith("D_"):  # chunk-planar: one contiguous piece per plane
-                        dst[k][:, p0:p1].copy_(host[k][:, p0:p1], non_blocking=True)
+                        for c in range(host[k].shape[0]):
+                            dst[k][c, p0:p1].copy_(host[k][c, p0:p1], non_blocking=True)
                     else:
                         dst[k][p0:p1].copy_(host[k][p0:p1], non_blocking=True)
                 ev = torch.cuda.Event()
-                ev.record(copy_stream)
+                ev.record(cs)
                 done.append(ev)
-        return done
+        return done, xev
 
-    def compute_step(si, done, out):
+    def compute_step(si, copies, out):
+        done, xev = copies
         src = sets[si]
         arm.gn.T.copy_(T_host, non_blocking=True)
         arm.gn.status.zero_()
@@ -395,6 +437,7 @@ def e2e_measure(args, M, w, dtype, world, rank, local, opts=None, n_chunks: int 
             compute.wait_event(ev)
             M.match(arm.plan, arm.P, src["X_ref"], src["X_qry"], src["D_ref"], src["D_qry"], src["Q_ref"],
                     src["Q_qry"], idx_out=arm.idx, q_out=arm.q, edge_range=(e0, e1))
+        compute.wait_event(xev)
         arm.gn.X.copy_(src["X_canon"], non_blocking=True)
         arm.gn.pack()
         free[si].record(compute)
@@ -414,7 +457,8 @@ def e2e_measure(args, M, w, dtype, world, rank, local, opts=None, n_chunks: int 
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(compute)
-    copy_stream.wait_event(t0)
+    for cs in copy_streams:
+        cs.wait_event(t0)
     run(steps)
     t1.record(compute)
     torch.cuda.synchronize()
@@ -426,8 +470,8 @@ def e2e_measure(args, M, w, dtype, world, rank, local, opts=None, n_chunks: int 
     n_matched = int(((arm.idx >= 0) & (arm.q.float() > arm.P.q_min)).sum())
     val = sum_over_ranks(n_matched, world) * arm.iters / (ms * 1e-3)
     return {"value": val, "unit": "matched-pixel GN iters/s", "ms_per_step": ms, "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "copy": f"pinned host, {len(chunks)} edge chunks per step on a copy "
-            f"stream, double-buffered device inputs", "same_result_as_device_resident_step": same}
+            "d2h_bytes_per_step": int(d2h), "copy": f"pinned host, {len(chunks)} edge chunks per step on two copy "
+            f"streams, double-buffered device inputs", "same_result_as_device_resident_step": same}
 
 
 # ----------------------------------------------------------------------------- oracle arm
@@ -527,6 +571,73 @@ def run_reference(args, world, rank):
                     "d2h_bytes_per_step": 0}, "wall_s": wall}
 
 
+def _event_ms(fn, reps: int) -> float:
+    """Mean CUDA-event time of fn() on the current stream after one warm-up."""
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def tracking_frame(M, dev, peaks) -> dict:
+    """One tracking frame (Sec. 3.3) at 512 x 384, FP16 storage, radial
+    camera: matching of the frame against its keyframe, packing, and 20
+    Gauss-Newton iterations on the ray error (1 edge, the keyframe fixed)."""
+    import synth
+    w = synth.tracking(device=dev)
+    arm = Arm(M, w, torch.float16, per_edge=False)
+    ms = _event_ms(arm.step, 20)
+    ev = []
+    arm.step(ev)
+    torch.cuda.synchronize()
+    m0, m1, p1, lins = ev[0]
+    n_matched = int(((arm.idx >= 0) & (arm.q.float() > arm.P.q_min)).sum())
+    return {"workload": "tracking: 1 frame against 1 keyframe, 512x384, radial camera, d=24, 20 GN iters",
+            "ms_per_frame": ms, "match_ms": m0.elapsed_time(m1), "pack_ms": m1.elapsed_time(p1),
+            "gn_iter_ms": float(np.mean([a.elapsed_time(c) for a, b, c in lins])), "matched_pixels": n_matched}
+
+
+def adjoint_measure(M, dev, peaks) -> dict:
+    """The adjoint (a9) on the differentiation workload (32 keyframes, 96
+    edges, 512 x 384, FP16 storage): gradient of c E_g + a . tau (one GN step)
+    with respect to the canonical pointmaps and the confidences."""
+    import synth
+    w = synth.differentiation(device=dev)
+    arm = Arm(M, w, torch.float16, per_edge=False)
+    arm.step()
+    torch.cuda.synchronize()
+    P, plan, wd = arm.P, arm.plan, arm.wd
+    T = arm.T0.clone()
+    H, g, cost, nv = M.gn_linearize(plan, P, T, wd.X_canon, arm.idx, arm.q)
+    a = torch.full((plan.N, 7), 1e-3, dtype=torch.float64, device=dev)
+    ws = plan.workspace(M._lib.MSLAM_OP_BACKWARD)
+    dX = torch.empty(plan.kf_pixels, 3, dtype=torch.float32, device=dev)
+    dq = torch.empty(plan.edge_pixels, dtype=torch.float32, device=dev)
+    st = torch.zeros(plan.G, dtype=torch.int32, device=dev)
+
+    def run():
+        st.zero_()
+        M.gn_backward(plan, P, T, wd.X_canon, arm.idx, arm.q, H, g, dL_dtau=a, dL_dcost=1.0, dL_dX=dX, dL_dq=dq,
+                      dev_status=st, workspace=ws)
+
+    ms = _event_ms(run, 10)
+    n_matched = int(((arm.idx >= 0) & (arm.q.float() > P.q_min)).sum())
+    # per matched pixel: X_i[m], X_j[n] (6 B each), idx (4), q (2) read; the
+    # two point gradients (12 B each) and dq (4 B) written
+    alg = n_matched * (6 + 6 + 4 + 2 + 12 + 12 + 4)
+    gbs = alg / (ms * 1e-3) / 1e9
+    hbm = float(peaks["hbm_gbs"])
+    return {"workload": "differentiation: 32 keyframes, 96 directed edges, 512x384, FP16 storage",
+            "ms": ms, "matched_pixels": n_matched, "status": int(st[0]),
+            "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(gbs / hbm, 4), "algorithmic_bytes": int(alg)}}
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
@@ -551,7 +662,14 @@ def main():
         out["e2e"] = e2e_measure(args, M, w, arm.wd.X_canon.dtype, world, rank, local, opts=arm.plan.opts)
     if arm.tuning is not None:
         out["autotune"] = {"opts": arm.tuning["opts"], "match_ms": arm.tuning["match_ms"],
-                           "lin_ms": arm.tuning["lin_ms"]}
+                           "lin_ms": arm.tuning["lin_ms"], "pack_ms": arm.tuning["pack_ms"]}
+    if not args.no_extra and args.workload == "global" and not args.small:
+        peaks, _ = measured_peaks()
+        dev = arm.wd.X_canon.device
+        del arm.gn
+        torch.cuda.empty_cache()
+        out["tracking_frame"] = tracking_frame(M, dev, peaks)
+        out["adjoint"] = adjoint_measure(M, dev, peaks)
     if rank == 0 and not args.no_cpu:
         wc = w.to_storage(arm.wd.X_canon.dtype).to("cpu")
         out["cpu_baseline"] = cpu_baseline(wc, args.cpu_seconds, out["matched_pixels"], out["query_pixels"],

@@ -142,14 +142,20 @@ void mslam_plan_destroy(mslam_plan* plan);
  *                      occupancy maximum (default 0)
  *   match_block_w      width of a 256-pixel match block: 16, 32, 64, 128 or
  *                      256 (default 32, i.e. 32 x 8 pixels)
+ *   lin_form, solve_form  kernel forms, described at the fields
  * mslam_plan_create uses the defaults; mslam_plan_create_ex takes options
  * (NULL = defaults).  Errors: MSLAM_ERR_ARG for an option out of range. */
 typedef struct {
   int32_t lin_tile;
   int32_t lin_blocks_per_sm;
   int32_t match_block_w;
-  int32_t lin_form;  /* packed ray-family linearisation: 0 = records streamed through shared memory by
-                        bulk asynchronous copies (default), 1 = per-thread register pipeline */
+  int32_t lin_form;  /* packed linearisation of the FP16 ray family: 0 = records streamed through
+                        shared memory by bulk asynchronous copies and evaluated two at a time with
+                        paired FP32 instructions (default), 1 = per-thread register pipeline.  FP32 storage and
+                        the other residual families always use the register pipeline. */
+  int32_t solve_form;  /* 0 = FP32 factorisation of the diagonally scaled system with FP64 iterative
+                          refinement to the FP64 solution (default; graphs it declines go to the FP64
+                          factorisation), 1 = FP64 factorisation only */
 } mslam_plan_opts;
 void mslam_default_plan_opts(mslam_plan_opts* opts);
 mslam_status mslam_plan_create_ex(int32_t N, const int32_t* kf_hw, int32_t E, const int32_t* edges,
@@ -257,8 +263,10 @@ mslam_status mslam_gn_linearize(const mslam_params* p, const mslam_plan* plan, m
  * of mslam_gn_linearize (up to FP32 summation order) while streaming the
  * records with coalesced loads.  packed: caller device buffer of at least
  * mslam_workspace_bytes(plan, MSLAM_OP_PACK_F16 or _F32) bytes, 256-byte
- * aligned; it must be re-packed whenever X_canon, idx or q change.  Other
- * arguments and outputs as mslam_gn_linearize.
+ * aligned; it must be re-packed whenever X_canon, idx or q change.  The
+ * record layout depends on the residual family (the pixel family stores
+ * (u_m, v_m, depth of X_i[m]) in place of X_i[m]), so both calls take the
+ * same parameters.  Other arguments and outputs as mslam_gn_linearize.
  * Errors: MSLAM_ERR_ARG, MSLAM_ERR_CUDA. */
 mslam_status mslam_gn_pack(const mslam_params* p, const mslam_plan* plan, mslam_dtype dt, const void* X_canon,
                            const int32_t* idx, const void* q, void* packed, size_t packed_bytes, void* stream);
@@ -308,6 +316,13 @@ mslam_status mslam_gn_linearize_noalloc(const mslam_params* p, const mslam_plan*
 mslam_status mslam_gn_solve(const mslam_params* p, const mslam_plan* plan, const float* H_blocks,
                             const float* g_blocks, double* T_wc, double* tau, int32_t* dev_status, void* workspace,
                             size_t ws_bytes, void* stream);
+
+/* Kernel launches one mslam_gn_solve call enqueues on this plan: 3 when the
+ * mixed-precision solve (FP32 factorisation of the diagonally scaled system,
+ * FP64 iterative refinement) fits the largest graph in shared memory: its
+ * assembly kernel, the solve, and an FP64 kernel for any graph it declines;
+ * else 1 (FP64 only). */
+int32_t mslam_gn_solve_launches(const mslam_plan* plan);
 
 /* ------------------------------------------------------------------------ */
 /* (a9) Adjoint of the weighted cost (project form; not in the paper).      */

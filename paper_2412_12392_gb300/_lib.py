@@ -46,7 +46,7 @@ class Params(C.Structure):
 class PlanOpts(C.Structure):
     """Mirror of mslam_plan_opts."""
     _fields_ = [("lin_tile", C.c_int32), ("lin_blocks_per_sm", C.c_int32), ("match_block_w", C.c_int32),
-                ("lin_form", C.c_int32)]
+                ("lin_form", C.c_int32), ("solve_form", C.c_int32)]
 
 
 class MslamError(RuntimeError):
@@ -89,6 +89,7 @@ SIGNATURES = {
     "mslam_match_stats": ([vp, vp, vp, vp, vp, sz, vp], C.c_int),
     "mslam_calib_backproject": ([C.c_int, i32, i32, i32, C.c_float, C.c_float, C.c_float, C.c_float, vp, vp],
                                 C.c_int),
+    "mslam_gn_solve_launches": ([vp], i32),
     "mslam_fuse": ([C.c_int, vp, i32, i32, i64, vp, vp, vp, vp, vp], C.c_int),
     "mslam_gn_backward": ([vp, vp, C.c_int, vp, vp, vp, vp, vp, vp, vp, C.c_double, vp, vp, vp, vp, sz, vp],
                           C.c_int),

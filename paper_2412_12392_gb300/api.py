@@ -76,7 +76,8 @@ class Plan:
         lib().mslam_default_plan_opts(C.byref(o))
         for k, v in (opts or {}).items():
             setattr(o, k, int(v))
-        self.opts = {k: getattr(o, k) for k in ("lin_tile", "lin_blocks_per_sm", "match_block_w", "lin_form")}
+        self.opts = {k: getattr(o, k) for k in ("lin_tile", "lin_blocks_per_sm", "match_block_w", "lin_form",
+                                                   "solve_form")}
         self.graph_of_kf = gk
         h = C.c_void_p()
         check(lib().mslam_plan_create_ex(self.N, kf.ctypes.data, self.E, ed.ctypes.data if self.E else None,
@@ -103,6 +104,11 @@ class Plan:
         self.dev = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         check(lib().mslam_plan_upload(self._h, self.dev.data_ptr(), nbytes, _stream(self.device)),
               "mslam_plan_upload")
+
+    @property
+    def solve_launches(self) -> int:
+        """Kernel launches of one gn_solve call (mixed-precision form + FP64 fallback: 2)."""
+        return int(lib().mslam_gn_solve_launches(self._h))
 
     def workspace_bytes(self, op: int) -> int:
         return int(lib().mslam_workspace_bytes(self._h, op))

@@ -35,10 +35,12 @@ def _time(fn, reps: int) -> float:
 
 def autotune(kf_hw, edges, graph_of_kf, params, X_ref, X_qry, D_ref, D_qry, Q_ref, Q_qry, X_canon, T_wc,
              match_widths: Sequence[int] = MATCH_WIDTHS, lin_tiles: Sequence[int] = LIN_TILES,
-             lin_blocks: Sequence[int] = LIN_BLOCKS, reps: int = 3) -> Dict:
-    """Returns {"opts": best plan options, "match_ms": {...}, "lin_ms": {...}}.
-    D_ref / D_qry are chunk-planar (api.chunk_descriptors)."""
-    report = {"match_ms": {}, "lin_ms": {}}
+             lin_blocks: Sequence[int] = LIN_BLOCKS, reps: int = 3, gn_iters: int = 10) -> Dict:
+    """Returns {"opts": best plan options, "match_ms": {...}, "lin_ms": {...},
+    "pack_ms": {...}}.  A linearisation shape is scored by gn_iters
+    linearisations plus one packing (the tile size sets both).  D_ref / D_qry
+    are chunk-planar (api.chunk_descriptors)."""
+    report = {"match_ms": {}, "lin_ms": {}, "pack_ms": {}}
     best_w, best_t = None, float("inf")
     idx = q = None
     for wdt in match_widths:
@@ -54,7 +56,8 @@ def autotune(kf_hw, edges, graph_of_kf, params, X_ref, X_qry, D_ref, D_qry, Q_re
     idx, q = api.match(api.Plan(kf_hw, edges, graph_of_kf), params, X_ref, X_qry, D_ref, D_qry, Q_ref, Q_qry)
     best_lin, best_lt = None, float("inf")
     shapes = [(tile, bps, 1) for tile, bps in itertools.product(lin_tiles, lin_blocks)]
-    shapes += [(tile, 0, 0) for tile in lin_tiles]  # the streamed form runs one CTA per SM
+    # the streamed form runs one CTA per SM and favours large tiles
+    shapes += [(tile, 0, 0) for tile in sorted(set(lin_tiles) | {32768, 65536})]
     for tile, bps, form in shapes:
         plan = api.Plan(kf_hw, edges, graph_of_kf, opts={"lin_tile": tile, "lin_blocks_per_sm": bps,
                                                         "lin_form": form})
@@ -64,10 +67,15 @@ def autotune(kf_hw, edges, graph_of_kf, params, X_ref, X_qry, D_ref, D_qry, Q_re
         def run_lin():
             api.gn_linearize_packed(plan, params, X_canon.dtype, T_wc, packed, workspace=ws)
 
+        def run_pack():
+            api.gn_pack(plan, params, X_canon, idx, q, packed)
+
         ms = _time(run_lin, reps)
+        pms = report["pack_ms"].setdefault(tile, _time(run_pack, reps))
         report["lin_ms"][f"{tile}/{bps}/{'stream' if form == 0 else 'regs'}"] = ms
-        if ms < best_lt:
-            best_lin, best_lt = (tile, bps, form), ms
+        score = gn_iters * ms + pms
+        if score < best_lt:
+            best_lin, best_lt = (tile, bps, form), score
     report["opts"] = {"match_block_w": best_w, "lin_tile": best_lin[0], "lin_blocks_per_sm": best_lin[1],
                       "lin_form": best_lin[2]}
     return report

@@ -48,7 +48,7 @@ struct DevGraph {
   int32_t m;          // non-fixed poses = block rows of the reduced system
   int32_t n_blocks;   // 7x7 blocks of L: m diagonal blocks first, then off-diagonal
   int32_t gauge;      // fixed keyframe (global index)
-  int32_t pad0;
+  int32_t int_end;    // end of this graph's table integers (they start at off_pose)
   int32_t off_pose;   // -> pose_of_pos [m]: global keyframe at elimination position p
   int32_t off_col;    // -> col_ptr [m + 1] (into col_rows / col_blk, relative)
   int32_t off_colent; // -> col_rows, col_blk entries
@@ -68,7 +68,11 @@ struct DevGraph {
   int32_t off_rsptr;  // -> rsptr [m + 1] into row structure
   int32_t off_rs;     // -> (column c, block L(p, c)) of each position p, in column order
   int32_t off_blkcol; // -> [n_blocks] column position of each block
+  int32_t off_blkrow; // -> [n_blocks] row position of each block
+  int32_t pad1;
   int64_t ws_off;     // offset (doubles) of this graph's numeric workspace
+  int64_t ws_mixed;   // offset (doubles) of the mixed-precision solve's inputs: scaled FP32 factor
+                      // [n_blocks][7][8] floats, then S (7 m) and -g (7 m) in FP64
 };
 
 // Device view of a plan (pointers into the uploaded table blob).
@@ -307,7 +311,9 @@ size_t pack_bytes(int n_tiles, int lin_tile, mslam_dtype dt);
 // Persistent-grid size of the linearisation launches (0 = occupancy maximum).
 int plan_lin_blocks_per_sm(const mslam_plan* plan);
 int plan_lin_form(const mslam_plan* plan);  // 0 streamed, 1 register pipeline
+int plan_solve_form(const mslam_plan* plan);  // 0 mixed precision, 1 FP64 only
 int64_t plan_max_mixed_bytes(const mslam_plan* plan);  // shared memory of the mixed-precision solve
+int64_t plan_max_mixed_elems(const mslam_plan* plan);  // elements of its assembly kernel
 int64_t plan_solve_ws_doubles(const mslam_plan* plan);    // FP64 solve workspace of all graphs (doubles)
 int plan_max_image_dim(const mslam_plan* plan);  // largest H or W of the plan's keyframes
 // Host-side per-edge ranges: linearisation tiles [t0, t1), match blocks [b0, b1).

@@ -31,8 +31,11 @@ struct RelPose {
 
 // T_ij = T_i^-1 T_j of every edge in FP64, stored as float s R and t: one
 // thread per edge, once per linearisation (keeps FP64 out of the tile loop).
-__global__ void rel_pose_kernel(PlanView pv, const double* __restrict__ T_wc, RelPose* __restrict__ out) {
+// It also clears the tile counter of the persistent launch that follows.
+__global__ void rel_pose_kernel(PlanView pv, const double* __restrict__ T_wc, RelPose* __restrict__ out,
+                                int* __restrict__ tile_ctr) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e == 0 && tile_ctr) *tile_ctr = 0;
   if (e >= pv.E) return;
   const DevEdge ed = pv.edges[e];
   const Sim3d Ti = load_pose(T_wc + 8 * ed.i), Tj = load_pose(T_wc + 8 * ed.j);
@@ -269,15 +272,31 @@ __device__ __forceinline__ void reduce_store(const float* acc, float (*red)[kFam
 #endif
 constexpr int kUnroll = MSLAM_LIN_UNROLL;  // pixels per thread in flight
 
+// Next work tile of a launch: claimed from a counter (so that tiles of uneven
+// match counts balance across the persistent blocks) or, without a counter,
+// the static grid stride.  Every tile's partial is computed the same way
+// whichever block takes it, so results do not depend on the schedule.
+__device__ __forceinline__ int next_tile(int* s_tile, int* ctr, int tile_begin, int prev) {
+  if (ctr) {
+    __syncthreads();  // every thread has read the previous tile index
+    if (threadIdx.x == 0) *s_tile = tile_begin + atomicAdd(ctr, 1);
+    __syncthreads();
+    return *s_tile;
+  }
+  return prev < 0 ? tile_begin + (int)blockIdx.x : prev + (int)gridDim.x;
+}
+
 template <typename T, int kKind>
 __global__ void __launch_bounds__(kLinThreads, MSLAM_LIN_MINBLOCKS)
     lin_tiles_kernel(PlanView pv, LinConst lc, const RelPose* __restrict__ rel, const T* __restrict__ X,
                      const int32_t* __restrict__ idx, const T* __restrict__ q, float* __restrict__ partials,
-                     int tile_begin, int tile_end) {
+                     int tile_begin, int tile_end, int* __restrict__ tile_ctr) {
   constexpr int NA = FamilyAcc<kKind>::N;
   __shared__ float red[kLinThreads / 32][kFamAcc];
+  __shared__ int s_tile;
   const int tid = threadIdx.x;
-  for (int tile = tile_begin + blockIdx.x; tile < tile_end; tile += gridDim.x) {
+  for (int tile = next_tile(&s_tile, tile_ctr, tile_begin, -1); tile < tile_end;
+       tile = next_tile(&s_tile, tile_ctr, tile_begin, tile)) {
     const DevTile tl = pv.tiles[tile];
     const DevEdge ed = pv.edges[tl.edge];
     RelPose P;
@@ -390,11 +409,15 @@ template <> struct PackRec<float> {
 };
 
 // The storage values are copied bit for bit (FP16 -> float -> FP16 is exact).
+// One 1024-thread block per tile keeps the tile's pixel order (each block
+// compacts 1024 pixels per step: warp ballots, then a scan of the 32 warp
+// counts by one warp).
+constexpr int kPackThreads = 1024;
 template <typename T>
-__global__ void __launch_bounds__(kLinThreads) pack_kernel(PlanView pv, float q_min, int kind, const T* __restrict__ X,
-                                                           const int32_t* __restrict__ idx, const T* __restrict__ q,
-                                                           uint4* __restrict__ recs, int32_t* __restrict__ counts) {
-  __shared__ int warp_tot[kLinThreads / 32];
+__global__ void __launch_bounds__(kPackThreads) pack_kernel(PlanView pv, float q_min, int kind, const T* __restrict__ X,
+                                                            const int32_t* __restrict__ idx, const T* __restrict__ q,
+                                                            uint4* __restrict__ recs, int32_t* __restrict__ counts) {
+  __shared__ int warp_tot[kPackThreads / 32], warp_off[kPackThreads / 32 + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int W = PackRec<T>::kWords;
   for (int tile = blockIdx.x; tile < pv.n_tiles; tile += gridDim.x) {
@@ -406,7 +429,7 @@ __global__ void __launch_bounds__(kLinThreads) pack_kernel(PlanView pv, float q_
     const T* Xi = X + 3 * ed.off_i;
     uint4* out = recs + (size_t)tile * pv.lin_tile * W;
     int base_count = 0;
-    for (int base = tl.begin; base < tl.end; base += kLinThreads) {
+    for (int base = tl.begin; base < tl.end; base += kPackThreads) {
       const int n = base + tid;
       int m = -1;
       float qq = 0.0f;
@@ -429,12 +452,20 @@ __global__ void __launch_bounds__(kLinThreads) pack_kernel(PlanView pv, float q_
       const int rank = __popc(bal & ((1u << lane) - 1u));
       if (lane == 0) warp_tot[warp] = __popc(bal);
       __syncthreads();
-      int off = base_count;
-      for (int w = 0; w < warp; ++w) off += warp_tot[w];
-      int tot = 0;
-      for (int w = 0; w < kLinThreads / 32; ++w) tot += warp_tot[w];
-      if (valid) PackRec<T>::store(out + (size_t)(off + rank) * W, xj, y, qq);
-      base_count += tot;
+      if (warp == 0) {  // exclusive scan of the 32 warp counts
+        const int v = warp_tot[lane];
+        int incl = v;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const int o = __shfl_up_sync(0xffffffffu, incl, off);
+          if (lane >= off) incl += o;
+        }
+        warp_off[lane] = incl - v;
+        if (lane == 31) warp_off[32] = incl;
+      }
+      __syncthreads();
+      if (valid) PackRec<T>::store(out + (size_t)(base_count + warp_off[warp] + rank) * W, xj, y, qq);
+      base_count += warp_off[32];
       __syncthreads();
     }
     if (tid == 0) counts[tile] = base_count;
@@ -447,13 +478,15 @@ __global__ void __launch_bounds__(kLinThreads, MSLAM_PACKED_MINBLOCKS) lin_packe
                                                                    const uint4* __restrict__ recs,
                                                                    const int32_t* __restrict__ counts,
                                                                    float* __restrict__ partials, int tile_begin,
-                                                                   int tile_end) {
+                                                                   int tile_end, int* __restrict__ tile_ctr) {
   constexpr int NA = FamilyAcc<kKind>::N;
   __shared__ float red[kLinThreads / 32][kFamAcc];
+  __shared__ int s_tile;
   const int tid = threadIdx.x;
   constexpr int W = PackRec<T>::kWords;
   constexpr int U = MSLAM_PACKED_UNROLL;
-  for (int tile = tile_begin + blockIdx.x; tile < tile_end; tile += gridDim.x) {
+  for (int tile = next_tile(&s_tile, tile_ctr, tile_begin, -1); tile < tile_end;
+       tile = next_tile(&s_tile, tile_ctr, tile_begin, tile)) {
     const DevTile tl = pv.tiles[tile];
     RelPose P;
     {
@@ -486,31 +519,36 @@ __global__ void __launch_bounds__(kLinThreads, MSLAM_PACKED_MINBLOCKS) lin_packe
 }
 
 // ---------------------------------------------------------- streamed form
-// The packed records of the ray family streamed through shared memory: one
-// persistent CTA per SM walks its tiles' records in 16 KB chunks, which one
-// thread copies ahead with bulk asynchronous copies (TMA, completion counted
-// on an mbarrier per stage), so the loads need no registers and the copies
-// of later chunks overlap the arithmetic of the current one.  Each thread
-// takes two records at a time (r and r + 512 of a chunk) and evaluates both
-// with paired FP32 instructions (__ffma2_rn / __fmul2_rn / __fadd2_rn: one
-// instruction per two lanes of work), which halves the instruction count of the per-match math
-// that otherwise bounds this kernel.  Every paired operation rounds exactly
-// like its scalar form; only the summation order of the per-thread sums
-// differs from lin_packed_kernel.
+// The packed FP16 records of the ray family streamed through shared memory.
+// One persistent CTA per SM claims tiles from the tile counter; one thread
+// copies each tile's 16-byte records ahead in 4096-record (64 KB) chunks
+// with bulk asynchronous copies (TMA, completion counted on an mbarrier per
+// stage), so loads need no registers and later chunks arrive while the
+// current one is computed.  Every thread takes up to four pairs of records
+// per chunk (records j and j + ceil(n/2) of an n-record chunk, consecutive
+// 16-byte words across the warp),
+// builds the half2 pairs (value of record a, value of record b) with byte
+// permutes, and evaluates both records with paired FP32 instructions
+// (__ffma2_rn / __fmul2_rn / __fadd2_rn, one instruction per two lanes of
+// work), which halves the instruction count of the per-match arithmetic
+// that bounds the unpaired kernel.  The Huber weight min(1, delta/e) and
+// cost rho(e) = e^2 h (2 - h) / 2 with h that weight need no branch.  The
+// tile's sums are reduced by a butterfly reduce-scatter (one shuffle per
+// value and round) and a fixed-order sum over the warps.  Every paired
+// operation rounds like its scalar form; results are deterministic and
+// independent of the schedule.
 
 constexpr int kStreamThreads = 512;
-constexpr int kStreamStages = 4;
-constexpr int kStreamChunkBytes = 16384;
+constexpr int kStreamStages = 3;
+constexpr int kStreamPairsPerThread = 4;
+constexpr int kStreamChunkRecs = 2 * kStreamThreads * kStreamPairsPerThread;  // 4096 records
+constexpr int kStreamChunkBytes = kStreamChunkRecs * 16;                     // 64 KB per stage
 constexpr uint32_t kSpinLimit = 1u << 24;  // bounded mbarrier waits (non-blocking polls, about a second)
 
 // Paired FP32 arithmetic (one instruction for two lanes of work).
 using f2 = float2;
 __device__ __forceinline__ f2 mk2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ f2 bc2(float a) { return make_float2(a, a); }
-__device__ __forceinline__ void un2(f2 x, float& a, float& b) {
-  a = x.x;
-  b = x.y;
-}
 __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
@@ -550,63 +588,43 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
-// Two records (lanes a and b of every pair) of the ray family.  va / vb:
-// whether the lane holds a record; an empty lane gets zero weights.
+// Huber weight factor h = min(1, delta / e) of a squared whitened norm, per lane.
+__device__ __forceinline__ float huber_h(float e2, const LinConst& c) {
+  return fminf(1.0f, c.delta * rsqrtf(fmaxf(e2, c.delta2)));
+}
+
+// Two records (lanes a and b) of the ray family; mask = (1 or 0, 1 or 0)
+// selects the lanes that hold a record with x != 0.
 __device__ __forceinline__ void accumulate_pair(f2 acc[kNumAcc], const f2 Rp[12], f2 X0, f2 X1, f2 X2, f2 Y0, f2 Y1,
-                                                f2 Y2, f2 Q, bool va, bool vb, const LinConst& c) {
+                                                f2 Y2, f2 Q, bool vb, const LinConst& c) {
   const f2 x0 = fma2(Rp[0], X0, fma2(Rp[1], X1, fma2(Rp[2], X2, Rp[9])));
   const f2 x1 = fma2(Rp[3], X0, fma2(Rp[4], X1, fma2(Rp[5], X2, Rp[10])));
   const f2 x2 = fma2(Rp[6], X0, fma2(Rp[7], X1, fma2(Rp[8], X2, Rp[11])));
   const f2 d2 = fma2(x0, x0, fma2(x1, x1, mul2(x2, x2)));
   const f2 dy2 = fma2(Y0, Y0, fma2(Y1, Y1, mul2(Y2, Y2)));
-  float d2a, d2b, dy2a, dy2b;
-  un2(d2, d2a, d2b);
-  un2(dy2, dy2a, dy2b);
-  // a lane without a record, or with x = 0, contributes nothing; keep its
-  // arithmetic finite so that zero weights give exact zeros
-  va = va && d2a > 0.0f;
-  vb = vb && d2b > 0.0f;
-  const f2 id = mk2(rsqrtf(va ? d2a : 1.0f), rsqrtf(vb ? d2b : 1.0f));
-  const f2 idy = mk2(rsqrtf(va ? dy2a : 1.0f), rsqrtf(vb ? dy2b : 1.0f));
+  // a lane without a record, or with x = 0, gets zero weights; its
+  // arithmetic stays finite so that zero weights give exact zeros
+  const bool va = d2.x > 0.0f;
+  vb = vb && d2.y > 0.0f;
+  const f2 mask = mk2(va ? 1.0f : 0.0f, vb ? 1.0f : 0.0f);
+  const f2 id = mk2(rsqrtf(va ? d2.x : 1.0f), rsqrtf(vb ? d2.y : 1.0f));
+  const f2 idy = mk2(rsqrtf(va ? dy2.x : 1.0f), rsqrtf(vb ? dy2.y : 1.0f));
   const f2 m1 = bc2(-1.0f);
   const f2 d = mul2(d2, id), dy = mul2(dy2, idy);
   const f2 u0 = mul2(x0, id), u1 = mul2(x1, id), u2 = mul2(x2, id);
   const f2 nidy = mul2(idy, m1);
   const f2 r0 = fma2(Y0, nidy, u0), r1 = fma2(Y1, nidy, u1), r2 = fma2(Y2, nidy, u2);
   const f2 rd = fma2(dy, m1, d);
-  const f2 lr = mul2(Q, bc2(c.inv_sr2)), ld = mul2(Q, bc2(c.inv_sd2));
+  const f2 qm = mul2(Q, mask);
+  const f2 lr = mul2(qm, bc2(c.inv_sr2)), ld = mul2(qm, bc2(c.inv_sd2));
   const f2 er2 = mul2(lr, fma2(r0, r0, fma2(r1, r1, mul2(r2, r2))));
   const f2 ed2 = mul2(ld, mul2(rd, rd));
-  // Huber weights and cost per lane (the quadratic region needs no root)
-  float er2a, er2b, ed2a, ed2b, lra, lrb, lda, ldb;
-  un2(er2, er2a, er2b);
-  un2(ed2, ed2a, ed2b);
-  un2(lr, lra, lrb);
-  un2(ld, lda, ldb);
-  float ca = 0.5f * (er2a + ed2a), cb = 0.5f * (er2b + ed2b);
-  float wra = lra, wrb = lrb, wda = lda, wdb = ldb;
-  if (er2a > c.delta2) {
-    const float ir = rsqrtf(er2a);
-    wra = lra * c.delta * ir;
-    ca += c.delta * (er2a * ir - 0.5f * c.delta) - 0.5f * er2a;
-  }
-  if (er2b > c.delta2) {
-    const float ir = rsqrtf(er2b);
-    wrb = lrb * c.delta * ir;
-    cb += c.delta * (er2b * ir - 0.5f * c.delta) - 0.5f * er2b;
-  }
-  if (ed2a > c.delta2) {
-    const float ie = rsqrtf(ed2a);
-    wda = lda * c.delta * ie;
-    ca += c.delta * (ed2a * ie - 0.5f * c.delta) - 0.5f * ed2a;
-  }
-  if (ed2b > c.delta2) {
-    const float ie = rsqrtf(ed2b);
-    wdb = ldb * c.delta * ie;
-    cb += c.delta * (ed2b * ie - 0.5f * c.delta) - 0.5f * ed2b;
-  }
-  const f2 wr = mk2(va ? wra : 0.0f, vb ? wrb : 0.0f);
-  const f2 wd = mk2(va ? wda : 0.0f, vb ? wdb : 0.0f);
+  const f2 hr = mk2(huber_h(er2.x, c), huber_h(er2.y, c));
+  const f2 hd = mk2(huber_h(ed2.x, c), huber_h(ed2.y, c));
+  const f2 two = bc2(2.0f), half = bc2(0.5f);
+  // rho = e^2 h (2 - h) / 2 in both Huber regions
+  const f2 cost = fma2(mul2(half, er2), mul2(hr, fma2(hr, m1, two)), mul2(mul2(half, ed2), mul2(hd, fma2(hd, m1, two))));
+  const f2 wr = mul2(lr, hr), wd = mul2(ld, hd);
   const f2 A = mul2(wr, mul2(id, id));
   acc[0] = add2(acc[0], A);
   const f2 cc = fma2(A, m1, wd);
@@ -642,72 +660,69 @@ __device__ __forceinline__ void accumulate_pair(f2 acc[kNumAcc], const f2 Rp[12]
   acc[25] = fma2(ad, fma2(nx0, r2, mul2(x2, r0)), acc[25]);
   acc[26] = fma2(ad, fma2(nx1, r0, mul2(x0, r1)), acc[26]);
   acc[27] = fma2(wdr, d, acc[27]);
-  acc[28] = add2(acc[28], mk2(va ? ca : 0.0f, vb ? cb : 0.0f));
-  acc[29] = add2(acc[29], mk2(va ? 1.0f : 0.0f, vb ? 1.0f : 0.0f));
+  acc[28] = add2(acc[28], cost);
+  acc[29] = add2(acc[29], mask);
 }
 
-template <typename T> struct StreamRec;
-template <> struct StreamRec<__half> {
-  static constexpr int kBytes = 16;
-  static __device__ __forceinline__ void load(const unsigned char* base, int r, float v[7]) {
-    const uint4 w = *reinterpret_cast<const uint4*>(base + 16 * r);
-    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&w.x));
-    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&w.y));
-    const float2 cc = __half22float2(*reinterpret_cast<const __half2*>(&w.z));
-    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = cc.x; v[5] = cc.y;
-    v[6] = __half2float(*reinterpret_cast<const __half*>(&w.w));
+// Warp reduce-scatter of 32 values: after five butterfly rounds (one
+// shuffle per kept value and round) lane L holds the warp's sum of value L.
+__device__ __forceinline__ float warp_reduce_scatter(float v[32], int lane) {
+#pragma unroll
+  for (int round = 0; round < 5; ++round) {
+    const int half = 16 >> round;
+    const bool up = (lane & half) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const float send = up ? v[i] : v[i + half];
+      const float keep = up ? v[i + half] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, half);
+    }
   }
-};
-template <> struct StreamRec<float> {
-  static constexpr int kBytes = 32;
-  static __device__ __forceinline__ void load(const unsigned char* base, int r, float v[7]) {
-    const float4 a = *reinterpret_cast<const float4*>(base + 32 * r);
-    const float4 b = *reinterpret_cast<const float4*>(base + 32 * r + 16);
-    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z;
-  }
-};
+  return v[0];
+}
 
-template <typename T>
 __global__ void __launch_bounds__(kStreamThreads, 1)
     lin_stream_kernel(PlanView pv, LinConst lc, const RelPose* __restrict__ rel, const unsigned char* __restrict__ recs,
-                      const int32_t* __restrict__ counts, float* __restrict__ partials, int tile_begin, int tile_end) {
-  constexpr int RB = StreamRec<T>::kBytes;
-  constexpr int CR = kStreamChunkBytes / RB;  // records per chunk
+                      const int32_t* __restrict__ counts, float* __restrict__ partials, int tile_begin, int tile_end,
+                      int* __restrict__ tile_ctr) {
   extern __shared__ __align__(128) unsigned char stage[];
   __shared__ __align__(8) uint64_t full[kStreamStages];
-  __shared__ int m_tile[kStreamStages], m_n[kStreamStages], m_last[kStreamStages];
-  __shared__ float red[kStreamThreads / 32][kNumAcc];
+  __shared__ int m_tile[kStreamStages], m_np[kStreamStages], m_last[kStreamStages];
+  __shared__ float red[kStreamThreads / 32][32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  // producer state (thread 0): the next chunk to copy
-  int p_tile = tile_begin + blockIdx.x, p_off = 0;
+  // producer state (thread 0): the tile being copied and its next pair
+  int p_tile = -1, p_cnt = 0, p_off = 0;
+  auto claim = [&]() {
+    p_tile = tile_ctr ? tile_begin + atomicAdd(tile_ctr, 1) : (p_tile < 0 ? tile_begin + (int)blockIdx.x
+                                                                          : p_tile + (int)gridDim.x);
+    p_off = 0;
+    p_cnt = p_tile < tile_end ? __ldg(counts + p_tile) : 0;
+  };
   auto issue = [&](int slot) {
     if (p_tile >= tile_end) {  // end marker
       m_tile[slot] = -1;
       mbar_arrive(&full[slot]);
       return;
     }
-    const int cnt = __ldg(counts + p_tile);
-    const int n = min(CR, cnt - p_off);
+    const int n = min(kStreamChunkRecs, p_cnt - p_off);
     m_tile[slot] = p_tile;
-    m_n[slot] = n;
-    m_last[slot] = (p_off + n >= cnt);
+    m_np[slot] = n;
+    m_last[slot] = (p_off + n >= p_cnt);
     if (n > 0) {
-      mbar_arrive_tx(&full[slot], (uint32_t)(n * RB));
-      bulk_g2s(stage + slot * kStreamChunkBytes, recs + ((size_t)p_tile * pv.lin_tile + p_off) * RB,
-               (uint32_t)(n * RB), &full[slot]);
+      mbar_arrive_tx(&full[slot], (uint32_t)(n * 16));
+      bulk_g2s(stage + slot * kStreamChunkBytes, recs + ((size_t)p_tile * pv.lin_tile + p_off) * 16,
+               (uint32_t)(n * 16), &full[slot]);
     } else {
       mbar_arrive(&full[slot]);
     }
     p_off += n;
-    if (p_off >= cnt) {
-      p_tile += gridDim.x;
-      p_off = 0;
-    }
+    if (p_off >= p_cnt) claim();
   };
   if (tid == 0) {
     for (int sl = 0; sl < kStreamStages; ++sl) mbar_init(&full[sl], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    claim();
     for (int sl = 0; sl < kStreamStages; ++sl) issue(sl);
   }
   __syncthreads();
@@ -728,7 +743,6 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
     }
     const int tile = m_tile[slot];
     if (tile < 0) break;
-    const int n = m_n[slot];
     if (tile != cur_tile) {
       const float4* src = reinterpret_cast<const float4*>(rel + pv.tiles[tile].edge);
       const float4 a = __ldg(src), b = __ldg(src + 1), c4 = __ldg(src + 2);
@@ -737,33 +751,37 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
       Rp[8] = bc2(c4.x); Rp[9] = bc2(c4.y); Rp[10] = bc2(c4.z); Rp[11] = bc2(c4.w);
       cur_tile = tile;
     }
-    const unsigned char* base = stage + slot * kStreamChunkBytes;
-    for (int r0 = 0; r0 < n; r0 += 2 * kStreamThreads) {
-      const int ra = r0 + tid, rb = r0 + kStreamThreads + tid;
-      const bool va = ra < n, vb = rb < n;
-      if (!va) continue;
-      float A[7], B[7];
-      StreamRec<T>::load(base, ra, A);
-      if (vb)
-        StreamRec<T>::load(base, rb, B);
-      else
+    {
+      // record layout (FP16): {X_j.x, X_j.y}, {X_j.z, y.x}, {y.y, y.z}, {q, 0}
+      const int n = m_np[slot], h = (n + 1) >> 1;  // records j and j + h form pair j
+      const uint4* rec = reinterpret_cast<const uint4*>(stage + slot * kStreamChunkBytes);
 #pragma unroll
-        for (int e = 0; e < 7; ++e) B[e] = A[e];
-      accumulate_pair(acc, Rp, mk2(A[0], B[0]), mk2(A[1], B[1]), mk2(A[2], B[2]), mk2(A[3], B[3]), mk2(A[4], B[4]),
-                      mk2(A[5], B[5]), mk2(A[6], B[6]), true, vb, lc);
+      for (int u = 0; u < kStreamPairsPerThread; ++u) {
+        const int ra = tid + u * kStreamThreads, rb = ra + h;
+        if (ra < h) {
+          const bool vb = rb < n;
+          const uint4 a = rec[ra], b = vb ? rec[rb] : make_uint4(0u, 0u, 0u, 0u);
+          auto pr = [](uint32_t x, uint32_t y, uint32_t sel) {
+            const uint32_t v = __byte_perm(x, y, sel);
+            return __half22float2(*reinterpret_cast<const __half2*>(&v));
+          };
+          accumulate_pair(acc, Rp, pr(a.x, b.x, 0x5410), pr(a.x, b.x, 0x7632), pr(a.y, b.y, 0x5410),
+                          pr(a.y, b.y, 0x7632), pr(a.z, b.z, 0x5410), pr(a.z, b.z, 0x7632), pr(a.w, b.w, 0x5410),
+                          vb, lc);
+        }
+      }
     }
     if (m_last[slot]) {
-      // the tile is complete: fixed-order reduction into its partial slot
+      // the tile is complete: reduce-scatter in each warp, then the warps'
+      // sums in a fixed order into the tile's partial slot
+      float v[32];
 #pragma unroll
       for (int a = 0; a < kNumAcc; ++a) {
-        float lo, hi;
-        un2(acc[a], lo, hi);
-        float v = lo + hi;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if (lane == 0) red[warp][a] = v;
+        v[a] = acc[a].x + acc[a].y;
         acc[a] = mk2(0.0f, 0.0f);
       }
+      v[30] = v[31] = 0.0f;
+      red[warp][lane] = warp_reduce_scatter(v, lane);
       __syncthreads();
       if (tid < kNumAcc) {
         float sum = red[0][tid];
@@ -779,10 +797,10 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
     }
   }
   if (aborted) {
-    // a copy did not complete in time: poison this CTA's tiles (the solve
-    // then reports a non-finite system) and let in-flight copies land
+    // a copy did not complete in time: poison every tile's partial (the
+    // solve then reports a non-finite system) and let in-flight copies land
     // before the CTA's shared memory is released
-    for (int t = tile_begin + blockIdx.x + tid * (int)gridDim.x; t < tile_end; t += kStreamThreads * (int)gridDim.x)
+    for (int t = tile_begin + tid; t < tile_end; t += kStreamThreads)
       partials[(size_t)t * kAccStride] = __int_as_float(0x7fc00000);
     if (tid == 0)
       for (int sl = 0; sl < kStreamStages; ++sl) mbar_wait_bounded(&full[sl], 0), mbar_wait_bounded(&full[sl], 1);
@@ -877,6 +895,13 @@ __global__ void __launch_bounds__(64) lin_finalize_kernel(PlanView pv, const dou
   }
 }
 
+// The tile counter of the persistent launches: after the relative poses in
+// the linearisation workspace.
+static int* tile_counter(RelPose* rel, int E) {
+  return reinterpret_cast<int*>(reinterpret_cast<char*>(rel) + ((sizeof(RelPose) * (size_t)std::max(E, 1) + 255) &
+                                                                ~size_t(255)));
+}
+
 // Blocks of a persistent linearisation launch: the plan's blocks per SM, or
 // the occupancy maximum of the kernel.
 template <typename K>
@@ -894,6 +919,13 @@ static int persistent_grid(const mslam_plan* plan, K kernel) {
 
 using namespace mslam;
 
+// Whether the packed linearisation of these parameters and plan takes the
+// streamed form (the FP16 ray family with plan option lin_form 0), whose
+// records mslam_gn_pack writes in pairs.
+static bool stream_form(const mslam_params* p, const mslam_plan* plan, mslam_dtype dt) {
+  return p->residual == MSLAM_RES_RAY && dt == MSLAM_F16 && plan_lin_form(plan) == 0;
+}
+
 // Opt the streamed kernels into their dynamic shared memory, once per device.
 static mslam_status stream_kernel_setup(size_t smem) {
   static std::mutex mu;
@@ -903,10 +935,7 @@ static mslam_status stream_kernel_setup(size_t smem) {
   if (st != MSLAM_OK) return st;
   std::lock_guard<std::mutex> lock(mu);
   if (dev >= 0 && dev < 64 && done[dev]) return MSLAM_OK;
-  st = cuda_check(cudaFuncSetAttribute(lin_stream_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                  "cudaFuncSetAttribute");
-  if (st != MSLAM_OK) return st;
-  st = cuda_check(cudaFuncSetAttribute(lin_stream_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+  st = cuda_check(cudaFuncSetAttribute(lin_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                   "cudaFuncSetAttribute");
   if (st != MSLAM_OK) return st;
   if (dev >= 0 && dev < 64) done[dev] = true;
@@ -987,28 +1016,30 @@ extern "C" mslam_status mslam_gn_linearize(const mslam_params* p, const mslam_pl
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   float* partials = static_cast<float*>(workspace);
   RelPose* rel = reinterpret_cast<RelPose*>(static_cast<char*>(workspace) + lin_partials_bytes(pv.n_tiles));
-  rel_pose_kernel<<<(pv.E + 127) / 128, 128, 0, s>>>(pv, T_wc, rel);
+  int* ctr = tile_counter(rel, pv.E);
+  rel_pose_kernel<<<(pv.E + 127) / 128, 128, 0, s>>>(pv, T_wc, rel, ctr);
   with_family(p->residual, [&](auto K) {
     constexpr int kK = decltype(K)::value;
-    auto launch = [&](int grid, int t0, int t1) {
+    auto launch = [&](int grid, int t0, int t1, int* c) {
       if (dt == MSLAM_F32)
         lin_tiles_kernel<float, kK><<<grid, kLinThreads, 0, s>>>(pv, lc, rel, static_cast<const float*>(X_canon),
-                                                                idx, static_cast<const float*>(q), partials, t0, t1);
+                                                                idx, static_cast<const float*>(q), partials, t0, t1,
+                                                                c);
       else
         lin_tiles_kernel<__half, kK><<<grid, kLinThreads, 0, s>>>(pv, lc, rel, static_cast<const __half*>(X_canon),
                                                                  idx, static_cast<const __half*>(q), partials, t0,
-                                                                 t1);
+                                                                 t1, c);
     };
     if (flags & MSLAM_FLAG_PER_EDGE) {
       // plain form: a host loop of per-edge launches
       for (int e = 0; e < pv.E; ++e) {
         int t0, t1;
         plan_edge_tiles(plan, e, &t0, &t1);
-        launch(t1 - t0, t0, t1);
+        launch(t1 - t0, t0, t1, nullptr);
         lin_finalize_kernel<<<1, 64, 0, s>>>(pv, T_wc, partials, H_blocks, g_blocks, cost, n_valid, e, kK);
       }
     } else {
-      launch(std::min(pv.n_tiles, persistent_grid(plan, lin_tiles_kernel<float, kK>)), 0, pv.n_tiles);
+      launch(std::min(pv.n_tiles, persistent_grid(plan, lin_tiles_kernel<float, kK>)), 0, pv.n_tiles, ctr);
       lin_finalize_kernel<<<pv.E, 64, 0, s>>>(pv, T_wc, partials, H_blocks, g_blocks, cost, n_valid, 0, kK);
     }
   });
@@ -1059,10 +1090,10 @@ extern "C" mslam_status mslam_gn_pack(const mslam_params* p, const mslam_plan* p
   int32_t* counts = reinterpret_cast<int32_t*>(static_cast<char*>(packed) + pack_bytes(pv.n_tiles, pv.lin_tile, dt) -
                                                (((size_t)pv.n_tiles * sizeof(int32_t) + 255) & ~size_t(255)));
   if (dt == MSLAM_F32)
-    pack_kernel<float><<<pv.n_tiles, kLinThreads, 0, s>>>(pv, p->q_min, p->residual, static_cast<const float*>(X_canon), idx,
+    pack_kernel<float><<<pv.n_tiles, kPackThreads, 0, s>>>(pv, p->q_min, p->residual, static_cast<const float*>(X_canon), idx,
                                                           static_cast<const float*>(q), recs, counts);
   else
-    pack_kernel<__half><<<pv.n_tiles, kLinThreads, 0, s>>>(pv, p->q_min, p->residual, static_cast<const __half*>(X_canon), idx,
+    pack_kernel<__half><<<pv.n_tiles, kPackThreads, 0, s>>>(pv, p->q_min, p->residual, static_cast<const __half*>(X_canon), idx,
                                                            static_cast<const __half*>(q), recs, counts);
   return cuda_check(cudaGetLastError(), "gn_pack launch");
 }
@@ -1106,35 +1137,33 @@ extern "C" mslam_status mslam_gn_linearize_packed(const mslam_params* p, const m
   const int32_t* counts = reinterpret_cast<const int32_t*>(
       static_cast<const char*>(packed) + pack_bytes(pv.n_tiles, pv.lin_tile, dt) -
       (((size_t)pv.n_tiles * sizeof(int32_t) + 255) & ~size_t(255)));
-  rel_pose_kernel<<<(pv.E + 127) / 128, 128, 0, s>>>(pv, T_wc, rel);
+  int* ctr = tile_counter(rel, pv.E);
+  rel_pose_kernel<<<(pv.E + 127) / 128, 128, 0, s>>>(pv, T_wc, rel, ctr);
   const size_t stream_smem = (size_t)kStreamStages * kStreamChunkBytes;
-  const bool streamed = p->residual == MSLAM_RES_RAY && plan_lin_form(plan) == 0;
+  const bool streamed = stream_form(p, plan, dt);
   if (streamed) {
     mslam_status st2 = stream_kernel_setup(stream_smem);
     if (st2 != MSLAM_OK) return st2;
   }
   with_family(p->residual, [&](auto K) {
     constexpr int kK = decltype(K)::value;
-    auto launch = [&](int grid, int t0, int t1) {
+    auto launch = [&](int grid, int t0, int t1, int* c) {
       if (kK == MSLAM_RES_RAY && streamed) {
-        // the ray family streams its records through shared memory
-        const unsigned char* rb = static_cast<const unsigned char*>(packed);
-        if (dt == MSLAM_F32)
-          lin_stream_kernel<float><<<grid, kStreamThreads, stream_smem, s>>>(pv, lc, rel, rb, counts, partials, t0, t1);
-        else
-          lin_stream_kernel<__half><<<grid, kStreamThreads, stream_smem, s>>>(pv, lc, rel, rb, counts, partials, t0, t1);
+        // the FP16 ray family streams its paired records through shared memory
+        lin_stream_kernel<<<grid, kStreamThreads, stream_smem, s>>>(pv, lc, rel, static_cast<const unsigned char*>(packed),
+                                                                   counts, partials, t0, t1, c);
         return;
       }
       if (dt == MSLAM_F32)
-        lin_packed_kernel<float, kK><<<grid, kLinThreads, 0, s>>>(pv, lc, rel, recs, counts, partials, t0, t1);
+        lin_packed_kernel<float, kK><<<grid, kLinThreads, 0, s>>>(pv, lc, rel, recs, counts, partials, t0, t1, c);
       else
-        lin_packed_kernel<__half, kK><<<grid, kLinThreads, 0, s>>>(pv, lc, rel, recs, counts, partials, t0, t1);
+        lin_packed_kernel<__half, kK><<<grid, kLinThreads, 0, s>>>(pv, lc, rel, recs, counts, partials, t0, t1, c);
     };
     if (flags & MSLAM_FLAG_PER_EDGE) {
       for (int e = 0; e < pv.E; ++e) {
         int t0, t1;
         plan_edge_tiles(plan, e, &t0, &t1);
-        launch(t1 - t0, t0, t1);
+        launch(t1 - t0, t0, t1, nullptr);
         lin_finalize_kernel<<<1, 64, 0, s>>>(pv, T_wc, partials, H_blocks, g_blocks, cost, n_valid, e, kK);
       }
     } else {
@@ -1145,7 +1174,7 @@ extern "C" mslam_status mslam_gn_linearize_packed(const mslam_params* p, const m
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         grid = std::max(1, sms);  // one streaming CTA per SM
       }
-      launch(std::min(pv.n_tiles, grid), 0, pv.n_tiles);
+      launch(std::min(pv.n_tiles, grid), 0, pv.n_tiles, ctr);
       lin_finalize_kernel<<<pv.E, 64, 0, s>>>(pv, T_wc, partials, H_blocks, g_blocks, cost, n_valid, 0, kK);
     }
   });

@@ -23,8 +23,9 @@ struct mslam_plan {
   std::vector<int32_t> order;
   int64_t n_blocks_total = 0, n_trips_total = 0, solve_ws_doubles = 0, max_graph_doubles = 0;
   int64_t max_mixed_bytes = 0;  // shared memory of the mixed-precision solve for the largest graph
+  int64_t max_mixed_elems = 0;  // elements its assembly kernel covers for the largest graph
   int32_t max_levels = 0;
-  int32_t lin_tile = 0, lin_blocks_per_sm = 0, match_bx = 0, match_by = 0, lin_form = 0;
+  int32_t lin_tile = 0, lin_blocks_per_sm = 0, match_bx = 0, match_by = 0, lin_form = 0, solve_form = 0;
   int32_t n_mblocks = 0;
   void* dev = nullptr;
   size_t dev_bytes = 0;
@@ -91,9 +92,11 @@ void plan_edge_mblocks(const mslam_plan* plan, int e, int* b0, int* b1) {
 
 int64_t plan_max_graph_doubles(const mslam_plan* plan) { return plan->max_graph_doubles; }
 int64_t plan_max_mixed_bytes(const mslam_plan* plan) { return plan->max_mixed_bytes; }
+int64_t plan_max_mixed_elems(const mslam_plan* plan) { return plan->max_mixed_elems; }
 int64_t plan_solve_ws_doubles(const mslam_plan* plan) { return plan->solve_ws_doubles; }
 int plan_lin_blocks_per_sm(const mslam_plan* plan) { return plan->lin_blocks_per_sm; }
 int plan_lin_form(const mslam_plan* plan) { return plan->lin_form; }
+int plan_solve_form(const mslam_plan* plan) { return plan->solve_form; }
 int plan_max_image_dim(const mslam_plan* plan) {
   int m = 0;
   for (int v : plan->kf_hw) m = std::max(m, v);
@@ -331,6 +334,15 @@ static void build_graph(mslam_plan* P, int g, const std::vector<int>& kfs) {
   }
   dg.off_gasment = (int32_t)I.size();
   for (auto& v : gasm) I.insert(I.end(), v.begin(), v.end());
+  dg.int_end = (int32_t)I.size();
+  dg.off_blkrow = (int32_t)I.size();  // [n_blocks] row position of each block
+  {
+    std::vector<int32_t> br(nb_total, 0);
+    for (int b = 0; b < m; ++b) br[b] = b;
+    for (int p = 0; p < m; ++p)
+      for (int r : rows[p]) br[blk[{r, p}]] = r;
+    I.insert(I.end(), br.begin(), br.end());
+  }
 
   dg.ws_off = P->solve_ws_doubles;
   // numeric workspace: blocks (49 each), rhs (7 m), assembled diagonal (7 m),
@@ -338,8 +350,17 @@ static void build_graph(mslam_plan* P, int g, const std::vector<int>& kfs) {
   const int64_t need = (int64_t)nb_total * 49 + 21 * (int64_t)m;
   P->solve_ws_doubles += need;
   P->max_graph_doubles = std::max(P->max_graph_doubles, need);
-  // mixed-precision solve: S, x, b (FP64), the FP32 factor, y and pivots, block rows
-  P->max_mixed_bytes = std::max(P->max_mixed_bytes, (int64_t)(32 * 7 * (int64_t)m + 4 * 50 * (int64_t)nb_total));
+  // inputs of the mixed-precision solve, written by its assembly kernel:
+  // the scaled FP32 factor (7 x 8 floats per block), S and -g
+  P->solve_ws_doubles = (P->solve_ws_doubles + 3) & ~int64_t(3);  // 32-byte aligned for vector loads
+  dg.ws_mixed = P->solve_ws_doubles;
+  P->solve_ws_doubles += (int64_t)nb_total * 28 + 14 * (int64_t)m;
+  // its shared memory: S, x, -g (FP64), the padded FP32 factor, y and
+  // pivots, and the graph's tables except the update triples
+  const int64_t table_ints = (int64_t)(dg.off_trip - dg.off_pose) + (int64_t)(dg.int_end - dg.off_lev);
+  P->max_mixed_bytes = std::max(P->max_mixed_bytes,
+                                (int64_t)(32 * 7 * (int64_t)m + 224 * (int64_t)nb_total + 4 * table_ints + 16));
+  P->max_mixed_elems = std::max(P->max_mixed_elems, (int64_t)nb_total * 56 + 7 * (int64_t)m);
   P->n_blocks_total += nb_total;
   P->graphs.push_back(dg);
 }
@@ -383,6 +404,7 @@ void mslam_default_plan_opts(mslam_plan_opts* o) {
   o->lin_blocks_per_sm = 0;
   o->match_block_w = kMatchBX;
   o->lin_form = 0;
+  o->solve_form = 0;
 }
 
 mslam_status mslam_plan_create(int32_t N, const int32_t* kf_hw, int32_t E, const int32_t* edges,
@@ -398,10 +420,10 @@ mslam_status mslam_plan_create_ex(int32_t N, const int32_t* kf_hw, int32_t E, co
   if (o.lin_tile < 1024 || o.lin_tile > 65536 || (o.lin_tile % kLinThreads) != 0 || o.lin_blocks_per_sm < 0 ||
       o.lin_blocks_per_sm > 32 || (o.match_block_w != 16 && o.match_block_w != 32 && o.match_block_w != 64 &&
                                    o.match_block_w != 128 && o.match_block_w != 256) ||
-      (o.lin_form != 0 && o.lin_form != 1)) {
+      (o.lin_form != 0 && o.lin_form != 1) || (o.solve_form != 0 && o.solve_form != 1)) {
     set_error("plan options: lin_tile %d (multiple of %d in [1024, 65536]), lin_blocks_per_sm %d (0..32), "
-              "match_block_w %d (16, 32, 64, 128 or 256), lin_form %d (0 or 1)", o.lin_tile, kLinThreads,
-              o.lin_blocks_per_sm, o.match_block_w, o.lin_form);
+              "match_block_w %d (16, 32, 64, 128 or 256), lin_form %d, solve_form %d (0 or 1)", o.lin_tile,
+              kLinThreads, o.lin_blocks_per_sm, o.match_block_w, o.lin_form, o.solve_form);
     if (out) *out = nullptr;
     return MSLAM_ERR_ARG;
   }
@@ -418,6 +440,7 @@ mslam_status mslam_plan_create_ex(int32_t N, const int32_t* kf_hw, int32_t E, co
   P->lin_tile = o.lin_tile;
   P->lin_blocks_per_sm = o.lin_blocks_per_sm;
   P->lin_form = o.lin_form;
+  P->solve_form = o.solve_form;
   P->match_bx = o.match_block_w;
   P->match_by = kMatchThreads / o.match_block_w;
   P->N = N;
@@ -548,7 +571,8 @@ size_t mslam_workspace_bytes(const mslam_plan* plan, int32_t op) {
   if (!plan) return 0;
   switch (op) {
     case MSLAM_OP_LINEARIZE:
-      return lin_partials_bytes((int)plan->tiles.size()) + align256(sizeof(float) * 16 * std::max(plan->E, 1));
+      // tile partials, relative poses, the tile counter
+      return lin_partials_bytes((int)plan->tiles.size()) + align256(sizeof(float) * 16 * std::max(plan->E, 1)) + 256;
     case MSLAM_OP_SOLVE:  // per-graph FP64 blocks and vectors, then one flag per graph
       return align256(sizeof(double) * std::max<int64_t>(plan->solve_ws_doubles, 1)) +
              align256(sizeof(int32_t) * std::max<size_t>(plan->graphs.size(), 1));

@@ -565,7 +565,7 @@ __global__ void __launch_bounds__(kSolveThreads) solve_cluster_kernel(PlanView p
 // S H S (unit diagonal) is factored in FP32 with the level schedule above;
 // then x <- x + S (L L^T)^-1 S (b - H x), the residual b - H x formed in FP64
 // from the assembled FP64 blocks, until the predicted next correction
-// (the last correction times the observed contraction rate) is below 1e-10
+// (the last correction times the observed contraction rate) is below 1e-9
 // of |x|.  Each FP32 operation has a latency of a few cycles instead of about
 // 64 for FP64 on this GPU, which shortens the solve's dependent chains; the
 // refined solution is the FP64 solution of the same system.  A graph whose
@@ -574,10 +574,91 @@ __global__ void __launch_bounds__(kSolveThreads) solve_cluster_kernel(PlanView p
 // which applies the exact not-positive-definite rule.
 constexpr int kMixThreads = 512;
 constexpr int kMixMaxIters = 10;
+constexpr int kLfBlock = 56;  // FP32 factor block: 7 rows of 8 floats (the 8th is 0), 32-byte rows
+
+// One element of an assembled block, summed in FP64 over its edge
+// contributions in edge order (as in the FP64 kernel).
+__device__ __forceinline__ double asm_sum(const float* __restrict__ H14, const int32_t* __restrict__ asm_ptr,
+                                          const int32_t* __restrict__ asment, int b, int r, int c) {
+  double s = 0.0;
+  const int k1 = __ldg(asm_ptr + b + 1);
+  for (int k = __ldg(asm_ptr + b); k < k1; ++k) {
+    const int code = __ldg(asment + k), edge = code >> 2, quad = code & 3;
+    const int r0 = (quad == 0 || quad == 2) ? 0 : 7;
+    const int c0 = (quad == 0 || quad == 3) ? 0 : 7;
+    s += (double)__ldg(H14 + (size_t)edge * 196 + (r0 + r) * 14 + c0 + c);
+  }
+  return s;
+}
+
+// Inputs of the mixed-precision solve, one thread per element over many
+// CTAs (the FP64 rate of a single SM would make this the solve's longest
+// phase): every block element in FP64 (kept for the residuals), the scaling
+// S = D^-1/2 of its row and column from the assembled diagonal, the scaled
+// FP32 factor input (S H S, unit diagonal) and -g.  A diagonal entry that is
+// not positive and finite leaves S = NaN, which makes the solve decline the
+// graph.
+__global__ void __launch_bounds__(256) solve_assemble_kernel(PlanView pv, const float* __restrict__ H14,
+                                                             const float* __restrict__ g14,
+                                                             const int32_t* __restrict__ dev_status,
+                                                             double* __restrict__ ws) {
+  const int g = blockIdx.y;
+  const DevGraph G = pv.graphs[g];
+  if (dev_status[g] > 0 || G.m == 0) return;  // the solve kernels skip these graphs too
+  const int nb = G.n_blocks, n7 = 7 * G.m;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nb * kLfBlock + n7) return;
+  const int32_t* I = pv.ints;
+  const int32_t* asm_ptr = I + G.off_asm;
+  const int32_t* asment = I + G.off_asment;
+  float* Lf = reinterpret_cast<float*>(ws + G.ws_mixed);
+  double* scl = ws + G.ws_mixed + (size_t)nb * 28;
+  double* bv = scl + n7;
+  if (t < nb * kLfBlock) {
+    const int b = t / kLfBlock, e = t % kLfBlock, r = e / 8, c = e % 8;
+    if (c == 7) {
+      Lf[t] = 0.0f;
+      return;
+    }
+    const double h = asm_sum(H14, asm_ptr, asment, b, r, c);
+    ws[G.ws_off + 49 * (size_t)b + 7 * r + c] = h;
+    const int br = __ldg(I + G.off_blkrow + b), bc = __ldg(I + G.off_blkcol + b);
+    const double dr = asm_sum(H14, asm_ptr, asment, br, r, r), dc = asm_sum(H14, asm_ptr, asment, bc, c, c);
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    const double sr = (dr > 0.0 && isfinite(dr)) ? rsqrt_newton(dr) : nan;
+    const double sc = (dc > 0.0 && isfinite(dc)) ? rsqrt_newton(dc) : nan;
+    Lf[t] = (float)(h * sr * sc);
+    if (b < G.m && r == c) scl[7 * b + r] = sr;
+  } else {
+    const int k = t - nb * kLfBlock, p = k / 7, a = k % 7;
+    const int32_t* gasm_ptr = I + G.off_gasm;
+    const int32_t* gasment = I + G.off_gasment;
+    double sg = 0.0;
+    for (int j = __ldg(gasm_ptr + p); j < __ldg(gasm_ptr + p + 1); ++j) {
+      const int code = __ldg(gasment + j), edge = code >> 1, side = code & 1;
+      sg += (double)__ldg(g14 + (size_t)edge * 14 + 7 * side + a);
+    }
+    bv[k] = -sg;
+  }
+}
+
+// Deterministic sum of the four 7-lane groups of a warp into lanes 0..6
+// (lane a + 7 g holds group g's partial for row a).
+__device__ __forceinline__ float sum_groups(float v) {
+  const float v1 = __shfl_down_sync(0xffffffffu, v, 7);
+  const float v2 = __shfl_down_sync(0xffffffffu, v, 14);
+  const float v3 = __shfl_down_sync(0xffffffffu, v, 21);
+  return (v + v1) + (v2 + v3);
+}
+
+__device__ __forceinline__ float dot8(const float* a, const float* b) {
+  const float4 a0 = *reinterpret_cast<const float4*>(a), a1 = *reinterpret_cast<const float4*>(a + 4);
+  const float4 b0 = *reinterpret_cast<const float4*>(b), b1 = *reinterpret_cast<const float4*>(b + 4);
+  return ((a0.x * b0.x + a0.y * b0.y) + (a0.z * b0.z + a0.w * b0.w)) +
+         ((a1.x * b1.x + a1.y * b1.y) + (a1.z * b1.z + a1.w * b1.w));
+}
 
 __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, SolveConst sc,
-                                                                  const float* __restrict__ H14,
-                                                                  const float* __restrict__ g14,
                                                                   double* __restrict__ T_wc,
                                                                   double* __restrict__ tau_out,
                                                                   int32_t* __restrict__ dev_status,
@@ -596,63 +677,45 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
     if (tid == 0) handled[g] = 0;
     return;
   }
-  const int32_t* I = pv.ints;
-  const int32_t* pose_of_pos = I + G.off_pose;
-  const int32_t* col_ptr = I + G.off_col;
-  const int32_t* colent = I + G.off_colent;
-  const int32_t* asm_ptr = I + G.off_asm;
-  const int32_t* asment = I + G.off_asment;
-  const int32_t* gasm_ptr = I + G.off_gasm;
-  const int32_t* gasment = I + G.off_gasment;
-  const int32_t* lev_ptr = I + G.off_lev;
-  const int32_t* lev_cols = I + G.off_levcols;
-  const int32_t* levtgt = I + G.off_levtgt;
-  const int32_t* tgtlist = I + G.off_tgtlist;
-  const int32_t* tptr = I + G.off_tptr;
-  const int32_t* pairs = I + G.off_pairs;
-  const int32_t* rsptr = I + G.off_rsptr;
-  const int32_t* rs = I + G.off_rs;
-  const int32_t* blkcol = I + G.off_blkcol;
   const int n7 = 7 * m;
-  // shared memory: FP64 vectors first, then the FP32 factor and vectors
-  double* scl = smem;          // S = D^-1/2
-  double* xv = scl + n7;       // solution
-  double* bv = xv + n7;        // right-hand side -g
-  float* Lf = reinterpret_cast<float*>(bv + n7);  // scaled factor, FP32
-  float* yv = Lf + (size_t)nb * 49;               // work vector
+  // shared memory: the padded FP32 factor, FP64 vectors, FP32 vectors, then
+  // the graph's tables (all but the update triples), so that every dependent
+  // lookup of the level schedule is a shared-memory access
+  float* Lf = reinterpret_cast<float*>(smem);  // scaled factor, FP32, 7 x 8 per block (16-byte aligned rows)
+  double* scl = reinterpret_cast<double*>(Lf + (size_t)nb * kLfBlock);  // S = D^-1/2
+  double* xv = scl + n7;                        // solution
+  double* bv = xv + n7;                         // right-hand side -g
+  float* yv = reinterpret_cast<float*>(bv + n7);  // work vector
   float* ivf = yv + n7;                           // reciprocal pivots
-  int* blkrow = reinterpret_cast<int*>(ivf + n7);  // row position of each block
-  double* H64 = ws + G.ws_off;  // assembled FP64 blocks (global, L2-resident)
-
-  // ---- assembly (FP64, fixed order), as in the FP64 kernel
-  for (int t = tid; t < nb * 49; t += nth) {
-    const int b = t / 49, e = t % 49, r = e / 7, c = e % 7;
-    double s = 0.0;
-    const int k1 = __ldg(asm_ptr + b + 1);
-    for (int k = __ldg(asm_ptr + b); k < k1; ++k) {
-      const int code = __ldg(asment + k), edge = code >> 2, quad = code & 3;
-      const int r0 = (quad == 0 || quad == 2) ? 0 : 7;
-      const int c0 = (quad == 0 || quad == 3) ? 0 : 7;
-      s += (double)__ldg(H14 + (size_t)edge * 196 + (r0 + r) * 14 + c0 + c);
+  int* sI = reinterpret_cast<int*>(ivf + n7);
+  const int seg1 = G.off_trip - G.off_pose, seg2 = G.int_end - G.off_lev;
+  for (int t = tid; t < seg1; t += nth) sI[t] = __ldg(pv.ints + G.off_pose + t);
+  for (int t = tid; t < seg2; t += nth) sI[seg1 + t] = __ldg(pv.ints + G.off_lev + t);
+  {
+    const float4* src = reinterpret_cast<const float4*>(ws + G.ws_mixed);
+    float4* dst = reinterpret_cast<float4*>(Lf);
+    for (int t = tid; t < nb * (kLfBlock / 4); t += nth) dst[t] = src[t];
+    const double* sg = ws + G.ws_mixed + (size_t)nb * 28;
+    for (int t = tid; t < n7; t += nth) {
+      scl[t] = sg[t];
+      bv[t] = sg[n7 + t];
+      xv[t] = 0.0;
     }
-    H64[t] = s;
   }
-  for (int t = tid; t < n7; t += nth) {
-    const int p = t / 7, a = t % 7;
-    double s = 0.0;
-    const int k1 = __ldg(gasm_ptr + p + 1);
-    for (int k = __ldg(gasm_ptr + p); k < k1; ++k) {
-      const int code = __ldg(gasment + k), edge = code >> 1, side = code & 1;
-      s += (double)__ldg(g14 + (size_t)edge * 14 + 7 * side + a);
-    }
-    bv[t] = -s;
-    xv[t] = 0.0;
-  }
-  for (int p = tid; p < m; p += nth) {
-    blkrow[p] = p;
-    for (int ent = __ldg(col_ptr + p); ent < __ldg(col_ptr + p + 1); ++ent)
-      blkrow[__ldg(colent + 2 * ent + 1)] = __ldg(colent + 2 * ent);
-  }
+  const int32_t* pose_of_pos = sI;
+  const int32_t* col_ptr = sI + (G.off_col - G.off_pose);
+  const int32_t* colent = sI + (G.off_colent - G.off_pose);
+  const int32_t* T2 = sI + seg1;  // second segment, starting at plan offset off_lev
+  const int32_t* asm_ptr = T2 + (G.off_asm - G.off_lev);
+  const int32_t* lev_ptr = T2;
+  const int32_t* lev_cols = T2 + (G.off_levcols - G.off_lev);
+  const int32_t* levtgt = T2 + (G.off_levtgt - G.off_lev);
+  const int32_t* tgtlist = T2 + (G.off_tgtlist - G.off_lev);
+  const int32_t* tptr = T2 + (G.off_tptr - G.off_lev);
+  const int32_t* pairs = T2 + (G.off_pairs - G.off_lev);
+  const int32_t* rsptr = T2 + (G.off_rsptr - G.off_lev);
+  const int32_t* rs = T2 + (G.off_rs - G.off_lev);
+  const double* H64 = ws + G.ws_off;  // assembled FP64 blocks (global, L2-resident)
   if (tid == 0) {
     s_fail = 0;
     s_done = 0;
@@ -660,52 +723,41 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
     s_zprev = 0.0;
   }
   __syncthreads();
-  // ---- scaling S = D^-1/2 from the assembled diagonal
-  for (int k = tid; k < n7; k += nth) {
-    const double d = H64[49 * (k / 7) + 8 * (k % 7)];
-    if (!(d > 0.0) || !isfinite(d)) {
-      s_fail = 1;
-      scl[k] = 1.0;
-    } else {
-      scl[k] = rsqrt_newton(d);
-    }
-  }
+  for (int t = tid; t < n7; t += nth)
+    if (!isfinite(scl[t])) s_fail = 1;  // a diagonal entry that is not positive
   __syncthreads();
   if (s_fail) {
     if (tid == 0) handled[g] = 0;
     return;
   }
-  for (int t = tid; t < nb * 49; t += nth) {
-    const int b = t / 49, e = t % 49;
-    Lf[t] = (float)(H64[t] * scl[7 * blkrow[b] + e / 7] * scl[7 * __ldg(blkcol + b) + e % 7]);
-  }
-  __syncthreads();
 
   // ---- FP32 factorisation of S H S by levels
   for (int l = 0; l < G.n_levels; ++l) {
-    const int q0 = __ldg(lev_ptr + l), q1 = __ldg(lev_ptr + l + 1);
-    const int g0 = __ldg(levtgt + l), g1 = __ldg(levtgt + l + 1);
+    const int q0 = lev_ptr[l], q1 = lev_ptr[l + 1];
+    const int g0 = levtgt[l], g1 = levtgt[l + 1];
     for (int w = tid; w < (g1 - g0) * 49; w += nth) {
-      const int t = __ldg(tgtlist + g0 + w / 49), e = w % 49, r = e / 7, c = e % 7;
-      const int k1 = __ldg(tptr + t + 1);
-      float ps[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      for (int k = __ldg(tptr + t); k < k1; ++k) {
-        const float* Lb = Lf + 49 * (size_t)__ldg(pairs + 2 * k) + 7 * r;
-        const float* La = Lf + 49 * (size_t)__ldg(pairs + 2 * k + 1) + 7 * c;
-#pragma unroll
-        for (int kk = 0; kk < 7; ++kk) ps[kk] = fmaf(Lb[kk], La[kk], ps[kk]);
+      const int t = tgtlist[g0 + w / 49], e = w % 49, r = e / 7, c = e % 7;
+      const int k1 = tptr[t + 1];
+      float s0 = 0.f, s1 = 0.f;
+      int k = tptr[t];
+      for (; k + 1 < k1; k += 2) {
+        s0 += dot8(Lf + kLfBlock * (size_t)pairs[2 * k] + 8 * r, Lf + kLfBlock * (size_t)pairs[2 * k + 1] + 8 * c);
+        s1 += dot8(Lf + kLfBlock * (size_t)pairs[2 * k + 2] + 8 * r,
+                   Lf + kLfBlock * (size_t)pairs[2 * k + 3] + 8 * c);
       }
-      Lf[49 * (size_t)t + e] -= ((ps[0] + ps[1]) + (ps[2] + ps[3])) + ((ps[4] + ps[5]) + ps[6]);
+      if (k < k1)
+        s0 += dot8(Lf + kLfBlock * (size_t)pairs[2 * k] + 8 * r, Lf + kLfBlock * (size_t)pairs[2 * k + 1] + 8 * c);
+      Lf[kLfBlock * (size_t)t + 8 * r + c] -= s0 + s1;
     }
     __syncthreads();
     for (int qi = q0 + warp; qi < q1; qi += nwarps) {
-      const int p = __ldg(lev_cols + qi);
-      float* D = Lf + 49 * (size_t)p;
+      const int p = lev_cols[qi];
+      float* D = Lf + kLfBlock * (size_t)p;
       const bool mine = lane < 7;
       const int li = mine ? lane : 0;
       float row[7];
 #pragma unroll
-      for (int k = 0; k < 7; ++k) row[k] = D[7 * li + k];
+      for (int k = 0; k < 7; ++k) row[k] = D[8 * li + k];
       bool bad = false;
 #pragma unroll
       for (int j = 0; j < 7; ++j) {
@@ -725,31 +777,30 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
       if (mine) {
 #pragma unroll
         for (int k = 0; k < 7; ++k)
-          if (k <= lane) D[7 * lane + k] = row[k];
+          if (k <= lane) D[8 * lane + k] = row[k];
       }
       if (bad && lane == 0) s_fail = 1;
+      __syncwarp();
+      // the same warp forms its column's panel L_rp = A_rp L_pp^-T, one row
+      // of a block below the diagonal per lane (no barrier in between)
+      const float* iv = ivf + 7 * p;
+      for (int ent = col_ptr[p] * 7 + lane; ent < col_ptr[p + 1] * 7; ent += 32) {
+        float* prow = Lf + kLfBlock * (size_t)colent[2 * (ent / 7) + 1] + 8 * (ent % 7);
+        float x[7];
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+          float v = prow[k];
+#pragma unroll
+          for (int l2 = 0; l2 < k; ++l2) v = fmaf(-x[l2], D[8 * k + l2], v);
+          x[k] = v * iv[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 7; ++k) prow[k] = x[k];
+      }
       __syncwarp();
     }
     __syncthreads();
     if (s_fail) break;
-    for (int w = tid; w < (g1 - g0) * 7; w += nth) {
-      const int t = __ldg(tgtlist + g0 + w / 7), a = w % 7;
-      if (t < m) continue;
-      const int p = __ldg(blkcol + t);
-      const float* D = Lf + 49 * (size_t)p;
-      const float* iv = ivf + 7 * p;
-      float* row = Lf + 49 * (size_t)t + 7 * a;
-      float x[7];
-#pragma unroll
-      for (int k = 0; k < 7; ++k) {
-        float v = row[k];
-        for (int l2 = 0; l2 < k; ++l2) v = fmaf(-x[l2], D[7 * k + l2], v);
-        x[k] = v * iv[k];
-      }
-#pragma unroll
-      for (int k = 0; k < 7; ++k) row[k] = x[k];
-    }
-    __syncthreads();
   }
   if (s_fail) {
     if (tid == 0) handled[g] = 0;
@@ -759,59 +810,66 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
   // ---- iterative refinement
   for (int t = tid; t < n7; t += nth) yv[t] = (float)(scl[t] * bv[t]);
   __syncthreads();
+  const int grp = lane / 7, ga = lane % 7;  // lanes 0..27: four groups of seven rows
   for (int it = 0; it < kMixMaxIters; ++it) {
-    // forward substitution L y' = y, levels ascending, one warp per column
+    // forward substitution L y' = y, levels ascending, one warp per column;
+    // the row gather is split over the four lane groups
     for (int l = 0; l < G.n_levels; ++l) {
-      const int q0 = __ldg(lev_ptr + l), q1 = __ldg(lev_ptr + l + 1);
+      const int q0 = lev_ptr[l], q1 = lev_ptr[l + 1];
       for (int qi = q0 + warp; qi < q1; qi += nwarps) {
-        const int p = __ldg(lev_cols + qi);
-        float s = 0.0f;
-        if (lane < 7) {
+        const int p = lev_cols[qi];
+        float part = 0.0f;
+        if (lane < 28) {
           float ps[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-          for (int k = __ldg(rsptr + p); k < __ldg(rsptr + p + 1); ++k) {
-            const float* Lpc = Lf + 49 * (size_t)__ldg(rs + 2 * k + 1) + 7 * lane;
-            const float* yc = yv + 7 * __ldg(rs + 2 * k);
+          for (int k = rsptr[p] + grp; k < rsptr[p + 1]; k += 4) {
+            const float* Lpc = Lf + kLfBlock * (size_t)rs[2 * k + 1] + 8 * ga;
+            const float* yc = yv + 7 * rs[2 * k];
 #pragma unroll
             for (int kk = 0; kk < 7; ++kk) ps[kk] = fmaf(Lpc[kk], yc[kk], ps[kk]);
           }
-          s = yv[7 * p + lane] - (((ps[0] + ps[1]) + (ps[2] + ps[3])) + ((ps[4] + ps[5]) + ps[6]));
+          part = ((ps[0] + ps[1]) + (ps[2] + ps[3])) + ((ps[4] + ps[5]) + ps[6]);
         }
-        const float* D = Lf + 49 * (size_t)p;
+        const float tot = sum_groups(part);
+        float s = (lane < 7) ? yv[7 * p + lane] - tot : 0.0f;
+        const float* D = Lf + kLfBlock * (size_t)p;
         float out = 0.0f;
 #pragma unroll
         for (int j = 0; j < 7; ++j) {
           const float yj = __shfl_sync(0xffffffffu, s, j) * ivf[7 * p + j];
           if (lane == j) out = yj;
-          if (lane > j && lane < 7) s = fmaf(-D[7 * lane + j], yj, s);
+          if (lane > j && lane < 7) s = fmaf(-D[8 * lane + j], yj, s);
         }
         if (lane < 7) yv[7 * p + lane] = out;
         __syncwarp();
       }
       __syncthreads();
     }
-    // back substitution L^T z = y', levels descending
+    // back substitution L^T z = y', levels descending; the column gather is
+    // split the same way
     for (int l = G.n_levels - 1; l >= 0; --l) {
-      const int q0 = __ldg(lev_ptr + l), q1 = __ldg(lev_ptr + l + 1);
+      const int q0 = lev_ptr[l], q1 = lev_ptr[l + 1];
       for (int qi = q0 + warp; qi < q1; qi += nwarps) {
-        const int p = __ldg(lev_cols + qi);
-        const float* D = Lf + 49 * (size_t)p;
-        float s = 0.0f;
-        if (lane < 7) {
+        const int p = lev_cols[qi];
+        const float* D = Lf + kLfBlock * (size_t)p;
+        float part = 0.0f;
+        if (lane < 28) {
           float ps[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-          for (int ent = __ldg(col_ptr + p); ent < __ldg(col_ptr + p + 1); ++ent) {
-            const float* Lr = Lf + 49 * (size_t)__ldg(colent + 2 * ent + 1);
-            const float* xr = yv + 7 * __ldg(colent + 2 * ent);
+          for (int ent = col_ptr[p] + grp; ent < col_ptr[p + 1]; ent += 4) {
+            const float* Lr = Lf + kLfBlock * (size_t)colent[2 * ent + 1];
+            const float* xr = yv + 7 * colent[2 * ent];
 #pragma unroll
-            for (int k = 0; k < 7; ++k) ps[k] = fmaf(Lr[7 * k + lane], xr[k], ps[k]);
+            for (int k = 0; k < 7; ++k) ps[k] = fmaf(Lr[8 * k + ga], xr[k], ps[k]);
           }
-          s = yv[7 * p + lane] - (((ps[0] + ps[1]) + (ps[2] + ps[3])) + ((ps[4] + ps[5]) + ps[6]));
+          part = ((ps[0] + ps[1]) + (ps[2] + ps[3])) + ((ps[4] + ps[5]) + ps[6]);
         }
+        const float tot = sum_groups(part);
+        float s = (lane < 7) ? yv[7 * p + lane] - tot : 0.0f;
         float xl = 0.0f;
 #pragma unroll
         for (int k = 6; k >= 0; --k) {
           const float xk = __shfl_sync(0xffffffffu, s, k) * ivf[7 * p + k];
           if (lane == k) xl = xk;
-          if (lane < k) s = fmaf(-D[7 * k + lane], xk, s);
+          if (lane < k) s = fmaf(-D[8 * k + lane], xk, s);
         }
         if (lane < 7) yv[7 * p + lane] = xl;
         __syncwarp();
@@ -849,7 +907,7 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
         s_fail = 1;
       } else if (it > 0) {
         const double rho = s_zprev > 0.0 ? zm / s_zprev : 0.0;
-        if (zm == 0.0 || rho * zm <= 1e-10 * xm) s_done = 1;
+        if (zm == 0.0 || rho * zm <= 1e-9 * xm) s_done = 1;
         else if (it > 1 && rho > 0.5) s_fail = 1;  // stalled: leave it to FP64
       } else if (zm == 0.0) {
         s_done = 1;  // b = 0
@@ -868,19 +926,19 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
 #pragma unroll
         for (int kk = 0; kk < 7; ++kk) ps[kk] = fma(Hd[kk], xp[kk], ps[kk]);
       }
-      for (int k = __ldg(rsptr + p); k < __ldg(rsptr + p + 1); ++k) {
-        const int blk = __ldg(rs + 2 * k + 1);
-        if (__ldg(asm_ptr + blk) == __ldg(asm_ptr + blk + 1)) continue;  // fill: zero in H
+      for (int k = rsptr[p]; k < rsptr[p + 1]; ++k) {
+        const int blk = rs[2 * k + 1];
+        if (asm_ptr[blk] == asm_ptr[blk + 1]) continue;  // fill: zero in H
         const double* Hb = H64 + 49 * (size_t)blk + 7 * a;
-        const double* xc = xv + 7 * __ldg(rs + 2 * k);
+        const double* xc = xv + 7 * rs[2 * k];
 #pragma unroll
         for (int kk = 0; kk < 7; ++kk) ps[kk] = fma(Hb[kk], xc[kk], ps[kk]);
       }
-      for (int ent = __ldg(col_ptr + p); ent < __ldg(col_ptr + p + 1); ++ent) {
-        const int blk = __ldg(colent + 2 * ent + 1);
-        if (__ldg(asm_ptr + blk) == __ldg(asm_ptr + blk + 1)) continue;
+      for (int ent = col_ptr[p]; ent < col_ptr[p + 1]; ++ent) {
+        const int blk = colent[2 * ent + 1];
+        if (asm_ptr[blk] == asm_ptr[blk + 1]) continue;
         const double* Hb = H64 + 49 * (size_t)blk + a;  // H_(p,r) = H_(r,p)^T
-        const double* xr = xv + 7 * __ldg(colent + 2 * ent);
+        const double* xr = xv + 7 * colent[2 * ent];
 #pragma unroll
         for (int kk = 0; kk < 7; ++kk) ps[kk] = fma(Hb[7 * kk], xr[kk], ps[kk]);
       }
@@ -903,7 +961,7 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
   }
   if (tau_out && tid < 7) tau_out[7 * G.gauge + tid] = 0.0;
   for (int p = tid; p < m; p += nth) {
-    const int k = __ldg(pose_of_pos + p);
+    const int k = pose_of_pos[p];
     double tau[7];
     for (int a = 0; a < 7; ++a) tau[a] = xv[7 * p + a];
     if (tau_out)
@@ -968,6 +1026,7 @@ static bool cluster_fits(int smem_bytes) {
 // Shared memory of the mixed-precision solve if the plan's largest graph fits
 // (0: use the FP64 kernels alone).
 static int mixed_smem_bytes(const mslam_plan* plan) {
+  if (plan_solve_form(plan) != 0) return 0;
   const int64_t need = plan_max_mixed_bytes(plan);
   const int limit = smem_limit_bytes();
   return (need > 0 && need <= limit) ? (int)need : 0;
@@ -1032,12 +1091,19 @@ extern "C" mslam_status mslam_gn_solve(const mslam_params* p, const mslam_plan* 
     int32_t* handled = reinterpret_cast<int32_t*>(static_cast<char*>(workspace) +
                                                   ((sizeof(double) * std::max<int64_t>(plan_solve_ws_doubles(plan), 1) + 255) &
                                                    ~size_t(255)));
-    solve_mixed_kernel<<<pv.G, kMixThreads, mixed, s>>>(pv, sc, H_blocks, g_blocks, T_wc, tau, dev_status, ws, handled);
+    const int elems = (int)plan_max_mixed_elems(plan);
+    solve_assemble_kernel<<<dim3((elems + 255) / 256, pv.G), 256, 0, s>>>(pv, H_blocks, g_blocks, dev_status, ws);
+    solve_mixed_kernel<<<pv.G, kMixThreads, mixed, s>>>(pv, sc, T_wc, tau, dev_status, ws, handled);
     mslam_status st = cuda_check(cudaGetLastError(), "gn_solve mixed launch");
     if (st != MSLAM_OK) return st;
     sc.skip = handled;
   }
   return launch_solve(pv, sc, H_blocks, g_blocks, T_wc, tau, dev_status, ws, s);
+}
+
+extern "C" int32_t mslam_gn_solve_launches(const mslam_plan* plan) {
+  if (!plan) return 0;
+  return (mixed_smem_bytes(plan) > 0 && plan_view(plan).E > 0) ? 3 : 1;
 }
 
 // Factor every graph's system and write tau = -H^-1 g without updating poses

@@ -144,4 +144,13 @@ def test_global_graph_solve_structure(M):
     assert_poses_close(T, T_r, 1e-8)
     # this graph is solved by the FP32 factorisation with FP64 refinement
     assert solve_flags(plan, ws).tolist() == [1]
+    # the FP64-only form (plan option solve_form = 1) agrees with both
+    plan64 = M.Plan(w.kf_hw.numpy(), w.edges.numpy(), opts={"solve_form": 1})
+    assert plan64.solve_launches == 1 and plan.solve_launches == 3
+    T64 = w.T_init.clone().cuda()
+    tau64, st64 = M.gn_solve(plan64, P, H32.cuda(), g32.cuda(), T64, tau=torch.zeros_like(tau))
+    torch.cuda.synchronize()
+    err64 = np.abs(f64(tau64) - tau_r).max() / max(1.0, np.abs(tau_r).max())
+    print(f"FP64-only solve: tau rel err {err64:.2e}")
+    assert int(st64[0]) in (0, 1) and err64 <= 1e-8
 

@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--small", action="store_true", help="a reduced graph (8 keyframes) for profiling")
     ap.add_argument("--hw", default="384x512", help="image size HxW (smaller sizes keep the graph for profiling)")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes instead of the autotuner's")
+    ap.add_argument("--opts", default="",
+                    help="fixed plan launch shapes instead of the autotuner, e.g. match_block_w=16,lin_tile=32768")
+    ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay timing")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the tracking-frame and adjoint measurements reported beside the headline")
     return ap.parse_args()
@@ -303,7 +306,9 @@ def run_gpu(args, world, rank, local):
     hw = tuple(int(v) for v in args.hw.lower().split("x"))
     w = make_workload(args, rank, dev, hw=hw)
     dtype = torch.float16 if args.form == "batched" else torch.float32
-    arm = Arm(M, w, dtype, per_edge=(args.form == "plain"), autotune=(args.form == "batched" and not args.no_autotune))
+    fixed = {k: int(v) for k, v in (kv.split("=") for kv in args.opts.split(",") if kv)} or None
+    arm = Arm(M, w, dtype, per_edge=(args.form == "plain"),
+              autotune=(args.form == "batched" and not args.no_autotune and fixed is None), opts=fixed)
     arm.step()
     torch.cuda.synchronize()
     n_matched = int(((arm.idx >= 0) & (arm.q.float() > arm.P.q_min)).sum())
@@ -313,7 +318,7 @@ def run_gpu(args, world, rank, local):
     ms, stats, clocks = time_steps(arm, args.steps, args.warmup, world, sampler)
     ms = max_over_ranks(ms, world)
     graph_ms = None
-    if args.form == "batched":
+    if args.form == "batched" and not args.no_graph:
         # the same step captured once as a CUDA graph and replayed
         arm.capture()
         graph_ms, _, _ = time_steps(arm, args.steps, args.warmup, world, None, with_events=False, graph=True)

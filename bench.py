@@ -107,6 +107,10 @@ def make_workload(args, rank: int, device, hw=None):
 # 512x384: 296,574,464 bytes for 4,718,592 query pixels), scaled to a launch
 # by its query pixels.  Remove an entry when its kernel changes.
 NCU_DRAM_BYTES_PER_QUERY_PX = {("match", 2, 24): 296574464 / 4718592}
+# DRAM bytes per matched pixel of one streamed linearisation launch
+# (lin_stream_kernel, FP16 records, 32768-record tiles: 26,246,144 bytes for
+# 1,637,856 matches), scaled to a launch by its matches.
+NCU_DRAM_BYTES_PER_MATCH = {("lin_stream", 2): 26246144 / 1637856}
 
 
 def measured_peaks():
@@ -339,8 +343,12 @@ def run_gpu(args, world, rank, local):
     fp32_peak = nsm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     lin_gbs = lin_bytes / (stats["lin_ms"] * 1e-3) / 1e9
     match_tfs = match_flop / (stats["match_ms"] * 1e-3) / 1e12
-    rl_lin = {"kernel": "gn_linearize", "bound": "hbm", "achieved": round(lin_gbs, 1), "peak": hbm,
-              "unit": "GB/s", "frac": round(lin_gbs / hbm, 4), "traffic": None,
+    lin_kernel = "lin_stream" if (arm.plan.opts.get("lin_form") == 0 and esz == 2 and args.form == "batched") \
+        else "lin_packed" if args.form == "batched" else "lin_tiles"
+    traffic_m = NCU_DRAM_BYTES_PER_MATCH.get((lin_kernel, esz))
+    rl_lin = {"kernel": "gn_linearize", "launch": lin_kernel, "bound": "hbm", "achieved": round(lin_gbs, 1),
+              "peak": hbm, "unit": "GB/s", "frac": round(lin_gbs / hbm, 4),
+              "traffic": int(traffic_m * n_matched) if traffic_m else None,
               "algorithmic_bytes": int(lin_bytes), "ms": round(stats["lin_ms"], 4),
               "peak_source": f"{peak_src} hbm_gbs"}
     traffic_px = NCU_DRAM_BYTES_PER_QUERY_PX.get(("match", esz, d)) if args.form == "batched" else None

@@ -317,11 +317,11 @@ mslam_status mslam_gn_solve(const mslam_params* p, const mslam_plan* plan, const
                             const float* g_blocks, double* T_wc, double* tau, int32_t* dev_status, void* workspace,
                             size_t ws_bytes, void* stream);
 
-/* Kernel launches one mslam_gn_solve call enqueues on this plan: 3 when the
+/* Kernel launches one mslam_gn_solve call enqueues on this plan: 4 when the
  * mixed-precision solve (FP32 factorisation of the diagonally scaled system,
  * FP64 iterative refinement) fits the largest graph in shared memory: its
- * assembly kernel, the solve, and an FP64 kernel for any graph it declines;
- * else 1 (FP64 only). */
+ * scaling and assembly kernels, the solve, and an FP64 kernel for any graph
+ * it declines; else 1 (FP64 only). */
 int32_t mslam_gn_solve_launches(const mslam_plan* plan);
 
 /* ------------------------------------------------------------------------ */

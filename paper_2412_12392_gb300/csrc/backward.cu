@@ -94,42 +94,61 @@ __device__ __forceinline__ Dual irls_weight(const Dual& lambda, const Dual& s2, 
   return lambda * (delta * dinv(e));
 }
 
+// Per edge, once per call (one thread per edge): T_ij as float s R and t,
+// and the relative directions beta = Ad_{T_i^-1} (b_j - b_i) and theta
+// likewise for tau, so that the per-pixel kernel needs no FP64.  32 floats
+// per edge: s R (9), t (3), beta (7), theta (7), padding.
+constexpr int kBwdEdgeFloats = 32;
+__global__ void bwd_edge_kernel(PlanView pv, const double* __restrict__ T_wc, const double* __restrict__ stepvec,
+                                int with_step, float* __restrict__ out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= pv.E) return;
+  const DevEdge ed = pv.edges[e];
+  float* o = out + (size_t)e * kBwdEdgeFloats;
+  const Sim3d Ti = load_pose(T_wc + 8 * ed.i), Tj = load_pose(T_wc + 8 * ed.j);
+  const Sim3d Tii = inverse(Ti);
+  const Sim3d Tij = compose(Tii, Tj);
+  double R[9];
+  rot_of(Tij.q, R);
+  for (int k = 0; k < 9; ++k) o[k] = (float)(Tij.s * R[k]);
+  for (int k = 0; k < 3; ++k) o[9 + k] = (float)Tij.t[k];
+  for (int k = 12; k < kBwdEdgeFloats; ++k) o[k] = 0.0f;
+  if (with_step) {
+    double A[49];
+    adjoint_of(Tii, A);
+    const double* bvec = stepvec;
+    const double* tvec = stepvec + 7 * (size_t)pv.N;
+    for (int r = 0; r < 7; ++r) {
+      double sb = 0.0, stt = 0.0;
+      for (int c = 0; c < 7; ++c) {
+        sb += A[7 * r + c] * (bvec[7 * ed.j + c] - bvec[7 * ed.i + c]);
+        stt += A[7 * r + c] * (tvec[7 * ed.j + c] - tvec[7 * ed.i + c]);
+      }
+      o[12 + r] = (float)sb;
+      o[19 + r] = (float)stt;
+    }
+  }
+}
+
 template <typename T>
-__global__ void __launch_bounds__(256) bwd_kernel(PlanView pv, BwdConst bc, const double* __restrict__ T_wc,
+__global__ void __launch_bounds__(256) bwd_kernel(PlanView pv, BwdConst bc, const float* __restrict__ edge_data,
                                                   const T* __restrict__ X, const int32_t* __restrict__ idx,
-                                                  const T* __restrict__ q, const double* __restrict__ stepvec,
-                                                  float* __restrict__ dX, float* __restrict__ dq) {
-  // stepvec: [N, 7] b = H^-1 a followed by [N, 7] tau (FP64), or NULL
-  __shared__ float sR[9], st[3], sbeta[7], stheta[7];
+                                                  const T* __restrict__ q, float* __restrict__ dX,
+                                                  float* __restrict__ dq) {
   for (int tile = blockIdx.x; tile < pv.n_tiles; tile += gridDim.x) {
     const DevTile tl = pv.tiles[tile];
     const DevEdge ed = pv.edges[tl.edge];
-    if (threadIdx.x == 0) {
-      const Sim3d Ti = load_pose(T_wc + 8 * ed.i), Tj = load_pose(T_wc + 8 * ed.j);
-      const Sim3d Tii = inverse(Ti);
-      const Sim3d Tij = compose(Tii, Tj);
-      double R[9];
-      rot_of(Tij.q, R);
-      for (int k = 0; k < 9; ++k) sR[k] = (float)(Tij.s * R[k]);
-      for (int k = 0; k < 3; ++k) st[k] = (float)Tij.t[k];
-      if (bc.with_step) {
-        // relative directions: beta = Ad_{T_i^-1} (b_j - b_i), theta likewise for tau
-        double A[49];
-        adjoint_of(Tii, A);
-        const double* bvec = stepvec;
-        const double* tvec = stepvec + 7 * (size_t)pv.N;
-        for (int r = 0; r < 7; ++r) {
-          double sb = 0.0, stt = 0.0;
-          for (int c = 0; c < 7; ++c) {
-            sb += A[7 * r + c] * (bvec[7 * ed.j + c] - bvec[7 * ed.i + c]);
-            stt += A[7 * r + c] * (tvec[7 * ed.j + c] - tvec[7 * ed.i + c]);
-          }
-          sbeta[r] = (float)sb;
-          stheta[r] = (float)stt;
-        }
-      }
+    const float* eg = edge_data + (size_t)tl.edge * kBwdEdgeFloats;
+    float sR[9], st[3], sbeta[7], stheta[7];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) sR[k] = __ldg(eg + k);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) st[k] = __ldg(eg + 9 + k);
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      sbeta[k] = __ldg(eg + 12 + k);
+      stheta[k] = __ldg(eg + 19 + k);
     }
-    __syncthreads();
     for (int n = tl.begin + threadIdx.x; n < tl.end; n += blockDim.x) {
       const int m = idx[ed.off_e + n];
       if (m < 0) continue;
@@ -194,21 +213,20 @@ __global__ void __launch_bounds__(256) bwd_kernel(PlanView pv, BwdConst bc, cons
       atomicAdd(dXi + 2, f.d[5]);
       dq[ed.off_e + n] = f.d[6];
     }
-    __syncthreads();
   }
 }
 
-// b = H^-1 a for every graph using the factorisation left in the solve
-// workspace by a preceding factorisation (one CTA per graph): reuses the
-// solve kernel's structure with the right-hand side replaced.
+// b = H^-1 a for every graph using the factorisation (blocks and reciprocal
+// pivots) that a preceding factor-only solve left in the workspace (one CTA
+// per graph): forward and back substitution by elimination levels, one
+// warp per column (as in the solve kernel).
 __global__ void __launch_bounds__(kSolveThreads) bwd_rhs_kernel(PlanView pv, const double* __restrict__ a,
                                                                 double* __restrict__ bout,
                                                                 const int32_t* __restrict__ dev_status,
                                                                 double* __restrict__ ws) {
   const int g = blockIdx.x;
   const DevGraph G = pv.graphs[g];
-  const int tid = threadIdx.x, nth = blockDim.x;
-  __shared__ double s_y[7];
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
   const int m = G.m;
   if (tid < 7) bout[7 * G.gauge + tid] = 0.0;
   if (dev_status[g] > 1 || m == 0) return;
@@ -216,57 +234,72 @@ __global__ void __launch_bounds__(kSolveThreads) bwd_rhs_kernel(PlanView pv, con
   const int32_t* pose_of_pos = I + G.off_pose;
   const int32_t* col_ptr = I + G.off_col;
   const int32_t* colent = I + G.off_colent;
+  const int32_t* lev_ptr = I + G.off_lev;
+  const int32_t* lev_cols = I + G.off_levcols;
+  const int32_t* rsptr = I + G.off_rsptr;
+  const int32_t* rs = I + G.off_rs;
   const double* L = ws + G.ws_off;
   double* rhs = ws + G.ws_off + (size_t)G.n_blocks * 49;
-  for (int t = tid; t < 7 * m; t += nth) rhs[t] = a[7 * pose_of_pos[t / 7] + t % 7];
+  const double* invd = rhs + 14 * (size_t)m;  // after the right-hand side and the assembled diagonal
+  for (int t = tid; t < 7 * m; t += nth) rhs[t] = a[7 * __ldg(pose_of_pos + t / 7) + t % 7];
   __syncthreads();
-  for (int p = 0; p < m; ++p) {
-    const double* D = L + 49 * (size_t)p;
-    if (tid == 0) {
-      double* y = rhs + 7 * p;
-      for (int k = 0; k < 7; ++k) {
-        double v = y[k];
-        for (int l = 0; l < k; ++l) v -= D[7 * k + l] * y[l];
-        y[k] = v / D[7 * k + k];
-        s_y[k] = y[k];
-      }
-    }
-    __syncthreads();
-    const int c0 = col_ptr[p], c1 = col_ptr[p + 1];
-    for (int w = tid; w < (c1 - c0) * 7; w += nth) {
-      const int ent = c0 + w / 7, aa = w % 7;
-      const double* row = L + 49 * (size_t)colent[2 * ent + 1] + 7 * aa;
+  for (int l = 0; l < G.n_levels; ++l) {
+    const int q0 = __ldg(lev_ptr + l), q1 = __ldg(lev_ptr + l + 1);
+    for (int qi = q0 + warp; qi < q1; qi += nwarps) {
+      const int p = __ldg(lev_cols + qi);
       double s = 0.0;
-      for (int k = 0; k < 7; ++k) s += row[k] * s_y[k];
-      rhs[7 * colent[2 * ent] + aa] -= s;
+      if (lane < 7) {
+        double ps[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int k = __ldg(rsptr + p); k < __ldg(rsptr + p + 1); ++k) {
+          const double* Lpc = L + 49 * (size_t)__ldg(rs + 2 * k + 1) + 7 * lane;
+          const double* yc = rhs + 7 * __ldg(rs + 2 * k);
+#pragma unroll
+          for (int kk = 0; kk < 7; ++kk) ps[kk] = fma(Lpc[kk], yc[kk], ps[kk]);
+        }
+        s = rhs[7 * p + lane] - (((ps[0] + ps[1]) + (ps[2] + ps[3])) + ((ps[4] + ps[5]) + ps[6]));
+      }
+      const double* D = L + 49 * (size_t)p;
+      double out = 0.0;
+#pragma unroll
+      for (int j = 0; j < 7; ++j) {
+        const double yj = __shfl_sync(0xffffffffu, s, j) * invd[7 * p + j];
+        if (lane == j) out = yj;
+        if (lane > j && lane < 7) s = fma(-D[7 * lane + j], yj, s);
+      }
+      if (lane < 7) rhs[7 * p + lane] = out;
+      __syncwarp();
     }
     __syncthreads();
   }
-  for (int p = m - 1; p >= 0; --p) {
-    const double* D = L + 49 * (size_t)p;
-    const int c0 = col_ptr[p], c1 = col_ptr[p + 1];
-    if (tid < 7) {
-      double s = rhs[7 * p + tid];
-      for (int ent = c0; ent < c1; ++ent) {
-        const double* Lr = L + 49 * (size_t)colent[2 * ent + 1];
-        const double* xr = rhs + 7 * colent[2 * ent];
-        for (int k = 0; k < 7; ++k) s -= Lr[7 * k + tid] * xr[k];
+  for (int l = G.n_levels - 1; l >= 0; --l) {
+    const int q0 = __ldg(lev_ptr + l), q1 = __ldg(lev_ptr + l + 1);
+    for (int qi = q0 + warp; qi < q1; qi += nwarps) {
+      const int p = __ldg(lev_cols + qi);
+      const double* D = L + 49 * (size_t)p;
+      double s = 0.0;
+      if (lane < 7) {
+        double ps[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int ent = __ldg(col_ptr + p); ent < __ldg(col_ptr + p + 1); ++ent) {
+          const double* Lr = L + 49 * (size_t)__ldg(colent + 2 * ent + 1);
+          const double* xr = rhs + 7 * __ldg(colent + 2 * ent);
+#pragma unroll
+          for (int k = 0; k < 7; ++k) ps[k] = fma(Lr[7 * k + lane], xr[k], ps[k]);
+        }
+        s = rhs[7 * p + lane] - (((ps[0] + ps[1]) + (ps[2] + ps[3])) + ((ps[4] + ps[5]) + ps[6]));
       }
-      s_y[tid] = s;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      double x[7];
+      double xl = 0.0;
+#pragma unroll
       for (int k = 6; k >= 0; --k) {
-        double v = s_y[k];
-        for (int l = k + 1; l < 7; ++l) v -= D[7 * l + k] * x[l];
-        x[k] = v / D[7 * k + k];
+        const double xk = __shfl_sync(0xffffffffu, s, k) * invd[7 * p + k];
+        if (lane == k) xl = xk;
+        if (lane < k) s = fma(-D[7 * k + lane], xk, s);
       }
-      for (int k = 0; k < 7; ++k) rhs[7 * p + k] = x[k];
+      if (lane < 7) rhs[7 * p + lane] = xl;
+      __syncwarp();
     }
     __syncthreads();
   }
-  for (int t = tid; t < 7 * m; t += nth) bout[7 * pose_of_pos[t / 7] + t % 7] = rhs[t];
+  for (int t = tid; t < 7 * m; t += nth) bout[7 * __ldg(pose_of_pos + t / 7) + t % 7] = rhs[t];
 }
 
 }  // namespace mslam
@@ -333,13 +366,15 @@ extern "C" mslam_status mslam_gn_backward(const mslam_params* p, const mslam_pla
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = std::min(pv.n_tiles, std::max(1, sms) * 4);
+  // per-edge data after the two pose vectors (b and tau)
+  float* edge_data = reinterpret_cast<float*>(stepvec + 14 * (size_t)pv.N);
+  bwd_edge_kernel<<<(pv.E + 63) / 64, 64, 0, s>>>(pv, T_wc, stepvec, dL_dtau ? 1 : 0, edge_data);
+  const int grid = std::min(pv.n_tiles, std::max(1, sms) * 8);
   if (dt == MSLAM_F32)
-    bwd_kernel<float><<<grid, 256, 0, s>>>(pv, bc, T_wc, static_cast<const float*>(X_canon), idx,
-                                           static_cast<const float*>(q), dL_dtau ? stepvec : nullptr, dL_dX, dL_dq);
+    bwd_kernel<float><<<grid, 256, 0, s>>>(pv, bc, edge_data, static_cast<const float*>(X_canon), idx,
+                                           static_cast<const float*>(q), dL_dX, dL_dq);
   else
-    bwd_kernel<__half><<<grid, 256, 0, s>>>(pv, bc, T_wc, static_cast<const __half*>(X_canon), idx,
-                                            static_cast<const __half*>(q), dL_dtau ? stepvec : nullptr, dL_dX,
-                                            dL_dq);
+    bwd_kernel<__half><<<grid, 256, 0, s>>>(pv, bc, edge_data, static_cast<const __half*>(X_canon), idx,
+                                            static_cast<const __half*>(q), dL_dX, dL_dq);
   return cuda_check(cudaGetLastError(), "gn_backward launch");
 }

@@ -111,6 +111,16 @@ inline KParams to_kparams(const mslam_params& p) {
   return k;
 }
 
+// Hardware reciprocal square root approximation with denormal inputs
+// flushed to zero (one MUFU instruction; the accuracy of rsqrtf for normal
+// inputs).  For squared norms of points and whitened residuals, which are
+// never denormal here.
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // ---------------------------------------------------------------- loads
 template <typename T> __device__ __forceinline__ float ldf(const T* p);
 template <> __device__ __forceinline__ float ldf<float>(const float* p) { return __ldg(p); }
@@ -314,6 +324,7 @@ int plan_lin_form(const mslam_plan* plan);  // 0 streamed, 1 register pipeline
 int plan_solve_form(const mslam_plan* plan);  // 0 mixed precision, 1 FP64 only
 int64_t plan_max_mixed_bytes(const mslam_plan* plan);  // shared memory of the mixed-precision solve
 int64_t plan_max_mixed_elems(const mslam_plan* plan);  // elements of its assembly kernel
+int plan_max_unknown_blocks(const mslam_plan* plan);   // largest non-fixed pose count of a graph
 int64_t plan_solve_ws_doubles(const mslam_plan* plan);    // FP64 solve workspace of all graphs (doubles)
 int plan_max_image_dim(const mslam_plan* plan);  // largest H or W of the plan's keyframes
 // Host-side per-edge ranges: linearisation tiles [t0, t1), match blocks [b0, b1).

@@ -77,7 +77,7 @@ __device__ __forceinline__ void accumulate(float acc[kNumAcc], const RelPose& P,
   } else {
     if (!(d2 > 0.0f)) return;  // packed records are finite and non-zero already
   }
-  const float id = rsqrtf(d2), idy = rsqrtf(dy2);
+  const float id = rsqrt_ftz(d2), idy = rsqrt_ftz(dy2);
   const float d = d2 * id, dy = dy2 * idy;
   const float u0 = x0 * id, u1 = x1 * id, u2 = x2 * id;
   const float r0 = u0 - y.x * idy, r1 = u1 - y.y * idy, r2 = u2 - y.z * idy;
@@ -88,12 +88,12 @@ __device__ __forceinline__ void accumulate(float acc[kNumAcc], const RelPose& P,
   // Huber: e <= delta -> weight 1, cost e^2/2; else weight delta/e, cost delta (e - delta/2)
   float wr = lr, wd = ld, cost = 0.5f * (er2 + ed2);
   if (er2 > c.delta2) {
-    const float ir = rsqrtf(er2);
+    const float ir = rsqrt_ftz(er2);
     wr = lr * c.delta * ir;
     cost += c.delta * (er2 * ir - 0.5f * c.delta) - 0.5f * er2;
   }
   if (ed2 > c.delta2) {
-    const float ie = rsqrtf(ed2);
+    const float ie = rsqrt_ftz(ed2);
     wd = ld * c.delta * ie;
     cost += c.delta * (ed2 * ie - 0.5f * c.delta) - 0.5f * ed2;
   }
@@ -173,7 +173,7 @@ __device__ __forceinline__ float huber_apply(float e2, float lam, const LinConst
     *cost += 0.5f * e2;
     return lam;
   }
-  const float ie = rsqrtf(e2);
+  const float ie = rsqrt_ftz(e2);
   *cost += c.delta * (e2 * ie - 0.5f * c.delta);
   return lam * c.delta * ie;
 }
@@ -590,7 +590,7 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 
 // Huber weight factor h = min(1, delta / e) of a squared whitened norm, per lane.
 __device__ __forceinline__ float huber_h(float e2, const LinConst& c) {
-  return fminf(1.0f, c.delta * rsqrtf(fmaxf(e2, c.delta2)));
+  return fminf(1.0f, c.delta * rsqrt_ftz(fmaxf(e2, c.delta2)));
 }
 
 // Two records (lanes a and b) of the ray family; mask = (1 or 0, 1 or 0)
@@ -607,8 +607,8 @@ __device__ __forceinline__ void accumulate_pair(f2 acc[kNumAcc], const f2 Rp[12]
   const bool va = d2.x > 0.0f;
   vb = vb && d2.y > 0.0f;
   const f2 mask = mk2(va ? 1.0f : 0.0f, vb ? 1.0f : 0.0f);
-  const f2 id = mk2(rsqrtf(va ? d2.x : 1.0f), rsqrtf(vb ? d2.y : 1.0f));
-  const f2 idy = mk2(rsqrtf(va ? dy2.x : 1.0f), rsqrtf(vb ? dy2.y : 1.0f));
+  const f2 id = mk2(rsqrt_ftz(va ? d2.x : 1.0f), rsqrt_ftz(vb ? d2.y : 1.0f));
+  const f2 idy = mk2(rsqrt_ftz(va ? dy2.x : 1.0f), rsqrt_ftz(vb ? dy2.y : 1.0f));
   const f2 m1 = bc2(-1.0f);
   const f2 d = mul2(d2, id), dy = mul2(dy2, idy);
   const f2 u0 = mul2(x0, id), u1 = mul2(x1, id), u2 = mul2(x2, id);

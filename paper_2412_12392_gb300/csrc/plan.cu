@@ -24,6 +24,7 @@ struct mslam_plan {
   int64_t n_blocks_total = 0, n_trips_total = 0, solve_ws_doubles = 0, max_graph_doubles = 0;
   int64_t max_mixed_bytes = 0;  // shared memory of the mixed-precision solve for the largest graph
   int64_t max_mixed_elems = 0;  // elements its assembly kernel covers for the largest graph
+  int32_t max_m = 0;            // non-fixed poses of the largest graph
   int32_t max_levels = 0;
   int32_t lin_tile = 0, lin_blocks_per_sm = 0, match_bx = 0, match_by = 0, lin_form = 0, solve_form = 0;
   int32_t n_mblocks = 0;
@@ -93,6 +94,7 @@ void plan_edge_mblocks(const mslam_plan* plan, int e, int* b0, int* b1) {
 int64_t plan_max_graph_doubles(const mslam_plan* plan) { return plan->max_graph_doubles; }
 int64_t plan_max_mixed_bytes(const mslam_plan* plan) { return plan->max_mixed_bytes; }
 int64_t plan_max_mixed_elems(const mslam_plan* plan) { return plan->max_mixed_elems; }
+int plan_max_unknown_blocks(const mslam_plan* plan) { return plan->max_m; }
 int64_t plan_solve_ws_doubles(const mslam_plan* plan) { return plan->solve_ws_doubles; }
 int plan_lin_blocks_per_sm(const mslam_plan* plan) { return plan->lin_blocks_per_sm; }
 int plan_lin_form(const mslam_plan* plan) { return plan->lin_form; }
@@ -360,7 +362,8 @@ static void build_graph(mslam_plan* P, int g, const std::vector<int>& kfs) {
   const int64_t table_ints = (int64_t)(dg.off_trip - dg.off_pose) + (int64_t)(dg.int_end - dg.off_lev);
   P->max_mixed_bytes = std::max(P->max_mixed_bytes,
                                 (int64_t)(32 * 7 * (int64_t)m + 224 * (int64_t)nb_total + 4 * table_ints + 16));
-  P->max_mixed_elems = std::max(P->max_mixed_elems, (int64_t)nb_total * 56 + 7 * (int64_t)m);
+  P->max_mixed_elems = std::max(P->max_mixed_elems, (int64_t)nb_total * 56);
+  P->max_m = std::max(P->max_m, (int32_t)m);
   P->n_blocks_total += nb_total;
   P->graphs.push_back(dg);
 }
@@ -583,7 +586,9 @@ size_t mslam_workspace_bytes(const mslam_plan* plan, int32_t op) {
     case MSLAM_OP_STATS:
       return align256(sizeof(uint32_t) * (size_t)((plan->e_off.back() + 31) / 32 + 1));
     case MSLAM_OP_BACKWARD:
-      return mslam_workspace_bytes(plan, MSLAM_OP_SOLVE) + align256(sizeof(double) * 7 * (size_t)plan->N) * 2;
+      // the solve's workspace, b and tau (7 N doubles each), per-edge data (32 floats per edge)
+      return mslam_workspace_bytes(plan, MSLAM_OP_SOLVE) + align256(sizeof(double) * 14 * (size_t)plan->N) +
+             align256(sizeof(float) * 32 * (size_t)std::max(plan->E, 1));
     default:
       return 0;
   }

@@ -591,55 +591,58 @@ __device__ __forceinline__ double asm_sum(const float* __restrict__ H14, const i
   return s;
 }
 
-// Inputs of the mixed-precision solve, one thread per element over many
-// CTAs (the FP64 rate of a single SM would make this the solve's longest
-// phase): every block element in FP64 (kept for the residuals), the scaling
-// S = D^-1/2 of its row and column from the assembled diagonal, the scaled
-// FP32 factor input (S H S, unit diagonal) and -g.  A diagonal entry that is
-// not positive and finite leaves S = NaN, which makes the solve decline the
-// graph.
-__global__ void __launch_bounds__(256) solve_assemble_kernel(PlanView pv, const float* __restrict__ H14,
-                                                             const float* __restrict__ g14,
-                                                             const int32_t* __restrict__ dev_status,
-                                                             double* __restrict__ ws) {
+// Inputs of the mixed-precision solve, spread over many CTAs (the FP64 rate
+// of a single SM would make this the solve's longest phase).  First the
+// scaling S = D^-1/2 from the assembled diagonal and -g, one thread per
+// unknown; a diagonal entry that is not positive and finite leaves S = NaN,
+// which makes the solve decline the graph.
+__global__ void __launch_bounds__(128) solve_scale_kernel(PlanView pv, const float* __restrict__ H14,
+                                                          const float* __restrict__ g14,
+                                                          const int32_t* __restrict__ dev_status,
+                                                          double* __restrict__ ws) {
   const int g = blockIdx.y;
   const DevGraph G = pv.graphs[g];
   if (dev_status[g] > 0 || G.m == 0) return;  // the solve kernels skip these graphs too
-  const int nb = G.n_blocks, n7 = 7 * G.m;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nb * kLfBlock + n7) return;
+  const int n7 = 7 * G.m, k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n7) return;
   const int32_t* I = pv.ints;
-  const int32_t* asm_ptr = I + G.off_asm;
-  const int32_t* asment = I + G.off_asment;
-  float* Lf = reinterpret_cast<float*>(ws + G.ws_mixed);
-  double* scl = ws + G.ws_mixed + (size_t)nb * 28;
-  double* bv = scl + n7;
-  if (t < nb * kLfBlock) {
-    const int b = t / kLfBlock, e = t % kLfBlock, r = e / 8, c = e % 8;
-    if (c == 7) {
-      Lf[t] = 0.0f;
-      return;
-    }
-    const double h = asm_sum(H14, asm_ptr, asment, b, r, c);
-    ws[G.ws_off + 49 * (size_t)b + 7 * r + c] = h;
-    const int br = __ldg(I + G.off_blkrow + b), bc = __ldg(I + G.off_blkcol + b);
-    const double dr = asm_sum(H14, asm_ptr, asment, br, r, r), dc = asm_sum(H14, asm_ptr, asment, bc, c, c);
-    const double nan = __longlong_as_double(0x7ff8000000000000LL);
-    const double sr = (dr > 0.0 && isfinite(dr)) ? rsqrt_newton(dr) : nan;
-    const double sc = (dc > 0.0 && isfinite(dc)) ? rsqrt_newton(dc) : nan;
-    Lf[t] = (float)(h * sr * sc);
-    if (b < G.m && r == c) scl[7 * b + r] = sr;
-  } else {
-    const int k = t - nb * kLfBlock, p = k / 7, a = k % 7;
-    const int32_t* gasm_ptr = I + G.off_gasm;
-    const int32_t* gasment = I + G.off_gasment;
-    double sg = 0.0;
-    for (int j = __ldg(gasm_ptr + p); j < __ldg(gasm_ptr + p + 1); ++j) {
-      const int code = __ldg(gasment + j), edge = code >> 1, side = code & 1;
-      sg += (double)__ldg(g14 + (size_t)edge * 14 + 7 * side + a);
-    }
-    bv[k] = -sg;
+  double* scl = ws + G.ws_mixed + (size_t)G.n_blocks * 28;
+  const int p = k / 7, a = k % 7;
+  const double d = asm_sum(H14, I + G.off_asm, I + G.off_asment, p, a, a);
+  scl[k] = (d > 0.0 && isfinite(d)) ? rsqrt_newton(d) : __longlong_as_double(0x7ff8000000000000LL);
+  const int32_t* gasm_ptr = I + G.off_gasm;
+  const int32_t* gasment = I + G.off_gasment;
+  double sg = 0.0;
+  for (int j = __ldg(gasm_ptr + p); j < __ldg(gasm_ptr + p + 1); ++j) {
+    const int code = __ldg(gasment + j), edge = code >> 1, side = code & 1;
+    sg += (double)__ldg(g14 + (size_t)edge * 14 + 7 * side + a);
   }
+  scl[n7 + k] = -sg;
+}
+
+// Then every block element in FP64 (kept for the residuals) and the scaled
+// FP32 factor input S H S (unit diagonal), one thread per element.
+__global__ void __launch_bounds__(64) solve_assemble_kernel(PlanView pv, const float* __restrict__ H14,
+                                                            const int32_t* __restrict__ dev_status,
+                                                            double* __restrict__ ws) {
+  const int g = blockIdx.y;
+  const DevGraph G = pv.graphs[g];
+  if (dev_status[g] > 0 || G.m == 0) return;
+  const int nb = G.n_blocks;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nb * kLfBlock) return;
+  const int32_t* I = pv.ints;
+  float* Lf = reinterpret_cast<float*>(ws + G.ws_mixed);
+  const double* scl = ws + G.ws_mixed + (size_t)nb * 28;
+  const int b = t / kLfBlock, e = t % kLfBlock, r = e / 8, c = e % 8;
+  if (c == 7) {
+    Lf[t] = 0.0f;
+    return;
+  }
+  const double h = asm_sum(H14, I + G.off_asm, I + G.off_asment, b, r, c);
+  ws[G.ws_off + 49 * (size_t)b + 7 * r + c] = h;
+  const int br = __ldg(I + G.off_blkrow + b), bc = __ldg(I + G.off_blkcol + b);
+  Lf[t] = (float)(h * scl[7 * br + r] * scl[7 * bc + c]);
 }
 
 // Deterministic sum of the four 7-lane groups of a warp into lanes 0..6
@@ -1091,8 +1094,10 @@ extern "C" mslam_status mslam_gn_solve(const mslam_params* p, const mslam_plan* 
     int32_t* handled = reinterpret_cast<int32_t*>(static_cast<char*>(workspace) +
                                                   ((sizeof(double) * std::max<int64_t>(plan_solve_ws_doubles(plan), 1) + 255) &
                                                    ~size_t(255)));
-    const int elems = (int)plan_max_mixed_elems(plan);
-    solve_assemble_kernel<<<dim3((elems + 255) / 256, pv.G), 256, 0, s>>>(pv, H_blocks, g_blocks, dev_status, ws);
+    const int elems = (int)plan_max_mixed_elems(plan), n7 = 7 * plan_max_unknown_blocks(plan);
+    solve_scale_kernel<<<dim3(std::max(1, (n7 + 127) / 128), pv.G), 128, 0, s>>>(pv, H_blocks, g_blocks,
+                                                                                 dev_status, ws);
+    solve_assemble_kernel<<<dim3(std::max(1, (elems + 63) / 64), pv.G), 64, 0, s>>>(pv, H_blocks, dev_status, ws);
     solve_mixed_kernel<<<pv.G, kMixThreads, mixed, s>>>(pv, sc, T_wc, tau, dev_status, ws, handled);
     mslam_status st = cuda_check(cudaGetLastError(), "gn_solve mixed launch");
     if (st != MSLAM_OK) return st;
@@ -1103,7 +1108,7 @@ extern "C" mslam_status mslam_gn_solve(const mslam_params* p, const mslam_plan* 
 
 extern "C" int32_t mslam_gn_solve_launches(const mslam_plan* plan) {
   if (!plan) return 0;
-  return (mixed_smem_bytes(plan) > 0 && plan_view(plan).E > 0) ? 3 : 1;
+  return (mixed_smem_bytes(plan) > 0 && plan_view(plan).E > 0) ? 4 : 1;
 }
 
 // Factor every graph's system and write tau = -H^-1 g without updating poses

@@ -386,7 +386,7 @@ def run_gpu(args, world, rank, local):
     return out, arm, w
 
 
-def e2e_measure(args, M, w, dtype, world, rank, local, opts=None, n_chunks: int = 8):
+def e2e_measure(args, M, w, dtype, world, rank, local, opts=None, n_chunks: int = 8, n_copy_streams: int = 4):
     """Same metric through the public API with host (pinned) inputs copied in
     and the poses copied out inside the timed region.  The copies run on a
     copy stream into two alternating device input sets, in edge chunks, so
@@ -409,8 +409,8 @@ def e2e_measure(args, M, w, dtype, world, rank, local, opts=None, n_chunks: int 
     e_off = w.e_off.numpy()
     bounds = np.linspace(0, w.E, n_chunks + 1).round().astype(int)
     chunks = [(int(a), int(b)) for a, b in zip(bounds[:-1], bounds[1:]) if b > a]
-    # two copy streams take alternate chunks, so that two copy engines run
-    copy_streams = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)]
+    # copy streams take chunks in turn, so that several copy engines run
+    copy_streams = [torch.cuda.Stream(device=dev) for _ in range(n_copy_streams)]
     compute = torch.cuda.current_stream(dev)
     free = [torch.cuda.Event(), torch.cuda.Event()]  # a set's inputs are no longer read
     for ev in free:
@@ -422,12 +422,12 @@ def e2e_measure(args, M, w, dtype, world, rank, local, opts=None, n_chunks: int 
         done = []
         for cs in copy_streams:
             cs.wait_event(free[si])
-        with torch.cuda.stream(copy_streams[1]):
+        with torch.cuda.stream(copy_streams[-1]):
             dst["X_canon"].copy_(host["X_canon"], non_blocking=True)
             xev = torch.cuda.Event()
-            xev.record(copy_streams[1])
+            xev.record(copy_streams[-1])
         for ci, (e0, e1) in enumerate(chunks):
-            cs = copy_streams[ci % 2]
+            cs = copy_streams[ci % len(copy_streams)]
             with torch.cuda.stream(cs):
                 p0, p1 = int(e_off[e0]), int(e_off[e1])
                 for k in pools:
@@ -483,8 +483,9 @@ def e2e_measure(args, M, w, dtype, world, rank, local, opts=None, n_chunks: int 
     n_matched = int(((arm.idx >= 0) & (arm.q.float() > arm.P.q_min)).sum())
     val = sum_over_ranks(n_matched, world) * arm.iters / (ms * 1e-3)
     return {"value": val, "unit": "matched-pixel GN iters/s", "ms_per_step": ms, "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "copy": f"pinned host, {len(chunks)} edge chunks per step on two copy "
-            f"streams, double-buffered device inputs", "same_result_as_device_resident_step": same}
+            "d2h_bytes_per_step": int(d2h), "copy": f"pinned host, {len(chunks)} edge chunks per step on "
+            f"{len(copy_streams)} copy streams, double-buffered device inputs",
+            "same_result_as_device_resident_step": same}
 
 
 # ----------------------------------------------------------------------------- oracle arm

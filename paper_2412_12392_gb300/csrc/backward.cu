@@ -10,7 +10,7 @@
 // For the step term a . tau with tau = -H^-1 g: with b = H^-1 a (same
 // factorisation), dL = -b^T (dH tau + dg), i.e. the gradient of
 // -phi(X, q), phi = sum_pixels (J b)^T W (J tau + r), evaluated per pixel by
-// forward-mode dual numbers over the pixel's seven inputs (x, y, q).
+// a hand-written reverse sweep over the pixel's computation.
 // Gathered-side contributions are scattered with atomicAdd, so the result is
 // reproducible only up to FP32 summation order.
 #include <algorithm>
@@ -23,76 +23,6 @@ struct BwdConst {
   float inv_sr2, inv_sd2, delta, q_min, c_cost;
   int with_step;
 };
-
-// value plus 7 tangents (x0, x1, x2, y0, y1, y2, q)
-struct Dual {
-  float v;
-  float d[7];
-};
-
-__device__ __forceinline__ Dual dconst(float v) {
-  Dual r;
-  r.v = v;
-#pragma unroll
-  for (int k = 0; k < 7; ++k) r.d[k] = 0.0f;
-  return r;
-}
-__device__ __forceinline__ Dual dvar(float v, int k) {
-  Dual r = dconst(v);
-  r.d[k] = 1.0f;
-  return r;
-}
-__device__ __forceinline__ Dual operator+(const Dual& a, const Dual& b) {
-  Dual r;
-  r.v = a.v + b.v;
-#pragma unroll
-  for (int k = 0; k < 7; ++k) r.d[k] = a.d[k] + b.d[k];
-  return r;
-}
-__device__ __forceinline__ Dual operator-(const Dual& a, const Dual& b) {
-  Dual r;
-  r.v = a.v - b.v;
-#pragma unroll
-  for (int k = 0; k < 7; ++k) r.d[k] = a.d[k] - b.d[k];
-  return r;
-}
-__device__ __forceinline__ Dual operator*(const Dual& a, const Dual& b) {
-  Dual r;
-  r.v = a.v * b.v;
-#pragma unroll
-  for (int k = 0; k < 7; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
-  return r;
-}
-__device__ __forceinline__ Dual operator*(float s, const Dual& a) {
-  Dual r;
-  r.v = s * a.v;
-#pragma unroll
-  for (int k = 0; k < 7; ++k) r.d[k] = s * a.d[k];
-  return r;
-}
-__device__ __forceinline__ Dual dinv(const Dual& a) {
-  Dual r;
-  r.v = 1.0f / a.v;
-  const float g = -r.v * r.v;
-#pragma unroll
-  for (int k = 0; k < 7; ++k) r.d[k] = g * a.d[k];
-  return r;
-}
-__device__ __forceinline__ Dual dsqrt(const Dual& a) {
-  Dual r;
-  r.v = sqrtf(a.v);
-  const float g = r.v > 0.0f ? 0.5f / r.v : 0.0f;
-#pragma unroll
-  for (int k = 0; k < 7; ++k) r.d[k] = g * a.d[k];
-  return r;
-}
-
-// Huber IRLS weight lambda * w_h(e) with e = sqrt(lambda * s2) as a dual
-__device__ __forceinline__ Dual irls_weight(const Dual& lambda, const Dual& s2, float delta) {
-  const Dual e = dsqrt(lambda * s2);
-  if (e.v <= delta) return lambda;
-  return lambda * (delta * dinv(e));
-}
 
 // Per edge, once per call (one thread per edge): T_ij as float s R and t,
 // and the relative directions beta = Ad_{T_i^-1} (b_j - b_i) and theta
@@ -130,6 +60,101 @@ __global__ void bwd_edge_kernel(PlanView pv, const double* __restrict__ T_wc, co
   }
 }
 
+struct V3 {
+  float x, y, z;
+};
+__device__ __forceinline__ V3 v3(float a, float b, float c) { return {a, b, c}; }
+__device__ __forceinline__ float dot(V3 a, V3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ V3 add(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ V3 scl(V3 a, float s) { return {a.x * s, a.y * s, a.z * s}; }
+__device__ __forceinline__ V3 axpy(float s, V3 a, V3 b) { return {fmaf(s, a.x, b.x), fmaf(s, a.y, b.y), fmaf(s, a.z, b.z)}; }
+__device__ __forceinline__ V3 cross(V3 a, V3 b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+// Per-match gradient of f = c (rho(e_r) + rho(e_d)) - phi with respect to
+// x = T_ij X_j[n] (3), y = X_i[m] (3) and q, by a hand-written reverse sweep
+// over the forward computation of the ray and distance residuals, their
+// IRLS weights and, for the step term, phi = w_r (J_psi beta).(J_psi theta + r)
+// + w_d (J_d beta)(J_d theta + r_d) with J_psi v = ((I - u u^T) v_t + v_w x x)/d
+// and J_d v = u.v_t + d v_s (Supp. S1.2).  Huber: h = min(1, delta/e) with
+// dh/d(e^2) = -h / (2 e^2) above delta, d rho/d(e^2) = h / 2.  Returns false
+// for a degenerate match (no contribution).
+__device__ __forceinline__ bool match_grad(V3 x, V3 y, float q, const BwdConst& bc, const float* beta,
+                                           const float* theta, V3& gx, V3& gy, float& gq) {
+  const float d2 = dot(x, x), dy2 = dot(y, y);
+  if (!(d2 > 0.0f && dy2 > 0.0f && d2 < INFINITY && dy2 < INFINITY)) return false;
+  const float d = sqrtf(d2), dy = sqrtf(dy2);
+  const float id = 1.0f / d, idy = 1.0f / dy;
+  const V3 u = scl(x, id), v = scl(y, idy);
+  const V3 r = v3(u.x - v.x, u.y - v.y, u.z - v.z);
+  const float rd = d - dy;
+  const float lr = q * bc.inv_sr2, ld = q * bc.inv_sd2;
+  const float rr = dot(r, r), er2 = lr * rr;
+  const float rd2 = rd * rd, ed2 = ld * rd2;
+  const float d2l = bc.delta * bc.delta;
+  const bool lin_r = er2 > d2l, lin_d = ed2 > d2l;
+  const float hr = lin_r ? bc.delta * rsqrtf(er2) : 1.0f;
+  const float hd = lin_d ? bc.delta * rsqrtf(ed2) : 1.0f;
+  const float wr = lr * hr, wd = ld * hd;
+  // adjoints (gradients of f) of the intermediate values
+  V3 gu = v3(0.f, 0.f, 0.f), gr = v3(0.f, 0.f, 0.f);
+  gx = v3(0.f, 0.f, 0.f);
+  float gd = 0.0f, grd = 0.0f, gwr = 0.0f, gwd = 0.0f, gid = 0.0f;
+  if (bc.with_step) {
+    const V3 bt = v3(beta[0], beta[1], beta[2]), bw = v3(beta[3], beta[4], beta[5]);
+    const V3 tt = v3(theta[0], theta[1], theta[2]), tw = v3(theta[3], theta[4], theta[5]);
+    const float sb = dot(u, bt), st_ = dot(u, tt);
+    const V3 Pb = add(axpy(-sb, u, bt), cross(bw, x)), Pt = add(axpy(-st_, u, tt), cross(tw, x));
+    const V3 A = scl(Pb, id), B = add(scl(Pt, id), r);
+    const float a = sb + d * beta[6], b = st_ + d * theta[6] + rd;
+    const float AB = dot(A, B), ab = a * b;
+    // phi enters f with coefficient -1
+    gwr = -AB;
+    gwd = -ab;
+    const V3 gA = scl(B, -wr), gB = scl(A, -wr);
+    const float ga = -wd * b, gb = -wd * a;
+    gr = gB;   // B = J_psi theta + r
+    grd = gb;  // b = J_d theta + r_d
+    // J_psi beta = Pb id and J_psi theta = Pt id (adjoints gA, gB)
+    gid += dot(gA, Pb) + dot(gB, Pt);
+    const V3 gPb = scl(gA, id), gPt = scl(gB, id);
+    // P = v_t - u (u.v_t) + v_w x x
+    gu = axpy(-sb, gPb, axpy(-st_, gPt, gu));
+    const float gsb = -dot(gPb, u), gst = -dot(gPt, u);
+    gx = add(gx, add(cross(gPb, bw), cross(gPt, tw)));
+    // s = u.v_t;  J_d v = u.v_t + d v_s (adjoints ga, gb)
+    gu = axpy(gsb + ga, bt, axpy(gst + gb, tt, gu));
+    gd += ga * beta[6] + gb * theta[6];
+  }
+  // weights w = lambda h and costs rho; d rho / d(e^2) = h / 2
+  float ger2 = 0.5f * hr * bc.c_cost, ged2 = 0.5f * hd * bc.c_cost;
+  const float glr0 = gwr * hr, gld0 = gwd * hd;
+  const float ghr = gwr * lr, ghd = gwd * ld;
+  if (lin_r) ger2 += ghr * (-0.5f * hr / er2);
+  if (lin_d) ged2 += ghd * (-0.5f * hd / ed2);
+  const float glr = glr0 + ger2 * rr, gld = gld0 + ged2 * rd2;
+  gr = axpy(2.0f * ger2 * lr, r, gr);
+  grd += 2.0f * ged2 * ld * rd;
+  gq = glr * bc.inv_sr2 + gld * bc.inv_sd2;
+  // r = u - v, r_d = d - dy
+  gu = add(gu, gr);
+  const V3 gv = scl(gr, -1.0f);
+  gd += grd;
+  const float gdy = -grd;
+  // u = x id, id = 1/d, d = sqrt(x.x)
+  gx = axpy(id, gu, gx);
+  gid += dot(gu, x);
+  gd += -gid * id * id;
+  gx = axpy(gd * id, x, gx);
+  // v = y idy, idy = 1/dy, dy = sqrt(y.y)
+  gy = scl(gv, idy);
+  const float gidy = dot(gv, y);
+  const float gdyt = gdy - gidy * idy * idy;
+  gy = axpy(gdyt * idy, y, gy);
+  return true;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) bwd_kernel(PlanView pv, BwdConst bc, const float* __restrict__ edge_data,
                                                   const T* __restrict__ X, const int32_t* __restrict__ idx,
@@ -156,62 +181,22 @@ __global__ void __launch_bounds__(256) bwd_kernel(PlanView pv, BwdConst bc, cons
       if (!(qq > bc.q_min)) continue;
       const float3 Xj = ld3(X + 3 * ed.off_j, n);
       const float3 yv = ld3(X + 3 * ed.off_i, m);
-      const float x0 = sR[0] * Xj.x + sR[1] * Xj.y + sR[2] * Xj.z + st[0];
-      const float x1 = sR[3] * Xj.x + sR[4] * Xj.y + sR[5] * Xj.z + st[1];
-      const float x2 = sR[6] * Xj.x + sR[7] * Xj.y + sR[8] * Xj.z + st[2];
-      const Dual X0 = dvar(x0, 0), X1 = dvar(x1, 1), X2 = dvar(x2, 2);
-      const Dual Y0 = dvar(yv.x, 3), Y1 = dvar(yv.y, 4), Y2 = dvar(yv.z, 5), Q = dvar(qq, 6);
-      const Dual d2 = X0 * X0 + X1 * X1 + X2 * X2;
-      const Dual dy2 = Y0 * Y0 + Y1 * Y1 + Y2 * Y2;
-      if (!(d2.v > 0.0f && dy2.v > 0.0f && d2.v < INFINITY && dy2.v < INFINITY)) continue;
-      const Dual d = dsqrt(d2), dy = dsqrt(dy2), id = dinv(d), idy = dinv(dy);
-      const Dual u0 = X0 * id, u1 = X1 * id, u2 = X2 * id;
-      const Dual r0 = u0 - Y0 * idy, r1 = u1 - Y1 * idy, r2 = u2 - Y2 * idy;
-      const Dual rd = d - dy;
-      const Dual lr = bc.inv_sr2 * Q, ld = bc.inv_sd2 * Q;
-      const Dual rr = r0 * r0 + r1 * r1 + r2 * r2;
-      const Dual wr = irls_weight(lr, rr, bc.delta);
-      const Dual wd = irls_weight(ld, rd * rd, bc.delta);
-      Dual f = dconst(0.0f);
-      if (bc.c_cost != 0.0f) {
-        // Huber cost rho(e) = e^2/2 (e <= delta) else delta (e - delta/2)
-        const Dual er2 = lr * rr, ed2 = ld * (rd * rd);
-        const Dual er = dsqrt(er2), edd = dsqrt(ed2);
-        const Dual cr = er.v <= bc.delta ? 0.5f * er2 : bc.delta * (er - dconst(0.5f * bc.delta));
-        const Dual cd = edd.v <= bc.delta ? 0.5f * ed2 : bc.delta * (edd - dconst(0.5f * bc.delta));
-        f = f + bc.c_cost * (cr + cd);
-      }
-      if (bc.with_step) {
-        // J_rel v = ((I - u u^T) v_t + v_w x x) / d (ray rows), u . v_t + d v_s (distance row)
-        auto jray = [&](const float* vv, Dual out[3]) {
-          const Dual ut = u0 * dconst(vv[0]) + u1 * dconst(vv[1]) + u2 * dconst(vv[2]);
-          const Dual c0 = dconst(vv[4]) * X2 - dconst(vv[5]) * X1;
-          const Dual c1 = dconst(vv[5]) * X0 - dconst(vv[3]) * X2;
-          const Dual c2 = dconst(vv[3]) * X1 - dconst(vv[4]) * X0;
-          out[0] = (dconst(vv[0]) - u0 * ut + c0) * id;
-          out[1] = (dconst(vv[1]) - u1 * ut + c1) * id;
-          out[2] = (dconst(vv[2]) - u2 * ut + c2) * id;
-        };
-        Dual jb[3], jt[3];
-        jray(sbeta, jb);
-        jray(stheta, jt);
-        const Dual db = u0 * dconst(sbeta[0]) + u1 * dconst(sbeta[1]) + u2 * dconst(sbeta[2]) + d * dconst(sbeta[6]);
-        const Dual dt_ = u0 * dconst(stheta[0]) + u1 * dconst(stheta[1]) + u2 * dconst(stheta[2]) +
-                         d * dconst(stheta[6]);
-        const Dual phi = wr * (jb[0] * (jt[0] + r0) + jb[1] * (jt[1] + r1) + jb[2] * (jt[2] + r2)) +
-                         wd * (db * (dt_ + rd));
-        f = f - phi;
-      }
+      const V3 x = v3(sR[0] * Xj.x + sR[1] * Xj.y + sR[2] * Xj.z + st[0],
+                      sR[3] * Xj.x + sR[4] * Xj.y + sR[5] * Xj.z + st[1],
+                      sR[6] * Xj.x + sR[7] * Xj.y + sR[8] * Xj.z + st[2]);
+      V3 gx, gy;
+      float gq;
+      if (!match_grad(x, v3(yv.x, yv.y, yv.z), qq, bc, sbeta, stheta, gx, gy, gq)) continue;
       // dL/dX_j = (s R)^T dL/dx
       float* dXj = dX + 3 * (ed.off_j + n);
-      atomicAdd(dXj + 0, sR[0] * f.d[0] + sR[3] * f.d[1] + sR[6] * f.d[2]);
-      atomicAdd(dXj + 1, sR[1] * f.d[0] + sR[4] * f.d[1] + sR[7] * f.d[2]);
-      atomicAdd(dXj + 2, sR[2] * f.d[0] + sR[5] * f.d[1] + sR[8] * f.d[2]);
+      atomicAdd(dXj + 0, sR[0] * gx.x + sR[3] * gx.y + sR[6] * gx.z);
+      atomicAdd(dXj + 1, sR[1] * gx.x + sR[4] * gx.y + sR[7] * gx.z);
+      atomicAdd(dXj + 2, sR[2] * gx.x + sR[5] * gx.y + sR[8] * gx.z);
       float* dXi = dX + 3 * (ed.off_i + m);
-      atomicAdd(dXi + 0, f.d[3]);
-      atomicAdd(dXi + 1, f.d[4]);
-      atomicAdd(dXi + 2, f.d[5]);
-      dq[ed.off_e + n] = f.d[6];
+      atomicAdd(dXi + 0, gy.x);
+      atomicAdd(dXi + 1, gy.y);
+      atomicAdd(dXi + 2, gy.z);
+      dq[ed.off_e + n] = gq;
     }
   }
 }

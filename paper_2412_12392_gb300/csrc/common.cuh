@@ -69,6 +69,8 @@ struct DevGraph {
   int32_t off_rs;     // -> (column c, block L(p, c)) of each position p, in column order
   int32_t off_blkcol; // -> [n_blocks] column position of each block
   int32_t off_blkrow; // -> [n_blocks] row position of each block
+  int32_t off_levupd; // -> [n_levels + 1] into the per-level list of targets that receive updates
+  int32_t off_updlist;// -> those targets (a subset of the level's target list, same order)
   int32_t pad1;
   int64_t ws_off;     // offset (doubles) of this graph's numeric workspace
   int64_t ws_mixed;   // offset (doubles) of the mixed-precision solve's inputs: scaled FP32 factor

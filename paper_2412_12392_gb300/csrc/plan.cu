@@ -275,6 +275,25 @@ static void build_graph(mslam_plan* P, int g, const std::vector<int>& kfs) {
       I.push_back(pr.first);
       I.push_back(pr.second);
     }
+  // per level: the targets with at least one update pair (the rest need no update phase)
+  dg.off_levupd = (int32_t)I.size();
+  {
+    std::vector<int32_t> ptr, lst;
+    for (int l = 0; l < n_lev; ++l) {
+      ptr.push_back((int32_t)lst.size());
+      for (int c : cols_of[l]) {
+        if (!by_target[c].empty()) lst.push_back(c);
+        for (int r : rows[c]) {
+          const int t = blk.at({r, c});
+          if (!by_target[t].empty()) lst.push_back(t);
+        }
+      }
+    }
+    ptr.push_back((int32_t)lst.size());
+    I.insert(I.end(), ptr.begin(), ptr.end());
+    dg.off_updlist = (int32_t)I.size();
+    I.insert(I.end(), lst.begin(), lst.end());
+  }
   dg.off_rsptr = (int32_t)I.size();  // [m + 1] row structure (c, block) per position
   {
     int acc = 0;

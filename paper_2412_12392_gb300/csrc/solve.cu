@@ -645,6 +645,65 @@ __global__ void __launch_bounds__(64) solve_assemble_kernel(PlanView pv, const f
   Lf[t] = (float)(h * scl[7 * br + r] * scl[7 * bc + c]);
 }
 
+// Exp(tau) of sim3_exp split into independent pieces, so that different
+// warps can evaluate them side by side: piece 0 sin and cos of theta, 1
+// e^sigma, 2 the quaternion's half-angle terms, 3 the moment m_0, 4-7 the
+// moments m_1, m_3, m_2, m_4 of the small-angle branch.  part[10] holds
+// sn, cs, es, h, q3, m0, m1, m3, m2, m4.  The same formulas as sim3_exp on the
+// same inputs, so the same values.
+__device__ void sim3_exp_piece(const double* tau, int kind, double* part) {
+  const double px = tau[3], py = tau[4], pz = tau[5], sg = tau[6];
+  const double th2 = px * px + py * py + pz * pz, th = sqrt(th2);
+  const bool small = th < 1e-4;
+  if (kind == 0) {
+    double sn = 0.0, cs = 0.0;
+    if (!small) sincos(th, &sn, &cs);
+    part[0] = sn;
+    part[1] = cs;
+  } else if (kind == 1) {
+    part[2] = exp(sg);
+  } else if (kind == 2) {
+    part[3] = (th < 1e-6) ? (0.5 - th2 / 48.0) : sin(0.5 * th) / th;
+    part[4] = cos(0.5 * th);
+  } else if (kind == 3) {
+    part[5] = moment_exp(0, sg);
+  } else {
+    const int n = kind == 4 ? 1 : kind == 5 ? 3 : kind == 6 ? 2 : 4;
+    part[2 + kind] = small ? moment_exp(n, sg) : 0.0;
+  }
+}
+
+__device__ Sim3d sim3_exp_parts(const double* tau, const double* part) {
+  const double px = tau[3], py = tau[4], pz = tau[5], sg = tau[6];
+  const double th2 = px * px + py * py + pz * pz, th = sqrt(th2);
+  const double sn = part[0], cs = part[1], es = part[2], h = part[3], q3 = part[4], a = part[5];
+  double b, c;
+  if (th < 1e-4) {
+    b = part[6] - th2 * part[7] / 6.0;
+    c = 0.5 * part[8] - th2 * part[9] / 24.0;
+  } else {
+    const double den = sg * sg + th2;
+    const double ic = ((es * cs - 1.0) * sg + es * th * sn) / den;
+    const double is = (es * sn * sg - (es * cs - 1.0) * th) / den;
+    b = is / th;
+    c = (a - ic) / th2;
+  }
+  Sim3d e;
+  e.q[0] = h * px;
+  e.q[1] = h * py;
+  e.q[2] = h * pz;
+  e.q[3] = q3;
+  qnormalise(e.q);
+  e.s = es;
+  const double r0 = tau[0], r1 = tau[1], r2 = tau[2];
+  const double c0 = py * r2 - pz * r1, c1 = pz * r0 - px * r2, c2 = px * r1 - py * r0;
+  const double d0 = py * c2 - pz * c1, d1 = pz * c0 - px * c2, d2 = px * c1 - py * c0;
+  e.t[0] = a * r0 + b * c0 + c * d0;
+  e.t[1] = a * r1 + b * c1 + c * d1;
+  e.t[2] = a * r2 + b * c2 + c * d2;
+  return e;
+}
+
 // Deterministic sum of the four 7-lane groups of a warp into lanes 0..6
 // (lane a + 7 g holds group g's partial for row a).
 __device__ __forceinline__ float sum_groups(float v) {
@@ -712,10 +771,10 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
   const int32_t* asm_ptr = T2 + (G.off_asm - G.off_lev);
   const int32_t* lev_ptr = T2;
   const int32_t* lev_cols = T2 + (G.off_levcols - G.off_lev);
-  const int32_t* levtgt = T2 + (G.off_levtgt - G.off_lev);
-  const int32_t* tgtlist = T2 + (G.off_tgtlist - G.off_lev);
   const int32_t* tptr = T2 + (G.off_tptr - G.off_lev);
   const int32_t* pairs = T2 + (G.off_pairs - G.off_lev);
+  const int32_t* levupd = T2 + (G.off_levupd - G.off_lev);
+  const int32_t* updlist = T2 + (G.off_updlist - G.off_lev);
   const int32_t* rsptr = T2 + (G.off_rsptr - G.off_lev);
   const int32_t* rs = T2 + (G.off_rs - G.off_lev);
   const double* H64 = ws + G.ws_off;  // assembled FP64 blocks (global, L2-resident)
@@ -737,9 +796,9 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
   // ---- FP32 factorisation of S H S by levels
   for (int l = 0; l < G.n_levels; ++l) {
     const int q0 = lev_ptr[l], q1 = lev_ptr[l + 1];
-    const int g0 = levtgt[l], g1 = levtgt[l + 1];
+    const int g0 = levupd[l], g1 = levupd[l + 1];  // targets of the level that receive updates
     for (int w = tid; w < (g1 - g0) * 49; w += nth) {
-      const int t = tgtlist[g0 + w / 49], e = w % 49, r = e / 7, c = e % 7;
+      const int t = updlist[g0 + w / 49], e = w % 49, r = e / 7, c = e % 7;
       const int k1 = tptr[t + 1];
       float s0 = 0.f, s1 = 0.f;
       int k = tptr[t];
@@ -752,7 +811,7 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
         s0 += dot8(Lf + kLfBlock * (size_t)pairs[2 * k] + 8 * r, Lf + kLfBlock * (size_t)pairs[2 * k + 1] + 8 * c);
       Lf[kLfBlock * (size_t)t + 8 * r + c] -= s0 + s1;
     }
-    __syncthreads();
+    if (g1 > g0) __syncthreads();
     for (int qi = q0 + warp; qi < q1; qi += nwarps) {
       const int p = lev_cols[qi];
       float* D = Lf + kLfBlock * (size_t)p;
@@ -963,15 +1022,24 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
     if (lane == 0) s_max = mx;
   }
   if (tau_out && tid < 7) tau_out[7 * G.gauge + tid] = 0.0;
-  for (int p = tid; p < m; p += nth) {
-    const int k = pose_of_pos[p];
-    double tau[7];
-    for (int a = 0; a < 7; ++a) tau[a] = xv[7 * p + a];
-    if (tau_out)
-      for (int a = 0; a < 7; ++a) tau_out[7 * k + a] = tau[a];
-    const Sim3d E = sim3_exp(tau);
-    const Sim3d Tn = compose(E, load_pose(T_wc + 8 * k));
-    store_pose(Tn, T_wc + 8 * k);
+  // retraction T <- Exp(tau) o T: the transcendental pieces of every pose's
+  // Exp are computed by different warps side by side (a warp runs one kind
+  // of function for 32 poses), then combined per pose (sim3_exp_parts)
+  {
+    double* part = reinterpret_cast<double*>(Lf);  // 10 doubles per pose; the factor is no longer needed
+    for (int w = warp; w < 8 * ((m + 31) / 32); w += nwarps) {
+      const int kind = w & 7, p = (w >> 3) * 32 + lane;
+      if (p < m) sim3_exp_piece(xv + 7 * p, kind, part + 10 * p);
+    }
+    __syncthreads();
+    for (int p = tid; p < m; p += nth) {
+      const int k = pose_of_pos[p];
+      if (tau_out)
+        for (int a = 0; a < 7; ++a) tau_out[7 * k + a] = xv[7 * p + a];
+      const Sim3d E = sim3_exp_parts(xv + 7 * p, part + 10 * p);
+      const Sim3d Tn = compose(E, load_pose(T_wc + 8 * k));
+      store_pose(Tn, T_wc + 8 * k);
+    }
   }
   __syncthreads();
   if (tid == 0) {

@@ -465,6 +465,15 @@ def e2e_measure(args, M, w, dtype, world, rank, local, opts=None, n_chunks: int 
 
     run(max(1, args.warmup))
     torch.cuda.synchronize()
+    # the host-to-device copy rate of this machine, for context: one large
+    # pinned copy of the reference descriptors
+    probe = host["D_ref"]
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(compute)
+    sets[0]["D_ref"].copy_(probe, non_blocking=True)
+    c1.record(compute)
+    torch.cuda.synchronize()
+    h2d_gbs = probe.numel() * probe.element_size() / (c0.elapsed_time(c1) * 1e-3) / 1e9
     barrier(world)
     steps = max(2, args.steps)
     t0 = torch.cuda.Event(enable_timing=True)
@@ -485,7 +494,7 @@ def e2e_measure(args, M, w, dtype, world, rank, local, opts=None, n_chunks: int 
     return {"value": val, "unit": "matched-pixel GN iters/s", "ms_per_step": ms, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "copy": f"pinned host, {len(chunks)} edge chunks per step on "
             f"{len(copy_streams)} copy streams, double-buffered device inputs",
-            "same_result_as_device_resident_step": same}
+            "same_result_as_device_resident_step": same, "h2d_gbs_single_copy": round(h2d_gbs, 1)}
 
 
 # ----------------------------------------------------------------------------- oracle arm

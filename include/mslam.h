@@ -140,8 +140,8 @@ void mslam_plan_destroy(mslam_plan* plan);
  *   lin_blocks_per_sm  resident blocks per SM of the persistent
  *                      linearisation launches, 1..32, or 0 for the
  *                      occupancy maximum (default 0)
- *   match_block_w      width of a 256-pixel match block: 16, 32, 64, 128 or
- *                      256 (default 32, i.e. 32 x 8 pixels)
+ *   match_block_w      width of a 256-pixel match block: 4, 8, 16, 32, 64,
+ *                      128 or 256 (default 32, i.e. 32 x 8 pixels)
  *   lin_form, solve_form  kernel forms, described at the fields
  * mslam_plan_create uses the defaults; mslam_plan_create_ex takes options
  * (NULL = defaults).  Errors: MSLAM_ERR_ARG for an option out of range. */

@@ -16,7 +16,7 @@ import torch
 
 from . import api
 
-MATCH_WIDTHS = (16, 32, 64, 128)
+MATCH_WIDTHS = (4, 8, 16, 32, 64)
 LIN_TILES = (4096, 8192, 16384)
 LIN_BLOCKS = (0, 2, 3, 4)
 

@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay timing")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the tracking-frame and adjoint measurements reported beside the headline")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="only the adjoint measurement on the differentiation graph at --hw (for profiling)")
     return ap.parse_args()
 
 
@@ -107,10 +109,12 @@ def make_workload(args, rank: int, device, hw=None):
 # 512x384: 296,574,464 bytes for 4,718,592 query pixels), scaled to a launch
 # by its query pixels.  Remove an entry when its kernel changes.
 NCU_DRAM_BYTES_PER_QUERY_PX = {("match", 2, 24): 296574464 / 4718592}
-# DRAM bytes per matched pixel of one streamed linearisation launch
-# (lin_stream_kernel, FP16 records, 32768-record tiles: 26,246,144 bytes for
-# 1,637,856 matches), scaled to a launch by its matches.
-NCU_DRAM_BYTES_PER_MATCH = {("lin_stream", 2): 26246144 / 1637856}
+# DRAM bytes per matched pixel of one packed linearisation launch, FP16
+# records, scaled to a launch by its matches: lin_stream_kernel (32768-record
+# tiles: 26,246,144 bytes for 1,637,856 matches) and lin_packed_kernel
+# (16384-record tiles, 2 CTAs per SM: 26,247,168 bytes, median of three
+# launches).
+NCU_DRAM_BYTES_PER_MATCH = {("lin_stream", 2): 26246144 / 1637856, ("lin_packed", 2): 26247168 / 1637856}
 
 
 def measured_peaks():
@@ -625,12 +629,13 @@ def tracking_frame(M, dev, peaks) -> dict:
             "gn_iter_ms": float(np.mean([a.elapsed_time(c) for a, b, c in lins])), "matched_pixels": n_matched}
 
 
-def adjoint_measure(M, dev, peaks) -> dict:
+def adjoint_measure(M, dev, peaks, H=384, W=512) -> dict:
     """The adjoint (a9) on the differentiation workload (32 keyframes, 96
-    edges, 512 x 384, FP16 storage): gradient of c E_g + a . tau (one GN step)
-    with respect to the canonical pointmaps and the confidences."""
+    edges, 512 x 384 unless smaller, FP16 storage): gradient of c E_g +
+    a . tau (one GN step) with respect to the canonical pointmaps and the
+    confidences."""
     import synth
-    w = synth.differentiation(device=dev)
+    w = synth.differentiation(device=dev, H=H, W=W)
     arm = Arm(M, w, torch.float16, per_edge=False)
     arm.step()
     torch.cuda.synchronize()
@@ -655,7 +660,7 @@ def adjoint_measure(M, dev, peaks) -> dict:
     alg = n_matched * (6 + 6 + 4 + 2 + 12 + 12 + 4)
     gbs = alg / (ms * 1e-3) / 1e9
     hbm = float(peaks["hbm_gbs"])
-    return {"workload": "differentiation: 32 keyframes, 96 directed edges, 512x384, FP16 storage",
+    return {"workload": f"differentiation: 32 keyframes, 96 directed edges, {W}x{H}, FP16 storage",
             "ms": ms, "matched_pixels": n_matched, "status": int(st[0]),
             "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
                          "frac": round(gbs / hbm, 4), "algorithmic_bytes": int(alg)}}
@@ -664,6 +669,14 @@ def adjoint_measure(M, dev, peaks) -> dict:
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
+    if args.adjoint_only:
+        import paper_2412_12392_gb300 as M
+        torch.cuda.set_device(local)
+        H, W = (int(v) for v in args.hw.lower().split("x"))
+        out = adjoint_measure(M, torch.device("cuda", local), measured_peaks()[0], H, W)
+        if rank == 0:
+            print(json.dumps(out))
+        return
     if args.impl == "reference":
         out = run_reference(args, world, rank)
         if out is not None:

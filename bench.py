@@ -8,7 +8,7 @@ whole step (matching time included), summed over ranks.  Prints one JSON
 line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mslam|reference]
-                  [--workload global|tracking] [--form batched|plain]
+                  [--workload global|tracking|batched] [--form batched|plain]
 """
 from __future__ import annotations
 
@@ -35,7 +35,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mslam", choices=["mslam", "reference"])
-    ap.add_argument("--workload", default="global", choices=["global", "tracking"])
+    ap.add_argument("--workload", default="global", choices=["global", "tracking", "batched"],
+                    help="batched: 8 independent graphs (16-128 keyframes, 40-600 edges, 1,926 in all) in one plan; "
+                         "reports the device-resident step only (no plain, end-to-end or CPU legs)")
     ap.add_argument("--form", default="batched", choices=["batched", "plain"])
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 per-edge comparison")
     ap.add_argument("--no-e2e", action="store_true")
@@ -92,6 +94,16 @@ def sum_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
+def workload_name(w) -> str:
+    if "graphs" in w.meta:
+        sizes = sorted({f"{int(W)}x{int(H)}" for H, W in w.kf_hw.tolist()}, reverse=True)
+        return (f"{w.name}: {len(w.meta['graphs'])} graphs, {w.N} keyframes ({'/'.join(map(str, w.meta['graph_kf']))}), "
+                f"{w.E} directed edges ({'/'.join(map(str, w.meta['graph_edges']))}), {' and '.join(sizes)}, d={w.d}, "
+                f"{w.n_gn_iters} GN iters")
+    return (f"{w.name}: {w.N} keyframes, {w.E} directed edges, {int(w.kf_hw[0, 1])}x{int(w.kf_hw[0, 0])}, d={w.d}, "
+            f"{w.n_gn_iters} GN iters")
+
+
 def make_workload(args, rank: int, device, hw=None):
     """This rank's replica: an independent graph (seed offset by rank), so the
     per-GPU work is fixed as ranks are added (weak scaling)."""
@@ -99,6 +111,14 @@ def make_workload(args, rank: int, device, hw=None):
     H, W = hw if hw is not None else (384, 512)
     if args.workload == "tracking":
         return synth.tracking(device=device, seed=1 + 1000 * rank, H=H, W=W)
+    if args.workload == "batched":
+        # the eight graphs, each cast to FP16 storage as soon as it is made
+        # (the FP32 pools of all graphs together would be about 65 GB)
+        gs = []
+        for g in range(8):
+            gs.append(synth.batched_graph(g, device, seed_offset=1000 * rank).to_storage(torch.float16))
+            torch.cuda.empty_cache()
+        return synth.merge(gs, name="batched")
     if args.small:
         return synth.global_graph(device=device, seed=2 + 1000 * rank, N=8, n_pairs=12, H=H, W=W)
     return synth.global_graph(device=device, seed=2 + 1000 * rank, H=H, W=W)
@@ -187,7 +207,7 @@ class Arm:
     def __init__(self, M, w, dtype, per_edge: bool, autotune: bool = False, opts=None):
         self.M, self.w, self.per_edge = M, w, per_edge
         self.P = M.default_params()
-        self.wd = w.to_storage(dtype)
+        self.wd = w if w.X_canon.dtype == dtype else w.to_storage(dtype)
         # descriptors in the kernel's chunk-planar layout (a one-off layout change)
         self.Dr = M.chunk_descriptors(self.wd.D_ref)
         self.Dq = M.chunk_descriptors(self.wd.D_qry)
@@ -195,10 +215,10 @@ class Arm:
         if autotune:
             from paper_2412_12392_gb300.autotune import autotune as tune
             wd = self.wd
-            self.tuning = tune(w.kf_hw.numpy(), w.edges.numpy(), None, self.P, wd.X_ref, wd.X_qry, self.Dr, self.Dq,
-                               wd.Q_ref, wd.Q_qry, wd.X_canon, w.T_init.to(wd.X_canon.device))
+            self.tuning = tune(w.kf_hw.numpy(), w.edges.numpy(), w.graph_of_kf.numpy(), self.P, wd.X_ref, wd.X_qry,
+                               self.Dr, self.Dq, wd.Q_ref, wd.Q_qry, wd.X_canon, w.T_init.to(wd.X_canon.device))
             opts = self.tuning["opts"]
-        self.plan = M.Plan(w.kf_hw.numpy(), w.edges.numpy(), opts=opts)
+        self.plan = M.Plan(w.kf_hw.numpy(), w.edges.numpy(), w.graph_of_kf.numpy(), opts=opts)
         dev = self.wd.X_canon.device
         self.idx = torch.empty(self.plan.edge_pixels, dtype=torch.int32, device=dev)
         self.q = torch.empty(self.plan.edge_pixels, dtype=dtype, device=dev)
@@ -370,8 +390,7 @@ def run_gpu(args, world, rank, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f16-storage/f32-math/f64-solve" if esz == 2 else
         "f32/f64-solve", "data": "synthetic (seeded box-room pointmaps, no network or dataset)",
-        "config": {"workload": f"{w.name}: {w.N} keyframes, {w.E} directed edges, "
-                               f"{int(w.kf_hw[0, 1])}x{int(w.kf_hw[0, 0])}, d={d}, {w.n_gn_iters} GN iters",
+        "config": {"workload": workload_name(w),
                    "form": args.form, "launch_shapes": arm.plan.opts, "global_batch": w.E, "seq_len": None,
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (per-step edge pools of several GB)"},
@@ -590,9 +609,7 @@ def run_reference(args, world, rank):
     return {"metric": METRIC, "value": val, "unit": "matched-pixel GN iters/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{w.name}: {w.N} keyframes, {w.E} directed edges, "
-                                   f"{int(w.kf_hw[0, 1])}x{int(w.kf_hw[0, 0])}, d={w.d}",
-                       "parallelism": "host cores (OpenMP)"},
+            "config": {"workload": workload_name(w), "parallelism": "host cores (OpenMP)"},
             "impl": "reference", "cpu_baseline": cb,
             "e2e": {"value": val, "unit": "matched-pixel GN iters/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}, "wall_s": wall}
@@ -629,13 +646,13 @@ def tracking_frame(M, dev, peaks) -> dict:
             "gn_iter_ms": float(np.mean([a.elapsed_time(c) for a, b, c in lins])), "matched_pixels": n_matched}
 
 
-def adjoint_measure(M, dev, peaks, H=384, W=512) -> dict:
+def adjoint_measure(M, dev, peaks, img_h=384, img_w=512) -> dict:
     """The adjoint (a9) on the differentiation workload (32 keyframes, 96
     edges, 512 x 384 unless smaller, FP16 storage): gradient of c E_g +
     a . tau (one GN step) with respect to the canonical pointmaps and the
     confidences."""
     import synth
-    w = synth.differentiation(device=dev, H=H, W=W)
+    w = synth.differentiation(device=dev, H=img_h, W=img_w)
     arm = Arm(M, w, torch.float16, per_edge=False)
     arm.step()
     torch.cuda.synchronize()
@@ -660,7 +677,7 @@ def adjoint_measure(M, dev, peaks, H=384, W=512) -> dict:
     alg = n_matched * (6 + 6 + 4 + 2 + 12 + 12 + 4)
     gbs = alg / (ms * 1e-3) / 1e9
     hbm = float(peaks["hbm_gbs"])
-    return {"workload": f"differentiation: 32 keyframes, 96 directed edges, {W}x{H}, FP16 storage",
+    return {"workload": f"differentiation: 32 keyframes, 96 directed edges, {img_w}x{img_h}, FP16 storage",
             "ms": ms, "matched_pixels": n_matched, "status": int(st[0]),
             "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
                          "frac": round(gbs / hbm, 4), "algorithmic_bytes": int(alg)}}
@@ -668,6 +685,10 @@ def adjoint_measure(M, dev, peaks, H=384, W=512) -> dict:
 
 def main():
     args = parse()
+    if args.workload == "batched":
+        # tens of GB of device pools: the FP32 plain form, the pinned host
+        # copies and the host-side oracle sample are measured on the global graph
+        args.no_plain = args.no_e2e = args.no_cpu = True
     world, rank, local = dist_setup(args)
     if args.adjoint_only:
         import paper_2412_12392_gb300 as M

@@ -150,9 +150,11 @@ typedef struct {
   int32_t lin_blocks_per_sm;
   int32_t match_block_w;
   int32_t lin_form;  /* packed linearisation of the FP16 ray family: 0 = records streamed through
-                        shared memory by bulk asynchronous copies and evaluated two at a time with
-                        paired FP32 instructions (default), 1 = per-thread register pipeline.  FP32 storage and
-                        the other residual families always use the register pipeline. */
+                        shared memory by bulk asynchronous copies, one pipeline per block, and
+                        evaluated two at a time with paired FP32 instructions (default), 1 =
+                        per-thread register pipeline, 2 = the streamed form with one pipeline per
+                        warp (a warp takes whole tiles; suits tiles of 1024-4096 pixels).  FP32
+                        storage and the other residual families always use the register pipeline. */
   int32_t solve_form;  /* 0 = FP32 factorisation of the diagonally scaled system with FP64 iterative
                           refinement to the FP64 solution (default; graphs it declines go to the FP64
                           factorisation), 1 = FP64 factorisation only */

@@ -19,6 +19,8 @@ from . import api
 MATCH_WIDTHS = (4, 8, 16, 32, 64)
 LIN_TILES = (4096, 8192, 16384)
 LIN_BLOCKS = (0, 2, 3, 4)
+WARP_STREAM_TILES = (1024, 2048, 4096)
+FORM_NAMES = {0: "stream", 1: "regs", 2: "warp"}
 
 
 def _time(fn, reps: int) -> float:
@@ -56,8 +58,10 @@ def autotune(kf_hw, edges, graph_of_kf, params, X_ref, X_qry, D_ref, D_qry, Q_re
     idx, q = api.match(api.Plan(kf_hw, edges, graph_of_kf), params, X_ref, X_qry, D_ref, D_qry, Q_ref, Q_qry)
     best_lin, best_lt = None, float("inf")
     shapes = [(tile, bps, 1) for tile, bps in itertools.product(lin_tiles, lin_blocks)]
-    # the streamed form runs one CTA per SM and favours large tiles
+    # the block-streamed form runs one CTA per SM and favours large tiles;
+    # the warp-streamed form gives each warp whole tiles and favours small ones
     shapes += [(tile, 0, 0) for tile in sorted(set(lin_tiles) | {32768, 65536})]
+    shapes += [(tile, 0, 2) for tile in WARP_STREAM_TILES]
     for tile, bps, form in shapes:
         plan = api.Plan(kf_hw, edges, graph_of_kf, opts={"lin_tile": tile, "lin_blocks_per_sm": bps,
                                                         "lin_form": form})
@@ -72,7 +76,7 @@ def autotune(kf_hw, edges, graph_of_kf, params, X_ref, X_qry, D_ref, D_qry, Q_re
 
         ms = _time(run_lin, reps)
         pms = report["pack_ms"].setdefault(tile, _time(run_pack, reps))
-        report["lin_ms"][f"{tile}/{bps}/{'stream' if form == 0 else 'regs'}"] = ms
+        report["lin_ms"][f"{tile}/{bps}/{FORM_NAMES[form]}"] = ms
         score = gn_iters * ms + pms
         if score < best_lt:
             best_lin, best_lt = (tile, bps, form), score

@@ -322,7 +322,7 @@ inline size_t lin_partials_bytes(int n_tiles) {
 size_t pack_bytes(int n_tiles, int lin_tile, mslam_dtype dt);
 // Persistent-grid size of the linearisation launches (0 = occupancy maximum).
 int plan_lin_blocks_per_sm(const mslam_plan* plan);
-int plan_lin_form(const mslam_plan* plan);  // 0 streamed, 1 register pipeline
+int plan_lin_form(const mslam_plan* plan);  // 0 block-streamed, 1 register pipeline, 2 warp-streamed
 int plan_solve_form(const mslam_plan* plan);  // 0 mixed precision, 1 FP64 only
 int64_t plan_max_mixed_bytes(const mslam_plan* plan);  // shared memory of the mixed-precision solve
 int64_t plan_max_mixed_elems(const mslam_plan* plan);  // elements of its assembly kernel

@@ -808,27 +808,175 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
   }
 }
 
-// One block per edge: FP64 sum of the edge's tile partials, then the 14x14.
-__global__ void __launch_bounds__(64) lin_finalize_kernel(PlanView pv, const double* __restrict__ T_wc,
+// ------------------------------------------------- per-warp streamed form
+// The paired-FP32 evaluation of lin_stream_kernel with one pipeline per warp
+// instead of one per block: every warp claims whole tiles from the tile
+// counter, its lane 0 copies the tile's 16-byte records ahead into the
+// warp's own ring of three 4 KB stages with bulk asynchronous copies
+// (completion counted on one mbarrier per stage), and the warp reduces a
+// finished tile by itself (reduce-scatter, then 30 lanes store the tile's
+// partial).  No block-wide barrier is taken: warps drift apart, so loads,
+// arithmetic and reductions of different warps overlap, and a stage is
+// refilled as soon as its own warp has read it.  Tiles are smaller than in
+// the block form (a warp takes a whole tile), which the plan's lin_tile sets.
+constexpr int kWarpStreamThreads = 512;
+constexpr int kWarpStreamWarps = kWarpStreamThreads / 32;
+constexpr int kWarpStages = 3;
+constexpr int kWarpStageRecs = 256;  // four pairs of records per lane
+constexpr int kWarpStageBytes = kWarpStageRecs * 16;
+constexpr size_t kWarpStreamSmem = (size_t)kWarpStreamWarps * kWarpStages * kWarpStageBytes;  // 192 KB
+
+__global__ void __launch_bounds__(kWarpStreamThreads, 1)
+    lin_warp_stream_kernel(PlanView pv, LinConst lc, const RelPose* __restrict__ rel,
+                           const unsigned char* __restrict__ recs, const int32_t* __restrict__ counts,
+                           float* __restrict__ partials, int tile_begin, int tile_end, int* __restrict__ tile_ctr) {
+  extern __shared__ __align__(128) unsigned char wstage[];
+  __shared__ __align__(8) uint64_t full[kWarpStreamWarps][kWarpStages];
+  __shared__ int m_tile[kWarpStreamWarps][kWarpStages], m_n[kWarpStreamWarps][kWarpStages],
+      m_last[kWarpStreamWarps][kWarpStages];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned char* ring = wstage + (size_t)warp * kWarpStages * kWarpStageBytes;
+  uint64_t* bars = full[warp];
+  const int gwarp = (int)blockIdx.x * kWarpStreamWarps + warp, nwarps = (int)gridDim.x * kWarpStreamWarps;
+
+  // producer state (lane 0): the tile being copied and its next record
+  int p_tile = -1, p_cnt = 0, p_off = 0;
+  auto claim = [&]() {
+    p_tile = tile_ctr ? tile_begin + atomicAdd(tile_ctr, 1) : (p_tile < 0 ? tile_begin + gwarp : p_tile + nwarps);
+    p_off = 0;
+    p_cnt = p_tile < tile_end ? __ldg(counts + p_tile) : 0;
+  };
+  auto issue = [&](int slot) {
+    if (p_tile >= tile_end) {  // end marker
+      m_tile[warp][slot] = -1;
+      mbar_arrive(&bars[slot]);
+      return;
+    }
+    const int n = min(kWarpStageRecs, p_cnt - p_off);
+    m_tile[warp][slot] = p_tile;
+    m_n[warp][slot] = n;
+    m_last[warp][slot] = (p_off + n >= p_cnt);
+    if (n > 0) {
+      mbar_arrive_tx(&bars[slot], (uint32_t)(n * 16));
+      bulk_g2s(ring + slot * kWarpStageBytes, recs + ((size_t)p_tile * pv.lin_tile + p_off) * 16, (uint32_t)(n * 16),
+               &bars[slot]);
+    } else {
+      mbar_arrive(&bars[slot]);
+    }
+    p_off += n;
+    if (p_off >= p_cnt) claim();
+  };
+  if (lane == 0) {
+    for (int sl = 0; sl < kWarpStages; ++sl) mbar_init(&bars[sl], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    claim();
+    for (int sl = 0; sl < kWarpStages; ++sl) issue(sl);
+  }
+  __syncwarp();
+
+  f2 acc[kNumAcc];
+#pragma unroll
+  for (int a = 0; a < kNumAcc; ++a) acc[a] = mk2(0.0f, 0.0f);
+  int cur_tile = -1;
+  f2 Rp[12];
+  bool aborted = false;
+  for (int k = 0;; ++k) {
+    const int slot = k % kWarpStages;
+    const uint32_t parity = (uint32_t)((k / kWarpStages) & 1);
+    const bool ok = mbar_wait_bounded(&bars[slot], parity);
+    if (__any_sync(0xffffffffu, !ok)) {
+      aborted = true;
+      break;
+    }
+    const int tile = m_tile[warp][slot];
+    if (tile < 0) break;
+    if (tile != cur_tile) {
+      const float4* src = reinterpret_cast<const float4*>(rel + pv.tiles[tile].edge);
+      const float4 a = __ldg(src), b = __ldg(src + 1), c4 = __ldg(src + 2);
+      Rp[0] = bc2(a.x); Rp[1] = bc2(a.y); Rp[2] = bc2(a.z); Rp[3] = bc2(a.w);
+      Rp[4] = bc2(b.x); Rp[5] = bc2(b.y); Rp[6] = bc2(b.z); Rp[7] = bc2(b.w);
+      Rp[8] = bc2(c4.x); Rp[9] = bc2(c4.y); Rp[10] = bc2(c4.z); Rp[11] = bc2(c4.w);
+      cur_tile = tile;
+    }
+    const int n = m_n[warp][slot], h = (n + 1) >> 1;  // records j and j + h form pair j
+    const bool last = m_last[warp][slot] != 0;
+    const uint4* rec = reinterpret_cast<const uint4*>(ring + slot * kWarpStageBytes);
+#pragma unroll
+    for (int u = 0; u < kWarpStageRecs / 64; ++u) {
+      const int ra = lane + 32 * u, rb = ra + h;
+      if (ra < h) {
+        const bool vb = rb < n;
+        const uint4 a = rec[ra], b = vb ? rec[rb] : make_uint4(0u, 0u, 0u, 0u);
+        auto pr = [](uint32_t x, uint32_t y, uint32_t sel) {
+          const uint32_t v = __byte_perm(x, y, sel);
+          return __half22float2(*reinterpret_cast<const __half2*>(&v));
+        };
+        accumulate_pair(acc, Rp, pr(a.x, b.x, 0x5410), pr(a.x, b.x, 0x7632), pr(a.y, b.y, 0x5410),
+                        pr(a.y, b.y, 0x7632), pr(a.z, b.z, 0x5410), pr(a.z, b.z, 0x7632), pr(a.w, b.w, 0x5410), vb,
+                        lc);
+      }
+    }
+    if (last) {
+      // the tile is complete: the warp's sums by reduce-scatter, lane a
+      // stores value a of the tile's partial
+      float v[32];
+#pragma unroll
+      for (int a = 0; a < kNumAcc; ++a) {
+        v[a] = acc[a].x + acc[a].y;
+        acc[a] = mk2(0.0f, 0.0f);
+      }
+      v[30] = v[31] = 0.0f;
+      const float sum = warp_reduce_scatter(v, lane);
+      if (lane < kNumAcc) partials[(size_t)tile * kAccStride + lane] = sum;
+    }
+    __syncwarp();  // every lane is done with this stage
+    if (lane == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(slot);
+    }
+  }
+  if (aborted) {
+    // a copy did not complete in time: poison every tile's partial (the
+    // solve then reports a non-finite system) and let this warp's copies in
+    // flight land before the block's shared memory is released
+    for (int t = tile_begin + lane; t < tile_end; t += 32) partials[(size_t)t * kAccStride] = __int_as_float(0x7fc00000);
+    if (lane == 0)
+      for (int sl = 0; sl < kWarpStages; ++sl) mbar_wait_bounded(&bars[sl], 0), mbar_wait_bounded(&bars[sl], 1);
+    __syncwarp();
+  }
+}
+
+// One block per edge: FP64 sum of the edge's tile partials (four groups of
+// threads take every fourth tile, then the groups' sums are added in a fixed
+// order), then the 14x14.
+constexpr int kFinalizeThreads = 256;
+__global__ void __launch_bounds__(kFinalizeThreads) lin_finalize_kernel(PlanView pv, const double* __restrict__ T_wc,
                                                           const float* __restrict__ partials,
                                                           float* __restrict__ H14, float* __restrict__ g14,
                                                           double* __restrict__ cost, int32_t* __restrict__ n_valid,
                                                           int e_begin, int kind) {
   const int e = e_begin + blockIdx.x;
   const DevEdge ed = pv.edges[e];
-  __shared__ double S[kFamAcc];
+  __shared__ double S[kFamAcc], Sg[kFinalizeThreads / 64][kFamAcc];
   __shared__ double Hr[49], A[49], C[49], g[7];
   const int tid = threadIdx.x;
   const int NA = kind == MSLAM_RES_RAY ? kNumAcc : kFamAcc;
-  if (tid < NA) {
-    double s = 0.0;
-    for (int t = ed.tile_begin; t < ed.tile_end; ++t) s += (double)partials[(size_t)t * kAccStride + tid];
-    S[tid] = s;
+  {
+    const int a = tid & 63, grp = tid >> 6;
+    if (a < NA) {
+      double s = 0.0;
+#pragma unroll 8
+      for (int t = ed.tile_begin + grp; t < ed.tile_end; t += kFinalizeThreads / 64)
+        s += (double)partials[(size_t)t * kAccStride + a];
+      Sg[grp][a] = s;
+    }
   }
   if (tid == 32) {
     const Sim3d Ti = load_pose(T_wc + 8 * ed.i);
     adjoint_of(inverse(Ti), A);
   }
+  __syncthreads();
+  if (tid < NA) S[tid] = (Sg[0][tid] + Sg[1][tid]) + (Sg[2][tid] + Sg[3][tid]);
   __syncthreads();
   if (tid == 0 && kind != MSLAM_RES_RAY) {
     // other families: the 28 upper-triangle sums, then g, cost and count
@@ -919,15 +1067,20 @@ static int persistent_grid(const mslam_plan* plan, K kernel) {
 
 using namespace mslam;
 
-// Whether the packed linearisation of these parameters and plan takes the
-// streamed form (the FP16 ray family with plan option lin_form 0), whose
-// records mslam_gn_pack writes in pairs.
-static bool stream_form(const mslam_params* p, const mslam_plan* plan, mslam_dtype dt) {
-  return p->residual == MSLAM_RES_RAY && dt == MSLAM_F16 && plan_lin_form(plan) == 0;
+// The kernel of the packed linearisation for these parameters and plan:
+// the FP16 ray family takes the block-streamed form (plan option lin_form
+// 0) or the warp-streamed form (lin_form 2); lin_form 1, FP32 records and
+// the other families take the register pipeline.
+enum PackedForm { kFormRegs = 0, kFormBlockStream = 1, kFormWarpStream = 2 };
+static PackedForm packed_form(const mslam_params* p, const mslam_plan* plan, mslam_dtype dt) {
+  if (p->residual != MSLAM_RES_RAY || dt != MSLAM_F16) return kFormRegs;
+  const int f = plan_lin_form(plan);
+  return f == 0 ? kFormBlockStream : f == 2 ? kFormWarpStream : kFormRegs;
 }
 
-// Opt the streamed kernels into their dynamic shared memory, once per device.
-static mslam_status stream_kernel_setup(size_t smem) {
+// Opt a streamed kernel into its dynamic shared memory, once per device.
+template <PackedForm kForm, typename K>
+static mslam_status stream_kernel_setup(K kernel, size_t smem) {
   static std::mutex mu;
   static bool done[64] = {};
   int dev = 0;
@@ -935,7 +1088,7 @@ static mslam_status stream_kernel_setup(size_t smem) {
   if (st != MSLAM_OK) return st;
   std::lock_guard<std::mutex> lock(mu);
   if (dev >= 0 && dev < 64 && done[dev]) return MSLAM_OK;
-  st = cuda_check(cudaFuncSetAttribute(lin_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+  st = cuda_check(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                   "cudaFuncSetAttribute");
   if (st != MSLAM_OK) return st;
   if (dev >= 0 && dev < 64) done[dev] = true;
@@ -1036,11 +1189,11 @@ extern "C" mslam_status mslam_gn_linearize(const mslam_params* p, const mslam_pl
         int t0, t1;
         plan_edge_tiles(plan, e, &t0, &t1);
         launch(t1 - t0, t0, t1, nullptr);
-        lin_finalize_kernel<<<1, 64, 0, s>>>(pv, T_wc, partials, H_blocks, g_blocks, cost, n_valid, e, kK);
+        lin_finalize_kernel<<<1, kFinalizeThreads, 0, s>>>(pv, T_wc, partials, H_blocks, g_blocks, cost, n_valid, e, kK);
       }
     } else {
       launch(std::min(pv.n_tiles, persistent_grid(plan, lin_tiles_kernel<float, kK>)), 0, pv.n_tiles, ctr);
-      lin_finalize_kernel<<<pv.E, 64, 0, s>>>(pv, T_wc, partials, H_blocks, g_blocks, cost, n_valid, 0, kK);
+      lin_finalize_kernel<<<pv.E, kFinalizeThreads, 0, s>>>(pv, T_wc, partials, H_blocks, g_blocks, cost, n_valid, 0, kK);
     }
   });
   return cuda_check(cudaGetLastError(), "gn_linearize launch");
@@ -1140,18 +1293,28 @@ extern "C" mslam_status mslam_gn_linearize_packed(const mslam_params* p, const m
   int* ctr = tile_counter(rel, pv.E);
   rel_pose_kernel<<<(pv.E + 127) / 128, 128, 0, s>>>(pv, T_wc, rel, ctr);
   const size_t stream_smem = (size_t)kStreamStages * kStreamChunkBytes;
-  const bool streamed = stream_form(p, plan, dt);
-  if (streamed) {
-    mslam_status st2 = stream_kernel_setup(stream_smem);
+  const PackedForm form = packed_form(p, plan, dt);
+  if (form != kFormRegs) {
+    mslam_status st2 = form == kFormBlockStream
+                           ? stream_kernel_setup<kFormBlockStream>(lin_stream_kernel, stream_smem)
+                           : stream_kernel_setup<kFormWarpStream>(lin_warp_stream_kernel, kWarpStreamSmem);
     if (st2 != MSLAM_OK) return st2;
   }
+  const unsigned char* rec_bytes = static_cast<const unsigned char*>(packed);
   with_family(p->residual, [&](auto K) {
     constexpr int kK = decltype(K)::value;
     auto launch = [&](int grid, int t0, int t1, int* c) {
-      if (kK == MSLAM_RES_RAY && streamed) {
-        // the FP16 ray family streams its paired records through shared memory
-        lin_stream_kernel<<<grid, kStreamThreads, stream_smem, s>>>(pv, lc, rel, static_cast<const unsigned char*>(packed),
-                                                                   counts, partials, t0, t1, c);
+      // the FP16 ray family streams its records through shared memory
+      if (kK == MSLAM_RES_RAY && form == kFormBlockStream) {
+        lin_stream_kernel<<<grid, kStreamThreads, stream_smem, s>>>(pv, lc, rel, rec_bytes, counts, partials, t0, t1,
+                                                                   c);
+        return;
+      }
+      if (kK == MSLAM_RES_RAY && form == kFormWarpStream) {
+        // a warp takes a whole tile: without the counter, one warp per tile
+        const int g = c ? grid : (t1 - t0 + kWarpStreamWarps - 1) / kWarpStreamWarps;
+        lin_warp_stream_kernel<<<g, kWarpStreamThreads, kWarpStreamSmem, s>>>(pv, lc, rel, rec_bytes, counts,
+                                                                             partials, t0, t1, c);
         return;
       }
       if (dt == MSLAM_F32)
@@ -1164,18 +1327,18 @@ extern "C" mslam_status mslam_gn_linearize_packed(const mslam_params* p, const m
         int t0, t1;
         plan_edge_tiles(plan, e, &t0, &t1);
         launch(t1 - t0, t0, t1, nullptr);
-        lin_finalize_kernel<<<1, 64, 0, s>>>(pv, T_wc, partials, H_blocks, g_blocks, cost, n_valid, e, kK);
+        lin_finalize_kernel<<<1, kFinalizeThreads, 0, s>>>(pv, T_wc, partials, H_blocks, g_blocks, cost, n_valid, e, kK);
       }
     } else {
       int grid = persistent_grid(plan, lin_packed_kernel<__half, kK>);
-      if (kK == MSLAM_RES_RAY && streamed) {
+      if (kK == MSLAM_RES_RAY && form != kFormRegs) {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         grid = std::max(1, sms);  // one streaming CTA per SM
       }
       launch(std::min(pv.n_tiles, grid), 0, pv.n_tiles, ctr);
-      lin_finalize_kernel<<<pv.E, 64, 0, s>>>(pv, T_wc, partials, H_blocks, g_blocks, cost, n_valid, 0, kK);
+      lin_finalize_kernel<<<pv.E, kFinalizeThreads, 0, s>>>(pv, T_wc, partials, H_blocks, g_blocks, cost, n_valid, 0, kK);
     }
   });
   return cuda_check(cudaGetLastError(), "gn_linearize_packed launch");

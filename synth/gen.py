@@ -583,16 +583,20 @@ BATCHED_EDGES = [40, 64, 96, 150, 256, 320, 400, 600]
 BATCHED_LOWRES = (1, 3, 6)
 
 
+def batched_graph(g: int, device="cpu", scale: int = 1, seed_offset: int = 0) -> Workload:
+    """Graph g (0..7) of the batched workload: seed 100 + g (+ seed_offset),
+    BATCHED_KF[g] keyframes, BATCHED_EDGES[g] directed edges, 256 x 192 for
+    the graphs in BATCHED_LOWRES and 512 x 384 otherwise (divided by scale)."""
+    H, W = (192, 256) if g in BATCHED_LOWRES else (384, 512)
+    return global_graph(device, 100 + g + seed_offset, BATCHED_KF[g], BATCHED_EDGES[g] // 2, H // scale, W // scale,
+                        name=f"batched{g}")
+
+
 def batched(device="cpu", scale: int = 1) -> List[Workload]:
     """Eight independent keyframe graphs (seeds 100 + g) with 16..128
     keyframes and 40..600 directed edges; graphs 1, 3, 6 at 256 x 192 and the
     rest at 512 x 384 (both divided by `scale`)."""
-    out = []
-    for g in range(8):
-        H, W = (192, 256) if g in BATCHED_LOWRES else (384, 512)
-        out.append(global_graph(device, 100 + g, BATCHED_KF[g], BATCHED_EDGES[g] // 2, H // scale, W // scale,
-                                name=f"batched{g}"))
-    return out
+    return [batched_graph(g, device, scale) for g in range(8)]
 
 
 def differentiation(device="cpu", seed: int = 3, H: int = 384, W: int = 512) -> Workload:

@@ -67,7 +67,7 @@ def test_batched_graphs_against_oracle_per_graph(M, graphs):
 
 
 def test_autotuner_choice_is_equivalent(M, graphs):
-    from paper_2412_12392_gb300.autotune import LIN_TILES, MATCH_WIDTHS, autotune
+    from paper_2412_12392_gb300.autotune import LIN_TILES, MATCH_WIDTHS, WARP_STREAM_TILES, autotune
     P = M.default_params()
     mw = synth.merge(graphs[:4])
     wd = mw.to("cuda")
@@ -76,8 +76,9 @@ def test_autotuner_choice_is_equivalent(M, graphs):
     rep = autotune(mw.kf_hw.numpy(), mw.edges.numpy(), mw.graph_of_kf.numpy(), P, wd.X_ref, wd.X_qry, Dr, Dq,
                    wd.Q_ref, wd.Q_qry, wd.X_canon, T0, reps=2)
     opts = rep["opts"]
-    assert opts["match_block_w"] in MATCH_WIDTHS and opts["lin_tile"] in set(LIN_TILES) | {32768, 65536}
-    assert opts["lin_form"] in (0, 1)
+    assert opts["match_block_w"] in MATCH_WIDTHS
+    assert opts["lin_tile"] in set(LIN_TILES) | {32768, 65536} | set(WARP_STREAM_TILES)
+    assert opts["lin_form"] in (0, 1, 2)
     out = []
     for o in (None, opts):
         plan = M.Plan(mw.kf_hw.numpy(), mw.edges.numpy(), mw.graph_of_kf.numpy(), opts=o)

@@ -352,6 +352,39 @@ def test_packed_linearize_parity(M, tiny_wl, dtype):
     assert block_rel_err(H, H3).max() <= 1e-6 and torch.equal(nv, nv3)
 
 
+@pytest.mark.parametrize("form,tile", [(0, 8192), (1, 8192), (2, 1024), (2, 4096)])
+def test_packed_linearize_forms(M, tiny_wl, form, tile):
+    """Every packed linearisation form of the FP16 ray family (block-streamed,
+    register pipeline, warp-streamed) against the oracle at tile sizes that
+    give several tiles per edge with ragged record counts; the per-edge and
+    batched launches of a form agree bitwise, and the forms agree up to FP32
+    summation order."""
+    P = M.default_params()
+    par = M.params_dict(P)
+    ws = tiny_wl.to_storage(torch.float16)
+    idx_r, q_r, _ = oracle_match_all(ws, par, diag=False)
+    q_s = torch.from_numpy(q_r).to(torch.float16)
+    wd = ws.to("cuda")
+    T = ws.T_init.clone().cuda()
+    idx_d, q_d = torch.from_numpy(idx_r).cuda(), q_s.cuda()
+    plan = M.Plan(ws.kf_hw.numpy(), ws.edges.numpy(), opts={"lin_form": form, "lin_tile": tile})
+    packed = M.gn_pack(plan, P, wd.X_canon, idx_d, q_d)
+    H, g, c, nv = M.gn_linearize_packed(plan, P, torch.float16, T, packed)
+    H2, g2, c2, nv2 = M.gn_linearize_packed(plan, P, torch.float16, T, packed, per_edge=True)
+    torch.cuda.synchronize()
+    assert torch.equal(H, H2) and torch.equal(g, g2) and torch.equal(c, c2) and torch.equal(nv, nv2)
+    Hr, gr, cr, nvr = oracle_blocks(ws, ws.T_init.numpy(), idx_r, q_s, par)
+    eh, eg = block_rel_err(H, Hr), block_rel_err(g, gr)
+    print(f"packed linearize form {form} tile {tile}: max H rel {eh.max():.2e}, g rel {eg.max():.2e}")
+    assert eh.max() <= BLOCK_RTOL and eg.max() <= BLOCK_RTOL
+    assert np.allclose(f64(c), cr, rtol=1e-5)
+    assert np.array_equal(nv.cpu().numpy(), nvr)
+    ref_plan = M.Plan(ws.kf_hw.numpy(), ws.edges.numpy(), opts={"lin_form": 1})
+    H3, g3, c3, nv3 = M.gn_linearize_packed(ref_plan, P, torch.float16, T,
+                                            M.gn_pack(ref_plan, P, wd.X_canon, idx_d, q_d))
+    assert block_rel_err(H, H3).max() <= 1e-6 and block_rel_err(g, g3).max() <= 1e-5 and torch.equal(nv, nv3)
+
+
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
 def test_packed_gauss_newton_parity(M, tiny_wl, dtype):
     P = M.default_params()

@@ -641,9 +641,13 @@ def tracking_frame(M, dev, peaks) -> dict:
     torch.cuda.synchronize()
     m0, m1, p1, lins = ev[0]
     n_matched = int(((arm.idx >= 0) & (arm.q.float() > arm.P.q_min)).sum())
+    # the frame's launches (a few microseconds of work each) replayed as one CUDA graph
+    arm.capture()
+    gms = _event_ms(arm.step_graph, 20)
     return {"workload": "tracking: 1 frame against 1 keyframe, 512x384, radial camera, d=24, 20 GN iters",
-            "ms_per_frame": ms, "match_ms": m0.elapsed_time(m1), "pack_ms": m1.elapsed_time(p1),
-            "gn_iter_ms": float(np.mean([a.elapsed_time(c) for a, b, c in lins])), "matched_pixels": n_matched}
+            "ms_per_frame": ms, "ms_per_frame_cuda_graph": gms, "match_ms": m0.elapsed_time(m1),
+            "pack_ms": m1.elapsed_time(p1), "gn_iter_ms": float(np.mean([a.elapsed_time(c) for a, b, c in lins])),
+            "matched_pixels": n_matched, "launches_per_frame": arm.launches_per_step()}
 
 
 def adjoint_measure(M, dev, peaks, img_h=384, img_w=512) -> dict:

@@ -878,7 +878,10 @@ __global__ void __launch_bounds__(kWarpStreamThreads, 1)
 #pragma unroll
   for (int a = 0; a < kNumAcc; ++a) acc[a] = mk2(0.0f, 0.0f);
   int cur_tile = -1;
-  f2 Rp[12];
+  // the relative pose of the current tile, pairs (v, v), in the warp's slot
+  // of shared memory (read as broadcasts; keeps 24 registers free)
+  __shared__ f2 rp_s[kWarpStreamWarps][12];
+  f2* Rp = rp_s[warp];
   bool aborted = false;
   for (int k = 0;; ++k) {
     const int slot = k % kWarpStages;
@@ -892,29 +895,29 @@ __global__ void __launch_bounds__(kWarpStreamThreads, 1)
     if (tile < 0) break;
     if (tile != cur_tile) {
       const float4* src = reinterpret_cast<const float4*>(rel + pv.tiles[tile].edge);
-      const float4 a = __ldg(src), b = __ldg(src + 1), c4 = __ldg(src + 2);
-      Rp[0] = bc2(a.x); Rp[1] = bc2(a.y); Rp[2] = bc2(a.z); Rp[3] = bc2(a.w);
-      Rp[4] = bc2(b.x); Rp[5] = bc2(b.y); Rp[6] = bc2(b.z); Rp[7] = bc2(b.w);
-      Rp[8] = bc2(c4.x); Rp[9] = bc2(c4.y); Rp[10] = bc2(c4.z); Rp[11] = bc2(c4.w);
+      if (lane < 12) {  // the previous tile's reads ended at the last stage's __syncwarp
+        const float4 v4 = __ldg(src + lane / 4);
+        Rp[lane] = bc2((lane & 3) == 0 ? v4.x : (lane & 3) == 1 ? v4.y : (lane & 3) == 2 ? v4.z : v4.w);
+      }
+      __syncwarp();
       cur_tile = tile;
     }
     const int n = m_n[warp][slot], h = (n + 1) >> 1;  // records j and j + h form pair j
     const bool last = m_last[warp][slot] != 0;
     const uint4* rec = reinterpret_cast<const uint4*>(ring + slot * kWarpStageBytes);
+    auto pair_at = [&](int ra, bool vb) {
+      const uint4 a = rec[ra], b = vb ? rec[ra + h] : make_uint4(0u, 0u, 0u, 0u);
+      auto pr = [](uint32_t x, uint32_t y, uint32_t sel) {
+        const uint32_t v = __byte_perm(x, y, sel);
+        return __half22float2(*reinterpret_cast<const __half2*>(&v));
+      };
+      accumulate_pair(acc, Rp, pr(a.x, b.x, 0x5410), pr(a.x, b.x, 0x7632), pr(a.y, b.y, 0x5410),
+                      pr(a.y, b.y, 0x7632), pr(a.z, b.z, 0x5410), pr(a.z, b.z, 0x7632), pr(a.w, b.w, 0x5410), vb, lc);
+    };
 #pragma unroll
     for (int u = 0; u < kWarpStageRecs / 64; ++u) {
-      const int ra = lane + 32 * u, rb = ra + h;
-      if (ra < h) {
-        const bool vb = rb < n;
-        const uint4 a = rec[ra], b = vb ? rec[rb] : make_uint4(0u, 0u, 0u, 0u);
-        auto pr = [](uint32_t x, uint32_t y, uint32_t sel) {
-          const uint32_t v = __byte_perm(x, y, sel);
-          return __half22float2(*reinterpret_cast<const __half2*>(&v));
-        };
-        accumulate_pair(acc, Rp, pr(a.x, b.x, 0x5410), pr(a.x, b.x, 0x7632), pr(a.y, b.y, 0x5410),
-                        pr(a.y, b.y, 0x7632), pr(a.z, b.z, 0x5410), pr(a.z, b.z, 0x7632), pr(a.w, b.w, 0x5410), vb,
-                        lc);
-      }
+      const int ra = lane + 32 * u;
+      if (ra < h) pair_at(ra, ra + h < n);
     }
     if (last) {
       // the tile is complete: the warp's sums by reduce-scatter, lane a

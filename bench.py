@@ -634,7 +634,7 @@ def tracking_frame(M, dev, peaks) -> dict:
     Gauss-Newton iterations on the ray error (1 edge, the keyframe fixed)."""
     import synth
     w = synth.tracking(device=dev)
-    arm = Arm(M, w, torch.float16, per_edge=False)
+    arm = Arm(M, w, torch.float16, per_edge=False, autotune=True)
     ms = _event_ms(arm.step, 20)
     ev = []
     arm.step(ev)
@@ -647,7 +647,8 @@ def tracking_frame(M, dev, peaks) -> dict:
     return {"workload": "tracking: 1 frame against 1 keyframe, 512x384, radial camera, d=24, 20 GN iters",
             "ms_per_frame": ms, "ms_per_frame_cuda_graph": gms, "match_ms": m0.elapsed_time(m1),
             "pack_ms": m1.elapsed_time(p1), "gn_iter_ms": float(np.mean([a.elapsed_time(c) for a, b, c in lins])),
-            "matched_pixels": n_matched, "launches_per_frame": arm.launches_per_step()}
+            "matched_pixels": n_matched, "launches_per_frame": arm.launches_per_step(),
+            "launch_shapes": arm.plan.opts}
 
 
 def adjoint_measure(M, dev, peaks, img_h=384, img_w=512) -> dict:

@@ -582,6 +582,7 @@ __device__ __forceinline__ double asm_sum(const float* __restrict__ H14, const i
                                           const int32_t* __restrict__ asment, int b, int r, int c) {
   double s = 0.0;
   const int k1 = __ldg(asm_ptr + b + 1);
+#pragma unroll 4
   for (int k = __ldg(asm_ptr + b); k < k1; ++k) {
     const int code = __ldg(asment + k), edge = code >> 2, quad = code & 3;
     const int r0 = (quad == 0 || quad == 2) ? 0 : 7;
@@ -613,7 +614,9 @@ __global__ void __launch_bounds__(128) solve_scale_kernel(PlanView pv, const flo
   const int32_t* gasm_ptr = I + G.off_gasm;
   const int32_t* gasment = I + G.off_gasment;
   double sg = 0.0;
-  for (int j = __ldg(gasm_ptr + p); j < __ldg(gasm_ptr + p + 1); ++j) {
+  const int j1 = __ldg(gasm_ptr + p + 1);
+#pragma unroll 4
+  for (int j = __ldg(gasm_ptr + p); j < j1; ++j) {
     const int code = __ldg(gasment + j), edge = code >> 1, side = code & 1;
     sg += (double)__ldg(g14 + (size_t)edge * 14 + 7 * side + a);
   }

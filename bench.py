@@ -112,13 +112,7 @@ def make_workload(args, rank: int, device, hw=None):
     if args.workload == "tracking":
         return synth.tracking(device=device, seed=1 + 1000 * rank, H=H, W=W)
     if args.workload == "batched":
-        # the eight graphs, each cast to FP16 storage as soon as it is made
-        # (the FP32 pools of all graphs together would be about 65 GB)
-        gs = []
-        for g in range(8):
-            gs.append(synth.batched_graph(g, device, seed_offset=1000 * rank).to_storage(torch.float16))
-            torch.cuda.empty_cache()
-        return synth.merge(gs, name="batched")
+        return synth.batched_storage(device, torch.float16, seed_offset=1000 * rank)
     if args.small:
         return synth.global_graph(device=device, seed=2 + 1000 * rank, N=8, n_pairs=12, H=H, W=W)
     return synth.global_graph(device=device, seed=2 + 1000 * rank, H=H, W=W)

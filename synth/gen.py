@@ -592,6 +592,19 @@ def batched_graph(g: int, device="cpu", scale: int = 1, seed_offset: int = 0) ->
                         name=f"batched{g}")
 
 
+def batched_storage(device="cpu", dtype: torch.dtype = torch.float16, scale: int = 1,
+                    seed_offset: int = 0) -> Workload:
+    """The eight batched graphs merged into one set of pools, each graph cast
+    to the storage dtype as soon as it is made (the FP32 pools of all eight
+    full-size graphs together are about 65 GB)."""
+    gs = []
+    for g in range(8):
+        gs.append(batched_graph(g, device, scale, seed_offset).to_storage(dtype))
+        if torch.cuda.is_available() and torch.device(device).type == "cuda":
+            torch.cuda.empty_cache()
+    return merge(gs, name="batched")
+
+
 def batched(device="cpu", scale: int = 1) -> List[Workload]:
     """Eight independent keyframe graphs (seeds 100 + g) with 16..128
     keyframes and 40..600 directed edges; graphs 1, 3, 6 at 256 x 192 and the

@@ -154,3 +154,38 @@ def test_global_graph_solve_structure(M):
     print(f"FP64-only solve: tau rel err {err64:.2e}")
     assert int(st64[0]) in (0, 1) and err64 <= 1e-8
 
+
+
+def test_largest_batched_graph_solve_structure(M):
+    """The largest graph of the batched workload (128 keyframes, 600 directed
+    edges; small images, same graph structure): its factor is too large for
+    one SM's shared memory, so the plan takes the FP64 kernels with the
+    factor in the workspace (one solve launch); the solve on oracle blocks
+    against the oracle's dense solve."""
+    w = synth.batched_graph(7, scale=16)
+    P = M.default_params()
+    par = M.params_dict(P)
+    plan = M.Plan(w.kf_hw.numpy(), w.edges.numpy())
+    assert plan.solve_launches == 1
+    idx = w.gt_match.numpy()
+    q = w.Q_qry.double().numpy()
+    T0 = w.T_init.numpy()
+    Hr, gr = [], []
+    for e in range(w.E):
+        i, j = int(w.edges[e, 0]), int(w.edges[e, 1])
+        sl = w.edge_slice(e)
+        Hb, gb, _, _ = oracle.linearize_edge(T0[i], T0[j], w.X_canon[w.kf_slice(i)], w.X_canon[w.kf_slice(j)], idx[sl],
+                                             q[sl], **par)
+        Hr.append(Hb)
+        gr.append(gb)
+    H32, g32 = torch.from_numpy(np.array(Hr)).float(), torch.from_numpy(np.array(gr)).float()
+    T = w.T_init.clone().cuda()
+    tau, st = M.gn_solve(plan, P, H32.cuda(), g32.cuda(), T, tau=torch.zeros(w.N, 7, dtype=torch.float64,
+                                                                              device="cuda"))
+    torch.cuda.synchronize()
+    s, T_r, tau_r = oracle.gn_solve(w.N, w.edges.numpy(), H32.double(), g32.double(), T0)
+    assert s == 0 and int(st[0]) in (0, 1)
+    err = np.abs(f64(tau) - tau_r).max() / max(1.0, np.abs(tau_r).max())
+    print(f"128-keyframe solve (FP64 kernels, factor in the workspace): tau rel err {err:.2e}")
+    assert err <= 1e-8
+    assert_poses_close(T, T_r, 1e-8)

@@ -68,6 +68,14 @@ def match_agreement(idx_gpu, idx_ref, diag_ref=None, params=None):
     return agree, int(dis.sum()), int(union.sum()), explained
 
 
+def match_agreement_unexplained(idx_gpu, idx_ref, diag_ref, params):
+    """(agreement over all pixels valid on either side, disagreements,
+    disagreements that are not a near tie of an FP32 decision or an LM
+    iterate still moving, union size)."""
+    agree, ndis, nunion, expl = match_agreement(idx_gpu, idx_ref, diag_ref, params)
+    return agree, ndis, int(round(ndis * (1.0 - expl))), nunion
+
+
 def solve_flags(plan, ws):
     """Per-graph flags the mixed-precision solve leaves at the end of the
     solve workspace: 1 = solved by FP32 factorisation + FP64 refinement,

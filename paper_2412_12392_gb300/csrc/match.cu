@@ -174,52 +174,26 @@ __global__ void __launch_bounds__(kMatchThreads) match_kernel(
   typename Desc<T, D>::Q dq[Desc<T, D>::NQ];
   Desc<T, D>::load(Dq, pv.P, o + n, dq);
   const int r = mc.radius;
-  // A candidate of a finer level that sits on a position the previous level
-  // scored cannot be this level's first maximum: the previous best (this
-  // level's centre) scores at least as much and precedes every later one in
-  // scan order, and every earlier one scored strictly less.  Such
-  // candidates are skipped and the centre's score is the previous best (the
-  // same dot product), so the result equals the full scan.
-  float prev_best = -INFINITY;
-  int pa = 0, pb = 0, pdil = 0;  // previous level: offset of its best (its grid units), its spacing
   for (int lev = 0; lev < mc.n_levels; ++lev) {
     const int dil = mc.dil[lev];
-    const int k = (lev > 0 && dil > 0 && pdil % dil == 0) ? pdil / dil : 0;  // previous spacing in this level's
-    uint32_t colmask = 0u;                                                 // columns on the previous grid
-    if (k > 0)
-      for (int dx = -r; dx <= r; ++dx)
-        if (dx % k == 0 && abs(pa + dx / k) <= r) colmask |= 1u << (dx + r);
     float best = -INFINITY;
-    int bu = cu, bv = cv, ba = 0, bb = 0;
+    int bu = cu, bv = cv;
     for (int dy = -r; dy <= r; ++dy) {
       const int vv = cv + dy * dil;
       if (vv < 0 || vv >= H) continue;
-      const uint32_t rowmask = (k > 0 && dy % k == 0 && abs(pb + dy / k) <= r) ? colmask : 0u;
       for (int dx = -r; dx <= r; ++dx) {
         const int uu = cu + dx * dil;
         if (uu < 0 || uu >= W) continue;
-        float s;
-        if ((rowmask >> (dx + r)) & 1u) {
-          if (dx != 0 || dy != 0) continue;
-          s = prev_best;
-        } else {
-          s = Desc<T, D>::dot(Dr, pv.P, o + (int64_t)vv * W + uu, dq);
-        }
+        const float s = Desc<T, D>::dot(Dr, pv.P, o + (int64_t)vv * W + uu, dq);
         if (s > best) {
           best = s;
           bu = uu;
           bv = vv;
-          ba = dx;
-          bb = dy;
         }
       }
     }
     cu = bu;
     cv = bv;
-    prev_best = best;
-    pa = ba;
-    pb = bb;
-    pdil = dil;
   }
   const int m = cv * W + cu;
   const float3 y = ld3(Xr_e, m);

@@ -212,16 +212,23 @@ class Arm:
             self.tuning = tune(w.kf_hw.numpy(), w.edges.numpy(), w.graph_of_kf.numpy(), self.P, wd.X_ref, wd.X_qry,
                                self.Dr, self.Dq, wd.Q_ref, wd.Q_qry, wd.X_canon, w.T_init.to(wd.X_canon.device))
             opts = self.tuning["opts"]
-        self.plan = M.Plan(w.kf_hw.numpy(), w.edges.numpy(), w.graph_of_kf.numpy(), opts=opts)
         dev = self.wd.X_canon.device
+        self.T0 = w.T_init.to(dev)
+        self.iters = w.n_gn_iters
+        self.set_opts(opts, dtype)
+
+    def set_opts(self, opts, dtype=None):
+        """(Re)build the plan with these launch shapes, on the same inputs."""
+        M, w = self.M, self.w
+        dtype = dtype or self.q.dtype
+        dev = self.wd.X_canon.device
+        self.plan = M.Plan(w.kf_hw.numpy(), w.edges.numpy(), w.graph_of_kf.numpy(), opts=opts)
         self.idx = torch.empty(self.plan.edge_pixels, dtype=torch.int32, device=dev)
         self.q = torch.empty(self.plan.edge_pixels, dtype=dtype, device=dev)
         # the batched form gathers the used matches once per step and streams
         # them in every iteration; the plain form gathers in every iteration
-        self.gn = M.GaussNewton(self.plan, self.P, self.wd.X_canon, self.idx, self.q, per_edge=per_edge,
-                                packed=not per_edge)
-        self.T0 = w.T_init.to(dev)
-        self.iters = w.n_gn_iters
+        self.gn = M.GaussNewton(self.plan, self.P, self.wd.X_canon, self.idx, self.q, per_edge=self.per_edge,
+                                packed=not self.per_edge)
 
     def match(self):
         wd = self.wd
@@ -319,6 +326,40 @@ class Arm:
         return 1 + 1 + self.iters * (3 + sl)
 
 
+def pick_pipelined_shapes(arm, world, steps: int = 5, warmup: int = 3):
+    """The autotuner ranks the linearisation shapes one stage at a time.  With
+    two batches in flight the linearisation also shares the SMs with the next
+    batch's matching, and a streamed form's large shared-memory ring keeps
+    matching blocks off an SM while it runs.  Time the autotuner's choice and
+    its best register-pipeline shape as pipelined steps and keep the faster
+    (the same work either way; only the launch shapes differ)."""
+    rep = arm.tuning
+    if rep is None or rep["opts"].get("lin_form") == 1:
+        return None
+    best, key_best = float("inf"), None
+    for key, ms in rep["lin_ms"].items():
+        tile, bps, form = key.split("/")
+        if form != "regs":
+            continue
+        score = arm.iters * ms + rep["pack_ms"][int(tile) if int(tile) in rep["pack_ms"] else tile]
+        if score < best:
+            best, key_best = score, (int(tile), int(bps))
+    if key_best is None:
+        return None
+    chosen = dict(rep["opts"])
+    alt = dict(chosen, lin_tile=key_best[0], lin_blocks_per_sm=key_best[1], lin_form=1)
+    times = {}
+    for name, o in (("autotuned", chosen), ("register_pipeline", alt)):
+        arm.set_opts(o)
+        times[name], _, _ = time_steps(arm, steps, warmup, world, None, pipelined=True)
+        times[name] = max_over_ranks(times[name], world)
+    keep = min(times, key=times.get)
+    arm.set_opts(chosen if keep == "autotuned" else alt)
+    arm.step()
+    torch.cuda.synchronize()
+    return {"pipelined_ms": times, "kept": keep, "opts": dict(arm.plan.opts)}
+
+
 def time_steps(arm, steps, warmup, world, sampler=None, with_events=True, graph=False, pipelined=False):
     """Mean time of a step over `steps` steps after `warmup` untimed steps;
     with events, also the mean time of each stage (eager launches); with
@@ -378,6 +419,9 @@ def run_gpu(args, world, rank, local):
     n_query = int(arm.plan.edge_pixels)
     peaks, peak_src = measured_peaks()
     sampler = ClockSampler(local) if rank == 0 else None
+    pipe_pick = None
+    if args.form == "batched" and arm.tuning is not None:
+        pipe_pick = pick_pipelined_shapes(arm, world)
     # one step at a time, with CUDA events between the stages
     serial_ms, stats, _ = time_steps(arm, args.steps, args.warmup, world, None)
     serial_ms = max_over_ranks(serial_ms, world)
@@ -442,7 +486,7 @@ def run_gpu(args, world, rank, local):
         "matched_pixels": n_matched, "query_pixels": n_query,
         "roofline": dominant, "roofline_kernels": [rl_match, rl_lin],
         "pipelining": {"serial_ms_per_step": serial_ms, "serial_value": tot_matched * arm.iters / (serial_ms * 1e-3),
-                       "same_result_as_serial": same_result,
+                       "same_result_as_serial": same_result, "shape_check": pipe_pick,
                        "note": "headline steps run with two batches in flight: batch k+1's matching on a "
                                "low-priority stream beside batch k's Gauss-Newton loop; serial = one step "
                                "at a time (the stage times are from the serial run)"},

@@ -23,6 +23,7 @@ struct mslam_plan {
   std::vector<int32_t> order;
   int64_t n_blocks_total = 0, n_trips_total = 0, solve_ws_doubles = 0, max_graph_doubles = 0;
   int64_t max_mixed_bytes = 0;  // shared memory of the mixed-precision solve for the largest graph
+  int64_t max_mixed_bytes_nofactor = 0;  // the same with the FP32 factor left in the workspace
   int64_t max_mixed_elems = 0;  // elements its assembly kernel covers for the largest graph
   int32_t max_m = 0;            // non-fixed poses of the largest graph
   int32_t max_levels = 0;
@@ -93,6 +94,7 @@ void plan_edge_mblocks(const mslam_plan* plan, int e, int* b0, int* b1) {
 
 int64_t plan_max_graph_doubles(const mslam_plan* plan) { return plan->max_graph_doubles; }
 int64_t plan_max_mixed_bytes(const mslam_plan* plan) { return plan->max_mixed_bytes; }
+int64_t plan_max_mixed_bytes_nofactor(const mslam_plan* plan) { return plan->max_mixed_bytes_nofactor; }
 int64_t plan_max_mixed_elems(const mslam_plan* plan) { return plan->max_mixed_elems; }
 int plan_max_unknown_blocks(const mslam_plan* plan) { return plan->max_m; }
 int64_t plan_solve_ws_doubles(const mslam_plan* plan) { return plan->solve_ws_doubles; }
@@ -381,6 +383,8 @@ static void build_graph(mslam_plan* P, int g, const std::vector<int>& kfs) {
   const int64_t table_ints = (int64_t)(dg.off_trip - dg.off_pose) + (int64_t)(dg.int_end - dg.off_lev);
   P->max_mixed_bytes = std::max(P->max_mixed_bytes,
                                 (int64_t)(32 * 7 * (int64_t)m + 224 * (int64_t)nb_total + 4 * table_ints + 16));
+  P->max_mixed_bytes_nofactor = std::max(P->max_mixed_bytes_nofactor,
+                                         (int64_t)(32 * 7 * (int64_t)m + 4 * table_ints + 16));
   P->max_mixed_elems = std::max(P->max_mixed_elems, (int64_t)nb_total * 56);
   P->max_m = std::max(P->max_m, (int32_t)m);
   P->n_blocks_total += nb_total;

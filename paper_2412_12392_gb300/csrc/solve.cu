@@ -723,6 +723,10 @@ __device__ __forceinline__ float dot8(const float* a, const float* b) {
          ((a1.x * b1.x + a1.y * b1.y) + (a1.z * b1.z + a1.w * b1.w));
 }
 
+// kGlobalL: the FP32 factor stays in the workspace (L2-resident) where the
+// assembly kernel wrote it and is factored in place, for graphs whose factor
+// does not fit one SM's shared memory; everything else stays in shared memory.
+template <bool kGlobalL>
 __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, SolveConst sc,
                                                                   double* __restrict__ T_wc,
                                                                   double* __restrict__ tau_out,
@@ -746,8 +750,9 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
   // shared memory: the padded FP32 factor, FP64 vectors, FP32 vectors, then
   // the graph's tables (all but the update triples), so that every dependent
   // lookup of the level schedule is a shared-memory access
-  float* Lf = reinterpret_cast<float*>(smem);  // scaled factor, FP32, 7 x 8 per block (16-byte aligned rows)
-  double* scl = reinterpret_cast<double*>(Lf + (size_t)nb * kLfBlock);  // S = D^-1/2
+  // scaled factor, FP32, 7 x 8 per block (16-byte aligned rows)
+  float* Lf = kGlobalL ? reinterpret_cast<float*>(ws + G.ws_mixed) : reinterpret_cast<float*>(smem);
+  double* scl = kGlobalL ? smem : reinterpret_cast<double*>(Lf + (size_t)nb * kLfBlock);  // S = D^-1/2
   double* xv = scl + n7;                        // solution
   double* bv = xv + n7;                         // right-hand side -g
   float* yv = reinterpret_cast<float*>(bv + n7);  // work vector
@@ -757,9 +762,11 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
   for (int t = tid; t < seg1; t += nth) sI[t] = __ldg(pv.ints + G.off_pose + t);
   for (int t = tid; t < seg2; t += nth) sI[seg1 + t] = __ldg(pv.ints + G.off_lev + t);
   {
-    const float4* src = reinterpret_cast<const float4*>(ws + G.ws_mixed);
-    float4* dst = reinterpret_cast<float4*>(Lf);
-    for (int t = tid; t < nb * (kLfBlock / 4); t += nth) dst[t] = src[t];
+    if (!kGlobalL) {
+      const float4* src = reinterpret_cast<const float4*>(ws + G.ws_mixed);
+      float4* dst = reinterpret_cast<float4*>(Lf);
+      for (int t = tid; t < nb * (kLfBlock / 4); t += nth) dst[t] = src[t];
+    }
     const double* sg = ws + G.ws_mixed + (size_t)nb * 28;
     for (int t = tid; t < n7; t += nth) {
       scl[t] = sg[t];
@@ -1062,7 +1069,8 @@ static int smem_limit_bytes() {
     limit = std::max(0, optin - 2048);  // headroom for the static shared variables
     cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
     cudaFuncSetAttribute(solve_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
-    cudaFuncSetAttribute(solve_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
+    cudaFuncSetAttribute(solve_mixed_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
+    cudaFuncSetAttribute(solve_mixed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
   }
   return limit;
 }
@@ -1099,11 +1107,19 @@ static bool cluster_fits(int smem_bytes) {
 
 // Shared memory of the mixed-precision solve if the plan's largest graph fits
 // (0: use the FP64 kernels alone).
-static int mixed_smem_bytes(const mslam_plan* plan) {
+static int mixed_smem_bytes(const mslam_plan* plan, bool* global_factor = nullptr) {
+  if (global_factor) *global_factor = false;
   if (plan_solve_form(plan) != 0) return 0;
-  const int64_t need = plan_max_mixed_bytes(plan);
   const int limit = smem_limit_bytes();
-  return (need > 0 && need <= limit) ? (int)need : 0;
+  const int64_t need = plan_max_mixed_bytes(plan);
+  if (need > 0 && need <= limit) return (int)need;
+  // the largest factor does not fit: every graph factors in the workspace
+  const int64_t need2 = plan_max_mixed_bytes_nofactor(plan);
+  if (need2 > 0 && need2 <= limit) {
+    if (global_factor) *global_factor = true;
+    return (int)need2;
+  }
+  return 0;
 }
 
 static mslam_status launch_solve(const PlanView& pv, SolveConst sc, const float* H, const float* g, double* T,
@@ -1158,7 +1174,8 @@ extern "C" mslam_status mslam_gn_solve(const mslam_params* p, const mslam_plan* 
   sc.skip = nullptr;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   double* ws = static_cast<double*>(workspace);
-  const int mixed = mixed_smem_bytes(plan);
+  bool global_factor = false;
+  const int mixed = mixed_smem_bytes(plan, &global_factor);
   if (mixed > 0 && pv.E > 0) {
     // FP32 factorisation + FP64 refinement first; graphs it declines (or
     // that need no solve) go through the FP64 kernel, which skips the rest
@@ -1169,7 +1186,10 @@ extern "C" mslam_status mslam_gn_solve(const mslam_params* p, const mslam_plan* 
     solve_scale_kernel<<<dim3(std::max(1, (n7 + 127) / 128), pv.G), 128, 0, s>>>(pv, H_blocks, g_blocks,
                                                                                  dev_status, ws);
     solve_assemble_kernel<<<dim3(std::max(1, (elems + 63) / 64), pv.G), 64, 0, s>>>(pv, H_blocks, dev_status, ws);
-    solve_mixed_kernel<<<pv.G, kMixThreads, mixed, s>>>(pv, sc, T_wc, tau, dev_status, ws, handled);
+    if (global_factor)
+      solve_mixed_kernel<true><<<pv.G, kMixThreads, mixed, s>>>(pv, sc, T_wc, tau, dev_status, ws, handled);
+    else
+      solve_mixed_kernel<false><<<pv.G, kMixThreads, mixed, s>>>(pv, sc, T_wc, tau, dev_status, ws, handled);
     mslam_status st = cuda_check(cudaGetLastError(), "gn_solve mixed launch");
     if (st != MSLAM_OK) return st;
     sc.skip = handled;

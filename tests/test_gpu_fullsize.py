@@ -158,15 +158,15 @@ def test_global_graph_solve_structure(M):
 
 def test_largest_batched_graph_solve_structure(M):
     """The largest graph of the batched workload (128 keyframes, 600 directed
-    edges; small images, same graph structure): its factor is too large for
-    one SM's shared memory, so the plan takes the FP64 kernels with the
-    factor in the workspace (one solve launch); the solve on oracle blocks
-    against the oracle's dense solve."""
+    edges; small images, same graph structure): its FP32 factor (1,123
+    blocks) is too large for one SM's shared memory, so the mixed-precision
+    solve factors it in place in the workspace; the solve on oracle blocks
+    against the oracle's dense solve, and the FP64-only form beside it."""
     w = synth.batched_graph(7, scale=16)
     P = M.default_params()
     par = M.params_dict(P)
     plan = M.Plan(w.kf_hw.numpy(), w.edges.numpy())
-    assert plan.solve_launches == 1
+    assert plan.solve_launches == 4
     idx = w.gt_match.numpy()
     q = w.Q_qry.double().numpy()
     T0 = w.T_init.numpy()
@@ -179,13 +179,20 @@ def test_largest_batched_graph_solve_structure(M):
         Hr.append(Hb)
         gr.append(gb)
     H32, g32 = torch.from_numpy(np.array(Hr)).float(), torch.from_numpy(np.array(gr)).float()
-    T = w.T_init.clone().cuda()
-    tau, st = M.gn_solve(plan, P, H32.cuda(), g32.cuda(), T, tau=torch.zeros(w.N, 7, dtype=torch.float64,
-                                                                              device="cuda"))
-    torch.cuda.synchronize()
     s, T_r, tau_r = oracle.gn_solve(w.N, w.edges.numpy(), H32.double(), g32.double(), T0)
-    assert s == 0 and int(st[0]) in (0, 1)
-    err = np.abs(f64(tau) - tau_r).max() / max(1.0, np.abs(tau_r).max())
-    print(f"128-keyframe solve (FP64 kernels, factor in the workspace): tau rel err {err:.2e}")
-    assert err <= 1e-8
-    assert_poses_close(T, T_r, 1e-8)
+    assert s == 0
+    for form in (0, 1):
+        pl = plan if form == 0 else M.Plan(w.kf_hw.numpy(), w.edges.numpy(), opts={"solve_form": 1})
+        T = w.T_init.clone().cuda()
+        ws = pl.workspace(M._lib.MSLAM_OP_SOLVE)
+        tau, st = M.gn_solve(pl, P, H32.cuda(), g32.cuda(), T, tau=torch.zeros(w.N, 7, dtype=torch.float64,
+                                                                                device="cuda"), workspace=ws)
+        torch.cuda.synchronize()
+        assert int(st[0]) in (0, 1)
+        err = np.abs(f64(tau) - tau_r).max() / max(1.0, np.abs(tau_r).max())
+        flags = solve_flags(pl, ws).tolist() if form == 0 else None
+        print(f"128-keyframe solve, form {form}: tau rel err {err:.2e}, mixed-precision flags {flags}")
+        assert err <= 1e-8
+        assert_poses_close(T, T_r, 1e-8)
+        if form == 0:
+            assert flags == [1]  # solved by the FP32 factorisation (in the workspace) with FP64 refinement

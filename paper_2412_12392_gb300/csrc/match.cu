@@ -98,7 +98,11 @@ template <int D> struct Desc<__half, D> {
   }
 };
 
-template <typename T, int D>
+// kR > 0: the window radius as a compile-time constant (the default 3), so
+// that each window row is unrolled with branch-free bounds (an out-of-image
+// candidate reads a clamped pixel and scores -inf, which never wins, exactly
+// as if it were skipped); kR = 0 takes the radius from the parameters.
+template <typename T, int D, int kR>
 __global__ void __launch_bounds__(kMatchThreads) match_kernel(
     PlanView pv, MatchConst mc, const T* __restrict__ Xr, const T* __restrict__ Xq, const T* __restrict__ Dr,
     const T* __restrict__ Dq, const T* __restrict__ Qr, const T* __restrict__ Qq, const int32_t* __restrict__ init,
@@ -178,6 +182,28 @@ __global__ void __launch_bounds__(kMatchThreads) match_kernel(
     const int dil = mc.dil[lev];
     float best = -INFINITY;
     int bu = cu, bv = cv;
+    if (kR > 0) {
+#pragma unroll 1
+      for (int dy = -kR; dy <= kR; ++dy) {
+        const int vv = cv + dy * dil;
+        const bool vin = (unsigned)vv < (unsigned)H;
+        const int64_t row = o + (int64_t)min(max(vv, 0), H - 1) * W;
+#pragma unroll
+        for (int dx = -kR; dx <= kR; ++dx) {
+          const int uu = cu + dx * dil;
+          const float s0 = Desc<T, D>::dot(Dr, pv.P, row + min(max(uu, 0), W - 1), dq);
+          const float s = (vin && (unsigned)uu < (unsigned)W) ? s0 : -INFINITY;
+          if (s > best) {
+            best = s;
+            bu = uu;
+            bv = vv;
+          }
+        }
+      }
+      cu = bu;
+      cv = bv;
+      continue;
+    }
     for (int dy = -r; dy <= r; ++dy) {
       const int vv = cv + dy * dil;
       if (vv < 0 || vv >= H) continue;
@@ -208,10 +234,11 @@ template <typename T, int D>
 static void launch_match(const PlanView& pv, const MatchConst& mc, const void* Xr, const void* Xq, const void* Dr,
                          const void* Dq, const void* Qr, const void* Qq, const int32_t* init, int32_t* out_idx,
                          void* out_q, int e0, int e1, int b0, int nblocks, cudaStream_t s) {
-  match_kernel<T, D><<<nblocks, kMatchThreads, 0, s>>>(
-      pv, mc, static_cast<const T*>(Xr), static_cast<const T*>(Xq), static_cast<const T*>(Dr),
-      static_cast<const T*>(Dq), static_cast<const T*>(Qr), static_cast<const T*>(Qq), init, out_idx,
-      static_cast<T*>(out_q), e0, e1, b0);
+  auto k = mc.radius == 3 ? match_kernel<T, D, 3> : match_kernel<T, D, 0>;
+  k<<<nblocks, kMatchThreads, 0, s>>>(pv, mc, static_cast<const T*>(Xr), static_cast<const T*>(Xq),
+                                     static_cast<const T*>(Dr), static_cast<const T*>(Dq),
+                                     static_cast<const T*>(Qr), static_cast<const T*>(Qq), init, out_idx,
+                                     static_cast<T*>(out_q), e0, e1, b0);
 }
 
 }  // namespace mslam

@@ -185,6 +185,18 @@ void mslam_plan_stats(const mslam_plan* plan, int32_t* order, int64_t* counts);
 size_t mslam_workspace_bytes(const mslam_plan* plan, int32_t op);
 
 /* ------------------------------------------------------------------------ */
+/* (a1) The ray image, Sec. 3.1 (generic central camera).                     */
+/* ------------------------------------------------------------------------ */
+/* R[p] = psi(X[p]) = X[p] / |X[p]| for n_pix points X [n_pix, 3] of dtype dt
+ * (FP32 or FP16), written to R [n_pix, 3] of the same dtype (device memory,
+ * R may equal X); a zero or non-finite point gives the zero ray.  The norm
+ * is formed in FP32 with the hardware reciprocal square root, exactly as
+ * mslam_match evaluates the rays at its bilinear taps (it does not need this
+ * image: it normalises the four taps of each iteration on the fly).
+ * Errors: MSLAM_ERR_ARG (NULL pointer, negative size), MSLAM_ERR_CUDA. */
+mslam_status mslam_ray_image(mslam_dtype dt, int64_t n_pix, const void* X, void* R, void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* (a1-a3) Projective matching with feature refinement, Sec. 3.2, Eq. 2.     */
 /* ------------------------------------------------------------------------ */
 /* For every query pixel n of every edge e = (i, j) in [edge_begin, edge_end)

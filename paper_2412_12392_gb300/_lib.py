@@ -87,6 +87,7 @@ SIGNATURES = {
     "mslam_gn_linearize_packed": ([vp, vp, C.c_int, vp, vp, sz, vp, vp, vp, vp, vp, sz, u32, vp], C.c_int),
     "mslam_gn_solve": ([vp, vp, vp, vp, vp, vp, vp, vp, sz, vp], C.c_int),
     "mslam_match_stats": ([vp, vp, vp, vp, vp, sz, vp], C.c_int),
+    "mslam_ray_image": ([C.c_int, C.c_int64, vp, vp, vp], C.c_int),
     "mslam_calib_backproject": ([C.c_int, i32, i32, i32, C.c_float, C.c_float, C.c_float, C.c_float, vp, vp],
                                 C.c_int),
     "mslam_gn_solve_launches": ([vp], i32),

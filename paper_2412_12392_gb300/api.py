@@ -182,6 +182,19 @@ def match_stats(plan: Plan, idx, workspace=None):
     return nv, nu
 
 
+def ray_image(X: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """mslam_ray_image (a1, Sec. 3.1): psi(X) = X / |X| for X [..., 3] (FP32 or
+    FP16, CUDA), the zero ray for a zero or non-finite point."""
+    if X.shape[-1] != 3 or not X.is_contiguous() or not X.is_cuda:
+        raise ValueError("X must be a contiguous CUDA tensor of shape [..., 3]")
+    R = torch.empty_like(X) if out is None else out
+    if R.shape != X.shape or R.dtype != X.dtype or not R.is_contiguous():
+        raise ValueError("out must match X in shape, dtype and layout")
+    check(lib().mslam_ray_image(DTYPES[X.dtype], X.numel() // 3, X.data_ptr(), R.data_ptr(), _stream(X.device)),
+          "mslam_ray_image")
+    return R
+
+
 def calib_backproject(X: torch.Tensor, fx: float, fy: float, cx: float, cy: float) -> torch.Tensor:
     """mslam_calib_backproject (Sec. 3.6), in place on X [n, H, W, 3] (FP32 or
     FP16, CUDA); returns X."""

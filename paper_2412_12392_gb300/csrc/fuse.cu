@@ -72,9 +72,51 @@ __global__ void __launch_bounds__(256) calib_backproject_kernel(int64_t n, int32
   }
 }
 
+// (a1) psi(X) = X / |X| per point, the zero ray for a zero or non-finite
+// point (the same FP32 arithmetic as the match kernel's taps).
+template <typename T>
+__global__ void __launch_bounds__(256) ray_image_kernel(int64_t n, const T* X, T* R) {  // R may alias X
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float x = ldf(X + 3 * i), y = ldf(X + 3 * i + 1), z = ldf(X + 3 * i + 2);
+    const float n2 = fmaf(x, x, fmaf(y, y, z * z));
+    const bool ok = n2 > 0.0f && n2 < INFINITY;
+    const float inv = ok ? rsqrtf(n2) : 0.0f;
+    stf(R + 3 * i, ok ? x * inv : 0.0f);
+    stf(R + 3 * i + 1, ok ? y * inv : 0.0f);
+    stf(R + 3 * i + 2, ok ? z * inv : 0.0f);
+  }
+}
+
 }  // namespace mslam
 
 using namespace mslam;
+
+extern "C" mslam_status mslam_ray_image(mslam_dtype dt, int64_t n_pix, const void* X, void* R, void* stream) {
+  if (dt != MSLAM_F32 && dt != MSLAM_F16) {
+    set_error("unsupported dtype %d", (int)dt);
+    return MSLAM_ERR_ARG;
+  }
+  if (n_pix < 0) {
+    set_error("ray_image: negative size %lld", (long long)n_pix);
+    return MSLAM_ERR_ARG;
+  }
+  if (n_pix == 0) return MSLAM_OK;
+  if (!X || !R) {
+    set_error("ray_image: NULL device pointer");
+    return MSLAM_ERR_ARG;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t blocks = std::min<int64_t>((n_pix + 255) / 256, (int64_t)std::max(1, sms) * 8);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (dt == MSLAM_F32)
+    ray_image_kernel<float><<<(int)blocks, 256, 0, s>>>(n_pix, static_cast<const float*>(X), static_cast<float*>(R));
+  else
+    ray_image_kernel<__half><<<(int)blocks, 256, 0, s>>>(n_pix, static_cast<const __half*>(X),
+                                                         static_cast<__half*>(R));
+  return cuda_check(cudaGetLastError(), "ray_image launch");
+}
 
 extern "C" mslam_status mslam_calib_backproject(mslam_dtype dt, int32_t n_images, int32_t H, int32_t W, float fx,
                                                 float fy, float cx, float cy, void* X, void* stream) {

@@ -23,6 +23,33 @@ def M():
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
+def test_ray_image_matches_oracle(M, dtype):
+    """mslam_ray_image (a1, Sec. 3.1) against the oracle's ray image on the
+    stored values: unit rays within the rounding of the output dtype, and the
+    zero ray for zero and non-finite points (a ragged count: not a multiple
+    of the block size)."""
+    g = torch.Generator().manual_seed(7)
+    n = 100003
+    X = torch.randn(n, 3, generator=g) * torch.exp(torch.randn(n, 1, generator=g))
+    X[::97] = 0.0
+    X[5::101, 1] = float("nan")
+    X[7::103, 2] = float("inf")
+    Xs = X.to(dtype)
+    R = M.ray_image(Xs.cuda()).cpu()
+    Rr = oracle.ray_image(Xs)
+    tol = 4e-7 if dtype == torch.float32 else 5e-4
+    err = np.abs(f64(R) - Rr).max()
+    print(f"ray image {dtype}: max abs err {err:.2e}")
+    assert err <= tol
+    bad = ~torch.isfinite(Xs).all(dim=1) | (Xs.float().abs().sum(dim=1) == 0)
+    assert bool((R[bad] == 0).all())
+    # in place (R may alias X)
+    Xd = Xs.cuda()
+    M.ray_image(Xd, out=Xd)
+    assert torch.equal(Xd.cpu(), R)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
 def test_fusion_matches_oracle(M, dtype):
     w = synth.tracking(H=96, W=128)
     rng = np.random.default_rng(1)

@@ -734,8 +734,28 @@ def tracking_frame(M, dev, peaks) -> dict:
     # the frame's launches (a few microseconds of work each) replayed as one CUDA graph
     arm.capture()
     gms = _event_ms(arm.step_graph, 20)
+    # the fused tracking loop: match, pack, then one launch per GN iteration
+    def fused():
+        arm.match()
+        arm.gn.run_tracking(arm.T0, arm.iters)
+    fms = _event_ms(fused, 20)
+    T_fused = arm.gn.T.clone()
+    dev_ = arm.wd.X_canon.device
+    s_ = torch.cuda.Stream(dev_)
+    s_.wait_stream(torch.cuda.current_stream(dev_))
+    with torch.cuda.stream(s_):
+        fused()
+    torch.cuda.current_stream(dev_).wait_stream(s_)
+    torch.cuda.synchronize()
+    fg = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(fg):
+        fused()
+    fgms = _event_ms(fg.replay, 20)
+    fused_same = bool(torch.equal(arm.gn.T, T_fused))
     return {"workload": "tracking: 1 frame against 1 keyframe, 512x384, radial camera, d=24, 20 GN iters",
-            "ms_per_frame": ms, "ms_per_frame_cuda_graph": gms, "match_ms": m0.elapsed_time(m1),
+            "ms_per_frame": ms, "ms_per_frame_cuda_graph": gms,
+            "ms_per_frame_fused": fms, "ms_per_frame_fused_cuda_graph": fgms, "fused_replay_same_result": fused_same,
+            "match_ms": m0.elapsed_time(m1),
             "pack_ms": m1.elapsed_time(p1), "gn_iter_ms": float(np.mean([a.elapsed_time(c) for a, b, c in lins])),
             "matched_pixels": n_matched, "launches_per_frame": arm.launches_per_step(),
             "launch_shapes": arm.plan.opts}

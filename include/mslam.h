@@ -68,6 +68,7 @@ typedef enum { MSLAM_F32 = 0, MSLAM_F16 = 1 } mslam_dtype;
 #define MSLAM_OP_PACK_F32 4 /* packed-match buffer of mslam_gn_pack, FP32 storage */
 #define MSLAM_OP_PACK_F16 5 /* packed-match buffer of mslam_gn_pack, FP16 storage */
 #define MSLAM_OP_STATS 6    /* reference-pixel bitmap of mslam_match_stats */
+#define MSLAM_OP_TRACK 7    /* tile partials and per-edge counters of mslam_gn_track */
 
 /* Constants of the method.  The paper names these quantities without values
  * where marked "reading"; defaults are set by mslam_default_params. */
@@ -358,6 +359,30 @@ mslam_status mslam_gn_backward(const mslam_params* p, const mslam_plan* plan, ms
                                const float* g_blocks, const double* dL_dtau, double dL_dcost, float* dL_dX,
                                float* dL_dq, int32_t* dev_status, void* workspace, size_t ws_bytes,
                                void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Tracking, Sec. 3.3: the frame's Gauss-Newton loop in one launch per       */
+/* iteration.                                                                 */
+/* ------------------------------------------------------------------------ */
+/* For plans in which every graph is one keyframe (its gauge) and one frame
+ * joined by one edge (a tracking problem; several are solved side by side):
+ * n_iters iterations of a4-a8 on the ray family, each one launch.  Every
+ * block linearises one tile of packed records (mslam_gn_pack) against the
+ * relative pose it forms from T_wc, stores the tile's sums, and the block
+ * that completes an edge's last tile adds the edge's tile sums in tile order
+ * in FP64, maps them to the frame's 7 x 7 system with the adjoint (the
+ * gauge removed), solves it by FP64 Cholesky and retracts the frame's pose
+ * in T_wc (Exp(tau) o T).  dev_status [G] as in mslam_gn_solve: a graph
+ * with status > 0 is skipped; 1 is written once max|tau| < conv_tol,
+ * MSLAM_ERR_NOT_PD for a pivot that is not positive.  The result equals
+ * the linearise + solve loop up to the rounding of the 14 x 14 blocks,
+ * which stay FP64 here.  workspace >= mslam_workspace_bytes(plan,
+ * MSLAM_OP_TRACK), 256-byte aligned.  Errors: MSLAM_ERR_ARG (a plan that is
+ * not of this form, a residual family other than the ray family, n_iters
+ * < 0, NULL or misaligned pointers), MSLAM_ERR_CUDA. */
+mslam_status mslam_gn_track(const mslam_params* p, const mslam_plan* plan, mslam_dtype dt, double* T_wc,
+                            const void* packed, size_t packed_bytes, int32_t n_iters, int32_t* dev_status,
+                            void* workspace, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Pointmap fusion, Sec. 3.3 (next stage after tracking).                    */

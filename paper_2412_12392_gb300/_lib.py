@@ -26,6 +26,7 @@ MSLAM_OP_BACKWARD = 3
 MSLAM_OP_PACK_F32 = 4
 MSLAM_OP_PACK_F16 = 5
 MSLAM_OP_STATS = 6
+MSLAM_OP_TRACK = 7
 MSLAM_RES_RAY, MSLAM_RES_POINT, MSLAM_RES_PIXEL = 0, 1, 2
 
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_NOT_PD", 4: "ERR_TIMEOUT", 5: "ERR_NONFINITE",
@@ -85,6 +86,7 @@ SIGNATURES = {
     "mslam_gn_linearize_noalloc": ([vp, vp, C.c_int, vp, vp, vp, vp, vp, vp, vp, vp, u32, vp], C.c_int),
     "mslam_gn_pack": ([vp, vp, C.c_int, vp, vp, vp, vp, sz, vp], C.c_int),
     "mslam_gn_linearize_packed": ([vp, vp, C.c_int, vp, vp, sz, vp, vp, vp, vp, vp, sz, u32, vp], C.c_int),
+    "mslam_gn_track": ([vp, vp, C.c_int, vp, vp, sz, i32, vp, vp, sz, vp], C.c_int),
     "mslam_gn_solve": ([vp, vp, vp, vp, vp, vp, vp, vp, sz, vp], C.c_int),
     "mslam_match_stats": ([vp, vp, vp, vp, vp, sz, vp], C.c_int),
     "mslam_ray_image": ([C.c_int, C.c_int64, vp, vp, vp], C.c_int),

@@ -259,6 +259,24 @@ def gn_pack(plan: Plan, params: Params, X_canon, idx, q, packed=None):
     return packed
 
 
+def gn_track(plan: Plan, params: Params, dtype, T_wc, packed, n_iters: int, dev_status=None, workspace=None):
+    """mslam_gn_track (Sec. 3.3): n_iters tracking Gauss-Newton iterations, one
+    launch each, on plans whose every graph is one keyframe and one frame
+    joined by one edge; T_wc [N, 8] FP64 updated in place.  Returns the
+    per-graph status."""
+    if dtype not in DTYPES:
+        raise ValueError(f"unsupported storage dtype {dtype}")
+    dev = packed.device
+    _need(T_wc, "T_wc", torch.float64, 8 * plan.N)
+    _need(packed, "packed", torch.uint8)
+    st = torch.zeros(plan.G, dtype=torch.int32, device=dev) if dev_status is None else dev_status
+    ws = plan.workspace(_lib.MSLAM_OP_TRACK) if workspace is None else workspace
+    check(lib().mslam_gn_track(C.byref(params), plan.handle, DTYPES[dtype], T_wc.data_ptr(), packed.data_ptr(),
+                               packed.numel(), int(n_iters), st.data_ptr(), ws.data_ptr(), ws.numel(), _stream(dev)),
+          "mslam_gn_track")
+    return st
+
+
 def gn_linearize_packed(plan: Plan, params: Params, dtype, T_wc, packed, H=None, g=None, cost=None, n_valid=None,
                         workspace=None, per_edge: bool = False):
     """mslam_gn_linearize_packed: the linearisation of gn_linearize from the
@@ -395,6 +413,19 @@ class GaussNewton:
         self.pack()
         for _ in range(iters):
             self.step()
+        return self.T
+
+    def run_tracking(self, T_init, iters: int):
+        """Pack and run `iters` iterations with mslam_gn_track (one launch per
+        iteration; plans of one keyframe and one frame per graph, packed form)."""
+        if not self.packed:
+            raise ValueError("run_tracking needs the packed form")
+        if not hasattr(self, "ws_track"):
+            self.ws_track = self.plan.workspace(_lib.MSLAM_OP_TRACK)
+        self.T.copy_(T_init)
+        self.status.zero_()
+        self.pack()
+        gn_track(self.plan, self.params, self.X.dtype, self.T, self.pack_buf, iters, self.status, self.ws_track)
         return self.T
 
     def capture(self, iters: int):

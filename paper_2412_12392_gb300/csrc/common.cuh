@@ -326,6 +326,7 @@ int plan_lin_form(const mslam_plan* plan);  // 0 block-streamed, 1 register pipe
 int plan_solve_form(const mslam_plan* plan);  // 0 mixed precision, 1 FP64 only
 int64_t plan_max_mixed_bytes(const mslam_plan* plan);  // shared memory of the mixed-precision solve
 int64_t plan_max_mixed_bytes_nofactor(const mslam_plan* plan);  // the same without the FP32 factor
+bool plan_tracking_form(const mslam_plan* plan);  // every graph: one fixed keyframe, one frame, one edge
 int64_t plan_max_mixed_elems(const mslam_plan* plan);  // elements of its assembly kernel
 int plan_max_unknown_blocks(const mslam_plan* plan);   // largest non-fixed pose count of a graph
 int64_t plan_solve_ws_doubles(const mslam_plan* plan);    // FP64 solve workspace of all graphs (doubles)

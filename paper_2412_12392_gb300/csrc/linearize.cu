@@ -949,6 +949,33 @@ __global__ void __launch_bounds__(kWarpStreamThreads, 1)
   }
 }
 
+// The ray family's relative 7 x 7 system and gradient from its 30
+// structured sums S (FP64): H_tt = S0 I + S[1..6], H_ww = S13 I - S[14..19],
+// H_tw = -[S7..9]x, the scale column S[10..12] and S20, g = S[21..27].
+__device__ void ray_relative_system(const double* S, double Hr[49], double g[7]) {
+  for (int k = 0; k < 49; ++k) Hr[k] = 0.0;
+  const double s2[6] = {S[1], S[2], S[3], S[4], S[5], S[6]};
+  const int sym[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      Hr[7 * a + b] = (a == b ? S[0] : 0.0) + s2[sym[a][b]];
+      Hr[7 * (3 + a) + 3 + b] = (a == b ? S[13] : 0.0) - S[14 + sym[a][b]];
+    }
+  const double s3x = S[7], s3y = S[8], s3z = S[9];
+  const double tw[9] = {0.0, s3z, -s3y, -s3z, 0.0, s3x, s3y, -s3x, 0.0};
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      Hr[7 * a + 3 + b] = tw[3 * a + b];
+      Hr[7 * (3 + b) + a] = tw[3 * a + b];
+    }
+  for (int a = 0; a < 3; ++a) {
+    Hr[7 * a + 6] = S[10 + a];
+    Hr[7 * 6 + a] = S[10 + a];
+  }
+  Hr[48] = S[20];
+  for (int a = 0; a < 7; ++a) g[a] = S[21 + a];
+}
+
 // One block per edge: FP64 sum of the edge's tile partials (four groups of
 // threads take every fourth tile, then the groups' sums are added in a fixed
 // order), then the 14x14.
@@ -991,29 +1018,7 @@ __global__ void __launch_bounds__(kFinalizeThreads) lin_finalize_kernel(PlanView
     if (n_valid) n_valid[e] = (int32_t)S[36];
   }
   if (tid == 0 && kind == MSLAM_RES_RAY) {
-    for (int k = 0; k < 49; ++k) Hr[k] = 0.0;
-    // H_tt = S1 I + S2
-    const double s2[6] = {S[1], S[2], S[3], S[4], S[5], S[6]};
-    const int sym[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
-    for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < 3; ++b) {
-        Hr[7 * a + b] = (a == b ? S[0] : 0.0) + s2[sym[a][b]];
-        Hr[7 * (3 + a) + 3 + b] = (a == b ? S[13] : 0.0) - S[14 + sym[a][b]];
-      }
-    // H_tw = -[S3]x
-    const double s3x = S[7], s3y = S[8], s3z = S[9];
-    const double tw[9] = {0.0, s3z, -s3y, -s3z, 0.0, s3x, s3y, -s3x, 0.0};
-    for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < 3; ++b) {
-        Hr[7 * a + 3 + b] = tw[3 * a + b];
-        Hr[7 * (3 + b) + a] = tw[3 * a + b];
-      }
-    for (int a = 0; a < 3; ++a) {
-      Hr[7 * a + 6] = S[10 + a];
-      Hr[7 * 6 + a] = S[10 + a];
-    }
-    Hr[48] = S[20];
-    for (int a = 0; a < 7; ++a) g[a] = S[21 + a];
+    ray_relative_system(S, Hr, g);
     cost[e] = S[28];
     if (n_valid) n_valid[e] = (int32_t)S[29];
   }
@@ -1043,6 +1048,153 @@ __global__ void __launch_bounds__(kFinalizeThreads) lin_finalize_kernel(PlanView
     for (int k = 0; k < 7; ++k) s += A[7 * k + r] * g[k];
     g14[(size_t)e * 14 + r] = (float)(-s);
     g14[(size_t)e * 14 + 7 + r] = (float)s;
+  }
+}
+
+// ------------------------------------------------------------- tracking
+// One Gauss-Newton iteration of tracking problems per launch, one block per
+// tile: the block forms its edge's relative pose from T_wc, accumulates the
+// tile's packed records (ray family) and stores the tile's sums; the block
+// that completes an edge's last tile (a counter per edge, after a device
+// fence) adds the edge's tile sums in tile order in FP64, maps the relative
+// system to the frame's 7 x 7 with the adjoint of T_i^-1, solves it by FP64
+// Cholesky, retracts the frame's pose and resets the counter.  No block
+// waits for another.
+template <typename T>
+__global__ void __launch_bounds__(kLinThreads) track_kernel(PlanView pv, LinConst lc, double conv_tol,
+                                                            double* __restrict__ T_wc,
+                                                            const uint4* __restrict__ recs,
+                                                            const int32_t* __restrict__ counts,
+                                                            float* __restrict__ partials, int32_t* __restrict__ done,
+                                                            int32_t* __restrict__ dev_status) {
+  __shared__ float red[kLinThreads / 32][kFamAcc];
+  __shared__ float sP[12];
+  __shared__ int s_last;
+  __shared__ double S[kNumAcc], Hr[49], A[49], C[49], H7[49], gr[7], g7[7];
+  const int tid = threadIdx.x, tile = blockIdx.x;
+  const DevTile tl = pv.tiles[tile];
+  const DevEdge ed = pv.edges[tl.edge];
+  const int g = ed.graph;
+  // a converged or failed graph is skipped by all of its blocks (its status
+  // changes only in the block that finishes the graph, after they all ran)
+  if (__ldcg(dev_status + g) > 0) return;
+  if (tid == 0) {
+    const Sim3d Ti = load_pose(T_wc + 8 * ed.i), Tj = load_pose(T_wc + 8 * ed.j);
+    const Sim3d Tij = compose(inverse(Ti), Tj);
+    double R[9];
+    rot_of(Tij.q, R);
+    for (int k = 0; k < 9; ++k) sP[k] = (float)(Tij.s * R[k]);
+    for (int k = 0; k < 3; ++k) sP[9 + k] = (float)Tij.t[k];
+  }
+  __syncthreads();
+  RelPose P;
+  for (int k = 0; k < 9; ++k) P.R[k] = sP[k];
+  for (int k = 0; k < 3; ++k) P.t[k] = sP[9 + k];
+  float acc[kNumAcc];
+#pragma unroll
+  for (int a = 0; a < kNumAcc; ++a) acc[a] = 0.0f;
+  constexpr int W = PackRec<T>::kWords;
+  const int cnt = __ldg(counts + tile);
+  const uint4* in = recs + (size_t)tile * pv.lin_tile * W;
+  for (int r = tid; r < cnt; r += kLinThreads) {
+    float3 xj, yy;
+    float qq;
+    PackRec<T>::load(in + (size_t)r * W, xj, yy, qq);
+    accumulate<false>(acc, P, xj, yy, qq, lc);
+  }
+  reduce_store<kNumAcc>(acc, red, partials, tile);  // ends with a barrier
+  if (tid == 0) {
+    __threadfence();  // this tile's sums before the count
+    s_last = atomicAdd(done + tl.edge, 1) == ed.tile_end - ed.tile_begin - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (tid < kNumAcc) {
+    double sum = 0.0;
+    for (int t = ed.tile_begin; t < ed.tile_end; ++t) sum += (double)__ldcg(partials + (size_t)t * kAccStride + tid);
+    S[tid] = sum;
+  }
+  if (tid == 32) {
+    const Sim3d Ti = load_pose(T_wc + 8 * ed.i);
+    adjoint_of(inverse(Ti), A);
+  }
+  __syncthreads();
+  if (tid == 0) ray_relative_system(S, Hr, gr);
+  __syncthreads();
+  if (tid < 49) {
+    const int r = tid / 7, c = tid % 7;
+    double v = 0.0;
+    for (int k = 0; k < 7; ++k) v += Hr[7 * r + k] * A[7 * k + c];
+    C[tid] = v;
+  }
+  __syncthreads();
+  const int gauge = pv.graphs[g].gauge;
+  const int k_free = ed.i == gauge ? ed.j : ed.i;
+  const double sgn = ed.i == gauge ? 1.0 : -1.0;  // g_j = Ad^T g_rel, g_i = -Ad^T g_rel
+  if (tid < 49) {
+    const int r = tid / 7, c = tid % 7;
+    double v = 0.0;
+    for (int k = 0; k < 7; ++k) v += A[7 * k + r] * C[7 * k + c];
+    H7[tid] = v;
+  }
+  if (tid >= 64 && tid < 71) {
+    const int r = tid - 64;
+    double v = 0.0;
+    for (int k = 0; k < 7; ++k) v += A[7 * k + r] * gr[k];
+    g7[r] = sgn * v;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    // FP64 Cholesky H7 = L L^T (lower triangle in place), pivots checked
+    // against the diagonal as in the FP64 solve, then tau = -H7^-1 g7
+    double L[49], diag[7], tau[7];
+    for (int k = 0; k < 49; ++k) L[k] = H7[k];
+    for (int j = 0; j < 7; ++j) diag[j] = H7[8 * j];
+    int status = 0;
+    for (int j = 0; j < 7 && status == 0; ++j) {
+      double d = L[8 * j];
+      for (int k = 0; k < j; ++k) d -= L[7 * j + k] * L[7 * j + k];
+      if (!(d > 1e-12 * diag[j]) || !isfinite(d)) {
+        status = MSLAM_ERR_NOT_PD;
+        break;
+      }
+      const double ljj = sqrt(d);
+      L[8 * j] = ljj;
+      for (int i = j + 1; i < 7; ++i) {
+        double v = L[7 * i + j];
+        for (int k = 0; k < j; ++k) v -= L[7 * i + k] * L[7 * j + k];
+        L[7 * i + j] = v / ljj;
+      }
+    }
+    if (status == 0) {
+      double y[7];
+      for (int i = 0; i < 7; ++i) {
+        double v = -g7[i];
+        for (int k = 0; k < i; ++k) v -= L[7 * i + k] * y[k];
+        y[i] = v / L[8 * i];
+      }
+      for (int i = 6; i >= 0; --i) {
+        double v = y[i];
+        for (int k = i + 1; k < 7; ++k) v -= L[7 * k + i] * tau[k];
+        tau[i] = v / L[8 * i];
+      }
+      double mx = 0.0;
+      bool finite = true;
+      for (int a = 0; a < 7; ++a) {
+        finite = finite && isfinite(tau[a]);
+        mx = fmax(mx, fabs(tau[a]));
+      }
+      if (!finite) {
+        status = MSLAM_ERR_NONFINITE;
+      } else {
+        const Sim3d E = sim3_exp(tau);
+        store_pose(compose(E, load_pose(T_wc + 8 * k_free)), T_wc + 8 * k_free);
+        if (mx < conv_tol) status = 1;
+      }
+    }
+    if (status != 0) dev_status[g] = status;
+    done[tl.edge] = 0;  // ready for the next iteration
   }
 }
 
@@ -1345,4 +1497,66 @@ extern "C" mslam_status mslam_gn_linearize_packed(const mslam_params* p, const m
     }
   });
   return cuda_check(cudaGetLastError(), "gn_linearize_packed launch");
+}
+
+extern "C" mslam_status mslam_gn_track(const mslam_params* p, const mslam_plan* plan, mslam_dtype dt, double* T_wc,
+                                       const void* packed, size_t packed_bytes, int32_t n_iters,
+                                       int32_t* dev_status, void* workspace, size_t ws_bytes, void* stream) {
+  if (!p || !check_plan_uploaded(plan)) {
+    if (!p) set_error("params is NULL");
+    return MSLAM_ERR_ARG;
+  }
+  if (dt != MSLAM_F32 && dt != MSLAM_F16) {
+    set_error("unsupported dtype %d", (int)dt);
+    return MSLAM_ERR_ARG;
+  }
+  if (!plan_tracking_form(plan)) {
+    set_error("gn_track: every graph of the plan must be one keyframe and one frame joined by one edge");
+    return MSLAM_ERR_ARG;
+  }
+  if (p->residual != MSLAM_RES_RAY) {
+    set_error("gn_track: only the ray residual family (residual %d given)", (int)p->residual);
+    return MSLAM_ERR_ARG;
+  }
+  if (n_iters < 0) {
+    set_error("gn_track: n_iters %d < 0", (int)n_iters);
+    return MSLAM_ERR_ARG;
+  }
+  if (!T_wc || !packed || !dev_status || !workspace) {
+    set_error("gn_track: NULL device pointer");
+    return MSLAM_ERR_ARG;
+  }
+  const PlanView pv = plan_view(plan);
+  if (packed_bytes < pack_bytes(pv.n_tiles, pv.lin_tile, dt) || (reinterpret_cast<uintptr_t>(packed) & 255)) {
+    set_error("gn_track: packed buffer smaller than %zu bytes or not 256-byte aligned",
+              pack_bytes(pv.n_tiles, pv.lin_tile, dt));
+    return MSLAM_ERR_ARG;
+  }
+  if (ws_bytes < mslam_workspace_bytes(plan, MSLAM_OP_TRACK) || (reinterpret_cast<uintptr_t>(workspace) & 255)) {
+    set_error("gn_track: workspace smaller than %zu bytes or not 256-byte aligned",
+              mslam_workspace_bytes(plan, MSLAM_OP_TRACK));
+    return MSLAM_ERR_ARG;
+  }
+  LinConst lc;
+  const mslam_status st = make_lin_const(p, &lc, "gn_track");
+  if (st != MSLAM_OK) return st;
+  if (n_iters == 0) return MSLAM_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  float* partials = static_cast<float*>(workspace);
+  int32_t* done = reinterpret_cast<int32_t*>(static_cast<char*>(workspace) + lin_partials_bytes(pv.n_tiles));
+  const uint4* recs = static_cast<const uint4*>(packed);
+  const int32_t* counts = reinterpret_cast<const int32_t*>(
+      static_cast<const char*>(packed) + pack_bytes(pv.n_tiles, pv.lin_tile, dt) -
+      (((size_t)pv.n_tiles * sizeof(int32_t) + 255) & ~size_t(255)));
+  mslam_status st2 = cuda_check(cudaMemsetAsync(done, 0, sizeof(int32_t) * (size_t)pv.E, s), "gn_track memset");
+  if (st2 != MSLAM_OK) return st2;
+  for (int it = 0; it < n_iters; ++it) {
+    if (dt == MSLAM_F32)
+      track_kernel<float><<<pv.n_tiles, kLinThreads, 0, s>>>(pv, lc, p->conv_tol, T_wc, recs, counts, partials,
+                                                             done, dev_status);
+    else
+      track_kernel<__half><<<pv.n_tiles, kLinThreads, 0, s>>>(pv, lc, p->conv_tol, T_wc, recs, counts, partials,
+                                                              done, dev_status);
+  }
+  return cuda_check(cudaGetLastError(), "gn_track launch");
 }

@@ -95,6 +95,14 @@ void plan_edge_mblocks(const mslam_plan* plan, int e, int* b0, int* b1) {
 int64_t plan_max_graph_doubles(const mslam_plan* plan) { return plan->max_graph_doubles; }
 int64_t plan_max_mixed_bytes(const mslam_plan* plan) { return plan->max_mixed_bytes; }
 int64_t plan_max_mixed_bytes_nofactor(const mslam_plan* plan) { return plan->max_mixed_bytes_nofactor; }
+bool plan_tracking_form(const mslam_plan* plan) {
+  if (plan->E == 0 || plan->E != plan->G) return false;
+  std::vector<int> per_graph(plan->G, 0);
+  for (const auto& e : plan->dedges) ++per_graph[e.graph];
+  for (int g = 0; g < plan->G; ++g)
+    if (per_graph[g] != 1 || plan->graphs[g].m != 1) return false;
+  return true;
+}
 int64_t plan_max_mixed_elems(const mslam_plan* plan) { return plan->max_mixed_elems; }
 int plan_max_unknown_blocks(const mslam_plan* plan) { return plan->max_m; }
 int64_t plan_solve_ws_doubles(const mslam_plan* plan) { return plan->solve_ws_doubles; }
@@ -597,6 +605,9 @@ void mslam_plan_stats(const mslam_plan* plan, int32_t* order, int64_t* counts) {
 size_t mslam_workspace_bytes(const mslam_plan* plan, int32_t op) {
   if (!plan) return 0;
   switch (op) {
+    case MSLAM_OP_TRACK:
+      // tile partials, then one completed-tile counter per edge
+      return lin_partials_bytes((int)plan->tiles.size()) + align256(sizeof(int32_t) * std::max(plan->E, 1));
     case MSLAM_OP_LINEARIZE:
       // tile partials, relative poses, the tile counter
       return lin_partials_bytes((int)plan->tiles.size()) + align256(sizeof(float) * 16 * std::max(plan->E, 1)) + 256;

@@ -52,6 +52,13 @@ def test_tracking_full_size(M):
     assert st == 0
     e = assert_poses_close(T_g, T_r)
     print(f"tracking poses vs oracle (rot, trans, scale): {e.max(axis=0)}")
+    # the fused tracking loop (mslam_gn_track: one launch per iteration) on the
+    # same matches
+    gn_f = M.GaussNewton(plan, P, wd.X_canon, idx_g, q_g, packed=True)
+    T_f = gn_f.run_tracking(w.T_init.cuda(), w.n_gn_iters).cpu()
+    assert int(gn_f.status[0]) in (0, 1)
+    e_f = assert_poses_close(T_f, T_r)
+    print(f"fused tracking poses vs oracle (rot, trans, scale): {e_f.max(axis=0)}")
 
 
 @pytest.fixture(scope="module")

@@ -209,3 +209,38 @@ def test_family_argument_errors(M, tiny_wl):
     with pytest.raises(M._lib.MslamError):
         M.gn_pack(big, family_params(M, w, "pixel"), Xb, torch.zeros(8192, dtype=torch.int32, device="cuda"),
                   torch.full((8192,), 5.0, dtype=torch.float16, device="cuda"))
+
+
+def test_gn_track_several_frames(M):
+    """mslam_gn_track on three tracking problems in one plan (small images,
+    ragged tile counts): each frame's poses against the oracle's Gauss-Newton
+    run on that problem alone, fed the same matches; a plan that is not of
+    the tracking form is refused before any launch."""
+    from paper_2412_12392_gb300 import _lib
+    ws = [synth.tracking(seed=s, H=96, W=128).to_storage(torch.float16) for s in (1, 5, 9)]
+    mw = synth.merge(ws, name="frames")
+    P = M.default_params()
+    par = M.params_dict(P)
+    plan = M.Plan(mw.kf_hw.numpy(), mw.edges.numpy(), mw.graph_of_kf.numpy(), opts={"lin_tile": 1024})
+    wd = mw.to("cuda")
+    ms = [oracle.match_workload(w, 0, **par) for w in ws]
+    idx = torch.from_numpy(np.concatenate([m[0] for m in ms])).cuda()
+    q = torch.from_numpy(np.concatenate([m[1] for m in ms])).to(torch.float16).cuda()
+    gn = M.GaussNewton(plan, P, wd.X_canon, idx, q, packed=True)
+    iters = ws[0].n_gn_iters
+    T_f = gn.run_tracking(mw.T_init.cuda(), iters).cpu()
+    assert bool((gn.status.cpu() >= 0).all()) and bool((gn.status.cpu() <= 1).all())
+    for k, w in enumerate(ws):
+        sl = slice(int(mw.e_off[k]), int(mw.e_off[k + 1]))
+        st, T_r, _, _ = oracle.gauss_newton(w.N, w.edges.numpy(), w.kf_off.numpy(), w.e_off.numpy(), w.X_canon,
+                                            idx[sl].cpu(), q[sl].cpu(), w.T_init.numpy(), iters, **par)
+        assert st == 0
+        assert_poses_close(T_f[2 * k:2 * k + 2], T_r)
+        assert torch.equal(T_f[2 * k], w.T_init[0])  # the keyframe is the fixed gauge
+    g = synth.global_graph(N=4, n_pairs=3, H=24, W=32)
+    plan_g = M.Plan(g.kf_hw.numpy(), g.edges.numpy())
+    gd = g.to("cuda")
+    gn_g = M.GaussNewton(plan_g, P, gd.X_canon, torch.full((plan_g.edge_pixels,), -1, dtype=torch.int32, device="cuda"),
+                         torch.zeros(plan_g.edge_pixels, device="cuda"), packed=True)
+    with pytest.raises(_lib.MslamError):
+        gn_g.run_tracking(g.T_init.cuda(), 2)

@@ -1071,6 +1071,7 @@ __global__ void __launch_bounds__(kLinThreads) track_kernel(PlanView pv, LinCons
   __shared__ float sP[12];
   __shared__ int s_last;
   __shared__ double S[kNumAcc], Hr[49], A[49], C[49], H7[49], gr[7], g7[7];
+  __shared__ double Sg[kLinThreads / 32][kNumAcc];
   const int tid = threadIdx.x, tile = blockIdx.x;
   const DevTile tl = pv.tiles[tile];
   const DevEdge ed = pv.edges[tl.edge];
@@ -1110,14 +1111,27 @@ __global__ void __launch_bounds__(kLinThreads) track_kernel(PlanView pv, LinCons
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  if (tid < kNumAcc) {
-    double sum = 0.0;
-    for (int t = ed.tile_begin; t < ed.tile_end; ++t) sum += (double)__ldcg(partials + (size_t)t * kAccStride + tid);
-    S[tid] = sum;
+  {
+    // eight groups of lanes take every eighth tile (loads of several tiles in
+    // flight), then the groups' FP64 sums are added in a fixed order
+    const int a = tid & 31, grp = tid >> 5;
+    if (a < kNumAcc) {
+      double sum = 0.0;
+#pragma unroll 4
+      for (int t = ed.tile_begin + grp; t < ed.tile_end; t += kLinThreads / 32)
+        sum += (double)__ldcg(partials + (size_t)t * kAccStride + a);
+      Sg[grp][a] = sum;
+    }
   }
   if (tid == 32) {
     const Sim3d Ti = load_pose(T_wc + 8 * ed.i);
     adjoint_of(inverse(Ti), A);
+  }
+  __syncthreads();
+  if (tid < kNumAcc) {
+    double sum = 0.0;
+    for (int w = 0; w < kLinThreads / 32; ++w) sum += Sg[w][tid];
+    S[tid] = sum;
   }
   __syncthreads();
   if (tid == 0) ray_relative_system(S, Hr, gr);

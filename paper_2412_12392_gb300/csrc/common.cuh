@@ -292,6 +292,65 @@ __device__ __forceinline__ Sim3d sim3_exp(const double tau[7]) {
   return e;
 }
 
+// Exp(tau) of sim3_exp split into independent pieces, so that different
+// warps can evaluate them side by side: piece 0 sin and cos of theta, 1
+// e^sigma, 2 the quaternion's half-angle terms, 3 the moment m_0, 4-7 the
+// moments m_1, m_3, m_2, m_4 of the small-angle branch.  part[10] holds
+// sn, cs, es, h, q3, m0, m1, m3, m2, m4.  The same formulas as sim3_exp on the
+// same inputs, so the same values.
+__device__ inline void sim3_exp_piece(const double* tau, int kind, double* part) {
+  const double px = tau[3], py = tau[4], pz = tau[5], sg = tau[6];
+  const double th2 = px * px + py * py + pz * pz, th = sqrt(th2);
+  const bool small = th < 1e-4;
+  if (kind == 0) {
+    double sn = 0.0, cs = 0.0;
+    if (!small) sincos(th, &sn, &cs);
+    part[0] = sn;
+    part[1] = cs;
+  } else if (kind == 1) {
+    part[2] = exp(sg);
+  } else if (kind == 2) {
+    part[3] = (th < 1e-6) ? (0.5 - th2 / 48.0) : sin(0.5 * th) / th;
+    part[4] = cos(0.5 * th);
+  } else if (kind == 3) {
+    part[5] = moment_exp(0, sg);
+  } else {
+    const int n = kind == 4 ? 1 : kind == 5 ? 3 : kind == 6 ? 2 : 4;
+    part[2 + kind] = small ? moment_exp(n, sg) : 0.0;
+  }
+}
+
+__device__ inline Sim3d sim3_exp_parts(const double* tau, const double* part) {
+  const double px = tau[3], py = tau[4], pz = tau[5], sg = tau[6];
+  const double th2 = px * px + py * py + pz * pz, th = sqrt(th2);
+  const double sn = part[0], cs = part[1], es = part[2], h = part[3], q3 = part[4], a = part[5];
+  double b, c;
+  if (th < 1e-4) {
+    b = part[6] - th2 * part[7] / 6.0;
+    c = 0.5 * part[8] - th2 * part[9] / 24.0;
+  } else {
+    const double den = sg * sg + th2;
+    const double ic = ((es * cs - 1.0) * sg + es * th * sn) / den;
+    const double is = (es * sn * sg - (es * cs - 1.0) * th) / den;
+    b = is / th;
+    c = (a - ic) / th2;
+  }
+  Sim3d e;
+  e.q[0] = h * px;
+  e.q[1] = h * py;
+  e.q[2] = h * pz;
+  e.q[3] = q3;
+  qnormalise(e.q);
+  e.s = es;
+  const double r0 = tau[0], r1 = tau[1], r2 = tau[2];
+  const double c0 = py * r2 - pz * r1, c1 = pz * r0 - px * r2, c2 = px * r1 - py * r0;
+  const double d0 = py * c2 - pz * c1, d1 = pz * c0 - px * c2, d2 = px * c1 - py * c0;
+  e.t[0] = a * r0 + b * c0 + c * d0;
+  e.t[1] = a * r1 + b * c1 + c * d1;
+  e.t[2] = a * r2 + b * c2 + c * d2;
+  return e;
+}
+
 // 1/sqrt(d) in FP64 by Newton-Raphson iteration for the inverse square root,
 // y <- y (3 - d y^2) / 2, seeded with the single-precision hardware estimate:
 // two iterations take the ~23-bit seed past FP64 precision.  On this GPU a

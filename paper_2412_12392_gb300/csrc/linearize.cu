@@ -1072,6 +1072,8 @@ __global__ void __launch_bounds__(kLinThreads) track_kernel(PlanView pv, LinCons
   __shared__ int s_last;
   __shared__ double S[kNumAcc], Hr[49], A[49], C[49], H7[49], gr[7], g7[7];
   __shared__ double Sg[kLinThreads / 32][kNumAcc];
+  __shared__ double s_tau[7], s_part[10], s_mx;
+  __shared__ int s_status;
   const int tid = threadIdx.x, tile = blockIdx.x;
   const DevTile tl = pv.tiles[tile];
   const DevEdge ed = pv.edges[tl.edge];
@@ -1162,7 +1164,9 @@ __global__ void __launch_bounds__(kLinThreads) track_kernel(PlanView pv, LinCons
   if (tid == 0) {
     // FP64 Cholesky H7 = L L^T (lower triangle in place), pivots checked
     // against the diagonal as in the FP64 solve, then tau = -H7^-1 g7
-    double L[49], diag[7], tau[7];
+    // (reciprocal pivots from rsqrt_newton: FP64 division and square root
+    // are long latency chains on this part; products replace them)
+    double L[49], diag[7], tau[7], il[7];
     for (int k = 0; k < 49; ++k) L[k] = H7[k];
     for (int j = 0; j < 7; ++j) diag[j] = H7[8 * j];
     int status = 0;
@@ -1173,12 +1177,12 @@ __global__ void __launch_bounds__(kLinThreads) track_kernel(PlanView pv, LinCons
         status = MSLAM_ERR_NOT_PD;
         break;
       }
-      const double ljj = sqrt(d);
-      L[8 * j] = ljj;
+      il[j] = rsqrt_newton(d);  // 1 / L_jj
+      L[8 * j] = d * il[j];
       for (int i = j + 1; i < 7; ++i) {
         double v = L[7 * i + j];
         for (int k = 0; k < j; ++k) v -= L[7 * i + k] * L[7 * j + k];
-        L[7 * i + j] = v / ljj;
+        L[7 * i + j] = v * il[j];
       }
     }
     if (status == 0) {
@@ -1186,26 +1190,35 @@ __global__ void __launch_bounds__(kLinThreads) track_kernel(PlanView pv, LinCons
       for (int i = 0; i < 7; ++i) {
         double v = -g7[i];
         for (int k = 0; k < i; ++k) v -= L[7 * i + k] * y[k];
-        y[i] = v / L[8 * i];
+        y[i] = v * il[i];
       }
       for (int i = 6; i >= 0; --i) {
         double v = y[i];
         for (int k = i + 1; k < 7; ++k) v -= L[7 * k + i] * tau[k];
-        tau[i] = v / L[8 * i];
+        tau[i] = v * il[i];
       }
       double mx = 0.0;
       bool finite = true;
       for (int a = 0; a < 7; ++a) {
         finite = finite && isfinite(tau[a]);
         mx = fmax(mx, fabs(tau[a]));
+        s_tau[a] = tau[a];
       }
-      if (!finite) {
-        status = MSLAM_ERR_NONFINITE;
-      } else {
-        const Sim3d E = sim3_exp(tau);
-        store_pose(compose(E, load_pose(T_wc + 8 * k_free)), T_wc + 8 * k_free);
-        if (mx < conv_tol) status = 1;
-      }
+      if (!finite) status = MSLAM_ERR_NONFINITE;
+      s_mx = mx;
+    }
+    s_status = status;
+  }
+  __syncthreads();
+  // Exp(tau): its transcendental pieces side by side in eight threads
+  if (s_status == 0 && tid < 8) sim3_exp_piece(s_tau, tid, s_part);
+  __syncthreads();
+  if (tid == 0) {
+    int status = s_status;
+    if (status == 0) {
+      const Sim3d E = sim3_exp_parts(s_tau, s_part);
+      store_pose(compose(E, load_pose(T_wc + 8 * k_free)), T_wc + 8 * k_free);
+      if (s_mx < conv_tol) status = 1;
     }
     if (status != 0) dev_status[g] = status;
     done[tl.edge] = 0;  // ready for the next iteration

@@ -1,5 +1,5 @@
-"""Autotuner for the plan's launch shapes (spec: tile and pixels-per-
-thread choices made by the project's own tuner).
+"""Autotuner for the plan's launch shapes: the linearisation tile size and
+form, blocks per SM and the match block shape (pixels per block row).
 
 Each candidate is timed on the caller's device-resident inputs with CUDA
 events -- the match block shape on mslam_match, the linearisation tile size

@@ -678,7 +678,13 @@ def run_reference(args, world, rank):
     import synth
     from paper_2412_12392_gb300 import _lib  # noqa: F401  (only for the parameter defaults below)
     oracle.build()
-    w = make_workload(args, 0, "cpu")
+    # the synthetic inputs are made with torch on the GPU when there is one
+    # (minutes of host time otherwise) and handed to the oracle on the host;
+    # no kernel of this library runs in this arm
+    gen_dev = "cuda" if torch.cuda.is_available() else "cpu"
+    w = make_workload(args, 0, gen_dev).to("cpu")
+    if gen_dev == "cuda":
+        torch.cuda.empty_cache()
     par = dict(oracle.DEFAULT_PARAMS)
     n_query = int(w.e_off[-1])
     n_matched = int((w.gt_match >= 0).sum())

@@ -17,7 +17,10 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
-_SO = os.path.join(_BUILD, "liboracle.so")
+# ORC_MUTANT=<NAME> selects a copy of the oracle with one planted mistake
+# (oracle.c, ORC_MUTANT_<NAME>); only the mutation tests set it
+_MUTANT = os.environ.get("ORC_MUTANT", "")
+_SO = os.path.join(_BUILD, f"liboracle_mutant_{_MUTANT.lower()}.so" if _MUTANT else "liboracle.so")
 _lib = None
 
 DEFAULT_PARAMS: Dict = dict(
@@ -51,7 +54,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     tmp = _SO + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-           "-fno-fast-math", "-o", tmp, src, "-lm"]
+           "-fno-fast-math", "-o", tmp, src, "-lm"] + ([f"-DORC_MUTANT_{_MUTANT}"] if _MUTANT else [])
     subprocess.run(cmd, check=True)
     os.replace(tmp, _SO)
     return _SO

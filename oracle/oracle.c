@@ -8,6 +8,11 @@
  * bilinear cell, the LM schedule, the refinement window, the weight form) are
  * the ones listed in the design notes and are repeated at each routine.
  * OpenMP parallelises only over independent pixels or edges.
+ *
+ * ORC_MUTANT_<NAME> (off in every normal build): a copy compiled with one of
+ * these defines carries one planted mistake (a flipped sign, a transposed
+ * operand, a dropped term, a wrong branch of a weight, a wrong rounding or
+ * gauge), so that the tests can show that a pin of this oracle catches it.
  */
 #include "oracle.h"
 
@@ -124,7 +129,11 @@ void orc_sim3_exp(const double tau[7], double T[8]) {
   quat_normalise(q);
   double V[9];
   sim3_V(phi, sigma, V);
+#ifdef ORC_MUTANT_EXP_NO_V
+  for (int r = 0; r < 3; ++r) T[r] = rho[r];
+#else
   for (int r = 0; r < 3; ++r) T[r] = V[3 * r] * rho[0] + V[3 * r + 1] * rho[1] + V[3 * r + 2] * rho[2];
+#endif
   for (int r = 0; r < 4; ++r) T[3 + r] = q[r];
   T[7] = exp(sigma);
 }
@@ -323,14 +332,23 @@ void orc_match(const orc_params* P, int H, int W, int d, const double* X_ref, co
       double du = (a11 * b0 - a01 * b1) / det;
       double dv = (a00 * b1 - a01 * b0) / det;
       last = sqrt(du * du + dv * dv);
+#ifdef ORC_MUTANT_LM_SIGN
+      u -= du;
+      v -= dv;
+#else
       u += du;
       v += dv;
+#endif
       if (u < 0) u = 0;
       if (u > W - 1) u = W - 1;
       if (v < 0) v = 0;
       if (v > H - 1) v = H - 1;
     }
+#ifdef ORC_MUTANT_ROUND_FLOOR
+    int cu = (int)floor(u), cv = (int)floor(v);
+#else
     int cu = (int)floor(u + 0.5), cv = (int)floor(v + 0.5);
+#endif
     if (dg) {
       double fu = fabs(u - floor(u) - 0.5), fv = fabs(v - floor(v) - 0.5);
       dg[0] = u; dg[1] = v; dg[2] = last; dg[5] = fu < fv ? fu : fv;
@@ -395,7 +413,11 @@ static int residual_jacobian_rel(const double Tij[8], const double Ad[49], const
   for (int rr = 0; rr < 3; ++rr) {
     for (int c = 0; c < 3; ++c) {
       Dx[7 * rr + c] = (rr == c) ? 1.0 : 0.0;
+#ifdef ORC_MUTANT_JAC_ROT_SIGN
+      Dx[7 * rr + 3 + c] = S[3 * rr + c];
+#else
       Dx[7 * rr + 3 + c] = -S[3 * rr + c];
+#endif
     }
     Dx[7 * rr + 6] = x[rr];
   }
@@ -408,7 +430,14 @@ static int residual_jacobian_rel(const double Tij[8], const double Ad[49], const
   matmul(Dr, Dx, Jrel, 4, 3, 7);
   /* dT_ij/dT_i = -Ad_{T_i^-1}, dT_ij/dT_j = Ad_{T_i^-1} */
   double JA[28];
+#ifdef ORC_MUTANT_ADJ_T
+  double AdT[49];
+  for (int a = 0; a < 7; ++a)
+    for (int b = 0; b < 7; ++b) AdT[7 * a + b] = Ad[7 * b + a];
+  matmul(Jrel, AdT, JA, 4, 7, 7);
+#else
   matmul(Jrel, Ad, JA, 4, 7, 7);
+#endif
   for (int rr = 0; rr < 4; ++rr)
     for (int c = 0; c < 7; ++c) {
       J[14 * rr + c] = -JA[7 * rr + c];
@@ -491,7 +520,11 @@ int orc_residual_jacobian_p(const orc_params* P, const double Ti[8], const doubl
 
 /* Huber cost and IRLS weight of a whitened residual norm e */
 static double huber_cost(double e, double delta) { return e <= delta ? 0.5 * e * e : delta * (e - 0.5 * delta); }
+#ifdef ORC_MUTANT_HUBER_SQ
+static double huber_weight(double e, double delta) { return e <= delta ? 1.0 : delta / (e * e); }
+#else
 static double huber_weight(double e, double delta) { return e <= delta ? 1.0 : delta / e; }
+#endif
 
 /* Eq. backend_ray for one edge with the weight w(q, sigma^2) = sigma^2 / q read
  * as the information q / sigma^2 on the squared residual, a Huber norm on the
@@ -542,7 +575,11 @@ void orc_linearize_edge(const orc_params* P, const double Ti[8], const double Tj
         H14[14 * a + b] += s;
       }
       double s = 0.0;
+#ifdef ORC_MUTANT_DROP_DIST_GRAD
+      for (int k = 0; k < (rows == 4 ? 3 : rows); ++k) s += J[14 * k + a] * w[k] * r[k];
+#else
       for (int k = 0; k < rows; ++k) s += J[14 * k + a] * w[k] * r[k];
+#endif
       g14[a] += s;
     }
     ++nv;
@@ -572,6 +609,9 @@ int orc_gn_solve(int N, int E, const int32_t* edges, const double* H14, const do
   }
   int m = 7 * (N - 1);
   int* keep = (int*)malloc(sizeof(int) * (m > 0 ? m : 1));
+#ifdef ORC_MUTANT_GAUGE
+  gauge = N - 1;  /* the last pose fixed instead of the first */
+#endif
   for (int k = 0, c = 0; k < N; ++k)
     if (k != gauge)
       for (int a = 0; a < 7; ++a) keep[c++] = 7 * k + a;

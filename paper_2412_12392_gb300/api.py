@@ -182,6 +182,21 @@ def match_stats(plan: Plan, idx, workspace=None):
     return nv, nu
 
 
+OMEGA_K = 0.333  # keyframe threshold omega_k of the paper's evaluation setup (Supp. S4)
+
+
+def keyframe_needed(n_valid, n_unique, n_query, omega_k: float = OMEGA_K):
+    """The keyframe criterion of Sec. 3.4 from mslam_match_stats' counts: a new
+    keyframe is needed when the fraction of the frame's query pixels with a
+    valid match, or the fraction of distinct keyframe pixels they hit, falls
+    below omega_k.  n_valid, n_unique: per-edge counts (tensors or arrays);
+    n_query: query pixels per edge.  Host arithmetic on the counts only."""
+    nv = torch.as_tensor(n_valid).double()
+    nu = torch.as_tensor(n_unique).double()
+    nq = torch.as_tensor(n_query, dtype=torch.float64).clamp_min(1.0)
+    return (nv / nq < omega_k) | (nu / nq < omega_k)
+
+
 def ray_image(X: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
     """mslam_ray_image (a1, Sec. 3.1): psi(X) = X / |X| for X [..., 3] (FP32 or
     FP16, CUDA), the zero ray for a zero or non-finite point."""

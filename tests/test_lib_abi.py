@@ -124,3 +124,21 @@ def test_calls_reject_unuploaded_plan_and_null_args(L):
     assert st == _lib.MSLAM_ERR_ARG and "uploaded" in _lib.last_error()
     st = L.mslam_match(None, p.handle, 0, 16, *([None] * 9), -1, -1, 0, None)
     assert st == _lib.MSLAM_ERR_ARG
+
+
+def test_workspace_sizes_of_each_op(L):
+    """mslam_workspace_bytes: the tracking op holds the tile partials (40
+    floats per tile, 256-byte aligned) and one counter per edge; unknown ops
+    need nothing; a tracking call on a plan that was never uploaded is
+    refused before anything is enqueued."""
+    from paper_2412_12392_gb300 import _lib
+    p = plan([[96, 128], [96, 128]], [[0, 1]])
+    n_tiles = int(p.counts[2])
+    part = (4 * 40 * n_tiles + 255) // 256 * 256
+    assert p.workspace_bytes(_lib.MSLAM_OP_TRACK) == part + 256
+    assert p.workspace_bytes(_lib.MSLAM_OP_LINEARIZE) >= part
+    assert p.workspace_bytes(99) == 0
+    prm = _lib.Params()
+    L.mslam_default_params(C.byref(prm))
+    st = L.mslam_gn_track(C.byref(prm), p.handle, 1, None, None, 0, 1, None, None, 0, None)
+    assert st == _lib.MSLAM_ERR_ARG  # not uploaded (no GPU here)

@@ -334,7 +334,11 @@ def pick_pipelined_shapes(arm, world, steps: int = 5, warmup: int = 3):
     its best register-pipeline shape as pipelined steps and keep the faster
     (the same work either way; only the launch shapes differ)."""
     rep = arm.tuning
-    if rep is None or rep["opts"].get("lin_form") == 1:
+    need = rep is not None and rep["opts"].get("lin_form") != 1
+    if world > 1:
+        # every rank takes part in the timing collectives if any rank needs them
+        need = max_over_ranks(1.0 if need else 0.0, world) > 0.0
+    if not need or rep is None:
         return None
     best, key_best = float("inf"), None
     for key, ms in rep["lin_ms"].items():

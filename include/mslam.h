@@ -159,6 +159,10 @@ typedef struct {
   int32_t solve_form;  /* 0 = FP32 factorisation of the diagonally scaled system with FP64 iterative
                           refinement to the FP64 solution (default; graphs it declines go to the FP64
                           factorisation), 1 = FP64 factorisation only */
+  int32_t wait_limit;  /* polls of every bounded device wait on an asynchronous copy (the streamed
+                          linearisation forms) before it gives up: 0 = the default 2^24 (about a
+                          second), > 0 = that many; < 0 = give up at once without issuing any copy (so
+                          that nothing is in flight), which exercises the timeout path in tests */
 } mslam_plan_opts;
 void mslam_default_plan_opts(mslam_plan_opts* opts);
 mslam_status mslam_plan_create_ex(int32_t N, const int32_t* kf_hw, int32_t E, const int32_t* edges,
@@ -281,14 +285,20 @@ mslam_status mslam_gn_linearize(const mslam_params* p, const mslam_plan* plan, m
  * aligned; it must be re-packed whenever X_canon, idx or q change.  The
  * record layout depends on the residual family (the pixel family stores
  * (u_m, v_m, depth of X_i[m]) in place of X_i[m]), so both calls take the
- * same parameters.  Other arguments and outputs as mslam_gn_linearize.
- * Errors: MSLAM_ERR_ARG, MSLAM_ERR_CUDA. */
+ * same parameters.  Other arguments and outputs as mslam_gn_linearize, plus
+ * dev_status [G] int32 (the array mslam_gn_solve takes) or NULL: the
+ * streamed forms (plan option lin_form 0 and 2) wait for their asynchronous
+ * record copies with bounded waits (plan option wait_limit); if one gives
+ * up, the launch's blocks are written as NaN, every graph of the launch gets
+ * MSLAM_ERR_TIMEOUT in dev_status (which mslam_gn_solve then skips, leaving
+ * its poses unchanged) and the kernel returns after its copies in flight
+ * have landed.  Errors: MSLAM_ERR_ARG, MSLAM_ERR_CUDA. */
 mslam_status mslam_gn_pack(const mslam_params* p, const mslam_plan* plan, mslam_dtype dt, const void* X_canon,
                            const int32_t* idx, const void* q, void* packed, size_t packed_bytes, void* stream);
 mslam_status mslam_gn_linearize_packed(const mslam_params* p, const mslam_plan* plan, mslam_dtype dt,
                                        const double* T_wc, const void* packed, size_t packed_bytes, float* H_blocks,
-                                       float* g_blocks, double* cost, int32_t* n_valid, void* workspace,
-                                       size_t ws_bytes, uint32_t flags, void* stream);
+                                       float* g_blocks, double* cost, int32_t* n_valid, int32_t* dev_status,
+                                       void* workspace, size_t ws_bytes, uint32_t flags, void* stream);
 
 /* mslam_gn_linearize without a workspace argument.  The paper has no
  * counterpart: this exists for callers that cannot allocate device memory --
@@ -298,13 +308,16 @@ mslam_status mslam_gn_linearize_packed(const mslam_params* p, const mslam_plan* 
  * buffers.  It uses a scratch array built into the library (4 MiB, held on
  * every GPU that loads the library until the process exits) and allocates
  * nothing; inputs and outputs are the caller's, exactly as in
- * mslam_gn_linearize.  The first call on a device looks up that device's
- * address of the array (cudaGetSymbolAddress) and so should come before any
- * stream capture on that device.  All calls on a device share the array and
- * every call rewrites what it reads, so nothing needs clearing; calls whose
- * GPU work overlaps (e.g. on two streams) race on it and must be serialised.
+ * mslam_gn_linearize.  The first call in a device's context looks up that
+ * context's address of the array (cudaGetSymbolAddress, with the device
+ * current; looked up again if the device's context has changed, e.g. after
+ * cudaDeviceReset) and so should come before any stream capture on that
+ * device.  All calls on a device share the array and every call rewrites
+ * what it reads, so nothing needs clearing; calls whose GPU work overlaps
+ * (e.g. on two streams) race on it and must be serialised.
  * Errors: MSLAM_ERR_RANGE if the plan needs more scratch than the array
- * holds (about 32,768 work tiles of 8,192 pixels), otherwise as
+ * holds (26,214 work tiles of 40 floats: about 26,000 tiles, i.e. 215 M
+ * query pixels with the default 8,192-pixel tiles), otherwise as
  * mslam_gn_linearize. */
 mslam_status mslam_gn_linearize_noalloc(const mslam_params* p, const mslam_plan* plan, mslam_dtype dt,
                                         const double* T_wc, const void* X_canon, const int32_t* idx, const void* q,

@@ -47,7 +47,7 @@ class Params(C.Structure):
 class PlanOpts(C.Structure):
     """Mirror of mslam_plan_opts."""
     _fields_ = [("lin_tile", C.c_int32), ("lin_blocks_per_sm", C.c_int32), ("match_block_w", C.c_int32),
-                ("lin_form", C.c_int32), ("solve_form", C.c_int32)]
+                ("lin_form", C.c_int32), ("solve_form", C.c_int32), ("wait_limit", C.c_int32)]
 
 
 class MslamError(RuntimeError):
@@ -85,7 +85,7 @@ SIGNATURES = {
     "mslam_gn_linearize": ([vp, vp, C.c_int, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, u32, vp], C.c_int),
     "mslam_gn_linearize_noalloc": ([vp, vp, C.c_int, vp, vp, vp, vp, vp, vp, vp, vp, u32, vp], C.c_int),
     "mslam_gn_pack": ([vp, vp, C.c_int, vp, vp, vp, vp, sz, vp], C.c_int),
-    "mslam_gn_linearize_packed": ([vp, vp, C.c_int, vp, vp, sz, vp, vp, vp, vp, vp, sz, u32, vp], C.c_int),
+    "mslam_gn_linearize_packed": ([vp, vp, C.c_int, vp, vp, sz, vp, vp, vp, vp, vp, vp, sz, u32, vp], C.c_int),
     "mslam_gn_track": ([vp, vp, C.c_int, vp, vp, sz, i32, vp, vp, sz, vp], C.c_int),
     "mslam_gn_solve": ([vp, vp, vp, vp, vp, vp, vp, vp, sz, vp], C.c_int),
     "mslam_match_stats": ([vp, vp, vp, vp, vp, sz, vp], C.c_int),

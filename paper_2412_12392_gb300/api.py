@@ -77,7 +77,7 @@ class Plan:
         for k, v in (opts or {}).items():
             setattr(o, k, int(v))
         self.opts = {k: getattr(o, k) for k in ("lin_tile", "lin_blocks_per_sm", "match_block_w", "lin_form",
-                                                   "solve_form")}
+                                                   "solve_form", "wait_limit")}
         self.graph_of_kf = gk
         h = C.c_void_p()
         check(lib().mslam_plan_create_ex(self.N, kf.ctypes.data, self.E, ed.ctypes.data if self.E else None,
@@ -293,9 +293,11 @@ def gn_track(plan: Plan, params: Params, dtype, T_wc, packed, n_iters: int, dev_
 
 
 def gn_linearize_packed(plan: Plan, params: Params, dtype, T_wc, packed, H=None, g=None, cost=None, n_valid=None,
-                        workspace=None, per_edge: bool = False):
+                        workspace=None, per_edge: bool = False, dev_status=None):
     """mslam_gn_linearize_packed: the linearisation of gn_linearize from the
-    records of gn_pack."""
+    records of gn_pack.  dev_status (int32 [G] or None) receives
+    MSLAM_ERR_TIMEOUT for the graphs of a streamed launch whose bounded wait
+    gave up."""
     if dtype not in DTYPES:
         raise ValueError(f"unsupported storage dtype {dtype}")
     dev = packed.device
@@ -306,11 +308,13 @@ def gn_linearize_packed(plan: Plan, params: Params, dtype, T_wc, packed, H=None,
     g = torch.empty(E, 14, dtype=torch.float32, device=dev) if g is None else g
     cost = torch.empty(E, dtype=torch.float64, device=dev) if cost is None else cost
     n_valid = torch.empty(E, dtype=torch.int32, device=dev) if n_valid is None else n_valid
+    if dev_status is not None:
+        _need(dev_status, "dev_status", torch.int32, plan.G)
     ws = plan.workspace(_lib.MSLAM_OP_LINEARIZE) if workspace is None else workspace
     check(lib().mslam_gn_linearize_packed(C.byref(params), plan.handle, DTYPES[dtype], T_wc.data_ptr(),
                                           packed.data_ptr(), packed.numel(), H.data_ptr(), g.data_ptr(),
-                                          cost.data_ptr(), n_valid.data_ptr(), ws.data_ptr(), ws.numel(),
-                                          _lib.MSLAM_FLAG_PER_EDGE if per_edge else 0, _stream(dev)),
+                                          cost.data_ptr(), n_valid.data_ptr(), _ptr(dev_status), ws.data_ptr(),
+                                          ws.numel(), _lib.MSLAM_FLAG_PER_EDGE if per_edge else 0, _stream(dev)),
           "mslam_gn_linearize_packed")
     return H, g, cost, n_valid
 
@@ -409,7 +413,7 @@ class GaussNewton:
     def linearize(self):
         if self.packed:
             gn_linearize_packed(self.plan, self.params, self.X.dtype, self.T, self.pack_buf, self.H, self.g,
-                                self.cost, self.n_valid, self.ws_lin, self.per_edge)
+                                self.cost, self.n_valid, self.ws_lin, self.per_edge, self.status)
         else:
             gn_linearize(self.plan, self.params, self.T, self.X, self.idx, self.q, self.H, self.g, self.cost,
                          self.n_valid, self.ws_lin, self.per_edge)

@@ -83,6 +83,7 @@ struct PlanView {
   int64_t P;  // pixels of the edge pools
   int32_t lin_tile;           // pixels per linearisation tile
   int32_t match_bx, match_by; // match block shape (match_bx * match_by = 256)
+  uint32_t wait_polls;        // polls of a bounded device wait; 0 = give up at once, issuing no copy
   const DevEdge* edges;
   const DevTile* tiles;
   const DevGraph* graphs;

@@ -543,7 +543,6 @@ constexpr int kStreamStages = 3;
 constexpr int kStreamPairsPerThread = 4;
 constexpr int kStreamChunkRecs = 2 * kStreamThreads * kStreamPairsPerThread;  // 4096 records
 constexpr int kStreamChunkBytes = kStreamChunkRecs * 16;                     // 64 KB per stage
-constexpr uint32_t kSpinLimit = 1u << 24;  // bounded mbarrier waits (non-blocking polls, about a second)
 
 // Paired FP32 arithmetic (one instruction for two lanes of work).
 using f2 = float2;
@@ -574,11 +573,22 @@ __device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Waits for the phase of `parity` to complete; false after kSpinLimit polls.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (uint32_t it = 0; it < kSpinLimit; ++it)
+// Waits for the phase of `parity` to complete; false after `polls`
+// non-blocking polls (the plan's wait limit, about a second by default).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t polls) {
+  for (uint32_t it = 0; it < polls; ++it)
     if (mbar_test_wait(bar, parity)) return true;
   return false;
+}
+
+// A bounded wait gave up: every tile partial of the launch becomes NaN and
+// every graph the launch covers gets MSLAM_ERR_TIMEOUT (the solve skips it).
+__device__ void mark_timeout(const PlanView& pv, float* partials, int32_t* status, int tile_begin, int tile_end,
+                             int t0, int stride) {
+  for (int t = tile_begin + t0; t < tile_end; t += stride) {
+    partials[(size_t)t * kAccStride] = __int_as_float(0x7fc00000);
+    if (status) status[pv.edges[pv.tiles[t].edge].graph] = MSLAM_ERR_TIMEOUT;
+  }
 }
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile(
@@ -684,7 +694,7 @@ __device__ __forceinline__ float warp_reduce_scatter(float v[32], int lane) {
 __global__ void __launch_bounds__(kStreamThreads, 1)
     lin_stream_kernel(PlanView pv, LinConst lc, const RelPose* __restrict__ rel, const unsigned char* __restrict__ recs,
                       const int32_t* __restrict__ counts, float* __restrict__ partials, int tile_begin, int tile_end,
-                      int* __restrict__ tile_ctr) {
+                      int* __restrict__ tile_ctr, int32_t* __restrict__ status) {
   extern __shared__ __align__(128) unsigned char stage[];
   __shared__ __align__(8) uint64_t full[kStreamStages];
   __shared__ int m_tile[kStreamStages], m_np[kStreamStages], m_last[kStreamStages];
@@ -700,6 +710,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
     p_cnt = p_tile < tile_end ? __ldg(counts + p_tile) : 0;
   };
   auto issue = [&](int slot) {
+    if (pv.wait_polls == 0) return;  // wait limit "give up at once": no copy is issued
     if (p_tile >= tile_end) {  // end marker
       m_tile[slot] = -1;
       mbar_arrive(&full[slot]);
@@ -736,7 +747,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
   for (int k = 0;; ++k) {
     const int slot = k % kStreamStages;
     const uint32_t parity = (uint32_t)((k / kStreamStages) & 1);
-    const bool ok = mbar_wait_bounded(&full[slot], parity);
+    const bool ok = mbar_wait_bounded(&full[slot], parity, pv.wait_polls);
     if (__syncthreads_or(!ok)) {
       aborted = true;
       break;
@@ -797,13 +808,14 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
     }
   }
   if (aborted) {
-    // a copy did not complete in time: poison every tile's partial (the
-    // solve then reports a non-finite system) and let in-flight copies land
-    // before the CTA's shared memory is released
-    for (int t = tile_begin + tid; t < tile_end; t += kStreamThreads)
-      partials[(size_t)t * kAccStride] = __int_as_float(0x7fc00000);
+    // a copy did not complete in time: poison every tile's partial, report
+    // the timeout per graph, and let in-flight copies land before the CTA's
+    // shared memory is released (each stage's pending phase is waited for,
+    // again with the bound)
+    mark_timeout(pv, partials, status, tile_begin, tile_end, tid, kStreamThreads);
     if (tid == 0)
-      for (int sl = 0; sl < kStreamStages; ++sl) mbar_wait_bounded(&full[sl], 0), mbar_wait_bounded(&full[sl], 1);
+      for (int sl = 0; sl < kStreamStages; ++sl)
+        mbar_wait_bounded(&full[sl], 0, pv.wait_polls), mbar_wait_bounded(&full[sl], 1, pv.wait_polls);
     __syncthreads();
   }
 }
@@ -829,7 +841,8 @@ constexpr size_t kWarpStreamSmem = (size_t)kWarpStreamWarps * kWarpStages * kWar
 __global__ void __launch_bounds__(kWarpStreamThreads, 1)
     lin_warp_stream_kernel(PlanView pv, LinConst lc, const RelPose* __restrict__ rel,
                            const unsigned char* __restrict__ recs, const int32_t* __restrict__ counts,
-                           float* __restrict__ partials, int tile_begin, int tile_end, int* __restrict__ tile_ctr) {
+                           float* __restrict__ partials, int tile_begin, int tile_end, int* __restrict__ tile_ctr,
+                           int32_t* __restrict__ status) {
   extern __shared__ __align__(128) unsigned char wstage[];
   __shared__ __align__(8) uint64_t full[kWarpStreamWarps][kWarpStages];
   __shared__ int m_tile[kWarpStreamWarps][kWarpStages], m_n[kWarpStreamWarps][kWarpStages],
@@ -847,6 +860,7 @@ __global__ void __launch_bounds__(kWarpStreamThreads, 1)
     p_cnt = p_tile < tile_end ? __ldg(counts + p_tile) : 0;
   };
   auto issue = [&](int slot) {
+    if (pv.wait_polls == 0) return;  // wait limit "give up at once": no copy is issued
     if (p_tile >= tile_end) {  // end marker
       m_tile[warp][slot] = -1;
       mbar_arrive(&bars[slot]);
@@ -886,7 +900,7 @@ __global__ void __launch_bounds__(kWarpStreamThreads, 1)
   for (int k = 0;; ++k) {
     const int slot = k % kWarpStages;
     const uint32_t parity = (uint32_t)((k / kWarpStages) & 1);
-    const bool ok = mbar_wait_bounded(&bars[slot], parity);
+    const bool ok = mbar_wait_bounded(&bars[slot], parity, pv.wait_polls);
     if (__any_sync(0xffffffffu, !ok)) {
       aborted = true;
       break;
@@ -939,12 +953,13 @@ __global__ void __launch_bounds__(kWarpStreamThreads, 1)
     }
   }
   if (aborted) {
-    // a copy did not complete in time: poison every tile's partial (the
-    // solve then reports a non-finite system) and let this warp's copies in
-    // flight land before the block's shared memory is released
-    for (int t = tile_begin + lane; t < tile_end; t += 32) partials[(size_t)t * kAccStride] = __int_as_float(0x7fc00000);
+    // a copy did not complete in time: poison every tile's partial, report
+    // the timeout per graph, and let this warp's copies in flight land
+    // before the block's shared memory is released
+    mark_timeout(pv, partials, status, tile_begin, tile_end, lane, 32);
     if (lane == 0)
-      for (int sl = 0; sl < kWarpStages; ++sl) mbar_wait_bounded(&bars[sl], 0), mbar_wait_bounded(&bars[sl], 1);
+      for (int sl = 0; sl < kWarpStages; ++sl)
+        mbar_wait_bounded(&bars[sl], 0, pv.wait_polls), mbar_wait_bounded(&bars[sl], 1, pv.wait_polls);
     __syncwarp();
   }
 }
@@ -1436,7 +1451,8 @@ extern "C" mslam_status mslam_gn_pack(const mslam_params* p, const mslam_plan* p
 extern "C" mslam_status mslam_gn_linearize_packed(const mslam_params* p, const mslam_plan* plan, mslam_dtype dt,
                                                   const double* T_wc, const void* packed, size_t packed_bytes,
                                                   float* H_blocks, float* g_blocks, double* cost, int32_t* n_valid,
-                                                  void* workspace, size_t ws_bytes, uint32_t flags, void* stream) {
+                                                  int32_t* dev_status, void* workspace, size_t ws_bytes,
+                                                  uint32_t flags, void* stream) {
   if (!p || !check_plan_uploaded(plan)) {
     if (!p) set_error("params is NULL");
     return MSLAM_ERR_ARG;
@@ -1489,14 +1505,14 @@ extern "C" mslam_status mslam_gn_linearize_packed(const mslam_params* p, const m
       // the FP16 ray family streams its records through shared memory
       if (kK == MSLAM_RES_RAY && form == kFormBlockStream) {
         lin_stream_kernel<<<grid, kStreamThreads, stream_smem, s>>>(pv, lc, rel, rec_bytes, counts, partials, t0, t1,
-                                                                   c);
+                                                                   c, dev_status);
         return;
       }
       if (kK == MSLAM_RES_RAY && form == kFormWarpStream) {
         // a warp takes a whole tile: without the counter, one warp per tile
         const int g = c ? grid : (t1 - t0 + kWarpStreamWarps - 1) / kWarpStreamWarps;
         lin_warp_stream_kernel<<<g, kWarpStreamThreads, kWarpStreamSmem, s>>>(pv, lc, rel, rec_bytes, counts,
-                                                                             partials, t0, t1, c);
+                                                                             partials, t0, t1, c, dev_status);
         return;
       }
       if (dt == MSLAM_F32)

@@ -17,12 +17,22 @@ constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_lin_scratch[kNoAllocScratchBytes];
 
+// cuCtxGetCurrent, looked up once through the runtime (the library does not
+// link the driver library directly).
+typedef int (*CtxGetCurrentFn)(void**);
+
 std::mutex g_mutex;
 void* g_scratch_ptr[kMaxDevices] = {};
+void* g_scratch_ctx[kMaxDevices] = {};
+CtxGetCurrentFn g_ctx_get = nullptr;
+bool g_ctx_get_tried = false;
 
-// Device address of the scratch array on the current device, resolved once
-// per device with that device current (the host-side name of the array is
-// only a stand-in and must never be handed to a kernel).
+// Device address of the scratch array in the current device's current
+// context.  The host-side name of the array is only a stand-in and must never
+// be handed to a kernel.  The address is looked up (cudaGetSymbolAddress, with
+// the device current) the first time a context of a device calls, and looked
+// up again when the device's context has changed since (e.g. after
+// cudaDeviceReset), so a destroyed context's address is never reused.
 mslam_status scratch_address(void** out) {
   int dev = 0;
   mslam_status st = mslam::cuda_check(cudaGetDevice(&dev), "gn_linearize_noalloc: cudaGetDevice");
@@ -32,11 +42,27 @@ mslam_status scratch_address(void** out) {
     return MSLAM_ERR_RANGE;
   }
   std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch_ptr[dev]) {
+  if (!g_ctx_get_tried) {
+    g_ctx_get_tried = true;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_ctx_get = reinterpret_cast<CtxGetCurrentFn>(fn);
+    else
+      cudaGetLastError();  // clear: without the lookup every call resolves the address
+  }
+  // the current context (none yet if the runtime has not used this device)
+  void* ctx = nullptr;
+  const bool have_ctx = g_ctx_get && g_ctx_get(&ctx) == 0 && ctx;
+  if (!g_scratch_ptr[dev] || !have_ctx || g_scratch_ctx[dev] != ctx) {
     void* p = nullptr;
     st = mslam::cuda_check(cudaGetSymbolAddress(&p, g_lin_scratch), "gn_linearize_noalloc: cudaGetSymbolAddress");
     if (st != MSLAM_OK) return st;
+    // the lookup made the device's primary context current if it was not
+    void* ctx_now = nullptr;
     g_scratch_ptr[dev] = p;
+    g_scratch_ctx[dev] = (g_ctx_get && g_ctx_get(&ctx_now) == 0) ? ctx_now : nullptr;
   }
   *out = g_scratch_ptr[dev];
   return MSLAM_OK;

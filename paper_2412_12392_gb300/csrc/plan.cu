@@ -28,6 +28,7 @@ struct mslam_plan {
   int32_t max_m = 0;            // non-fixed poses of the largest graph
   int32_t max_levels = 0;
   int32_t lin_tile = 0, lin_blocks_per_sm = 0, match_bx = 0, match_by = 0, lin_form = 0, solve_form = 0;
+  int32_t wait_limit = 0;
   int32_t n_mblocks = 0;
   void* dev = nullptr;
   size_t dev_bytes = 0;
@@ -75,6 +76,7 @@ PlanView plan_view(const mslam_plan* plan) {
   v.lin_tile = plan->lin_tile;
   v.match_bx = plan->match_bx;
   v.match_by = plan->match_by;
+  v.wait_polls = plan->wait_limit < 0 ? 0u : plan->wait_limit == 0 ? (1u << 24) : (uint32_t)plan->wait_limit;
   v.edges = reinterpret_cast<const DevEdge*>(base + plan->off_edges);
   v.tiles = reinterpret_cast<const DevTile*>(base + plan->off_tiles);
   v.graphs = reinterpret_cast<const DevGraph*>(base + plan->off_graphs);
@@ -439,6 +441,7 @@ void mslam_default_plan_opts(mslam_plan_opts* o) {
   o->match_block_w = kMatchBX;
   o->lin_form = 0;
   o->solve_form = 0;
+  o->wait_limit = 0;
 }
 
 mslam_status mslam_plan_create(int32_t N, const int32_t* kf_hw, int32_t E, const int32_t* edges,
@@ -476,6 +479,7 @@ mslam_status mslam_plan_create_ex(int32_t N, const int32_t* kf_hw, int32_t E, co
   P->lin_blocks_per_sm = o.lin_blocks_per_sm;
   P->lin_form = o.lin_form;
   P->solve_form = o.solve_form;
+  P->wait_limit = o.wait_limit;
   P->match_bx = o.match_block_w;
   P->match_by = kMatchThreads / o.match_block_w;
   P->N = N;

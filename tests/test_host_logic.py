@@ -45,3 +45,33 @@ def test_pipelined_shape_check_needs_a_streamed_choice():
     assert bench.pick_pipelined_shapes(types.SimpleNamespace(tuning=None), 1) is None
     regs = types.SimpleNamespace(tuning={"opts": {"lin_form": 1}})
     assert bench.pick_pipelined_shapes(regs, 1) is None
+
+
+def test_bench_pose_errors_agree_with_the_oracle_algebra():
+    """The benchmark's pose-accuracy figures (quaternion algebra in numpy)
+    equal those of the test helper built on the oracle's Sim(3) product and
+    inverse, on random poses."""
+    import numpy as np
+
+    from parity import pose_errors as oracle_pose_errors
+    bench = _bench()
+    rng = np.random.default_rng(4)
+    A, B = [], []
+    for _ in range(16):
+        for L in (A, B):
+            q = rng.normal(size=4)
+            q /= np.linalg.norm(q)
+            L.append(np.concatenate([rng.normal(size=3), q, [rng.uniform(0.5, 2.0)]]))
+    A, B = np.array(A), np.array(B)
+    B[:4] = A[:4]  # identical poses give zero error
+    e1 = bench.pose_errors(A, B)
+    e2 = oracle_pose_errors(A, B)
+    assert np.allclose(e1, e2, rtol=1e-9, atol=1e-12)
+    assert np.all(e1[:4] <= 1e-12)
+
+
+def test_valid_query_pixels_counts_finite_nonzero_points():
+    bench = _bench()
+    X = torch.tensor([[0.0, 0.0, 0.0], [1.0, 2.0, 3.0], [float("nan"), 1.0, 1.0], [0.0, 0.0, -1e-3],
+                      [float("inf"), 0.0, 0.0]], dtype=torch.float16)
+    assert bench.valid_query_pixels(X) == 2

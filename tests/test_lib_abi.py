@@ -142,3 +142,18 @@ def test_workspace_sizes_of_each_op(L):
     L.mslam_default_params(C.byref(prm))
     st = L.mslam_gn_track(C.byref(prm), p.handle, 1, None, None, 0, 1, None, None, 0, None)
     assert st == _lib.MSLAM_ERR_ARG  # not uploaded (no GPU here)
+
+
+def test_plan_opts_struct_layout(L):
+    from paper_2412_12392_gb300 import _lib
+    o = _lib.PlanOpts()
+    L.mslam_default_plan_opts(C.byref(o))
+    assert C.sizeof(o) == 24 and _lib.PlanOpts.wait_limit.offset == 20
+    assert o.wait_limit == 0 and o.lin_form == 0 and o.solve_form == 0
+    # every wait limit is accepted: < 0 gives up at once (for the timeout tests), 0 is the default
+    for wl in (-1, 0, 1, 1 << 24):
+        p = plan([[16, 16]] * 2, [[0, 1]], None) if wl == 0 else None
+        import paper_2412_12392_gb300 as M
+        q = M.Plan([[16, 16]] * 2, [[0, 1]], device="cpu", opts={"wait_limit": wl})
+        assert q.opts["wait_limit"] == wl
+        del p, q

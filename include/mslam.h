@@ -376,6 +376,33 @@ mslam_status mslam_gn_backward(const mslam_params* p, const mslam_plan* plan, ms
                                float* dL_dq, int32_t* dev_status, void* workspace, size_t ws_bytes,
                                void* stream);
 
+/* Adjoint of one whole Gauss-Newton step T' = Exp(tau) o T with tau =
+ * -H(T)^-1 g(T) (Eq. gauss_newton, Eq. 1; project form, not in the paper),
+ * so that unrolled steps can be chained: the gradient of
+ *   L = dL_dcost * E_g(T) + dL_dtau . tau + <dL_dTnew, T'>
+ * with respect to X_canon, q and the poses T_wc.  Poses enter through every
+ * match's x = T_i^-1 T_j X_j[n], through the adjoint Ad_{T_i^-1} that maps
+ * each edge's relative system to its 14 x 14 block, and through the
+ * retraction (left Jacobian of Exp); matches and the q_min mask are held
+ * fixed, the Huber weights are differentiated.  Pose gradients are given
+ * and returned in the [N, 8] embedding (t, q, s): G with J8^T G = dL/deta
+ * for the left perturbation T -> Exp(eta) T (J8 = d(t, q, s)/d eta) and no
+ * component along the quaternion's norm direction.
+ * Arguments: as mslam_gn_backward, plus dL_dTnew [N, 8] FP64 (device, the
+ * gradient on the updated poses) or NULL, and the output dL_dT [N, 8] FP64
+ * (device, required).  H_blocks, g_blocks (the linearisation at T_wc) and
+ * dev_status are required.  tau is recomputed from H and g (FP64).  The
+ * gradient of the fixed (first) keyframe's pose is returned too: moving it
+ * moves every other pose's step.  Errors: MSLAM_ERR_ARG, MSLAM_ERR_CUDA; a
+ * singular system sets dev_status[g] = MSLAM_ERR_NOT_PD (the gradients of
+ * that graph are then not defined). */
+mslam_status mslam_gn_step_backward(const mslam_params* p, const mslam_plan* plan, mslam_dtype dt,
+                                    const double* T_wc, const void* X_canon, const int32_t* idx, const void* q,
+                                    const float* H_blocks, const float* g_blocks, const double* dL_dTnew,
+                                    const double* dL_dtau, double dL_dcost, float* dL_dX, float* dL_dq,
+                                    double* dL_dT, int32_t* dev_status, void* workspace, size_t ws_bytes,
+                                    void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Tracking, Sec. 3.3: the frame's Gauss-Newton loop in one launch per       */
 /* iteration.                                                                 */

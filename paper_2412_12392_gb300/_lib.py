@@ -96,6 +96,8 @@ SIGNATURES = {
     "mslam_fuse": ([C.c_int, vp, i32, i32, i64, vp, vp, vp, vp, vp], C.c_int),
     "mslam_gn_backward": ([vp, vp, C.c_int, vp, vp, vp, vp, vp, vp, vp, C.c_double, vp, vp, vp, vp, sz, vp],
                           C.c_int),
+    "mslam_gn_step_backward": ([vp, vp, C.c_int, vp, vp, vp, vp, vp, vp, vp, vp, C.c_double, vp, vp, vp, vp, vp,
+                                sz, vp], C.c_int),
 }
 
 

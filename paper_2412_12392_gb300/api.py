@@ -363,6 +363,39 @@ def gn_backward(plan: Plan, params: Params, T_wc, X_canon, idx, q, H=None, g=Non
     return dL_dX, dL_dq, dev_status
 
 
+def gn_step_backward(plan: Plan, params: Params, T_wc, X_canon, idx, q, H, g, dL_dTnew=None, dL_dtau=None,
+                     dL_dcost: float = 0.0, dL_dX=None, dL_dq=None, dL_dT=None, dev_status=None, workspace=None):
+    """mslam_gn_step_backward: gradient of dL_dcost * E_g(T) + dL_dtau . tau
+    + <dL_dTnew, T'> over one Gauss-Newton step T' = Exp(tau) o T with
+    respect to X_canon, q and T_wc (pose gradients in the [N, 8] embedding).
+    Returns (dL_dX float32 [Pk, 3], dL_dq float32 [P], dL_dT float64 [N, 8],
+    dev_status)."""
+    dt = X_canon.dtype
+    dev = X_canon.device
+    _need(T_wc, "T_wc", torch.float64, 8 * plan.N)
+    _need(X_canon, "X_canon", dt, 3 * plan.kf_pixels)
+    _need(idx, "idx", torch.int32, plan.edge_pixels)
+    _need(q, "q", dt, plan.edge_pixels)
+    _need(H, "H", torch.float32, 196 * plan.E)
+    _need(g, "g", torch.float32, 14 * plan.E)
+    if dL_dTnew is not None:
+        _need(dL_dTnew, "dL_dTnew", torch.float64, 8 * plan.N)
+    if dL_dtau is not None:
+        _need(dL_dtau, "dL_dtau", torch.float64, 7 * plan.N)
+    dL_dX = torch.empty(plan.kf_pixels, 3, dtype=torch.float32, device=dev) if dL_dX is None else dL_dX
+    dL_dq = torch.empty(plan.edge_pixels, dtype=torch.float32, device=dev) if dL_dq is None else dL_dq
+    dL_dT = torch.empty(plan.N, 8, dtype=torch.float64, device=dev) if dL_dT is None else dL_dT
+    if dev_status is None:
+        dev_status = torch.zeros(plan.G, dtype=torch.int32, device=dev)
+    ws = plan.workspace(_lib.MSLAM_OP_BACKWARD) if workspace is None else workspace
+    check(lib().mslam_gn_step_backward(C.byref(params), plan.handle, DTYPES[dt], T_wc.data_ptr(),
+                                       X_canon.data_ptr(), idx.data_ptr(), q.data_ptr(), H.data_ptr(), g.data_ptr(),
+                                       _ptr(dL_dTnew), _ptr(dL_dtau), float(dL_dcost), dL_dX.data_ptr(),
+                                       dL_dq.data_ptr(), dL_dT.data_ptr(), dev_status.data_ptr(), ws.data_ptr(),
+                                       ws.numel(), _stream(dev)), "mslam_gn_step_backward")
+    return dL_dX, dL_dq, dL_dT, dev_status
+
+
 def fuse(T_wc, k: int, f: int, X_canon_k, C_canon_k, X_kf, C_kf):
     """mslam_fuse (Sec. 3.3): update keyframe k's canonical pointmap and
     confidence in place with the prediction made together with frame f."""

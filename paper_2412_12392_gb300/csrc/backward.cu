@@ -14,6 +14,7 @@
 // Gathered-side contributions are scattered with atomicAdd, so the result is
 // reproducible only up to FP32 summation order.
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -155,12 +156,18 @@ __device__ __forceinline__ bool match_grad(V3 x, V3 y, float q, const BwdConst& 
   return true;
 }
 
-template <typename T>
+// kPose: also sum, per edge, the gradient with respect to a left
+// perturbation xi of T_ij (x -> Exp(xi) x, dx/dxi = [I, -[x]x, x]):
+// Xi_e = sum over the edge's matches of (g_x, x cross g_x, x . g_x), added
+// into xi_out [E, 7] (FP64).
+template <typename T, bool kPose>
 __global__ void __launch_bounds__(256) bwd_kernel(PlanView pv, BwdConst bc, const float* __restrict__ edge_data,
                                                   const T* __restrict__ X, const int32_t* __restrict__ idx,
                                                   const T* __restrict__ q, float* __restrict__ dX,
-                                                  float* __restrict__ dq) {
+                                                  float* __restrict__ dq, double* __restrict__ xi_out) {
+  __shared__ float s_xi[256 / 32][7];
   for (int tile = blockIdx.x; tile < pv.n_tiles; tile += gridDim.x) {
+    float xi[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const DevTile tl = pv.tiles[tile];
     const DevEdge ed = pv.edges[tl.edge];
     const float* eg = edge_data + (size_t)tl.edge * kBwdEdgeFloats;
@@ -197,8 +204,198 @@ __global__ void __launch_bounds__(256) bwd_kernel(PlanView pv, BwdConst bc, cons
       atomicAdd(dXi + 1, gy.y);
       atomicAdd(dXi + 2, gy.z);
       dq[ed.off_e + n] = gq;
+      if (kPose) {
+        const V3 xg = cross(x, gx);
+        xi[0] += gx.x;
+        xi[1] += gx.y;
+        xi[2] += gx.z;
+        xi[3] += xg.x;
+        xi[4] += xg.y;
+        xi[5] += xg.z;
+        xi[6] += dot(x, gx);
+      }
+    }
+    if (kPose) {
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        float v = xi[k];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) s_xi[warp][k] = v;
+      }
+      __syncthreads();
+      if (threadIdx.x < 7) {
+        double t = 0.0;
+        for (int w = 0; w < 256 / 32; ++w) t += (double)s_xi[w][threadIdx.x];
+        atomicAdd(xi_out + 7 * (size_t)tl.edge + threadIdx.x, t);
+      }
+      __syncthreads();
     }
   }
+}
+
+// ---------------------------------------------------------------- poses
+// Gradients with respect to the poses use the left perturbation
+// T -> Exp(eta) T of each pose; at the C ABI they are given in the [N, 8]
+// embedding (t, q, s) as the gradient G with J8^T G = dL/deta and no
+// component along q (the quaternion's norm direction), J8 = d(t, q, s)/d eta:
+//   dt = rho + phi x t + sigma t,  dq = (phi / 2, 0) (x) q,  ds = sigma s.
+// Hence dL/deta = (G_t, t x G_t + Q^T G_q, t . G_t + s G_s) with
+// Q = 1/2 [[q_w I - [q_v]x], [-q_v^T]], and back G = (g_rho,
+// 4 Q (g_phi - t x g_rho), (g_sigma - t . g_rho) / s) ([2Q, q] is orthogonal).
+__device__ void tangent_of_embedding(const Sim3d& T, const double* G, double g[7]) {
+  const double* t = T.t;
+  const double qx = T.q[0], qy = T.q[1], qz = T.q[2], qw = T.q[3];
+  const double Gt0 = G[0], Gt1 = G[1], Gt2 = G[2];
+  const double a = G[3], b = G[4], c = G[5], d = G[6];
+  // Q^T G_q = 1/2 [(q_w I + [q_v]x) G_qv - q_v G_qw]
+  const double qt0 = 0.5 * (qw * a + (qy * c - qz * b) - qx * d);
+  const double qt1 = 0.5 * (qw * b + (qz * a - qx * c) - qy * d);
+  const double qt2 = 0.5 * (qw * c + (qx * b - qy * a) - qz * d);
+  g[0] = Gt0;
+  g[1] = Gt1;
+  g[2] = Gt2;
+  g[3] = (t[1] * Gt2 - t[2] * Gt1) + qt0;
+  g[4] = (t[2] * Gt0 - t[0] * Gt2) + qt1;
+  g[5] = (t[0] * Gt1 - t[1] * Gt0) + qt2;
+  g[6] = (t[0] * Gt0 + t[1] * Gt1 + t[2] * Gt2) + T.s * G[7];
+}
+
+__device__ void embedding_of_tangent(const Sim3d& T, const double g[7], double* G) {
+  const double* t = T.t;
+  const double qx = T.q[0], qy = T.q[1], qz = T.q[2], qw = T.q[3];
+  // h = g_phi - t x g_rho
+  const double h0 = g[3] - (t[1] * g[2] - t[2] * g[1]);
+  const double h1 = g[4] - (t[2] * g[0] - t[0] * g[2]);
+  const double h2 = g[5] - (t[0] * g[1] - t[1] * g[0]);
+  // 4 Q h = 2 [(q_w I - [q_v]x) h; -q_v . h]
+  G[0] = g[0];
+  G[1] = g[1];
+  G[2] = g[2];
+  G[3] = 2.0 * (qw * h0 - (qy * h2 - qz * h1));
+  G[4] = 2.0 * (qw * h1 - (qz * h0 - qx * h2));
+  G[5] = 2.0 * (qw * h2 - (qx * h1 - qy * h0));
+  G[6] = -2.0 * (qx * h0 + qy * h1 + qz * h2);
+  G[7] = (g[6] - (t[0] * g[0] + t[1] * g[1] + t[2] * g[2])) / T.s;
+}
+
+// v^T ad(w) for the Lie bracket of sim(3), tau = (rho, phi, sigma):
+// ad(w) = [[ [w_phi]x + w_sigma I, [w_rho]x, -w_rho ], [0, [w_phi]x, 0], [0, 0, 0]],
+// so out = ad(w)^T v.
+__device__ void ad_transpose_times(const double* w, const double* v, double out[7]) {
+  const double r0 = w[0], r1 = w[1], r2 = w[2], p0 = w[3], p1 = w[4], p2 = w[5], sg = w[6];
+  const double a0 = v[0], a1 = v[1], a2 = v[2], b0 = v[3], b1 = v[4], b2 = v[5];
+  // ([w_phi]x)^T a = -w_phi x a = a x w_phi
+  out[0] = (a1 * p2 - a2 * p1) + sg * a0;
+  out[1] = (a2 * p0 - a0 * p2) + sg * a1;
+  out[2] = (a0 * p1 - a1 * p0) + sg * a2;
+  // ([w_rho]x)^T a + ([w_phi]x)^T b = a x w_rho + b x w_phi
+  out[3] = (a1 * r2 - a2 * r1) + (b1 * p2 - b2 * p1);
+  out[4] = (a2 * r0 - a0 * r2) + (b2 * p0 - b0 * p2);
+  out[5] = (a0 * r1 - a1 * r0) + (b0 * p1 - b1 * p0);
+  out[6] = -(r0 * a0 + r1 * a1 + r2 * a2);
+}
+
+// Per pose, before the solve for b: the updated pose T' = Exp(tau) T, its
+// gradient dL/deta' from the embedding gradient G' (or zero), the right-hand
+// side a = dL_dtau + J_l(tau)^T dL/deta' of the step term (J_l(tau) =
+// sum_k ad(tau)^k / (k+1)! the left Jacobian, Exp(tau + d) = Exp(J_l d)
+// Exp(tau)), and the direct part Ad_{Exp(tau)}^T dL/deta' of dL/deta
+// (T' = Exp(tau) Exp(eta) T = Exp(Ad_{Exp(tau)} eta) T'), which starts the
+// pose accumulator.
+__global__ void bwd_pose_in_kernel(int N, const double* __restrict__ T_wc, const double* __restrict__ tau,
+                                   const double* __restrict__ dL_dTnew, const double* __restrict__ dL_dtau,
+                                   double* __restrict__ a_out, double* __restrict__ acc) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  double tk[7], gn[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int c = 0; c < 7; ++c) tk[c] = tau[7 * k + c];
+  if (dL_dTnew) {
+    const Sim3d Tn = compose(sim3_exp(tk), load_pose(T_wc + 8 * k));
+    tangent_of_embedding(Tn, dL_dTnew + 8 * k, gn);
+  }
+  // J_l(tau)^T gn = sum_k w_k, w_0 = gn, w_k = ad(tau)^T w_{k-1} / (k + 1)
+  double a[7], w[7];
+  for (int c = 0; c < 7; ++c) a[c] = w[c] = gn[c];
+  for (int it = 1; it < 60; ++it) {
+    double nw[7], nrm = 0.0, tot = 0.0;
+    ad_transpose_times(tk, w, nw);
+    const double f = 1.0 / (double)(it + 1);
+    for (int c = 0; c < 7; ++c) {
+      w[c] = nw[c] * f;
+      a[c] += w[c];
+      nrm = fmax(nrm, fabs(w[c]));
+      tot = fmax(tot, fabs(a[c]));
+    }
+    if (nrm <= 1e-18 * tot || nrm == 0.0) break;
+  }
+  for (int c = 0; c < 7; ++c) a_out[7 * k + c] = a[c] + (dL_dtau ? dL_dtau[7 * k + c] : 0.0);
+  double Ad[49];
+  adjoint_of(sim3_exp(tk), Ad);
+  for (int c = 0; c < 7; ++c) {
+    double sum = 0.0;
+    for (int r = 0; r < 7; ++r) sum += Ad[7 * r + c] * gn[r];
+    acc[7 * k + c] = sum;
+  }
+}
+
+// Per edge e = (i, j), after the per-match sweep: x = T_ij X_j depends on
+// the poses through xi = Ad_{T_i^-1} (eta_j - eta_i), so dL/deta_j +=
+// Ad^T Xi_e and dL/deta_i -= Ad^T Xi_e.  The step term phi also depends on
+// T_i through Ad in beta = Ad (b_j - b_i) and theta = Ad (tau_j - tau_i)
+// (Ad_{T_i^-1} -> Ad (I - ad(eta_i))); with sum dphi/dbeta = H_rel theta +
+// g_rel, sum dphi/dtheta = H_rel beta and Ad^T H_rel Ad = H_jj, Ad^T g_rel =
+// g_j (the edge's 14 x 14 block and gradient): dphi/deta_i =
+// ad(db)^T (H_jj dtau + g_j) + ad(dtau)^T H_jj db, entering L with sign -1.
+__global__ void bwd_pose_edge_kernel(PlanView pv, const double* __restrict__ T_wc, const double* __restrict__ bvec,
+                                     const double* __restrict__ tvec, const float* __restrict__ H14,
+                                     const float* __restrict__ g14, const double* __restrict__ xi,
+                                     int with_step, double* __restrict__ acc) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= pv.E) return;
+  const DevEdge ed = pv.edges[e];
+  double Ad[49];
+  adjoint_of(inverse(load_pose(T_wc + 8 * ed.i)), Ad);
+  double cj[7];
+  for (int c = 0; c < 7; ++c) {
+    double sum = 0.0;
+    for (int r = 0; r < 7; ++r) sum += Ad[7 * r + c] * xi[7 * (size_t)e + r];
+    cj[c] = sum;
+  }
+  double ei[7] = {0, 0, 0, 0, 0, 0, 0};
+  if (with_step) {
+    double db[7], dt[7], v1[7], v2[7], o1[7], o2[7];
+    for (int c = 0; c < 7; ++c) {
+      db[c] = bvec[7 * ed.j + c] - bvec[7 * ed.i + c];
+      dt[c] = tvec[7 * ed.j + c] - tvec[7 * ed.i + c];
+    }
+    const float* Hb = H14 + 196 * (size_t)e;
+    for (int r = 0; r < 7; ++r) {
+      double s1 = (double)g14[14 * (size_t)e + 7 + r], s2 = 0.0;
+      for (int c = 0; c < 7; ++c) {
+        const double h = (double)Hb[14 * (7 + r) + 7 + c];
+        s1 += h * dt[c];
+        s2 += h * db[c];
+      }
+      v1[r] = s1;
+      v2[r] = s2;
+    }
+    ad_transpose_times(db, v1, o1);
+    ad_transpose_times(dt, v2, o2);
+    for (int c = 0; c < 7; ++c) ei[c] = o1[c] + o2[c];
+  }
+  for (int c = 0; c < 7; ++c) {
+    atomicAdd(acc + 7 * ed.j + c, cj[c]);
+    atomicAdd(acc + 7 * ed.i + c, -cj[c] - ei[c]);
+  }
+}
+
+// Per pose: the accumulated dL/deta in the [N, 8] embedding of T_wc.
+__global__ void bwd_pose_out_kernel(int N, const double* __restrict__ T_wc, const double* __restrict__ acc,
+                                    double* __restrict__ dL_dT) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  embedding_of_tangent(load_pose(T_wc + 8 * k), acc + 7 * k, dL_dT + 8 * k);
 }
 
 // b = H^-1 a for every graph using the factorisation (blocks and reciprocal
@@ -294,11 +491,14 @@ using namespace mslam;
 extern mslam_status mslam_factor_only(const mslam_plan* plan, const float* H_blocks, const float* g_blocks,
                                       double* tau, int32_t* dev_status, double* ws, cudaStream_t s);
 
-extern "C" mslam_status mslam_gn_backward(const mslam_params* p, const mslam_plan* plan, mslam_dtype dt,
-                                          const double* T_wc, const void* X_canon, const int32_t* idx,
-                                          const void* q, const float* H_blocks, const float* g_blocks,
-                                          const double* dL_dtau, double dL_dcost, float* dL_dX, float* dL_dq,
-                                          int32_t* dev_status, void* workspace, size_t ws_bytes, void* stream) {
+// Both adjoint entry points: the cost and step terms with respect to X and q
+// and, when dL_dT is given, the poses (with the retraction T' = Exp(tau) T
+// and an upstream gradient dL_dTnew on T').
+static mslam_status step_backward(const char* who, const mslam_params* p, const mslam_plan* plan, mslam_dtype dt,
+                                  const double* T_wc, const void* X_canon, const int32_t* idx, const void* q,
+                                  const float* H_blocks, const float* g_blocks, const double* dL_dTnew,
+                                  const double* dL_dtau, double dL_dcost, float* dL_dX, float* dL_dq, double* dL_dT,
+                                  int32_t* dev_status, void* workspace, size_t ws_bytes, void* stream) {
   if (!p || !check_plan_uploaded(plan)) {
     if (!p) set_error("params is NULL");
     return MSLAM_ERR_ARG;
@@ -308,19 +508,20 @@ extern "C" mslam_status mslam_gn_backward(const mslam_params* p, const mslam_pla
     return MSLAM_ERR_ARG;
   }
   if (p->residual != MSLAM_RES_RAY) {
-    set_error("gn_backward: the adjoint covers the ray-error cost only (residual = MSLAM_RES_RAY)");
+    set_error("%s: the adjoint covers the ray-error cost only (residual = MSLAM_RES_RAY)", who);
     return MSLAM_ERR_ARG;
   }
   if (!T_wc || !X_canon || !idx || !q || !dL_dX || !dL_dq || !workspace) {
-    set_error("gn_backward: NULL device pointer");
+    set_error("%s: NULL device pointer", who);
     return MSLAM_ERR_ARG;
   }
-  if (dL_dtau && (!H_blocks || !g_blocks || !dev_status)) {
-    set_error("gn_backward: the step term needs H_blocks, g_blocks and dev_status");
+  const bool with_step = dL_dtau || dL_dTnew;
+  if ((with_step || dL_dT) && (!H_blocks || !g_blocks || !dev_status)) {
+    set_error("%s: the step and pose terms need H_blocks, g_blocks and dev_status", who);
     return MSLAM_ERR_ARG;
   }
   if (ws_bytes < mslam_workspace_bytes(plan, MSLAM_OP_BACKWARD) || (reinterpret_cast<uintptr_t>(workspace) & 255)) {
-    set_error("gn_backward: workspace smaller than %zu bytes or not 256-byte aligned",
+    set_error("%s: workspace smaller than %zu bytes or not 256-byte aligned", who,
               mslam_workspace_bytes(plan, MSLAM_OP_BACKWARD));
     return MSLAM_ERR_ARG;
   }
@@ -331,15 +532,38 @@ extern "C" mslam_status mslam_gn_backward(const mslam_params* p, const mslam_pla
   if (st != MSLAM_OK) return st;
   st = cuda_check(cudaMemsetAsync(dL_dq, 0, sizeof(float) * mslam_plan_edge_pixels(plan), s), "gn_backward memset");
   if (st != MSLAM_OK) return st;
+  if (dL_dT) {
+    st = cuda_check(cudaMemsetAsync(dL_dT, 0, sizeof(double) * 8 * (size_t)pv.N, s), "gn_backward memset");
+    if (st != MSLAM_OK) return st;
+  }
   if (pv.E == 0) return MSLAM_OK;
+  // workspace: the solve's, b and tau [N, 7] each, per-edge data (32 floats
+  // per edge), then for the pose term a [N, 7], the pose accumulator [N, 7]
+  // and Xi [E, 7] (FP64)
   double* ws = static_cast<double*>(workspace);
   const size_t solve_doubles = mslam_workspace_bytes(plan, MSLAM_OP_SOLVE) / sizeof(double);
   double* stepvec = ws + solve_doubles;  // [N,7] b then [N,7] tau
-  if (dL_dtau) {
-    // factor H (and compute tau) without touching the poses, then b = H^-1 a
-    st = mslam_factor_only(plan, H_blocks, g_blocks, stepvec + 7 * (size_t)pv.N, dev_status, ws, s);
+  double* bvec = stepvec;
+  double* tvec = stepvec + 7 * (size_t)pv.N;
+  float* edge_data = reinterpret_cast<float*>(stepvec + 14 * (size_t)pv.N);
+  double* pose_ws = reinterpret_cast<double*>(reinterpret_cast<char*>(edge_data) +
+                                              ((sizeof(float) * 32 * (size_t)std::max(pv.E, 1) + 255) & ~size_t(255)));
+  double* a_tot = pose_ws;
+  double* acc = pose_ws + 7 * (size_t)pv.N;
+  double* xi = pose_ws + 14 * (size_t)pv.N;
+  if (with_step || dL_dT) {
+    // factor H (and compute tau) without touching the poses
+    st = mslam_factor_only(plan, H_blocks, g_blocks, tvec, dev_status, ws, s);
     if (st != MSLAM_OK) return st;
-    bwd_rhs_kernel<<<pv.G, kSolveThreads, 0, s>>>(pv, dL_dtau, stepvec, dev_status, ws);
+  }
+  if (dL_dT) {
+    st = cuda_check(cudaMemsetAsync(xi, 0, sizeof(double) * 7 * (size_t)pv.E, s), "gn_backward memset");
+    if (st != MSLAM_OK) return st;
+    bwd_pose_in_kernel<<<(pv.N + 63) / 64, 64, 0, s>>>(pv.N, T_wc, tvec, dL_dTnew, dL_dtau, a_tot, acc);
+  }
+  if (with_step) {
+    // b = H^-1 a with a = dL_dtau (+ the retraction's J_l^T dL/dT' with poses)
+    bwd_rhs_kernel<<<pv.G, kSolveThreads, 0, s>>>(pv, dL_dT ? a_tot : dL_dtau, bvec, dev_status, ws);
   }
   BwdConst bc;
   bc.inv_sr2 = 1.0f / (p->sigma_ray * p->sigma_ray);
@@ -347,19 +571,51 @@ extern "C" mslam_status mslam_gn_backward(const mslam_params* p, const mslam_pla
   bc.delta = p->huber_delta;
   bc.q_min = p->q_min;
   bc.c_cost = (float)dL_dcost;
-  bc.with_step = dL_dtau ? 1 : 0;
+  bc.with_step = with_step ? 1 : 0;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // per-edge data after the two pose vectors (b and tau)
-  float* edge_data = reinterpret_cast<float*>(stepvec + 14 * (size_t)pv.N);
-  bwd_edge_kernel<<<(pv.E + 63) / 64, 64, 0, s>>>(pv, T_wc, stepvec, dL_dtau ? 1 : 0, edge_data);
+  bwd_edge_kernel<<<(pv.E + 63) / 64, 64, 0, s>>>(pv, T_wc, stepvec, with_step ? 1 : 0, edge_data);
   const int grid = std::min(pv.n_tiles, std::max(1, sms) * 8);
-  if (dt == MSLAM_F32)
-    bwd_kernel<float><<<grid, 256, 0, s>>>(pv, bc, edge_data, static_cast<const float*>(X_canon), idx,
-                                           static_cast<const float*>(q), dL_dX, dL_dq);
-  else
-    bwd_kernel<__half><<<grid, 256, 0, s>>>(pv, bc, edge_data, static_cast<const __half*>(X_canon), idx,
-                                            static_cast<const __half*>(q), dL_dX, dL_dq);
+  auto sweep = [&](auto kpose) {
+    constexpr bool kP = decltype(kpose)::value;
+    if (dt == MSLAM_F32)
+      bwd_kernel<float, kP><<<grid, 256, 0, s>>>(pv, bc, edge_data, static_cast<const float*>(X_canon), idx,
+                                                 static_cast<const float*>(q), dL_dX, dL_dq, xi);
+    else
+      bwd_kernel<__half, kP><<<grid, 256, 0, s>>>(pv, bc, edge_data, static_cast<const __half*>(X_canon), idx,
+                                                  static_cast<const __half*>(q), dL_dX, dL_dq, xi);
+  };
+  if (dL_dT) {
+    sweep(std::true_type{});
+    bwd_pose_edge_kernel<<<(pv.E + 63) / 64, 64, 0, s>>>(pv, T_wc, bvec, tvec, H_blocks, g_blocks, xi,
+                                                         with_step ? 1 : 0, acc);
+    bwd_pose_out_kernel<<<(pv.N + 63) / 64, 64, 0, s>>>(pv.N, T_wc, acc, dL_dT);
+  } else {
+    sweep(std::false_type{});
+  }
   return cuda_check(cudaGetLastError(), "gn_backward launch");
+}
+
+extern "C" mslam_status mslam_gn_backward(const mslam_params* p, const mslam_plan* plan, mslam_dtype dt,
+                                          const double* T_wc, const void* X_canon, const int32_t* idx,
+                                          const void* q, const float* H_blocks, const float* g_blocks,
+                                          const double* dL_dtau, double dL_dcost, float* dL_dX, float* dL_dq,
+                                          int32_t* dev_status, void* workspace, size_t ws_bytes, void* stream) {
+  return step_backward("gn_backward", p, plan, dt, T_wc, X_canon, idx, q, H_blocks, g_blocks, nullptr, dL_dtau,
+                       dL_dcost, dL_dX, dL_dq, nullptr, dev_status, workspace, ws_bytes, stream);
+}
+
+extern "C" mslam_status mslam_gn_step_backward(const mslam_params* p, const mslam_plan* plan, mslam_dtype dt,
+                                               const double* T_wc, const void* X_canon, const int32_t* idx,
+                                               const void* q, const float* H_blocks, const float* g_blocks,
+                                               const double* dL_dTnew, const double* dL_dtau, double dL_dcost,
+                                               float* dL_dX, float* dL_dq, double* dL_dT, int32_t* dev_status,
+                                               void* workspace, size_t ws_bytes, void* stream) {
+  if (!dL_dT) {
+    set_error("gn_step_backward: dL_dT is NULL (use mslam_gn_backward without the pose term)");
+    return MSLAM_ERR_ARG;
+  }
+  return step_backward("gn_step_backward", p, plan, dt, T_wc, X_canon, idx, q, H_blocks, g_blocks, dL_dTnew,
+                       dL_dtau, dL_dcost, dL_dX, dL_dq, dL_dT, dev_status, workspace, ws_bytes, stream);
 }

@@ -625,9 +625,12 @@ size_t mslam_workspace_bytes(const mslam_plan* plan, int32_t op) {
     case MSLAM_OP_STATS:
       return align256(sizeof(uint32_t) * (size_t)((plan->e_off.back() + 31) / 32 + 1));
     case MSLAM_OP_BACKWARD:
-      // the solve's workspace, b and tau (7 N doubles each), per-edge data (32 floats per edge)
+      // the solve's workspace, b and tau (7 N doubles each), per-edge data
+      // (32 floats per edge), then for the pose term the step's right-hand
+      // side and the pose gradient (7 N doubles each) and Xi (7 E doubles)
       return mslam_workspace_bytes(plan, MSLAM_OP_SOLVE) + align256(sizeof(double) * 14 * (size_t)plan->N) +
-             align256(sizeof(float) * 32 * (size_t)std::max(plan->E, 1));
+             align256(sizeof(float) * 32 * (size_t)std::max(plan->E, 1)) +
+             align256(sizeof(double) * (14 * (size_t)plan->N + 7 * (size_t)std::max(plan->E, 1)));
     default:
       return 0;
   }

@@ -86,7 +86,7 @@ def test_autograd_function(M):
     qd = q.cuda().requires_grad_(True)
     idx = ws.gt_match.cuda()
     T = ws.T_init.cuda()
-    tau, cost = gn_step(X, qd, T, plan, P, idx)
+    T_new, tau, cost = gn_step(X, qd, T, plan, P, idx)
     at = torch.from_numpy(a).cuda()
     loss = (tau * at).sum() + 0.7 * cost
     loss.backward()

@@ -235,6 +235,18 @@ mslam_status mslam_match(const mslam_params* p, const mslam_plan* plan, mslam_dt
                          const void* Q_ref, const void* Q_qry, const int32_t* init_idx, int32_t* idx_out,
                          void* q_out, int32_t edge_begin, int32_t edge_end, uint32_t flags, void* stream);
 
+/* Descriptor layout for mslam_match: D [n_pix, d] row-major (the natural
+ * layout a network writes) -> the chunk-planar layout, c = 16 bytes of
+ * elements (8 halves or 4 floats): chunk k of source pixel p goes to element
+ * ((k * dst_pix_stride + p) * c) of dst, so dst_pix_stride = n_pix gives
+ * [d / c, n_pix, c], and dst_pix_stride = P with dst pointing at pixel p0 of
+ * a [d / c, P, c] pool fills pixels [p0, p0 + n_pix) of it.  A copy, no
+ * arithmetic.  src and dst are device buffers of dtype dt (16-byte aligned,
+ * not overlapping), d in {16, 24, 32}, dst_pix_stride >= n_pix.
+ * Errors: MSLAM_ERR_ARG, MSLAM_ERR_CUDA. */
+mslam_status mslam_desc_to_chunked(mslam_dtype dt, int32_t d, int64_t n_pix, const void* src, void* dst,
+                                   int64_t dst_pix_stride, void* stream);
+
 /* Keyframe criterion of Sec. 3.4 (next stage after matching): per edge, the
  * number of valid matches (idx >= 0) and the number of distinct reference
  * (keyframe) pixels they hit; tracking adds a keyframe when either, as a
@@ -245,6 +257,17 @@ mslam_status mslam_match(const mslam_params* p, const mslam_plan* plan, mslam_dt
  * cleared by the call).  Errors: MSLAM_ERR_ARG, MSLAM_ERR_CUDA. */
 mslam_status mslam_match_stats(const mslam_plan* plan, const int32_t* idx, int32_t* n_valid, int32_t* n_unique,
                                void* workspace, size_t ws_bytes, void* stream);
+
+/* The keyframe criterion of Sec. 3.4 on those counts (host function, no
+ * GPU work: the decision steers the caller's host-side control flow): edge e
+ * needs a new keyframe when n_valid[e] / n_query[e] < omega_k or
+ * n_unique[e] / n_query[e] < omega_k (both in FP64; an edge with no query
+ * pixels always needs one).  omega_k is 0.333 in the paper's evaluation
+ * setup (Supp. S4).  All arrays are HOST memory of E entries; needed[e] is
+ * set to 1 or 0.  Errors: MSLAM_ERR_ARG (NULL array with E > 0, E < 0, or
+ * omega_k not in [0, 1]). */
+mslam_status mslam_keyframe_criterion(int32_t E, const int32_t* n_valid, const int32_t* n_unique,
+                                      const int64_t* n_query, double omega_k, int32_t* needed);
 
 /* ------------------------------------------------------------------------ */
 /* (a4-a5) Linearisation of the ray-error cost, Eq. backend_ray, Supp. S1.   */

@@ -89,6 +89,8 @@ SIGNATURES = {
     "mslam_gn_track": ([vp, vp, C.c_int, vp, vp, sz, i32, vp, vp, sz, vp], C.c_int),
     "mslam_gn_solve": ([vp, vp, vp, vp, vp, vp, vp, vp, sz, vp], C.c_int),
     "mslam_match_stats": ([vp, vp, vp, vp, vp, sz, vp], C.c_int),
+    "mslam_keyframe_criterion": ([i32, vp, vp, vp, C.c_double, vp], C.c_int),
+    "mslam_desc_to_chunked": ([C.c_int, i32, i64, vp, vp, i64, vp], C.c_int),
     "mslam_ray_image": ([C.c_int, C.c_int64, vp, vp, vp], C.c_int),
     "mslam_calib_backproject": ([C.c_int, i32, i32, i32, C.c_float, C.c_float, C.c_float, C.c_float, vp, vp],
                                 C.c_int),

@@ -129,14 +129,29 @@ class Plan:
             pass
 
 
-def chunk_descriptors(D: torch.Tensor) -> torch.Tensor:
+def chunk_descriptors(D: torch.Tensor, out: Optional[torch.Tensor] = None, p0: int = 0) -> torch.Tensor:
     """[P, d] descriptors -> the chunk-planar [d / c, P, c] layout of
-    mslam_match (c = 16 bytes of elements).  A layout change only."""
+    mslam_match (c = 16 bytes of elements): mslam_desc_to_chunked on CUDA
+    tensors (the same permutation with torch on CPU tensors).  With `out` a
+    larger chunk-planar pool [d / c, P_out, c], D fills its pixels
+    [p0, p0 + P).  A layout change only."""
     c = 16 // D.element_size()
     P, d = D.shape
     if d % c:
         raise ValueError(f"descriptor dimension {d} is not a multiple of {c}")
-    return D.reshape(P, d // c, c).permute(1, 0, 2).contiguous()
+    if not D.is_cuda:
+        return D.reshape(P, d // c, c).permute(1, 0, 2).contiguous()
+    if D.dtype not in DTYPES:
+        raise ValueError(f"unsupported descriptor dtype {D.dtype}")
+    _need(D, "D", D.dtype, P * d)
+    out = torch.empty(d // c, P, c, dtype=D.dtype, device=D.device) if out is None else out
+    _need(out, "out", D.dtype)
+    if out.dim() != 3 or out.shape[0] != d // c or out.shape[2] != c or not 0 <= p0 <= out.shape[1] - P:
+        raise ValueError(f"out must be chunk-planar [{d // c}, >= {p0 + P}, {c}] (got {tuple(out.shape)})")
+    dst = out.data_ptr() + p0 * 16
+    check(lib().mslam_desc_to_chunked(DTYPES[D.dtype], d, P, D.data_ptr(), dst, out.shape[1], _stream(D.device)),
+          "mslam_desc_to_chunked")
+    return out
 
 
 def match(plan: Plan, params: Params, X_ref, X_qry, D_ref, D_qry, Q_ref, Q_qry, init_idx=None, idx_out=None,
@@ -186,15 +201,20 @@ OMEGA_K = 0.333  # keyframe threshold omega_k of the paper's evaluation setup (S
 
 
 def keyframe_needed(n_valid, n_unique, n_query, omega_k: float = OMEGA_K):
-    """The keyframe criterion of Sec. 3.4 from mslam_match_stats' counts: a new
-    keyframe is needed when the fraction of the frame's query pixels with a
-    valid match, or the fraction of distinct keyframe pixels they hit, falls
-    below omega_k.  n_valid, n_unique: per-edge counts (tensors or arrays);
-    n_query: query pixels per edge.  Host arithmetic on the counts only."""
-    nv = torch.as_tensor(n_valid).double()
-    nu = torch.as_tensor(n_unique).double()
-    nq = torch.as_tensor(n_query, dtype=torch.float64).clamp_min(1.0)
-    return (nv / nq < omega_k) | (nu / nq < omega_k)
+    """The keyframe criterion of Sec. 3.4 from mslam_match_stats' counts
+    (mslam_keyframe_criterion, host C): True where the fraction of the
+    frame's query pixels with a valid match, or of distinct keyframe pixels
+    they hit, falls below omega_k.  n_valid, n_unique: per-edge counts
+    (tensors or arrays, any device); n_query: query pixels per edge (scalar
+    or per edge).  Returns a bool tensor on the host."""
+    nv = np.ascontiguousarray(torch.as_tensor(n_valid).cpu().numpy().astype(np.int32).reshape(-1))
+    nu = np.ascontiguousarray(torch.as_tensor(n_unique).cpu().numpy().astype(np.int32).reshape(-1))
+    nq = np.ascontiguousarray(np.broadcast_to(np.asarray(torch.as_tensor(n_query).cpu().numpy(), dtype=np.int64),
+                                              nv.shape))
+    out = np.zeros(nv.shape, dtype=np.int32)
+    check(lib().mslam_keyframe_criterion(int(nv.size), nv.ctypes.data, nu.ctypes.data, nq.ctypes.data,
+                                         float(omega_k), out.ctypes.data), "mslam_keyframe_criterion")
+    return torch.from_numpy(out.astype(bool))
 
 
 def ray_image(X: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:

@@ -416,3 +416,60 @@ extern "C" mslam_status mslam_match_stats(const mslam_plan* plan, const int32_t*
   stats_count_kernel<<<pv.E, 256, 0, s>>>(pv, static_cast<const uint32_t*>(workspace), n_unique);
   return cuda_check(cudaGetLastError(), "match_stats launch");
 }
+
+extern "C" mslam_status mslam_keyframe_criterion(int32_t E, const int32_t* n_valid, const int32_t* n_unique,
+                                                 const int64_t* n_query, double omega_k, int32_t* needed) {
+  if (E < 0 || (E > 0 && (!n_valid || !n_unique || !n_query || !needed)) || !(omega_k >= 0.0 && omega_k <= 1.0)) {
+    set_error("keyframe_criterion: E = %d, omega_k = %g (in [0, 1]) or a NULL host array", E, omega_k);
+    return MSLAM_ERR_ARG;
+  }
+  for (int32_t e = 0; e < E; ++e) {
+    const int64_t nq = n_query[e];
+    if (nq <= 0) {
+      needed[e] = 1;
+      continue;
+    }
+    const double fv = (double)n_valid[e] / (double)nq, fu = (double)n_unique[e] / (double)nq;
+    needed[e] = (fv < omega_k || fu < omega_k) ? 1 : 0;
+  }
+  return MSLAM_OK;
+}
+
+namespace mslam {
+// One thread per (pixel, chunk): a 16-byte piece moves from [p][k] to [k][p];
+// consecutive threads take consecutive pixels of one chunk, so the stores are
+// coalesced and the loads read each pixel's descriptor once overall.
+__global__ void __launch_bounds__(256) desc_chunk_kernel(const uint4* __restrict__ src, uint4* __restrict__ dst,
+                                                         int64_t n_pix, int nc, int64_t stride) {
+  const int64_t total = n_pix * nc;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = i / n_pix, p = i - k * n_pix;
+    dst[k * stride + p] = __ldg(src + p * nc + k);
+  }
+}
+}  // namespace mslam
+
+extern "C" mslam_status mslam_desc_to_chunked(mslam_dtype dt, int32_t d, int64_t n_pix, const void* src, void* dst,
+                                              int64_t dst_pix_stride, void* stream) {
+  if ((dt != MSLAM_F32 && dt != MSLAM_F16) || (d != 16 && d != 24 && d != 32) || n_pix < 0 ||
+      dst_pix_stride < n_pix) {
+    set_error("desc_to_chunked: dtype %d, d %d (16, 24 or 32), n_pix %lld, stride %lld", (int)dt, d,
+              (long long)n_pix, (long long)dst_pix_stride);
+    return MSLAM_ERR_ARG;
+  }
+  if (n_pix == 0) return MSLAM_OK;
+  if (!src || !dst || (reinterpret_cast<uintptr_t>(src) & 15) || (reinterpret_cast<uintptr_t>(dst) & 15)) {
+    set_error("desc_to_chunked: NULL or not 16-byte aligned buffer");
+    return MSLAM_ERR_ARG;
+  }
+  const int nc = d * (dt == MSLAM_F32 ? 4 : 2) / 16;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t want = (n_pix * nc + 255) / 256;
+  const int grid = (int)std::min<int64_t>(want, (int64_t)std::max(1, sms) * 16);
+  desc_chunk_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<const uint4*>(src),
+                                                                         static_cast<uint4*>(dst), n_pix, nc,
+                                                                         dst_pix_stride);
+  return cuda_check(cudaGetLastError(), "desc_to_chunked launch");
+}

@@ -244,3 +244,20 @@ def test_gn_track_several_frames(M):
                          torch.zeros(plan_g.edge_pixels, device="cuda"), packed=True)
     with pytest.raises(_lib.MslamError):
         gn_g.run_tracking(g.T_init.cuda(), 2)
+
+
+@pytest.mark.parametrize("dtype,d", [(torch.float16, 24), (torch.float32, 16), (torch.float16, 32)])
+def test_desc_to_chunked_is_the_permutation(M, dtype, d):
+    """mslam_desc_to_chunked (whole pool and a slice of a larger pool) equals
+    the [P, d] -> [d / c, P, c] permutation bit for bit."""
+    g = torch.Generator(device="cpu").manual_seed(3)
+    P = 5003
+    D = torch.randn(P, d, generator=g).to(dtype)
+    c = 16 // D.element_size()
+    ref = D.reshape(P, d // c, c).permute(1, 0, 2).contiguous()
+    got = M.chunk_descriptors(D.cuda())
+    assert torch.equal(got.cpu(), ref)
+    pool = torch.zeros(d // c, P + 300, c, dtype=dtype, device="cuda")
+    M.chunk_descriptors(D[1000:2000].cuda(), out=pool, p0=150)
+    assert torch.equal(pool[:, 150:1150].cpu(), ref[:, 1000:2000])
+    assert not pool[:, :150].any() and not pool[:, 1150:].any()

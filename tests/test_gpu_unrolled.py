@@ -30,7 +30,6 @@ def oracle_loss(w, X, q, T0, steps, Wt, a, c, par):
     """L of `steps` oracle Gauss-Newton steps from T0 (numpy FP64)."""
     T = np.array(T0, dtype=np.float64)
     edges = w.edges.numpy()
-    idx = w_idx = None
     L = 0.0
     for k in range(steps):
         Hs, gs, cost = [], [], 0.0
@@ -71,7 +70,7 @@ def setup(w, dtype, seed):
     return ws, rng, Wt, a
 
 
-def check_against_fd(M, w, dtype, steps, n_x=12, n_q=8, poses=(1, 2), seed=0, tol=2e-4):
+def check_against_fd(M, w, dtype, steps, n_x=12, n_q=8, poses=(1, 2), seed=0, tol=2e-4, tol_pose=2e-4):
     ws, rng, Wt, a = setup(w, dtype, seed)
     P = M.default_params()
     par = M.params_dict(P)
@@ -129,7 +128,7 @@ def check_against_fd(M, w, dtype, steps, n_x=12, n_q=8, poses=(1, 2), seed=0, to
         g, f = np.array(g), np.array(f)
         err = np.abs(g - f).max() / max(np.abs(f).max(), 1e-300)
         print(f"{w.name} {dtype} steps={steps} d{name}: max |gpu - fd| / max |fd| = {err:.2e} over {len(f)}")
-        assert err <= tol, (name, g, f)
+        assert err <= (tol_pose if name == "T" else tol), (name, g, f)
 
 
 def test_one_step_with_poses(M):
@@ -146,6 +145,9 @@ def test_three_unrolled_steps_differentiation_graph(M):
 
 def test_three_unrolled_steps_fp16(M):
     """FP16-stored pointmaps and confidences (FP32 math): gradients with
-    respect to the stored values against the oracle on the dequantised ones."""
+    respect to the stored values against the oracle on the dequantised ones.
+    autograd returns a tensor's gradient in the tensor's dtype, so the point
+    and confidence gradients come back rounded to FP16 (relative 2^-11 per
+    entry, summed over the three steps): the bar for them is 1e-3."""
     w = synth.differentiation(H=24, W=32)
-    check_against_fd(M, w, torch.float16, 3, n_x=8, n_q=4, poses=(5,), seed=1)
+    check_against_fd(M, w, torch.float16, 3, n_x=8, n_q=4, poses=(5,), seed=1, tol=1e-3, tol_pose=2e-4)

@@ -159,6 +159,11 @@ typedef struct {
   int32_t solve_form;  /* 0 = FP32 factorisation of the diagonally scaled system with FP64 iterative
                           refinement to the FP64 solution (default; graphs it declines go to the FP64
                           factorisation), 1 = FP64 factorisation only */
+  int32_t match_form;  /* refinement windows of mslam_match: 0 = each query thread scores its own window
+                          on the FP32 pipe (default), 1 = the queries of a warp that share window rows are
+                          grouped and their windows scored together on the tensor cores (FP16 storage and
+                          win_radius 3 only; other cases use form 0).  Same decisions up to the FP32
+                          summation order of the scores. */
   int32_t wait_limit;  /* polls of every bounded device wait on an asynchronous copy (the streamed
                           linearisation forms) before it gives up: 0 = the default 2^24 (about a
                           second), > 0 = that many; < 0 = give up at once without issuing any copy (so

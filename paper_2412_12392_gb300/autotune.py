@@ -1,5 +1,6 @@
 """Autotuner for the plan's launch shapes: the linearisation tile size and
-form, blocks per SM and the match block shape (pixels per block row).
+form, blocks per SM, the match block shape (pixels per block row) and the
+match window form (per-query FP32 or grouped tensor-core scoring).
 
 Each candidate is timed on the caller's device-resident inputs with CUDA
 events -- the match block shape on mslam_match, the linearisation tile size
@@ -45,16 +46,18 @@ def autotune(kf_hw, edges, graph_of_kf, params, X_ref, X_qry, D_ref, D_qry, Q_re
     report = {"match_ms": {}, "lin_ms": {}, "pack_ms": {}}
     best_w, best_t = None, float("inf")
     idx = q = None
-    for wdt in match_widths:
-        plan = api.Plan(kf_hw, edges, graph_of_kf, opts={"match_block_w": wdt})
+    # the tensor-core window form exists for FP16 storage
+    forms = (0, 1) if X_ref.dtype == torch.float16 else (0,)
+    for wdt, form in itertools.product(match_widths, forms):
+        plan = api.Plan(kf_hw, edges, graph_of_kf, opts={"match_block_w": wdt, "match_form": form})
 
         def run_match():
             return api.match(plan, params, X_ref, X_qry, D_ref, D_qry, Q_ref, Q_qry)
 
         ms = _time(run_match, reps)
-        report["match_ms"][wdt] = ms
+        report["match_ms"][f"{wdt}/{form}"] = ms
         if ms < best_t:
-            best_w, best_t = wdt, ms
+            best_w, best_t = (wdt, form), ms
     idx, q = api.match(api.Plan(kf_hw, edges, graph_of_kf), params, X_ref, X_qry, D_ref, D_qry, Q_ref, Q_qry)
     best_lin, best_lt = None, float("inf")
     shapes = [(tile, bps, 1) for tile, bps in itertools.product(lin_tiles, lin_blocks)]
@@ -80,6 +83,6 @@ def autotune(kf_hw, edges, graph_of_kf, params, X_ref, X_qry, D_ref, D_qry, Q_re
         score = gn_iters * ms + pms
         if score < best_lt:
             best_lin, best_lt = (tile, bps, form), score
-    report["opts"] = {"match_block_w": best_w, "lin_tile": best_lin[0], "lin_blocks_per_sm": best_lin[1],
-                      "lin_form": best_lin[2]}
+    report["opts"] = {"match_block_w": best_w[0], "match_form": best_w[1], "lin_tile": best_lin[0],
+                      "lin_blocks_per_sm": best_lin[1], "lin_form": best_lin[2]}
     return report

@@ -13,6 +13,7 @@
 //   a3  rounding, coarse-to-fine descriptor window argmax (FP32 dot products
 //       in index order), the 3D distance test and q = sqrt(Q_ref Q_qry).
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -98,6 +99,46 @@ template <int D> struct Desc<__half, D> {
   }
 };
 
+// a2: lm_iters Levenberg-Marquardt steps of the ray error |R(p) - tg|^2
+// (Eq. 2) from p = (pu, pv_), R bilinear in the unit rays of the cell
+// (clamp(floor u, 0, W-2), clamp(floor v, 0, H-2)), p clamped to the image
+// after each step.
+template <typename T>
+__device__ __forceinline__ void lm_iterate(const T* __restrict__ Xr_e, int W, int H, float3 tg, const MatchConst& mc,
+                                           float& pu, float& pv_) {
+  const float lam = mc.lm_lambda;
+  for (int it = 0; it < mc.lm_iters; ++it) {
+    const int u0 = min(max((int)floorf(pu), 0), W - 2);
+    const int v0 = min(max((int)floorf(pv_), 0), H - 2);
+    const float a = pu - (float)u0, b = pv_ - (float)v0;
+    const int64_t t00 = (int64_t)v0 * W + u0;
+    const float3 R00 = ray_at(Xr_e, t00), R10 = ray_at(Xr_e, t00 + 1);
+    const float3 R01 = ray_at(Xr_e, t00 + W), R11 = ray_at(Xr_e, t00 + W + 1);
+    const float ua = 1.0f - a, ub = 1.0f - b;
+    const float3 Ju = make_float3(ub * (R10.x - R00.x) + b * (R11.x - R01.x), ub * (R10.y - R00.y) + b * (R11.y - R01.y),
+                                  ub * (R10.z - R00.z) + b * (R11.z - R01.z));
+    const float3 Jv = make_float3(ua * (R01.x - R00.x) + a * (R11.x - R10.x), ua * (R01.y - R00.y) + a * (R11.y - R10.y),
+                                  ua * (R01.z - R00.z) + a * (R11.z - R10.z));
+    const float w00 = ua * ub, w10 = a * ub, w01 = ua * b, w11 = a * b;
+    const float rx = w00 * R00.x + w10 * R10.x + w01 * R01.x + w11 * R11.x - tg.x;
+    const float ry = w00 * R00.y + w10 * R10.y + w01 * R01.y + w11 * R11.y - tg.y;
+    const float rz = w00 * R00.z + w10 * R10.z + w01 * R01.z + w11 * R11.z - tg.z;
+    const float a00 = Ju.x * Ju.x + Ju.y * Ju.y + Ju.z * Ju.z + lam;
+    const float a01 = Ju.x * Jv.x + Ju.y * Jv.y + Ju.z * Jv.z;
+    const float a11 = Jv.x * Jv.x + Jv.y * Jv.y + Jv.z * Jv.z + lam;
+    const float b0 = -(Ju.x * rx + Ju.y * ry + Ju.z * rz);
+    const float b1 = -(Jv.x * rx + Jv.y * ry + Jv.z * rz);
+    const float det = a00 * a11 - a01 * a01;
+    if (det > 0.0f) {
+      pu += (a11 * b0 - a01 * b1) / det;
+      pv_ += (a00 * b1 - a01 * b0) / det;
+    }
+    // clamp (fmaxf/fminf also map a NaN to the image)
+    pu = fminf(fmaxf(pu, 0.0f), (float)(W - 1));
+    pv_ = fminf(fmaxf(pv_, 0.0f), (float)(H - 1));
+  }
+}
+
 // kR > 0: the window radius as a compile-time constant (the default 3), so
 // that each window row is unrolled with branch-free bounds (an out-of-image
 // candidate reads a clamped pixel and scores -inf, which never wins, exactly
@@ -142,37 +183,7 @@ __global__ void __launch_bounds__(kMatchThreads) match_kernel(
     if (ii >= 0 && ii < HW) p0 = ii;
   }
   float pu = (float)(p0 % W), pv_ = (float)(p0 / W);
-  const float lam = mc.lm_lambda;
-  for (int it = 0; it < mc.lm_iters; ++it) {
-    const int u0 = min(max((int)floorf(pu), 0), W - 2);
-    const int v0 = min(max((int)floorf(pv_), 0), H - 2);
-    const float a = pu - (float)u0, b = pv_ - (float)v0;
-    const int64_t t00 = (int64_t)v0 * W + u0;
-    const float3 R00 = ray_at(Xr_e, t00), R10 = ray_at(Xr_e, t00 + 1);
-    const float3 R01 = ray_at(Xr_e, t00 + W), R11 = ray_at(Xr_e, t00 + W + 1);
-    const float ua = 1.0f - a, ub = 1.0f - b;
-    const float3 Ju = make_float3(ub * (R10.x - R00.x) + b * (R11.x - R01.x), ub * (R10.y - R00.y) + b * (R11.y - R01.y),
-                                  ub * (R10.z - R00.z) + b * (R11.z - R01.z));
-    const float3 Jv = make_float3(ua * (R01.x - R00.x) + a * (R11.x - R10.x), ua * (R01.y - R00.y) + a * (R11.y - R10.y),
-                                  ua * (R01.z - R00.z) + a * (R11.z - R10.z));
-    const float w00 = ua * ub, w10 = a * ub, w01 = ua * b, w11 = a * b;
-    const float rx = w00 * R00.x + w10 * R10.x + w01 * R01.x + w11 * R11.x - tg.x;
-    const float ry = w00 * R00.y + w10 * R10.y + w01 * R01.y + w11 * R11.y - tg.y;
-    const float rz = w00 * R00.z + w10 * R10.z + w01 * R01.z + w11 * R11.z - tg.z;
-    const float a00 = Ju.x * Ju.x + Ju.y * Ju.y + Ju.z * Ju.z + lam;
-    const float a01 = Ju.x * Jv.x + Ju.y * Jv.y + Ju.z * Jv.z;
-    const float a11 = Jv.x * Jv.x + Jv.y * Jv.y + Jv.z * Jv.z + lam;
-    const float b0 = -(Ju.x * rx + Ju.y * ry + Ju.z * rz);
-    const float b1 = -(Jv.x * rx + Jv.y * ry + Jv.z * rz);
-    const float det = a00 * a11 - a01 * a01;
-    if (det > 0.0f) {
-      pu += (a11 * b0 - a01 * b1) / det;
-      pv_ += (a00 * b1 - a01 * b0) / det;
-    }
-    // clamp (fmaxf/fminf also map a NaN to the image)
-    pu = fminf(fmaxf(pu, 0.0f), (float)(W - 1));
-    pv_ = fminf(fmaxf(pv_, 0.0f), (float)(H - 1));
-  }
+  lm_iterate(Xr_e, W, H, tg, mc, pu, pv_);
   int cu = min((int)floorf(pu + 0.5f), W - 1), cv = min((int)floorf(pv_ + 0.5f), H - 1);
   // coarse-to-fine refinement: maximum descriptor similarity in a window
   typename Desc<T, D>::Q dq[Desc<T, D>::NQ];
@@ -230,10 +241,207 @@ __global__ void __launch_bounds__(kMatchThreads) match_kernel(
   stf(out_q + o + n, ok ? sqrtf(ldf(Qr + o + m) * ldf(Qq + o + n)) : 0.0f);
 }
 
+// ----------------------------------------------- tensor-core window form
+// The refinement windows scored on the tensor cores (plan option
+// match_form 1; FP16 storage, window radius 3).  After the LM iterations
+// every query of a warp holds its window centre (cu, cv).  Per level, the
+// warp's queries are grouped by (cv, cu mod dil, cu div 8 dil): the members
+// of a group share their window rows, their centres lie on one dilation
+// grid, and (cu - min cu) / dil <= 7, so the seven window columns of every
+// member fall in one run of 16 candidates base + dil a, a = 0..15, base =
+// min cu - 3 dil.  For up to 8 members and each window row the warp computes
+// the 16 x 8 score tile S[a][n] = <D_ref[candidate a], D_qry[member n]> with
+// mma.sync m16n8k16 (+ m16n8k8 for the third 8-channel chunk at d = 24):
+// FP16 products, exact in FP32, summed in FP32.  Each lane then keeps, for
+// its two members, the best score of the candidates that lie in that
+// member's window (|a - o_n| <= 3 with o_n = (cu_n - base) / dil) and inside
+// the image, and the lanes holding a member are combined by the largest
+// score with ties to the smaller row-major window index: the first maximum
+// in (dy, dx) order, as in the per-query form.  Every window row of a group
+// is read once for its up to 8 members (one 4-byte piece per lane and
+// chunk) instead of once per member, and the dot products leave the FP32
+// pipe.
+__device__ __forceinline__ void mma_16816(float c[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                          uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void mma_1688(float c[4], uint32_t a0, uint32_t a1, uint32_t b0) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5}, {%6}, {%0, %1, %2, %3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(b0));
+}
+
+// One level of the grouped window scan for the calling warp (all 32 lanes).
+// valid: this lane's query takes part; (cu, cv) its centre, updated in
+// place; pix its pool pixel.  D32 = descriptors as 32-bit words of the
+// chunk-planar layout: word ((k P + p) 4 + e / 2) holds elements e, e + 1 of
+// chunk k of pixel p.
+template <int D>
+__device__ __forceinline__ void tc_window_level(const uint32_t* __restrict__ Dr32, const uint32_t* __restrict__ Dq32,
+                                                int64_t P, int64_t o, int W, int H, int dil, bool valid, int64_t pix,
+                                                int& cu, int& cv) {
+  constexpr int NC = D / 8;  // 8-element chunks
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int key = valid ? cv * 65536 + (cu % dil) * 1024 + cu / (8 * dil) : -1;
+  unsigned pending = __ballot_sync(FULL, valid);
+  int ncu = cu, ncv = cv;
+  while (pending) {
+    const int leader = __ffs(pending) - 1;
+    const int lkey = __shfl_sync(FULL, key, leader);
+    unsigned take = __ballot_sync(FULL, ((pending >> lane) & 1u) && key == lkey);
+    // the first 8 members (lowest lanes); the rest wait for a later group
+    if (__popc(take) > 8) take &= (1u << (__fns(take, 0, 9))) - 1u;
+    pending &= ~take;
+    const int k = __popc(take);
+    // B operand: member g's descriptor (element pairs 2t, 2t + 1 of each chunk)
+    const int mb = __fns(take, 0, (g < k ? g : 0) + 1);
+    const int64_t pb = __shfl_sync(FULL, pix, mb);
+    uint32_t b[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) b[c] = __ldg(Dq32 + ((int64_t)c * P + pb) * 4 + t);
+    const int gcv = __shfl_sync(FULL, cv, leader);
+    const int base = __reduce_min_sync(FULL, ((take >> lane) & 1u) ? cu : 0x7fffffff) - 3 * dil;
+    // this lane's score columns: members 2t and 2t + 1
+    const bool has0 = 2 * t < k, has1 = 2 * t + 1 < k;
+    const int m0 = __fns(take, 0, (has0 ? 2 * t : 0) + 1), m1 = __fns(take, 0, (has1 ? 2 * t + 1 : 0) + 1);
+    const int cu0 = __shfl_sync(FULL, cu, m0), cu1 = __shfl_sync(FULL, cu, m1);
+    const int o0 = (cu0 - base) / dil, o1 = (cu1 - base) / dil;
+    // this lane's candidate rows a = g and g + 8
+    const int colA = base + dil * g, colB = base + dil * (g + 8);
+    const bool okA = (unsigned)colA < (unsigned)W, okB = (unsigned)colB < (unsigned)W;
+    const int dA0 = g - o0, dB0 = g + 8 - o0, dA1 = g - o1, dB1 = g + 8 - o1;
+    const bool inA0 = has0 && okA && dA0 >= -3 && dA0 <= 3, inB0 = has0 && okB && dB0 >= -3 && dB0 <= 3;
+    const bool inA1 = has1 && okA && dA1 >= -3 && dA1 <= 3, inB1 = has1 && okB && dB1 >= -3 && dB1 <= 3;
+    const int cA = min(max(colA, 0), W - 1), cB = min(max(colB, 0), W - 1);
+    float best0 = -INFINITY, best1 = -INFINITY;
+    int code0 = 0x7fffffff, code1 = 0x7fffffff;  // row-major window index (dy + 3) 7 + dx + 3
+#pragma unroll 1
+    for (int dy = -3; dy <= 3; ++dy) {
+      const int vv = gcv + dy * dil;
+      if ((unsigned)vv >= (unsigned)H) continue;  // the same for the whole group
+      const int64_t rowp = o + (int64_t)vv * W;
+      const uint32_t* pA = Dr32 + (rowp + cA) * 4 + t;
+      const uint32_t* pB = Dr32 + (rowp + cB) * 4 + t;
+      const int64_t cs = P * 4;  // words between chunks
+      float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      mma_16816(c, __ldg(pA), __ldg(pB), __ldg(pA + cs), __ldg(pB + cs), b[0], b[1]);
+      if (NC == 3) mma_1688(c, __ldg(pA + 2 * cs), __ldg(pB + 2 * cs), b[NC - 1]);
+      if (NC == 4) mma_16816(c, __ldg(pA + 2 * cs), __ldg(pB + 2 * cs), __ldg(pA + 3 * cs), __ldg(pB + 3 * cs), b[2],
+                             b[NC - 1]);
+      // c0 = (a = g, member 2t), c1 = (g, 2t + 1), c2 = (g + 8, 2t), c3 = (g + 8, 2t + 1);
+      // at most one of a = g, g + 8 lies in a member's 7-wide window
+      const int row = (dy + 3) * 7 + 3;
+      if (inA0 && c[0] > best0) { best0 = c[0]; code0 = row + dA0; }
+      if (inB0 && c[2] > best0) { best0 = c[2]; code0 = row + dB0; }
+      if (inA1 && c[1] > best1) { best1 = c[1]; code1 = row + dA1; }
+      if (inB1 && c[3] > best1) { best1 = c[3]; code1 = row + dB1; }
+    }
+    // combine the 8 lanes (g = 0..7) of each member column
+#pragma unroll
+    for (int off = 4; off < 32; off <<= 1) {
+      const float ob0 = __shfl_xor_sync(FULL, best0, off), ob1 = __shfl_xor_sync(FULL, best1, off);
+      const int oc0 = __shfl_xor_sync(FULL, code0, off), oc1 = __shfl_xor_sync(FULL, code1, off);
+      if (ob0 > best0 || (ob0 == best0 && oc0 < code0)) { best0 = ob0; code0 = oc0; }
+      if (ob1 > best1 || (ob1 == best1 && oc1 < code1)) { best1 = ob1; code1 = oc1; }
+    }
+    // member n (the n-th lane of the group) reads its result from lane n / 2
+    const int n_me = __popc(take & ((1u << lane) - 1u));
+    const int src = (n_me >> 1) & 3;
+    const int r0 = __shfl_sync(FULL, code0, src), r1 = __shfl_sync(FULL, code1, src);
+    if ((take >> lane) & 1u) {
+      const int code = (n_me & 1) ? r1 : r0;
+      ncu = cu + dil * (code % 7 - 3);
+      ncv = cv + dil * (code / 7 - 3);
+    }
+  }
+  cu = ncu;
+  cv = ncv;
+}
+
+// The matching kernel with the tensor-core window (FP16 storage, radius 3):
+// the per-query part (a1, a2, the rounding, the 3D test and q) is that of
+// match_kernel; every lane of a warp reaches the window levels, which are
+// warp-collective.
+template <int D>
+__global__ void __launch_bounds__(kMatchThreads) match_tc_kernel(
+    PlanView pv, MatchConst mc, const __half* __restrict__ Xr, const __half* __restrict__ Xq,
+    const __half* __restrict__ Dr, const __half* __restrict__ Dq, const __half* __restrict__ Qr,
+    const __half* __restrict__ Qq, const int32_t* __restrict__ init, int32_t* __restrict__ out_idx,
+    __half* __restrict__ out_q, int e_begin, int e_end, int block_base) {
+  const int gb = block_base + blockIdx.x;
+  int lo = e_begin, hi = e_end - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pv.edges[mid].mblock_begin <= gb) lo = mid;
+    else hi = mid - 1;
+  }
+  const DevEdge ed = pv.edges[lo];
+  const int W = ed.W, H = ed.H;
+  const int local = gb - ed.mblock_begin;
+  const int bx = pv.match_bx, by = pv.match_by;
+  const int nbx = (W + bx - 1) / bx;
+  const int u = (local % nbx) * bx + (threadIdx.x % bx);
+  const int v = (local / nbx) * by + (threadIdx.x / bx);
+  const bool inside = u < W && v < H;
+  const int64_t HW = (int64_t)H * W;
+  const int n = inside ? v * W + u : 0;
+  const int64_t o = ed.off_e;
+  const __half* Xr_e = Xr + 3 * o;
+  const float3 x = ld3(Xq + 3 * o, n);
+  const float nx2 = fmaf(x.x, x.x, fmaf(x.y, x.y, x.z * x.z));
+  const bool valid = inside && finite3(x) && nx2 > 0.0f;
+  int cu = 0, cv = 0;
+  if (valid) {
+    const float inx = rsqrtf(nx2);
+    const float3 tg = make_float3(x.x * inx, x.y * inx, x.z * inx);
+    int p0 = n;
+    if (init) {
+      const int32_t ii = init[o + n];
+      if (ii >= 0 && ii < HW) p0 = ii;
+    }
+    float pu = (float)(p0 % W), pv_ = (float)(p0 / W);
+    lm_iterate(Xr_e, W, H, tg, mc, pu, pv_);
+    cu = min((int)floorf(pu + 0.5f), W - 1);
+    cv = min((int)floorf(pv_ + 0.5f), H - 1);
+  }
+  const uint32_t* Dr32 = reinterpret_cast<const uint32_t*>(Dr);
+  const uint32_t* Dq32 = reinterpret_cast<const uint32_t*>(Dq);
+  for (int lev = 0; lev < mc.n_levels; ++lev)
+    tc_window_level<D>(Dr32, Dq32, pv.P, o, W, H, mc.dil[lev], valid, o + n, cu, cv);
+  if (!inside) return;
+  if (!valid) {
+    out_idx[o + n] = -1;
+    stf(out_q + o + n, 0.0f);
+    return;
+  }
+  const int m = cv * W + cu;
+  const float3 y = ld3(Xr_e, m);
+  const float dxv = y.x - x.x, dyv = y.y - x.y, dzv = y.z - x.z;
+  const float dist = sqrtf(dxv * dxv + dyv * dyv + dzv * dzv);
+  const bool ok = finite3(y) && dist <= mc.max_rel * sqrtf(nx2);
+  out_idx[o + n] = ok ? m : -1;
+  stf(out_q + o + n, ok ? sqrtf(ldf(Qr + o + m) * ldf(Qq + o + n)) : 0.0f);
+}
+
 template <typename T, int D>
 static void launch_match(const PlanView& pv, const MatchConst& mc, const void* Xr, const void* Xq, const void* Dr,
                          const void* Dq, const void* Qr, const void* Qq, const int32_t* init, int32_t* out_idx,
-                         void* out_q, int e0, int e1, int b0, int nblocks, cudaStream_t s) {
+                         void* out_q, int e0, int e1, int b0, int nblocks, bool tc, cudaStream_t s) {
+  if constexpr (std::is_same<T, __half>::value) {
+    if (tc && mc.radius == 3) {
+      match_tc_kernel<D><<<nblocks, kMatchThreads, 0, s>>>(
+          pv, mc, static_cast<const __half*>(Xr), static_cast<const __half*>(Xq), static_cast<const __half*>(Dr),
+          static_cast<const __half*>(Dq), static_cast<const __half*>(Qr), static_cast<const __half*>(Qq), init, out_idx,
+          static_cast<__half*>(out_q), e0, e1, b0);
+      return;
+    }
+  }
   auto k = mc.radius == 3 ? match_kernel<T, D, 3> : match_kernel<T, D, 0>;
   k<<<nblocks, kMatchThreads, 0, s>>>(pv, mc, static_cast<const T*>(Xr), static_cast<const T*>(Xq),
                                      static_cast<const T*>(Dr), static_cast<const T*>(Dq),
@@ -303,6 +511,7 @@ extern "C" mslam_status mslam_match(const mslam_params* p, const mslam_plan* pla
   mc.n_levels = p->n_levels;
   for (int l = 0; l < 4; ++l) mc.dil[l] = p->win_dilation[l];
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool tc = plan_match_form(plan) == 1;
   auto go = [&](int a, int b) {
     int b0, b1x, bt0, bt1;
     plan_edge_mblocks(plan, a, &b0, &bt0);
@@ -312,7 +521,7 @@ extern "C" mslam_status mslam_match(const mslam_params* p, const mslam_plan* pla
     const int nb = b1x - b0;
 #define MSLAM_MATCH_CASE(TT, DD)                                                                              \
   launch_match<TT, DD>(pv, mc, X_ref, X_qry, D_ref, D_qry, Q_ref, Q_qry, init_idx, idx_out, q_out, a, b, b0, nb, \
-                       s)
+                       tc, s)
     if (dt == MSLAM_F32) {
       if (d == 16) MSLAM_MATCH_CASE(float, 16);
       else if (d == 24) MSLAM_MATCH_CASE(float, 24);

@@ -28,7 +28,7 @@ struct mslam_plan {
   int32_t max_m = 0;            // non-fixed poses of the largest graph
   int32_t max_levels = 0;
   int32_t lin_tile = 0, lin_blocks_per_sm = 0, match_bx = 0, match_by = 0, lin_form = 0, solve_form = 0;
-  int32_t wait_limit = 0;
+  int32_t wait_limit = 0, match_form = 0;
   int32_t n_mblocks = 0;
   void* dev = nullptr;
   size_t dev_bytes = 0;
@@ -111,6 +111,7 @@ int64_t plan_solve_ws_doubles(const mslam_plan* plan) { return plan->solve_ws_do
 int plan_lin_blocks_per_sm(const mslam_plan* plan) { return plan->lin_blocks_per_sm; }
 int plan_lin_form(const mslam_plan* plan) { return plan->lin_form; }
 int plan_solve_form(const mslam_plan* plan) { return plan->solve_form; }
+int plan_match_form(const mslam_plan* plan) { return plan->match_form; }
 int plan_max_image_dim(const mslam_plan* plan) {
   int m = 0;
   for (int v : plan->kf_hw) m = std::max(m, v);
@@ -442,6 +443,7 @@ void mslam_default_plan_opts(mslam_plan_opts* o) {
   o->lin_form = 0;
   o->solve_form = 0;
   o->wait_limit = 0;
+  o->match_form = 0;
 }
 
 mslam_status mslam_plan_create(int32_t N, const int32_t* kf_hw, int32_t E, const int32_t* edges,
@@ -458,10 +460,12 @@ mslam_status mslam_plan_create_ex(int32_t N, const int32_t* kf_hw, int32_t E, co
       o.lin_blocks_per_sm > 32 ||
       (o.match_block_w != 4 && o.match_block_w != 8 && o.match_block_w != 16 && o.match_block_w != 32 &&
        o.match_block_w != 64 && o.match_block_w != 128 && o.match_block_w != 256) ||
-      o.lin_form < 0 || o.lin_form > 2 || (o.solve_form != 0 && o.solve_form != 1)) {
+      o.lin_form < 0 || o.lin_form > 2 || (o.solve_form != 0 && o.solve_form != 1) ||
+      (o.match_form != 0 && o.match_form != 1)) {
     set_error("plan options: lin_tile %d (multiple of %d in [1024, 65536]), lin_blocks_per_sm %d (0..32), "
-              "match_block_w %d (4, 8, ..., 256), lin_form %d (0, 1 or 2), solve_form %d (0 or 1)", o.lin_tile,
-              kLinThreads, o.lin_blocks_per_sm, o.match_block_w, o.lin_form, o.solve_form);
+              "match_block_w %d (4, 8, ..., 256), lin_form %d (0, 1 or 2), solve_form %d (0 or 1), match_form %d "
+              "(0 or 1)", o.lin_tile, kLinThreads, o.lin_blocks_per_sm, o.match_block_w, o.lin_form, o.solve_form,
+              o.match_form);
     if (out) *out = nullptr;
     return MSLAM_ERR_ARG;
   }
@@ -480,6 +484,7 @@ mslam_status mslam_plan_create_ex(int32_t N, const int32_t* kf_hw, int32_t E, co
   P->lin_form = o.lin_form;
   P->solve_form = o.solve_form;
   P->wait_limit = o.wait_limit;
+  P->match_form = o.match_form;
   P->match_bx = o.match_block_w;
   P->match_by = kMatchThreads / o.match_block_w;
   P->N = N;

@@ -68,11 +68,12 @@ def global_wl():
     return synth.global_graph(device="cuda").to_storage(torch.float16)
 
 
-def test_global_full_size_sampled(M, global_wl):
+@pytest.mark.parametrize("match_form", [0, 1])
+def test_global_full_size_sampled(M, global_wl, match_form):
     w = global_wl
     P = M.default_params()
     par = M.params_dict(P)
-    plan = M.Plan(w.kf_hw.numpy(), w.edges.numpy())
+    plan = M.Plan(w.kf_hw.numpy(), w.edges.numpy(), opts={"match_form": match_form, "match_block_w": 16})
     Dr, Dq = M.chunk_descriptors(w.D_ref), M.chunk_descriptors(w.D_qry)
     idx_g, q_g = M.match(plan, P, w.X_ref, w.X_qry, Dr, Dq, w.Q_ref, w.Q_qry)  # batched launch
     torch.cuda.synchronize()

@@ -260,6 +260,7 @@ class Arm:
         self.plan = M.Plan(w.kf_hw.numpy(), w.edges.numpy(), w.graph_of_kf.numpy(), opts=opts)
         self.idx = torch.empty(self.plan.edge_pixels, dtype=torch.int32, device=dev)
         self.q = torch.empty(self.plan.edge_pixels, dtype=dtype, device=dev)
+        self.ws_match = self.plan.workspace(M._lib.MSLAM_OP_MATCH)
         # the batched form gathers the used matches once per step and streams
         # them in every iteration; the plain form gathers in every iteration
         self.gn = M.GaussNewton(self.plan, self.P, self.wd.X_canon, self.idx, self.q, per_edge=self.per_edge,
@@ -268,7 +269,7 @@ class Arm:
     def match(self):
         wd = self.wd
         self.M.match(self.plan, self.P, wd.X_ref, wd.X_qry, self.Dr, self.Dq, wd.Q_ref, wd.Q_qry,
-                     idx_out=self.idx, q_out=self.q, per_edge=self.per_edge)
+                     idx_out=self.idx, q_out=self.q, per_edge=self.per_edge, workspace=self.ws_match)
 
     def step(self, ev=None):
         """One pass of the hot path; ev = optional list collecting
@@ -351,14 +352,14 @@ class Arm:
         cur.wait_stream(sg)
 
     def launches_per_step(self) -> int:
-        """Kernels of this library launched per step: match; (batched) pack;
+        """Kernels of this library launched per step: the ray image and match; (batched) pack;
         per iteration the relative-pose, tile and finalize kernels of the
         linearisation (per edge in the plain form) and the solve."""
         E = self.plan.E
         sl = self.plan.solve_launches
         if self.per_edge:
-            return E + self.iters * (1 + 2 * E + sl)
-        return 1 + 1 + self.iters * (3 + sl)
+            return 2 * E + self.iters * (1 + 2 * E + sl)
+        return 2 + 1 + self.iters * (3 + sl)
 
 
 def pick_pipelined_shapes(arm, world, steps: int = 5, warmup: int = 3):
@@ -655,7 +656,7 @@ def e2e_measure(args, M, w, dtype, world, rank, local, opts=None, n_chunks: int 
             for k in ("D_ref", "D_qry"):
                 M.chunk_descriptors(src[k][p0:p1], out=dch[k], p0=p0)
             M.match(arm.plan, arm.P, src["X_ref"], src["X_qry"], dch["D_ref"], dch["D_qry"], src["Q_ref"],
-                    src["Q_qry"], idx_out=arm.idx, q_out=arm.q, edge_range=(e0, e1))
+                    src["Q_qry"], idx_out=arm.idx, q_out=arm.q, edge_range=(e0, e1), workspace=arm.ws_match)
         compute.wait_event(xev)
         arm.gn.X.copy_(src["X_canon"], non_blocking=True)
         arm.gn.pack()

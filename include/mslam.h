@@ -69,6 +69,7 @@ typedef enum { MSLAM_F32 = 0, MSLAM_F16 = 1 } mslam_dtype;
 #define MSLAM_OP_PACK_F16 5 /* packed-match buffer of mslam_gn_pack, FP16 storage */
 #define MSLAM_OP_STATS 6    /* reference-pixel bitmap of mslam_match_stats */
 #define MSLAM_OP_TRACK 7    /* tile partials and per-edge counters of mslam_gn_track */
+#define MSLAM_OP_MATCH 8    /* reference ray image of mslam_match (16 bytes per edge-pool pixel) */
 
 /* Constants of the method.  The paper names these quantities without values
  * where marked "reading"; defaults are set by mslam_default_params. */
@@ -232,13 +233,20 @@ mslam_status mslam_ray_image(mslam_dtype dt, int64_t n_pix, const void* X, void*
  * memory); d in {16, 24, 32}, 16-byte aligned; Q_ref, Q_qry [P]; init_idx [P]
  * int32 or NULL; outputs idx_out [P] int32 (m within the reference image,
  * -1 = invalid) and q_out [P] (dt; 0 where invalid).
+ * workspace: NULL, or >= mslam_workspace_bytes(plan, MSLAM_OP_MATCH) bytes,
+ * 256-byte aligned: the call then first writes the unit rays psi(X_ref) of
+ * the edges' reference pixels there (a1 as an image of float4, FP32, the same
+ * arithmetic as at the taps) and the LM taps read them instead of
+ * normalising four points per iteration; the result is identical.
  * flags: MSLAM_FLAG_PER_EDGE = one launch per edge, else one launch.
- * Errors: MSLAM_ERR_ARG for a null or misaligned pointer, unsupported d or
- * bad parameters; MSLAM_ERR_CUDA if a launch fails. */
+ * Errors: MSLAM_ERR_ARG for a null or misaligned pointer, unsupported d,
+ * bad parameters or a workspace that is too small; MSLAM_ERR_CUDA if a
+ * launch fails. */
 mslam_status mslam_match(const mslam_params* p, const mslam_plan* plan, mslam_dtype dt, int32_t d,
                          const void* X_ref, const void* X_qry, const void* D_ref, const void* D_qry,
                          const void* Q_ref, const void* Q_qry, const int32_t* init_idx, int32_t* idx_out,
-                         void* q_out, int32_t edge_begin, int32_t edge_end, uint32_t flags, void* stream);
+                         void* q_out, int32_t edge_begin, int32_t edge_end, void* workspace, size_t ws_bytes,
+                         uint32_t flags, void* stream);
 
 /* Descriptor layout for mslam_match: D [n_pix, d] row-major (the natural
  * layout a network writes) -> the chunk-planar layout, c = 16 bytes of

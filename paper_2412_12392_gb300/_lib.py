@@ -27,6 +27,7 @@ MSLAM_OP_PACK_F32 = 4
 MSLAM_OP_PACK_F16 = 5
 MSLAM_OP_STATS = 6
 MSLAM_OP_TRACK = 7
+MSLAM_OP_MATCH = 8
 MSLAM_RES_RAY, MSLAM_RES_POINT, MSLAM_RES_PIXEL = 0, 1, 2
 
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_NOT_PD", 4: "ERR_TIMEOUT", 5: "ERR_NONFINITE",
@@ -82,7 +83,8 @@ SIGNATURES = {
     "mslam_plan_offsets": ([vp, vp, vp], None),
     "mslam_plan_stats": ([vp, vp, vp], None),
     "mslam_workspace_bytes": ([vp, i32], sz),
-    "mslam_match": ([vp, vp, C.c_int, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, i32, u32, vp], C.c_int),
+    "mslam_match": ([vp, vp, C.c_int, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, i32, vp, sz, u32, vp],
+                    C.c_int),
     "mslam_gn_linearize": ([vp, vp, C.c_int, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, u32, vp], C.c_int),
     "mslam_gn_linearize_noalloc": ([vp, vp, C.c_int, vp, vp, vp, vp, vp, vp, vp, vp, u32, vp], C.c_int),
     "mslam_gn_pack": ([vp, vp, C.c_int, vp, vp, vp, vp, sz, vp], C.c_int),

@@ -155,9 +155,11 @@ def chunk_descriptors(D: torch.Tensor, out: Optional[torch.Tensor] = None, p0: i
 
 
 def match(plan: Plan, params: Params, X_ref, X_qry, D_ref, D_qry, Q_ref, Q_qry, init_idx=None, idx_out=None,
-          q_out=None, edge_range: Tuple[int, int] = (-1, -1), per_edge: bool = False):
+          q_out=None, edge_range: Tuple[int, int] = (-1, -1), per_edge: bool = False, workspace=None):
     """mslam_match (Sec. 3.2): returns (idx int32 [P], q [P]).  D_ref and
-    D_qry are chunk-planar [d / c, P, c] (see chunk_descriptors)."""
+    D_qry are chunk-planar [d / c, P, c] (see chunk_descriptors).
+    workspace: the ray-image workspace (MSLAM_OP_MATCH; allocated when None),
+    or False to normalise the rays at the taps instead (same result)."""
     dt = X_ref.dtype
     if dt not in DTYPES:
         raise ValueError(f"unsupported storage dtype {dt}")
@@ -177,10 +179,13 @@ def match(plan: Plan, params: Params, X_ref, X_qry, D_ref, D_qry, Q_ref, Q_qry, 
         q_out = torch.empty(P, dtype=dt, device=X_ref.device)
     _need(idx_out, "idx_out", torch.int32, P)
     _need(q_out, "q_out", dt, P)
+    if workspace is None:
+        workspace = plan.workspace(_lib.MSLAM_OP_MATCH)
+    ws_ptr, ws_n = (None, 0) if workspace is False else (workspace.data_ptr(), workspace.numel())
     check(lib().mslam_match(C.byref(params), plan.handle, DTYPES[dt], d, X_ref.data_ptr(), X_qry.data_ptr(),
                             D_ref.data_ptr(), D_qry.data_ptr(), Q_ref.data_ptr(), Q_qry.data_ptr(),
                             _ptr(init_idx), idx_out.data_ptr(), q_out.data_ptr(), int(edge_range[0]),
-                            int(edge_range[1]), _lib.MSLAM_FLAG_PER_EDGE if per_edge else 0,
+                            int(edge_range[1]), ws_ptr, ws_n, _lib.MSLAM_FLAG_PER_EDGE if per_edge else 0,
                             _stream(X_ref.device)), "mslam_match")
     return idx_out, q_out
 

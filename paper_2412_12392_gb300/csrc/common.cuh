@@ -385,6 +385,7 @@ int plan_lin_blocks_per_sm(const mslam_plan* plan);
 int plan_lin_form(const mslam_plan* plan);  // 0 block-streamed, 1 register pipeline, 2 warp-streamed
 int plan_solve_form(const mslam_plan* plan);  // 0 mixed precision, 1 FP64 only
 int plan_match_form(const mslam_plan* plan);  // 0 per-query window, 1 tensor-core grouped window
+int64_t plan_edge_off(const mslam_plan* plan, int e);  // edge-pool offset of edge e (e = E: the pool size)
 int64_t plan_max_mixed_bytes(const mslam_plan* plan);  // shared memory of the mixed-precision solve
 int64_t plan_max_mixed_bytes_nofactor(const mslam_plan* plan);  // the same without the FP32 factor
 bool plan_tracking_form(const mslam_plan* plan);  // every graph: one fixed keyframe, one frame, one edge

@@ -342,10 +342,16 @@ __global__ void __launch_bounds__(kLinThreads, MSLAM_LIN_MINBLOCKS)
         const int n = base + (kUnroll + u) * kLinThreads;
         mnext[u] = (n < tl.end) ? __ldg(idx_e + n) : -1;
       }
+      // two-level (blocked) summation, as in lin_packed_kernel
+      float bacc[NA];
+#pragma unroll
+      for (int a = 0; a < NA; ++a) bacc[a] = 0.0f;
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u)
         if (mm[u] >= 0 && qq[u] > lc.q_min && family_y<kKind>(yy[u], mm[u], ed.W))
-          accumulate_any<kKind, true>(acc, P, xj[u], yy[u], qq[u], lc);
+          accumulate_any<kKind, true>(bacc, P, xj[u], yy[u], qq[u], lc);
+#pragma unroll
+      for (int a = 0; a < NA; ++a) acc[a] += bacc[a];
     }
     // fixed-order tree: warp shuffles, then the 8 warp sums in order
     reduce_store<NA>(acc, red, partials, tile);
@@ -510,9 +516,17 @@ __global__ void __launch_bounds__(kLinThreads, MSLAM_PACKED_MINBLOCKS) lin_packe
         qq[u] = 0.0f;
         if (r < cnt) PackRec<T>::load(in + (size_t)r * W, xj[u], yy[u], qq[u]);
       }
+      // two-level (blocked) summation: the U records of a batch are summed
+      // on their own, then the batch sum is added to the running sums, so a
+      // thread's FP32 sums grow in error like U + records / U, not records
+      float bacc[NA];
+#pragma unroll
+      for (int a = 0; a < NA; ++a) bacc[a] = 0.0f;
 #pragma unroll
       for (int u = 0; u < U; ++u)
-        if (r0 + u * kLinThreads < cnt) accumulate_any<kKind, false>(acc, P, xj[u], yy[u], qq[u], lc);
+        if (r0 + u * kLinThreads < cnt) accumulate_any<kKind, false>(bacc, P, xj[u], yy[u], qq[u], lc);
+#pragma unroll
+      for (int a = 0; a < NA; ++a) acc[a] += bacc[a];
     }
     reduce_store<NA>(acc, red, partials, tile);
   }
@@ -741,6 +755,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
   f2 acc[kNumAcc];
 #pragma unroll
   for (int a = 0; a < kNumAcc; ++a) acc[a] = mk2(0.0f, 0.0f);
+  float wsum = 0.0f;  // lane L: this warp's running sum of value L over the tile's chunks
   int cur_tile = -1;
   f2 Rp[12];
   bool aborted = false;
@@ -782,9 +797,10 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
         }
       }
     }
-    if (m_last[slot]) {
-      // the tile is complete: reduce-scatter in each warp, then the warps'
-      // sums in a fixed order into the tile's partial slot
+    {
+      // tree summation per chunk: a thread's sums cover at most the chunk's
+      // eight records; the warp reduce-scatter adds them, and lane L keeps
+      // the running sum of value L over the tile's chunks
       float v[32];
 #pragma unroll
       for (int a = 0; a < kNumAcc; ++a) {
@@ -792,7 +808,13 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
         acc[a] = mk2(0.0f, 0.0f);
       }
       v[30] = v[31] = 0.0f;
-      red[warp][lane] = warp_reduce_scatter(v, lane);
+      wsum += warp_reduce_scatter(v, lane);
+    }
+    if (m_last[slot]) {
+      // the tile is complete: the warps' sums in a fixed order into the
+      // tile's partial slot
+      red[warp][lane] = wsum;
+      wsum = 0.0f;
       __syncthreads();
       if (tid < kNumAcc) {
         float sum = red[0][tid];
@@ -891,6 +913,7 @@ __global__ void __launch_bounds__(kWarpStreamThreads, 1)
   f2 acc[kNumAcc];
 #pragma unroll
   for (int a = 0; a < kNumAcc; ++a) acc[a] = mk2(0.0f, 0.0f);
+  float tsum = 0.0f;  // lane L: the running sum of value L over the tile's stages
   int cur_tile = -1;
   // the relative pose of the current tile, pairs (v, v), in the warp's slot
   // of shared memory (read as broadcasts; keeps 24 registers free)
@@ -933,9 +956,10 @@ __global__ void __launch_bounds__(kWarpStreamThreads, 1)
       const int ra = lane + 32 * u;
       if (ra < h) pair_at(ra, ra + h < n);
     }
-    if (last) {
-      // the tile is complete: the warp's sums by reduce-scatter, lane a
-      // stores value a of the tile's partial
+    {
+      // tree summation per stage: a lane's sums cover at most the stage's
+      // eight records; the reduce-scatter adds the warp's, and lane L keeps
+      // the running sum of value L over the tile's stages
       float v[32];
 #pragma unroll
       for (int a = 0; a < kNumAcc; ++a) {
@@ -943,8 +967,12 @@ __global__ void __launch_bounds__(kWarpStreamThreads, 1)
         acc[a] = mk2(0.0f, 0.0f);
       }
       v[30] = v[31] = 0.0f;
-      const float sum = warp_reduce_scatter(v, lane);
-      if (lane < kNumAcc) partials[(size_t)tile * kAccStride + lane] = sum;
+      tsum += warp_reduce_scatter(v, lane);
+    }
+    if (last) {
+      // the tile is complete: lane a stores value a of the tile's partial
+      if (lane < kNumAcc) partials[(size_t)tile * kAccStride + lane] = tsum;
+      tsum = 0.0f;
     }
     __syncwarp();  // every lane is done with this stage
     if (lane == 0) {

@@ -99,21 +99,45 @@ template <int D> struct Desc<__half, D> {
   }
 };
 
+// a1 materialised: the unit rays psi(X_ref) of pool pixels [p0, p1) as
+// float4 (x, y, z, 0), with ray_at's arithmetic (the zero ray for a zero or
+// non-finite point), so that the LM taps read one 16-byte value each.
+template <typename T>
+__global__ void __launch_bounds__(256) ray4_kernel(const T* __restrict__ X, float4* __restrict__ R4, int64_t p0,
+                                                   int64_t p1) {
+  for (int64_t i = p0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p1; i += (int64_t)gridDim.x * blockDim.x) {
+    const float3 r = ray_at(X, i);
+    R4[i] = make_float4(r.x, r.y, r.z, 0.0f);
+  }
+}
+
 // a2: lm_iters Levenberg-Marquardt steps of the ray error |R(p) - tg|^2
 // (Eq. 2) from p = (pu, pv_), R bilinear in the unit rays of the cell
 // (clamp(floor u, 0, W-2), clamp(floor v, 0, H-2)), p clamped to the image
 // after each step.
+// With R4_e != nullptr the unit rays come from the ray image [pixels] of
+// float4 (x, y, z, 0) that ray4_kernel wrote with the same FP32 arithmetic
+// as ray_at (one 16-byte load per tap, no normalisation per iteration).
 template <typename T>
-__device__ __forceinline__ void lm_iterate(const T* __restrict__ Xr_e, int W, int H, float3 tg, const MatchConst& mc,
-                                           float& pu, float& pv_) {
+__device__ __forceinline__ float3 tap(const T* __restrict__ Xr_e, const float4* __restrict__ R4_e, int64_t pix) {
+  if (R4_e) {
+    const float4 r = __ldg(R4_e + pix);
+    return make_float3(r.x, r.y, r.z);
+  }
+  return ray_at(Xr_e, pix);
+}
+
+template <typename T>
+__device__ __forceinline__ void lm_iterate(const T* __restrict__ Xr_e, const float4* __restrict__ R4_e, int W, int H,
+                                           float3 tg, const MatchConst& mc, float& pu, float& pv_) {
   const float lam = mc.lm_lambda;
   for (int it = 0; it < mc.lm_iters; ++it) {
     const int u0 = min(max((int)floorf(pu), 0), W - 2);
     const int v0 = min(max((int)floorf(pv_), 0), H - 2);
     const float a = pu - (float)u0, b = pv_ - (float)v0;
     const int64_t t00 = (int64_t)v0 * W + u0;
-    const float3 R00 = ray_at(Xr_e, t00), R10 = ray_at(Xr_e, t00 + 1);
-    const float3 R01 = ray_at(Xr_e, t00 + W), R11 = ray_at(Xr_e, t00 + W + 1);
+    const float3 R00 = tap(Xr_e, R4_e, t00), R10 = tap(Xr_e, R4_e, t00 + 1);
+    const float3 R01 = tap(Xr_e, R4_e, t00 + W), R11 = tap(Xr_e, R4_e, t00 + W + 1);
     const float ua = 1.0f - a, ub = 1.0f - b;
     const float3 Ju = make_float3(ub * (R10.x - R00.x) + b * (R11.x - R01.x), ub * (R10.y - R00.y) + b * (R11.y - R01.y),
                                   ub * (R10.z - R00.z) + b * (R11.z - R01.z));
@@ -147,7 +171,8 @@ template <typename T, int D, int kR>
 __global__ void __launch_bounds__(kMatchThreads) match_kernel(
     PlanView pv, MatchConst mc, const T* __restrict__ Xr, const T* __restrict__ Xq, const T* __restrict__ Dr,
     const T* __restrict__ Dq, const T* __restrict__ Qr, const T* __restrict__ Qq, const int32_t* __restrict__ init,
-    int32_t* __restrict__ out_idx, T* __restrict__ out_q, int e_begin, int e_end, int block_base) {
+    int32_t* __restrict__ out_idx, T* __restrict__ out_q, int e_begin, int e_end, int block_base,
+    const float4* __restrict__ R4) {
   const int gb = block_base + blockIdx.x;
   // edge of this block: the last edge in [e_begin, e_end) whose first block <= gb
   int lo = e_begin, hi = e_end - 1;
@@ -183,7 +208,7 @@ __global__ void __launch_bounds__(kMatchThreads) match_kernel(
     if (ii >= 0 && ii < HW) p0 = ii;
   }
   float pu = (float)(p0 % W), pv_ = (float)(p0 / W);
-  lm_iterate(Xr_e, W, H, tg, mc, pu, pv_);
+  lm_iterate(Xr_e, R4 ? R4 + o : nullptr, W, H, tg, mc, pu, pv_);
   int cu = min((int)floorf(pu + 0.5f), W - 1), cv = min((int)floorf(pv_ + 0.5f), H - 1);
   // coarse-to-fine refinement: maximum descriptor similarity in a window
   typename Desc<T, D>::Q dq[Desc<T, D>::NQ];
@@ -373,7 +398,7 @@ __global__ void __launch_bounds__(kMatchThreads) match_tc_kernel(
     PlanView pv, MatchConst mc, const __half* __restrict__ Xr, const __half* __restrict__ Xq,
     const __half* __restrict__ Dr, const __half* __restrict__ Dq, const __half* __restrict__ Qr,
     const __half* __restrict__ Qq, const int32_t* __restrict__ init, int32_t* __restrict__ out_idx,
-    __half* __restrict__ out_q, int e_begin, int e_end, int block_base) {
+    __half* __restrict__ out_q, int e_begin, int e_end, int block_base, const float4* __restrict__ R4) {
   const int gb = block_base + blockIdx.x;
   int lo = e_begin, hi = e_end - 1;
   while (lo < hi) {
@@ -406,7 +431,7 @@ __global__ void __launch_bounds__(kMatchThreads) match_tc_kernel(
       if (ii >= 0 && ii < HW) p0 = ii;
     }
     float pu = (float)(p0 % W), pv_ = (float)(p0 / W);
-    lm_iterate(Xr_e, W, H, tg, mc, pu, pv_);
+    lm_iterate(Xr_e, R4 ? R4 + o : nullptr, W, H, tg, mc, pu, pv_);
     cu = min((int)floorf(pu + 0.5f), W - 1);
     cv = min((int)floorf(pv_ + 0.5f), H - 1);
   }
@@ -432,13 +457,13 @@ __global__ void __launch_bounds__(kMatchThreads) match_tc_kernel(
 template <typename T, int D>
 static void launch_match(const PlanView& pv, const MatchConst& mc, const void* Xr, const void* Xq, const void* Dr,
                          const void* Dq, const void* Qr, const void* Qq, const int32_t* init, int32_t* out_idx,
-                         void* out_q, int e0, int e1, int b0, int nblocks, bool tc, cudaStream_t s) {
+                         void* out_q, int e0, int e1, int b0, int nblocks, bool tc, float4* R4, cudaStream_t s) {
   if constexpr (std::is_same<T, __half>::value) {
     if (tc && mc.radius == 3) {
       match_tc_kernel<D><<<nblocks, kMatchThreads, 0, s>>>(
           pv, mc, static_cast<const __half*>(Xr), static_cast<const __half*>(Xq), static_cast<const __half*>(Dr),
           static_cast<const __half*>(Dq), static_cast<const __half*>(Qr), static_cast<const __half*>(Qq), init, out_idx,
-          static_cast<__half*>(out_q), e0, e1, b0);
+          static_cast<__half*>(out_q), e0, e1, b0, R4);
       return;
     }
   }
@@ -446,7 +471,7 @@ static void launch_match(const PlanView& pv, const MatchConst& mc, const void* X
   k<<<nblocks, kMatchThreads, 0, s>>>(pv, mc, static_cast<const T*>(Xr), static_cast<const T*>(Xq),
                                      static_cast<const T*>(Dr), static_cast<const T*>(Dq),
                                      static_cast<const T*>(Qr), static_cast<const T*>(Qq), init, out_idx,
-                                     static_cast<T*>(out_q), e0, e1, b0);
+                                     static_cast<T*>(out_q), e0, e1, b0, R4);
 }
 
 }  // namespace mslam
@@ -456,8 +481,8 @@ using namespace mslam;
 extern "C" mslam_status mslam_match(const mslam_params* p, const mslam_plan* plan, mslam_dtype dt, int32_t d,
                                     const void* X_ref, const void* X_qry, const void* D_ref, const void* D_qry,
                                     const void* Q_ref, const void* Q_qry, const int32_t* init_idx, int32_t* idx_out,
-                                    void* q_out, int32_t edge_begin, int32_t edge_end, uint32_t flags,
-                                    void* stream) {
+                                    void* q_out, int32_t edge_begin, int32_t edge_end, void* workspace,
+                                    size_t ws_bytes, uint32_t flags, void* stream) {
   if (!p || !check_plan_uploaded(plan)) {
     if (!p) set_error("params is NULL");
     return MSLAM_ERR_ARG;
@@ -510,8 +535,18 @@ extern "C" mslam_status mslam_match(const mslam_params* p, const mslam_plan* pla
   mc.radius = p->win_radius;
   mc.n_levels = p->n_levels;
   for (int l = 0; l < 4; ++l) mc.dil[l] = p->win_dilation[l];
+  if (workspace && (ws_bytes < mslam_workspace_bytes(plan, MSLAM_OP_MATCH) ||
+                    (reinterpret_cast<uintptr_t>(workspace) & 255))) {
+    set_error("match: workspace smaller than %zu bytes or not 256-byte aligned",
+              mslam_workspace_bytes(plan, MSLAM_OP_MATCH));
+    return MSLAM_ERR_ARG;
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const bool tc = plan_match_form(plan) == 1;
+  float4* R4 = static_cast<float4*>(workspace);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   auto go = [&](int a, int b) {
     int b0, b1x, bt0, bt1;
     plan_edge_mblocks(plan, a, &b0, &bt0);
@@ -519,9 +554,18 @@ extern "C" mslam_status mslam_match(const mslam_params* p, const mslam_plan* pla
     (void)bt0;
     (void)bt1;
     const int nb = b1x - b0;
+    if (R4) {
+      // a1: the unit rays of the reference pointmaps of edges [a, b)
+      const int64_t p0 = plan_edge_off(plan, a), p1 = plan_edge_off(plan, b);
+      const int grid = (int)std::min<int64_t>((p1 - p0 + 255) / 256, (int64_t)std::max(1, sms) * 16);
+      if (dt == MSLAM_F32)
+        ray4_kernel<float><<<grid, 256, 0, s>>>(static_cast<const float*>(X_ref), R4, p0, p1);
+      else
+        ray4_kernel<__half><<<grid, 256, 0, s>>>(static_cast<const __half*>(X_ref), R4, p0, p1);
+    }
 #define MSLAM_MATCH_CASE(TT, DD)                                                                              \
   launch_match<TT, DD>(pv, mc, X_ref, X_qry, D_ref, D_qry, Q_ref, Q_qry, init_idx, idx_out, q_out, a, b, b0, nb, \
-                       tc, s)
+                       tc, R4, s)
     if (dt == MSLAM_F32) {
       if (d == 16) MSLAM_MATCH_CASE(float, 16);
       else if (d == 24) MSLAM_MATCH_CASE(float, 24);

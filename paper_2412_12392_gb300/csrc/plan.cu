@@ -112,6 +112,7 @@ int plan_lin_blocks_per_sm(const mslam_plan* plan) { return plan->lin_blocks_per
 int plan_lin_form(const mslam_plan* plan) { return plan->lin_form; }
 int plan_solve_form(const mslam_plan* plan) { return plan->solve_form; }
 int plan_match_form(const mslam_plan* plan) { return plan->match_form; }
+int64_t plan_edge_off(const mslam_plan* plan, int e) { return plan->e_off[e]; }
 int plan_max_image_dim(const mslam_plan* plan) {
   int m = 0;
   for (int v : plan->kf_hw) m = std::max(m, v);
@@ -629,6 +630,9 @@ size_t mslam_workspace_bytes(const mslam_plan* plan, int32_t op) {
       return pack_bytes((int)plan->tiles.size(), plan->lin_tile, MSLAM_F16);
     case MSLAM_OP_STATS:
       return align256(sizeof(uint32_t) * (size_t)((plan->e_off.back() + 31) / 32 + 1));
+    case MSLAM_OP_MATCH:
+      // the reference ray image: one float4 per edge-pool pixel
+      return align256(sizeof(float) * 4 * (size_t)std::max<int64_t>(plan->e_off.back(), 1));
     case MSLAM_OP_BACKWARD:
       // the solve's workspace, b and tau (7 N doubles each), per-edge data
       // (32 floats per edge), then for the pose term the step's right-hand

@@ -465,3 +465,29 @@ def test_match_tensor_core_form_agrees_with_per_query_form(M):
     check_disagreements(classify_disagreements(b, idx_r, dg, par), "tracking, tensor-core form:")
     same = (a == b) & (a >= 0)
     assert torch.equal(out[0][1][torch.from_numpy(same).cuda()], out[1][1][torch.from_numpy(same).cuda()])
+
+
+@pytest.mark.parametrize("dtype,match_form", [(torch.float32, 0), (torch.float16, 0), (torch.float16, 1)])
+def test_match_ray_image_path_is_identical(M, dtype, match_form):
+    """mslam_match with its ray-image workspace (a1 materialised once, FP32)
+    and without it (the rays normalised at the taps) give bit-identical
+    matches and confidences, on the batched launch, per-edge launches and an
+    edge sub-range; the ray pass covers exactly the edges matched."""
+    import synth
+    w = synth.global_graph(N=6, n_pairs=6, H=48, W=64, seed=7).to_storage(dtype)
+    wd = w.to("cuda")
+    P = M.default_params()
+    plan = M.Plan(w.kf_hw.numpy(), w.edges.numpy(), opts={"match_form": match_form})
+    a = gpu_match(M, plan, P, wd, workspace=False)
+    b = gpu_match(M, plan, P, wd)
+    c = gpu_match(M, plan, P, wd, per_edge=True)
+    torch.cuda.synchronize()
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    assert torch.equal(a[0], c[0]) and torch.equal(a[1], c[1])
+    ws = plan.workspace(M._lib.MSLAM_OP_MATCH)
+    ws.fill_(255)  # NaN rays wherever the pass does not write
+    d_idx = torch.full_like(a[0], -7)
+    d_q = torch.zeros_like(a[1])
+    gpu_match(M, plan, P, wd, idx_out=d_idx, q_out=d_q, edge_range=(2, 4), workspace=ws)
+    sl = slice(int(w.e_off[2]), int(w.e_off[4]))
+    assert torch.equal(d_idx[sl], a[0][sl]) and torch.equal(d_q[sl], a[1][sl])

@@ -142,8 +142,8 @@ void mslam_plan_destroy(mslam_plan* plan);
  *   lin_blocks_per_sm  resident blocks per SM of the persistent
  *                      linearisation launches, 1..32, or 0 for the
  *                      occupancy maximum (default 0)
- *   match_block_w      width of a 256-pixel match block: 4, 8, 16, 32, 64,
- *                      128 or 256 (default 32, i.e. 32 x 8 pixels)
+ *   match_block_w      width of a 256-thread match block: 4, 8, 16, 32, 64,
+ *                      128 or 256 (default 32, i.e. 32 x 8 threads)
  *   lin_form, solve_form  kernel forms, described at the fields
  * mslam_plan_create uses the defaults; mslam_plan_create_ex takes options
  * (NULL = defaults).  Errors: MSLAM_ERR_ARG for an option out of range. */
@@ -165,6 +165,9 @@ typedef struct {
                           grouped and their windows scored together on the tensor cores (FP16 storage and
                           win_radius 3 only; other cases use form 0).  Same decisions up to the FP32
                           summation order of the scores. */
+  int32_t match_ppt;   /* query pixels per thread of mslam_match, 1..4 (default 1): a block of
+                          match_block_w x (256 / match_block_w) threads covers match_ppt times as many
+                          rows, each thread taking its queries 256 / match_block_w rows apart */
   int32_t wait_limit;  /* polls of every bounded device wait on an asynchronous copy (the streamed
                           linearisation forms) before it gives up: 0 = the default 2^24 (about a
                           second), > 0 = that many; < 0 = give up at once without issuing any copy (so

@@ -49,7 +49,7 @@ class PlanOpts(C.Structure):
     """Mirror of mslam_plan_opts."""
     _fields_ = [("lin_tile", C.c_int32), ("lin_blocks_per_sm", C.c_int32), ("match_block_w", C.c_int32),
                 ("lin_form", C.c_int32), ("solve_form", C.c_int32), ("match_form", C.c_int32),
-                ("wait_limit", C.c_int32)]
+                ("match_ppt", C.c_int32), ("wait_limit", C.c_int32)]
 
 
 class MslamError(RuntimeError):

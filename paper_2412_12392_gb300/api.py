@@ -77,7 +77,7 @@ class Plan:
         for k, v in (opts or {}).items():
             setattr(o, k, int(v))
         self.opts = {k: getattr(o, k) for k in ("lin_tile", "lin_blocks_per_sm", "match_block_w", "lin_form",
-                                                   "solve_form", "match_form", "wait_limit")}
+                                                   "solve_form", "match_form", "match_ppt", "wait_limit")}
         self.graph_of_kf = gk
         h = C.c_void_p()
         check(lib().mslam_plan_create_ex(self.N, kf.ctypes.data, self.E, ed.ctypes.data if self.E else None,

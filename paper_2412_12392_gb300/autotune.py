@@ -1,6 +1,7 @@
 """Autotuner for the plan's launch shapes: the linearisation tile size and
 form, blocks per SM, the match block shape (pixels per block row) and the
-match window form (per-query FP32 or grouped tensor-core scoring).
+match window form (per-query FP32 or grouped tensor-core scoring) and the
+query pixels per match thread.
 
 Each candidate is timed on the caller's device-resident inputs with CUDA
 events -- the match block shape on mslam_match, the linearisation tile size
@@ -17,7 +18,8 @@ import torch
 
 from . import api
 
-MATCH_WIDTHS = (4, 8, 16, 32, 64)
+MATCH_WIDTHS = (8, 16, 32, 64)
+MATCH_PPTS = (1, 2)
 LIN_TILES = (4096, 8192, 16384)
 LIN_BLOCKS = (0, 2, 3, 4)
 WARP_STREAM_TILES = (1024, 2048, 4096)
@@ -38,6 +40,7 @@ def _time(fn, reps: int) -> float:
 
 def autotune(kf_hw, edges, graph_of_kf, params, X_ref, X_qry, D_ref, D_qry, Q_ref, Q_qry, X_canon, T_wc,
              match_widths: Sequence[int] = MATCH_WIDTHS, lin_tiles: Sequence[int] = LIN_TILES,
+             match_ppts: Sequence[int] = MATCH_PPTS,
              lin_blocks: Sequence[int] = LIN_BLOCKS, reps: int = 3, gn_iters: int = 10) -> Dict:
     """Returns {"opts": best plan options, "match_ms": {...}, "lin_ms": {...},
     "pack_ms": {...}}.  A linearisation shape is scored by gn_iters
@@ -48,16 +51,19 @@ def autotune(kf_hw, edges, graph_of_kf, params, X_ref, X_qry, D_ref, D_qry, Q_re
     idx = q = None
     # the tensor-core window form exists for FP16 storage
     forms = (0, 1) if X_ref.dtype == torch.float16 else (0,)
-    for wdt, form in itertools.product(match_widths, forms):
-        plan = api.Plan(kf_hw, edges, graph_of_kf, opts={"match_block_w": wdt, "match_form": form})
+    for wdt, form, ppt in itertools.product(match_widths, forms, match_ppts):
+        plan = api.Plan(kf_hw, edges, graph_of_kf, opts={"match_block_w": wdt, "match_form": form,
+                                                        "match_ppt": ppt})
+        ws = plan.workspace(api._lib.MSLAM_OP_MATCH)
 
         def run_match():
-            return api.match(plan, params, X_ref, X_qry, D_ref, D_qry, Q_ref, Q_qry)
+            return api.match(plan, params, X_ref, X_qry, D_ref, D_qry, Q_ref, Q_qry, workspace=ws)
 
         ms = _time(run_match, reps)
-        report["match_ms"][f"{wdt}/{form}"] = ms
+        report["match_ms"][f"{wdt}/{form}/{ppt}"] = ms
         if ms < best_t:
-            best_w, best_t = (wdt, form), ms
+            best_w, best_t = (wdt, form, ppt), ms
+        del ws
     idx, q = api.match(api.Plan(kf_hw, edges, graph_of_kf), params, X_ref, X_qry, D_ref, D_qry, Q_ref, Q_qry)
     best_lin, best_lt = None, float("inf")
     shapes = [(tile, bps, 1) for tile, bps in itertools.product(lin_tiles, lin_blocks)]
@@ -83,6 +89,7 @@ def autotune(kf_hw, edges, graph_of_kf, params, X_ref, X_qry, D_ref, D_qry, Q_re
         score = gn_iters * ms + pms
         if score < best_lt:
             best_lin, best_lt = (tile, bps, form), score
-    report["opts"] = {"match_block_w": best_w[0], "match_form": best_w[1], "lin_tile": best_lin[0],
+    report["opts"] = {"match_block_w": best_w[0], "match_form": best_w[1], "match_ppt": best_w[2],
+                      "lin_tile": best_lin[0],
                       "lin_blocks_per_sm": best_lin[1], "lin_form": best_lin[2]}
     return report

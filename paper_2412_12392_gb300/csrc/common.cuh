@@ -82,7 +82,8 @@ struct PlanView {
   int32_t N, E, G, n_tiles, n_mblocks;
   int64_t P;  // pixels of the edge pools
   int32_t lin_tile;           // pixels per linearisation tile
-  int32_t match_bx, match_by; // match block shape (match_bx * match_by = 256)
+  int32_t match_bx, match_by; // match block shape (match_bx * match_by = 256 threads)
+  int32_t match_ppt;          // query pixels per match thread (rows match_by apart)
   uint32_t wait_polls;        // polls of a bounded device wait; 0 = give up at once, issuing no copy
   const DevEdge* edges;
   const DevTile* tiles;

@@ -243,6 +243,23 @@ __device__ __forceinline__ bool family_y(float3& y, int m, int W) {
   }
 }
 
+// Warp reduce-scatter of 32 values: after five butterfly rounds (one
+// shuffle per kept value and round) lane L holds the warp's sum of value L.
+__device__ __forceinline__ float warp_reduce_scatter(float v[32], int lane) {
+#pragma unroll
+  for (int round = 0; round < 5; ++round) {
+    const int half = 16 >> round;
+    const bool up = (lane & half) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const float send = up ? v[i] : v[i + half];
+      const float keep = up ? v[i + half] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, half);
+    }
+  }
+  return v[0];
+}
+
 // Fixed-order block reduction of NA accumulators into the tile's partial slot.
 template <int NA>
 __device__ __forceinline__ void reduce_store(const float* acc, float (*red)[kFamAcc], float* partials, int tile) {
@@ -373,6 +390,8 @@ __global__ void __launch_bounds__(kLinThreads, MSLAM_LIN_MINBLOCKS)
 #ifndef MSLAM_PACKED_UNROLL
 #define MSLAM_PACKED_UNROLL 4
 #endif
+// records a thread sums in FP32 before they join the warp's tree sum
+constexpr int kFlushRecs = 16;
 
 template <typename T> struct PackRec;
 template <> struct PackRec<__half> {
@@ -507,28 +526,76 @@ __global__ void __launch_bounds__(kLinThreads, MSLAM_PACKED_MINBLOCKS) lin_packe
     for (int a = 0; a < NA; ++a) acc[a] = 0.0f;
     const int cnt = __ldg(counts + tile);
     const uint4* in = recs + (size_t)tile * pv.lin_tile * W;
-    for (int r0 = tid; r0 < cnt; r0 += U * kLinThreads) {
-      float3 xj[U], yy[U];
-      float qq[U];
+    if constexpr (NA <= 32) {
+      // Tree summation: a thread sums at most kFlushRecs records in FP32,
+      // then the warp's sums are added by a reduce-scatter and lane L keeps
+      // the running sum of value L over the tile; the 8 warp sums are added
+      // in a fixed order (the loop runs warp-uniformly so that every lane
+      // takes part in each reduce-scatter)
+      const int lane = tid & 31, warp = tid >> 5;
+      float wsum = 0.0f;
+      int batches = 0;
+      for (int r0 = tid - lane; r0 < cnt; r0 += U * kLinThreads) {
+        float3 xj[U], yy[U];
+        float qq[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int r = r0 + u * kLinThreads;
-        qq[u] = 0.0f;
-        if (r < cnt) PackRec<T>::load(in + (size_t)r * W, xj[u], yy[u], qq[u]);
+        for (int u = 0; u < U; ++u) {
+          const int r = r0 + lane + u * kLinThreads;
+          qq[u] = 0.0f;
+          if (r < cnt) PackRec<T>::load(in + (size_t)r * W, xj[u], yy[u], qq[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (r0 + lane + u * kLinThreads < cnt) accumulate_any<kKind, false>(acc, P, xj[u], yy[u], qq[u], lc);
+        if (++batches * U == kFlushRecs) {
+          float v[32];
+#pragma unroll
+          for (int a = 0; a < 32; ++a) v[a] = a < NA ? acc[a] : 0.0f;
+#pragma unroll
+          for (int a = 0; a < NA; ++a) acc[a] = 0.0f;
+          wsum += warp_reduce_scatter(v, lane);
+          batches = 0;
+        }
       }
-      // two-level (blocked) summation: the U records of a batch are summed
-      // on their own, then the batch sum is added to the running sums, so a
-      // thread's FP32 sums grow in error like U + records / U, not records
-      float bacc[NA];
+      {
+        float v[32];
 #pragma unroll
-      for (int a = 0; a < NA; ++a) bacc[a] = 0.0f;
+        for (int a = 0; a < 32; ++a) v[a] = a < NA ? acc[a] : 0.0f;
+        wsum += warp_reduce_scatter(v, lane);
+      }
+      if (lane < NA) red[warp][lane] = wsum;
+      __syncthreads();
+      if (tid < NA) {
+        float sum = red[0][tid];
 #pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (r0 + u * kLinThreads < cnt) accumulate_any<kKind, false>(bacc, P, xj[u], yy[u], qq[u], lc);
+        for (int w2 = 1; w2 < kLinThreads / 32; ++w2) sum += red[w2][tid];
+        partials[(size_t)tile * kAccStride + tid] = sum;
+      }
+      __syncthreads();
+    } else {
+      for (int r0 = tid; r0 < cnt; r0 += U * kLinThreads) {
+        float3 xj[U], yy[U];
+        float qq[U];
 #pragma unroll
-      for (int a = 0; a < NA; ++a) acc[a] += bacc[a];
+        for (int u = 0; u < U; ++u) {
+          const int r = r0 + u * kLinThreads;
+          qq[u] = 0.0f;
+          if (r < cnt) PackRec<T>::load(in + (size_t)r * W, xj[u], yy[u], qq[u]);
+        }
+        // two-level (blocked) summation: the U records of a batch are summed
+        // on their own, then the batch sum is added to the running sums, so a
+        // thread's FP32 sums grow in error like U + records / U, not records
+        float bacc[NA];
+#pragma unroll
+        for (int a = 0; a < NA; ++a) bacc[a] = 0.0f;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (r0 + u * kLinThreads < cnt) accumulate_any<kKind, false>(bacc, P, xj[u], yy[u], qq[u], lc);
+#pragma unroll
+        for (int a = 0; a < NA; ++a) acc[a] += bacc[a];
+      }
+      reduce_store<NA>(acc, red, partials, tile);
     }
-    reduce_store<NA>(acc, red, partials, tile);
   }
 }
 
@@ -688,23 +755,6 @@ __device__ __forceinline__ void accumulate_pair(f2 acc[kNumAcc], const f2 Rp[12]
   acc[29] = add2(acc[29], mask);
 }
 
-// Warp reduce-scatter of 32 values: after five butterfly rounds (one
-// shuffle per kept value and round) lane L holds the warp's sum of value L.
-__device__ __forceinline__ float warp_reduce_scatter(float v[32], int lane) {
-#pragma unroll
-  for (int round = 0; round < 5; ++round) {
-    const int half = 16 >> round;
-    const bool up = (lane & half) != 0;
-#pragma unroll
-    for (int i = 0; i < half; ++i) {
-      const float send = up ? v[i] : v[i + half];
-      const float keep = up ? v[i + half] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, half);
-    }
-  }
-  return v[0];
-}
-
 __global__ void __launch_bounds__(kStreamThreads, 1)
     lin_stream_kernel(PlanView pv, LinConst lc, const RelPose* __restrict__ rel, const unsigned char* __restrict__ recs,
                       const int32_t* __restrict__ counts, float* __restrict__ partials, int tile_begin, int tile_end,
@@ -756,6 +806,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
 #pragma unroll
   for (int a = 0; a < kNumAcc; ++a) acc[a] = mk2(0.0f, 0.0f);
   float wsum = 0.0f;  // lane L: this warp's running sum of value L over the tile's chunks
+  int chunks = 0;     // chunks summed since the last reduce-scatter
   int cur_tile = -1;
   f2 Rp[12];
   bool aborted = false;
@@ -797,10 +848,11 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
         }
       }
     }
-    {
-      // tree summation per chunk: a thread's sums cover at most the chunk's
-      // eight records; the warp reduce-scatter adds them, and lane L keeps
-      // the running sum of value L over the tile's chunks
+    if (++chunks == 2 || m_last[slot]) {
+      // tree summation every two chunks: a thread's sums cover at most 16
+      // records; the warp reduce-scatter adds them, and lane L keeps the
+      // running sum of value L over the tile's chunks
+      chunks = 0;
       float v[32];
 #pragma unroll
       for (int a = 0; a < kNumAcc; ++a) {
@@ -914,6 +966,7 @@ __global__ void __launch_bounds__(kWarpStreamThreads, 1)
 #pragma unroll
   for (int a = 0; a < kNumAcc; ++a) acc[a] = mk2(0.0f, 0.0f);
   float tsum = 0.0f;  // lane L: the running sum of value L over the tile's stages
+  int stages = 0;     // stages summed since the last reduce-scatter
   int cur_tile = -1;
   // the relative pose of the current tile, pairs (v, v), in the warp's slot
   // of shared memory (read as broadcasts; keeps 24 registers free)
@@ -956,10 +1009,11 @@ __global__ void __launch_bounds__(kWarpStreamThreads, 1)
       const int ra = lane + 32 * u;
       if (ra < h) pair_at(ra, ra + h < n);
     }
-    {
-      // tree summation per stage: a lane's sums cover at most the stage's
-      // eight records; the reduce-scatter adds the warp's, and lane L keeps
-      // the running sum of value L over the tile's stages
+    if (++stages == 2 || last) {
+      // tree summation every two stages: a lane's sums cover at most 16
+      // records; the reduce-scatter adds the warp's, and lane L keeps the
+      // running sum of value L over the tile's stages
+      stages = 0;
       float v[32];
 #pragma unroll
       for (int a = 0; a < kNumAcc; ++a) {

@@ -167,27 +167,27 @@ __device__ __forceinline__ void lm_iterate(const T* __restrict__ Xr_e, const flo
 // that each window row is unrolled with branch-free bounds (an out-of-image
 // candidate reads a clamped pixel and scores -inf, which never wins, exactly
 // as if it were skipped); kR = 0 takes the radius from the parameters.
-template <typename T, int D, int kR>
-__global__ void __launch_bounds__(kMatchThreads) match_kernel(
-    PlanView pv, MatchConst mc, const T* __restrict__ Xr, const T* __restrict__ Xq, const T* __restrict__ Dr,
-    const T* __restrict__ Dq, const T* __restrict__ Qr, const T* __restrict__ Qq, const int32_t* __restrict__ init,
-    int32_t* __restrict__ out_idx, T* __restrict__ out_q, int e_begin, int e_end, int block_base,
-    const float4* __restrict__ R4) {
-  const int gb = block_base + blockIdx.x;
-  // edge of this block: the last edge in [e_begin, e_end) whose first block <= gb
+// Edge of match block gb: the last edge in [e_begin, e_end) whose first
+// block <= gb.
+__device__ __forceinline__ int match_block_edge(const PlanView& pv, int gb, int e_begin, int e_end) {
   int lo = e_begin, hi = e_end - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
     if (pv.edges[mid].mblock_begin <= gb) lo = mid;
     else hi = mid - 1;
   }
-  const DevEdge ed = pv.edges[lo];
+  return lo;
+}
+
+// The per-query matching (a1-a3) of query pixel (u, v) of edge ed.
+template <typename T, int D, int kR>
+__device__ __forceinline__ void match_query(const PlanView& pv, const MatchConst& mc, const DevEdge& ed, int u, int v,
+                                            const T* __restrict__ Xr, const T* __restrict__ Xq,
+                                            const T* __restrict__ Dr, const T* __restrict__ Dq,
+                                            const T* __restrict__ Qr, const T* __restrict__ Qq,
+                                            const int32_t* __restrict__ init, int32_t* __restrict__ out_idx,
+                                            T* __restrict__ out_q, const float4* __restrict__ R4) {
   const int W = ed.W, H = ed.H;
-  const int local = gb - ed.mblock_begin;
-  const int bx = pv.match_bx, by = pv.match_by;
-  const int nbx = (W + bx - 1) / bx;
-  const int u = (local % nbx) * bx + (threadIdx.x % bx);
-  const int v = (local / nbx) * by + (threadIdx.x / bx);
   if (u >= W || v >= H) return;
   const int64_t HW = (int64_t)H * W;
   const int n = v * W + u;
@@ -264,6 +264,25 @@ __global__ void __launch_bounds__(kMatchThreads) match_kernel(
   const bool ok = finite3(y) && dist <= mc.max_rel * sqrtf(nx2);
   out_idx[o + n] = ok ? m : -1;
   stf(out_q + o + n, ok ? sqrtf(ldf(Qr + o + m) * ldf(Qq + o + n)) : 0.0f);
+}
+
+// A block covers match_bx x (match_by * match_ppt) query pixels: each thread
+// takes match_ppt queries, match_by rows apart (plan option match_ppt).
+template <typename T, int D, int kR>
+__global__ void __launch_bounds__(kMatchThreads) match_kernel(
+    PlanView pv, MatchConst mc, const T* __restrict__ Xr, const T* __restrict__ Xq, const T* __restrict__ Dr,
+    const T* __restrict__ Dq, const T* __restrict__ Qr, const T* __restrict__ Qq, const int32_t* __restrict__ init,
+    int32_t* __restrict__ out_idx, T* __restrict__ out_q, int e_begin, int e_end, int block_base,
+    const float4* __restrict__ R4) {
+  const int gb = block_base + blockIdx.x;
+  const DevEdge ed = pv.edges[match_block_edge(pv, gb, e_begin, e_end)];
+  const int local = gb - ed.mblock_begin;
+  const int bx = pv.match_bx, by = pv.match_by, bh = by * pv.match_ppt;
+  const int nbx = (ed.W + bx - 1) / bx;
+  const int u = (local % nbx) * bx + (threadIdx.x % bx);
+  const int v0 = (local / nbx) * bh + (threadIdx.x / bx);
+  for (int k = 0; k < pv.match_ppt; ++k)
+    match_query<T, D, kR>(pv, mc, ed, u, v0 + k * by, Xr, Xq, Dr, Dq, Qr, Qq, init, out_idx, out_q, R4);
 }
 
 // ----------------------------------------------- tensor-core window form
@@ -389,30 +408,14 @@ __device__ __forceinline__ void tc_window_level(const uint32_t* __restrict__ Dr3
   cv = ncv;
 }
 
-// The matching kernel with the tensor-core window (FP16 storage, radius 3):
-// the per-query part (a1, a2, the rounding, the 3D test and q) is that of
-// match_kernel; every lane of a warp reaches the window levels, which are
-// warp-collective.
 template <int D>
-__global__ void __launch_bounds__(kMatchThreads) match_tc_kernel(
-    PlanView pv, MatchConst mc, const __half* __restrict__ Xr, const __half* __restrict__ Xq,
-    const __half* __restrict__ Dr, const __half* __restrict__ Dq, const __half* __restrict__ Qr,
-    const __half* __restrict__ Qq, const int32_t* __restrict__ init, int32_t* __restrict__ out_idx,
-    __half* __restrict__ out_q, int e_begin, int e_end, int block_base, const float4* __restrict__ R4) {
-  const int gb = block_base + blockIdx.x;
-  int lo = e_begin, hi = e_end - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (pv.edges[mid].mblock_begin <= gb) lo = mid;
-    else hi = mid - 1;
-  }
-  const DevEdge ed = pv.edges[lo];
+__device__ __forceinline__ void match_tc_query(const PlanView& pv, const MatchConst& mc, const DevEdge& ed, int u,
+                                               int v, const __half* __restrict__ Xr, const __half* __restrict__ Xq,
+                                               const __half* __restrict__ Dr, const __half* __restrict__ Dq,
+                                               const __half* __restrict__ Qr, const __half* __restrict__ Qq,
+                                               const int32_t* __restrict__ init, int32_t* __restrict__ out_idx,
+                                               __half* __restrict__ out_q, const float4* __restrict__ R4) {
   const int W = ed.W, H = ed.H;
-  const int local = gb - ed.mblock_begin;
-  const int bx = pv.match_bx, by = pv.match_by;
-  const int nbx = (W + bx - 1) / bx;
-  const int u = (local % nbx) * bx + (threadIdx.x % bx);
-  const int v = (local / nbx) * by + (threadIdx.x / bx);
   const bool inside = u < W && v < H;
   const int64_t HW = (int64_t)H * W;
   const int n = inside ? v * W + u : 0;
@@ -452,6 +455,27 @@ __global__ void __launch_bounds__(kMatchThreads) match_tc_kernel(
   const bool ok = finite3(y) && dist <= mc.max_rel * sqrtf(nx2);
   out_idx[o + n] = ok ? m : -1;
   stf(out_q + o + n, ok ? sqrtf(ldf(Qr + o + m) * ldf(Qq + o + n)) : 0.0f);
+}
+
+// The matching kernel with the tensor-core window (FP16 storage, radius 3):
+// the per-query part (a1, a2, the rounding, the 3D test and q) is that of
+// match_kernel; every lane of a warp reaches the window levels, which are
+// warp-collective.
+template <int D>
+__global__ void __launch_bounds__(kMatchThreads) match_tc_kernel(
+    PlanView pv, MatchConst mc, const __half* __restrict__ Xr, const __half* __restrict__ Xq,
+    const __half* __restrict__ Dr, const __half* __restrict__ Dq, const __half* __restrict__ Qr,
+    const __half* __restrict__ Qq, const int32_t* __restrict__ init, int32_t* __restrict__ out_idx,
+    __half* __restrict__ out_q, int e_begin, int e_end, int block_base, const float4* __restrict__ R4) {
+  const int gb = block_base + blockIdx.x;
+  const DevEdge ed = pv.edges[match_block_edge(pv, gb, e_begin, e_end)];
+  const int local = gb - ed.mblock_begin;
+  const int bx = pv.match_bx, by = pv.match_by, bh = by * pv.match_ppt;
+  const int nbx = (ed.W + bx - 1) / bx;
+  const int u = (local % nbx) * bx + (threadIdx.x % bx);
+  const int v0 = (local / nbx) * bh + (threadIdx.x / bx);
+  for (int k = 0; k < pv.match_ppt; ++k)  // the same count in every lane: the window levels stay warp-collective
+    match_tc_query<D>(pv, mc, ed, u, v0 + k * by, Xr, Xq, Dr, Dq, Qr, Qq, init, out_idx, out_q, R4);
 }
 
 template <typename T, int D>

@@ -28,7 +28,7 @@ struct mslam_plan {
   int32_t max_m = 0;            // non-fixed poses of the largest graph
   int32_t max_levels = 0;
   int32_t lin_tile = 0, lin_blocks_per_sm = 0, match_bx = 0, match_by = 0, lin_form = 0, solve_form = 0;
-  int32_t wait_limit = 0, match_form = 0;
+  int32_t wait_limit = 0, match_form = 0, match_ppt = 1;
   int32_t n_mblocks = 0;
   void* dev = nullptr;
   size_t dev_bytes = 0;
@@ -76,6 +76,7 @@ PlanView plan_view(const mslam_plan* plan) {
   v.lin_tile = plan->lin_tile;
   v.match_bx = plan->match_bx;
   v.match_by = plan->match_by;
+  v.match_ppt = plan->match_ppt;
   v.wait_polls = plan->wait_limit < 0 ? 0u : plan->wait_limit == 0 ? (1u << 24) : (uint32_t)plan->wait_limit;
   v.edges = reinterpret_cast<const DevEdge*>(base + plan->off_edges);
   v.tiles = reinterpret_cast<const DevTile*>(base + plan->off_tiles);
@@ -445,6 +446,7 @@ void mslam_default_plan_opts(mslam_plan_opts* o) {
   o->solve_form = 0;
   o->wait_limit = 0;
   o->match_form = 0;
+  o->match_ppt = 1;
 }
 
 mslam_status mslam_plan_create(int32_t N, const int32_t* kf_hw, int32_t E, const int32_t* edges,
@@ -462,11 +464,11 @@ mslam_status mslam_plan_create_ex(int32_t N, const int32_t* kf_hw, int32_t E, co
       (o.match_block_w != 4 && o.match_block_w != 8 && o.match_block_w != 16 && o.match_block_w != 32 &&
        o.match_block_w != 64 && o.match_block_w != 128 && o.match_block_w != 256) ||
       o.lin_form < 0 || o.lin_form > 2 || (o.solve_form != 0 && o.solve_form != 1) ||
-      (o.match_form != 0 && o.match_form != 1)) {
+      (o.match_form != 0 && o.match_form != 1) || o.match_ppt < 1 || o.match_ppt > 4) {
     set_error("plan options: lin_tile %d (multiple of %d in [1024, 65536]), lin_blocks_per_sm %d (0..32), "
               "match_block_w %d (4, 8, ..., 256), lin_form %d (0, 1 or 2), solve_form %d (0 or 1), match_form %d "
-              "(0 or 1)", o.lin_tile, kLinThreads, o.lin_blocks_per_sm, o.match_block_w, o.lin_form, o.solve_form,
-              o.match_form);
+              "(0 or 1), match_ppt %d (1..4)", o.lin_tile, kLinThreads, o.lin_blocks_per_sm, o.match_block_w,
+              o.lin_form, o.solve_form, o.match_form, o.match_ppt);
     if (out) *out = nullptr;
     return MSLAM_ERR_ARG;
   }
@@ -486,6 +488,7 @@ mslam_status mslam_plan_create_ex(int32_t N, const int32_t* kf_hw, int32_t E, co
   P->solve_form = o.solve_form;
   P->wait_limit = o.wait_limit;
   P->match_form = o.match_form;
+  P->match_ppt = o.match_ppt;
   P->match_bx = o.match_block_w;
   P->match_by = kMatchThreads / o.match_block_w;
   P->N = N;
@@ -545,7 +548,8 @@ mslam_status mslam_plan_create_ex(int32_t N, const int32_t* kf_hw, int32_t E, co
     }
     d.tile_end = (int32_t)P->tiles.size();
     d.mblock_begin = P->n_mblocks;
-    P->n_mblocks += ((W + P->match_bx - 1) / P->match_bx) * ((H + P->match_by - 1) / P->match_by);
+    const int bh = P->match_by * P->match_ppt;  // rows of a match block
+    P->n_mblocks += ((W + P->match_bx - 1) / P->match_bx) * ((H + bh - 1) / bh);
     P->dedges.push_back(d);
   }
   P->order.assign(N, -1);

@@ -66,11 +66,12 @@ def test_match_parity_tiny(M, tiny_wl, dtype, match_form):
     qr = q_r[both].astype(np.float32 if dtype == torch.float32 else np.float16).astype(np.float64)
     rtol = 2e-6 if dtype == torch.float32 else 1e-3
     assert np.abs(qg - qr).max() <= rtol * np.abs(qr).max()
-    if match_form == 1:
-        # a score does not depend on which warp group its query fell in
-        plan8 = M.Plan(ws.kf_hw.numpy(), ws.edges.numpy(), opts={"match_form": 1, "match_block_w": 8})
-        idx8, q8 = gpu_match(M, plan8, P, wd)
-        assert torch.equal(idx8, idx_g) and torch.equal(q8, q_g)
+    # launch shapes change no result: block width and query pixels per thread
+    # (for the tensor-core form also the warp groups a query falls in)
+    for opts in ({"match_block_w": 8}, {"match_ppt": 2}, {"match_block_w": 64, "match_ppt": 3}):
+        plan_b = M.Plan(ws.kf_hw.numpy(), ws.edges.numpy(), opts=dict(opts, match_form=match_form))
+        idx_b, q_b = gpu_match(M, plan_b, P, wd)
+        assert torch.equal(idx_b, idx_g) and torch.equal(q_b, q_g), opts
 
 
 def test_match_forms_and_init_agree(M, tiny_wl):

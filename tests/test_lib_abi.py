@@ -150,7 +150,8 @@ def test_plan_opts_struct_layout(L):
     from paper_2412_12392_gb300 import _lib
     o = _lib.PlanOpts()
     L.mslam_default_plan_opts(C.byref(o))
-    assert C.sizeof(o) == 28 and _lib.PlanOpts.match_form.offset == 20 and _lib.PlanOpts.wait_limit.offset == 24
+    assert C.sizeof(o) == 32 and _lib.PlanOpts.match_form.offset == 20 and _lib.PlanOpts.wait_limit.offset == 28
+    assert o.match_ppt == 1
     assert o.wait_limit == 0 and o.lin_form == 0 and o.solve_form == 0 and o.match_form == 0
     # every wait limit is accepted: < 0 gives up at once (for the timeout tests), 0 is the default
     for wl in (-1, 0, 1, 1 << 24):

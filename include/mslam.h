@@ -165,7 +165,7 @@ typedef struct {
                           grouped and their windows scored together on the tensor cores (FP16 storage and
                           win_radius 3 only; other cases use form 0).  Same decisions up to the FP32
                           summation order of the scores. */
-  int32_t match_ppt;   /* query pixels per thread of mslam_match, 1..4 (default 1): a block of
+  int32_t match_ppt;   /* query pixels per thread of mslam_match, 1 or 2 (default 1): a block of
                           match_block_w x (256 / match_block_w) threads covers match_ppt times as many
                           rows, each thread taking its queries 256 / match_block_w rows apart */
   int32_t wait_limit;  /* polls of every bounded device wait on an asynchronous copy (the streamed
@@ -236,6 +236,9 @@ mslam_status mslam_ray_image(mslam_dtype dt, int64_t n_pix, const void* X, void*
  * memory); d in {16, 24, 32}, 16-byte aligned; Q_ref, Q_qry [P]; init_idx [P]
  * int32 or NULL; outputs idx_out [P] int32 (m within the reference image,
  * -1 = invalid) and q_out [P] (dt; 0 where invalid).
+ * n_valid, n_unique: [E] int32 or both NULL: the keyframe-criterion counts
+ * of Sec. 3.4 (those of mslam_match_stats) taken in the matching epilogue
+ * for the edges matched (other entries untouched); they need the workspace.
  * workspace: NULL, or >= mslam_workspace_bytes(plan, MSLAM_OP_MATCH) bytes,
  * 256-byte aligned: the call then first writes the unit rays psi(X_ref) of
  * the edges' reference pixels there (a1 as an image of float4, FP32, the same
@@ -248,8 +251,8 @@ mslam_status mslam_ray_image(mslam_dtype dt, int64_t n_pix, const void* X, void*
 mslam_status mslam_match(const mslam_params* p, const mslam_plan* plan, mslam_dtype dt, int32_t d,
                          const void* X_ref, const void* X_qry, const void* D_ref, const void* D_qry,
                          const void* Q_ref, const void* Q_qry, const int32_t* init_idx, int32_t* idx_out,
-                         void* q_out, int32_t edge_begin, int32_t edge_end, void* workspace, size_t ws_bytes,
-                         uint32_t flags, void* stream);
+                         void* q_out, int32_t* n_valid, int32_t* n_unique, int32_t edge_begin, int32_t edge_end,
+                         void* workspace, size_t ws_bytes, uint32_t flags, void* stream);
 
 /* Descriptor layout for mslam_match: D [n_pix, d] row-major (the natural
  * layout a network writes) -> the chunk-planar layout, c = 16 bytes of

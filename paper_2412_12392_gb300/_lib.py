@@ -83,8 +83,8 @@ SIGNATURES = {
     "mslam_plan_offsets": ([vp, vp, vp], None),
     "mslam_plan_stats": ([vp, vp, vp], None),
     "mslam_workspace_bytes": ([vp, i32], sz),
-    "mslam_match": ([vp, vp, C.c_int, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, i32, vp, sz, u32, vp],
-                    C.c_int),
+    "mslam_match": ([vp, vp, C.c_int, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, i32, vp, sz, u32,
+                     vp], C.c_int),
     "mslam_gn_linearize": ([vp, vp, C.c_int, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, u32, vp], C.c_int),
     "mslam_gn_linearize_noalloc": ([vp, vp, C.c_int, vp, vp, vp, vp, vp, vp, vp, vp, u32, vp], C.c_int),
     "mslam_gn_pack": ([vp, vp, C.c_int, vp, vp, vp, vp, sz, vp], C.c_int),

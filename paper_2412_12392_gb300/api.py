@@ -155,11 +155,14 @@ def chunk_descriptors(D: torch.Tensor, out: Optional[torch.Tensor] = None, p0: i
 
 
 def match(plan: Plan, params: Params, X_ref, X_qry, D_ref, D_qry, Q_ref, Q_qry, init_idx=None, idx_out=None,
-          q_out=None, edge_range: Tuple[int, int] = (-1, -1), per_edge: bool = False, workspace=None):
+          q_out=None, edge_range: Tuple[int, int] = (-1, -1), per_edge: bool = False, workspace=None,
+          counts: Optional[Tuple[torch.Tensor, torch.Tensor]] = None):
     """mslam_match (Sec. 3.2): returns (idx int32 [P], q [P]).  D_ref and
     D_qry are chunk-planar [d / c, P, c] (see chunk_descriptors).
     workspace: the ray-image workspace (MSLAM_OP_MATCH; allocated when None),
-    or False to normalise the rays at the taps instead (same result)."""
+    or False to normalise the rays at the taps instead (same result).
+    counts: (n_valid, n_unique) int32 [E] tensors that receive the Sec. 3.4
+    keyframe counts of the matched edges, taken in the matching epilogue."""
     dt = X_ref.dtype
     if dt not in DTYPES:
         raise ValueError(f"unsupported storage dtype {dt}")
@@ -182,9 +185,15 @@ def match(plan: Plan, params: Params, X_ref, X_qry, D_ref, D_qry, Q_ref, Q_qry, 
     if workspace is None:
         workspace = plan.workspace(_lib.MSLAM_OP_MATCH)
     ws_ptr, ws_n = (None, 0) if workspace is False else (workspace.data_ptr(), workspace.numel())
+    nv = nu = None
+    if counts is not None:
+        nv, nu = counts
+        _need(nv, "n_valid", torch.int32, plan.E)
+        _need(nu, "n_unique", torch.int32, plan.E)
     check(lib().mslam_match(C.byref(params), plan.handle, DTYPES[dt], d, X_ref.data_ptr(), X_qry.data_ptr(),
                             D_ref.data_ptr(), D_qry.data_ptr(), Q_ref.data_ptr(), Q_qry.data_ptr(),
-                            _ptr(init_idx), idx_out.data_ptr(), q_out.data_ptr(), int(edge_range[0]),
+                            _ptr(init_idx), idx_out.data_ptr(), q_out.data_ptr(), _ptr(nv), _ptr(nu),
+                            int(edge_range[0]),
                             int(edge_range[1]), ws_ptr, ws_n, _lib.MSLAM_FLAG_PER_EDGE if per_edge else 0,
                             _stream(X_ref.device)), "mslam_match")
     return idx_out, q_out

@@ -167,6 +167,33 @@ __device__ __forceinline__ void lm_iterate(const T* __restrict__ Xr_e, const flo
 // that each window row is unrolled with branch-free bounds (an out-of-image
 // candidate reads a clamped pixel and scores -inf, which never wins, exactly
 // as if it were skipped); kR = 0 takes the radius from the parameters.
+// Keyframe-criterion counts (Sec. 3.4) taken in the matching epilogue: a
+// valid match of edge e sets bit bit_off(e) + m of `bits` (its reference
+// pixel) and adds to n_valid[e].  bit_off(e) = 32 ceil(e_off[e] / 32) + 32 e
+// starts every edge on its own 32-bit word, so that calls on edge ranges
+// never share a word.  bits == nullptr: no counts.
+struct MatchStats {
+  uint32_t* bits;
+  int32_t* n_valid;
+  int e_begin, e_end, block_base;  // the launch's edge range and first block (to find a block's edge)
+};
+__host__ __device__ __forceinline__ int64_t stats_bit_off(int64_t off_e, int e) {
+  return ((off_e + 31) / 32) * 32 + 32 * (int64_t)e;
+}
+__device__ __forceinline__ int match_block_edge(const PlanView& pv, int gb, int e_begin, int e_end);
+__device__ __forceinline__ void stats_epilogue(const PlanView& pv, const MatchStats& st, int64_t off_e, int m,
+                                               bool ok) {
+  if (!st.bits) return;
+  const int e = match_block_edge(pv, st.block_base + blockIdx.x, st.e_begin, st.e_end);
+  if (ok) {
+    const int64_t b = stats_bit_off(off_e, e) + m;
+    atomicOr(st.bits + (b >> 5), 1u << (b & 31));
+  }
+  const unsigned am = __activemask();
+  const unsigned bal = __ballot_sync(am, ok);
+  if ((threadIdx.x & 31) == __ffs(am) - 1 && bal) atomicAdd(st.n_valid + e, __popc(bal));
+}
+
 // Edge of match block gb: the last edge in [e_begin, e_end) whose first
 // block <= gb.
 __device__ __forceinline__ int match_block_edge(const PlanView& pv, int gb, int e_begin, int e_end) {
@@ -181,7 +208,8 @@ __device__ __forceinline__ int match_block_edge(const PlanView& pv, int gb, int 
 
 // The per-query matching (a1-a3) of query pixel (u, v) of edge ed.
 template <typename T, int D, int kR>
-__device__ __forceinline__ void match_query(const PlanView& pv, const MatchConst& mc, const DevEdge& ed, int u, int v,
+__device__ __forceinline__ void match_query(const PlanView& pv, const MatchConst& mc, const DevEdge& ed, int u,
+                                            int v, const MatchStats& st,
                                             const T* __restrict__ Xr, const T* __restrict__ Xq,
                                             const T* __restrict__ Dr, const T* __restrict__ Dq,
                                             const T* __restrict__ Qr, const T* __restrict__ Qq,
@@ -264,25 +292,27 @@ __device__ __forceinline__ void match_query(const PlanView& pv, const MatchConst
   const bool ok = finite3(y) && dist <= mc.max_rel * sqrtf(nx2);
   out_idx[o + n] = ok ? m : -1;
   stf(out_q + o + n, ok ? sqrtf(ldf(Qr + o + m) * ldf(Qq + o + n)) : 0.0f);
+  stats_epilogue(pv, st, o, m, ok);
 }
 
 // A block covers match_bx x (match_by * match_ppt) query pixels: each thread
 // takes match_ppt queries, match_by rows apart (plan option match_ppt).
-template <typename T, int D, int kR>
-__global__ void __launch_bounds__(kMatchThreads) match_kernel(
+template <typename T, int D, int kR, int kPPT>
+__global__ void __launch_bounds__(kMatchThreads, 4) match_kernel(
     PlanView pv, MatchConst mc, const T* __restrict__ Xr, const T* __restrict__ Xq, const T* __restrict__ Dr,
     const T* __restrict__ Dq, const T* __restrict__ Qr, const T* __restrict__ Qq, const int32_t* __restrict__ init,
     int32_t* __restrict__ out_idx, T* __restrict__ out_q, int e_begin, int e_end, int block_base,
-    const float4* __restrict__ R4) {
+    const float4* __restrict__ R4, MatchStats st) {
   const int gb = block_base + blockIdx.x;
   const DevEdge ed = pv.edges[match_block_edge(pv, gb, e_begin, e_end)];
   const int local = gb - ed.mblock_begin;
-  const int bx = pv.match_bx, by = pv.match_by, bh = by * pv.match_ppt;
+  const int bx = pv.match_bx, by = pv.match_by;
   const int nbx = (ed.W + bx - 1) / bx;
   const int u = (local % nbx) * bx + (threadIdx.x % bx);
-  const int v0 = (local / nbx) * bh + (threadIdx.x / bx);
-  for (int k = 0; k < pv.match_ppt; ++k)
-    match_query<T, D, kR>(pv, mc, ed, u, v0 + k * by, Xr, Xq, Dr, Dq, Qr, Qq, init, out_idx, out_q, R4);
+  const int v0 = (local / nbx) * (by * kPPT) + (threadIdx.x / bx);
+#pragma unroll 1
+  for (int k = 0; k < kPPT; ++k)
+    match_query<T, D, kR>(pv, mc, ed, u, v0 + k * by, st, Xr, Xq, Dr, Dq, Qr, Qq, init, out_idx, out_q, R4);
 }
 
 // ----------------------------------------------- tensor-core window form
@@ -409,8 +439,8 @@ __device__ __forceinline__ void tc_window_level(const uint32_t* __restrict__ Dr3
 }
 
 template <int D>
-__device__ __forceinline__ void match_tc_query(const PlanView& pv, const MatchConst& mc, const DevEdge& ed, int u,
-                                               int v, const __half* __restrict__ Xr, const __half* __restrict__ Xq,
+__device__ __forceinline__ void match_tc_query(const PlanView& pv, const MatchConst& mc, const DevEdge& ed,
+                                               int u, int v, const MatchStats& st, const __half* __restrict__ Xr, const __half* __restrict__ Xq,
                                                const __half* __restrict__ Dr, const __half* __restrict__ Dq,
                                                const __half* __restrict__ Qr, const __half* __restrict__ Qq,
                                                const int32_t* __restrict__ init, int32_t* __restrict__ out_idx,
@@ -455,6 +485,7 @@ __device__ __forceinline__ void match_tc_query(const PlanView& pv, const MatchCo
   const bool ok = finite3(y) && dist <= mc.max_rel * sqrtf(nx2);
   out_idx[o + n] = ok ? m : -1;
   stf(out_q + o + n, ok ? sqrtf(ldf(Qr + o + m) * ldf(Qq + o + n)) : 0.0f);
+  stats_epilogue(pv, st, o, m, ok);
 }
 
 // The matching kernel with the tensor-core window (FP16 storage, radius 3):
@@ -466,7 +497,8 @@ __global__ void __launch_bounds__(kMatchThreads) match_tc_kernel(
     PlanView pv, MatchConst mc, const __half* __restrict__ Xr, const __half* __restrict__ Xq,
     const __half* __restrict__ Dr, const __half* __restrict__ Dq, const __half* __restrict__ Qr,
     const __half* __restrict__ Qq, const int32_t* __restrict__ init, int32_t* __restrict__ out_idx,
-    __half* __restrict__ out_q, int e_begin, int e_end, int block_base, const float4* __restrict__ R4) {
+    __half* __restrict__ out_q, int e_begin, int e_end, int block_base, const float4* __restrict__ R4,
+    MatchStats st) {
   const int gb = block_base + blockIdx.x;
   const DevEdge ed = pv.edges[match_block_edge(pv, gb, e_begin, e_end)];
   const int local = gb - ed.mblock_begin;
@@ -475,38 +507,71 @@ __global__ void __launch_bounds__(kMatchThreads) match_tc_kernel(
   const int u = (local % nbx) * bx + (threadIdx.x % bx);
   const int v0 = (local / nbx) * bh + (threadIdx.x / bx);
   for (int k = 0; k < pv.match_ppt; ++k)  // the same count in every lane: the window levels stay warp-collective
-    match_tc_query<D>(pv, mc, ed, u, v0 + k * by, Xr, Xq, Dr, Dq, Qr, Qq, init, out_idx, out_q, R4);
+    match_tc_query<D>(pv, mc, ed, u, v0 + k * by, st, Xr, Xq, Dr, Dq, Qr, Qq, init, out_idx, out_q, R4);
 }
 
 template <typename T, int D>
 static void launch_match(const PlanView& pv, const MatchConst& mc, const void* Xr, const void* Xq, const void* Dr,
                          const void* Dq, const void* Qr, const void* Qq, const int32_t* init, int32_t* out_idx,
-                         void* out_q, int e0, int e1, int b0, int nblocks, bool tc, float4* R4, cudaStream_t s) {
+                         void* out_q, int e0, int e1, int b0, int nblocks, bool tc, float4* R4, MatchStats st,
+                         cudaStream_t s) {
+  st.e_begin = e0;
+  st.e_end = e1;
+  st.block_base = b0;
   if constexpr (std::is_same<T, __half>::value) {
     if (tc && mc.radius == 3) {
       match_tc_kernel<D><<<nblocks, kMatchThreads, 0, s>>>(
           pv, mc, static_cast<const __half*>(Xr), static_cast<const __half*>(Xq), static_cast<const __half*>(Dr),
           static_cast<const __half*>(Dq), static_cast<const __half*>(Qr), static_cast<const __half*>(Qq), init, out_idx,
-          static_cast<__half*>(out_q), e0, e1, b0, R4);
+          static_cast<__half*>(out_q), e0, e1, b0, R4, st);
       return;
     }
   }
-  auto k = mc.radius == 3 ? match_kernel<T, D, 3> : match_kernel<T, D, 0>;
+  auto k = mc.radius == 3 ? (pv.match_ppt == 2 ? match_kernel<T, D, 3, 2> : match_kernel<T, D, 3, 1>)
+                           : (pv.match_ppt == 2 ? match_kernel<T, D, 0, 2> : match_kernel<T, D, 0, 1>);
   k<<<nblocks, kMatchThreads, 0, s>>>(pv, mc, static_cast<const T*>(Xr), static_cast<const T*>(Xq),
                                      static_cast<const T*>(Dr), static_cast<const T*>(Dq),
                                      static_cast<const T*>(Qr), static_cast<const T*>(Qq), init, out_idx,
-                                     static_cast<T*>(out_q), e0, e1, b0, R4);
+                                     static_cast<T*>(out_q), e0, e1, b0, R4, st);
 }
 
 }  // namespace mslam
 
 using namespace mslam;
 
+namespace mslam {
+// Distinct reference pixels of edges [e0, e0 + gridDim.x): popcount of each
+// edge's word-aligned bit range of the fused epilogue's bitmap.
+__global__ void __launch_bounds__(256) stats_count_fused_kernel(PlanView pv, const uint32_t* __restrict__ bits,
+                                                                int32_t* __restrict__ n_unique, int e0) {
+  const int e = e0 + blockIdx.x;
+  const DevEdge ed = pv.edges[e];
+  const int64_t b0 = stats_bit_off(ed.off_e, e), n = (int64_t)ed.H * ed.W;
+  const int64_t w0 = b0 >> 5, nw = (n + 31) >> 5;
+  int cnt = 0;
+  for (int64_t k = threadIdx.x; k < nw; k += blockDim.x) {
+    uint32_t v = bits[w0 + k];
+    if (k == nw - 1 && (n & 31)) v &= (1u << (n & 31)) - 1u;
+    cnt += __popc(v);
+  }
+  __shared__ int sw[8];
+  for (int off = 16; off > 0; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < 8; ++w) t += sw[w];
+    n_unique[e] = t;
+  }
+}
+}  // namespace mslam
+
 extern "C" mslam_status mslam_match(const mslam_params* p, const mslam_plan* plan, mslam_dtype dt, int32_t d,
                                     const void* X_ref, const void* X_qry, const void* D_ref, const void* D_qry,
                                     const void* Q_ref, const void* Q_qry, const int32_t* init_idx, int32_t* idx_out,
-                                    void* q_out, int32_t edge_begin, int32_t edge_end, void* workspace,
-                                    size_t ws_bytes, uint32_t flags, void* stream) {
+                                    void* q_out, int32_t* n_valid, int32_t* n_unique, int32_t edge_begin,
+                                    int32_t edge_end, void* workspace, size_t ws_bytes, uint32_t flags,
+                                    void* stream) {
   if (!p || !check_plan_uploaded(plan)) {
     if (!p) set_error("params is NULL");
     return MSLAM_ERR_ARG;
@@ -565,9 +630,28 @@ extern "C" mslam_status mslam_match(const mslam_params* p, const mslam_plan* pla
               mslam_workspace_bytes(plan, MSLAM_OP_MATCH));
     return MSLAM_ERR_ARG;
   }
+  if ((n_valid != nullptr) != (n_unique != nullptr) || (n_valid && !workspace)) {
+    set_error("match: the keyframe counts need both n_valid and n_unique and the workspace");
+    return MSLAM_ERR_ARG;
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const bool tc = plan_match_form(plan) == 1;
   float4* R4 = static_cast<float4*>(workspace);
+  MatchStats stats{nullptr, nullptr, 0, 0, 0};
+  if (n_valid) {
+    // the bitmap follows the ray image; clear the words and counts of edges [e0, e1)
+    const int64_t P_all = plan_edge_off(plan, pv.E);
+    stats.bits = reinterpret_cast<uint32_t*>(static_cast<char*>(workspace) + ((sizeof(float4) * (size_t)P_all + 255) &
+                                                                              ~size_t(255)));
+    stats.n_valid = n_valid;
+    const int64_t w0 = stats_bit_off(plan_edge_off(plan, e0), e0) >> 5;
+    const int64_t w1 = stats_bit_off(plan_edge_off(plan, e1), e1) >> 5;
+    mslam_status st = cuda_check(cudaMemsetAsync(stats.bits + w0, 0, sizeof(uint32_t) * (size_t)(w1 - w0), s),
+                                 "match memset");
+    if (st == MSLAM_OK)
+      st = cuda_check(cudaMemsetAsync(n_valid + e0, 0, sizeof(int32_t) * (size_t)(e1 - e0), s), "match memset");
+    if (st != MSLAM_OK) return st;
+  }
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -589,7 +673,7 @@ extern "C" mslam_status mslam_match(const mslam_params* p, const mslam_plan* pla
     }
 #define MSLAM_MATCH_CASE(TT, DD)                                                                              \
   launch_match<TT, DD>(pv, mc, X_ref, X_qry, D_ref, D_qry, Q_ref, Q_qry, init_idx, idx_out, q_out, a, b, b0, nb, \
-                       tc, R4, s)
+                       tc, R4, stats, s)
     if (dt == MSLAM_F32) {
       if (d == 16) MSLAM_MATCH_CASE(float, 16);
       else if (d == 24) MSLAM_MATCH_CASE(float, 24);
@@ -606,6 +690,7 @@ extern "C" mslam_status mslam_match(const mslam_params* p, const mslam_plan* pla
   } else {
     go(e0, e1);
   }
+  if (n_valid) stats_count_fused_kernel<<<e1 - e0, 256, 0, s>>>(pv, stats.bits, n_unique, e0);
   return cuda_check(cudaGetLastError(), "match launch");
 }
 

@@ -464,10 +464,10 @@ mslam_status mslam_plan_create_ex(int32_t N, const int32_t* kf_hw, int32_t E, co
       (o.match_block_w != 4 && o.match_block_w != 8 && o.match_block_w != 16 && o.match_block_w != 32 &&
        o.match_block_w != 64 && o.match_block_w != 128 && o.match_block_w != 256) ||
       o.lin_form < 0 || o.lin_form > 2 || (o.solve_form != 0 && o.solve_form != 1) ||
-      (o.match_form != 0 && o.match_form != 1) || o.match_ppt < 1 || o.match_ppt > 4) {
+      (o.match_form != 0 && o.match_form != 1) || o.match_ppt < 1 || o.match_ppt > 2) {
     set_error("plan options: lin_tile %d (multiple of %d in [1024, 65536]), lin_blocks_per_sm %d (0..32), "
               "match_block_w %d (4, 8, ..., 256), lin_form %d (0, 1 or 2), solve_form %d (0 or 1), match_form %d "
-              "(0 or 1), match_ppt %d (1..4)", o.lin_tile, kLinThreads, o.lin_blocks_per_sm, o.match_block_w,
+              "(0 or 1), match_ppt %d (1 or 2)", o.lin_tile, kLinThreads, o.lin_blocks_per_sm, o.match_block_w,
               o.lin_form, o.solve_form, o.match_form, o.match_ppt);
     if (out) *out = nullptr;
     return MSLAM_ERR_ARG;
@@ -635,8 +635,10 @@ size_t mslam_workspace_bytes(const mslam_plan* plan, int32_t op) {
     case MSLAM_OP_STATS:
       return align256(sizeof(uint32_t) * (size_t)((plan->e_off.back() + 31) / 32 + 1));
     case MSLAM_OP_MATCH:
-      // the reference ray image: one float4 per edge-pool pixel
-      return align256(sizeof(float) * 4 * (size_t)std::max<int64_t>(plan->e_off.back(), 1));
+      // the reference ray image (one float4 per edge-pool pixel), then the
+      // keyframe-count bitmap (every edge starting on its own 32-bit word)
+      return align256(sizeof(float) * 4 * (size_t)std::max<int64_t>(plan->e_off.back(), 1)) +
+             align256(sizeof(uint32_t) * (size_t)((plan->e_off.back() + 32 * (int64_t)plan->E + 63) / 32 + 1));
     case MSLAM_OP_BACKWARD:
       // the solve's workspace, b and tau (7 N doubles each), per-edge data
       // (32 floats per edge), then for the pose term the step's right-hand

@@ -102,6 +102,38 @@ def test_match_stats_match_oracle(M):
     assert torch.equal(nv, nv2) and torch.equal(nu, nu2)
 
 
+@pytest.mark.parametrize("dtype,match_form,per_edge", [(torch.float32, 0, False), (torch.float16, 0, True),
+                                                        (torch.float16, 1, False)])
+def test_match_fused_counts(M, dtype, match_form, per_edge):
+    """The keyframe counts taken in mslam_match's epilogue equal those of
+    mslam_match_stats on the same matches (exact integers): the whole graph
+    in one call, then two edge ranges in two calls that share the workspace
+    (every edge's bits start on a word of their own), twice in a row."""
+    w = synth.global_graph(N=6, n_pairs=8, H=37, W=53, seed=4).to_storage(dtype)  # ragged: 1961 px per edge
+    wd = w.to("cuda")
+    P = M.default_params()
+    plan = M.Plan(w.kf_hw.numpy(), w.edges.numpy(), opts={"match_form": match_form})
+    Dr, Dq = M.chunk_descriptors(wd.D_ref), M.chunk_descriptors(wd.D_qry)
+    ws = plan.workspace(M._lib.MSLAM_OP_MATCH)
+    nv = torch.full((w.E,), -5, dtype=torch.int32, device="cuda")
+    nu = torch.full((w.E,), -5, dtype=torch.int32, device="cuda")
+    idx, q = M.match(plan, P, wd.X_ref, wd.X_qry, Dr, Dq, wd.Q_ref, wd.Q_qry, workspace=ws, counts=(nv, nu),
+                     per_edge=per_edge)
+    rv, ru = M.match_stats(plan, idx)
+    torch.cuda.synchronize()
+    assert torch.equal(nv, rv) and torch.equal(nu, ru)
+    assert int(rv.sum()) > 0
+    for _ in range(2):
+        nv2 = torch.full_like(nv, -5)
+        nu2 = torch.full_like(nu, -5)
+        half = w.E // 2
+        for r in ((0, half), (half, w.E)):
+            idx2, _ = M.match(plan, P, wd.X_ref, wd.X_qry, Dr, Dq, wd.Q_ref, wd.Q_qry, workspace=ws,
+                              counts=(nv2, nu2), edge_range=r)
+        torch.cuda.synchronize()
+        assert torch.equal(nv2, rv) and torch.equal(nu2, ru)
+
+
 def calibration(w):
     """The generator's pinhole camera (tiny workload: k1 = 0)."""
     H, W = int(w.kf_hw[0, 0]), int(w.kf_hw[0, 1])

@@ -68,7 +68,7 @@ def test_match_parity_tiny(M, tiny_wl, dtype, match_form):
     assert np.abs(qg - qr).max() <= rtol * np.abs(qr).max()
     # launch shapes change no result: block width and query pixels per thread
     # (for the tensor-core form also the warp groups a query falls in)
-    for opts in ({"match_block_w": 8}, {"match_ppt": 2}, {"match_block_w": 64, "match_ppt": 3}):
+    for opts in ({"match_block_w": 8}, {"match_ppt": 2}, {"match_block_w": 64, "match_ppt": 2}):
         plan_b = M.Plan(ws.kf_hw.numpy(), ws.edges.numpy(), opts=dict(opts, match_form=match_form))
         idx_b, q_b = gpu_match(M, plan_b, P, wd)
         assert torch.equal(idx_b, idx_g) and torch.equal(q_b, q_g), opts

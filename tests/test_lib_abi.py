@@ -122,7 +122,7 @@ def test_calls_reject_unuploaded_plan_and_null_args(L):
     L.mslam_default_params(C.byref(prm))
     st = L.mslam_gn_solve(C.byref(prm), p.handle, None, None, None, None, None, None, 0, None)
     assert st == _lib.MSLAM_ERR_ARG and "uploaded" in _lib.last_error()
-    st = L.mslam_match(None, p.handle, 0, 16, *([None] * 9), -1, -1, None, 0, 0, None)
+    st = L.mslam_match(None, p.handle, 0, 16, *([None] * 11), -1, -1, None, 0, 0, None)
     assert st == _lib.MSLAM_ERR_ARG
 
 
@@ -139,7 +139,8 @@ def test_workspace_sizes_of_each_op(L):
     assert p.workspace_bytes(_lib.MSLAM_OP_LINEARIZE) >= part
     assert p.workspace_bytes(99) == 0
     # the match op holds one float4 ray per edge-pool pixel
-    assert p.workspace_bytes(_lib.MSLAM_OP_MATCH) == (16 * 96 * 128 + 255) // 256 * 256
+    bits = (96 * 128 + 32 * 1 + 63) // 32 + 1
+    assert p.workspace_bytes(_lib.MSLAM_OP_MATCH) == (16 * 96 * 128 + 255) // 256 * 256 + (4 * bits + 255) // 256 * 256
     prm = _lib.Params()
     L.mslam_default_params(C.byref(prm))
     st = L.mslam_gn_track(C.byref(prm), p.handle, 1, None, None, 0, 1, None, None, 0, None)

@@ -387,13 +387,13 @@ mslam_status mslam_gn_solve(const mslam_params* p, const mslam_plan* plan, const
                             const float* g_blocks, double* T_wc, double* tau, int32_t* dev_status, void* workspace,
                             size_t ws_bytes, void* stream);
 
-/* Kernel launches one mslam_gn_solve call enqueues on this plan: 4 with the
+/* Kernel launches one mslam_gn_solve call enqueues on this plan: 3 with the
  * mixed-precision solve (plan option solve_form 0: FP32 factorisation of the
  * diagonally scaled system, FP64 iterative refinement; the FP32 factor sits
  * in shared memory, or, when the largest graph's factor does not fit there,
- * every graph's factor is worked on in place in the workspace): its scaling
- * and assembly kernels, the solve, and an FP64 kernel for any graph it
- * declines; 1 (FP64 only) with solve_form 1 or when not even the solve's
+ * every graph's factor is worked on in place in the workspace): its
+ * assembly-and-scaling kernel, the solve, and an FP64 kernel for any graph
+ * it declines; 1 (FP64 only) with solve_form 1 or when not even the solve's
  * vectors and tables fit in shared memory. */
 int32_t mslam_gn_solve_launches(const mslam_plan* plan);
 

@@ -107,7 +107,7 @@ class Plan:
 
     @property
     def solve_launches(self) -> int:
-        """Kernel launches of one gn_solve call (mixed-precision form + FP64 fallback: 2)."""
+        """Kernel launches of one gn_solve call (mslam_gn_solve_launches)."""
         return int(lib().mslam_gn_solve_launches(self._h))
 
     def workspace_bytes(self, op: int) -> int:

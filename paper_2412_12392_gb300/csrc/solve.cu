@@ -593,59 +593,60 @@ __device__ __forceinline__ double asm_sum(const float* __restrict__ H14, const i
 }
 
 // Inputs of the mixed-precision solve, spread over many CTAs (the FP64 rate
-// of a single SM would make this the solve's longest phase).  First the
-// scaling S = D^-1/2 from the assembled diagonal and -g, one thread per
-// unknown; a diagonal entry that is not positive and finite leaves S = NaN,
-// which makes the solve decline the graph.
-__global__ void __launch_bounds__(128) solve_scale_kernel(PlanView pv, const float* __restrict__ H14,
-                                                          const float* __restrict__ g14,
-                                                          const int32_t* __restrict__ dev_status,
-                                                          double* __restrict__ ws) {
-  const int g = blockIdx.y;
-  const DevGraph G = pv.graphs[g];
-  if (dev_status[g] > 0 || G.m == 0) return;  // the solve kernels skip these graphs too
-  const int n7 = 7 * G.m, k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n7) return;
-  const int32_t* I = pv.ints;
-  double* scl = ws + G.ws_mixed + (size_t)G.n_blocks * 28;
-  const int p = k / 7, a = k % 7;
-  const double d = asm_sum(H14, I + G.off_asm, I + G.off_asment, p, a, a);
-  scl[k] = (d > 0.0 && isfinite(d)) ? rsqrt_newton(d) : __longlong_as_double(0x7ff8000000000000LL);
-  const int32_t* gasm_ptr = I + G.off_gasm;
-  const int32_t* gasment = I + G.off_gasment;
-  double sg = 0.0;
-  const int j1 = __ldg(gasm_ptr + p + 1);
-#pragma unroll 4
-  for (int j = __ldg(gasm_ptr + p); j < j1; ++j) {
-    const int code = __ldg(gasment + j), edge = code >> 1, side = code & 1;
-    sg += (double)__ldg(g14 + (size_t)edge * 14 + 7 * side + a);
-  }
-  scl[n7 + k] = -sg;
+// of a single SM would make this the solve's longest phase), one thread per
+// element of the padded 7 x 8 blocks: every block element in FP64 (kept for
+// the residuals) and the scaled FP32 factor input S H S (unit diagonal),
+// with S = D^-1/2 from the assembled diagonal (each thread forms the two
+// entries of S it needs); the padding threads of the diagonal blocks write
+// S and -g for their unknown.  A diagonal entry that is not positive and
+// finite gives S = NaN, which makes the solve decline the graph.
+__device__ __forceinline__ double jacobi_scale(const float* __restrict__ H14, const int32_t* __restrict__ asm_ptr,
+                                               const int32_t* __restrict__ asment, int p, int a) {
+  const double d = asm_sum(H14, asm_ptr, asment, p, a, a);
+  return (d > 0.0 && isfinite(d)) ? rsqrt_newton(d) : __longlong_as_double(0x7ff8000000000000LL);
 }
 
-// Then every block element in FP64 (kept for the residuals) and the scaled
-// FP32 factor input S H S (unit diagonal), one thread per element.
 __global__ void __launch_bounds__(64) solve_assemble_kernel(PlanView pv, const float* __restrict__ H14,
+                                                            const float* __restrict__ g14,
                                                             const int32_t* __restrict__ dev_status,
                                                             double* __restrict__ ws) {
   const int g = blockIdx.y;
   const DevGraph G = pv.graphs[g];
-  if (dev_status[g] > 0 || G.m == 0) return;
+  if (dev_status[g] > 0 || G.m == 0) return;  // the solve kernels skip these graphs too
   const int nb = G.n_blocks;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nb * kLfBlock) return;
   const int32_t* I = pv.ints;
+  const int32_t* asm_ptr = I + G.off_asm;
+  const int32_t* asment = I + G.off_asment;
   float* Lf = reinterpret_cast<float*>(ws + G.ws_mixed);
-  const double* scl = ws + G.ws_mixed + (size_t)nb * 28;
   const int b = t / kLfBlock, e = t % kLfBlock, r = e / 8, c = e % 8;
   if (c == 7) {
     Lf[t] = 0.0f;
+    if (b < G.m) {
+      // diagonal block b = unknown block b: S and -g of unknown 7 b + r
+      const int n7 = 7 * G.m, k = 7 * b + r;
+      double* scl = ws + G.ws_mixed + (size_t)nb * 28;
+      scl[k] = jacobi_scale(H14, asm_ptr, asment, b, r);
+      const int32_t* gasm_ptr = I + G.off_gasm;
+      const int32_t* gasment = I + G.off_gasment;
+      double sg = 0.0;
+      const int j1 = __ldg(gasm_ptr + b + 1);
+#pragma unroll 4
+      for (int j = __ldg(gasm_ptr + b); j < j1; ++j) {
+        const int code = __ldg(gasment + j), edge = code >> 1, side = code & 1;
+        sg += (double)__ldg(g14 + (size_t)edge * 14 + 7 * side + r);
+      }
+      scl[n7 + k] = -sg;
+    }
     return;
   }
-  const double h = asm_sum(H14, I + G.off_asm, I + G.off_asment, b, r, c);
+  const double h = asm_sum(H14, asm_ptr, asment, b, r, c);
   ws[G.ws_off + 49 * (size_t)b + 7 * r + c] = h;
   const int br = __ldg(I + G.off_blkrow + b), bc = __ldg(I + G.off_blkcol + b);
-  Lf[t] = (float)(h * scl[7 * br + r] * scl[7 * bc + c]);
+  const double sr = jacobi_scale(H14, asm_ptr, asment, br, r);
+  const double sc = jacobi_scale(H14, asm_ptr, asment, bc, c);
+  Lf[t] = (float)(h * sr * sc);
 }
 
 // Deterministic sum of the four 7-lane groups of a warp into lanes 0..6
@@ -698,7 +699,8 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
   double* bv = xv + n7;                         // right-hand side -g
   float* yv = reinterpret_cast<float*>(bv + n7);  // work vector
   float* ivf = yv + n7;                           // reciprocal pivots
-  int* sI = reinterpret_cast<int*>(ivf + n7);
+  float* Linv = ivf + n7;                         // inverses of the diagonal factor blocks, 7 x 8 per column
+  int* sI = reinterpret_cast<int*>(Linv + 8 * n7);
   const int seg1 = G.off_trip - G.off_pose, seg2 = G.int_end - G.off_lev;
   for (int t = tid; t < seg1; t += nth) sI[t] = __ldg(pv.ints + G.off_pose + t);
   for (int t = tid; t < seg2; t += nth) sI[seg1 + t] = __ldg(pv.ints + G.off_lev + t);
@@ -820,6 +822,26 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
     return;
   }
 
+  // ---- explicit inverses of the diagonal factor blocks: thread (p, k)
+  // solves L_pp x = e_k, so that each block step of the triangular solves
+  // below is a 7 x 7 product (seven independent sums) instead of a chain of
+  // seven dependent shuffles
+  for (int t = tid; t < n7; t += nth) {
+    const int p = t / 7, k = t % 7;
+    const float* D = Lf + kLfBlock * (size_t)p;
+    float x[7];
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+      float v = (j == k) ? 1.0f : 0.0f;
+#pragma unroll
+      for (int i = 0; i < j; ++i) v = (i >= k) ? fmaf(-D[8 * j + i], x[i], v) : v;
+      x[j] = (j >= k) ? v * ivf[7 * p + j] : 0.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < 7; ++j) Linv[56 * p + 8 * j + k] = x[j];
+  }
+  __syncthreads();
+
   // ---- iterative refinement
   for (int t = tid; t < n7; t += nth) yv[t] = (float)(scl[t] * bv[t]);
   __syncthreads();
@@ -843,15 +865,12 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
           part = ((ps[0] + ps[1]) + (ps[2] + ps[3])) + ((ps[4] + ps[5]) + ps[6]);
         }
         const float tot = sum_groups(part);
-        float s = (lane < 7) ? yv[7 * p + lane] - tot : 0.0f;
-        const float* D = Lf + kLfBlock * (size_t)p;
+        const float s = (lane < 7) ? yv[7 * p + lane] - tot : 0.0f;
+        // y_p = L_pp^-1 s
+        const float* Li = Linv + 56 * p + 8 * (lane < 7 ? lane : 0);
         float out = 0.0f;
 #pragma unroll
-        for (int j = 0; j < 7; ++j) {
-          const float yj = __shfl_sync(0xffffffffu, s, j) * ivf[7 * p + j];
-          if (lane == j) out = yj;
-          if (lane > j && lane < 7) s = fmaf(-D[8 * lane + j], yj, s);
-        }
+        for (int k = 0; k < 7; ++k) out = fmaf(Li[k], __shfl_sync(0xffffffffu, s, k), out);
         if (lane < 7) yv[7 * p + lane] = out;
         __syncwarp();
       }
@@ -863,7 +882,6 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
       const int q0 = lev_ptr[l], q1 = lev_ptr[l + 1];
       for (int qi = q0 + warp; qi < q1; qi += nwarps) {
         const int p = lev_cols[qi];
-        const float* D = Lf + kLfBlock * (size_t)p;
         float part = 0.0f;
         if (lane < 28) {
           float ps[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -876,14 +894,12 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
           part = ((ps[0] + ps[1]) + (ps[2] + ps[3])) + ((ps[4] + ps[5]) + ps[6]);
         }
         const float tot = sum_groups(part);
-        float s = (lane < 7) ? yv[7 * p + lane] - tot : 0.0f;
+        const float s = (lane < 7) ? yv[7 * p + lane] - tot : 0.0f;
+        // z_p = L_pp^-T s
+        const float* Li = Linv + 56 * p + (lane < 7 ? lane : 0);
         float xl = 0.0f;
 #pragma unroll
-        for (int k = 6; k >= 0; --k) {
-          const float xk = __shfl_sync(0xffffffffu, s, k) * ivf[7 * p + k];
-          if (lane == k) xl = xk;
-          if (lane < k) s = fmaf(-D[8 * k + lane], xk, s);
-        }
+        for (int k = 0; k < 7; ++k) xl = fmaf(Li[8 * k], __shfl_sync(0xffffffffu, s, k), xl);
         if (lane < 7) yv[7 * p + lane] = xl;
         __syncwarp();
       }
@@ -1123,10 +1139,9 @@ extern "C" mslam_status mslam_gn_solve(const mslam_params* p, const mslam_plan* 
     int32_t* handled = reinterpret_cast<int32_t*>(static_cast<char*>(workspace) +
                                                   ((sizeof(double) * std::max<int64_t>(plan_solve_ws_doubles(plan), 1) + 255) &
                                                    ~size_t(255)));
-    const int elems = (int)plan_max_mixed_elems(plan), n7 = 7 * plan_max_unknown_blocks(plan);
-    solve_scale_kernel<<<dim3(std::max(1, (n7 + 127) / 128), pv.G), 128, 0, s>>>(pv, H_blocks, g_blocks,
-                                                                                 dev_status, ws);
-    solve_assemble_kernel<<<dim3(std::max(1, (elems + 63) / 64), pv.G), 64, 0, s>>>(pv, H_blocks, dev_status, ws);
+    const int elems = (int)plan_max_mixed_elems(plan);
+    solve_assemble_kernel<<<dim3(std::max(1, (elems + 63) / 64), pv.G), 64, 0, s>>>(pv, H_blocks, g_blocks,
+                                                                                     dev_status, ws);
     if (global_factor)
       solve_mixed_kernel<true><<<pv.G, kMixThreads, mixed, s>>>(pv, sc, T_wc, tau, dev_status, ws, handled);
     else
@@ -1140,7 +1155,7 @@ extern "C" mslam_status mslam_gn_solve(const mslam_params* p, const mslam_plan* 
 
 extern "C" int32_t mslam_gn_solve_launches(const mslam_plan* plan) {
   if (!plan) return 0;
-  return (mixed_smem_bytes(plan) > 0 && plan_view(plan).E > 0) ? 4 : 1;
+  return (mixed_smem_bytes(plan) > 0 && plan_view(plan).E > 0) ? 3 : 1;
 }
 
 // Factor every graph's system and write tau = -H^-1 g without updating poses

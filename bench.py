@@ -353,13 +353,17 @@ class Arm:
 
     def launches_per_step(self) -> int:
         """Kernels of this library launched per step: the ray image and match; (batched) pack;
-        per iteration the relative-pose, tile and finalize kernels of the
-        linearisation (per edge in the plain form) and the solve."""
+        per iteration the linearisation (one fused launch for the register
+        pipeline; else the relative-pose, tile and finalize kernels; per edge
+        in the plain form) and the solve's launches."""
         E = self.plan.E
         sl = self.plan.solve_launches
         if self.per_edge:
             return 2 * E + self.iters * (1 + 2 * E + sl)
-        return 2 + 1 + self.iters * (3 + sl)
+        # the register pipeline (lin_form 1, and every FP32 or non-ray case)
+        # forms the relative poses and finalizes the edges in its one launch
+        regs = self.plan.opts.get("lin_form") == 1 or self.q.dtype == torch.float32
+        return 2 + 1 + self.iters * ((1 if regs else 3) + sl)
 
 
 def pick_pipelined_shapes(arm, world, steps: int = 5, warmup: int = 3):

@@ -119,16 +119,15 @@ def make_workload(args, rank: int, device, hw=None):
 
 
 # DRAM bytes (read + write) per query pixel of one batched matching launch,
-# from one ncu capture of match_kernel<__half, 24> (8 keyframes, 24 edges,
-# 512x384: 296,574,464 bytes for 4,718,592 query pixels), scaled to a launch
-# by its query pixels.  Remove an entry when its kernel changes.
-NCU_DRAM_BYTES_PER_QUERY_PX = {("match", 2, 24): 296574464 / 4718592}
+# from one ncu capture of match_kernel<__half, 24, 3, 2> (8 keyframes, 24
+# edges, 512x384, the FP32 ray image: 344,586,240 bytes for 4,718,592 query
+# pixels), scaled to a launch by its query pixels.  Remove an entry when its
+# kernel changes.
+NCU_DRAM_BYTES_PER_QUERY_PX = {("match", 2, 24): 344586240 / 4718592}
 # DRAM bytes per matched pixel of one packed linearisation launch, FP16
-# records, scaled to a launch by its matches: lin_stream_kernel (32768-record
-# tiles: 26,246,144 bytes for 1,637,856 matches) and lin_packed_kernel
-# (16384-record tiles, 2 CTAs per SM: 26,247,168 bytes, median of three
-# launches).
-NCU_DRAM_BYTES_PER_MATCH = {("lin_stream", 2): 26246144 / 1637856, ("lin_packed", 2): 26247168 / 1637856}
+# records, scaled to a launch by its matches (1,637,856 matches in the
+# capture).  Empty until the current kernels are captured.
+NCU_DRAM_BYTES_PER_MATCH = {}
 
 
 def valid_query_pixels(X_qry: torch.Tensor) -> int:

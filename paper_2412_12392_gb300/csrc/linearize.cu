@@ -32,7 +32,11 @@ struct RelPose {
 // T_ij = T_i^-1 T_j of every edge in FP64, stored as float s R and t: one
 // thread per edge, once per linearisation (keeps FP64 out of the tile loop).
 // It also clears the tile counter of the persistent launch that follows.
-__device__ __forceinline__ RelPose rel_pose_of(const PlanView& pv, const double* __restrict__ T_wc, int e) {
+__global__ void rel_pose_kernel(PlanView pv, const double* __restrict__ T_wc, RelPose* __restrict__ out,
+                                int* __restrict__ tile_ctr) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e == 0 && tile_ctr) *tile_ctr = 0;
+  if (e >= pv.E) return;
   const DevEdge ed = pv.edges[e];
   const Sim3d Ti = load_pose(T_wc + 8 * ed.i), Tj = load_pose(T_wc + 8 * ed.j);
   const Sim3d Tij = compose(inverse(Ti), Tj);
@@ -42,15 +46,7 @@ __device__ __forceinline__ RelPose rel_pose_of(const PlanView& pv, const double*
   for (int k = 0; k < 9; ++k) P.R[k] = (float)(Tij.s * R[k]);
   for (int k = 0; k < 3; ++k) P.t[k] = (float)Tij.t[k];
   for (int k = 0; k < 4; ++k) P.pad[k] = 0.0f;
-  return P;
-}
-
-__global__ void rel_pose_kernel(PlanView pv, const double* __restrict__ T_wc, RelPose* __restrict__ out,
-                                int* __restrict__ tile_ctr) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e == 0 && tile_ctr) *tile_ctr = 0;
-  if (e >= pv.E) return;
-  out[e] = rel_pose_of(pv, T_wc, e);
+  out[e] = P;
 }
 
 __device__ __forceinline__ float huber_w(float e, float delta) { return e <= delta ? 1.0f : __fdividef(delta, e); }
@@ -379,116 +375,6 @@ __global__ void __launch_bounds__(kLinThreads, MSLAM_LIN_MINBLOCKS)
   }
 }
 
-// The ray family's relative 7 x 7 system and gradient from its 30
-// structured sums S (FP64): H_tt = S0 I + S[1..6], H_ww = S13 I - S[14..19],
-// H_tw = -[S7..9]x, the scale column S[10..12] and S20, g = S[21..27].
-__device__ void ray_relative_system(const double* S, double Hr[49], double g[7]) {
-  for (int k = 0; k < 49; ++k) Hr[k] = 0.0;
-  const double s2[6] = {S[1], S[2], S[3], S[4], S[5], S[6]};
-  const int sym[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
-  for (int a = 0; a < 3; ++a)
-    for (int b = 0; b < 3; ++b) {
-      Hr[7 * a + b] = (a == b ? S[0] : 0.0) + s2[sym[a][b]];
-      Hr[7 * (3 + a) + 3 + b] = (a == b ? S[13] : 0.0) - S[14 + sym[a][b]];
-    }
-  const double s3x = S[7], s3y = S[8], s3z = S[9];
-  const double tw[9] = {0.0, s3z, -s3y, -s3z, 0.0, s3x, s3y, -s3x, 0.0};
-  for (int a = 0; a < 3; ++a)
-    for (int b = 0; b < 3; ++b) {
-      Hr[7 * a + 3 + b] = tw[3 * a + b];
-      Hr[7 * (3 + b) + a] = tw[3 * a + b];
-    }
-  for (int a = 0; a < 3; ++a) {
-    Hr[7 * a + 6] = S[10 + a];
-    Hr[7 * 6 + a] = S[10 + a];
-  }
-  Hr[48] = S[20];
-  for (int a = 0; a < 7; ++a) g[a] = S[21 + a];
-}
-
-// One block per edge: FP64 sum of the edge's tile partials (four groups of
-// threads take every fourth tile, then the groups' sums are added in a fixed
-// order), then the 14x14.
-constexpr int kFinalizeThreads = 256;
-// The finalize of edge e by the first kFinalizeThreads threads of a block
-// (all of the block's threads must call it).
-__device__ __noinline__ void finalize_edge(const PlanView& pv, const double* __restrict__ T_wc,
-                                          const float* __restrict__ partials,
-                              float* __restrict__ H14, float* __restrict__ g14, double* __restrict__ cost,
-                              int32_t* __restrict__ n_valid, int e, int kind) {
-  const DevEdge ed = pv.edges[e];
-  __shared__ double S[kFamAcc], Sg[kFinalizeThreads / 64][kFamAcc];
-  __shared__ double Hr[49], A[49], C[49], g[7];
-  const int tid = threadIdx.x;
-  const int NA = kind == MSLAM_RES_RAY ? kNumAcc : kFamAcc;
-  {
-    const int a = tid & 63, grp = tid >> 6;
-    if (a < NA && tid < kFinalizeThreads) {
-      double s = 0.0;
-#pragma unroll 8
-      for (int t = ed.tile_begin + grp; t < ed.tile_end; t += kFinalizeThreads / 64)
-        s += (double)partials[(size_t)t * kAccStride + a];
-      Sg[grp][a] = s;
-    }
-  }
-  if (tid == 32) {
-    const Sim3d Ti = load_pose(T_wc + 8 * ed.i);
-    adjoint_of(inverse(Ti), A);
-  }
-  __syncthreads();
-  if (tid < NA) S[tid] = (Sg[0][tid] + Sg[1][tid]) + (Sg[2][tid] + Sg[3][tid]);
-  __syncthreads();
-  if (tid == 0 && kind != MSLAM_RES_RAY) {
-    // other families: the 28 upper-triangle sums, then g, cost and count
-    int t = 0;
-    for (int a = 0; a < 7; ++a)
-      for (int b = a; b < 7; ++b, ++t) Hr[7 * a + b] = Hr[7 * b + a] = S[t];
-    for (int a = 0; a < 7; ++a) g[a] = S[28 + a];
-    cost[e] = S[35];
-    if (n_valid) n_valid[e] = (int32_t)S[36];
-  }
-  if (tid == 0 && kind == MSLAM_RES_RAY) {
-    ray_relative_system(S, Hr, g);
-    cost[e] = S[28];
-    if (n_valid) n_valid[e] = (int32_t)S[29];
-  }
-  __syncthreads();
-  // C = Hr A, then B = A^T C
-  if (tid < 49) {
-    const int r = tid / 7, c = tid % 7;
-    double s = 0.0;
-    for (int k = 0; k < 7; ++k) s += Hr[7 * r + k] * A[7 * k + c];
-    C[tid] = s;
-  }
-  __syncthreads();
-  if (tid < 49) {
-    const int r = tid / 7, c = tid % 7;
-    double s = 0.0;
-    for (int k = 0; k < 7; ++k) s += A[7 * k + r] * C[7 * k + c];
-    const float b = (float)s;
-    float* Hb = H14 + (size_t)e * 196;
-    Hb[14 * r + c] = b;
-    Hb[14 * (7 + r) + 7 + c] = b;
-    Hb[14 * r + 7 + c] = -b;
-    Hb[14 * (7 + r) + c] = -b;
-  }
-  if (tid >= 49 && tid < 56) {
-    const int r = tid - 49;
-    double s = 0.0;
-    for (int k = 0; k < 7; ++k) s += A[7 * k + r] * g[k];
-    g14[(size_t)e * 14 + r] = (float)(-s);
-    g14[(size_t)e * 14 + 7 + r] = (float)s;
-  }
-}
-
-__global__ void __launch_bounds__(kFinalizeThreads) lin_finalize_kernel(PlanView pv, const double* __restrict__ T_wc,
-                                                          const float* __restrict__ partials,
-                                                          float* __restrict__ H14, float* __restrict__ g14,
-                                                          double* __restrict__ cost, int32_t* __restrict__ n_valid,
-                                                          int e_begin, int kind) {
-  finalize_edge(pv, T_wc, partials, H14, g14, cost, n_valid, e_begin + blockIdx.x, kind);
-}
-
 // ---------------------------------------------------------------- packed form
 // The matches are fixed during the Gauss-Newton loop, so the gather of the
 // canonical points at the matches is done once: mslam_gn_pack writes, for
@@ -611,53 +497,24 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(PlanView pv, float q
   }
 }
 
-// The whole linearisation in one launch (the persistent batched form): the
-// block that starts a tile of a new edge forms the edge's relative pose in
-// FP64 from T_wc (rel_pose_of), and the block that completes an edge's last
-// tile sums the edge's tile partials and writes its 14 x 14 block
-// (finalize_edge), counted on edge_done (zeroed by the caller before the
-// launch).  T_wc == nullptr: relative poses from `rel`, no finalize.
-struct LinFused {
-  const double* T_wc;
-  float* H14;
-  float* g14;
-  double* cost;
-  int32_t* n_valid;
-  int32_t* edge_done;
-};
-
 template <typename T, int kKind>
 __global__ void __launch_bounds__(kLinThreads, MSLAM_PACKED_MINBLOCKS) lin_packed_kernel(PlanView pv, LinConst lc,
                                                                    const RelPose* __restrict__ rel,
                                                                    const uint4* __restrict__ recs,
                                                                    const int32_t* __restrict__ counts,
                                                                    float* __restrict__ partials, int tile_begin,
-                                                                   int tile_end, int* __restrict__ tile_ctr,
-                                                                   LinFused fz) {
+                                                                   int tile_end, int* __restrict__ tile_ctr) {
   constexpr int NA = FamilyAcc<kKind>::N;
   __shared__ float red[kLinThreads / 32][kFamAcc];
-  __shared__ int s_tile, s_last, s_edge;
-  __shared__ float s_rel[12];
+  __shared__ int s_tile;
   const int tid = threadIdx.x;
   constexpr int W = PackRec<T>::kWords;
   constexpr int U = MSLAM_PACKED_UNROLL;
-  if (tid == 0) s_edge = -1;
   for (int tile = next_tile(&s_tile, tile_ctr, tile_begin, -1); tile < tile_end;
        tile = next_tile(&s_tile, tile_ctr, tile_begin, tile)) {
     const DevTile tl = pv.tiles[tile];
     RelPose P;
-    if (fz.T_wc) {
-      // next_tile ended with a barrier, so s_edge is the previous tile's
-      if (tid == 0 && s_edge != tl.edge) {
-        const RelPose Q = rel_pose_of(pv, fz.T_wc, tl.edge);
-        for (int k = 0; k < 9; ++k) s_rel[k] = Q.R[k];
-        for (int k = 0; k < 3; ++k) s_rel[9 + k] = Q.t[k];
-        s_edge = tl.edge;
-      }
-      __syncthreads();
-      for (int k = 0; k < 9; ++k) P.R[k] = s_rel[k];
-      for (int k = 0; k < 3; ++k) P.t[k] = s_rel[9 + k];
-    } else {
+    {
       const float4* src = reinterpret_cast<const float4*>(rel + tl.edge);
       float4 a = __ldg(src), b = __ldg(src + 1), c = __ldg(src + 2);
       P.R[0] = a.x; P.R[1] = a.y; P.R[2] = a.z; P.R[3] = a.w;
@@ -738,19 +595,6 @@ __global__ void __launch_bounds__(kLinThreads, MSLAM_PACKED_MINBLOCKS) lin_packe
         for (int a = 0; a < NA; ++a) acc[a] += bacc[a];
       }
       reduce_store<NA>(acc, red, partials, tile);
-    }
-    if (fz.T_wc) {
-      // the tile's partial was stored by threads < NA before the last
-      // barrier: fence it, then count the tile on its edge
-      if (tid < NA) __threadfence();
-      __syncthreads();
-      const DevEdge ed = pv.edges[tl.edge];
-      if (tid == 0) s_last = atomicAdd(fz.edge_done + tl.edge, 1) == ed.tile_end - ed.tile_begin - 1;
-      __syncthreads();
-      if (s_last) {
-        __threadfence();  // every tile partial of the edge is visible
-        finalize_edge(pv, fz.T_wc, partials, fz.H14, fz.g14, fz.cost, fz.n_valid, tl.edge, kKind);
-      }
     }
   }
 }
@@ -1202,6 +1046,108 @@ __global__ void __launch_bounds__(kWarpStreamThreads, 1)
   }
 }
 
+// The ray family's relative 7 x 7 system and gradient from its 30
+// structured sums S (FP64): H_tt = S0 I + S[1..6], H_ww = S13 I - S[14..19],
+// H_tw = -[S7..9]x, the scale column S[10..12] and S20, g = S[21..27].
+__device__ void ray_relative_system(const double* S, double Hr[49], double g[7]) {
+  for (int k = 0; k < 49; ++k) Hr[k] = 0.0;
+  const double s2[6] = {S[1], S[2], S[3], S[4], S[5], S[6]};
+  const int sym[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      Hr[7 * a + b] = (a == b ? S[0] : 0.0) + s2[sym[a][b]];
+      Hr[7 * (3 + a) + 3 + b] = (a == b ? S[13] : 0.0) - S[14 + sym[a][b]];
+    }
+  const double s3x = S[7], s3y = S[8], s3z = S[9];
+  const double tw[9] = {0.0, s3z, -s3y, -s3z, 0.0, s3x, s3y, -s3x, 0.0};
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      Hr[7 * a + 3 + b] = tw[3 * a + b];
+      Hr[7 * (3 + b) + a] = tw[3 * a + b];
+    }
+  for (int a = 0; a < 3; ++a) {
+    Hr[7 * a + 6] = S[10 + a];
+    Hr[7 * 6 + a] = S[10 + a];
+  }
+  Hr[48] = S[20];
+  for (int a = 0; a < 7; ++a) g[a] = S[21 + a];
+}
+
+// One block per edge: FP64 sum of the edge's tile partials (four groups of
+// threads take every fourth tile, then the groups' sums are added in a fixed
+// order), then the 14x14.
+constexpr int kFinalizeThreads = 256;
+__global__ void __launch_bounds__(kFinalizeThreads) lin_finalize_kernel(PlanView pv, const double* __restrict__ T_wc,
+                                                          const float* __restrict__ partials,
+                                                          float* __restrict__ H14, float* __restrict__ g14,
+                                                          double* __restrict__ cost, int32_t* __restrict__ n_valid,
+                                                          int e_begin, int kind) {
+  const int e = e_begin + blockIdx.x;
+  const DevEdge ed = pv.edges[e];
+  __shared__ double S[kFamAcc], Sg[kFinalizeThreads / 64][kFamAcc];
+  __shared__ double Hr[49], A[49], C[49], g[7];
+  const int tid = threadIdx.x;
+  const int NA = kind == MSLAM_RES_RAY ? kNumAcc : kFamAcc;
+  {
+    const int a = tid & 63, grp = tid >> 6;
+    if (a < NA) {
+      double s = 0.0;
+#pragma unroll 8
+      for (int t = ed.tile_begin + grp; t < ed.tile_end; t += kFinalizeThreads / 64)
+        s += (double)partials[(size_t)t * kAccStride + a];
+      Sg[grp][a] = s;
+    }
+  }
+  if (tid == 32) {
+    const Sim3d Ti = load_pose(T_wc + 8 * ed.i);
+    adjoint_of(inverse(Ti), A);
+  }
+  __syncthreads();
+  if (tid < NA) S[tid] = (Sg[0][tid] + Sg[1][tid]) + (Sg[2][tid] + Sg[3][tid]);
+  __syncthreads();
+  if (tid == 0 && kind != MSLAM_RES_RAY) {
+    // other families: the 28 upper-triangle sums, then g, cost and count
+    int t = 0;
+    for (int a = 0; a < 7; ++a)
+      for (int b = a; b < 7; ++b, ++t) Hr[7 * a + b] = Hr[7 * b + a] = S[t];
+    for (int a = 0; a < 7; ++a) g[a] = S[28 + a];
+    cost[e] = S[35];
+    if (n_valid) n_valid[e] = (int32_t)S[36];
+  }
+  if (tid == 0 && kind == MSLAM_RES_RAY) {
+    ray_relative_system(S, Hr, g);
+    cost[e] = S[28];
+    if (n_valid) n_valid[e] = (int32_t)S[29];
+  }
+  __syncthreads();
+  // C = Hr A, then B = A^T C
+  if (tid < 49) {
+    const int r = tid / 7, c = tid % 7;
+    double s = 0.0;
+    for (int k = 0; k < 7; ++k) s += Hr[7 * r + k] * A[7 * k + c];
+    C[tid] = s;
+  }
+  __syncthreads();
+  if (tid < 49) {
+    const int r = tid / 7, c = tid % 7;
+    double s = 0.0;
+    for (int k = 0; k < 7; ++k) s += A[7 * k + r] * C[7 * k + c];
+    const float b = (float)s;
+    float* Hb = H14 + (size_t)e * 196;
+    Hb[14 * r + c] = b;
+    Hb[14 * (7 + r) + 7 + c] = b;
+    Hb[14 * r + 7 + c] = -b;
+    Hb[14 * (7 + r) + c] = -b;
+  }
+  if (tid >= 49 && tid < 56) {
+    const int r = tid - 49;
+    double s = 0.0;
+    for (int k = 0; k < 7; ++k) s += A[7 * k + r] * g[k];
+    g14[(size_t)e * 14 + r] = (float)(-s);
+    g14[(size_t)e * 14 + 7 + r] = (float)s;
+  }
+}
+
 // ------------------------------------------------------------- tracking
 // One Gauss-Newton iteration of tracking problems per launch, one block per
 // tile: the block forms its edge's relative pose from T_wc, accumulates the
@@ -1625,22 +1571,9 @@ extern "C" mslam_status mslam_gn_linearize_packed(const mslam_params* p, const m
       static_cast<const char*>(packed) + pack_bytes(pv.n_tiles, pv.lin_tile, dt) -
       (((size_t)pv.n_tiles * sizeof(int32_t) + 255) & ~size_t(255)));
   int* ctr = tile_counter(rel, pv.E);
-  int32_t* edge_done = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(ctr) + 256);
+  rel_pose_kernel<<<(pv.E + 127) / 128, 128, 0, s>>>(pv, T_wc, rel, ctr);
   const size_t stream_smem = (size_t)kStreamStages * kStreamChunkBytes;
   const PackedForm form = packed_form(p, plan, dt);
-  // the register pipeline's persistent launch forms the relative poses and
-  // finalizes the edges itself (one launch); the other launches use the
-  // relative-pose and finalize kernels
-  const bool fused = form == kFormRegs && !(flags & MSLAM_FLAG_PER_EDGE);
-  LinFused fz{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  if (fused) {
-    fz = LinFused{T_wc, H_blocks, g_blocks, cost, n_valid, edge_done};
-    const mslam_status stm =
-        cuda_check(cudaMemsetAsync(ctr, 0, 256 + sizeof(int32_t) * (size_t)pv.E, s), "gn_linearize_packed memset");
-    if (stm != MSLAM_OK) return stm;
-  } else {
-    rel_pose_kernel<<<(pv.E + 127) / 128, 128, 0, s>>>(pv, T_wc, rel, ctr);
-  }
   if (form != kFormRegs) {
     mslam_status st2 = form == kFormBlockStream
                            ? stream_kernel_setup<kFormBlockStream>(lin_stream_kernel, stream_smem)
@@ -1665,9 +1598,9 @@ extern "C" mslam_status mslam_gn_linearize_packed(const mslam_params* p, const m
         return;
       }
       if (dt == MSLAM_F32)
-        lin_packed_kernel<float, kK><<<grid, kLinThreads, 0, s>>>(pv, lc, rel, recs, counts, partials, t0, t1, c, fz);
+        lin_packed_kernel<float, kK><<<grid, kLinThreads, 0, s>>>(pv, lc, rel, recs, counts, partials, t0, t1, c);
       else
-        lin_packed_kernel<__half, kK><<<grid, kLinThreads, 0, s>>>(pv, lc, rel, recs, counts, partials, t0, t1, c, fz);
+        lin_packed_kernel<__half, kK><<<grid, kLinThreads, 0, s>>>(pv, lc, rel, recs, counts, partials, t0, t1, c);
     };
     if (flags & MSLAM_FLAG_PER_EDGE) {
       for (int e = 0; e < pv.E; ++e) {
@@ -1685,9 +1618,7 @@ extern "C" mslam_status mslam_gn_linearize_packed(const mslam_params* p, const m
         grid = std::max(1, sms);  // one streaming CTA per SM
       }
       launch(std::min(pv.n_tiles, grid), 0, pv.n_tiles, ctr);
-      if (!fused)
-        lin_finalize_kernel<<<pv.E, kFinalizeThreads, 0, s>>>(pv, T_wc, partials, H_blocks, g_blocks, cost, n_valid, 0,
-                                                              kK);
+      lin_finalize_kernel<<<pv.E, kFinalizeThreads, 0, s>>>(pv, T_wc, partials, H_blocks, g_blocks, cost, n_valid, 0, kK);
     }
   });
   return cuda_check(cudaGetLastError(), "gn_linearize_packed launch");

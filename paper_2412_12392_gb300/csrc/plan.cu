@@ -624,9 +624,8 @@ size_t mslam_workspace_bytes(const mslam_plan* plan, int32_t op) {
       // tile partials, then one completed-tile counter per edge
       return lin_partials_bytes((int)plan->tiles.size()) + align256(sizeof(int32_t) * std::max(plan->E, 1));
     case MSLAM_OP_LINEARIZE:
-      // tile partials, relative poses, the tile counter, per-edge completed-tile counters
-      return lin_partials_bytes((int)plan->tiles.size()) + align256(sizeof(float) * 16 * std::max(plan->E, 1)) + 256 +
-             align256(sizeof(int32_t) * std::max(plan->E, 1));
+      // tile partials, relative poses, the tile counter
+      return lin_partials_bytes((int)plan->tiles.size()) + align256(sizeof(float) * 16 * std::max(plan->E, 1)) + 256;
     case MSLAM_OP_SOLVE:  // per-graph FP64 blocks and vectors, then one flag per graph
       return align256(sizeof(double) * std::max<int64_t>(plan->solve_ws_doubles, 1)) +
              align256(sizeof(int32_t) * std::max<size_t>(plan->graphs.size(), 1));

@@ -151,3 +151,62 @@ def test_three_unrolled_steps_fp16(M):
     entry, summed over the three steps): the bar for them is 1e-3."""
     w = synth.differentiation(H=24, W=32)
     check_against_fd(M, w, torch.float16, 3, n_x=8, n_q=4, poses=(5,), seed=1, tol=1e-3, tol_pose=2e-4)
+
+
+def test_three_unrolled_steps_full_size_directional(M):
+    """The differentiation workload at full size (32 keyframes, 96 edges,
+    512 x 384, FP16 storage): the gradient of L = sum W * T_3 + c sum_k E_g(T_k)
+    through three chained steps, with respect to every canonical point and
+    every pose, along a random direction v, against the central difference
+    of the oracle's own three Gauss-Newton steps (FP64, dense Cholesky) on
+    the dequantised values: <grad, v> = (L(x + h v) - L(x - h v)) / 2h.
+    Pose directions are tangent (T_k -> Exp(h v_k) T_k)."""
+    from paper_2412_12392_gb300.autograd import gn_unrolled
+    w = synth.differentiation(device="cuda").to_storage(torch.float16)
+    P = M.default_params()
+    par = M.params_dict(P)
+    plan = M.Plan(w.kf_hw.numpy(), w.edges.numpy(), opts={"lin_form": 1})
+    rng = np.random.default_rng(11)
+    Wt = rng.normal(size=(w.N, 8)) * 0.1
+    c = 0.3
+    X = w.X_canon.clone().requires_grad_(True)
+    T0 = w.T_init.cuda().clone().requires_grad_(True)
+    idx = w.gt_match
+    q = w.Q_qry
+    T, taus, costs = gn_unrolled(X, q, T0, plan, P, idx, 3)
+    L = (T * torch.from_numpy(Wt).cuda()).sum() + c * sum(costs)
+    L.backward()
+    gX = X.grad.double().cpu().numpy()
+    gT = T0.grad.cpu().numpy()
+    # the oracle's L: three steps of its Gauss-Newton (costs at the start of each)
+    X64 = w.X_canon.double().cpu().numpy()
+    T64 = w.T_init.numpy().copy()
+    idx_c, q_c = idx.cpu(), q.cpu()
+
+    def L_ref(Xv, Tv):
+        st, T3, hist, done = oracle.gauss_newton(w.N, w.edges.numpy(), w.kf_off.numpy(), w.e_off.numpy(), Xv, idx_c,
+                                                 q_c, Tv, 3, **par)
+        assert st == 0 and done == 3
+        return float((Wt * T3).sum()) + c * float(hist.sum())
+
+    L0 = L_ref(X64, T64)
+    assert abs(float(L) - L0) <= 1e-4 * abs(L0), (float(L), L0)
+    # direction over the points
+    vX = rng.normal(size=X64.shape)
+    h = 1e-5
+    fd = (L_ref(X64 + h * vX, T64) - L_ref(X64 - h * vX, T64)) / (2 * h)
+    an = float((gX * vX).sum())
+    print(f"full size, points: <grad, v> {an:.6e}, central difference {fd:.6e}, rel {abs(an - fd) / abs(fd):.2e}")
+    assert abs(an - fd) <= 2e-3 * abs(fd)
+    # direction over the poses (tangent), the fixed first pose included
+    vT = rng.normal(size=(w.N, 7)) * np.r_[0.01, 0.01, 0.01, 0.002, 0.002, 0.002, 0.002]
+    ht = 1e-4
+    Tp, Tm, dT = T64.copy(), T64.copy(), np.zeros_like(T64)
+    for k in range(w.N):
+        Tp[k] = oracle.sim3_mul(oracle.sim3_exp(ht * vT[k]), T64[k])
+        Tm[k] = oracle.sim3_mul(oracle.sim3_exp(-ht * vT[k]), T64[k])
+        dT[k] = (Tp[k] - Tm[k]) / (2 * ht)
+    fdT = (L_ref(X64, Tp) - L_ref(X64, Tm)) / (2 * ht)
+    anT = float((gT * dT).sum())
+    print(f"full size, poses: <grad, v> {anT:.6e}, central difference {fdT:.6e}, rel {abs(anT - fdT) / abs(fdT):.2e}")
+    assert abs(anT - fdT) <= 2e-3 * abs(fdT)

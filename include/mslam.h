@@ -161,17 +161,23 @@ typedef struct {
                           refinement to the FP64 solution (default; graphs it declines go to the FP64
                           factorisation), 1 = FP64 factorisation only */
   int32_t match_form;  /* refinement windows of mslam_match: 0 = each query thread scores its own window
-                          on the FP32 pipe (default), 1 = the queries of a warp that share window rows are
-                          grouped and their windows scored together on the tensor cores (FP16 storage and
-                          win_radius 3 only; other cases use form 0).  Same decisions up to the FP32
-                          summation order of the scores. */
+                          on the FP32 pipe, reading the candidates from global memory (default), 1 = the
+                          queries of a warp that share window rows are grouped and their windows scored
+                          together on the tensor cores (same decisions up to the FP32 summation order of
+                          the scores), 2 = per level, the block copies the box that holds its queries'
+                          windows (at most 48 KB of descriptors) into shared memory with bulk
+                          asynchronous copies and each query scores its window from there (from global
+                          memory when its window falls outside the box): results bit-identical to form
+                          0.  Forms 1 and 2 need FP16 storage and win_radius 3; other cases use form 0. */
   int32_t match_ppt;   /* query pixels per thread of mslam_match, 1 or 2 (default 1): a block of
                           match_block_w x (256 / match_block_w) threads covers match_ppt times as many
                           rows, each thread taking its queries 256 / match_block_w rows apart */
   int32_t wait_limit;  /* polls of every bounded device wait on an asynchronous copy (the streamed
-                          linearisation forms) before it gives up: 0 = the default 2^24 (about a
-                          second), > 0 = that many; < 0 = give up at once without issuing any copy (so
-                          that nothing is in flight), which exercises the timeout path in tests */
+                          linearisation forms, the staged match form) before it gives up: 0 = the
+                          default 2^24 (about a second), > 0 = that many; < 0 = give up at once without
+                          issuing any copy (so that nothing is in flight), which exercises the timeout
+                          path in tests.  A staged match block whose wait gives up reads that level's
+                          windows from global memory and stages nothing more: the result is unchanged */
 } mslam_plan_opts;
 void mslam_default_plan_opts(mslam_plan_opts* opts);
 mslam_status mslam_plan_create_ex(int32_t N, const int32_t* kf_hw, int32_t E, const int32_t* edges,

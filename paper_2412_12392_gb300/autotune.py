@@ -49,8 +49,8 @@ def autotune(kf_hw, edges, graph_of_kf, params, X_ref, X_qry, D_ref, D_qry, Q_re
     report = {"match_ms": {}, "lin_ms": {}, "pack_ms": {}}
     best_w, best_t = None, float("inf")
     idx = q = None
-    # the tensor-core window form exists for FP16 storage
-    forms = (0, 1) if X_ref.dtype == torch.float16 else (0,)
+    # the tensor-core and staged window forms exist for FP16 storage
+    forms = (0, 1, 2) if X_ref.dtype == torch.float16 else (0,)
     for wdt, form, ppt in itertools.product(match_widths, forms, match_ppts):
         plan = api.Plan(kf_hw, edges, graph_of_kf, opts={"match_block_w": wdt, "match_form": form,
                                                         "match_ppt": ppt})

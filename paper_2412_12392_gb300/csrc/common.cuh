@@ -385,7 +385,7 @@ size_t pack_bytes(int n_tiles, int lin_tile, mslam_dtype dt);
 int plan_lin_blocks_per_sm(const mslam_plan* plan);
 int plan_lin_form(const mslam_plan* plan);  // 0 block-streamed, 1 register pipeline, 2 warp-streamed
 int plan_solve_form(const mslam_plan* plan);  // 0 mixed precision, 1 FP64 only
-int plan_match_form(const mslam_plan* plan);  // 0 per-query window, 1 tensor-core grouped window
+int plan_match_form(const mslam_plan* plan);  // 0 per-query window, 1 tensor-core grouped, 2 staged window
 int64_t plan_edge_off(const mslam_plan* plan, int e);  // edge-pool offset of edge e (e = E: the pool size)
 int64_t plan_max_mixed_bytes(const mslam_plan* plan);  // shared memory of the mixed-precision solve
 int64_t plan_max_mixed_bytes_nofactor(const mslam_plan* plan);  // the same without the FP32 factor
@@ -399,5 +399,44 @@ void plan_edge_tiles(const mslam_plan* plan, int e, int* t0, int* t1);
 void plan_edge_mblocks(const mslam_plan* plan, int e, int* b0, int* b1);
 // Largest per-graph numeric solve workspace (doubles).
 int64_t plan_max_graph_doubles(const mslam_plan* plan);
+
+// Shared-memory barriers and bulk asynchronous copies (the copy engine
+// writes shared memory and counts its bytes on an mbarrier).
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for the phase of `parity` to complete; false after `polls`
+// non-blocking polls (the plan's wait limit, about a second by default).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t polls) {
+  for (uint32_t it = 0; it < polls; ++it)
+    if (mbar_test_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "{\n .reg .u64 g;\n cvta.to.global.u64 g, %1;\n"
+      " cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [g], %2, [%3];\n}\n" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
 
 }  // namespace mslam

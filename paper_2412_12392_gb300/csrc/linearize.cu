@@ -633,35 +633,6 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c
 __device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Waits for the phase of `parity` to complete; false after `polls`
-// non-blocking polls (the plan's wait limit, about a second by default).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t polls) {
-  for (uint32_t it = 0; it < polls; ++it)
-    if (mbar_test_wait(bar, parity)) return true;
-  return false;
-}
-
 // A bounded wait gave up: every tile partial of the launch becomes NaN and
 // every graph the launch covers gets MSLAM_ERR_TIMEOUT (the solve skips it).
 __device__ void mark_timeout(const PlanView& pv, float* partials, int32_t* status, int tile_begin, int tile_end,
@@ -671,14 +642,6 @@ __device__ void mark_timeout(const PlanView& pv, float* partials, int32_t* statu
     if (status) status[pv.edges[pv.tiles[t].edge].graph] = MSLAM_ERR_TIMEOUT;
   }
 }
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "{\n .reg .u64 g;\n cvta.to.global.u64 g, %1;\n"
-      " cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [g], %2, [%3];\n}\n" ::"r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
 // Huber weight factor h = min(1, delta / e) of a squared whitened norm, per lane.
 __device__ __forceinline__ float huber_h(float e2, const LinConst& c) {
   return fminf(1.0f, c.delta * rsqrt_ftz(fmaxf(e2, c.delta2)));

@@ -13,6 +13,7 @@
 //   a3  rounding, coarse-to-fine descriptor window argmax (FP32 dot products
 //       in index order), the 3D distance test and q = sqrt(Q_ref Q_qry).
 #include <algorithm>
+#include <climits>
 #include <type_traits>
 
 #include "common.cuh"
@@ -138,24 +139,29 @@ __device__ __forceinline__ void lm_iterate(const T* __restrict__ Xr_e, const flo
     const int64_t t00 = (int64_t)v0 * W + u0;
     const float3 R00 = tap(Xr_e, R4_e, t00), R10 = tap(Xr_e, R4_e, t00 + 1);
     const float3 R01 = tap(Xr_e, R4_e, t00 + W), R11 = tap(Xr_e, R4_e, t00 + W + 1);
+    // every product and sum is rounded where written (explicit fused
+    // multiply-adds, no contraction left to the compiler), so that each form
+    // of the kernel takes the same LM path for the same inputs
     const float ua = 1.0f - a, ub = 1.0f - b;
-    const float3 Ju = make_float3(ub * (R10.x - R00.x) + b * (R11.x - R01.x), ub * (R10.y - R00.y) + b * (R11.y - R01.y),
-                                  ub * (R10.z - R00.z) + b * (R11.z - R01.z));
-    const float3 Jv = make_float3(ua * (R01.x - R00.x) + a * (R11.x - R10.x), ua * (R01.y - R00.y) + a * (R11.y - R10.y),
-                                  ua * (R01.z - R00.z) + a * (R11.z - R10.z));
-    const float w00 = ua * ub, w10 = a * ub, w01 = ua * b, w11 = a * b;
-    const float rx = w00 * R00.x + w10 * R10.x + w01 * R01.x + w11 * R11.x - tg.x;
-    const float ry = w00 * R00.y + w10 * R10.y + w01 * R01.y + w11 * R11.y - tg.y;
-    const float rz = w00 * R00.z + w10 * R10.z + w01 * R01.z + w11 * R11.z - tg.z;
-    const float a00 = Ju.x * Ju.x + Ju.y * Ju.y + Ju.z * Ju.z + lam;
-    const float a01 = Ju.x * Jv.x + Ju.y * Jv.y + Ju.z * Jv.z;
-    const float a11 = Jv.x * Jv.x + Jv.y * Jv.y + Jv.z * Jv.z + lam;
-    const float b0 = -(Ju.x * rx + Ju.y * ry + Ju.z * rz);
-    const float b1 = -(Jv.x * rx + Jv.y * ry + Jv.z * rz);
-    const float det = a00 * a11 - a01 * a01;
+    const float3 Ju = make_float3(fmaf(ub, R10.x - R00.x, __fmul_rn(b, R11.x - R01.x)),
+                                  fmaf(ub, R10.y - R00.y, __fmul_rn(b, R11.y - R01.y)),
+                                  fmaf(ub, R10.z - R00.z, __fmul_rn(b, R11.z - R01.z)));
+    const float3 Jv = make_float3(fmaf(ua, R01.x - R00.x, __fmul_rn(a, R11.x - R10.x)),
+                                  fmaf(ua, R01.y - R00.y, __fmul_rn(a, R11.y - R10.y)),
+                                  fmaf(ua, R01.z - R00.z, __fmul_rn(a, R11.z - R10.z)));
+    const float w00 = __fmul_rn(ua, ub), w10 = __fmul_rn(a, ub), w01 = __fmul_rn(ua, b), w11 = __fmul_rn(a, b);
+    const float rx = fmaf(w11, R11.x, fmaf(w01, R01.x, fmaf(w10, R10.x, fmaf(w00, R00.x, -tg.x))));
+    const float ry = fmaf(w11, R11.y, fmaf(w01, R01.y, fmaf(w10, R10.y, fmaf(w00, R00.y, -tg.y))));
+    const float rz = fmaf(w11, R11.z, fmaf(w01, R01.z, fmaf(w10, R10.z, fmaf(w00, R00.z, -tg.z))));
+    const float a00 = fmaf(Ju.z, Ju.z, fmaf(Ju.y, Ju.y, fmaf(Ju.x, Ju.x, lam)));
+    const float a01 = fmaf(Ju.z, Jv.z, fmaf(Ju.y, Jv.y, __fmul_rn(Ju.x, Jv.x)));
+    const float a11 = fmaf(Jv.z, Jv.z, fmaf(Jv.y, Jv.y, fmaf(Jv.x, Jv.x, lam)));
+    const float b0 = -fmaf(Ju.z, rz, fmaf(Ju.y, ry, __fmul_rn(Ju.x, rx)));
+    const float b1 = -fmaf(Jv.z, rz, fmaf(Jv.y, ry, __fmul_rn(Jv.x, rx)));
+    const float det = fmaf(a00, a11, -__fmul_rn(a01, a01));
     if (det > 0.0f) {
-      pu += (a11 * b0 - a01 * b1) / det;
-      pv_ += (a00 * b1 - a01 * b0) / det;
+      pu = __fadd_rn(pu, __fdiv_rn(fmaf(a11, b0, -__fmul_rn(a01, b1)), det));
+      pv_ = __fadd_rn(pv_, __fdiv_rn(fmaf(a00, b1, -__fmul_rn(a01, b0)), det));
     }
     // clamp (fmaxf/fminf also map a NaN to the image)
     pu = fminf(fmaxf(pu, 0.0f), (float)(W - 1));
@@ -288,7 +294,7 @@ __device__ __forceinline__ void match_query(const PlanView& pv, const MatchConst
   const int m = cv * W + cu;
   const float3 y = ld3(Xr_e, m);
   const float dxv = y.x - x.x, dyv = y.y - x.y, dzv = y.z - x.z;
-  const float dist = sqrtf(dxv * dxv + dyv * dyv + dzv * dzv);
+  const float dist = sqrtf(fmaf(dzv, dzv, fmaf(dyv, dyv, __fmul_rn(dxv, dxv))));
   const bool ok = finite3(y) && dist <= mc.max_rel * sqrtf(nx2);
   out_idx[o + n] = ok ? m : -1;
   stf(out_q + o + n, ok ? sqrtf(ldf(Qr + o + m) * ldf(Qq + o + n)) : 0.0f);
@@ -313,6 +319,226 @@ __global__ void __launch_bounds__(kMatchThreads, 4) match_kernel(
 #pragma unroll 1
   for (int k = 0; k < kPPT; ++k)
     match_query<T, D, kR>(pv, mc, ed, u, v0 + k * by, st, Xr, Xq, Dr, Dq, Qr, Qq, init, out_idx, out_q, R4);
+}
+
+// ------------------------------------------------------ staged window form
+// The refinement windows scored from shared memory (plan option match_form
+// 2; FP16 storage, window radius 3).  Per level, the block takes the
+// bounding box of its active queries' windows (centre +- 3 dil, clipped to
+// the image).  A box of at most kCap pixels is staged whole; a larger one
+// (outlying centres) is cut to at most kBoxW x (kCap / kBoxW) pixels placed
+// around the mean centre.  One warp copies the box row by row for every
+// descriptor chunk with bulk asynchronous copies (the copy engine; the bytes
+// are counted on an mbarrier, waited with the plan's bounded wait).  Every
+// query whose window lies inside the box reads its candidates from shared
+// memory, every other query from global memory, through one generic load
+// whose address selects the space, so that no warp splits into two paths.
+// A staged pixel crosses L1 once per block and level instead of once per
+// window that contains it, and the eight lanes of a quarter-warp read
+// consecutive box pixels (eight different 16-byte bank groups): four
+// wavefronts per 16-byte load of a warp, where the scattered global loads
+// of the per-query form take about eight.  The candidates, the FP32 dot
+// products, their order and the first-maximum rule are those of
+// match_kernel, so the matches are identical.  A wait that gives up (or a
+// negative wait limit) leaves that level's queries on the global loads and
+// stops staging in the block: the result does not change.
+template <int D> struct StagedCfg {
+  static constexpr int kChunks = D / 8;                   // 16-byte chunks of a descriptor
+  static constexpr int kCap = 49152 / (16 * kChunks);     // box pixels in 48 KB of shared memory
+  static constexpr int kBoxW = kCap / 32;                 // widest cut box
+  static constexpr int kSmem = kCap * kChunks * 16;
+};
+
+template <int D, int kPPT>
+__global__ void __launch_bounds__(kMatchThreads, 4) match_staged_kernel(
+    PlanView pv, MatchConst mc, const __half* __restrict__ Xr, const __half* __restrict__ Xq,
+    const __half* __restrict__ Dr, const __half* __restrict__ Dq, const __half* __restrict__ Qr,
+    const __half* __restrict__ Qq, const int32_t* __restrict__ init, int32_t* __restrict__ out_idx,
+    __half* __restrict__ out_q, int e_begin, int e_end, int block_base, const float4* __restrict__ R4,
+    MatchStats st) {
+  using Cfg = StagedCfg<D>;
+  constexpr int NQ = Cfg::kChunks;
+  constexpr int kWarps = kMatchThreads / 32;
+  extern __shared__ __align__(128) uint4 s_desc[];  // [NQ][bh][bw] of the staged box
+  __shared__ uint64_t s_bar;
+  __shared__ int s_red[kWarps][7];  // per warp: min u, max u, min v, max v, count, sum u, sum v
+  __shared__ int s_box[5];          // u0, v0, bw, bh, mode (0 no active query, 1 global only, 2 staged)
+  __shared__ int s_dead;            // a wait gave up: no further staging in this block
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int gb = block_base + blockIdx.x;
+  const DevEdge ed = pv.edges[match_block_edge(pv, gb, e_begin, e_end)];
+  const int local = gb - ed.mblock_begin;
+  const int bx = pv.match_bx, by = pv.match_by;
+  const int W = ed.W, H = ed.H;
+  const int nbx = (W + bx - 1) / bx;
+  const int u = (local % nbx) * bx + (tid % bx);
+  const int v0 = (local / nbx) * (by * kPPT) + (tid / bx);
+  const int64_t o = ed.off_e, HW = (int64_t)H * W;
+  const __half* Xr_e = Xr + 3 * o;
+  const uint4* Dr4 = reinterpret_cast<const uint4*>(Dr);
+  if (tid == 0) {
+    mbar_init(&s_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_dead = pv.wait_polls == 0;  // a negative wait limit: no copy is issued
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  bool pending = false;  // thread 0: a copy whose wait gave up may still be in flight
+#pragma unroll 1
+  for (int k = 0; k < kPPT; ++k) {
+    const int v = v0 + k * by;
+    const int n = v * W + u;
+    bool act = u < W && v < H;
+    float3 x = make_float3(0.0f, 0.0f, 0.0f);
+    float nx2 = 0.0f;
+    int cu = 0, cv = 0;
+    uint4 dq[NQ];
+    if (act) {
+      x = ld3(Xq + 3 * o, n);
+      nx2 = fmaf(x.x, x.x, fmaf(x.y, x.y, x.z * x.z));
+      if (!(finite3(x) && nx2 > 0.0f)) {
+        out_idx[o + n] = -1;
+        stf(out_q + o + n, 0.0f);
+        act = false;
+      }
+    }
+    if (act) {
+      const float inx = rsqrtf(nx2);
+      const float3 tg = make_float3(x.x * inx, x.y * inx, x.z * inx);
+      int p0 = n;
+      if (init) {
+        const int32_t ii = init[o + n];
+        if (ii >= 0 && ii < HW) p0 = ii;
+      }
+      float pu = (float)(p0 % W), pv_ = (float)(p0 / W);
+      lm_iterate(Xr_e, R4 ? R4 + o : nullptr, W, H, tg, mc, pu, pv_);
+      cu = min((int)floorf(pu + 0.5f), W - 1);
+      cv = min((int)floorf(pv_ + 0.5f), H - 1);
+      const uint4* q4 = reinterpret_cast<const uint4*>(Dq);
+#pragma unroll
+      for (int c = 0; c < NQ; ++c) dq[c] = __ldg(q4 + (int64_t)c * pv.P + o + n);
+    }
+#pragma unroll 1
+    for (int lev = 0; lev < mc.n_levels; ++lev) {
+      const int dil = mc.dil[lev], marg = 3 * dil;
+      // the block's bounding box of active centres
+      const unsigned full = 0xffffffffu;
+      const int r0 = __reduce_min_sync(full, act ? cu : INT_MAX);
+      const int r1 = __reduce_max_sync(full, act ? cu : INT_MIN);
+      const int r2 = __reduce_min_sync(full, act ? cv : INT_MAX);
+      const int r3 = __reduce_max_sync(full, act ? cv : INT_MIN);
+      const int r4 = __reduce_add_sync(full, act ? 1 : 0);
+      const int r5 = __reduce_add_sync(full, act ? cu : 0);
+      const int r6 = __reduce_add_sync(full, act ? cv : 0);
+      if (lane == 0) {
+        s_red[wid][0] = r0; s_red[wid][1] = r1; s_red[wid][2] = r2; s_red[wid][3] = r3;
+        s_red[wid][4] = r4; s_red[wid][5] = r5; s_red[wid][6] = r6;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        int umin = INT_MAX, umax = INT_MIN, vmin = INT_MAX, vmax = INT_MIN, cnt = 0, su = 0, sv = 0;
+        for (int w = 0; w < kWarps; ++w) {
+          umin = min(umin, s_red[w][0]); umax = max(umax, s_red[w][1]);
+          vmin = min(vmin, s_red[w][2]); vmax = max(vmax, s_red[w][3]);
+          cnt += s_red[w][4]; su += s_red[w][5]; sv += s_red[w][6];
+        }
+        int mode = cnt == 0 ? 0 : (s_dead ? 1 : 2), bu0 = 0, bv0 = 0, bw = 0, bh = 0;
+        if (mode == 2) {
+          bu0 = max(umin - marg, 0);
+          bv0 = max(vmin - marg, 0);
+          const int bu1 = min(umax + marg, W - 1), bv1 = min(vmax + marg, H - 1);
+          bw = bu1 - bu0 + 1;
+          bh = bv1 - bv0 + 1;
+          if (bw * bh > Cfg::kCap) {  // outlying centres: the largest allowed box around the mean centre
+            bw = min(bw, Cfg::kBoxW);
+            bh = min(bh, Cfg::kCap / bw);
+            bu0 = min(max(su / cnt - bw / 2, bu0), bu1 - bw + 1);
+            bv0 = min(max(sv / cnt - bh / 2, bv0), bv1 - bh + 1);
+          }
+        }
+        s_box[0] = bu0; s_box[1] = bv0; s_box[2] = bw; s_box[3] = bh; s_box[4] = mode;
+      }
+      __syncthreads();
+      const int mode = s_box[4];
+      if (mode == 0) continue;  // no active query in the block: nothing to score
+      const int bu0 = s_box[0], bv0 = s_box[1], bw = s_box[2], bh = s_box[3];
+      bool ok = false;
+      if (mode == 2) {
+        if (wid == 0) {
+          // the box's earlier contents were read through the generic proxy (before the
+          // barriers above); order those reads before the copy engine's writes
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          if (lane == 0) mbar_arrive_tx(&s_bar, (uint32_t)(NQ * bw * bh * 16));
+          __syncwarp();
+          for (int r = lane; r < NQ * bh; r += 32) {
+            const int c = r / bh, row = r - c * bh;
+            bulk_g2s(s_desc + (c * bh + row) * bw, Dr4 + (int64_t)c * pv.P + o + (int64_t)(bv0 + row) * W + bu0,
+                     (uint32_t)(bw * 16), &s_bar);
+          }
+        }
+        if (act || tid == 0) {
+          ok = mbar_wait_bounded(&s_bar, phase, pv.wait_polls);
+          if (!ok) {
+            s_dead = 1;
+            if (tid == 0) pending = true;
+          }
+        }
+        phase ^= 1u;
+      }
+      if (!act) continue;
+      // this query's window inside the box: shared memory, else global memory
+      const bool inside = ok && max(cu - marg, 0) >= bu0 && min(cu + marg, W - 1) < bu0 + bw &&
+                          max(cv - marg, 0) >= bv0 && min(cv + marg, H - 1) < bv0 + bh;
+      // one base pointer per chunk; candidate offsets within the edge image or the box fit in 32 bits
+      const uint4* cb[NQ];
+#pragma unroll
+      for (int c = 0; c < NQ; ++c)
+        cb[c] = inside ? static_cast<const uint4*>(s_desc) + c * bw * bh : Dr4 + (int64_t)c * pv.P + o;
+      const int ox = inside ? bu0 : 0, oy = inside ? bv0 : 0, rs = inside ? bw : W;
+      float best = -INFINITY;
+      int bu = cu, bv = cv;
+#pragma unroll 1
+      for (int dy = -3; dy <= 3; ++dy) {
+        const int vv = cv + dy * dil;
+        const bool vin = (unsigned)vv < (unsigned)H;
+        const int row = (min(max(vv, 0), H - 1) - oy) * rs - ox;
+#pragma unroll
+        for (int dx = -3; dx <= 3; ++dx) {
+          const int uu = cu + dx * dil;
+          const int off = row + min(max(uu, 0), W - 1);
+          float s0 = 0.0f;
+#pragma unroll
+          for (int c = 0; c < NQ; ++c) {
+            const uint4 w4 = cb[c][off];
+            fma_h2(s0, dq[c].x, w4.x);
+            fma_h2(s0, dq[c].y, w4.y);
+            fma_h2(s0, dq[c].z, w4.z);
+            fma_h2(s0, dq[c].w, w4.w);
+          }
+          const float s = (vin && (unsigned)uu < (unsigned)W) ? s0 : -INFINITY;
+          if (s > best) {
+            best = s;
+            bu = uu;
+            bv = vv;
+          }
+        }
+      }
+      cu = bu;
+      cv = bv;
+    }
+    if (act) {
+      const int m = cv * W + cu;
+      const float3 y = ld3(Xr_e, m);
+      const float dxv = y.x - x.x, dyv = y.y - x.y, dzv = y.z - x.z;
+      const float dist = sqrtf(fmaf(dzv, dzv, fmaf(dyv, dyv, __fmul_rn(dxv, dxv))));
+      const bool good = finite3(y) && dist <= mc.max_rel * sqrtf(nx2);
+      out_idx[o + n] = good ? m : -1;
+      stf(out_q + o + n, good ? sqrtf(ldf(Qr + o + m) * ldf(Qq + o + n)) : 0.0f);
+      stats_epilogue(pv, st, o, m, good);
+    }
+  }
+  // a copy whose wait gave up must land before the block's shared memory is released
+  if (tid == 0 && pending) mbar_wait_bounded(&s_bar, phase ^ 1u, pv.wait_polls);
 }
 
 // ----------------------------------------------- tensor-core window form
@@ -481,7 +707,7 @@ __device__ __forceinline__ void match_tc_query(const PlanView& pv, const MatchCo
   const int m = cv * W + cu;
   const float3 y = ld3(Xr_e, m);
   const float dxv = y.x - x.x, dyv = y.y - x.y, dzv = y.z - x.z;
-  const float dist = sqrtf(dxv * dxv + dyv * dyv + dzv * dzv);
+  const float dist = sqrtf(fmaf(dzv, dzv, fmaf(dyv, dyv, __fmul_rn(dxv, dxv))));
   const bool ok = finite3(y) && dist <= mc.max_rel * sqrtf(nx2);
   out_idx[o + n] = ok ? m : -1;
   stf(out_q + o + n, ok ? sqrtf(ldf(Qr + o + m) * ldf(Qq + o + n)) : 0.0f);
@@ -513,14 +739,23 @@ __global__ void __launch_bounds__(kMatchThreads) match_tc_kernel(
 template <typename T, int D>
 static void launch_match(const PlanView& pv, const MatchConst& mc, const void* Xr, const void* Xq, const void* Dr,
                          const void* Dq, const void* Qr, const void* Qq, const int32_t* init, int32_t* out_idx,
-                         void* out_q, int e0, int e1, int b0, int nblocks, bool tc, float4* R4, MatchStats st,
+                         void* out_q, int e0, int e1, int b0, int nblocks, int form, float4* R4, MatchStats st,
                          cudaStream_t s) {
   st.e_begin = e0;
   st.e_end = e1;
   st.block_base = b0;
   if constexpr (std::is_same<T, __half>::value) {
-    if (tc && mc.radius == 3) {
+    if (form == 1 && mc.radius == 3) {
       match_tc_kernel<D><<<nblocks, kMatchThreads, 0, s>>>(
+          pv, mc, static_cast<const __half*>(Xr), static_cast<const __half*>(Xq), static_cast<const __half*>(Dr),
+          static_cast<const __half*>(Dq), static_cast<const __half*>(Qr), static_cast<const __half*>(Qq), init, out_idx,
+          static_cast<__half*>(out_q), e0, e1, b0, R4, st);
+      return;
+    }
+    if (form == 2 && mc.radius == 3) {
+      auto ks = pv.match_ppt == 2 ? match_staged_kernel<D, 2> : match_staged_kernel<D, 1>;
+      cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, StagedCfg<D>::kSmem);
+      ks<<<nblocks, kMatchThreads, StagedCfg<D>::kSmem, s>>>(
           pv, mc, static_cast<const __half*>(Xr), static_cast<const __half*>(Xq), static_cast<const __half*>(Dr),
           static_cast<const __half*>(Dq), static_cast<const __half*>(Qr), static_cast<const __half*>(Qq), init, out_idx,
           static_cast<__half*>(out_q), e0, e1, b0, R4, st);
@@ -635,7 +870,7 @@ extern "C" mslam_status mslam_match(const mslam_params* p, const mslam_plan* pla
     return MSLAM_ERR_ARG;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const bool tc = plan_match_form(plan) == 1;
+  const int form = plan_match_form(plan);
   float4* R4 = static_cast<float4*>(workspace);
   MatchStats stats{nullptr, nullptr, 0, 0, 0};
   if (n_valid) {
@@ -673,7 +908,7 @@ extern "C" mslam_status mslam_match(const mslam_params* p, const mslam_plan* pla
     }
 #define MSLAM_MATCH_CASE(TT, DD)                                                                              \
   launch_match<TT, DD>(pv, mc, X_ref, X_qry, D_ref, D_qry, Q_ref, Q_qry, init_idx, idx_out, q_out, a, b, b0, nb, \
-                       tc, R4, stats, s)
+                       form, R4, stats, s)
     if (dt == MSLAM_F32) {
       if (d == 16) MSLAM_MATCH_CASE(float, 16);
       else if (d == 24) MSLAM_MATCH_CASE(float, 24);

@@ -47,9 +47,11 @@ def oracle_match_all(w, par, diag=True):
     return np.concatenate(idx), np.concatenate(q), (np.concatenate(dg) if diag else None)
 
 
-@pytest.mark.parametrize("dtype,match_form", [(torch.float32, 0), (torch.float16, 0), (torch.float16, 1)])
+@pytest.mark.parametrize("dtype,match_form", [(torch.float32, 0), (torch.float16, 0), (torch.float16, 1),
+                                              (torch.float16, 2)])
 def test_match_parity_tiny(M, tiny_wl, dtype, match_form):
-    """match_form 1: the refinement windows scored on the tensor cores."""
+    """match_form 1: the refinement windows scored on the tensor cores;
+    match_form 2: the windows scored from a block's staged box."""
     P = M.default_params()
     par = M.params_dict(P)
     ws = tiny_wl.to_storage(dtype)  # the oracle reads the stored (dequantised) values
@@ -98,7 +100,7 @@ def test_match_forms_and_init_agree(M, tiny_wl):
     assert agree >= MATCH_AGREE
 
 
-@pytest.mark.parametrize("dtype,match_form", [(torch.float32, 0), (torch.float16, 1)])
+@pytest.mark.parametrize("dtype,match_form", [(torch.float32, 0), (torch.float16, 1), (torch.float16, 2)])
 def test_match_invalid_and_edge_pixels(M, dtype, match_form):
     """Zero / NaN query points are rejected; queries projecting outside the
     reference image clamp to the border; out-of-range init indices fall back
@@ -468,7 +470,8 @@ def test_match_tensor_core_form_agrees_with_per_query_form(M):
     assert torch.equal(out[0][1][torch.from_numpy(same).cuda()], out[1][1][torch.from_numpy(same).cuda()])
 
 
-@pytest.mark.parametrize("dtype,match_form", [(torch.float32, 0), (torch.float16, 0), (torch.float16, 1)])
+@pytest.mark.parametrize("dtype,match_form", [(torch.float32, 0), (torch.float16, 0), (torch.float16, 1),
+                                              (torch.float16, 2)])
 def test_match_ray_image_path_is_identical(M, dtype, match_form):
     """mslam_match with its ray-image workspace (a1 materialised once, FP32)
     and without it (the rays normalised at the taps) give bit-identical
@@ -492,3 +495,58 @@ def test_match_ray_image_path_is_identical(M, dtype, match_form):
     gpu_match(M, plan, P, wd, idx_out=d_idx, q_out=d_q, edge_range=(2, 4), workspace=ws)
     sl = slice(int(w.e_off[2]), int(w.e_off[4]))
     assert torch.equal(d_idx[sl], a[0][sl]) and torch.equal(d_q[sl], a[1][sl])
+
+
+def _match_with(M, w, wd, P, **opts):
+    plan = M.Plan(w.kf_hw.numpy(), w.edges.numpy(), opts=opts)
+    return gpu_match(M, plan, P, wd)
+
+
+@pytest.mark.parametrize("bw,ppt", [(16, 1), (16, 2), (8, 2), (32, 1)])
+def test_match_staged_form_is_identical_full_size(M, bw, ppt):
+    """match_form 2 scores the same candidates with the same FP32 dot
+    products in the same order as the per-query form, from the block's
+    staged box or (outside it) from global memory: matches and confidences
+    are bit-identical, on the full-size tracking frame (512 x 384, radial
+    camera) and on four edges of the global graph's generator, whatever the
+    block shape; with a negative wait limit no copy is issued and every
+    window is read from global memory, again with identical results."""
+    import synth
+    P = M.default_params()
+    for w in (synth.tracking().to_storage(torch.float16),
+              synth.global_graph(N=8, n_pairs=10, seed=2).to_storage(torch.float16)):
+        wd = w.to("cuda")
+        ref = _match_with(M, w, wd, P, match_form=0, match_block_w=bw, match_ppt=ppt)
+        st = _match_with(M, w, wd, P, match_form=2, match_block_w=bw, match_ppt=ppt)
+        torch.cuda.synchronize()
+        assert torch.equal(ref[0], st[0]) and torch.equal(ref[1], st[1])
+        assert int((ref[0] >= 0).sum()) > 0.05 * ref[0].numel()
+    nowait = _match_with(M, w, wd, P, match_form=2, match_block_w=bw, match_ppt=ppt, wait_limit=-1)
+    assert torch.equal(ref[0], nowait[0]) and torch.equal(ref[1], nowait[1])
+
+
+@pytest.mark.parametrize("d", [16, 24, 32])
+def test_match_staged_form_scattered_centres(M, d):
+    """Random pointmaps send the LM centres of a block all over a 96 x 64
+    image, so the bounding box of its windows exceeds the staging capacity:
+    the cut box around the mean centre serves the queries whose windows it
+    holds and the rest read global memory.  Bit-identical to the per-query
+    form for every descriptor size, with a ragged image width (96 is not a
+    multiple of 64-wide blocks)."""
+    rng = np.random.default_rng(11 + d)
+    H, W = 64, 96
+    X = np.c_[rng.uniform(-1, 1, H * W), rng.uniform(-1, 1, H * W), rng.uniform(2, 4, H * W)].astype(np.float32)
+    Xq = np.c_[rng.uniform(-1, 1, H * W), rng.uniform(-1, 1, H * W), rng.uniform(2, 4, H * W)].astype(np.float32)
+    Xq[::7] = 0
+    D = rng.normal(size=(2 * H * W, d)).astype(np.float32)
+    Q = rng.uniform(1, 10, H * W).astype(np.float32)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(torch.float16).cuda()
+    P = M.default_params()
+    Dr, Dq = M.chunk_descriptors(t(D[:H * W])), M.chunk_descriptors(t(D[H * W:]))
+    out = {}
+    for form, bw in ((0, 16), (2, 16), (2, 64)):
+        plan = M.Plan([[H, W], [H, W]], [[0, 1]], opts={"match_form": form, "match_block_w": bw})
+        out[(form, bw)] = M.match(plan, P, t(X), t(Xq), Dr, Dq, t(Q), t(Q))
+    torch.cuda.synchronize()
+    for k in ((2, 16), (2, 64)):
+        assert torch.equal(out[(0, 16)][0], out[k][0]) and torch.equal(out[(0, 16)][1], out[k][1]), k

@@ -153,6 +153,36 @@ def test_three_unrolled_steps_fp16(M):
     check_against_fd(M, w, torch.float16, 3, n_x=8, n_q=4, poses=(5,), seed=1, tol=1e-3, tol_pose=2e-4)
 
 
+def near_kink_points(w, X64, idx, q, Ts, par, band=1e-3):
+    """Canonical points that take part in a match whose whitened ray or
+    distance residual lies within `band` (relative) of the Huber threshold
+    at any of the pose sets Ts (FP64).  There the step's derivative jumps
+    (the weight's derivative is 0 below the threshold and -h / (2 e^2)
+    above), so the adjoint takes the side its FP32 evaluation lands on and
+    a central difference straddles the kink."""
+    edges, kf_off, e_off = w.edges.numpy(), w.kf_off.numpy(), w.e_off.numpy()
+    idx, q = np.asarray(idx), np.asarray(q, dtype=np.float64)
+    d2 = par["huber_delta"] ** 2
+    mark = np.zeros(X64.shape[0], dtype=bool)
+    for T in Ts:
+        for e in range(w.E):
+            i, j = int(edges[e, 0]), int(edges[e, 1])
+            sl = slice(int(e_off[e]), int(e_off[e + 1]))
+            m, qe = idx[sl], q[sl]
+            n = np.nonzero((m >= 0) & (qe > par["q_min"]))[0]
+            Mx = oracle.sim3_matrix(oracle.sim3_mul(oracle.sim3_inv(T[i]), T[j]))
+            x = X64[kf_off[j] + n] @ Mx[:3, :3].T + Mx[:3, 3]
+            y = X64[kf_off[i] + m[n]]
+            dx, dy = np.linalg.norm(x, axis=1), np.linalg.norm(y, axis=1)
+            rr = x / dx[:, None] - y / dy[:, None]
+            er2 = qe[n] / par["sigma_ray"] ** 2 * (rr * rr).sum(1)
+            ed2 = qe[n] / par["sigma_dist"] ** 2 * (dx - dy) ** 2
+            bad = (np.abs(er2 / d2 - 1) < band) | (np.abs(ed2 / d2 - 1) < band)
+            mark[kf_off[j] + n[bad]] = True
+            mark[kf_off[i] + m[n[bad]]] = True
+    return mark
+
+
 def test_three_unrolled_steps_full_size_directional(M):
     """The differentiation workload at full size (32 keyframes, 96 edges,
     512 x 384, FP16 storage): the gradient of L = sum W * T_3 + c sum_k E_g(T_k)
@@ -160,7 +190,12 @@ def test_three_unrolled_steps_full_size_directional(M):
     every pose, along a random direction v, against the central difference
     of the oracle's own three Gauss-Newton steps (FP64, dense Cholesky) on
     the dequantised values: <grad, v> = (L(x + h v) - L(x - h v)) / 2h.
-    Pose directions are tangent (T_k -> Exp(h v_k) T_k)."""
+    Pose directions are tangent (T_k -> Exp(h v_k) T_k).  The point
+    direction leaves out the points of matches within 1e-3 of the Huber
+    threshold at any of the three linearisation poses (a few hundred of
+    6.3 M): there the step is not differentiable, and h = 1e-6 keeps every
+    other match on its side of the threshold.  The bar, 1e-3, is the FP16
+    rounding of the returned point gradients (2^-11 per entry)."""
     from paper_2412_12392_gb300.autograd import gn_unrolled
     w = synth.differentiation(device="cuda").to_storage(torch.float16)
     P = M.default_params()
@@ -182,31 +217,36 @@ def test_three_unrolled_steps_full_size_directional(M):
     X64 = w.X_canon.double().cpu().numpy()
     T64 = w.T_init.numpy().copy()
     idx_c, q_c = idx.cpu(), q.cpu()
+    args = (w.N, w.edges.numpy(), w.kf_off.numpy(), w.e_off.numpy())
 
-    def L_ref(Xv, Tv):
-        st, T3, hist, done = oracle.gauss_newton(w.N, w.edges.numpy(), w.kf_off.numpy(), w.e_off.numpy(), Xv, idx_c,
-                                                 q_c, Tv, 3, **par)
-        assert st == 0 and done == 3
-        return float((Wt * T3).sum()) + c * float(hist.sum())
+    def L_ref(Xv, Tv, steps=3):
+        st, T3, hist, done = oracle.gauss_newton(*args, Xv, idx_c, q_c, Tv, steps, **par)
+        assert st == 0 and done == steps
+        return float((Wt * T3).sum()) + c * float(hist.sum()), T3
 
-    L0 = L_ref(X64, T64)
+    L0, _ = L_ref(X64, T64)
     assert abs(float(L) - L0) <= 1e-4 * abs(L0), (float(L), L0)
+    Ts = [T64, L_ref(X64, T64, 1)[1], L_ref(X64, T64, 2)[1]]
+    kink = near_kink_points(w, X64, idx_c.numpy(), q_c.double().numpy(), Ts, par)
+    print(f"full size: {int(kink.sum())} of {len(kink)} points touch a match near the Huber threshold")
+    assert kink.sum() < 1e-3 * len(kink)
     # direction over the points
     vX = rng.normal(size=X64.shape)
-    h = 1e-5
-    fd = (L_ref(X64 + h * vX, T64) - L_ref(X64 - h * vX, T64)) / (2 * h)
+    vX[kink] = 0.0
+    h = 1e-6
+    fd = (L_ref(X64 + h * vX, T64)[0] - L_ref(X64 - h * vX, T64)[0]) / (2 * h)
     an = float((gX * vX).sum())
     print(f"full size, points: <grad, v> {an:.6e}, central difference {fd:.6e}, rel {abs(an - fd) / abs(fd):.2e}")
-    assert abs(an - fd) <= 2e-3 * abs(fd)
+    assert abs(an - fd) <= 1e-3 * abs(fd)
     # direction over the poses (tangent), the fixed first pose included
     vT = rng.normal(size=(w.N, 7)) * np.r_[0.01, 0.01, 0.01, 0.002, 0.002, 0.002, 0.002]
-    ht = 1e-4
+    ht = 1e-5
     Tp, Tm, dT = T64.copy(), T64.copy(), np.zeros_like(T64)
     for k in range(w.N):
         Tp[k] = oracle.sim3_mul(oracle.sim3_exp(ht * vT[k]), T64[k])
         Tm[k] = oracle.sim3_mul(oracle.sim3_exp(-ht * vT[k]), T64[k])
         dT[k] = (Tp[k] - Tm[k]) / (2 * ht)
-    fdT = (L_ref(X64, Tp) - L_ref(X64, Tm)) / (2 * ht)
+    fdT = (L_ref(X64, Tp)[0] - L_ref(X64, Tm)[0]) / (2 * ht)
     anT = float((gT * dT).sum())
     print(f"full size, poses: <grad, v> {anT:.6e}, central difference {fdT:.6e}, rel {abs(anT - fdT) / abs(fdT):.2e}")
-    assert abs(anT - fdT) <= 2e-3 * abs(fdT)
+    assert abs(anT - fdT) <= 1e-3 * abs(fdT)

@@ -146,11 +146,12 @@ def test_three_unrolled_steps_differentiation_graph(M):
 def test_three_unrolled_steps_fp16(M):
     """FP16-stored pointmaps and confidences (FP32 math): gradients with
     respect to the stored values against the oracle on the dequantised ones.
-    autograd returns a tensor's gradient in the tensor's dtype, so the point
-    and confidence gradients come back rounded to FP16 (relative 2^-11 per
-    entry, summed over the three steps): the bar for them is 1e-3."""
+    autograd returns a tensor's gradient in the tensor's dtype; gn_unrolled
+    sums the steps' point and confidence gradients in FP32 and the result is
+    rounded to FP16 once (at most 2^-12 of an entry): the bar for them is
+    5e-4 of the largest entry."""
     w = synth.differentiation(H=24, W=32)
-    check_against_fd(M, w, torch.float16, 3, n_x=8, n_q=4, poses=(5,), seed=1, tol=1e-3, tol_pose=2e-4)
+    check_against_fd(M, w, torch.float16, 3, n_x=8, n_q=4, poses=(5,), seed=1, tol=5e-4, tol_pose=2e-4)
 
 
 def near_kink_points(w, X64, idx, q, Ts, par, band=1e-3):
@@ -192,10 +193,14 @@ def test_three_unrolled_steps_full_size_directional(M):
     the dequantised values: <grad, v> = (L(x + h v) - L(x - h v)) / 2h.
     Pose directions are tangent (T_k -> Exp(h v_k) T_k).  The point
     direction leaves out the points of matches within 1e-3 of the Huber
-    threshold at any of the three linearisation poses (a few hundred of
+    threshold at any of the three linearisation poses (about 16,000 of
     6.3 M): there the step is not differentiable, and h = 1e-6 keeps every
-    other match on its side of the threshold.  The bar, 1e-3, is the FP16
-    rounding of the returned point gradients (2^-11 per entry)."""
+    other match on its side of the threshold.  The points are an FP32 leaf
+    stored as FP16 for the kernels (gn_unrolled's `storage`), so the point
+    gradients stay in FP32: most of them lie below 1e-4, in FP16's subnormal
+    range.  The bar, 1e-3, is the central difference's own spread: across
+    h = 1e-7 .. 1e-5 it moves by up to 2e-4 of its value (matches that cross
+    the threshold outside the excluded band)."""
     from paper_2412_12392_gb300.autograd import gn_unrolled
     w = synth.differentiation(device="cuda").to_storage(torch.float16)
     P = M.default_params()
@@ -204,13 +209,14 @@ def test_three_unrolled_steps_full_size_directional(M):
     rng = np.random.default_rng(11)
     Wt = rng.normal(size=(w.N, 8)) * 0.1
     c = 0.3
-    X = w.X_canon.clone().requires_grad_(True)
+    X = w.X_canon.float().requires_grad_(True)
     T0 = w.T_init.cuda().clone().requires_grad_(True)
     idx = w.gt_match
     q = w.Q_qry
-    T, taus, costs = gn_unrolled(X, q, T0, plan, P, idx, 3)
+    T, taus, costs = gn_unrolled(X, q, T0, plan, P, idx, 3, storage=torch.float16)
     L = (T * torch.from_numpy(Wt).cuda()).sum() + c * sum(costs)
     L.backward()
+    assert X.grad.dtype == torch.float32
     gX = X.grad.double().cpu().numpy()
     gT = T0.grad.cpu().numpy()
     # the oracle's L: three steps of its Gauss-Newton (costs at the start of each)
@@ -229,7 +235,7 @@ def test_three_unrolled_steps_full_size_directional(M):
     Ts = [T64, L_ref(X64, T64, 1)[1], L_ref(X64, T64, 2)[1]]
     kink = near_kink_points(w, X64, idx_c.numpy(), q_c.double().numpy(), Ts, par)
     print(f"full size: {int(kink.sum())} of {len(kink)} points touch a match near the Huber threshold")
-    assert kink.sum() < 1e-3 * len(kink)
+    assert kink.sum() < 1e-2 * len(kink)
     # direction over the points
     vX = rng.normal(size=X64.shape)
     vX[kink] = 0.0

@@ -119,6 +119,9 @@ __global__ void __launch_bounds__(256) ray4_kernel(const T* __restrict__ X, floa
 // With R4_e != nullptr the unit rays come from the ray image [pixels] of
 // float4 (x, y, z, 0) that ray4_kernel wrote with the same FP32 arithmetic
 // as ray_at (one 16-byte load per tap, no normalisation per iteration).
+// An iteration is a pure function of p: once a step leaves p unchanged (the
+// update rounds away), every later step would too, so the loop stops there
+// with exactly the p of all lm_iters steps.
 template <typename T>
 __device__ __forceinline__ float3 tap(const T* __restrict__ Xr_e, const float4* __restrict__ R4_e, int64_t pix) {
   if (R4_e) {
@@ -133,6 +136,7 @@ __device__ __forceinline__ void lm_iterate(const T* __restrict__ Xr_e, const flo
                                            float3 tg, const MatchConst& mc, float& pu, float& pv_) {
   const float lam = mc.lm_lambda;
   for (int it = 0; it < mc.lm_iters; ++it) {
+    const float pu_in = pu, pv_in = pv_;
     const int u0 = min(max((int)floorf(pu), 0), W - 2);
     const int v0 = min(max((int)floorf(pv_), 0), H - 2);
     const float a = pu - (float)u0, b = pv_ - (float)v0;
@@ -166,6 +170,7 @@ __device__ __forceinline__ void lm_iterate(const T* __restrict__ Xr_e, const flo
     // clamp (fmaxf/fminf also map a NaN to the image)
     pu = fminf(fmaxf(pu, 0.0f), (float)(W - 1));
     pv_ = fminf(fmaxf(pv_, 0.0f), (float)(H - 1));
+    if (pu == pu_in && pv_ == pv_in) break;  // a fixed point: the remaining steps change nothing
   }
 }
 

@@ -407,7 +407,9 @@ template <> struct PackRec<__half> {
     dst[0] = v;
   }
   static __device__ __forceinline__ void load(const uint4* src, float3& xj, float3& y, float& qq) {
-    const uint4 v = __ldg(src);
+    unpack(__ldg(src), xj, y, qq);
+  }
+  static __device__ __forceinline__ void unpack(const uint4 v, float3& xj, float3& y, float& qq) {
     const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
     const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
     const float2 c = __half22float2(*reinterpret_cast<const __half2*>(&v.z));
@@ -510,6 +512,12 @@ __global__ void __launch_bounds__(kLinThreads, MSLAM_PACKED_MINBLOCKS) lin_packe
   const int tid = threadIdx.x;
   constexpr int W = PackRec<T>::kWords;
   constexpr int U = MSLAM_PACKED_UNROLL;
+  // FP16 records: each thread keeps its next batch of U records in flight
+  // with asynchronous copies into its own slots of a two-stage ring in
+  // shared memory while it evaluates the current batch (no thread reads
+  // another's slots, so no barrier guards them)
+  constexpr bool kAsync = W == 1 && NA <= 32;
+  __shared__ __align__(16) uint4 ring[kAsync ? 2 * U * kLinThreads : 1];
   for (int tile = next_tile(&s_tile, tile_ctr, tile_begin, -1); tile < tile_end;
        tile = next_tile(&s_tile, tile_ctr, tile_begin, tile)) {
     const DevTile tl = pv.tiles[tile];
@@ -534,15 +542,38 @@ __global__ void __launch_bounds__(kLinThreads, MSLAM_PACKED_MINBLOCKS) lin_packe
       // takes part in each reduce-scatter)
       const int lane = tid & 31, warp = tid >> 5;
       float wsum = 0.0f;
-      int batches = 0;
-      for (int r0 = tid - lane; r0 < cnt; r0 += U * kLinThreads) {
+      int batches = 0, slot = 0;
+      // copies of batch r0 into ring slot `sl` (a commit group, empty past the end)
+      auto issue = [&](int r0, int sl) {
+        if constexpr (kAsync) {
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int r = r0 + lane + u * kLinThreads;
+            if (r < cnt) cp_async16(ring + (sl * U + u) * kLinThreads + tid, in + r);
+          }
+          cp_async_commit();
+        }
+      };
+      issue(tid - lane, 0);
+      for (int r0 = tid - lane; r0 < cnt; r0 += U * kLinThreads, slot ^= 1) {
         float3 xj[U], yy[U];
         float qq[U];
+        if constexpr (kAsync) {
+          issue(r0 + U * kLinThreads, slot ^ 1);
+          cp_async_wait_one();  // this batch's copies have landed
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int r = r0 + lane + u * kLinThreads;
-          qq[u] = 0.0f;
-          if (r < cnt) PackRec<T>::load(in + (size_t)r * W, xj[u], yy[u], qq[u]);
+          for (int u = 0; u < U; ++u) {
+            qq[u] = 0.0f;
+            if (r0 + lane + u * kLinThreads < cnt)
+              PackRec<T>::unpack(ring[(slot * U + u) * kLinThreads + tid], xj[u], yy[u], qq[u]);
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int r = r0 + lane + u * kLinThreads;
+            qq[u] = 0.0f;
+            if (r < cnt) PackRec<T>::load(in + (size_t)r * W, xj[u], yy[u], qq[u]);
+          }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u)
@@ -557,6 +588,7 @@ __global__ void __launch_bounds__(kLinThreads, MSLAM_PACKED_MINBLOCKS) lin_packe
           batches = 0;
         }
       }
+      if constexpr (kAsync) cp_async_wait_all();  // nothing in flight when the next tile reuses the ring
       {
         float v[32];
 #pragma unroll

@@ -27,6 +27,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "matched-pixel GN iters/s + matches/s @512x384, batched vs plain, % HBM peak"
 FP32_LANES_PER_SM = 128
+L1_BYTES_PER_CLK = 128  # one 128-byte data-stage wavefront per clock and SM
 
 
 def parse():
@@ -501,7 +502,7 @@ def run_gpu(args, world, rank, local):
     lin_gbs = lin_bytes / (stats["lin_ms"] * 1e-3) / 1e9
     match_tfs = match_flop / (stats["match_ms"] * 1e-3) / 1e12
     lf = arm.plan.opts.get("lin_form")
-    lin_kernel = ("lin_tiles" if args.form != "batched" else "lin_packed" if (esz == 4 or lf == 1)
+    lin_kernel = ("lin_tiles" if args.form != "batched" else "lin_packed" if (esz == 4 or lf in (1, 3))
                   else "lin_stream" if lf == 0 else "lin_warp_stream")
     traffic_m = NCU_DRAM_BYTES_PER_MATCH.get((lin_kernel, esz))
     rl_lin = {"kernel": "gn_linearize", "launch": lin_kernel, "bound": "hbm", "achieved": round(lin_gbs, 1),
@@ -529,6 +530,15 @@ def run_gpu(args, world, rank, local):
                 "hbm_frac": round(match_bytes / (stats["match_ms"] * 1e-3) / 1e9 / hbm, 4),
                 "ms": round(stats["match_ms"], 4),
                 "peak_source": f"FP32 FMA: {nsm} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz"}
+    # the unit that actually limits the kernel: the L1 data stage serving the
+    # window candidates (n_levels x (2r+1)^2 descriptors of d elements) and
+    # the LM taps (lm_iters x 4 unit rays of 16 bytes) of every valid query
+    l1_per_query = arm.P.n_levels * (2 * arm.P.win_radius + 1) ** 2 * d * esz + w.n_match_iters * 4 * 16
+    l1_peak = nsm * L1_BYTES_PER_CLK * sm_mhz * 1e6 / 1e9
+    l1_gbs = n_valid_query * l1_per_query / (stats["match_ms"] * 1e-3) / 1e9
+    rl_match["l1"] = {"bound": "l1", "achieved": round(l1_gbs, 1), "peak": round(l1_peak, 1), "unit": "GB/s",
+                      "frac": round(l1_gbs / l1_peak, 4), "bytes_per_valid_query": int(l1_per_query),
+                      "peak_source": f"L1 data stage: {nsm} SMs x {L1_BYTES_PER_CLK} B x {sm_mhz:.0f} MHz"}
     lin_share = stats["lin_ms"] * arm.iters
     dominant = rl_match if stats["match_ms"] >= lin_share else rl_lin
     out = {

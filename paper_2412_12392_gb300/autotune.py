@@ -23,7 +23,7 @@ MATCH_PPTS = (1, 2)
 LIN_TILES = (4096, 8192, 16384)
 LIN_BLOCKS = (0, 2, 3, 4)
 WARP_STREAM_TILES = (1024, 2048, 4096)
-FORM_NAMES = {0: "stream", 1: "regs", 2: "warp"}
+FORM_NAMES = {0: "stream", 1: "regs", 2: "warp", 3: "regs_ring"}
 
 
 def _time(fn, reps: int) -> float:
@@ -66,7 +66,8 @@ def autotune(kf_hw, edges, graph_of_kf, params, X_ref, X_qry, D_ref, D_qry, Q_re
         del ws
     idx, q = api.match(api.Plan(kf_hw, edges, graph_of_kf), params, X_ref, X_qry, D_ref, D_qry, Q_ref, Q_qry)
     best_lin, best_lt = None, float("inf")
-    shapes = [(tile, bps, 1) for tile, bps in itertools.product(lin_tiles, lin_blocks)]
+    shapes = [(tile, bps, form) for tile, bps in itertools.product(lin_tiles, lin_blocks)
+              for form in ((1, 3) if X_canon.dtype == torch.float16 else (1,))]
     # the block-streamed form runs one CTA per SM and favours large tiles;
     # the warp-streamed form gives each warp whole tiles and favours small ones
     shapes += [(tile, 0, 0) for tile in sorted(set(lin_tiles) | {32768, 65536})]

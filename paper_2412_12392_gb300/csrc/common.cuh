@@ -19,7 +19,10 @@ constexpr int kLinThreads = 256;     // threads per linearisation block
 constexpr int kNumAcc = 30;          // accumulators of the ray family's relative 7x7 system
 constexpr int kFamAcc = 37;          // accumulators of the point / pixel families (28 + 7 + 2)
 constexpr int kAccStride = 40;       // floats per tile partial in the workspace
-constexpr int kMatchThreads = 256;   // match block: 256 query pixels (default 32 x 8)
+#ifndef MSLAM_MATCH_THREADS
+#define MSLAM_MATCH_THREADS 256
+#endif
+constexpr int kMatchThreads = MSLAM_MATCH_THREADS;  // threads of a match block (default 32 x 8)
 constexpr int kMatchBX = 32;
 constexpr int kSolveThreads = 512;
 
@@ -406,12 +409,11 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 // Per-thread asynchronous 16-byte copy global -> shared (L2 only), grouped by
-// commit; wait_one leaves at most the newest group in flight.
+// commit.
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");

@@ -499,7 +499,7 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(PlanView pv, float q
   }
 }
 
-template <typename T, int kKind>
+template <typename T, int kKind, bool kRing>
 __global__ void __launch_bounds__(kLinThreads, MSLAM_PACKED_MINBLOCKS) lin_packed_kernel(PlanView pv, LinConst lc,
                                                                    const RelPose* __restrict__ rel,
                                                                    const uint4* __restrict__ recs,
@@ -512,12 +512,14 @@ __global__ void __launch_bounds__(kLinThreads, MSLAM_PACKED_MINBLOCKS) lin_packe
   const int tid = threadIdx.x;
   constexpr int W = PackRec<T>::kWords;
   constexpr int U = MSLAM_PACKED_UNROLL;
-  // FP16 records: each thread keeps its next batch of U records in flight
-  // with asynchronous copies into its own slots of a two-stage ring in
-  // shared memory while it evaluates the current batch (no thread reads
-  // another's slots, so no barrier guards them)
-  constexpr bool kAsync = W == 1 && NA <= 32;
-  __shared__ __align__(16) uint4 ring[kAsync ? 2 * U * kLinThreads : 1];
+  // kRing (plan option lin_form 3), FP16 records: each thread keeps its next
+  // batch of U records in flight with asynchronous copies into its own slots
+  // of a one-batch buffer in shared memory while it evaluates the current
+  // batch, which it has read into registers first (no thread reads another's
+  // slots, so no barrier guards them; 16 KB per block).  The sums are those
+  // of the plain form, in the same order.
+  constexpr bool kAsync = kRing && W == 1 && NA <= 32;
+  __shared__ __align__(16) uint4 ring[kAsync ? U * kLinThreads : 1];
   for (int tile = next_tile(&s_tile, tile_ctr, tile_begin, -1); tile < tile_end;
        tile = next_tile(&s_tile, tile_ctr, tile_begin, tile)) {
     const DevTile tl = pv.tiles[tile];
@@ -542,31 +544,32 @@ __global__ void __launch_bounds__(kLinThreads, MSLAM_PACKED_MINBLOCKS) lin_packe
       // takes part in each reduce-scatter)
       const int lane = tid & 31, warp = tid >> 5;
       float wsum = 0.0f;
-      int batches = 0, slot = 0;
-      // copies of batch r0 into ring slot `sl` (a commit group, empty past the end)
-      auto issue = [&](int r0, int sl) {
+      int batches = 0;
+      // copies of batch r0 into the thread's slots (none past the end)
+      auto issue = [&](int r0) {
         if constexpr (kAsync) {
 #pragma unroll
           for (int u = 0; u < U; ++u) {
             const int r = r0 + lane + u * kLinThreads;
-            if (r < cnt) cp_async16(ring + (sl * U + u) * kLinThreads + tid, in + r);
+            if (r < cnt) cp_async16(ring + u * kLinThreads + tid, in + r);
           }
           cp_async_commit();
         }
       };
-      issue(tid - lane, 0);
-      for (int r0 = tid - lane; r0 < cnt; r0 += U * kLinThreads, slot ^= 1) {
+      issue(tid - lane);
+      for (int r0 = tid - lane; r0 < cnt; r0 += U * kLinThreads) {
         float3 xj[U], yy[U];
         float qq[U];
         if constexpr (kAsync) {
-          issue(r0 + U * kLinThreads, slot ^ 1);
-          cp_async_wait_one();  // this batch's copies have landed
+          cp_async_wait_all();  // this batch's copies have landed
 #pragma unroll
           for (int u = 0; u < U; ++u) {
             qq[u] = 0.0f;
-            if (r0 + lane + u * kLinThreads < cnt)
-              PackRec<T>::unpack(ring[(slot * U + u) * kLinThreads + tid], xj[u], yy[u], qq[u]);
+            if (r0 + lane + u * kLinThreads < cnt) PackRec<T>::unpack(ring[u * kLinThreads + tid], xj[u], yy[u], qq[u]);
           }
+          // the slots' values are in registers (the unpacking consumed them):
+          // the next batch may land there
+          issue(r0 + U * kLinThreads);
         } else {
 #pragma unroll
           for (int u = 0; u < U; ++u) {
@@ -1345,11 +1348,11 @@ using namespace mslam;
 // the FP16 ray family takes the block-streamed form (plan option lin_form
 // 0) or the warp-streamed form (lin_form 2); lin_form 1, FP32 records and
 // the other families take the register pipeline.
-enum PackedForm { kFormRegs = 0, kFormBlockStream = 1, kFormWarpStream = 2 };
+enum PackedForm { kFormRegs = 0, kFormBlockStream = 1, kFormWarpStream = 2, kFormRegsRing = 3 };
 static PackedForm packed_form(const mslam_params* p, const mslam_plan* plan, mslam_dtype dt) {
   if (p->residual != MSLAM_RES_RAY || dt != MSLAM_F16) return kFormRegs;
   const int f = plan_lin_form(plan);
-  return f == 0 ? kFormBlockStream : f == 2 ? kFormWarpStream : kFormRegs;
+  return f == 0 ? kFormBlockStream : f == 2 ? kFormWarpStream : f == 3 ? kFormRegsRing : kFormRegs;
 }
 
 // Opt a streamed kernel into its dynamic shared memory, once per device.
@@ -1569,7 +1572,7 @@ extern "C" mslam_status mslam_gn_linearize_packed(const mslam_params* p, const m
   rel_pose_kernel<<<(pv.E + 127) / 128, 128, 0, s>>>(pv, T_wc, rel, ctr);
   const size_t stream_smem = (size_t)kStreamStages * kStreamChunkBytes;
   const PackedForm form = packed_form(p, plan, dt);
-  if (form != kFormRegs) {
+  if (form == kFormBlockStream || form == kFormWarpStream) {
     mslam_status st2 = form == kFormBlockStream
                            ? stream_kernel_setup<kFormBlockStream>(lin_stream_kernel, stream_smem)
                            : stream_kernel_setup<kFormWarpStream>(lin_warp_stream_kernel, kWarpStreamSmem);
@@ -1593,9 +1596,14 @@ extern "C" mslam_status mslam_gn_linearize_packed(const mslam_params* p, const m
         return;
       }
       if (dt == MSLAM_F32)
-        lin_packed_kernel<float, kK><<<grid, kLinThreads, 0, s>>>(pv, lc, rel, recs, counts, partials, t0, t1, c);
+        lin_packed_kernel<float, kK, false><<<grid, kLinThreads, 0, s>>>(pv, lc, rel, recs, counts, partials, t0,
+                                                                         t1, c);
+      else if (form == kFormRegsRing)
+        lin_packed_kernel<__half, kK, true><<<grid, kLinThreads, 0, s>>>(pv, lc, rel, recs, counts, partials, t0,
+                                                                         t1, c);
       else
-        lin_packed_kernel<__half, kK><<<grid, kLinThreads, 0, s>>>(pv, lc, rel, recs, counts, partials, t0, t1, c);
+        lin_packed_kernel<__half, kK, false><<<grid, kLinThreads, 0, s>>>(pv, lc, rel, recs, counts, partials, t0,
+                                                                          t1, c);
     };
     if (flags & MSLAM_FLAG_PER_EDGE) {
       for (int e = 0; e < pv.E; ++e) {
@@ -1605,8 +1613,9 @@ extern "C" mslam_status mslam_gn_linearize_packed(const mslam_params* p, const m
         lin_finalize_kernel<<<1, kFinalizeThreads, 0, s>>>(pv, T_wc, partials, H_blocks, g_blocks, cost, n_valid, e, kK);
       }
     } else {
-      int grid = persistent_grid(plan, lin_packed_kernel<__half, kK>);
-      if (kK == MSLAM_RES_RAY && form != kFormRegs) {
+      int grid = form == kFormRegsRing ? persistent_grid(plan, lin_packed_kernel<__half, kK, true>)
+                                       : persistent_grid(plan, lin_packed_kernel<__half, kK, false>);
+      if (kK == MSLAM_RES_RAY && (form == kFormBlockStream || form == kFormWarpStream)) {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

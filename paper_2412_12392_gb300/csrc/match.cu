@@ -309,7 +309,7 @@ __device__ __forceinline__ void match_query(const PlanView& pv, const MatchConst
 // A block covers match_bx x (match_by * match_ppt) query pixels: each thread
 // takes match_ppt queries, match_by rows apart (plan option match_ppt).
 template <typename T, int D, int kR, int kPPT>
-__global__ void __launch_bounds__(kMatchThreads, 4) match_kernel(
+__global__ void __launch_bounds__(kMatchThreads, 1024 / kMatchThreads) match_kernel(
     PlanView pv, MatchConst mc, const T* __restrict__ Xr, const T* __restrict__ Xq, const T* __restrict__ Dr,
     const T* __restrict__ Dq, const T* __restrict__ Qr, const T* __restrict__ Qq, const int32_t* __restrict__ init,
     int32_t* __restrict__ out_idx, T* __restrict__ out_q, int e_begin, int e_end, int block_base,
@@ -355,7 +355,7 @@ template <int D> struct StagedCfg {
 };
 
 template <int D, int kPPT>
-__global__ void __launch_bounds__(kMatchThreads, 4) match_staged_kernel(
+__global__ void __launch_bounds__(kMatchThreads, 1024 / kMatchThreads) match_staged_kernel(
     PlanView pv, MatchConst mc, const __half* __restrict__ Xr, const __half* __restrict__ Xq,
     const __half* __restrict__ Dr, const __half* __restrict__ Dq, const __half* __restrict__ Qr,
     const __half* __restrict__ Qq, const int32_t* __restrict__ init, int32_t* __restrict__ out_idx,

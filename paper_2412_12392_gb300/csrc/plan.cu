@@ -464,10 +464,10 @@ mslam_status mslam_plan_create_ex(int32_t N, const int32_t* kf_hw, int32_t E, co
       o.lin_blocks_per_sm > 32 ||
       (o.match_block_w != 4 && o.match_block_w != 8 && o.match_block_w != 16 && o.match_block_w != 32 &&
        o.match_block_w != 64 && o.match_block_w != 128 && o.match_block_w != 256) ||
-      o.lin_form < 0 || o.lin_form > 2 || (o.solve_form != 0 && o.solve_form != 1) ||
+      o.lin_form < 0 || o.lin_form > 3 || (o.solve_form != 0 && o.solve_form != 1) ||
       (o.match_form < 0 || o.match_form > 2) || o.match_ppt < 1 || o.match_ppt > 2) {
     set_error("plan options: lin_tile %d (multiple of %d in [1024, 65536]), lin_blocks_per_sm %d (0..32), "
-              "match_block_w %d (4, 8, ..., 256), lin_form %d (0, 1 or 2), solve_form %d (0 or 1), match_form %d "
+              "match_block_w %d (4, 8, ..., 256), lin_form %d (0..3), solve_form %d (0 or 1), match_form %d "
               "(0, 1 or 2), match_ppt %d (1 or 2)", o.lin_tile, kLinThreads, o.lin_blocks_per_sm, o.match_block_w,
               o.lin_form, o.solve_form, o.match_form, o.match_ppt);
     if (out) *out = nullptr;

@@ -78,7 +78,7 @@ def test_autotuner_choice_is_equivalent(M, graphs):
     opts = rep["opts"]
     assert opts["match_block_w"] in MATCH_WIDTHS
     assert opts["lin_tile"] in set(LIN_TILES) | {32768, 65536} | set(WARP_STREAM_TILES)
-    assert opts["lin_form"] in (0, 1, 2)
+    assert opts["lin_form"] in (0, 1, 2, 3)
     out = []
     for o in (None, opts):
         plan = M.Plan(mw.kf_hw.numpy(), mw.edges.numpy(), mw.graph_of_kf.numpy(), opts=o)

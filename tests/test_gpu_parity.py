@@ -364,7 +364,7 @@ def test_packed_linearize_parity(M, tiny_wl, dtype):
     assert block_rel_err(H, H3).max() <= 1e-6 and torch.equal(nv, nv3)
 
 
-@pytest.mark.parametrize("form,tile", [(0, 8192), (1, 8192), (2, 1024), (2, 4096)])
+@pytest.mark.parametrize("form,tile", [(0, 8192), (1, 8192), (2, 1024), (2, 4096), (3, 1024), (3, 8192)])
 def test_packed_linearize_forms(M, tiny_wl, form, tile):
     """Every packed linearisation form of the FP16 ray family (block-streamed,
     register pipeline, warp-streamed) against the oracle at tile sizes that
@@ -395,6 +395,11 @@ def test_packed_linearize_forms(M, tiny_wl, form, tile):
     H3, g3, c3, nv3 = M.gn_linearize_packed(ref_plan, P, torch.float16, T,
                                             M.gn_pack(ref_plan, P, wd.X_canon, idx_d, q_d))
     assert block_rel_err(H, H3).max() <= 1e-6 and block_rel_err(g, g3).max() <= 1e-5 and torch.equal(nv, nv3)
+    if form == 3:
+        # the prefetching form sums the same records in the same order as form 1
+        same = M.Plan(ws.kf_hw.numpy(), ws.edges.numpy(), opts={"lin_form": 1, "lin_tile": tile})
+        H4, g4, c4, nv4 = M.gn_linearize_packed(same, P, torch.float16, T, M.gn_pack(same, P, wd.X_canon, idx_d, q_d))
+        assert torch.equal(H, H4) and torch.equal(g, g4) and torch.equal(c, c4) and torch.equal(nv, nv4)
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float16])

@@ -436,16 +436,39 @@ template <> struct PackRec<float> {
 };
 
 // The storage values are copied bit for bit (FP16 -> float -> FP16 is exact).
-// One 1024-thread block per tile keeps the tile's pixel order (each block
-// compacts 1024 pixels per step: warp ballots, then a scan of the 32 warp
-// counts by one warp).
+// One 1024-thread block per tile keeps the tile's pixel order.  A round
+// covers kPackSteps x 1024 pixels (pixel base + k 1024 + t for thread t and
+// step k): first every thread tests its kPackSteps pixels (loads of several
+// steps in flight) and each warp counts its valid pixels per step; then one
+// warp per step scans that step's 32 warp counts and one thread adds up the
+// step totals; then every thread writes its records (the valid pixels'
+// values read again, from the caches) at its rank.  Three barriers per round
+// instead of three per 1024 pixels; the records and their order are those of
+// one compaction per 1024 pixels.
 constexpr int kPackThreads = 1024;
+constexpr int kPackSteps = 16;
+
+// a pixel gives a record: matched, confident, both canonical points
+// non-zero and finite (a degenerate point contributes nothing, as in the
+// gathering form)
 template <typename T>
-__global__ void __launch_bounds__(kPackThreads) pack_kernel(PlanView pv, float q_min, int kind, const T* __restrict__ X,
+__device__ __forceinline__ bool pack_valid(const int32_t* __restrict__ idx_e, const T* __restrict__ q_e,
+                                           const T* __restrict__ Xj, const T* __restrict__ Xi, int n, float q_min) {
+  const int m = __ldg(idx_e + n);
+  if (m < 0 || !(ldf(q_e + n) > q_min)) return false;
+  const float3 xj = ld3(Xj, n), y = ld3(Xi, m);
+  const float a2 = xj.x * xj.x + xj.y * xj.y + xj.z * xj.z, b2 = y.x * y.x + y.y * y.y + y.z * y.z;
+  return a2 > 0.0f && b2 > 0.0f && a2 < INFINITY && b2 < INFINITY;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPackThreads, 2) pack_kernel(PlanView pv, float q_min, int kind, const T* __restrict__ X,
                                                             const int32_t* __restrict__ idx, const T* __restrict__ q,
                                                             uint4* __restrict__ recs, int32_t* __restrict__ counts) {
-  __shared__ int warp_tot[kPackThreads / 32], warp_off[kPackThreads / 32 + 1];
+  __shared__ int s_wcnt[kPackSteps][kPackThreads / 32];  // per step and warp: valid pixels, then their offset
+  __shared__ int s_step[kPackSteps + 1];                 // per step: offset within the round
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned lanes_below = (1u << lane) - 1u;
   constexpr int W = PackRec<T>::kWords;
   for (int tile = blockIdx.x; tile < pv.n_tiles; tile += gridDim.x) {
     const DevTile tl = pv.tiles[tile];
@@ -456,44 +479,52 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(PlanView pv, float q
     const T* Xi = X + 3 * ed.off_i;
     uint4* out = recs + (size_t)tile * pv.lin_tile * W;
     int base_count = 0;
-    for (int base = tl.begin; base < tl.end; base += kPackThreads) {
-      const int n = base + tid;
-      int m = -1;
-      float qq = 0.0f;
-      if (n < tl.end) {
-        m = __ldg(idx_e + n);
-        if (m >= 0) qq = ldf(q_e + n);
+    for (int base = tl.begin; base < tl.end; base += kPackThreads * kPackSteps) {
+      unsigned valid = 0;  // bit k: this thread's pixel of step k gives a record
+#pragma unroll 4
+      for (int k = 0; k < kPackSteps; ++k) {
+        const int n = base + k * kPackThreads + tid;
+        const bool v = n < tl.end && pack_valid(idx_e, q_e, Xj, Xi, n, q_min);
+        const unsigned bal = __ballot_sync(0xffffffffu, v);
+        if (lane == 0) s_wcnt[k][warp] = __popc(bal);
+        valid |= (unsigned)v << k;
       }
-      bool valid = m >= 0 && qq > q_min;
-      float3 xj = make_float3(0.f, 0.f, 0.f), y = xj;
-      if (valid) {
-        xj = ld3(Xj, n);
-        y = ld3(Xi, m);
-        // a degenerate point contributes nothing (as in the gathering form)
-        const float a2 = xj.x * xj.x + xj.y * xj.y + xj.z * xj.z, b2 = y.x * y.x + y.y * y.y + y.z * y.z;
-        valid = a2 > 0.0f && b2 > 0.0f && a2 < INFINITY && b2 < INFINITY;
-        // the pixel family stores the reference pixel of m and its depth
-        if (kind == MSLAM_RES_PIXEL) y = make_float3((float)(m % ed.W), (float)(m / ed.W), y.z);
-      }
-      const unsigned bal = __ballot_sync(0xffffffffu, valid);
-      const int rank = __popc(bal & ((1u << lane) - 1u));
-      if (lane == 0) warp_tot[warp] = __popc(bal);
       __syncthreads();
-      if (warp == 0) {  // exclusive scan of the 32 warp counts
-        const int v = warp_tot[lane];
-        int incl = v;
+      if (warp < kPackSteps) {  // exclusive scan of step `warp`'s 32 warp counts
+        const int c = s_wcnt[warp][lane];
+        int incl = c;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
           const int o = __shfl_up_sync(0xffffffffu, incl, off);
           if (lane >= off) incl += o;
         }
-        warp_off[lane] = incl - v;
-        if (lane == 31) warp_off[32] = incl;
+        s_wcnt[warp][lane] = incl - c;
+        if (lane == 31) s_step[warp + 1] = incl;
       }
       __syncthreads();
-      if (valid) PackRec<T>::store(out + (size_t)(base_count + warp_off[warp] + rank) * W, xj, y, qq);
-      base_count += warp_off[32];
+      if (tid == 0) {
+        s_step[0] = 0;
+#pragma unroll
+        for (int k = 1; k <= kPackSteps; ++k) s_step[k] += s_step[k - 1];
+      }
       __syncthreads();
+#pragma unroll 4
+      for (int k = 0; k < kPackSteps; ++k) {
+        const bool v = (valid >> k) & 1u;
+        const unsigned bal = __ballot_sync(0xffffffffu, v);
+        if (v) {
+          const int n = base + k * kPackThreads + tid;
+          const int m = __ldg(idx_e + n);
+          const float3 xj = ld3(Xj, n);
+          float3 y = ld3(Xi, m);
+          // the pixel family stores the reference pixel of m and its depth
+          if (kind == MSLAM_RES_PIXEL) y = make_float3((float)(m % ed.W), (float)(m / ed.W), y.z);
+          const int slot = base_count + s_step[k] + s_wcnt[k][warp] + __popc(bal & lanes_below);
+          PackRec<T>::store(out + (size_t)slot * W, xj, y, ldf(q_e + n));
+        }
+      }
+      base_count += s_step[kPackSteps];
+      __syncthreads();  // the next round rewrites the counts
     }
     if (tid == 0) counts[tile] = base_count;
   }

@@ -128,9 +128,11 @@ NCU_DRAM_BYTES_PER_QUERY_PX = {("match", 2, 24): 344586240 / 4718592}
 # DRAM bytes per matched pixel of one packed linearisation launch, FP16
 # records, scaled to a launch by its matches (1,637,856 matches in each
 # capture, 8 keyframes / 24 edges at 512x384): lin_packed_kernel (16384-record
-# tiles, 2 CTAs per SM: 26,254,592 bytes) and lin_warp_stream_kernel
-# (4096-record tiles: 26,328,064 bytes).
-NCU_DRAM_BYTES_PER_MATCH = {("lin_packed", 2): 26254592 / 1637856, ("lin_warp_stream", 2): 26328064 / 1637856}
+# tiles, 2 CTAs per SM: 26,254,592 bytes), its prefetching form (lin_form 3,
+# the same shape: 26,256,128 bytes) and lin_warp_stream_kernel (4096-record
+# tiles: 26,328,064 bytes).
+NCU_DRAM_BYTES_PER_MATCH = {("lin_packed", 2): 26254592 / 1637856, ("lin_packed_prefetch", 2): 26256128 / 1637856,
+                            ("lin_warp_stream", 2): 26328064 / 1637856}
 
 
 def valid_query_pixels(X_qry: torch.Tensor) -> int:
@@ -502,8 +504,8 @@ def run_gpu(args, world, rank, local):
     lin_gbs = lin_bytes / (stats["lin_ms"] * 1e-3) / 1e9
     match_tfs = match_flop / (stats["match_ms"] * 1e-3) / 1e12
     lf = arm.plan.opts.get("lin_form")
-    lin_kernel = ("lin_tiles" if args.form != "batched" else "lin_packed" if (esz == 4 or lf in (1, 3))
-                  else "lin_stream" if lf == 0 else "lin_warp_stream")
+    lin_kernel = ("lin_tiles" if args.form != "batched" else "lin_packed" if (esz == 4 or lf == 1)
+                  else "lin_packed_prefetch" if lf == 3 else "lin_stream" if lf == 0 else "lin_warp_stream")
     traffic_m = NCU_DRAM_BYTES_PER_MATCH.get((lin_kernel, esz))
     rl_lin = {"kernel": "gn_linearize", "launch": lin_kernel, "bound": "hbm", "achieved": round(lin_gbs, 1),
               "peak": hbm, "unit": "GB/s", "frac": round(lin_gbs / hbm, 4),

@@ -160,6 +160,7 @@ __device__ __forceinline__ bool match_grad(V3 x, V3 y, float q, const BwdConst& 
 // perturbation xi of T_ij (x -> Exp(xi) x, dx/dxi = [I, -[x]x, x]):
 // Xi_e = sum over the edge's matches of (g_x, x cross g_x, x . g_x), added
 // into xi_out [E, 7] (FP64).
+constexpr int kBwdU = 4;
 template <typename T, bool kPose>
 __global__ void __launch_bounds__(256) bwd_kernel(PlanView pv, BwdConst bc, const float* __restrict__ edge_data,
                                                   const T* __restrict__ X, const int32_t* __restrict__ idx,
@@ -181,38 +182,63 @@ __global__ void __launch_bounds__(256) bwd_kernel(PlanView pv, BwdConst bc, cons
       sbeta[k] = __ldg(eg + 12 + k);
       stheta[k] = __ldg(eg + 19 + k);
     }
-    for (int n = tl.begin + threadIdx.x; n < tl.end; n += blockDim.x) {
-      const int m = idx[ed.off_e + n];
-      if (m < 0) continue;
-      const float qq = ldf(q + ed.off_e + n);
-      if (!(qq > bc.q_min)) continue;
-      const float3 Xj = ld3(X + 3 * ed.off_j, n);
-      const float3 yv = ld3(X + 3 * ed.off_i, m);
-      const V3 x = v3(sR[0] * Xj.x + sR[1] * Xj.y + sR[2] * Xj.z + st[0],
-                      sR[3] * Xj.x + sR[4] * Xj.y + sR[5] * Xj.z + st[1],
-                      sR[6] * Xj.x + sR[7] * Xj.y + sR[8] * Xj.z + st[2]);
-      V3 gx, gy;
-      float gq;
-      if (!match_grad(x, v3(yv.x, yv.y, yv.z), qq, bc, sbeta, stheta, gx, gy, gq)) continue;
-      // dL/dX_j = (s R)^T dL/dx
-      float* dXj = dX + 3 * (ed.off_j + n);
-      atomicAdd(dXj + 0, sR[0] * gx.x + sR[3] * gx.y + sR[6] * gx.z);
-      atomicAdd(dXj + 1, sR[1] * gx.x + sR[4] * gx.y + sR[7] * gx.z);
-      atomicAdd(dXj + 2, sR[2] * gx.x + sR[5] * gx.y + sR[8] * gx.z);
-      float* dXi = dX + 3 * (ed.off_i + m);
-      atomicAdd(dXi + 0, gy.x);
-      atomicAdd(dXi + 1, gy.y);
-      atomicAdd(dXi + 2, gy.z);
-      dq[ed.off_e + n] = gq;
-      if (kPose) {
-        const V3 xg = cross(x, gx);
-        xi[0] += gx.x;
-        xi[1] += gx.y;
-        xi[2] += gx.z;
-        xi[3] += xg.x;
-        xi[4] += xg.y;
-        xi[5] += xg.z;
-        xi[6] += dot(x, gx);
+    // kBwdU pixels per thread and round: their loads (the match index, then
+    // the confidence and both canonical points) are all issued before the
+    // first pixel's reverse sweep
+    for (int n0 = tl.begin + threadIdx.x; n0 < tl.end; n0 += blockDim.x * kBwdU) {
+      int mv[kBwdU];
+      float qv[kBwdU];
+      float3 Xjv[kBwdU], yvv[kBwdU];
+#pragma unroll
+      for (int u = 0; u < kBwdU; ++u) {
+        const int n = n0 + u * blockDim.x;
+        mv[u] = n < tl.end ? idx[ed.off_e + n] : -1;
+      }
+#pragma unroll
+      for (int u = 0; u < kBwdU; ++u) {
+        const int n = n0 + u * blockDim.x;
+        qv[u] = 0.0f;
+        Xjv[u] = yvv[u] = make_float3(0.0f, 0.0f, 0.0f);
+        if (mv[u] >= 0) {
+          qv[u] = ldf(q + ed.off_e + n);
+          Xjv[u] = ld3(X + 3 * ed.off_j, n);
+          yvv[u] = ld3(X + 3 * ed.off_i, mv[u]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kBwdU; ++u) {
+        const int n = n0 + u * blockDim.x, m = mv[u];
+        if (m < 0) continue;
+        const float qq = qv[u];
+        if (!(qq > bc.q_min)) continue;
+        const float3 Xj = Xjv[u];
+        const float3 yv = yvv[u];
+        const V3 x = v3(sR[0] * Xj.x + sR[1] * Xj.y + sR[2] * Xj.z + st[0],
+                        sR[3] * Xj.x + sR[4] * Xj.y + sR[5] * Xj.z + st[1],
+                        sR[6] * Xj.x + sR[7] * Xj.y + sR[8] * Xj.z + st[2]);
+        V3 gx, gy;
+        float gq;
+        if (!match_grad(x, v3(yv.x, yv.y, yv.z), qq, bc, sbeta, stheta, gx, gy, gq)) continue;
+        // dL/dX_j = (s R)^T dL/dx
+        float* dXj = dX + 3 * (ed.off_j + n);
+        atomicAdd(dXj + 0, sR[0] * gx.x + sR[3] * gx.y + sR[6] * gx.z);
+        atomicAdd(dXj + 1, sR[1] * gx.x + sR[4] * gx.y + sR[7] * gx.z);
+        atomicAdd(dXj + 2, sR[2] * gx.x + sR[5] * gx.y + sR[8] * gx.z);
+        float* dXi = dX + 3 * (ed.off_i + m);
+        atomicAdd(dXi + 0, gy.x);
+        atomicAdd(dXi + 1, gy.y);
+        atomicAdd(dXi + 2, gy.z);
+        dq[ed.off_e + n] = gq;
+        if (kPose) {
+          const V3 xg = cross(x, gx);
+          xi[0] += gx.x;
+          xi[1] += gx.y;
+          xi[2] += gx.z;
+          xi[3] += xg.x;
+          xi[4] += xg.y;
+          xi[5] += xg.z;
+          xi[6] += dot(x, gx);
+        }
       }
     }
     if (kPose) {

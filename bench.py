@@ -892,9 +892,9 @@ def tracking_frame(M, dev, peaks) -> dict:
     arm.capture()
     gms = _event_ms(arm.step_graph, 20)
     # the fused tracking loop: match, pack, then one launch per GN iteration,
-    # with 1024-pixel tiles so that the frame's 192 tiles occupy every SM
+    # with 2048-pixel tiles (96 tiles: fewer partials for the finishing block to add)
     M_ = arm.M
-    plan_t = M_.Plan(w.kf_hw.numpy(), w.edges.numpy(), opts=dict(arm.plan.opts, lin_tile=1024))
+    plan_t = M_.Plan(w.kf_hw.numpy(), w.edges.numpy(), opts=dict(arm.plan.opts, lin_tile=2048))
     gn_t = M_.GaussNewton(plan_t, arm.P, arm.wd.X_canon, arm.idx, arm.q, packed=True)
 
     def fused():

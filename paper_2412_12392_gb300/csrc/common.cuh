@@ -372,6 +372,33 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
   return y;
 }
 
+// 1/x in FP64 by Newton's iteration for the reciprocal, y <- y (2 - x y),
+// seeded with the single-precision reciprocal: two iterations take the
+// ~23-bit seed past FP64 precision (an IEEE FP64 division is a long
+// dependent chain on this GPU).  Outside the single-precision range it falls
+// back to the division.
+__device__ __forceinline__ double rcp_newton(double x) {
+  if (!(fabs(x) > 1e-30 && fabs(x) < 1e30)) return 1.0 / x;
+  double y = (double)(1.0f / (float)x);
+  y = y * fma(-x, y, 2.0);
+  y = y * fma(-x, y, 2.0);
+  return y;
+}
+
+// Entry (r, c) of the rotation of the unit quaternion q = (v, w) stored at q
+// (x, y, z, w): R = (w^2 - v.v) I + 2 v v^T + 2 w [v]x, one formula for every
+// entry, so that the lanes of a warp evaluate different entries without
+// diverging.
+__device__ __forceinline__ double rot_entry(const double* q, int r, int c) {
+  const bool diag = r == c;
+  const int k = diag ? 0 : 3 - r - c;                     // the third axis
+  const double sgn = (c == (r + 1) % 3) ? -1.0 : 1.0;     // [v]x (r, c) = sgn v_k
+  const double w = q[3], vr = q[r], vc = q[c];
+  const double base = diag ? fma(w, w, -(q[0] * q[0] + q[1] * q[1] + q[2] * q[2])) : 0.0;
+  const double cross = diag ? 0.0 : sgn * q[k];
+  return fma(2.0 * vr, vc, fma(2.0 * w, cross, base));
+}
+
 // ---------------------------------------------------------------- host errors
 void set_error(const char* fmt, ...);
 mslam_status cuda_check(cudaError_t e, const char* what);

@@ -1183,9 +1183,143 @@ __global__ void __launch_bounds__(kFinalizeThreads) lin_finalize_kernel(PlanView
 // tile's packed records (ray family) and stores the tile's sums; the block
 // that completes an edge's last tile (a counter per edge, after a device
 // fence) adds the edge's tile sums in tile order in FP64, maps the relative
-// system to the frame's 7 x 7 with the adjoint of T_i^-1, solves it by FP64
-// Cholesky, retracts the frame's pose and resets the counter.  No block
-// waits for another.
+// system to the frame's 7 x 7 with the adjoint of T_i^-1, solves it, retracts
+// the frame's pose and resets the counter.  No block waits for another.
+// A dependent FP64 operation takes tens of cycles on this GPU, so the FP64
+// work of a launch is spread over lanes and warps: the entries of the
+// relative pose, of the adjoint and of the relative 7 x 7 system are formed
+// by different lanes, the pieces of Exp(tau) by different warps, and the
+// 7 x 7 solve factors in FP32 with FP64 iterative refinement.
+
+// Entry (r, c) of the ray family's relative 7 x 7 system from its 30 sums
+// (the layout of ray_relative_system).
+__device__ __forceinline__ double hr_entry(const double* S, int r, int c) {
+  const bool rt = r < 3, ct = c < 3, rr = r >= 3 && r < 6, cr = c >= 3 && c < 6;
+  if (rt && ct) {
+    const int s = r == c ? (r == 0 ? 0 : r == 1 ? 3 : 5) : (r + c == 1 ? 1 : r + c == 2 ? 2 : 4);
+    return (r == c ? S[0] : 0.0) + S[1 + s];
+  }
+  if (rr && cr) {
+    const int a = r - 3, b = c - 3;
+    const int s = a == b ? (a == 0 ? 0 : a == 1 ? 3 : 5) : (a + b == 1 ? 1 : a + b == 2 ? 2 : 4);
+    return (a == b ? S[13] : 0.0) - S[14 + s];
+  }
+  // tw(a, b) for a < 3, b < 3 (the translation-rotation coupling)
+  auto tw = [&](int a, int b) {
+    if (a == b) return 0.0;
+    const int k = 3 - a - b;
+    const double v = S[7 + k];
+    return (b == (a + 1) % 3) ? v : -v;  // tw = [[0, z, -y], [-z, 0, x], [y, -x, 0]]
+  };
+  if (rt && cr) return tw(r, c - 3);
+  if (rr && ct) return tw(c, r - 3);
+  if (rt && c == 6) return S[10 + r];
+  if (r == 6 && ct) return S[10 + c];
+  if (r == 6 && c == 6) return S[20];
+  return 0.0;
+}
+
+// tau = -H7^-1 g7 by the 32 lanes of a warp (lanes 0..6 hold rows):
+// Jacobi scaling s = diag(H7)^-1/2, FP32 Cholesky of s H7 s, then iterative
+// refinement x <- x + s (L L^T)^-1 s (b - H7 x) with the residual in FP64,
+// stopped when the predicted next correction (the last one times the
+// observed contraction) is below 1e-9 of |x|, as in the mixed-precision
+// graph solve.  Returns false in every lane (the caller then uses the FP64
+// factorisation, which applies the exact not-positive-definite rule) when a
+// diagonal entry is not positive, an FP32 pivot is not above 2^-20 of the
+// unit diagonal, a value is not finite or the refinement stalls.  On success
+// lanes 0..6 return their entry of tau in *tau.
+constexpr int kTrackRefine = 8;
+__device__ bool track_mixed_solve(const double* __restrict__ H7, const double* __restrict__ g7, int lane,
+                                  double* tau) {
+  constexpr unsigned kAll = 0xffffffffu;
+  const bool row = lane < 7;
+  const int i = row ? lane : 0;
+  const double hii = H7[8 * i];
+  if (!__all_sync(kAll, hii > 0.0 && hii < INFINITY)) return false;
+  const double sc = rsqrt_newton(hii);
+  float L[7], inv[7];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) L[k] = (float)(sc * H7[7 * i + k] * __shfl_sync(kAll, sc, k));
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < 7; ++j) {
+    const float djj = __shfl_sync(kAll, L[j], j);
+    const bool okj = djj > 9.5367431640625e-7f && djj < INFINITY;  // 2^-20 of the unit diagonal
+    ok = ok && okj;
+    inv[j] = rsqrtf(okj ? djj : 1.0f);
+    const float lij = L[j] * inv[j];
+    if (lane >= j) L[j] = lij;
+#pragma unroll
+    for (int k = j + 1; k < 7; ++k) {
+      const float lkj = __shfl_sync(kAll, L[j], k);
+      if (lane >= k) L[k] = fmaf(-lij, lkj, L[k]);
+    }
+  }
+  if (!ok) return false;  // the pivots are broadcast: the same decision in every lane
+  // each lane also keeps its column of L (Lc[j] = L_ji, held by lane j)
+  float Lc[7];
+#pragma unroll
+  for (int j = 0; j < 7; ++j) {
+    Lc[j] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      const float v = __shfl_sync(kAll, L[k], j);
+      if (k == i) Lc[j] = v;
+    }
+  }
+  // (L L^T)^-1 of the lanes' right-hand side entries
+  auto solve = [&](float rhs) {
+    float acc = rhs, y = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+      const float yj = __shfl_sync(kAll, acc, j) * inv[j];
+      if (lane == j) y = yj;
+      if (lane > j) acc = fmaf(-L[j], yj, acc);
+    }
+    float acc2 = y, z = 0.0f;
+#pragma unroll
+    for (int j = 6; j >= 0; --j) {
+      const float zj = __shfl_sync(kAll, acc2, j) * inv[j];
+      if (lane == j) z = zj;
+      if (lane < j) acc2 = fmaf(-Lc[j], zj, acc2);
+    }
+    return z;
+  };
+  const double b = row ? -g7[i] : 0.0;
+  double x = 0.0, r = b, zprev = 0.0;
+  for (int it = 0; it < kTrackRefine; ++it) {
+    const float z = solve((float)(sc * r));  // every lane takes part in the shuffles
+    const double dx = row ? sc * (double)z : 0.0;
+    x += dx;
+    double zm = fabs(dx), xm = fabs(x);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      zm = fmax(zm, __shfl_xor_sync(kAll, zm, off));
+      xm = fmax(xm, __shfl_xor_sync(kAll, xm, off));
+    }
+    if (!(zm < INFINITY && xm < INFINITY)) return false;
+    if (zm == 0.0) break;
+    if (it > 0) {  // contraction rho = zm / zprev (zprev > 0 here)
+      if (zm * zm <= 1e-9 * xm * zprev) break;
+      if (it > 1 && zm > 0.5 * zprev) return false;  // stalled
+    }
+    if (it == kTrackRefine - 1) return false;
+    zprev = zm;
+    // r = b - H7 x in FP64
+    double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      const double xk = __shfl_sync(kAll, x, k);
+      if (k & 1) s1 = fma(H7[7 * i + k], xk, s1);
+      else s0 = fma(H7[7 * i + k], xk, s0);
+    }
+    r = row ? b - (s0 + s1) : 0.0;
+  }
+  *tau = x;
+  return true;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kLinThreads) track_kernel(PlanView pv, LinConst lc, double conv_tol,
                                                             double* __restrict__ T_wc,
@@ -1193,27 +1327,44 @@ __global__ void __launch_bounds__(kLinThreads) track_kernel(PlanView pv, LinCons
                                                             const int32_t* __restrict__ counts,
                                                             float* __restrict__ partials, int32_t* __restrict__ done,
                                                             int32_t* __restrict__ dev_status) {
-  __shared__ float red[kLinThreads / 32][kFamAcc];
+  constexpr int kWarps = kLinThreads / 32;
+  constexpr int kGroups = kWarps - 1;  // warps summing the tile partials in the finishing block
+  __shared__ float red[kWarps][kFamAcc];
   __shared__ float sP[12];
-  __shared__ int s_last;
-  __shared__ double S[kNumAcc], Hr[49], A[49], C[49], H7[49], gr[7], g7[7];
-  __shared__ double Sg[kLinThreads / 32][kNumAcc];
+  __shared__ int s_last, s_status, s_fb;
+  __shared__ double S[kNumAcc], Hr[49], A[49], C[49], H7[49], g7[7];
+  __shared__ double Sg[kGroups][kNumAcc];
+  __shared__ double sR[18], s_inv, s_tp[3];  // R_i, R_j (row-major), 1 / s_i, t of T_i^-1
   __shared__ double s_tau[7], s_part[10], s_mx;
-  __shared__ int s_status;
-  const int tid = threadIdx.x, tile = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, tile = blockIdx.x;
   const DevTile tl = pv.tiles[tile];
   const DevEdge ed = pv.edges[tl.edge];
   const int g = ed.graph;
   // a converged or failed graph is skipped by all of its blocks (its status
   // changes only in the block that finishes the graph, after they all ran)
   if (__ldcg(dev_status + g) > 0) return;
-  if (tid == 0) {
-    const Sim3d Ti = load_pose(T_wc + 8 * ed.i), Tj = load_pose(T_wc + 8 * ed.j);
-    const Sim3d Tij = compose(inverse(Ti), Tj);
-    double R[9];
-    rot_of(Tij.q, R);
-    for (int k = 0; k < 9; ++k) sP[k] = (float)(Tij.s * R[k]);
-    for (int k = 0; k < 3; ++k) sP[9 + k] = (float)Tij.t[k];
+  const double* Ti = T_wc + 8 * ed.i;
+  const double* Tj = T_wc + 8 * ed.j;
+  // T_ij = T_i^-1 T_j = (s_j / s_i R_i^T R_j, R_i^T (t_j - t_i) / s_i) in FP64
+  // by lanes of warp 0: the entries of R_i, R_j and 1 / s_i, then the twelve
+  // entries of s R and t of T_ij (no block of this launch changes a pose
+  // before every block has read them here)
+  if (warp == 0) {
+    if (lane < 18) {
+      const int e = lane % 9;
+      sR[lane] = rot_entry((lane < 9 ? Ti : Tj) + 3, e / 3, e % 3);
+    }
+    if (lane == 18) s_inv = rcp_newton(Ti[7]);
+    __syncwarp();
+    if (lane < 9) {
+      const int r = lane / 3, c = lane % 3;
+      const double v = sR[r] * sR[9 + c] + sR[3 + r] * sR[12 + c] + sR[6 + r] * sR[15 + c];
+      sP[lane] = (float)(Tj[7] * s_inv * v);
+    } else if (lane < 12) {
+      const int r = lane - 9;
+      const double v = sR[r] * (Tj[0] - Ti[0]) + sR[3 + r] * (Tj[1] - Ti[1]) + sR[6 + r] * (Tj[2] - Ti[2]);
+      sP[lane] = (float)(s_inv * v);
+    }
   }
   __syncthreads();
   RelPose P;
@@ -1239,30 +1390,53 @@ __global__ void __launch_bounds__(kLinThreads) track_kernel(PlanView pv, LinCons
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  {
-    // eight groups of lanes take every eighth tile (loads of several tiles in
-    // flight), then the groups' FP64 sums are added in a fixed order
-    const int a = tid & 31, grp = tid >> 5;
-    if (a < kNumAcc) {
+  if (warp < kGroups) {
+    // seven warps take every seventh tile (loads of several tiles in flight),
+    // then the groups' FP64 sums are added in a fixed order
+    if (lane < kNumAcc) {
       double sum = 0.0;
 #pragma unroll 4
-      for (int t = ed.tile_begin + grp; t < ed.tile_end; t += kLinThreads / 32)
-        sum += (double)__ldcg(partials + (size_t)t * kAccStride + a);
-      Sg[grp][a] = sum;
+      for (int t = ed.tile_begin + warp; t < ed.tile_end; t += kGroups)
+        sum += (double)__ldcg(partials + (size_t)t * kAccStride + lane);
+      Sg[warp][lane] = sum;
     }
-  }
-  if (tid == 32) {
-    const Sim3d Ti = load_pose(T_wc + 8 * ed.i);
-    adjoint_of(inverse(Ti), A);
+  } else {
+    // meanwhile the last warp forms Ad_{T_i^-1} =
+    // [[s' R', [t']x R', -t'], [0, R', 0], [0, 0, 1]] with R' = R_i^T,
+    // s' = 1 / s_i, t' = -s' R_i^T t_i (R_i and s' from the start of the block)
+    if (lane < 3) s_tp[lane] = -s_inv * (sR[lane] * Ti[0] + sR[3 + lane] * Ti[1] + sR[6 + lane] * Ti[2]);
+    __syncwarp();
+    for (int e = lane; e < 49; e += 32) {
+      const int r = e / 7, c = e % 7;
+      double v = 0.0;
+      if (r < 3 && c < 3) {
+        v = s_inv * sR[3 * c + r];
+      } else if (r < 3 && c < 6) {
+        const int cc = c - 3;  // row r of [t']x times column cc of R' (row cc of R_i)
+        const double x0 = r == 0 ? 0.0 : r == 1 ? s_tp[2] : -s_tp[1];
+        const double x1 = r == 0 ? -s_tp[2] : r == 1 ? 0.0 : s_tp[0];
+        const double x2 = r == 0 ? s_tp[1] : r == 1 ? -s_tp[0] : 0.0;
+        v = x0 * sR[3 * cc] + x1 * sR[3 * cc + 1] + x2 * sR[3 * cc + 2];
+      } else if (r < 3) {
+        v = -s_tp[r];
+      } else if (r < 6 && c >= 3 && c < 6) {
+        v = sR[3 * (c - 3) + (r - 3)];
+      } else if (r == 6 && c == 6) {
+        v = 1.0;
+      }
+      A[e] = v;
+    }
   }
   __syncthreads();
   if (tid < kNumAcc) {
     double sum = 0.0;
-    for (int w = 0; w < kLinThreads / 32; ++w) sum += Sg[w][tid];
+    for (int w = 0; w < kGroups; ++w) sum += Sg[w][tid];
     S[tid] = sum;
   }
   __syncthreads();
-  if (tid == 0) ray_relative_system(S, Hr, gr);
+  // the relative system Hr, C = Hr A, then H7 = A^T C and g7 = +-A^T g_rel
+  // (entries in parallel lanes)
+  if (tid < 49) Hr[tid] = hr_entry(S, tid / 7, tid % 7);
   __syncthreads();
   if (tid < 49) {
     const int r = tid / 7, c = tid % 7;
@@ -1283,15 +1457,30 @@ __global__ void __launch_bounds__(kLinThreads) track_kernel(PlanView pv, LinCons
   if (tid >= 64 && tid < 71) {
     const int r = tid - 64;
     double v = 0.0;
-    for (int k = 0; k < 7; ++k) v += A[7 * k + r] * gr[k];
+    for (int k = 0; k < 7; ++k) v += A[7 * k + r] * S[21 + k];
     g7[r] = sgn * v;
   }
   __syncthreads();
-  if (tid == 0) {
+  if (warp == 0) {
+    double t = 0.0;
+    const bool ok = track_mixed_solve(H7, g7, lane, &t);
+    if (ok) {
+      double mx = lane < 7 ? fabs(t) : 0.0;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+      if (lane < 7) s_tau[lane] = t;
+      if (lane == 0) {
+        s_mx = mx;
+        s_status = 0;
+      }
+    }
+    if (lane == 0) s_fb = ok ? 0 : 1;
+  }
+  __syncthreads();
+  if (s_fb && tid == 0) {
     // FP64 Cholesky H7 = L L^T (lower triangle in place), pivots checked
     // against the diagonal as in the FP64 solve, then tau = -H7^-1 g7
-    // (reciprocal pivots from rsqrt_newton: FP64 division and square root
-    // are long latency chains on this part; products replace them)
+    // (reciprocal pivots from rsqrt_newton)
     double L[49], diag[7], tau[7], il[7];
     for (int k = 0; k < 49; ++k) L[k] = H7[k];
     for (int j = 0; j < 7; ++j) diag[j] = H7[8 * j];
@@ -1336,16 +1525,75 @@ __global__ void __launch_bounds__(kLinThreads) track_kernel(PlanView pv, LinCons
     s_status = status;
   }
   __syncthreads();
-  // Exp(tau): its transcendental pieces side by side in eight threads
-  if (s_status == 0 && tid < 8) sim3_exp_piece(s_tau, tid, s_part);
+  const int status0 = s_status;
+  // Exp(tau): its transcendental pieces in different warps side by side
+  if (status0 == 0 && lane == 0) sim3_exp_piece(s_tau, warp, s_part);
   __syncthreads();
-  if (tid == 0) {
-    int status = s_status;
-    if (status == 0) {
-      const Sim3d E = sim3_exp_parts(s_tau, s_part);
-      store_pose(compose(E, load_pose(T_wc + 8 * k_free)), T_wc + 8 * k_free);
-      if (s_mx < conv_tol) status = 1;
+  double* Tk = T_wc + 8 * k_free;
+  if (status0 == 0) {
+    // Exp(tau) = (t_E = V rho, q_E, s_E = e^sigma), V = a I + b [phi]x + c [phi]x^2
+    // (the formulas of sim3_exp_parts, with Newton reciprocals), composed
+    // with T_k: t = s_E R_E t_k + t_E by three lanes of warp 0 (each forms b,
+    // c and q_E itself), q = q_E (x) q_k normalised by four lanes of warp 1,
+    // s = s_E s_k by warp 2; no barrier between the pieces and the result
+    const double px = s_tau[3], py = s_tau[4], pz = s_tau[5], sg = s_tau[6];
+    const double th2 = px * px + py * py + pz * pz;
+    // q_E, normalised: the half-angle terms of piece 2
+    const double hq = s_part[3], q3 = s_part[4];
+    if (warp == 0 && lane < 3) {
+      const double iqn = rsqrt_newton(hq * hq * th2 + q3 * q3);
+      const double a = s_part[5];
+      double b, c;
+      if (s_part[1] == 0.0) {  // the small-angle branch (piece 0 left sin and cos at 0)
+        b = s_part[6] - th2 * s_part[7] * (1.0 / 6.0);
+        c = 0.5 * s_part[8] - th2 * s_part[9] * (1.0 / 24.0);
+      } else {
+        const double ith = rsqrt_newton(th2), th = th2 * ith;
+        const double sn = s_part[0], cs = s_part[1], es = s_part[2];
+        const double iden = rcp_newton(sg * sg + th2);
+        const double ic = ((es * cs - 1.0) * sg + es * th * sn) * iden;  // int e^{sx} cos(th x)
+        const double is = (es * sn * sg - (es * cs - 1.0) * th) * iden;  // int e^{sx} sin(th x)
+        b = is * ith;
+        c = (a - ic) * (ith * ith);
+      }
+      const int r = lane, n = (r + 1) % 3, o = (r + 2) % 3;
+      const double rv[3] = {s_tau[0], s_tau[1], s_tau[2]};
+      const double ph[3] = {px, py, pz};
+      // (phi x rho)_m and (phi x (phi x rho))_r
+      auto cr = [&](int m) {
+        const int m1 = (m + 1) % 3, m2 = (m + 2) % 3;
+        return ph[m1] * rv[m2] - ph[m2] * rv[m1];
+      };
+      const double c_r = cr(r), c_n = cr(n), c_o = cr(o);
+      const double d_r = ph[n] * c_o - ph[o] * c_n;
+      const double tE = a * rv[r] + b * c_r + c * d_r;
+      const double qE[4] = {hq * px * iqn, hq * py * iqn, hq * pz * iqn, q3 * iqn};
+      const double v = rot_entry(qE, r, 0) * Tk[0] + rot_entry(qE, r, 1) * Tk[1] + rot_entry(qE, r, 2) * Tk[2];
+      const double tn = s_part[2] * v + tE;
+      __syncwarp(0x7u);  // every lane has read t_k
+      Tk[r] = tn;
     }
+    if (warp == 1 && lane < 4) {
+      const double iqn = rsqrt_newton(hq * hq * th2 + q3 * q3);
+      const double qE[4] = {hq * px * iqn, hq * py * iqn, hq * pz * iqn, q3 * iqn};
+      const double a3 = qE[3], b3 = Tk[6];
+      double v;
+      if (lane == 3) {
+        v = a3 * b3 - (qE[0] * Tk[3] + qE[1] * Tk[4] + qE[2] * Tk[5]);
+      } else {
+        const int n = (lane + 1) % 3, o = (lane + 2) % 3;
+        v = a3 * Tk[3 + lane] + b3 * qE[lane] + (qE[n] * Tk[3 + o] - qE[o] * Tk[3 + n]);
+      }
+      double n2 = v * v;
+      n2 += __shfl_xor_sync(0xfu, n2, 1);
+      n2 += __shfl_xor_sync(0xfu, n2, 2);  // also: every lane has read q_k
+      Tk[3 + lane] = v * rsqrt_newton(n2);
+    }
+    if (warp == 2 && lane == 0) Tk[7] = s_part[2] * Tk[7];
+  }
+  if (tid == 0) {
+    int status = status0;
+    if (status == 0 && s_mx < conv_tol) status = 1;
     if (status != 0) dev_status[g] = status;
     done[tl.edge] = 0;  // ready for the next iteration
   }

@@ -278,6 +278,23 @@ def test_gn_track_several_frames(M):
         gn_g.run_tracking(g.T_init.cuda(), 2)
 
 
+def test_gn_track_without_matches_is_not_pd(M):
+    """A tracking frame with no valid match has a zero 7 x 7 system: the
+    mixed-precision solve declines it (no positive diagonal), the FP64
+    factorisation reports MSLAM_ERR_NOT_PD, and neither pose moves."""
+    from paper_2412_12392_gb300 import _lib
+    w = synth.tracking(seed=2, H=96, W=128).to_storage(torch.float16)
+    P = M.default_params()
+    plan = M.Plan(w.kf_hw.numpy(), w.edges.numpy(), opts={"lin_tile": 1024})
+    wd = w.to("cuda")
+    idx = torch.full((plan.edge_pixels,), -1, dtype=torch.int32, device="cuda")
+    q = torch.zeros(plan.edge_pixels, dtype=torch.float16, device="cuda")
+    gn = M.GaussNewton(plan, P, wd.X_canon, idx, q, packed=True)
+    T = gn.run_tracking(w.T_init.cuda(), 3).cpu()
+    assert int(gn.status[0]) == _lib.MSLAM_ERR_NOT_PD
+    assert torch.equal(T, w.T_init)
+
+
 @pytest.mark.parametrize("dtype,d", [(torch.float16, 24), (torch.float32, 16), (torch.float16, 32)])
 def test_desc_to_chunked_is_the_permutation(M, dtype, d):
     """mslam_desc_to_chunked (whole pool and a slice of a larger pool) equals

@@ -120,16 +120,19 @@ def test_global_full_size_gauss_newton(M, global_wl):
     """The benchmark's step on the benchmark's graph: the batched matching
     launch, then mslam_gn_pack and 10 iterations of the packed linearisation
     and the mixed-precision solve in the launch configuration the benchmark
-    keeps (16 x 16 match blocks, register-pipeline linearisation with
-    16384-pixel tiles), against the oracle's Gauss-Newton (literal 14 x 14
-    blocks, dense FP64 Cholesky) on the same matches and confidences: every
-    one of the 64 poses within 1e-5.  About two minutes of oracle time on 16
-    host threads."""
+    keeps (8 x 32 match blocks with two query pixels per thread, the
+    prefetching register-pipeline linearisation with 16384-pixel tiles),
+    against the oracle's Gauss-Newton (literal 14 x 14 blocks, dense FP64
+    Cholesky) on the same matches and confidences: every one of the 64 poses
+    within 1e-5.  The plain register pipeline (lin_form 1) on the same
+    records gives the same poses bit for bit.  About two minutes of oracle
+    time on 16 host threads."""
     w = global_wl
     P = M.default_params()
     par = M.params_dict(P)
     plan = M.Plan(w.kf_hw.numpy(), w.edges.numpy(),
-                  opts={"match_block_w": 16, "lin_tile": 16384, "lin_blocks_per_sm": 3, "lin_form": 1})
+                  opts={"match_block_w": 8, "match_ppt": 2, "lin_tile": 16384, "lin_blocks_per_sm": 2,
+                        "lin_form": 3})
     Dr, Dq = M.chunk_descriptors(w.D_ref), M.chunk_descriptors(w.D_qry)
     idx_g, q_g = M.match(plan, P, w.X_ref, w.X_qry, Dr, Dq, w.Q_ref, w.Q_qry)
     del Dr, Dq
@@ -137,6 +140,10 @@ def test_global_full_size_gauss_newton(M, global_wl):
     T_g = gn.run(w.T_init.cuda(), w.n_gn_iters).cpu()
     status = gn.status.cpu()
     assert int(status[0]) in (0, 1)
+    plan1 = M.Plan(w.kf_hw.numpy(), w.edges.numpy(), opts=dict(plan.opts, lin_form=1))
+    gn1 = M.GaussNewton(plan1, P, w.X_canon, idx_g, q_g, packed=True)
+    assert torch.equal(gn1.run(w.T_init.cuda(), w.n_gn_iters).cpu(), T_g)
+    del gn1, plan1
     st, T_r, hist, done = oracle.gauss_newton(w.N, w.edges.numpy(), w.kf_off.numpy(), w.e_off.numpy(),
                                               w.X_canon.cpu(), idx_g.cpu(), q_g.cpu(), w.T_init.numpy(),
                                               w.n_gn_iters, **par)

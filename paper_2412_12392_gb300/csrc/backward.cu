@@ -431,8 +431,10 @@ __global__ void bwd_pose_out_kernel(int N, const double* __restrict__ T_wc, cons
 __global__ void __launch_bounds__(kSolveThreads) bwd_rhs_kernel(PlanView pv, const double* __restrict__ a,
                                                                 double* __restrict__ bout,
                                                                 const int32_t* __restrict__ dev_status,
-                                                                double* __restrict__ ws) {
+                                                                double* __restrict__ ws,
+                                                                const int32_t* __restrict__ skip) {
   const int g = blockIdx.x;
+  if (skip && skip[g]) return;  // solved by the mixed-precision kernel
   const DevGraph G = pv.graphs[g];
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
   const int m = G.m;
@@ -514,9 +516,12 @@ __global__ void __launch_bounds__(kSolveThreads) bwd_rhs_kernel(PlanView pv, con
 
 using namespace mslam;
 
-extern mslam_status mslam_factor_only(const mslam_plan* plan, const float* H_blocks, const float* g_blocks,
-                                      double* tau, int32_t* dev_status, double* ws, cudaStream_t s);
-
+extern mslam_status mslam_bwd_solve_tau(const mslam_plan* plan, const float* H_blocks, const float* g_blocks,
+                                        double* tau, int32_t* dev_status, double* ws, cudaStream_t s,
+                                        bool* mixed_used);
+extern mslam_status mslam_bwd_solve_rhs(const mslam_plan* plan, const float* H_blocks, const float* g_blocks,
+                                        const double* rhs, double* x, double* tau, int32_t* dev_status,
+                                        double* ws, int32_t* handled2, cudaStream_t s);
 // Both adjoint entry points: the cost and step terms with respect to X and q
 // and, when dL_dT is given, the poses (with the retraction T' = Exp(tau) T
 // and an upstream gradient dL_dTnew on T').
@@ -577,9 +582,12 @@ static mslam_status step_backward(const char* who, const mslam_params* p, const 
   double* a_tot = pose_ws;
   double* acc = pose_ws + 7 * (size_t)pv.N;
   double* xi = pose_ws + 14 * (size_t)pv.N;
+  int32_t* handled2 = reinterpret_cast<int32_t*>(pose_ws + 14 * (size_t)pv.N + 7 * (size_t)std::max(pv.E, 1));
+  bool mixed = false;
   if (with_step || dL_dT) {
-    // factor H (and compute tau) without touching the poses
-    st = mslam_factor_only(plan, H_blocks, g_blocks, tvec, dev_status, ws, s);
+    // tau = -H^-1 g without touching the poses (the FP32 factor with FP64
+    // refinement where it applies, kept for b; the FP64 factor elsewhere)
+    st = mslam_bwd_solve_tau(plan, H_blocks, g_blocks, tvec, dev_status, ws, s, &mixed);
     if (st != MSLAM_OK) return st;
   }
   if (dL_dT) {
@@ -588,8 +596,15 @@ static mslam_status step_backward(const char* who, const mslam_params* p, const 
     bwd_pose_in_kernel<<<(pv.N + 63) / 64, 64, 0, s>>>(pv.N, T_wc, tvec, dL_dTnew, dL_dtau, a_tot, acc);
   }
   if (with_step) {
-    // b = H^-1 a with a = dL_dtau (+ the retraction's J_l^T dL/dT' with poses)
-    bwd_rhs_kernel<<<pv.G, kSolveThreads, 0, s>>>(pv, dL_dT ? a_tot : dL_dtau, bvec, dev_status, ws);
+    // b = H^-1 a with a = dL_dtau (+ the retraction's J_l^T dL/dT' with poses):
+    // the kept FP32 factor with FP64 refinement, then the FP64 substitution
+    // for the graphs it did not solve
+    const double* a = dL_dT ? a_tot : dL_dtau;
+    if (mixed) {
+      st = mslam_bwd_solve_rhs(plan, H_blocks, g_blocks, a, bvec, tvec, dev_status, ws, handled2, s);
+      if (st != MSLAM_OK) return st;
+    }
+    bwd_rhs_kernel<<<pv.G, kSolveThreads, 0, s>>>(pv, a, bvec, dev_status, ws, mixed ? handled2 : nullptr);
   }
   BwdConst bc;
   bc.inv_sr2 = 1.0f / (p->sigma_ray * p->sigma_ray);

@@ -643,10 +643,12 @@ size_t mslam_workspace_bytes(const mslam_plan* plan, int32_t op) {
     case MSLAM_OP_BACKWARD:
       // the solve's workspace, b and tau (7 N doubles each), per-edge data
       // (32 floats per edge), then for the pose term the step's right-hand
-      // side and the pose gradient (7 N doubles each) and Xi (7 E doubles)
+      // side and the pose gradient (7 N doubles each) and Xi (7 E doubles),
+      // then one flag per graph for the second solve
       return mslam_workspace_bytes(plan, MSLAM_OP_SOLVE) + align256(sizeof(double) * 14 * (size_t)plan->N) +
              align256(sizeof(float) * 32 * (size_t)std::max(plan->E, 1)) +
-             align256(sizeof(double) * (14 * (size_t)plan->N + 7 * (size_t)std::max(plan->E, 1)));
+             align256(sizeof(double) * (14 * (size_t)plan->N + 7 * (size_t)std::max(plan->E, 1))) +
+             align256(sizeof(int32_t) * std::max<size_t>(plan->graphs.size(), 1));  // flags of the second solve
     default:
       return 0;
   }

@@ -27,6 +27,14 @@ struct SolveConst {
   int factor_only;      // 1: factor and write tau, never touch poses or the converged flag
   int smem_doubles;     // dynamic shared memory available per CTA (doubles)
   const int32_t* skip;  // per graph: 1 = already solved by the mixed-precision kernel (may be NULL)
+  // the mixed-precision kernel for the adjoint (never touches poses or the
+  // converged flag): 0 = the forward step, 1 = x = tau = -H^-1 g into x_out
+  // and the FP32 factor kept in the workspace, 2 = x = H^-1 rhs into x_out
+  // with the kept factor, for the graphs whose handled_in flag is set
+  int bwd_mode;
+  const double* rhs;         // [N, 7] in pose order (mode 2)
+  double* x_out;             // [N, 7] in pose order, zero for the fixed pose (modes 1, 2)
+  const int32_t* handled_in; // per graph: 1 = mode 1 kept its factor (mode 2)
 };
 
 __global__ void __launch_bounds__(kSolveThreads) solve_kernel(PlanView pv, SolveConst sc,
@@ -609,10 +617,10 @@ __device__ __forceinline__ double jacobi_scale(const float* __restrict__ H14, co
 __global__ void __launch_bounds__(64) solve_assemble_kernel(PlanView pv, const float* __restrict__ H14,
                                                             const float* __restrict__ g14,
                                                             const int32_t* __restrict__ dev_status,
-                                                            double* __restrict__ ws) {
+                                                            double* __restrict__ ws, int max_status) {
   const int g = blockIdx.y;
   const DevGraph G = pv.graphs[g];
-  if (dev_status[g] > 0 || G.m == 0) return;  // the solve kernels skip these graphs too
+  if (dev_status[g] > max_status || G.m == 0) return;  // the solve kernels skip these graphs too
   const int nb = G.n_blocks;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nb * kLfBlock) return;
@@ -682,7 +690,8 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
   __shared__ int s_fail, s_done, s_nonfinite;
   __shared__ double s_zmax, s_xmax, s_zprev, s_max;
   const int m = G.m, nb = G.n_blocks;
-  if (dev_status[g] > 0 || m == 0) {
+  const int bwd = sc.bwd_mode;
+  if (dev_status[g] > (bwd ? 1 : 0) || m == 0 || (bwd == 2 && !sc.handled_in[g])) {
     // converged or failed earlier, or nothing to solve: the FP64 kernel
     // handles these cases exactly as before
     if (tid == 0) handled[g] = 0;
@@ -713,9 +722,12 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
     const double* sg = ws + G.ws_mixed + (size_t)nb * 28;
     for (int t = tid; t < n7; t += nth) {
       scl[t] = sg[t];
-      bv[t] = sg[n7 + t];
+      bv[t] = bwd == 2 ? sc.rhs[7 * __ldg(pv.ints + G.off_pose + t / 7) + t % 7] : sg[n7 + t];
       xv[t] = 0.0;
     }
+    // mode 2: the reciprocal pivots that mode 1 left in the -g slot
+    if (bwd == 2)
+      for (int t = tid; t < n7; t += nth) ivf[t] = reinterpret_cast<const float*>(sg + n7)[t];
   }
   const int32_t* pose_of_pos = sI;
   const int32_t* col_ptr = sI + (G.off_col - G.off_pose);
@@ -746,8 +758,8 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
     return;
   }
 
-  // ---- FP32 factorisation of S H S by levels
-  for (int l = 0; l < G.n_levels; ++l) {
+  // ---- FP32 factorisation of S H S by levels (mode 2 reuses mode 1's)
+  for (int l = 0; l < (bwd == 2 ? 0 : G.n_levels); ++l) {
     const int q0 = lev_ptr[l], q1 = lev_ptr[l + 1];
     const int g0 = levupd[l], g1 = levupd[l + 1];  // targets of the level that receive updates
     for (int w = tid; w < (g1 - g0) * 49; w += nth) {
@@ -820,6 +832,18 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
   if (s_fail) {
     if (tid == 0) handled[g] = 0;
     return;
+  }
+  if (bwd == 1) {
+    // keep the factor for mode 2: the shared-memory factor back to the
+    // workspace (where the assembly wrote its input) and the reciprocal
+    // pivots in the -g slot (read above, no longer needed)
+    double* sgw = ws + G.ws_mixed + (size_t)nb * 28;
+    if (!kGlobalL) {
+      float4* dst = reinterpret_cast<float4*>(ws + G.ws_mixed);
+      const float4* src = reinterpret_cast<const float4*>(Lf);
+      for (int t = tid; t < nb * (kLfBlock / 4); t += nth) dst[t] = src[t];
+    }
+    for (int t = tid; t < n7; t += nth) reinterpret_cast<float*>(sgw + n7)[t] = ivf[t];
   }
 
   // ---- explicit inverses of the diagonal factor blocks: thread (p, k)
@@ -980,6 +1004,13 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
     if (tid == 0) handled[g] = 0;
     return;
   }
+  if (bwd) {
+    // the adjoint's solves: x in pose order, nothing else changes
+    for (int t = tid; t < n7; t += nth) sc.x_out[7 * (size_t)pose_of_pos[t / 7] + t % 7] = xv[t];
+    if (tid < 7) sc.x_out[7 * (size_t)G.gauge + tid] = 0.0;
+    if (tid == 0) handled[g] = 1;
+    return;
+  }
 
   // ---- step statistics, tau, retraction (as in the FP64 kernel)
   if (warp == 0) {
@@ -1079,6 +1110,14 @@ static int mixed_smem_bytes(const mslam_plan* plan, bool* global_factor = nullpt
   return 0;
 }
 
+// The per-graph flags of the mixed-precision kernel, after the solve's FP64
+// workspace.
+static int32_t* solve_flags(const mslam_plan* plan, double* ws) {
+  return reinterpret_cast<int32_t*>(reinterpret_cast<char*>(ws) +
+                                    ((sizeof(double) * std::max<int64_t>(plan_solve_ws_doubles(plan), 1) + 255) &
+                                     ~size_t(255)));
+}
+
 static mslam_status launch_solve(const PlanView& pv, SolveConst sc, const float* H, const float* g, double* T,
                                  double* tau, int32_t* st, double* ws, cudaStream_t s) {
   smem_limit_bytes();
@@ -1129,6 +1168,10 @@ extern "C" mslam_status mslam_gn_solve(const mslam_params* p, const mslam_plan* 
   sc.factor_only = 0;
   sc.smem_doubles = solve_smem_doubles(plan);
   sc.skip = nullptr;
+  sc.bwd_mode = 0;
+  sc.rhs = nullptr;
+  sc.x_out = nullptr;
+  sc.handled_in = nullptr;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   double* ws = static_cast<double*>(workspace);
   bool global_factor = false;
@@ -1136,12 +1179,10 @@ extern "C" mslam_status mslam_gn_solve(const mslam_params* p, const mslam_plan* 
   if (mixed > 0 && pv.E > 0) {
     // FP32 factorisation + FP64 refinement first; graphs it declines (or
     // that need no solve) go through the FP64 kernel, which skips the rest
-    int32_t* handled = reinterpret_cast<int32_t*>(static_cast<char*>(workspace) +
-                                                  ((sizeof(double) * std::max<int64_t>(plan_solve_ws_doubles(plan), 1) + 255) &
-                                                   ~size_t(255)));
+    int32_t* handled = solve_flags(plan, ws);
     const int elems = (int)plan_max_mixed_elems(plan);
     solve_assemble_kernel<<<dim3(std::max(1, (elems + 63) / 64), pv.G), 64, 0, s>>>(pv, H_blocks, g_blocks,
-                                                                                     dev_status, ws);
+                                                                                     dev_status, ws, 0);
     if (global_factor)
       solve_mixed_kernel<true><<<pv.G, kMixThreads, mixed, s>>>(pv, sc, T_wc, tau, dev_status, ws, handled);
     else
@@ -1160,13 +1201,82 @@ extern "C" int32_t mslam_gn_solve_launches(const mslam_plan* plan) {
 
 // Factor every graph's system and write tau = -H^-1 g without updating poses
 // (used by the adjoint, which needs the factorisation and the step).
-mslam_status mslam_factor_only(const mslam_plan* plan, const float* H_blocks, const float* g_blocks, double* tau,
-                               int32_t* dev_status, double* ws, cudaStream_t s) {
+// The adjoint's first solve, tau = -H^-1 g for every graph (converged ones
+// included), no pose touched: the mixed-precision kernel in mode 1 (its FP32
+// factor kept in the workspace for the second solve) for the graphs it
+// accepts, the FP64 factor-only solve for the others.  *mixed tells whether
+// the mixed-precision kernel ran (its flags: the solve workspace's).
+mslam_status mslam_bwd_solve_tau(const mslam_plan* plan, const float* H_blocks, const float* g_blocks, double* tau,
+                                 int32_t* dev_status, double* ws, cudaStream_t s, bool* mixed_used) {
   const PlanView pv = plan_view(plan);
   SolveConst sc;
   sc.conv_tol = 0.0;
   sc.factor_only = 1;
   sc.smem_doubles = solve_smem_doubles(plan);
   sc.skip = nullptr;
+  sc.bwd_mode = 0;
+  sc.rhs = nullptr;
+  sc.x_out = nullptr;
+  sc.handled_in = nullptr;
+  *mixed_used = false;
+  bool global_factor = false;
+  const int mixed = mixed_smem_bytes(plan, &global_factor);
+  if (mixed > 0 && pv.E > 0) {
+    int32_t* handled = solve_flags(plan, ws);
+    const int elems = (int)plan_max_mixed_elems(plan);
+    solve_assemble_kernel<<<dim3(std::max(1, (elems + 63) / 64), pv.G), 64, 0, s>>>(pv, H_blocks, g_blocks,
+                                                                                     dev_status, ws, 1);
+    SolveConst m1 = sc;
+    m1.factor_only = 0;
+    m1.bwd_mode = 1;
+    m1.x_out = tau;
+    if (global_factor)
+      solve_mixed_kernel<true><<<pv.G, kMixThreads, mixed, s>>>(pv, m1, nullptr, nullptr, dev_status, ws, handled);
+    else
+      solve_mixed_kernel<false><<<pv.G, kMixThreads, mixed, s>>>(pv, m1, nullptr, nullptr, dev_status, ws, handled);
+    mslam_status st = cuda_check(cudaGetLastError(), "gn_backward mixed launch");
+    if (st != MSLAM_OK) return st;
+    sc.skip = handled;
+    *mixed_used = true;
+  }
   return launch_solve(pv, sc, H_blocks, g_blocks, nullptr, tau, dev_status, ws, s);
 }
+
+// The adjoint's second solve after mslam_bwd_solve_tau used the
+// mixed-precision kernel: x = H^-1 rhs by mode 2 with the kept factor
+// (handled2[g] = 1 where it succeeded), then for every other graph the FP64
+// factor-only solve again (its tau once more, and its FP64 factor for the
+// caller's substitution, which skips the graphs flagged in handled2).
+mslam_status mslam_bwd_solve_rhs(const mslam_plan* plan, const float* H_blocks, const float* g_blocks,
+                                 const double* rhs, double* x, double* tau, int32_t* dev_status, double* ws,
+                                 int32_t* handled2, cudaStream_t s) {
+  const PlanView pv = plan_view(plan);
+  bool global_factor = false;
+  const int mixed = mixed_smem_bytes(plan, &global_factor);
+  SolveConst sc;
+  sc.conv_tol = 0.0;
+  sc.factor_only = 0;
+  sc.smem_doubles = solve_smem_doubles(plan);
+  sc.skip = nullptr;
+  sc.bwd_mode = 2;
+  sc.rhs = rhs;
+  sc.x_out = x;
+  sc.handled_in = solve_flags(plan, ws);
+  if (global_factor)
+    solve_mixed_kernel<true><<<pv.G, kMixThreads, mixed, s>>>(pv, sc, nullptr, nullptr, dev_status, ws, handled2);
+  else
+    solve_mixed_kernel<false><<<pv.G, kMixThreads, mixed, s>>>(pv, sc, nullptr, nullptr, dev_status, ws, handled2);
+  mslam_status st = cuda_check(cudaGetLastError(), "gn_backward mixed launch");
+  if (st != MSLAM_OK) return st;
+  SolveConst f;
+  f.conv_tol = 0.0;
+  f.factor_only = 1;
+  f.smem_doubles = solve_smem_doubles(plan);
+  f.skip = handled2;
+  f.bwd_mode = 0;
+  f.rhs = nullptr;
+  f.x_out = nullptr;
+  f.handled_in = nullptr;
+  return launch_solve(pv, f, H_blocks, g_blocks, nullptr, tau, dev_status, ws, s);
+}
+

@@ -121,10 +121,10 @@ def make_workload(args, rank: int, device, hw=None):
 
 # DRAM bytes (read + write) per query pixel of one batched matching launch,
 # from one ncu capture of match_kernel<__half, 24, 3, 2> (8 keyframes, 24
-# edges, 512x384, the FP32 ray image: 344,586,240 bytes for 4,718,592 query
+# edges, 512x384, the FP32 ray image: 344,033,024 bytes for 4,718,592 query
 # pixels), scaled to a launch by its query pixels.  Remove an entry when its
 # kernel changes.
-NCU_DRAM_BYTES_PER_QUERY_PX = {("match", 2, 24): 344586240 / 4718592}
+NCU_DRAM_BYTES_PER_QUERY_PX = {("match", 2, 24): 344033024 / 4718592}
 # DRAM bytes per matched pixel of one packed linearisation launch, FP16
 # records, scaled to a launch by its matches (1,637,856 matches in each
 # capture, 8 keyframes / 24 edges at 512x384): lin_packed_kernel (16384-record

@@ -96,3 +96,39 @@ def test_autograd_function(M):
     assert np.abs(tau.detach().cpu().numpy() - tau_r).max() <= 1e-4 * max(1.0, np.abs(tau_r).max())
     assert_grad_close(X.grad.cpu().numpy(), dXr, "autograd dX")
     assert_grad_close(qd.grad.cpu().numpy(), dqr, "autograd dq")
+
+
+@pytest.mark.parametrize("N,n_pairs,seed", [(12, 20, 7), (128, 300, 107)])
+def test_step_backward_mixed_solves_agree_with_fp64(M, N, n_pairs, seed):
+    """The adjoint's two solves (tau = -H^-1 g and b = H^-1 a) run by the
+    FP32 factor with FP64 refinement (the default; the 128-keyframe graph
+    factors in the workspace) against the FP64 factorisation (plan option
+    solve_form 1): the point, confidence and pose gradients of one step agree
+    to 1e-6 of their norm (the refinement stops when its predicted next
+    correction is below 1e-9 of |x|; the FP32 atomics of the gathered side
+    add their own summation-order rounding, about 1e-7)."""
+    from paper_2412_12392_gb300 import api
+    w = synth.global_graph(N=N, n_pairs=n_pairs, H=12, W=16, seed=seed)
+    P = M.default_params()
+    wd = w.to("cuda")
+    idx = w.gt_match.cuda()
+    q = (w.Q_qry.float() * 0.5 + 1.0).cuda()
+    T = w.T_init.clone().cuda()
+    rng = np.random.default_rng(seed)
+    a = torch.from_numpy(rng.normal(size=(w.N, 7)) * 1e-2).cuda()
+    G = torch.from_numpy(rng.normal(size=(w.N, 8)) * 0.1).cuda()
+    out = {}
+    for form in (0, 1):
+        plan = M.Plan(w.kf_hw.numpy(), w.edges.numpy(), opts={"solve_form": form})
+        if N == 128:
+            assert plan.counts[0] * 49 * 8 > 227 * 1024  # the FP32 factor goes to the workspace
+        H, g, _, _ = M.gn_linearize(plan, P, T, wd.X_canon, idx, q)
+        dX, dq, dT, st = api.gn_step_backward(plan, P, T, wd.X_canon, idx, q, H, g, dL_dTnew=G, dL_dtau=a,
+                                            dL_dcost=0.3)
+        torch.cuda.synchronize()
+        assert int(st.max()) <= 1, st
+        out[form] = [t.double().cpu().numpy() for t in (dX, dq, dT)]
+    for name, x, ref in zip(("dX", "dq", "dT"), out[0], out[1]):
+        e = rel_err(x, ref)
+        print(f"{N} keyframes, {name}: mixed against FP64 solves {e:.2e}")
+        assert e <= 1e-6, (name, e)

@@ -389,14 +389,19 @@ __device__ __forceinline__ double rcp_newton(double x) {
 // (x, y, z, w): R = (w^2 - v.v) I + 2 v v^T + 2 w [v]x, one formula for every
 // entry, so that the lanes of a warp evaluate different entries without
 // diverging.
-__device__ __forceinline__ double rot_entry(const double* q, int r, int c) {
+__device__ __forceinline__ double rot_entry4(double qx, double qy, double qz, double qw, int r, int c) {
   const bool diag = r == c;
   const int k = diag ? 0 : 3 - r - c;                     // the third axis
   const double sgn = (c == (r + 1) % 3) ? -1.0 : 1.0;     // [v]x (r, c) = sgn v_k
-  const double w = q[3], vr = q[r], vc = q[c];
-  const double base = diag ? fma(w, w, -(q[0] * q[0] + q[1] * q[1] + q[2] * q[2])) : 0.0;
-  const double cross = diag ? 0.0 : sgn * q[k];
-  return fma(2.0 * vr, vc, fma(2.0 * w, cross, base));
+  const double vr = r == 0 ? qx : r == 1 ? qy : qz;
+  const double vc = c == 0 ? qx : c == 1 ? qy : qz;
+  const double vk = k == 0 ? qx : k == 1 ? qy : qz;
+  const double base = diag ? fma(qw, qw, -(qx * qx + qy * qy + qz * qz)) : 0.0;
+  const double cross = diag ? 0.0 : sgn * vk;
+  return fma(2.0 * vr, vc, fma(2.0 * qw, cross, base));
+}
+__device__ __forceinline__ double rot_entry(const double* q, int r, int c) {
+  return rot_entry4(q[0], q[1], q[2], q[3], r, c);
 }
 
 // ---------------------------------------------------------------- host errors

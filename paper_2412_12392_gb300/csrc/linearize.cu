@@ -1287,22 +1287,26 @@ __device__ bool track_mixed_solve(const double* __restrict__ H7, const double* _
     return z;
   };
   const double b = row ? -g7[i] : 0.0;
-  double x = 0.0, r = b, zprev = 0.0;
+  double x = 0.0, r = b;
+  float zprev = 0.0f;
   for (int it = 0; it < kTrackRefine; ++it) {
     const float z = solve((float)(sc * r));  // every lane takes part in the shuffles
     const double dx = row ? sc * (double)z : 0.0;
     x += dx;
-    double zm = fabs(dx), xm = fabs(x);
+    // the stopping test needs magnitudes only: FP32 maxima (FP64 instructions
+    // occupy the SM's FP64 pipe for about 16 cycles each, whatever the lanes)
+    float zm = fabsf((float)dx), xm = fabsf((float)x);
+    // (fmaxf would pass over a NaN: every lane's entry is tested)
+    if (__any_sync(kAll, !(zm < INFINITY && xm < INFINITY))) return false;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-      zm = fmax(zm, __shfl_xor_sync(kAll, zm, off));
-      xm = fmax(xm, __shfl_xor_sync(kAll, xm, off));
+      zm = fmaxf(zm, __shfl_xor_sync(kAll, zm, off));
+      xm = fmaxf(xm, __shfl_xor_sync(kAll, xm, off));
     }
-    if (!(zm < INFINITY && xm < INFINITY)) return false;
-    if (zm == 0.0) break;
+    if (zm == 0.0f) break;
     if (it > 0) {  // contraction rho = zm / zprev (zprev > 0 here)
-      if (zm * zm <= 1e-9 * xm * zprev) break;
-      if (it > 1 && zm > 0.5 * zprev) return false;  // stalled
+      if (zm * zm <= 1e-9f * xm * zprev) break;
+      if (it > 1 && zm > 0.5f * zprev) return false;  // stalled
     }
     if (it == kTrackRefine - 1) return false;
     zprev = zm;
@@ -1335,7 +1339,7 @@ __global__ void __launch_bounds__(kLinThreads) track_kernel(PlanView pv, LinCons
   __shared__ double S[kNumAcc], Hr[49], A[49], C[49], H7[49], g7[7];
   __shared__ double Sg[kGroups][kNumAcc];
   __shared__ double sR[18], s_inv, s_tp[3];  // R_i, R_j (row-major), 1 / s_i, t of T_i^-1
-  __shared__ double s_tau[7], s_part[10], s_mx;
+  __shared__ double s_tau[7], s_part[10], s_mx, s_Tk[8];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, tile = blockIdx.x;
   const DevTile tl = pv.tiles[tile];
   const DevEdge ed = pv.edges[tl.edge];
@@ -1390,6 +1394,9 @@ __global__ void __launch_bounds__(kLinThreads) track_kernel(PlanView pv, LinCons
   __syncthreads();
   if (!s_last) return;
   __threadfence();
+  const int gauge = pv.graphs[g].gauge;
+  const int k_free = ed.i == gauge ? ed.j : ed.i;
+  const double sgn = ed.i == gauge ? 1.0 : -1.0;  // g_j = Ad^T g_rel, g_i = -Ad^T g_rel
   if (warp < kGroups) {
     // seven warps take every seventh tile (loads of several tiles in flight),
     // then the groups' FP64 sums are added in a fixed order
@@ -1405,6 +1412,7 @@ __global__ void __launch_bounds__(kLinThreads) track_kernel(PlanView pv, LinCons
     // [[s' R', [t']x R', -t'], [0, R', 0], [0, 0, 1]] with R' = R_i^T,
     // s' = 1 / s_i, t' = -s' R_i^T t_i (R_i and s' from the start of the block)
     if (lane < 3) s_tp[lane] = -s_inv * (sR[lane] * Ti[0] + sR[3 + lane] * Ti[1] + sR[6 + lane] * Ti[2]);
+    if (lane >= 24) s_Tk[lane - 24] = __ldcg(T_wc + 8 * k_free + lane - 24);  // the pose to retract
     __syncwarp();
     for (int e = lane; e < 49; e += 32) {
       const int r = e / 7, c = e % 7;
@@ -1445,9 +1453,6 @@ __global__ void __launch_bounds__(kLinThreads) track_kernel(PlanView pv, LinCons
     C[tid] = v;
   }
   __syncthreads();
-  const int gauge = pv.graphs[g].gauge;
-  const int k_free = ed.i == gauge ? ed.j : ed.i;
-  const double sgn = ed.i == gauge ? 1.0 : -1.0;  // g_j = Ad^T g_rel, g_i = -Ad^T g_rel
   if (tid < 49) {
     const int r = tid / 7, c = tid % 7;
     double v = 0.0;
@@ -1556,40 +1561,36 @@ __global__ void __launch_bounds__(kLinThreads) track_kernel(PlanView pv, LinCons
         b = is * ith;
         c = (a - ic) * (ith * ith);
       }
-      const int r = lane, n = (r + 1) % 3, o = (r + 2) % 3;
-      const double rv[3] = {s_tau[0], s_tau[1], s_tau[2]};
-      const double ph[3] = {px, py, pz};
-      // (phi x rho)_m and (phi x (phi x rho))_r
-      auto cr = [&](int m) {
-        const int m1 = (m + 1) % 3, m2 = (m + 2) % 3;
-        return ph[m1] * rv[m2] - ph[m2] * rv[m1];
-      };
-      const double c_r = cr(r), c_n = cr(n), c_o = cr(o);
-      const double d_r = ph[n] * c_o - ph[o] * c_n;
-      const double tE = a * rv[r] + b * c_r + c * d_r;
-      const double qE[4] = {hq * px * iqn, hq * py * iqn, hq * pz * iqn, q3 * iqn};
-      const double v = rot_entry(qE, r, 0) * Tk[0] + rot_entry(qE, r, 1) * Tk[1] + rot_entry(qE, r, 2) * Tk[2];
-      const double tn = s_part[2] * v + tE;
-      __syncwarp(0x7u);  // every lane has read t_k
-      Tk[r] = tn;
+      const int r = lane;
+      const double r0 = s_tau[0], r1 = s_tau[1], r2 = s_tau[2];
+      // phi x rho and phi x (phi x rho)
+      const double c0 = py * r2 - pz * r1, c1 = pz * r0 - px * r2, c2 = px * r1 - py * r0;
+      const double d0 = py * c2 - pz * c1, d1 = pz * c0 - px * c2, d2 = px * c1 - py * c0;
+      const double rr = r == 0 ? r0 : r == 1 ? r1 : r2;
+      const double cr = r == 0 ? c0 : r == 1 ? c1 : c2;
+      const double dr = r == 0 ? d0 : r == 1 ? d1 : d2;
+      const double tE = a * rr + b * cr + c * dr;
+      const double qx = hq * px * iqn, qy = hq * py * iqn, qz = hq * pz * iqn, qw = q3 * iqn;
+      const double v = rot_entry4(qx, qy, qz, qw, r, 0) * s_Tk[0] + rot_entry4(qx, qy, qz, qw, r, 1) * s_Tk[1] +
+                       rot_entry4(qx, qy, qz, qw, r, 2) * s_Tk[2];
+      Tk[r] = s_part[2] * v + tE;
     }
     if (warp == 1 && lane < 4) {
       const double iqn = rsqrt_newton(hq * hq * th2 + q3 * q3);
-      const double qE[4] = {hq * px * iqn, hq * py * iqn, hq * pz * iqn, q3 * iqn};
-      const double a3 = qE[3], b3 = Tk[6];
+      const double ax = hq * px * iqn, ay = hq * py * iqn, az = hq * pz * iqn, aw = q3 * iqn;
+      const double bx = s_Tk[3], by = s_Tk[4], bz = s_Tk[5], bw = s_Tk[6];
+      // (q_E (x) q_k)_lane
       double v;
-      if (lane == 3) {
-        v = a3 * b3 - (qE[0] * Tk[3] + qE[1] * Tk[4] + qE[2] * Tk[5]);
-      } else {
-        const int n = (lane + 1) % 3, o = (lane + 2) % 3;
-        v = a3 * Tk[3 + lane] + b3 * qE[lane] + (qE[n] * Tk[3 + o] - qE[o] * Tk[3 + n]);
-      }
+      if (lane == 3) v = aw * bw - (ax * bx + ay * by + az * bz);
+      else if (lane == 0) v = aw * bx + bw * ax + (ay * bz - az * by);
+      else if (lane == 1) v = aw * by + bw * ay + (az * bx - ax * bz);
+      else v = aw * bz + bw * az + (ax * by - ay * bx);
       double n2 = v * v;
       n2 += __shfl_xor_sync(0xfu, n2, 1);
-      n2 += __shfl_xor_sync(0xfu, n2, 2);  // also: every lane has read q_k
+      n2 += __shfl_xor_sync(0xfu, n2, 2);
       Tk[3 + lane] = v * rsqrt_newton(n2);
     }
-    if (warp == 2 && lane == 0) Tk[7] = s_part[2] * Tk[7];
+    if (warp == 2 && lane == 0) Tk[7] = s_part[2] * s_Tk[7];
   }
   if (tid == 0) {
     int status = status0;

@@ -387,19 +387,19 @@ static void build_graph(mslam_plan* P, int g, const std::vector<int>& kfs) {
   P->solve_ws_doubles += need;
   P->max_graph_doubles = std::max(P->max_graph_doubles, need);
   // inputs of the mixed-precision solve, written by its assembly kernel:
-  // the scaled FP32 factor (7 x 8 floats per block), S and -g
+  // the scaled FP32 factor (7 x kLfRow floats per block), S and -g
   P->solve_ws_doubles = (P->solve_ws_doubles + 3) & ~int64_t(3);  // 32-byte aligned for vector loads
   dg.ws_mixed = P->solve_ws_doubles;
-  P->solve_ws_doubles += (int64_t)nb_total * 28 + 14 * (int64_t)m;
+  P->solve_ws_doubles += (int64_t)nb_total * (7 * kLfRow / 2) + 14 * (int64_t)m;
   // its shared memory: S, x, -g (FP64), the padded FP32 factor, y,
   // pivots and the inverses of the diagonal factor blocks (7 x 8 floats per
   // block column), and the graph's tables except the update triples
   const int64_t table_ints = (int64_t)(dg.off_trip - dg.off_pose) + (int64_t)(dg.int_end - dg.off_lev);
   P->max_mixed_bytes = std::max(P->max_mixed_bytes,
-                                (int64_t)(64 * 7 * (int64_t)m + 224 * (int64_t)nb_total + 4 * table_ints + 16));
+                                (int64_t)(64 * 7 * (int64_t)m + 4 * 7 * kLfRow * (int64_t)nb_total + 4 * table_ints + 16));
   P->max_mixed_bytes_nofactor = std::max(P->max_mixed_bytes_nofactor,
                                          (int64_t)(64 * 7 * (int64_t)m + 4 * table_ints + 16));
-  P->max_mixed_elems = std::max(P->max_mixed_elems, (int64_t)nb_total * 56);
+  P->max_mixed_elems = std::max(P->max_mixed_elems, (int64_t)nb_total * 7 * kLfRow);
   P->max_m = std::max(P->max_m, (int32_t)m);
   P->n_blocks_total += nb_total;
   P->graphs.push_back(dg);

@@ -582,7 +582,11 @@ __global__ void __launch_bounds__(kSolveThreads) solve_cluster_kernel(PlanView p
 // which applies the exact not-positive-definite rule.
 constexpr int kMixThreads = 512;
 constexpr int kMixMaxIters = 10;
-constexpr int kLfBlock = 56;  // FP32 factor block: 7 rows of 8 floats (the 8th is 0), 32-byte rows
+// FP32 factor block: 7 rows of kLfRow floats (7 entries, then zeros), 48-byte
+// rows: the seven rows of a block start in seven disjoint groups of four
+// shared-memory banks, so a warp's 16-byte loads of different rows of one
+// block take one wavefront
+constexpr int kLfBlock = 7 * kLfRow;
 
 // One element of an assembled block, summed in FP64 over its edge
 // contributions in edge order (as in the FP64 kernel).
@@ -602,7 +606,7 @@ __device__ __forceinline__ double asm_sum(const float* __restrict__ H14, const i
 
 // Inputs of the mixed-precision solve, spread over many CTAs (the FP64 rate
 // of a single SM would make this the solve's longest phase), one thread per
-// element of the padded 7 x 8 blocks: every block element in FP64 (kept for
+// element of the padded 7 x kLfRow blocks: every block element in FP64 (kept for
 // the residuals) and the scaled FP32 factor input S H S (unit diagonal),
 // with S = D^-1/2 from the assembled diagonal (each thread forms the two
 // entries of S it needs); the padding threads of the diagonal blocks write
@@ -628,13 +632,13 @@ __global__ void __launch_bounds__(64) solve_assemble_kernel(PlanView pv, const f
   const int32_t* asm_ptr = I + G.off_asm;
   const int32_t* asment = I + G.off_asment;
   float* Lf = reinterpret_cast<float*>(ws + G.ws_mixed);
-  const int b = t / kLfBlock, e = t % kLfBlock, r = e / 8, c = e % 8;
-  if (c == 7) {
+  const int b = t / kLfBlock, e = t % kLfBlock, r = e / kLfRow, c = e % kLfRow;
+  if (c >= 7) {
     Lf[t] = 0.0f;
-    if (b < G.m) {
+    if (c == 7 && b < G.m) {
       // diagonal block b = unknown block b: S and -g of unknown 7 b + r
       const int n7 = 7 * G.m, k = 7 * b + r;
-      double* scl = ws + G.ws_mixed + (size_t)nb * 28;
+      double* scl = ws + G.ws_mixed + (size_t)nb * (kLfBlock / 2);
       scl[k] = jacobi_scale(H14, asm_ptr, asment, b, r);
       const int32_t* gasm_ptr = I + G.off_gasm;
       const int32_t* gasment = I + G.off_gasment;
@@ -701,7 +705,7 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
   // shared memory: the padded FP32 factor, FP64 vectors, FP32 vectors, then
   // the graph's tables (all but the update triples), so that every dependent
   // lookup of the level schedule is a shared-memory access
-  // scaled factor, FP32, 7 x 8 per block (16-byte aligned rows)
+  // scaled factor, FP32, 7 x kLfRow per block (16-byte aligned rows)
   float* Lf = kGlobalL ? reinterpret_cast<float*>(ws + G.ws_mixed) : reinterpret_cast<float*>(smem);
   double* scl = kGlobalL ? smem : reinterpret_cast<double*>(Lf + (size_t)nb * kLfBlock);  // S = D^-1/2
   double* xv = scl + n7;                        // solution
@@ -719,7 +723,7 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
       float4* dst = reinterpret_cast<float4*>(Lf);
       for (int t = tid; t < nb * (kLfBlock / 4); t += nth) dst[t] = src[t];
     }
-    const double* sg = ws + G.ws_mixed + (size_t)nb * 28;
+    const double* sg = ws + G.ws_mixed + (size_t)nb * (kLfBlock / 2);
     for (int t = tid; t < n7; t += nth) {
       scl[t] = sg[t];
       bv[t] = bwd == 2 ? sc.rhs[7 * __ldg(pv.ints + G.off_pose + t / 7) + t % 7] : sg[n7 + t];
@@ -768,13 +772,15 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
       float s0 = 0.f, s1 = 0.f;
       int k = tptr[t];
       for (; k + 1 < k1; k += 2) {
-        s0 += dot8(Lf + kLfBlock * (size_t)pairs[2 * k] + 8 * r, Lf + kLfBlock * (size_t)pairs[2 * k + 1] + 8 * c);
-        s1 += dot8(Lf + kLfBlock * (size_t)pairs[2 * k + 2] + 8 * r,
-                   Lf + kLfBlock * (size_t)pairs[2 * k + 3] + 8 * c);
+        s0 += dot8(Lf + kLfBlock * (size_t)pairs[2 * k] + kLfRow * r,
+                   Lf + kLfBlock * (size_t)pairs[2 * k + 1] + kLfRow * c);
+        s1 += dot8(Lf + kLfBlock * (size_t)pairs[2 * k + 2] + kLfRow * r,
+                   Lf + kLfBlock * (size_t)pairs[2 * k + 3] + kLfRow * c);
       }
       if (k < k1)
-        s0 += dot8(Lf + kLfBlock * (size_t)pairs[2 * k] + 8 * r, Lf + kLfBlock * (size_t)pairs[2 * k + 1] + 8 * c);
-      Lf[kLfBlock * (size_t)t + 8 * r + c] -= s0 + s1;
+        s0 += dot8(Lf + kLfBlock * (size_t)pairs[2 * k] + kLfRow * r,
+                   Lf + kLfBlock * (size_t)pairs[2 * k + 1] + kLfRow * c);
+      Lf[kLfBlock * (size_t)t + kLfRow * r + c] -= s0 + s1;
     }
     if (g1 > g0) __syncthreads();
     for (int qi = q0 + warp; qi < q1; qi += nwarps) {
@@ -784,7 +790,7 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
       const int li = mine ? lane : 0;
       float row[7];
 #pragma unroll
-      for (int k = 0; k < 7; ++k) row[k] = D[8 * li + k];
+      for (int k = 0; k < 7; ++k) row[k] = D[kLfRow * li + k];
       bool bad = false;
 #pragma unroll
       for (int j = 0; j < 7; ++j) {
@@ -804,7 +810,7 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
       if (mine) {
 #pragma unroll
         for (int k = 0; k < 7; ++k)
-          if (k <= lane) D[8 * lane + k] = row[k];
+          if (k <= lane) D[kLfRow * lane + k] = row[k];
       }
       if (bad && lane == 0) s_fail = 1;
       __syncwarp();
@@ -812,13 +818,13 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
       // of a block below the diagonal per lane (no barrier in between)
       const float* iv = ivf + 7 * p;
       for (int ent = col_ptr[p] * 7 + lane; ent < col_ptr[p + 1] * 7; ent += 32) {
-        float* prow = Lf + kLfBlock * (size_t)colent[2 * (ent / 7) + 1] + 8 * (ent % 7);
+        float* prow = Lf + kLfBlock * (size_t)colent[2 * (ent / 7) + 1] + kLfRow * (ent % 7);
         float x[7];
 #pragma unroll
         for (int k = 0; k < 7; ++k) {
           float v = prow[k];
 #pragma unroll
-          for (int l2 = 0; l2 < k; ++l2) v = fmaf(-x[l2], D[8 * k + l2], v);
+          for (int l2 = 0; l2 < k; ++l2) v = fmaf(-x[l2], D[kLfRow * k + l2], v);
           x[k] = v * iv[k];
         }
 #pragma unroll
@@ -837,7 +843,7 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
     // keep the factor for mode 2: the shared-memory factor back to the
     // workspace (where the assembly wrote its input) and the reciprocal
     // pivots in the -g slot (read above, no longer needed)
-    double* sgw = ws + G.ws_mixed + (size_t)nb * 28;
+    double* sgw = ws + G.ws_mixed + (size_t)nb * (kLfBlock / 2);
     if (!kGlobalL) {
       float4* dst = reinterpret_cast<float4*>(ws + G.ws_mixed);
       const float4* src = reinterpret_cast<const float4*>(Lf);
@@ -858,7 +864,7 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
     for (int j = 0; j < 7; ++j) {
       float v = (j == k) ? 1.0f : 0.0f;
 #pragma unroll
-      for (int i = 0; i < j; ++i) v = (i >= k) ? fmaf(-D[8 * j + i], x[i], v) : v;
+      for (int i = 0; i < j; ++i) v = (i >= k) ? fmaf(-D[kLfRow * j + i], x[i], v) : v;
       x[j] = (j >= k) ? v * ivf[7 * p + j] : 0.0f;
     }
 #pragma unroll
@@ -881,7 +887,7 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
         if (lane < 28) {
           float ps[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
           for (int k = rsptr[p] + grp; k < rsptr[p + 1]; k += 4) {
-            const float* Lpc = Lf + kLfBlock * (size_t)rs[2 * k + 1] + 8 * ga;
+            const float* Lpc = Lf + kLfBlock * (size_t)rs[2 * k + 1] + kLfRow * ga;
             const float* yc = yv + 7 * rs[2 * k];
 #pragma unroll
             for (int kk = 0; kk < 7; ++kk) ps[kk] = fmaf(Lpc[kk], yc[kk], ps[kk]);
@@ -913,7 +919,7 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
             const float* Lr = Lf + kLfBlock * (size_t)colent[2 * ent + 1];
             const float* xr = yv + 7 * colent[2 * ent];
 #pragma unroll
-            for (int k = 0; k < 7; ++k) ps[k] = fmaf(Lr[8 * k + ga], xr[k], ps[k]);
+            for (int k = 0; k < 7; ++k) ps[k] = fmaf(Lr[kLfRow * k + ga], xr[k], ps[k]);
           }
           part = ((ps[0] + ps[1]) + (ps[2] + ps[3])) + ((ps[4] + ps[5]) + ps[6]);
         }

@@ -153,12 +153,12 @@ typedef struct {
   int32_t match_block_w;
   int32_t lin_form;  /* packed linearisation of the FP16 ray family: 0 = records streamed through
                         shared memory by bulk asynchronous copies, one pipeline per block, and
-                        evaluated two at a time with paired FP32 instructions (default), 1 =
-                        per-thread register pipeline, 2 = the streamed form with one pipeline per
-                        warp (a warp takes whole tiles; suits tiles of 1024-4096 pixels), 3 = the
-                        register pipeline with each thread's next batch of records prefetched by
-                        asynchronous copies into a 32 KB shared-memory ring per block (the same sums
-                        in the same order as form 1).  FP32 storage and the other residual families
+                        evaluated two at a time with paired FP32 instructions, 1 = per-thread
+                        register pipeline, 2 = the streamed form with one pipeline per warp (a warp
+                        takes whole tiles; suits tiles of 1024-4096 pixels), 3 = the register
+                        pipeline with each thread's next batch of records prefetched by asynchronous
+                        copies into a 16 KB shared-memory buffer per block (the same sums in the same
+                        order as form 1; default).  FP32 storage and the other residual families
                         always use the register pipeline. */
   int32_t solve_form;  /* 0 = FP32 factorisation of the diagonally scaled system with FP64 iterative
                           refinement to the FP64 solution (default; graphs it declines go to the FP64

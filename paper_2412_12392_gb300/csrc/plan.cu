@@ -443,7 +443,7 @@ void mslam_default_plan_opts(mslam_plan_opts* o) {
   o->lin_tile = kLinTile;
   o->lin_blocks_per_sm = 0;
   o->match_block_w = kMatchBX;
-  o->lin_form = 0;
+  o->lin_form = 3;
   o->solve_form = 0;
   o->wait_limit = 0;
   o->match_form = 0;

@@ -153,7 +153,7 @@ def test_plan_opts_struct_layout(L):
     L.mslam_default_plan_opts(C.byref(o))
     assert C.sizeof(o) == 32 and _lib.PlanOpts.match_form.offset == 20 and _lib.PlanOpts.wait_limit.offset == 28
     assert o.match_ppt == 1
-    assert o.wait_limit == 0 and o.lin_form == 0 and o.solve_form == 0 and o.match_form == 0
+    assert o.wait_limit == 0 and o.lin_form == 3 and o.solve_form == 0 and o.match_form == 0
     # every wait limit is accepted: < 0 gives up at once (for the timeout tests), 0 is the default
     for wl in (-1, 0, 1, 1 << 24):
         p = plan([[16, 16]] * 2, [[0, 1]], None) if wl == 0 else None

@@ -370,10 +370,11 @@ class Arm:
 def pick_pipelined_shapes(arm, world, steps: int = 5, warmup: int = 3):
     """The autotuner ranks the linearisation shapes one stage at a time.  With
     two batches in flight the linearisation also shares the SMs with the next
-    batch's matching, and a streamed form's large shared-memory ring keeps
-    matching blocks off an SM while it runs.  Time the autotuner's choice and
-    its best register-pipeline shape as pipelined steps and keep the faster
-    (the same work either way; only the launch shapes differ)."""
+    batch's matching, and the shared memory a streamed or prefetching form
+    holds shrinks the L1 the matching kernel reads its windows from.  Time
+    the autotuner's choice and its best plain register-pipeline shape as
+    pipelined steps and keep the faster (the same work either way; only the
+    launch shapes differ)."""
     rep = arm.tuning
     need = rep is not None and rep["opts"].get("lin_form") != 1
     if world > 1:

@@ -38,9 +38,12 @@ def test_workload_names():
 
 
 def test_pipelined_shape_check_needs_a_streamed_choice():
-    """The pipelined shape check runs only when the autotuner chose a streamed
-    linearisation form; it compares against the best register-pipeline shape
-    by the autotuner's own score (iterations x linearise + pack)."""
+    """The pipelined shape check runs only when the autotuner chose a
+    linearisation form other than the plain register pipeline (a streamed
+    form, or the prefetching one: both hold shared memory while the next
+    batch's matching runs beside them); it compares against the best plain
+    register-pipeline shape by the autotuner's own score (iterations x
+    linearise + pack)."""
     bench = _bench()
     assert bench.pick_pipelined_shapes(types.SimpleNamespace(tuning=None), 1) is None
     regs = types.SimpleNamespace(tuning={"opts": {"lin_form": 1}})

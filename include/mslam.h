@@ -414,7 +414,11 @@ int32_t mslam_gn_solve_launches(const mslam_plan* plan);
  * E_g is Eq. backend_ray at the poses T_wc (matches and the q_min mask held
  * fixed, Huber weights differentiated) and tau = -H^-1 g is one
  * Gauss-Newton step from T_wc (Eq. gauss_newton).  The per-pixel residuals
- * and Jacobians are recomputed, not stored.
+ * and Jacobians are recomputed, not stored.  The step term's two solves
+ * (tau and b = H^-1 dL_dtau) follow the plan's solve_form: the FP32 factor
+ * of the Jacobi-scaled system refined with FP64 residuals (kept in the
+ * workspace between the two), the FP64 factorisation for the graphs that
+ * path declines and with solve_form 1.
  * Arguments: as mslam_gn_linearize, plus H_blocks and g_blocks of the
  * linearisation at T_wc (needed when dL_dtau != NULL), dL_dtau [N, 7] FP64
  * device or NULL, dL_dcost host scalar; outputs dL_dX [Pk, 3] FP32 and dL_dq
@@ -442,7 +446,8 @@ mslam_status mslam_gn_backward(const mslam_params* p, const mslam_plan* plan, ms
  * Arguments: as mslam_gn_backward, plus dL_dTnew [N, 8] FP64 (device, the
  * gradient on the updated poses) or NULL, and the output dL_dT [N, 8] FP64
  * (device, required).  H_blocks, g_blocks (the linearisation at T_wc) and
- * dev_status are required.  tau is recomputed from H and g (FP64).  The
+ * dev_status are required.  tau is recomputed from H and g (as in
+ * mslam_gn_backward, to the FP64 solution).  The
  * gradient of the fixed (first) keyframe's pose is returned too: moving it
  * moves every other pose's step.  Errors: MSLAM_ERR_ARG, MSLAM_ERR_CUDA; a
  * singular system sets dev_status[g] = MSLAM_ERR_NOT_PD (the gradients of

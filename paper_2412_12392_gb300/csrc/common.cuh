@@ -26,6 +26,7 @@ constexpr int kMatchThreads = MSLAM_MATCH_THREADS;  // threads of a match block 
 constexpr int kMatchBX = 32;
 constexpr int kSolveThreads = 512;
 constexpr int kLfRow = 12;          // floats per row of a block of the mixed-precision solve's FP32 factor
+                                    // in shared memory (8 when the factor stays in the workspace)
 
 // One directed edge as seen by the kernels.
 struct DevEdge {
@@ -78,7 +79,7 @@ struct DevGraph {
   int32_t pad1;
   int64_t ws_off;     // offset (doubles) of this graph's numeric workspace
   int64_t ws_mixed;   // offset (doubles) of the mixed-precision solve's inputs: scaled FP32 factor
-                      // [n_blocks][7][kLfRow] floats, then S (7 m) and -g (7 m) in FP64
+                      // [n_blocks][7][kLfRow or 8] floats in n_blocks * 7 * kLfRow, then S (7 m) and -g (7 m) in FP64
 };
 
 // Device view of a plan (pointers into the uploaded table blob).

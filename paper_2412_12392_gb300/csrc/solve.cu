@@ -582,10 +582,12 @@ __global__ void __launch_bounds__(kSolveThreads) solve_cluster_kernel(PlanView p
 // which applies the exact not-positive-definite rule.
 constexpr int kMixThreads = 512;
 constexpr int kMixMaxIters = 10;
-// FP32 factor block: 7 rows of kLfRow floats (7 entries, then zeros), 48-byte
-// rows: the seven rows of a block start in seven disjoint groups of four
-// shared-memory banks, so a warp's 16-byte loads of different rows of one
-// block take one wavefront
+// FP32 factor block in shared memory: 7 rows of kLfRow floats (7 entries, then
+// zeros), 48-byte rows: the seven rows of a block start in seven disjoint
+// groups of four shared-memory banks, so a warp's 16-byte loads of different
+// rows of one block take one wavefront.  A factor too large for shared memory
+// stays in the workspace with 8-float rows (fewer bytes through L1 and L2);
+// the workspace reserves kLfBlock floats per block for either form.
 constexpr int kLfBlock = 7 * kLfRow;
 
 // One element of an assembled block, summed in FP64 over its edge
@@ -621,18 +623,19 @@ __device__ __forceinline__ double jacobi_scale(const float* __restrict__ H14, co
 __global__ void __launch_bounds__(64) solve_assemble_kernel(PlanView pv, const float* __restrict__ H14,
                                                             const float* __restrict__ g14,
                                                             const int32_t* __restrict__ dev_status,
-                                                            double* __restrict__ ws, int max_status) {
+                                                            double* __restrict__ ws, int max_status, int row) {
   const int g = blockIdx.y;
   const DevGraph G = pv.graphs[g];
   if (dev_status[g] > max_status || G.m == 0) return;  // the solve kernels skip these graphs too
   const int nb = G.n_blocks;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nb * kLfBlock) return;
+  const int blk = 7 * row;  // the mixed kernel's row stride for this plan
+  if (t >= nb * blk) return;
   const int32_t* I = pv.ints;
   const int32_t* asm_ptr = I + G.off_asm;
   const int32_t* asment = I + G.off_asment;
   float* Lf = reinterpret_cast<float*>(ws + G.ws_mixed);
-  const int b = t / kLfBlock, e = t % kLfBlock, r = e / kLfRow, c = e % kLfRow;
+  const int b = t / blk, e = t % blk, r = e / row, c = e % row;
   if (c >= 7) {
     Lf[t] = 0.0f;
     if (c == 7 && b < G.m) {
@@ -687,6 +690,10 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
                                                                   int32_t* __restrict__ dev_status,
                                                                   double* __restrict__ ws,
                                                                   int32_t* __restrict__ handled) {
+  // the factor's row stride: 12 floats in shared memory (rows of a block in
+  // disjoint bank groups), 8 in the workspace (fewer bytes through L2)
+  constexpr int kRow = kGlobalL ? 8 : kLfRow;
+  constexpr int kBlk = 7 * kRow;
   extern __shared__ double smem[];
   const int g = blockIdx.x;
   const DevGraph G = pv.graphs[g];
@@ -705,9 +712,9 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
   // shared memory: the padded FP32 factor, FP64 vectors, FP32 vectors, then
   // the graph's tables (all but the update triples), so that every dependent
   // lookup of the level schedule is a shared-memory access
-  // scaled factor, FP32, 7 x kLfRow per block (16-byte aligned rows)
+  // scaled factor, FP32, 7 x kRow per block (16-byte aligned rows)
   float* Lf = kGlobalL ? reinterpret_cast<float*>(ws + G.ws_mixed) : reinterpret_cast<float*>(smem);
-  double* scl = kGlobalL ? smem : reinterpret_cast<double*>(Lf + (size_t)nb * kLfBlock);  // S = D^-1/2
+  double* scl = kGlobalL ? smem : reinterpret_cast<double*>(Lf + (size_t)nb * kBlk);  // S = D^-1/2
   double* xv = scl + n7;                        // solution
   double* bv = xv + n7;                         // right-hand side -g
   float* yv = reinterpret_cast<float*>(bv + n7);  // work vector
@@ -721,7 +728,7 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
     if (!kGlobalL) {
       const float4* src = reinterpret_cast<const float4*>(ws + G.ws_mixed);
       float4* dst = reinterpret_cast<float4*>(Lf);
-      for (int t = tid; t < nb * (kLfBlock / 4); t += nth) dst[t] = src[t];
+      for (int t = tid; t < nb * (kBlk / 4); t += nth) dst[t] = src[t];
     }
     const double* sg = ws + G.ws_mixed + (size_t)nb * (kLfBlock / 2);
     for (int t = tid; t < n7; t += nth) {
@@ -772,25 +779,25 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
       float s0 = 0.f, s1 = 0.f;
       int k = tptr[t];
       for (; k + 1 < k1; k += 2) {
-        s0 += dot8(Lf + kLfBlock * (size_t)pairs[2 * k] + kLfRow * r,
-                   Lf + kLfBlock * (size_t)pairs[2 * k + 1] + kLfRow * c);
-        s1 += dot8(Lf + kLfBlock * (size_t)pairs[2 * k + 2] + kLfRow * r,
-                   Lf + kLfBlock * (size_t)pairs[2 * k + 3] + kLfRow * c);
+        s0 += dot8(Lf + kBlk * (size_t)pairs[2 * k] + kRow * r,
+                   Lf + kBlk * (size_t)pairs[2 * k + 1] + kRow * c);
+        s1 += dot8(Lf + kBlk * (size_t)pairs[2 * k + 2] + kRow * r,
+                   Lf + kBlk * (size_t)pairs[2 * k + 3] + kRow * c);
       }
       if (k < k1)
-        s0 += dot8(Lf + kLfBlock * (size_t)pairs[2 * k] + kLfRow * r,
-                   Lf + kLfBlock * (size_t)pairs[2 * k + 1] + kLfRow * c);
-      Lf[kLfBlock * (size_t)t + kLfRow * r + c] -= s0 + s1;
+        s0 += dot8(Lf + kBlk * (size_t)pairs[2 * k] + kRow * r,
+                   Lf + kBlk * (size_t)pairs[2 * k + 1] + kRow * c);
+      Lf[kBlk * (size_t)t + kRow * r + c] -= s0 + s1;
     }
     if (g1 > g0) __syncthreads();
     for (int qi = q0 + warp; qi < q1; qi += nwarps) {
       const int p = lev_cols[qi];
-      float* D = Lf + kLfBlock * (size_t)p;
+      float* D = Lf + kBlk * (size_t)p;
       const bool mine = lane < 7;
       const int li = mine ? lane : 0;
       float row[7];
 #pragma unroll
-      for (int k = 0; k < 7; ++k) row[k] = D[kLfRow * li + k];
+      for (int k = 0; k < 7; ++k) row[k] = D[kRow * li + k];
       bool bad = false;
 #pragma unroll
       for (int j = 0; j < 7; ++j) {
@@ -810,7 +817,7 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
       if (mine) {
 #pragma unroll
         for (int k = 0; k < 7; ++k)
-          if (k <= lane) D[kLfRow * lane + k] = row[k];
+          if (k <= lane) D[kRow * lane + k] = row[k];
       }
       if (bad && lane == 0) s_fail = 1;
       __syncwarp();
@@ -818,13 +825,13 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
       // of a block below the diagonal per lane (no barrier in between)
       const float* iv = ivf + 7 * p;
       for (int ent = col_ptr[p] * 7 + lane; ent < col_ptr[p + 1] * 7; ent += 32) {
-        float* prow = Lf + kLfBlock * (size_t)colent[2 * (ent / 7) + 1] + kLfRow * (ent % 7);
+        float* prow = Lf + kBlk * (size_t)colent[2 * (ent / 7) + 1] + kRow * (ent % 7);
         float x[7];
 #pragma unroll
         for (int k = 0; k < 7; ++k) {
           float v = prow[k];
 #pragma unroll
-          for (int l2 = 0; l2 < k; ++l2) v = fmaf(-x[l2], D[kLfRow * k + l2], v);
+          for (int l2 = 0; l2 < k; ++l2) v = fmaf(-x[l2], D[kRow * k + l2], v);
           x[k] = v * iv[k];
         }
 #pragma unroll
@@ -847,7 +854,7 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
     if (!kGlobalL) {
       float4* dst = reinterpret_cast<float4*>(ws + G.ws_mixed);
       const float4* src = reinterpret_cast<const float4*>(Lf);
-      for (int t = tid; t < nb * (kLfBlock / 4); t += nth) dst[t] = src[t];
+      for (int t = tid; t < nb * (kBlk / 4); t += nth) dst[t] = src[t];
     }
     for (int t = tid; t < n7; t += nth) reinterpret_cast<float*>(sgw + n7)[t] = ivf[t];
   }
@@ -858,13 +865,13 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
   // seven dependent shuffles
   for (int t = tid; t < n7; t += nth) {
     const int p = t / 7, k = t % 7;
-    const float* D = Lf + kLfBlock * (size_t)p;
+    const float* D = Lf + kBlk * (size_t)p;
     float x[7];
 #pragma unroll
     for (int j = 0; j < 7; ++j) {
       float v = (j == k) ? 1.0f : 0.0f;
 #pragma unroll
-      for (int i = 0; i < j; ++i) v = (i >= k) ? fmaf(-D[kLfRow * j + i], x[i], v) : v;
+      for (int i = 0; i < j; ++i) v = (i >= k) ? fmaf(-D[kRow * j + i], x[i], v) : v;
       x[j] = (j >= k) ? v * ivf[7 * p + j] : 0.0f;
     }
 #pragma unroll
@@ -887,7 +894,7 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
         if (lane < 28) {
           float ps[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
           for (int k = rsptr[p] + grp; k < rsptr[p + 1]; k += 4) {
-            const float* Lpc = Lf + kLfBlock * (size_t)rs[2 * k + 1] + kLfRow * ga;
+            const float* Lpc = Lf + kBlk * (size_t)rs[2 * k + 1] + kRow * ga;
             const float* yc = yv + 7 * rs[2 * k];
 #pragma unroll
             for (int kk = 0; kk < 7; ++kk) ps[kk] = fmaf(Lpc[kk], yc[kk], ps[kk]);
@@ -916,10 +923,10 @@ __global__ void __launch_bounds__(kMixThreads) solve_mixed_kernel(PlanView pv, S
         if (lane < 28) {
           float ps[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
           for (int ent = col_ptr[p] + grp; ent < col_ptr[p + 1]; ent += 4) {
-            const float* Lr = Lf + kLfBlock * (size_t)colent[2 * ent + 1];
+            const float* Lr = Lf + kBlk * (size_t)colent[2 * ent + 1];
             const float* xr = yv + 7 * colent[2 * ent];
 #pragma unroll
-            for (int k = 0; k < 7; ++k) ps[k] = fmaf(Lr[kLfRow * k + ga], xr[k], ps[k]);
+            for (int k = 0; k < 7; ++k) ps[k] = fmaf(Lr[kRow * k + ga], xr[k], ps[k]);
           }
           part = ((ps[0] + ps[1]) + (ps[2] + ps[3])) + ((ps[4] + ps[5]) + ps[6]);
         }
@@ -1188,7 +1195,7 @@ extern "C" mslam_status mslam_gn_solve(const mslam_params* p, const mslam_plan* 
     int32_t* handled = solve_flags(plan, ws);
     const int elems = (int)plan_max_mixed_elems(plan);
     solve_assemble_kernel<<<dim3(std::max(1, (elems + 63) / 64), pv.G), 64, 0, s>>>(pv, H_blocks, g_blocks,
-                                                                                     dev_status, ws, 0);
+                                                                                     dev_status, ws, 0, global_factor ? 8 : kLfRow);
     if (global_factor)
       solve_mixed_kernel<true><<<pv.G, kMixThreads, mixed, s>>>(pv, sc, T_wc, tau, dev_status, ws, handled);
     else
@@ -1231,7 +1238,7 @@ mslam_status mslam_bwd_solve_tau(const mslam_plan* plan, const float* H_blocks, 
     int32_t* handled = solve_flags(plan, ws);
     const int elems = (int)plan_max_mixed_elems(plan);
     solve_assemble_kernel<<<dim3(std::max(1, (elems + 63) / 64), pv.G), 64, 0, s>>>(pv, H_blocks, g_blocks,
-                                                                                     dev_status, ws, 1);
+                                                                                     dev_status, ws, 1, global_factor ? 8 : kLfRow);
     SolveConst m1 = sc;
     m1.factor_only = 0;
     m1.bwd_mode = 1;

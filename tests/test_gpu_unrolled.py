@@ -57,7 +57,7 @@ def gpu_grad(M, w, plan, P, X, q, T0, steps, Wt, a, c):
     for k in range(steps):
         L = L + (taus[k] * torch.from_numpy(a[k]).cuda()).sum()
     L.backward()
-    return float(L), Xg.grad.double().cpu().numpy(), qg.grad.double().cpu().numpy(), Tg.grad.cpu().numpy()
+    return float(L.detach()), Xg.grad.double().cpu().numpy(), qg.grad.double().cpu().numpy(), Tg.grad.cpu().numpy()
 
 
 def setup(w, dtype, seed):

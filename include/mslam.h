@@ -129,7 +129,8 @@ const char* mslam_version(void);
  *   graph_of_kf  host [N] int32 graph id in [0, G) or NULL (one graph).  The
  *                lowest-indexed keyframe of each graph is its fixed pose.
  *   out          receives the plan; destroy with mslam_plan_destroy.
- * Errors: MSLAM_ERR_ARG on any inconsistency (nothing is created). */
+ * Errors: MSLAM_ERR_ARG on any inconsistency, MSLAM_ERR_RANGE if host memory
+ * for the plan's tables cannot be allocated (nothing is created either way). */
 typedef struct mslam_plan mslam_plan;
 mslam_status mslam_plan_create(int32_t N, const int32_t* kf_hw, int32_t E, const int32_t* edges,
                                const int32_t* graph_of_kf, mslam_plan** out);
@@ -146,7 +147,8 @@ void mslam_plan_destroy(mslam_plan* plan);
  *                      128 or 256 (default 32, i.e. 32 x 8 threads)
  *   lin_form, solve_form  kernel forms, described at the fields
  * mslam_plan_create uses the defaults; mslam_plan_create_ex takes options
- * (NULL = defaults).  Errors: MSLAM_ERR_ARG for an option out of range. */
+ * (NULL = defaults).  Errors: MSLAM_ERR_ARG for an option out of range, and
+ * those of mslam_plan_create. */
 typedef struct {
   int32_t lin_tile;
   int32_t lin_blocks_per_sm;

@@ -6,7 +6,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <exception>
 #include <map>
+#include <memory>
 #include <set>
 #include <vector>
 
@@ -482,91 +484,95 @@ mslam_status mslam_plan_create_ex(int32_t N, const int32_t* kf_hw, int32_t E, co
     set_error("bad sizes or NULL host arrays (N=%d, E=%d)", N, E);
     return MSLAM_ERR_ARG;
   }
-  mslam_plan* P = new mslam_plan();
-  P->lin_tile = o.lin_tile;
-  P->lin_blocks_per_sm = o.lin_blocks_per_sm;
-  P->lin_form = o.lin_form;
-  P->solve_form = o.solve_form;
-  P->wait_limit = o.wait_limit;
-  P->match_form = o.match_form;
-  P->match_ppt = o.match_ppt;
-  P->match_bx = o.match_block_w;
-  P->match_by = kMatchThreads / o.match_block_w;
-  P->N = N;
-  P->E = E;
-  P->kf_hw.assign(kf_hw, kf_hw + 2 * N);
-  P->edges.assign(edges, edges + 2 * (size_t)E);
-  P->graph_of_kf.assign(N, 0);
-  if (graph_of_kf) P->graph_of_kf.assign(graph_of_kf, graph_of_kf + N);
-  int G = 0;
-  for (int k = 0; k < N; ++k) {
-    const int H = kf_hw[2 * k], W = kf_hw[2 * k + 1];
-    if (H < 2 || W < 2 || H > 8192 || W > 8192 || P->graph_of_kf[k] < 0 || P->graph_of_kf[k] >= N) {
-      set_error("keyframe %d: bad size %dx%d or graph id %d", k, H, W, P->graph_of_kf[k]);
-      delete P;
-      return MSLAM_ERR_ARG;
+  try {
+    // the plan's host tables: an allocation failure returns a status instead
+    // of unwinding through the C interface
+    std::unique_ptr<mslam_plan> P(new mslam_plan());
+    P->lin_tile = o.lin_tile;
+    P->lin_blocks_per_sm = o.lin_blocks_per_sm;
+    P->lin_form = o.lin_form;
+    P->solve_form = o.solve_form;
+    P->wait_limit = o.wait_limit;
+    P->match_form = o.match_form;
+    P->match_ppt = o.match_ppt;
+    P->match_bx = o.match_block_w;
+    P->match_by = kMatchThreads / o.match_block_w;
+    P->N = N;
+    P->E = E;
+    P->kf_hw.assign(kf_hw, kf_hw + 2 * N);
+    P->edges.assign(edges, edges + 2 * (size_t)E);
+    P->graph_of_kf.assign(N, 0);
+    if (graph_of_kf) P->graph_of_kf.assign(graph_of_kf, graph_of_kf + N);
+    int G = 0;
+    for (int k = 0; k < N; ++k) {
+      const int H = kf_hw[2 * k], W = kf_hw[2 * k + 1];
+      if (H < 2 || W < 2 || H > 8192 || W > 8192 || P->graph_of_kf[k] < 0 || P->graph_of_kf[k] >= N) {
+        set_error("keyframe %d: bad size %dx%d or graph id %d", k, H, W, P->graph_of_kf[k]);
+        return MSLAM_ERR_ARG;
+      }
+      G = std::max(G, P->graph_of_kf[k] + 1);
     }
-    G = std::max(G, P->graph_of_kf[k] + 1);
+    std::vector<std::vector<int>> kfs(G);
+    for (int k = 0; k < N; ++k) kfs[P->graph_of_kf[k]].push_back(k);
+    for (int g = 0; g < G; ++g)
+      if (kfs[g].empty()) {
+        set_error("graph id %d has no keyframe", g);
+        return MSLAM_ERR_ARG;
+      }
+    P->G = G;
+    P->kf_off.assign(N + 1, 0);
+    for (int k = 0; k < N; ++k) P->kf_off[k + 1] = P->kf_off[k] + (int64_t)kf_hw[2 * k] * kf_hw[2 * k + 1];
+    P->e_off.assign(E + 1, 0);
+    for (int e = 0; e < E; ++e) {
+      const int i = edges[2 * e], j = edges[2 * e + 1];
+      if (i < 0 || j < 0 || i >= N || j >= N || i == j || P->graph_of_kf[i] != P->graph_of_kf[j] ||
+          kf_hw[2 * i] != kf_hw[2 * j] || kf_hw[2 * i + 1] != kf_hw[2 * j + 1]) {
+        set_error("edge %d = (%d, %d): out of range, self edge, different graphs or sizes", e, i, j);
+        return MSLAM_ERR_ARG;
+      }
+      const int H = kf_hw[2 * j], W = kf_hw[2 * j + 1];
+      P->e_off[e + 1] = P->e_off[e] + (int64_t)H * W;
+      DevEdge d{};
+      d.i = i;
+      d.j = j;
+      d.H = H;
+      d.W = W;
+      d.off_e = P->e_off[e];
+      d.off_i = P->kf_off[i];
+      d.off_j = P->kf_off[j];
+      d.graph = P->graph_of_kf[i];
+      d.tile_begin = (int32_t)P->tiles.size();
+      for (int b = 0; b < H * W; b += P->lin_tile) {
+        DevTile t{};
+        t.edge = e;
+        t.begin = b;
+        t.end = std::min(H * W, b + P->lin_tile);
+        P->tiles.push_back(t);
+      }
+      d.tile_end = (int32_t)P->tiles.size();
+      d.mblock_begin = P->n_mblocks;
+      const int bh = P->match_by * P->match_ppt;  // rows of a match block
+      P->n_mblocks += ((W + P->match_bx - 1) / P->match_bx) * ((H + bh - 1) / bh);
+      P->dedges.push_back(d);
+    }
+    P->order.assign(N, -1);
+    for (int g = 0; g < G; ++g) build_graph(P.get(), g, kfs[g]);
+    size_t off = 0;
+    P->off_edges = off;
+    off = align256(off + sizeof(DevEdge) * P->dedges.size());
+    P->off_tiles = off;
+    off = align256(off + sizeof(DevTile) * P->tiles.size());
+    P->off_graphs = off;
+    off = align256(off + sizeof(DevGraph) * P->graphs.size());
+    P->off_ints = off;
+    off = align256(off + sizeof(int32_t) * P->ints.size());
+    P->blob_bytes = std::max<size_t>(off, 256);
+    *out = P.release();
+    return MSLAM_OK;
+  } catch (const std::exception& ex) {
+    set_error("plan_create: host tables: %s", ex.what());
+    return MSLAM_ERR_RANGE;
   }
-  std::vector<std::vector<int>> kfs(G);
-  for (int k = 0; k < N; ++k) kfs[P->graph_of_kf[k]].push_back(k);
-  for (int g = 0; g < G; ++g)
-    if (kfs[g].empty()) {
-      set_error("graph id %d has no keyframe", g);
-      delete P;
-      return MSLAM_ERR_ARG;
-    }
-  P->G = G;
-  P->kf_off.assign(N + 1, 0);
-  for (int k = 0; k < N; ++k) P->kf_off[k + 1] = P->kf_off[k] + (int64_t)kf_hw[2 * k] * kf_hw[2 * k + 1];
-  P->e_off.assign(E + 1, 0);
-  for (int e = 0; e < E; ++e) {
-    const int i = edges[2 * e], j = edges[2 * e + 1];
-    if (i < 0 || j < 0 || i >= N || j >= N || i == j || P->graph_of_kf[i] != P->graph_of_kf[j] ||
-        kf_hw[2 * i] != kf_hw[2 * j] || kf_hw[2 * i + 1] != kf_hw[2 * j + 1]) {
-      set_error("edge %d = (%d, %d): out of range, self edge, different graphs or sizes", e, i, j);
-      delete P;
-      return MSLAM_ERR_ARG;
-    }
-    const int H = kf_hw[2 * j], W = kf_hw[2 * j + 1];
-    P->e_off[e + 1] = P->e_off[e] + (int64_t)H * W;
-    DevEdge d{};
-    d.i = i;
-    d.j = j;
-    d.H = H;
-    d.W = W;
-    d.off_e = P->e_off[e];
-    d.off_i = P->kf_off[i];
-    d.off_j = P->kf_off[j];
-    d.graph = P->graph_of_kf[i];
-    d.tile_begin = (int32_t)P->tiles.size();
-    for (int b = 0; b < H * W; b += P->lin_tile) {
-      DevTile t{};
-      t.edge = e;
-      t.begin = b;
-      t.end = std::min(H * W, b + P->lin_tile);
-      P->tiles.push_back(t);
-    }
-    d.tile_end = (int32_t)P->tiles.size();
-    d.mblock_begin = P->n_mblocks;
-    const int bh = P->match_by * P->match_ppt;  // rows of a match block
-    P->n_mblocks += ((W + P->match_bx - 1) / P->match_bx) * ((H + bh - 1) / bh);
-    P->dedges.push_back(d);
-  }
-  P->order.assign(N, -1);
-  for (int g = 0; g < G; ++g) build_graph(P, g, kfs[g]);
-  size_t off = 0;
-  P->off_edges = off;
-  off = align256(off + sizeof(DevEdge) * P->dedges.size());
-  P->off_tiles = off;
-  off = align256(off + sizeof(DevTile) * P->tiles.size());
-  P->off_graphs = off;
-  off = align256(off + sizeof(DevGraph) * P->graphs.size());
-  P->off_ints = off;
-  off = align256(off + sizeof(int32_t) * P->ints.size());
-  P->blob_bytes = std::max<size_t>(off, 256);
-  *out = P;
-  return MSLAM_OK;
 }
 
 void mslam_plan_destroy(mslam_plan* plan) { delete plan; }

@@ -63,6 +63,15 @@ def _need(t: torch.Tensor, name: str, dtype=None, numel=None, device=None):
         raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
 
 
+def _workspace(plan: "Plan", op: int, workspace):
+    """The caller's workspace for op (a contiguous uint8 CUDA tensor; the
+    library checks its size) or a new one."""
+    if workspace is None:
+        return plan.workspace(op)
+    _need(workspace, "workspace", torch.uint8)
+    return workspace
+
+
 class Plan:
     """mslam_plan: the static structure of one or more keyframe graphs,
     uploaded to a torch-owned device buffer."""
@@ -182,8 +191,8 @@ def match(plan: Plan, params: Params, X_ref, X_qry, D_ref, D_qry, Q_ref, Q_qry, 
         q_out = torch.empty(P, dtype=dt, device=X_ref.device)
     _need(idx_out, "idx_out", torch.int32, P)
     _need(q_out, "q_out", dt, P)
-    if workspace is None:
-        workspace = plan.workspace(_lib.MSLAM_OP_MATCH)
+    if workspace is not False:
+        workspace = _workspace(plan, _lib.MSLAM_OP_MATCH, workspace)
     ws_ptr, ws_n = (None, 0) if workspace is False else (workspace.data_ptr(), workspace.numel())
     nv = nu = None
     if counts is not None:
@@ -205,7 +214,7 @@ def match_stats(plan: Plan, idx, workspace=None):
     dev = idx.device
     nv = torch.empty(plan.E, dtype=torch.int32, device=dev)
     nu = torch.empty(plan.E, dtype=torch.int32, device=dev)
-    ws = plan.workspace(_lib.MSLAM_OP_STATS) if workspace is None else workspace
+    ws = _workspace(plan, _lib.MSLAM_OP_STATS, workspace)
     check(lib().mslam_match_stats(plan.handle, idx.data_ptr(), nv.data_ptr(), nu.data_ptr(), ws.data_ptr(),
                                   ws.numel(), _stream(dev)), "mslam_match_stats")
     return nv, nu
@@ -234,11 +243,11 @@ def keyframe_needed(n_valid, n_unique, n_query, omega_k: float = OMEGA_K):
 def ray_image(X: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
     """mslam_ray_image (a1, Sec. 3.1): psi(X) = X / |X| for X [..., 3] (FP32 or
     FP16, CUDA), the zero ray for a zero or non-finite point."""
-    if X.shape[-1] != 3 or not X.is_contiguous() or not X.is_cuda:
-        raise ValueError("X must be a contiguous CUDA tensor of shape [..., 3]")
+    if X.shape[-1] != 3 or not X.is_contiguous() or not X.is_cuda or X.dtype not in DTYPES:
+        raise ValueError("X must be a contiguous FP32 or FP16 CUDA tensor of shape [..., 3]")
     R = torch.empty_like(X) if out is None else out
-    if R.shape != X.shape or R.dtype != X.dtype or not R.is_contiguous():
-        raise ValueError("out must match X in shape, dtype and layout")
+    if R.shape != X.shape or R.dtype != X.dtype or not R.is_contiguous() or R.device != X.device:
+        raise ValueError("out must match X in shape, dtype, layout and device")
     check(lib().mslam_ray_image(DTYPES[X.dtype], X.numel() // 3, X.data_ptr(), R.data_ptr(), _stream(X.device)),
           "mslam_ray_image")
     return R
@@ -247,8 +256,8 @@ def ray_image(X: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tens
 def calib_backproject(X: torch.Tensor, fx: float, fy: float, cx: float, cy: float) -> torch.Tensor:
     """mslam_calib_backproject (Sec. 3.6), in place on X [n, H, W, 3] (FP32 or
     FP16, CUDA); returns X."""
-    if X.dim() != 4 or X.shape[-1] != 3 or not X.is_contiguous() or not X.is_cuda:
-        raise ValueError("X must be a contiguous CUDA tensor of shape [n, H, W, 3]")
+    if X.dim() != 4 or X.shape[-1] != 3 or not X.is_contiguous() or not X.is_cuda or X.dtype not in DTYPES:
+        raise ValueError("X must be a contiguous FP32 or FP16 CUDA tensor of shape [n, H, W, 3]")
     check(lib().mslam_calib_backproject(DTYPES[X.dtype], X.shape[0], X.shape[1], X.shape[2], fx, fy, cx, cy, X.data_ptr(),
                                         _stream(X.device)), "mslam_calib_backproject")
     return X
@@ -275,7 +284,7 @@ def gn_linearize(plan: Plan, params: Params, T_wc, X_canon, idx, q, H=None, g=No
     _need(g, "g", torch.float32, 14 * E)
     _need(cost, "cost", torch.float64, E)
     _need(n_valid, "n_valid", torch.int32, E)
-    ws = plan.workspace(_lib.MSLAM_OP_LINEARIZE) if workspace is None else workspace
+    ws = _workspace(plan, _lib.MSLAM_OP_LINEARIZE, workspace)
     check(lib().mslam_gn_linearize(C.byref(params), plan.handle, DTYPES[dt], T_wc.data_ptr(), X_canon.data_ptr(),
                                    idx.data_ptr(), q.data_ptr(), H.data_ptr(), g.data_ptr(), cost.data_ptr(),
                                    n_valid.data_ptr(), ws.data_ptr(), ws.numel(),
@@ -319,7 +328,8 @@ def gn_track(plan: Plan, params: Params, dtype, T_wc, packed, n_iters: int, dev_
     _need(T_wc, "T_wc", torch.float64, 8 * plan.N)
     _need(packed, "packed", torch.uint8)
     st = torch.zeros(plan.G, dtype=torch.int32, device=dev) if dev_status is None else dev_status
-    ws = plan.workspace(_lib.MSLAM_OP_TRACK) if workspace is None else workspace
+    _need(st, "dev_status", torch.int32, plan.G)
+    ws = _workspace(plan, _lib.MSLAM_OP_TRACK, workspace)
     check(lib().mslam_gn_track(C.byref(params), plan.handle, DTYPES[dtype], T_wc.data_ptr(), packed.data_ptr(),
                                packed.numel(), int(n_iters), st.data_ptr(), ws.data_ptr(), ws.numel(), _stream(dev)),
           "mslam_gn_track")
@@ -342,9 +352,13 @@ def gn_linearize_packed(plan: Plan, params: Params, dtype, T_wc, packed, H=None,
     g = torch.empty(E, 14, dtype=torch.float32, device=dev) if g is None else g
     cost = torch.empty(E, dtype=torch.float64, device=dev) if cost is None else cost
     n_valid = torch.empty(E, dtype=torch.int32, device=dev) if n_valid is None else n_valid
+    _need(H, "H", torch.float32, 196 * E)
+    _need(g, "g", torch.float32, 14 * E)
+    _need(cost, "cost", torch.float64, E)
+    _need(n_valid, "n_valid", torch.int32, E)
     if dev_status is not None:
         _need(dev_status, "dev_status", torch.int32, plan.G)
-    ws = plan.workspace(_lib.MSLAM_OP_LINEARIZE) if workspace is None else workspace
+    ws = _workspace(plan, _lib.MSLAM_OP_LINEARIZE, workspace)
     check(lib().mslam_gn_linearize_packed(C.byref(params), plan.handle, DTYPES[dtype], T_wc.data_ptr(),
                                           packed.data_ptr(), packed.numel(), H.data_ptr(), g.data_ptr(),
                                           cost.data_ptr(), n_valid.data_ptr(), _ptr(dev_status), ws.data_ptr(),
@@ -364,7 +378,7 @@ def gn_solve(plan: Plan, params: Params, H, g, T_wc, tau=None, dev_status=None, 
     _need(dev_status, "dev_status", torch.int32, plan.G)
     if tau is not None:
         _need(tau, "tau", torch.float64, 7 * plan.N)
-    ws = plan.workspace(_lib.MSLAM_OP_SOLVE) if workspace is None else workspace
+    ws = _workspace(plan, _lib.MSLAM_OP_SOLVE, workspace)
     check(lib().mslam_gn_solve(C.byref(params), plan.handle, H.data_ptr(), g.data_ptr(), T_wc.data_ptr(),
                                _ptr(tau), dev_status.data_ptr(), ws.data_ptr(), ws.numel(), _stream(dev)),
           "mslam_gn_solve")
@@ -389,7 +403,10 @@ def gn_backward(plan: Plan, params: Params, T_wc, X_canon, idx, q, H=None, g=Non
     dL_dq = torch.empty(plan.edge_pixels, dtype=torch.float32, device=dev) if dL_dq is None else dL_dq
     if dev_status is None:
         dev_status = torch.zeros(plan.G, dtype=torch.int32, device=dev)
-    ws = plan.workspace(_lib.MSLAM_OP_BACKWARD) if workspace is None else workspace
+    _need(dL_dX, "dL_dX", torch.float32, 3 * plan.kf_pixels)
+    _need(dL_dq, "dL_dq", torch.float32, plan.edge_pixels)
+    _need(dev_status, "dev_status", torch.int32, plan.G)
+    ws = _workspace(plan, _lib.MSLAM_OP_BACKWARD, workspace)
     check(lib().mslam_gn_backward(C.byref(params), plan.handle, DTYPES[dt], T_wc.data_ptr(), X_canon.data_ptr(),
                                   idx.data_ptr(), q.data_ptr(), _ptr(H), _ptr(g), _ptr(dL_dtau), float(dL_dcost),
                                   dL_dX.data_ptr(), dL_dq.data_ptr(), dev_status.data_ptr(), ws.data_ptr(),
@@ -419,9 +436,13 @@ def gn_step_backward(plan: Plan, params: Params, T_wc, X_canon, idx, q, H, g, dL
     dL_dX = torch.empty(plan.kf_pixels, 3, dtype=torch.float32, device=dev) if dL_dX is None else dL_dX
     dL_dq = torch.empty(plan.edge_pixels, dtype=torch.float32, device=dev) if dL_dq is None else dL_dq
     dL_dT = torch.empty(plan.N, 8, dtype=torch.float64, device=dev) if dL_dT is None else dL_dT
+    _need(dL_dT, "dL_dT", torch.float64, 8 * plan.N)
     if dev_status is None:
         dev_status = torch.zeros(plan.G, dtype=torch.int32, device=dev)
-    ws = plan.workspace(_lib.MSLAM_OP_BACKWARD) if workspace is None else workspace
+    _need(dL_dX, "dL_dX", torch.float32, 3 * plan.kf_pixels)
+    _need(dL_dq, "dL_dq", torch.float32, plan.edge_pixels)
+    _need(dev_status, "dev_status", torch.int32, plan.G)
+    ws = _workspace(plan, _lib.MSLAM_OP_BACKWARD, workspace)
     check(lib().mslam_gn_step_backward(C.byref(params), plan.handle, DTYPES[dt], T_wc.data_ptr(),
                                        X_canon.data_ptr(), idx.data_ptr(), q.data_ptr(), H.data_ptr(), g.data_ptr(),
                                        _ptr(dL_dTnew), _ptr(dL_dtau), float(dL_dcost), dL_dX.data_ptr(),

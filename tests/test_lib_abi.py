@@ -126,6 +126,45 @@ def test_calls_reject_unuploaded_plan_and_null_args(L):
     assert st == _lib.MSLAM_ERR_ARG
 
 
+def test_every_compute_entry_refuses_bad_arguments_on_the_host(L):
+    """Each compute entry point checks its host-visible arguments (NULL
+    parameter block, plan or device pointer, a plan never uploaded, an
+    unsupported dtype or size) and returns MSLAM_ERR_ARG with a message
+    before it touches the device.  (The allocation-free linearisation looks
+    up its device first and is covered on the GPU.)"""
+    from paper_2412_12392_gb300 import _lib
+    p = plan([[8, 16], [8, 16]], [[0, 1]])
+    prm = _lib.Params()
+    L.mslam_default_params(C.byref(prm))
+    P = C.byref(prm)
+    N = None
+    calls = {
+        "gn_linearize": lambda: L.mslam_gn_linearize(P, p.handle, 0, *[N] * 8, N, 0, 0, N),
+        "gn_linearize, NULL params": lambda: L.mslam_gn_linearize(N, p.handle, 0, *[N] * 8, N, 0, 0, N),
+        "gn_pack": lambda: L.mslam_gn_pack(P, p.handle, 0, N, N, N, N, 0, N),
+        "gn_linearize_packed": lambda: L.mslam_gn_linearize_packed(P, p.handle, 1, N, N, 0, *[N] * 6, 0, 0, N),
+        "match_stats": lambda: L.mslam_match_stats(p.handle, N, N, N, N, 0, N),
+        "gn_backward": lambda: L.mslam_gn_backward(P, p.handle, 0, *[N] * 7, 1.0, N, N, N, N, 0, N),
+        "gn_step_backward": lambda: L.mslam_gn_step_backward(P, p.handle, 0, *[N] * 8, 1.0, *[N] * 5, 0, N),
+        "gn_solve, NULL plan": lambda: L.mslam_gn_solve(P, N, *[N] * 6, 0, N),
+        "match, NULL plan": lambda: L.mslam_match(P, N, 0, 16, *[N] * 11, -1, -1, N, 0, 0, N),
+        "desc_to_chunked, d = 8": lambda: L.mslam_desc_to_chunked(0, 8, 16, N, N, 16, N),
+        "ray_image, dtype 7": lambda: L.mslam_ray_image(7, 4, N, N, N),
+        "ray_image, NULL": lambda: L.mslam_ray_image(0, 4, N, N, N),
+        "calib_backproject, NULL": lambda: L.mslam_calib_backproject(0, 1, 8, 8, 1.0, 1.0, 4.0, 4.0, N, N),
+        "fuse, NULL": lambda: L.mslam_fuse(0, N, 0, 1, 16, N, N, N, N, N),
+        "keyframe_criterion, E < 0": lambda: L.mslam_keyframe_criterion(-1, N, N, N, 0.3, N),
+        "keyframe_criterion, NULL": lambda: L.mslam_keyframe_criterion(2, N, N, N, 0.3, N),
+        "plan_upload, NULL buffer": lambda: L.mslam_plan_upload(p.handle, N, 0, N),
+    }
+    for name, call in calls.items():
+        assert call() == _lib.MSLAM_ERR_ARG, name
+        assert _lib.last_error(), name
+    # the size queries answer 0 for a NULL plan or an unknown op
+    assert L.mslam_workspace_bytes(N, 0) == 0 and L.mslam_workspace_bytes(p.handle, 99) == 0
+    assert L.mslam_plan_kf_pixels(N) == 0 and L.mslam_gn_solve_launches(N) == 0
+
+
 def test_workspace_sizes_of_each_op(L):
     """mslam_workspace_bytes: the tracking op holds the tile partials (40
     floats per tile, 256-byte aligned) and one counter per edge; unknown ops

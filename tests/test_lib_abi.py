@@ -85,18 +85,22 @@ def symbolic_blocks(N, edges, order):
     return m + nnz, trips
 
 
-def test_symbolic_factorisation_matches_dense_elimination(L):
+@pytest.mark.parametrize("N,n_pairs,seed", [(8, 10, 3), (24, 40, 5), (64, 128, 2), (128, 300, 107)])
+def test_symbolic_factorisation_matches_dense_elimination(L, N, n_pairs, seed):
     import synth
-    w = synth.global_graph(N=64, n_pairs=128, H=8, W=8)
+    w = synth.global_graph(N=N, n_pairs=n_pairs, H=8, W=8, seed=seed)
     p = plan(w.kf_hw.numpy(), w.edges.numpy())
-    nb, nt = symbolic_blocks(64, w.edges.numpy(), p.order)
+    nb, nt = symbolic_blocks(N, w.edges.numpy(), p.order)
     assert (p.counts[0], p.counts[1]) == (nb, nt)
     # the ordering is a permutation of the non-fixed keyframes
-    assert sorted(p.order[1:]) == list(range(63))
-    # minimum degree beats the natural order on this loop graph
-    nat = np.r_[-1, np.arange(63)]
-    nb_nat, nt_nat = symbolic_blocks(64, w.edges.numpy(), nat)
-    assert nt < nt_nat
+    assert sorted(p.order[1:]) == list(range(N - 1))
+    # minimum degree is no worse than the natural order on these loop
+    # graphs, and strictly better once the loop closures give it a choice
+    nat = np.r_[-1, np.arange(N - 1)]
+    nb_nat, nt_nat = symbolic_blocks(N, w.edges.numpy(), nat)
+    assert nt <= nt_nat
+    if N >= 64:
+        assert nt < nt_nat
 
 
 @pytest.mark.parametrize("kf,edges,graph", [
